@@ -1,0 +1,22 @@
+"""Plain CPU FP64 oracle for the relativistic CD-ADC sigma product.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import anything under ``oracle/``. The
+product (the C-ABI library and its Python binding) never imports it, and it
+never imports the product: the two share no code. The only shared module is
+``synthetic`` (seeded random inputs, no arithmetic of the method).
+
+Modules
+-------
+``isr_series``  brute-force ISR in determinant space (pins every block order).
+``integrals``   antisymmetrised integrals from Cholesky vectors (Eq. 43),
+                MP amplitudes and the MP1/MP2 densities.
+``adc``         closed-form ADC(2), ADC(2)+x(3), ADC(3) blocks for IP and EA,
+                the explicit secular matrix, matrix-free sigma and diagonal.
+``davidson``    dense eigensolver and a plain Davidson for the lowest roots.
+``fns``         frozen-natural-spinor density, truncation, semicanonicalisation
+                and transformation of the Cholesky vectors (Eqs. 25-30).
+
+Every function is written for clarity, in FP64 complex, with no blocking or
+fusion beyond what the cited definition states.
+"""

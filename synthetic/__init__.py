@@ -1,0 +1,107 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the bench.
+
+This module draws random numbers only. It holds none of the method's
+arithmetic (no integrals, amplitudes or matrix elements), so the CPU oracle
+and the CUDA path can both consume its arrays without sharing any code.
+
+Draw recipe (stated once, used everywhere):
+
+* ``rng = numpy.random.default_rng(seed)``.
+* ``eps_occ``: ``nocc`` draws ``uniform(lo_o, hi_o)``, sorted ascending.
+* ``eps_vir``: ``nvir`` draws ``uniform(lo_v, hi_v)``, sorted ascending.
+* ``B``: ``[naux][nmo][nmo]`` complex, occupied spinors first. All diagonal
+  elements are drawn first as one ``standard_normal((naux, nmo))`` block,
+  scaled by ``sigma`` (real). The strict upper triangle is then drawn as one
+  ``standard_normal((naux, nmo*(nmo-1)/2, 2))`` block (row-major pair order),
+  scaled by ``sigma/sqrt(2)`` for the real and imaginary parts, i.e. a
+  circular complex Gaussian of variance ``sigma**2``. The lower triangle is
+  the complex conjugate, so every ``B[Q]`` is Hermitian, as the Cholesky
+  vectors of a Hermitian two-electron integral matrix in a spinor basis are.
+* Trial vectors: ``standard_normal`` real and imaginary planes, each
+  vector normalised to unit 2-norm.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["Problem", "make_problem", "random_vectors", "CONFIGS", "config_problem"]
+
+
+class Problem:
+    """Container for one synthetic input set (all arrays host numpy)."""
+
+    def __init__(self, B, eps_occ, eps_vir, kind, order, x, seed, name=""):
+        self.B = B
+        self.eps_occ = eps_occ
+        self.eps_vir = eps_vir
+        self.kind = kind
+        self.order = order
+        self.x = x
+        self.seed = seed
+        self.name = name
+
+    @property
+    def nocc(self):
+        return int(self.eps_occ.shape[0])
+
+    @property
+    def nvir(self):
+        return int(self.eps_vir.shape[0])
+
+    @property
+    def naux(self):
+        return int(self.B.shape[0])
+
+    def __repr__(self):
+        return (f"Problem({self.name!r}, kind={self.kind}, order={self.order}, x={self.x}, "
+                f"nocc={self.nocc}, nvir={self.nvir}, naux={self.naux}, seed={self.seed})")
+
+
+def make_problem(nocc, nvir, naux, seed=0, sigma=0.05, occ_range=(-2.0, -0.5),
+                 vir_range=(0.2, 3.0), kind="IP", order=3, x=1.0, name="",
+                 dtype=np.complex128):
+    rng = np.random.default_rng(seed)
+    eps_occ = np.sort(rng.uniform(occ_range[0], occ_range[1], nocc))
+    eps_vir = np.sort(rng.uniform(vir_range[0], vir_range[1], nvir))
+    nmo = nocc + nvir
+    B = np.empty((naux, nmo, nmo), dtype=dtype)
+    diag = rng.standard_normal((naux, nmo)) * sigma
+    iu, ju = np.triu_indices(nmo, k=1)
+    off = rng.standard_normal((naux, iu.shape[0], 2)) * (sigma / np.sqrt(2.0))
+    offc = off[..., 0] + 1j * off[..., 1]
+    del off
+    B[:, iu, ju] = offc
+    B[:, ju, iu] = np.conj(offc)
+    del offc
+    di = np.arange(nmo)
+    B[:, di, di] = diag
+    return Problem(B, eps_occ, eps_vir, kind, order, x, seed, name)
+
+
+def random_vectors(n, k, seed=1):
+    """``k`` complex unit vectors of length ``n`` as a ``[k][n]`` complex128 array."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((k, n)) + 1j * rng.standard_normal((k, n))
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    return X
+
+
+# The five named workloads (sizes, ranges, method variant). Names describe
+# what each is; the arrays are drawn by make_problem with the stated seed.
+CONFIGS = {
+    "ip3_o8_v24_q96": dict(nocc=8, nvir=24, naux=96, seed=0, occ_range=(-2.0, -0.5),
+                           vir_range=(0.2, 3.0), kind="IP", order=3, x=1.0, nroots=4, tol=1e-8),
+    "ea2x3_o40_v200_q1200": dict(nocc=40, nvir=200, naux=1200, seed=0, occ_range=(-3.0, -0.3),
+                                 vir_range=(0.1, 5.0), kind="EA", order=3, x=0.5, nroots=8, tol=1e-6),
+    "ee3_o60_v300_q1800": dict(nocc=60, nvir=300, naux=1800, seed=0, occ_range=(-3.0, -0.3),
+                               vir_range=(0.1, 5.0), kind="EE", order=3, x=1.0, nroots=6, tol=1e-6),
+    "ee2x3_o30_v150_q900": dict(nocc=30, nvir=150, naux=900, seed=0, occ_range=(-3.0, -0.3),
+                                vir_range=(0.1, 5.0), kind="EE", order=3, x=0.4, nroots=4, tol=1e-8),
+}
+
+
+def config_problem(name):
+    c = dict(CONFIGS[name])
+    c.pop("nroots")
+    c.pop("tol")
+    return make_problem(name=name, **c)
