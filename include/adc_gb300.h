@@ -1,0 +1,173 @@
+/*
+ * adc_gb300.h -- C ABI of the GB300 relativistic CD-ADC sigma library.
+ *
+ * The library computes the matrix-free product S = M X of the ISR secular
+ * matrix M of IP-ADC (1h + 2h1p) and EA-ADC (1p + 2p1h) at second order,
+ * third order, or the scaled ADC(2)+x(3) mixture (Sec. 2.1, Eqs. 10-12 of
+ * arXiv:2511.21640), solves M X = X Omega for the lowest roots by a block
+ * Davidson method, and builds the MP2 virtual density and frozen natural
+ * spinors (Sec. 2.4, Eqs. 25-30). Antisymmetrised integrals are assembled on
+ * the device from Cholesky vectors, <pq||rs> = sum_Q (B_pr B_qs - B_ps B_qr)
+ * (Sec. 2.5, Eq. 43).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Complex numbers are interleaved (re, im) doubles: adc_c128.
+ * Spinors are numbered occupied first: 0..nocc-1 occupied, nocc..nmo-1 virtual,
+ * nmo = nocc + nvir. The reference is canonical Hartree-Fock: the Fock matrix
+ * is diag(eps_occ, eps_vir).
+ * Pointer arguments may be host or device (CUDA unified addressing decides).
+ * Host pointers make the call synchronous; device pointers make it
+ * asynchronous on the context's stream, except where stated.
+ * The library copies every input it keeps; the caller keeps ownership of all
+ * buffers it passes. Every call returns ADC_OK (0) or a negative ADC_ERR_*
+ * code; no call aborts, traps or exits the process. adc_strerror() names
+ * the code and adc_last_error() gives the context's last message.
+ *
+ * Vector layout (dimension N = n1 + n2, basis-state phases of Eqs. 3-4):
+ *   IP: [ X_i (n1 = nocc) | X_(i<j),a (n2 = nocc(nocc-1)/2 * nvir) ]
+ *       state a+_a a_i a_j |Psi0>, a fastest, pairs row-major over i<j.
+ *   EA: [ X_a (n1 = nvir) | X_j,(a<b) (n2 = nocc * nvir(nvir-1)/2) ]
+ *       state a+_a a+_b a_j |Psi0>, pair fastest, pairs row-major over a<b.
+ * Blocks of k vectors are row-major [k][N].
+ */
+#ifndef ADC_GB300_H
+#define ADC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double re, im;
+} adc_c128;
+
+typedef struct adc_ctx adc_ctx;
+
+enum { ADC_IP = 0, ADC_EA = 1, ADC_EE = 2 };
+
+/* Arithmetic of a sigma product.
+ * ADC_PREC_FP64:   every operation in FP64 (CUDA cores).
+ * ADC_PREC_BF16X3: the dense contractions on the tensor cores (tcgen05) with
+ *   each FP64 operand split into two BF16 parts (hi + lo) and the three
+ *   products hi*hi + hi*lo + lo*hi accumulated in FP32; complex arithmetic by
+ *   the real 2x2 embedding. Diagonal terms stay FP64. */
+enum { ADC_PREC_FP64 = 0, ADC_PREC_BF16X3 = 1 };
+
+enum {
+  ADC_OK = 0,
+  ADC_ERR_ARG = -1,         /* invalid argument (sizes, kind, order, non-Hermitian B) */
+  ADC_ERR_OOM = -2,         /* device memory exhausted (or above opts.mem_limit) */
+  ADC_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  ADC_ERR_NOCONV = -4,      /* Davidson did not converge; best results returned */
+  ADC_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
+  ADC_ERR_UNSUPPORTED = -6, /* combination not built (e.g. EE) */
+  ADC_ERR_STATE = -7,       /* context not initialised / unusable */
+  ADC_ERR_NUMERIC = -8      /* NaN or Inf met in a residual or input */
+};
+
+typedef struct {
+  int precision;        /* default precision of adc_davidson's mixed phase */
+  void *stream;         /* cudaStream_t to run on; NULL = the context's own */
+  int block;            /* Davidson block size (new vectors per iteration), 0 = nroots */
+  int max_subspace;     /* Davidson subspace limit, 0 = automatic */
+  double herm_tol;      /* relative tolerance of the Hermiticity check of B */
+  int64_t mem_limit;    /* bytes the context may allocate, 0 = no limit */
+  int verbose;          /* 1 = per-iteration lines on stderr */
+} adc_opts;
+
+typedef struct {
+  int iterations;       /* Davidson iterations (mixed + FP64 phases) */
+  int iterations_fp64;  /* iterations of the FP64 refinement phase */
+  int sigma_calls;      /* vectors multiplied by M (all precisions) */
+  int sigma_calls_fp64; /* of those, in FP64 */
+  double time_total_s;  /* wall time of the call */
+  double time_sigma_s;  /* time inside sigma products */
+  double max_residual;  /* largest final FP64 residual norm over the roots */
+} adc_stats;
+
+/* Fills *opts with the defaults (precision FP64, own stream, herm_tol 1e-12). */
+int adc_opts_default(adc_opts *opts);
+
+/* Creates a context for one ADC problem and precomputes on the device
+ * everything that does not depend on the trial vectors: the first- and
+ * second-order MP amplitudes, the ground-state densities, the static main
+ * block (1h or 1p), the coupling block, the packed antisymmetrised ladder
+ * integrals (<ab||cd> for EA, <ij||kl> for IP), the ring integrals and the
+ * exact diagonal of M (Sec. 2.1 Eqs. 10-12, Sec. 2.5 Eq. 43).
+ *   B        [naux][nmo][nmo] Cholesky vectors, B[Q][p][q] = conj(B[Q][q][p]);
+ *            checked to opts->herm_tol * max|B|, else ADC_ERR_ARG.
+ *   eps_occ  [nocc], eps_vir [nvir]: orbital energies (Hartree); every
+ *            eps_occ must lie below every eps_vir, else ADC_ERR_ARG.
+ *   kind     ADC_IP or ADC_EA (ADC_EE gives ADC_ERR_UNSUPPORTED).
+ *   order    2 (ADC(2)) or 3 (ADC(2)+x(3); x = 1 is ADC(3), x = 0 is ADC(2)).
+ *   x        scale of every term ADC(3) adds to ADC(2) (used when order == 3).
+ *   opts     NULL for the defaults.
+ * On success *ctx owns device memory until adc_free(). Synchronous. */
+int adc_init(adc_ctx **ctx, const adc_c128 *B, int64_t naux,
+             const double *eps_occ, int64_t nocc, const double *eps_vir,
+             int64_t nvir, int kind, int order, double x,
+             const adc_opts *opts);
+
+/* n1, n2 of the vector layout above. */
+int adc_dims(const adc_ctx *ctx, int64_t *n1, int64_t *n2);
+
+/* S[r] = M X[r] for r < k (Eqs. 10-12). X, S: [k][N], host or device, not
+ * overlapping. precision: ADC_PREC_FP64 or ADC_PREC_BF16X3. Uses scratch
+ * device memory owned by the context (grown on demand). */
+int adc_sigma(adc_ctx *ctx, const adc_c128 *X, adc_c128 *S, int64_t k,
+              int precision);
+
+/* Exact diagonal of M as real numbers, [N] (host or device). */
+int adc_diagonal(adc_ctx *ctx, double *diag);
+
+/* Static main block (IP: [nocc][nocc], EA: [nvir][nvir], row-major). */
+int adc_main_block(adc_ctx *ctx, adc_c128 *M11);
+
+/* Lowest nroots eigenpairs of M (Eq. 10: M X = X Omega, X^H X = 1) by a
+ * block Davidson method. Subspace matrices, Rayleigh-Ritz, residual norms,
+ * orthogonalisation and denominators are always FP64. With
+ * precision = ADC_PREC_BF16X3 the trial-vector sigma products run on the
+ * tensor cores until the residuals stall near the split-precision floor;
+ * the method then switches to FP64 sigma products, keeping the subspace,
+ * until every FP64 residual norm is <= tol.
+ *   guess   NULL, or [nguess][N] starting vectors (orthonormalised inside).
+ *   omega   [nroots] eigenvalues, ascending (host or device).
+ *   Y       NULL or [nroots][N] eigenvectors.
+ *   err64   NULL or [nroots] FP64 residual norms ||M y - omega y||.
+ *   st      NULL or statistics.
+ * Returns ADC_ERR_NOCONV (with the best results written) if max_iter is hit. */
+int adc_davidson(adc_ctx *ctx, int nroots, double tol, int max_iter,
+                 int precision, const adc_c128 *guess, int64_t nguess,
+                 double *omega, adc_c128 *Y, double *err64, adc_stats *st);
+
+/* MP2 virtual-virtual density and frozen natural spinors (Eqs. 25-30):
+ *   D_ab = 1/2 sum_cij <ac||ij><ij||bc> / (eps_ij^ac eps_ij^bc)      [nvir][nvir]
+ *   D V = V eta, eta descending; keep eta_i >= eta_crit (n_keep of them);
+ *   F~ = V~^H diag(eps_vir) V~, F~ Z~ = Z~ eps~ (eps~ ascending);
+ *   U = V~ Z~                                                   [nvir][n_keep].
+ * Outputs (host or device): D, eta [nvir], V (NULL or [nvir][nvir], column i =
+ * natural spinor i), n_keep (host), U (NULL or [nvir][nvir] with the first
+ * n_keep columns used, row-major, leading dimension nvir), eps_new (NULL or
+ * [nvir], first n_keep used). Eigenvector phases are arbitrary. */
+int adc_fns_density(adc_ctx *ctx, adc_c128 *D, double *eta, adc_c128 *V,
+                    double eta_crit, int64_t *n_keep, adc_c128 *U,
+                    double *eps_new);
+
+/* Releases every resource of the context (NULL is accepted). */
+void adc_free(adc_ctx *ctx);
+
+/* Static string naming an ADC_ERR_* code. */
+const char *adc_strerror(int code);
+
+/* Last error message recorded by the context (or by the library when ctx is
+ * NULL); valid until the next call on the same context. */
+const char *adc_last_error(const adc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADC_GB300_H */

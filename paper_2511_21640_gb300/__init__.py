@@ -1,0 +1,225 @@
+"""Python binding of the GB300 relativistic CD-ADC library (libadc_gb300.so).
+
+Argument marshalling only: every arithmetic step runs in the library's CUDA
+kernels. Inputs may be numpy arrays (host) or torch tensors (host or CUDA);
+complex arrays must be complex128 and C-contiguous. There is no CPU fallback:
+importing this package fails when the compiled library is missing.
+
+The C ABI is declared in ``include/adc_gb300.h``; the names here mirror it:
+``Context(...)`` wraps ``adc_init``/``adc_free``, ``Context.sigma`` wraps
+``adc_sigma``, ``Context.davidson`` wraps ``adc_davidson``,
+``Context.fns_density`` wraps ``adc_fns_density``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libadc_gb300.so")
+
+ADC_IP, ADC_EA, ADC_EE = 0, 1, 2
+ADC_PREC_FP64, ADC_PREC_BF16X3 = 0, 1
+KINDS = {"IP": ADC_IP, "EA": ADC_EA, "EE": ADC_EE}
+PRECISIONS = {"fp64": ADC_PREC_FP64, "bf16x3": ADC_PREC_BF16X3}
+ERRORS = {0: "ADC_OK", -1: "ADC_ERR_ARG", -2: "ADC_ERR_OOM", -3: "ADC_ERR_CUDA", -4: "ADC_ERR_NOCONV",
+          -5: "ADC_ERR_TIMEOUT", -6: "ADC_ERR_UNSUPPORTED", -7: "ADC_ERR_STATE", -8: "ADC_ERR_NUMERIC"}
+
+
+class AdcError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"{ERRORS.get(code, code)}: {message}")
+        self.code = code
+
+
+class adc_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("block", ctypes.c_int),
+                ("max_subspace", ctypes.c_int), ("herm_tol", ctypes.c_double),
+                ("mem_limit", ctypes.c_int64), ("verbose", ctypes.c_int)]
+
+
+class adc_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("iterations_fp64", ctypes.c_int),
+                ("sigma_calls", ctypes.c_int), ("sigma_calls_fp64", ctypes.c_int),
+                ("time_total_s", ctypes.c_double), ("time_sigma_s", ctypes.c_double),
+                ("max_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(or python paper_2511_21640_gb300/build.py)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I64, I, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "adc_opts_default": (I, [ctypes.POINTER(adc_opts)]),
+        "adc_init": (I, [ctypes.POINTER(P), P, I64, P, I64, P, I64, I, I, D, ctypes.POINTER(adc_opts)]),
+        "adc_dims": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+        "adc_sigma": (I, [P, P, P, I64, I]),
+        "adc_diagonal": (I, [P, P]),
+        "adc_main_block": (I, [P, P]),
+        "adc_davidson": (I, [P, I, D, I, I, P, I64, P, P, P, ctypes.POINTER(adc_stats)]),
+        "adc_fns_density": (I, [P, P, P, P, D, ctypes.POINTER(I64), P, P]),
+        "adc_free": (None, [P]),
+        "adc_strerror": (ctypes.c_char_p, [I]),
+        "adc_last_error": (ctypes.c_char_p, [P]),
+        "adc_diag_gemm": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _check(rc, ctx=None):
+    if rc != 0:
+        msg = lib.adc_last_error(ctx)
+        raise AdcError(rc, msg.decode() if msg else "")
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """Raw pointer of a C-contiguous array of the given numpy dtype."""
+    if a is None:
+        return None
+    if _is_torch(a):
+        import torch
+        want = {np.complex128: torch.complex128, np.float64: torch.float64}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _empty_like_kind(ref, shape, dtype):
+    if ref is not None and _is_torch(ref):
+        import torch
+        tdt = {np.complex128: torch.complex128, np.float64: torch.float64}[dtype]
+        return torch.empty(shape, dtype=tdt, device=ref.device)
+    return np.empty(shape, dtype=dtype)
+
+
+class Context:
+    """One ADC problem on the GPU (``adc_init``)."""
+
+    def __init__(self, B, eps_occ, eps_vir, kind="IP", order=3, x=1.0, precision="fp64", stream=None,
+                 block=0, max_subspace=0, herm_tol=1e-12, mem_limit=0, verbose=False):
+        o = adc_opts()
+        lib.adc_opts_default(ctypes.byref(o))
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.stream = stream
+        o.block = block
+        o.max_subspace = max_subspace
+        o.herm_tol = herm_tol
+        o.mem_limit = mem_limit
+        o.verbose = 1 if verbose else 0
+        naux, nmo, nmo2 = B.shape
+        nocc, nvir = eps_occ.shape[0], eps_vir.shape[0]
+        if nmo != nmo2 or nmo != nocc + nvir:
+            raise ValueError("B must be [naux][nmo][nmo] with nmo = nocc + nvir")
+        self._h = ctypes.c_void_p()
+        self.kind = kind
+        self.nocc, self.nvir, self.naux = nocc, nvir, naux
+        rc = lib.adc_init(ctypes.byref(self._h), _ptr(B, np.complex128), naux, _ptr(eps_occ, np.float64), nocc,
+                          _ptr(eps_vir, np.float64), nvir, KINDS[kind] if isinstance(kind, str) else kind,
+                          order, float(x), ctypes.byref(o))
+        _check(rc)
+        n1, n2 = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.adc_dims(self._h, ctypes.byref(n1), ctypes.byref(n2)), self._h)
+        self.n1, self.n2 = n1.value, n2.value
+        self.N = self.n1 + self.n2
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.adc_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def sigma(self, X, precision="fp64", out=None):
+        """S = M X for X of shape [k][N] (``adc_sigma``)."""
+        k = X.shape[0] if X.ndim == 2 else 1
+        if X.shape[-1] != self.N:
+            raise ValueError("last dimension of X must be N")
+        S = out if out is not None else _empty_like_kind(X, tuple(X.shape), np.complex128)
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _check(lib.adc_sigma(self._h, _ptr(X, np.complex128), _ptr(S, np.complex128), k, p), self._h)
+        return S
+
+    def diagonal(self):
+        d = np.empty(self.N, dtype=np.float64)
+        _check(lib.adc_diagonal(self._h, _ptr(d, np.float64)), self._h)
+        return d
+
+    def main_block(self):
+        m = np.empty((self.n1, self.n1), dtype=np.complex128)
+        _check(lib.adc_main_block(self._h, _ptr(m, np.complex128)), self._h)
+        return m
+
+    def davidson(self, nroots, tol=1e-8, max_iter=200, precision="fp64", guess=None, want_vectors=True,
+                 raise_on_noconv=True):
+        """Lowest roots (``adc_davidson``): returns (omega, Y or None, err64, stats dict, rc)."""
+        omega = np.empty(nroots, dtype=np.float64)
+        err = np.empty(nroots, dtype=np.float64)
+        Y = np.empty((nroots, self.N), dtype=np.complex128) if want_vectors else None
+        st = adc_stats()
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        ng = 0 if guess is None else guess.shape[0]
+        rc = lib.adc_davidson(self._h, nroots, float(tol), int(max_iter), p, _ptr(guess, np.complex128), ng,
+                              _ptr(omega, np.float64), _ptr(Y, np.complex128) if Y is not None else None,
+                              _ptr(err, np.float64), ctypes.byref(st))
+        if rc != 0 and not (rc == -4 and not raise_on_noconv):
+            _check(rc, self._h)
+        return omega, Y, err, st.as_dict(), rc
+
+    def fns_density(self, eta_crit):
+        """MP2 virtual density and frozen natural spinors (``adc_fns_density``)."""
+        nvir = self.nvir
+        D = np.empty((nvir, nvir), dtype=np.complex128)
+        eta = np.empty(nvir, dtype=np.float64)
+        V = np.empty((nvir, nvir), dtype=np.complex128)
+        U = np.empty((nvir, nvir), dtype=np.complex128)
+        en = np.empty(nvir, dtype=np.float64)
+        nk = ctypes.c_int64()
+        _check(lib.adc_fns_density(self._h, _ptr(D, np.complex128), _ptr(eta, np.float64),
+                                   _ptr(V, np.complex128), float(eta_crit), ctypes.byref(nk),
+                                   _ptr(U, np.complex128), _ptr(en, np.float64)), self._h)
+        k = nk.value
+        return {"D": D, "eta": eta, "V": V, "n_keep": k, "U": U[:, :k].copy(), "eps_new": en[:k].copy()}
+
+
+def diag_gemm(which, M, N, K, seed=1, reps=3):
+    """Accuracy and time of one contraction kernel (``adc_diag_gemm``): (rel_err, ms)."""
+    e, t = ctypes.c_double(), ctypes.c_double()
+    rc = lib.adc_diag_gemm(int(which), int(M), int(N), int(K), int(seed), int(reps), ctypes.byref(e),
+                           ctypes.byref(t))
+    _check(rc)
+    return e.value, t.value
+
+
+__all__ = ["Context", "AdcError", "diag_gemm", "lib", "LIB_PATH", "ADC_IP", "ADC_EA", "ADC_EE",
+           "ADC_PREC_FP64", "ADC_PREC_BF16X3"]

@@ -1,0 +1,312 @@
+// C ABI of the library (declared in include/adc_gb300.h). Every entry point
+// converts internal errors into negative return codes; nothing aborts.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ctx.cuh"
+#include "tc_gemm.cuh"
+
+namespace adc {
+int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision, const cplx *guess,
+                 int64_t nguess, double *omega, cplx *Yout, double *err64, adc_stats *st_out);
+void fns_run(adc_ctx *c, cplx *D, double *eta, cplx *Vout, double eta_crit, int64_t *n_keep, cplx *U,
+             double *eps_new);
+}  // namespace adc
+
+using namespace adc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// device view of a caller input (copied when it lives on the host)
+struct DevIn {
+  DBuf buf;
+  const void *p = nullptr;
+  DevIn(Exec &ex, const void *src, size_t bytes) {
+    if (!src || !bytes) return;
+    if (is_device_ptr(src)) { p = src; return; }
+    buf = DBuf(ex, bytes);
+    ADC_CUDA(cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, ex.stream));
+    p = buf.p;
+  }
+};
+
+// device target for a caller output (copied back at finish() when on the host)
+struct DevOut {
+  DBuf buf;
+  void *user = nullptr, *p = nullptr;
+  size_t bytes = 0;
+  bool host = false;
+  DevOut(Exec &ex, void *dst, size_t b) : user(dst), bytes(b) {
+    if (!dst || !b) return;
+    if (is_device_ptr(dst)) { p = dst; return; }
+    host = true;
+    buf = DBuf(ex, b);
+    p = buf.p;
+  }
+  void finish(Exec &ex) {
+    if (host && user) ADC_CUDA(cudaMemcpyAsync(user, p, bytes, cudaMemcpyDeviceToHost, ex.stream));
+  }
+};
+
+__device__ inline void atomic_max_nonneg(double *addr, double v) {
+  atomicMax((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_herm_check(const cplx *B, int64_t Q, int64_t n, double *out) {
+  const int64_t total = Q * n * n;
+  double dev = 0.0, mag = 0.0;
+  bool bad = false;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = idx % n, r = idx / n;
+    int64_t p = r % n, Qi = r / n;
+    cplx a = B[idx], b = B[(Qi * n + q) * n + p];
+    if (!isfinite(a.x) || !isfinite(a.y)) bad = true;
+    dev = fmax(dev, fmax(fabs(a.x - b.x), fabs(a.y + b.y)));
+    mag = fmax(mag, fmax(fabs(a.x), fabs(a.y)));
+  }
+  if (bad) dev = 1e300;
+  atomic_max_nonneg(out, dev);
+  atomic_max_nonneg(out + 1, mag);
+}
+
+int fail(adc_ctx *c, const std::exception &e, int code) {
+  if (c) c->err = e.what();
+  g_last_error = e.what();
+  return code;
+}
+
+#define ADC_API_TRY try {
+#define ADC_API_CATCH(ctxp)                                           \
+  }                                                                   \
+  catch (const adc::Error &e) { return fail((ctxp), e, e.code); }     \
+  catch (const std::bad_alloc &e) { return fail((ctxp), e, ADC_ERR_OOM); } \
+  catch (const std::exception &e) { return fail((ctxp), e, ADC_ERR_CUDA); }
+
+}  // namespace
+
+adc_ctx::~adc_ctx() {
+  release_tc(this);
+  scratch.reset();
+  t1.reset(); W.reset(); Glad.reset(); diag.reset(); d2.reset(); Cpl.reset(); M11.reset();
+  B.reset(); eo.reset(); ev.reset();
+  if (ex.stream) cudaStreamSynchronize(ex.stream);
+  if (own_stream && ex.stream) cudaStreamDestroy(ex.stream);
+}
+
+extern "C" {
+
+int adc_opts_default(adc_opts *o) {
+  if (!o) return ADC_ERR_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = ADC_PREC_FP64;
+  o->herm_tol = 1e-12;
+  return ADC_OK;
+}
+
+int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_occ, int64_t nocc,
+             const double *eps_vir, int64_t nvir, int kind, int order, double x,
+             const adc_opts *opts) {
+  if (!out) return ADC_ERR_ARG;
+  *out = nullptr;
+  adc_ctx *c = nullptr;
+  try {
+    if (kind == ADC_EE) throw Error(ADC_ERR_UNSUPPORTED, "EE-ADC is not built");
+    if (kind != ADC_IP && kind != ADC_EA) throw Error(ADC_ERR_ARG, "kind must be ADC_IP or ADC_EA");
+    if (order != 2 && order != 3) throw Error(ADC_ERR_ARG, "order must be 2 or 3");
+    if (!B || !eps_occ || !eps_vir) throw Error(ADC_ERR_ARG, "NULL input");
+    if (naux < 1 || nocc < 1 || nvir < 1) throw Error(ADC_ERR_ARG, "sizes must be positive");
+    if (!std::isfinite(x)) throw Error(ADC_ERR_ARG, "x must be finite");
+    if (kind == ADC_IP && nocc < 2) throw Error(ADC_ERR_ARG, "IP needs nocc >= 2");
+    if (kind == ADC_EA && nvir < 2) throw Error(ADC_ERR_ARG, "EA needs nvir >= 2");
+    c = new adc_ctx();
+    if (opts) c->opts = *opts;
+    else adc_opts_default(&c->opts);
+    if (c->opts.herm_tol <= 0.0) c->opts.herm_tol = 1e-12;
+    c->kind = kind;
+    c->order = order;
+    c->x = (order == 3) ? x : 0.0;
+    c->o = nocc; c->v = nvir; c->Q = naux; c->nmo = nocc + nvir;
+    if (kind == ADC_IP) { c->n1 = nocc; c->n2 = npairs(nocc) * nvir; }
+    else { c->n1 = nvir; c->n2 = nocc * npairs(nvir); }
+    c->N = c->n1 + c->n2;
+    c->ex.mem_limit = c->opts.mem_limit;
+    if (c->opts.stream) {
+      c->ex.stream = (cudaStream_t)c->opts.stream;
+    } else {
+      ADC_CUDA(cudaStreamCreateWithFlags(&c->ex.stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    Exec &ex = c->ex;
+    // orbital energies
+    std::vector<double> eo(nocc), ev(nvir);
+    if (is_device_ptr(eps_occ)) ADC_CUDA(cudaMemcpy(eo.data(), eps_occ, nocc * 8, cudaMemcpyDeviceToHost));
+    else std::memcpy(eo.data(), eps_occ, nocc * 8);
+    if (is_device_ptr(eps_vir)) ADC_CUDA(cudaMemcpy(ev.data(), eps_vir, nvir * 8, cudaMemcpyDeviceToHost));
+    else std::memcpy(ev.data(), eps_vir, nvir * 8);
+    for (double e : eo) if (!std::isfinite(e)) throw Error(ADC_ERR_ARG, "non-finite eps_occ");
+    for (double e : ev) if (!std::isfinite(e)) throw Error(ADC_ERR_ARG, "non-finite eps_vir");
+    if (*std::max_element(eo.begin(), eo.end()) >= *std::min_element(ev.begin(), ev.end()))
+      throw Error(ADC_ERR_ARG, "every occupied energy must lie below every virtual energy");
+    c->eo = DBuf(ex, nocc * sizeof(double));
+    c->ev = DBuf(ex, nvir * sizeof(double));
+    ADC_CUDA(cudaMemcpyAsync(c->eo.p, eo.data(), nocc * 8, cudaMemcpyHostToDevice, ex.stream));
+    ADC_CUDA(cudaMemcpyAsync(c->ev.p, ev.data(), nvir * 8, cudaMemcpyHostToDevice, ex.stream));
+    // Cholesky vectors
+    const int64_t nb = naux * c->nmo * c->nmo;
+    c->B = cbuf(ex, nb);
+    ADC_CUDA(cudaMemcpyAsync(c->B.p, B, nb * sizeof(cplx),
+                             is_device_ptr(B) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ex.stream));
+    {
+      DBuf chk(ex, 2 * sizeof(double));
+      fill_zero(ex, chk.p, chk.bytes);
+      k_herm_check<<<grid1d(nb, 256) > 4096 ? 4096 : grid1d(nb, 256), 256, 0, ex.stream>>>(c->B.c(), naux,
+                                                                                         c->nmo, chk.d());
+      ADC_CHECK_LAUNCH();
+      double h[2];
+      ADC_CUDA(cudaMemcpyAsync(h, chk.p, sizeof(h), cudaMemcpyDeviceToHost, ex.stream));
+      ADC_CUDA(cudaStreamSynchronize(ex.stream));
+      if (!(h[0] <= c->opts.herm_tol * std::max(h[1], 1e-300)))
+        throw Error(ADC_ERR_ARG, "B is not Hermitian in (p,q) (max deviation " + std::to_string(h[0]) +
+                                     ", max |B| " + std::to_string(h[1]) + ")");
+    }
+    setup_operators(c);
+    *out = c;
+    return ADC_OK;
+  } catch (const adc::Error &e) {
+    g_last_error = e.what();
+    delete c;
+    return e.code;
+  } catch (const std::bad_alloc &e) {
+    g_last_error = e.what();
+    delete c;
+    return ADC_ERR_OOM;
+  } catch (const std::exception &e) {
+    g_last_error = e.what();
+    delete c;
+    return ADC_ERR_CUDA;
+  }
+}
+
+int adc_dims(const adc_ctx *c, int64_t *n1, int64_t *n2) {
+  if (!c) return ADC_ERR_STATE;
+  if (n1) *n1 = c->n1;
+  if (n2) *n2 = c->n2;
+  return ADC_OK;
+}
+
+int adc_sigma(adc_ctx *c, const adc_c128 *X, adc_c128 *S, int64_t k, int precision) {
+  if (!c) return ADC_ERR_STATE;
+  if (k < 0 || (k > 0 && (!X || !S))) return ADC_ERR_ARG;
+  if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3) return ADC_ERR_ARG;
+  if (k == 0) return ADC_OK;
+  ADC_API_TRY
+  const size_t bytes = (size_t)k * c->N * sizeof(cplx);
+  DevIn xin(c->ex, X, bytes);
+  DevOut sout(c->ex, S, bytes);
+  sigma(c, (const cplx *)xin.p, (cplx *)sout.p, k, precision);
+  sout.finish(c->ex);
+  if (sout.host || xin.buf.p) ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
+int adc_diagonal(adc_ctx *c, double *diag) {
+  if (!c) return ADC_ERR_STATE;
+  if (!diag) return ADC_ERR_ARG;
+  ADC_API_TRY
+  ADC_CUDA(cudaMemcpyAsync(diag, c->diag.p, c->N * sizeof(double), cudaMemcpyDefault, c->ex.stream));
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
+int adc_main_block(adc_ctx *c, adc_c128 *M11) {
+  if (!c) return ADC_ERR_STATE;
+  if (!M11) return ADC_ERR_ARG;
+  ADC_API_TRY
+  ADC_CUDA(cudaMemcpyAsync(M11, c->M11.p, c->n1 * c->n1 * sizeof(cplx), cudaMemcpyDefault, c->ex.stream));
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
+int adc_davidson(adc_ctx *c, int nroots, double tol, int max_iter, int precision, const adc_c128 *guess,
+                 int64_t nguess, double *omega, adc_c128 *Y, double *err64, adc_stats *st) {
+  if (!c) return ADC_ERR_STATE;
+  if (!omega || nroots < 1 || max_iter < 1) return ADC_ERR_ARG;
+  ADC_API_TRY
+  const size_t vb = (size_t)nroots * c->N * sizeof(cplx);
+  DevIn gin(c->ex, guess, guess ? (size_t)nguess * c->N * sizeof(cplx) : 0);
+  DevOut yout(c->ex, Y, Y ? vb : 0);
+  std::vector<double> om(nroots), er(nroots);
+  int rc = davidson_run(c, nroots, tol, max_iter, precision, (const cplx *)gin.p, guess ? nguess : 0,
+                        om.data(), (cplx *)yout.p, er.data(), st);
+  yout.finish(c->ex);
+  ADC_CUDA(cudaMemcpyAsync(omega, om.data(), nroots * sizeof(double), cudaMemcpyDefault, c->ex.stream));
+  if (err64) ADC_CUDA(cudaMemcpyAsync(err64, er.data(), nroots * sizeof(double), cudaMemcpyDefault, c->ex.stream));
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  if (rc == ADC_ERR_NOCONV) c->err = "Davidson did not converge within max_iter";
+  return rc;
+  ADC_API_CATCH(c)
+}
+
+int adc_fns_density(adc_ctx *c, adc_c128 *D, double *eta, adc_c128 *V, double eta_crit, int64_t *n_keep,
+                    adc_c128 *U, double *eps_new) {
+  if (!c) return ADC_ERR_STATE;
+  if (!n_keep) return ADC_ERR_ARG;
+  ADC_API_TRY
+  const int64_t v = c->v;
+  DevOut dD(c->ex, D, D ? v * v * sizeof(cplx) : 0);
+  DevOut dE(c->ex, eta, eta ? v * sizeof(double) : 0);
+  DevOut dV(c->ex, V, V ? v * v * sizeof(cplx) : 0);
+  DevOut dU(c->ex, U, U ? v * v * sizeof(cplx) : 0);
+  DevOut dN(c->ex, eps_new, eps_new ? v * sizeof(double) : 0);
+  if (dU.p) fill_zero(c->ex, dU.p, dU.bytes);
+  if (dN.p) fill_zero(c->ex, dN.p, dN.bytes);
+  int64_t nk = 0;
+  fns_run(c, (cplx *)dD.p, (double *)dE.p, (cplx *)dV.p, eta_crit, &nk, (cplx *)dU.p, (double *)dN.p);
+  dD.finish(c->ex); dE.finish(c->ex); dV.finish(c->ex); dU.finish(c->ex); dN.finish(c->ex);
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  *n_keep = nk;
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
+void adc_free(adc_ctx *c) { delete c; }
+
+const char *adc_strerror(int code) {
+  switch (code) {
+    case ADC_OK: return "ADC_OK";
+    case ADC_ERR_ARG: return "ADC_ERR_ARG: invalid argument";
+    case ADC_ERR_OOM: return "ADC_ERR_OOM: out of device memory";
+    case ADC_ERR_CUDA: return "ADC_ERR_CUDA: CUDA runtime error";
+    case ADC_ERR_NOCONV: return "ADC_ERR_NOCONV: Davidson did not converge";
+    case ADC_ERR_TIMEOUT: return "ADC_ERR_TIMEOUT: bounded device wait gave up";
+    case ADC_ERR_UNSUPPORTED: return "ADC_ERR_UNSUPPORTED: combination not built";
+    case ADC_ERR_STATE: return "ADC_ERR_STATE: context not usable";
+    case ADC_ERR_NUMERIC: return "ADC_ERR_NUMERIC: NaN or Inf encountered";
+    default: return "unknown ADC error code";
+  }
+}
+
+const char *adc_last_error(const adc_ctx *c) {
+  if (c && !c->err.empty()) return c->err.c_str();
+  return g_last_error.c_str();
+}
+
+}  // extern "C"

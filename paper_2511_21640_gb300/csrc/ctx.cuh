@@ -1,0 +1,50 @@
+// Context of one ADC problem: sizes, device operators, caches.
+#pragma once
+
+#include <memory>
+
+#include "tensor.cuh"
+
+namespace adc {
+struct TcCache;  // split-precision operator copies (tc_gemm.cu)
+}
+
+struct adc_ctx {
+  adc::Exec ex;
+  bool own_stream = false;
+  int kind = 0, order = 2;
+  double x = 0.0;   // the x of ADC(2)+x(3); 0 for order 2
+  int64_t o = 0, v = 0, Q = 0, nmo = 0, n1 = 0, n2 = 0, N = 0;
+  adc_opts opts;
+  std::string err;
+
+  // inputs on the device
+  adc::DBuf B;    // [Q][nmo][nmo]
+  adc::DBuf eo, ev;
+
+  // operators of the sigma product (FP64)
+  adc::DBuf M11;   // [n1][n1] static main block (all orders, x applied)
+  adc::DBuf Cpl;   // [n1][n2] coupling block, first order + x * second order
+  adc::DBuf d2;    // [n2] zeroth-order satellite diagonal (real)
+  adc::DBuf diag;  // [N] exact diagonal of M (real)
+  adc::DBuf Glad;  // ladder integrals, packed: EA [Pv][Pv] <ab||cd>; IP [Po][Po] <kl||ij>
+  adc::DBuf W;     // ring integrals [o][v][o][v]: W[j][a][k][c] = <ak||cj>
+  adc::DBuf t1;    // first-order doubles [o][o][v][v]
+
+  // split-precision copies for the tensor-core sigma
+  std::unique_ptr<adc::TcCache> tc;
+
+  // per-call scratch, grown on demand
+  adc::DBuf scratch;
+
+  ~adc_ctx();
+};
+
+namespace adc {
+void setup_operators(adc_ctx *c);
+void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
+void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
+void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision);
+void release_tc(adc_ctx *c);
+cplx *scratch(adc_ctx *c, int64_t ncplx);
+}  // namespace adc

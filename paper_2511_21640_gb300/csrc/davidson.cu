@@ -1,0 +1,372 @@
+// Block Davidson for the lowest roots of M (Eq. 10: M X = X Omega, X^H X = 1).
+//
+// Subspace matrices, Rayleigh-Ritz (device Jacobi), residual norms, Gram-Schmidt
+// and the diagonal preconditioner are FP64 throughout. With the split-precision
+// sigma the method runs in two phases:
+//   1. plain Davidson with tensor-core sigma products until the residual norms
+//      stop decreasing (the split-precision floor);
+//   2. refinement: the subspace is collapsed onto the current Ritz vectors and
+//      their sigma is recomputed in FP64, so that sigma(y + delta) =
+//      sigma64(y) + sigma_mixed(delta); new correction vectors keep using the
+//      tensor-core product. Every collapse (subspace full, stall, or apparent
+//      convergence) recomputes sigma64 of the Ritz vectors, and convergence is
+//      only accepted on FP64 residuals ||sigma64(y) - omega y|| <= tol.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+
+#include "ctx.cuh"
+#include "eig.cuh"
+
+namespace adc {
+
+namespace {
+
+__global__ void k_hermitize(const cplx *G, int ldg, int m, cplx *H, int ldh) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m * m) return;
+  int i = idx / m, j = idx % m;
+  cplx a = G[(int64_t)i * ldg + j], b = G[(int64_t)j * ldg + i];
+  H[(int64_t)i * ldh + j] = cmake(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+}
+
+// G[m0 + i][j] = conj(G[j][m0 + i]) for j < m0
+__global__ void k_fill_lower(cplx *G, int ldg, int m0, int na) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= na * m0) return;
+  int i = idx / m0, j = idx % m0;
+  cplx a = G[(int64_t)j * ldg + m0 + i];
+  G[(int64_t)(m0 + i) * ldg + j] = cmake(a.x, -a.y);
+}
+
+// R[r] = SY[r] - w[r] Y[r]
+__global__ void k_residual(const cplx *SY, const cplx *Y, const double *w, int64_t k, int64_t n,
+                           cplx *R) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < k * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = idx / n;
+    cplx s = SY[idx], y = Y[idx];
+    R[idx] = cmake(s.x - w[r] * y.x, s.y - w[r] * y.y);
+  }
+}
+
+// out[r] = || X[r] ||_2, one block per row
+__global__ void k_row_norms(const cplx *X, int64_t n, int64_t ld, double *out) {
+  __shared__ double red[32];
+  const cplx *x = X + blockIdx.x * ld;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += x[i].x * x[i].x + x[i].y * x[i].y;
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s);
+  }
+}
+
+// T[r] = R[r] / (w[r] - diag), |denominator| floored at 1e-4
+__global__ void k_precondition(const cplx *R, const double *w, const int *rows, const double *diag,
+                               int64_t nt, int64_t n, cplx *T) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nt * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = idx / n, i = idx % n;
+    int r = rows[t];
+    double den = w[r] - diag[i];
+    if (fabs(den) < 1e-4) den = (den < 0.0) ? -1e-4 : 1e-4;
+    cplx v = R[(int64_t)r * n + i];
+    T[idx] = cmake(v.x / den, v.y / den);
+  }
+}
+
+__global__ void k_scale_row(cplx *X, int64_t n, const double *nrm) {
+  double s = 1.0 / nrm[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    X[i].x *= s;
+    X[i].y *= s;
+  }
+}
+
+__global__ void k_unit_vectors(cplx *V, int64_t n, const int64_t *idx, int k) {
+  int r = blockIdx.x;
+  if (r >= k) return;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) V[(int64_t)r * n + i] = cmake(0.0, 0.0);
+  __syncthreads();
+  if (threadIdx.x == 0) V[(int64_t)r * n + idx[r]] = cmake(1.0, 0.0);
+}
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double s() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+}  // namespace
+
+struct Davidson {
+  adc_ctx *c;
+  Exec &ex;
+  int64_t N;
+  int nroots, mmax;
+  DBuf V, AV, G, H, Cv, w, T, Y, SY, R, nrm, rowsb, info, tmp;
+  adc_stats st{};
+  double tsig = 0.0;
+  int m = 0;
+
+  Davidson(adc_ctx *c_, int nr, int mmax_) : c(c_), ex(c_->ex), N(c_->N), nroots(nr), mmax(mmax_) {
+    V = cbuf(ex, (int64_t)mmax * N);
+    AV = cbuf(ex, (int64_t)mmax * N);
+    G = cbuf(ex, (int64_t)mmax * mmax);
+    H = cbuf(ex, (int64_t)mmax * mmax);
+    Cv = cbuf(ex, (int64_t)mmax * mmax);
+    w = DBuf(ex, mmax * sizeof(double));
+    T = cbuf(ex, (int64_t)nr * N);
+    Y = cbuf(ex, (int64_t)nr * N);
+    SY = cbuf(ex, (int64_t)nr * N);
+    R = cbuf(ex, (int64_t)nr * N);
+    nrm = DBuf(ex, mmax * sizeof(double));
+    rowsb = DBuf(ex, mmax * sizeof(int));
+    info = DBuf(ex, 16);
+    tmp = cbuf(ex, (int64_t)mmax * mmax);
+  }
+
+  void apply_sigma(const cplx *X, cplx *S, int64_t k, int prec) {
+    Timer t;
+    sigma(c, X, S, k, prec);
+    ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    tsig += t.s();
+    st.sigma_calls += (int)k;
+    if (prec == ADC_PREC_FP64) st.sigma_calls_fp64 += (int)k;
+  }
+
+  // G[0:m+na][m:m+na] = V^H AV[m:m+na], lower part by Hermiticity
+  void extend_projection(int m0, int na) {
+    int mt = m0 + na;
+    zgemm(ex, mt, na, N, 1, C1(), V.c(), 0, N, 1, true, AV.c() + (int64_t)m0 * N, 0, 1, N, false,
+          C0(), G.c() + m0, 0, mmax, 1);
+    if (m0 > 0) {
+      k_fill_lower<<<(na * m0 + 255) / 256, 256, 0, ex.stream>>>(G.c(), mmax, m0, na);
+      ADC_CHECK_LAUNCH();
+    }
+  }
+
+  std::vector<double> row_norms(const cplx *X, int k) {
+    std::vector<double> h(k);
+    if (!k) return h;
+    k_row_norms<<<k, 512, 0, ex.stream>>>(X, N, N, nrm.d());
+    ADC_CHECK_LAUNCH();
+    ADC_CUDA(cudaMemcpyAsync(h.data(), nrm.d(), k * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
+    ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    return h;
+  }
+
+  // project out span(V[0:m]) from T[0:nt] twice, then MGS within T; returns the
+  // number of accepted (orthonormal) vectors, compacted to the front of T
+  int orthonormalise(int nt) {
+    std::vector<double> n0 = row_norms(T.c(), nt);
+    for (int pass = 0; pass < 2 && m > 0; ++pass) {
+      // P = T V^H (nt x m), T -= P V
+      zgemm(ex, nt, m, N, 1, C1(), T.c(), 0, N, 1, false, V.c(), 0, 1, N, true, C0(), tmp.c(), 0, m, 1);
+      zgemm(ex, nt, N, m, 1, CR(-1.0), tmp.c(), 0, m, 1, false, V.c(), 0, N, 1, false, C1(), T.c(), 0, N, 1);
+    }
+    int acc = 0;
+    for (int i = 0; i < nt; ++i) {
+      cplx *ti = T.c() + (int64_t)i * N;
+      for (int pass = 0; pass < 2; ++pass) {
+        if (acc > 0) {  // against the accepted new vectors
+          zgemm(ex, 1, acc, N, 1, C1(), ti, 0, N, 1, false, T.c(), 0, 1, N, true, C0(), tmp.c(), 0, acc, 1);
+          zgemm(ex, 1, N, acc, 1, CR(-1.0), tmp.c(), 0, acc, 1, false, T.c(), 0, N, 1, false, C1(), ti, 0, N, 1);
+        }
+        if (m > 0 && pass == 1) {
+          zgemm(ex, 1, m, N, 1, C1(), ti, 0, N, 1, false, V.c(), 0, 1, N, true, C0(), tmp.c(), 0, m, 1);
+          zgemm(ex, 1, N, m, 1, CR(-1.0), tmp.c(), 0, m, 1, false, V.c(), 0, N, 1, false, C1(), ti, 0, N, 1);
+        }
+      }
+      std::vector<double> ni = row_norms(ti, 1);
+      if (!(ni[0] > 1e-8 * std::max(n0[i], 1e-300)) || !(ni[0] > 1e-14) || !std::isfinite(ni[0]))
+        continue;
+      k_scale_row<<<grid1d(N, 256), 256, 0, ex.stream>>>(ti, N, nrm.d());
+      ADC_CHECK_LAUNCH();
+      if (acc != i)
+        ADC_CUDA(cudaMemcpyAsync(T.c() + (int64_t)acc * N, ti, N * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                                 ex.stream));
+      ++acc;
+    }
+    return acc;
+  }
+
+  // Rayleigh-Ritz on V[0:m]: w (host copy), Y, SY, R for the lowest nroots
+  std::vector<double> ritz(int nr) {
+    k_hermitize<<<(m * m + 255) / 256, 256, 0, ex.stream>>>(G.c(), mmax, m, H.c(), mmax);
+    ADC_CHECK_LAUNCH();
+    jacobi_eigh(ex, H.c(), m, mmax, w.d(), Cv.c(), mmax, (int *)info.p);
+    // Y[r][n] = sum_i Cv[i][r] V[i][n]
+    zgemm(ex, nr, N, m, 1, C1(), Cv.c(), 0, 1, mmax, false, V.c(), 0, N, 1, false, C0(), Y.c(), 0, N, 1);
+    zgemm(ex, nr, N, m, 1, C1(), Cv.c(), 0, 1, mmax, false, AV.c(), 0, N, 1, false, C0(), SY.c(), 0, N, 1);
+    k_residual<<<grid1d((int64_t)nr * N, 256), 256, 0, ex.stream>>>(SY.c(), Y.c(), w.d(), nr, N, R.c());
+    ADC_CHECK_LAUNCH();
+    std::vector<double> wh(m);
+    ADC_CUDA(cudaMemcpyAsync(wh.data(), w.d(), m * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
+    ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    return wh;
+  }
+
+  // V <- Y (orthonormal Ritz vectors), AV <- sigma64(Y) or SY, G <- Y^H AV
+  void collapse(int nr, bool fp64_sigma) {
+    ADC_CUDA(cudaMemcpyAsync(V.c(), Y.c(), (int64_t)nr * N * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
+    if (fp64_sigma) apply_sigma(V.c(), AV.c(), nr, ADC_PREC_FP64);
+    else
+      ADC_CUDA(cudaMemcpyAsync(AV.c(), SY.c(), (int64_t)nr * N * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
+    m = 0;
+    extend_projection(0, nr);
+    m = nr;
+  }
+};
+
+int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision, const cplx *guess,
+                 int64_t nguess, double *omega, cplx *Yout, double *err64, adc_stats *st_out) {
+  Timer total;
+  const int64_t N = c->N;
+  ADC_REQUIRE(nroots >= 1 && nroots <= N, ADC_ERR_ARG, "nroots out of range");
+  ADC_REQUIRE(tol > 0.0, ADC_ERR_ARG, "tol must be positive");
+  ADC_REQUIRE(precision == ADC_PREC_FP64 || precision == ADC_PREC_BF16X3, ADC_ERR_ARG, "precision");
+  const int kb = std::max(nroots, c->opts.block);
+  int mmax = c->opts.max_subspace > 0 ? c->opts.max_subspace : std::max(6 * kb, 3 * kb + 2 * nroots);
+  mmax = (int)std::min<int64_t>(std::min<int64_t>(mmax, N), 1024);
+  mmax = std::max(mmax, std::min<int>((int)N, nroots + 1));
+  Davidson d(c, nroots, mmax);
+  Exec &ex = c->ex;
+
+  // ---- starting space
+  int m0;
+  ADC_REQUIRE(!(guess && nguess > 0) || nguess >= nroots, ADC_ERR_ARG, "need at least nroots guess vectors");
+  if (guess && nguess > 0) {
+    m0 = (int)std::min<int64_t>(nguess, mmax);
+    ADC_CUDA(cudaMemcpyAsync(d.T.c(), guess, (int64_t)std::min<int64_t>(m0, nroots) * N * sizeof(cplx),
+                             cudaMemcpyDeviceToDevice, ex.stream));
+    m0 = std::min(m0, nroots);
+  } else {
+    m0 = (int)std::min<int64_t>(N, std::min(mmax - nroots, std::max(2 * nroots, kb)));
+    m0 = std::max(m0, std::min<int>((int)N, nroots));
+    std::vector<double> dh(N);
+    ADC_CUDA(cudaMemcpyAsync(dh.data(), c->diag.d(), N * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
+    ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    std::vector<int64_t> idx(N);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::partial_sort(idx.begin(), idx.begin() + m0, idx.end(),
+                      [&](int64_t a, int64_t b) { return dh[a] < dh[b] || (dh[a] == dh[b] && a < b); });
+    DBuf ib(ex, m0 * sizeof(int64_t));
+    ADC_CUDA(cudaMemcpyAsync(ib.p, idx.data(), m0 * sizeof(int64_t), cudaMemcpyHostToDevice, ex.stream));
+    k_unit_vectors<<<m0, 256, 0, ex.stream>>>(d.V.c(), N, (const int64_t *)ib.p, m0);
+    ADC_CHECK_LAUNCH();
+    ADC_CUDA(cudaStreamSynchronize(ex.stream));
+  }
+  if (guess && nguess > 0) {
+    // guesses go through the orthonormalisation into V
+    d.m = 0;
+    int acc = d.orthonormalise(m0);
+    ADC_REQUIRE(acc > 0, ADC_ERR_ARG, "guess vectors are linearly dependent");
+    ADC_CUDA(cudaMemcpyAsync(d.V.c(), d.T.c(), (int64_t)acc * N * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                             ex.stream));
+    m0 = acc;
+  }
+  int phase = (precision == ADC_PREC_FP64) ? 2 : 0;  // 0 mixed, 1 refine, 2 plain FP64
+  int prec_new = (phase == 2) ? ADC_PREC_FP64 : ADC_PREC_BF16X3;
+  d.apply_sigma(d.V.c(), d.AV.c(), m0, prec_new);
+  d.m = 0;
+  d.extend_projection(0, m0);
+  d.m = m0;
+
+  std::vector<double> wh, rn(nroots, 0.0), hist;
+  bool converged = false;
+  int it = 0;
+  const int nr = std::min<int>(nroots, d.m);
+  for (it = 1; it <= max_iter; ++it) {
+    wh = d.ritz(std::min(nroots, d.m));
+    rn = d.row_norms(d.R.c(), nroots);
+    double mx = *std::max_element(rn.begin(), rn.end());
+    ADC_REQUIRE(std::isfinite(mx), ADC_ERR_NUMERIC, "non-finite residual norm in Davidson");
+    if (c->opts.verbose)
+      fprintf(stderr, "[davidson] it %d phase %d m %d max|r| %.3e w0 %.12f\n", it, phase, d.m, mx, wh[0]);
+    hist.push_back(mx);
+    d.st.iterations = it;
+    if (phase == 1) d.st.iterations_fp64++;
+    if (phase == 2) d.st.iterations_fp64++;
+    if (mx <= tol) {
+      if (phase == 2) { converged = true; break; }
+      // verify on FP64 residuals: collapse with sigma64
+      d.collapse(nroots, true);
+      phase = 1;
+      wh = d.ritz(nroots);
+      rn = d.row_norms(d.R.c(), nroots);
+      mx = *std::max_element(rn.begin(), rn.end());
+      if (c->opts.verbose) fprintf(stderr, "[davidson] fp64 check max|r| %.3e\n", mx);
+      if (mx <= tol) { converged = true; break; }
+      hist.clear();
+    } else if (phase == 0) {
+      // stall of the mixed phase: no 2x improvement over the last 3 iterations
+      size_t h = hist.size();
+      if (h >= 4 && hist[h - 1] > 0.5 * hist[h - 4]) {
+        d.collapse(nroots, true);
+        phase = 1;
+        hist.clear();
+        continue;
+      }
+    } else if (phase == 1) {
+      size_t h = hist.size();
+      if (h >= 4 && hist[h - 1] > 0.5 * hist[h - 4]) {
+        d.collapse(nroots, true);
+        hist.clear();
+        continue;
+      }
+    }
+    // new correction vectors for the unconverged roots
+    std::vector<int> rows;
+    for (int r = 0; r < nroots; ++r)
+      if (rn[r] > tol) rows.push_back(r);
+    if (d.m + (int)rows.size() > d.mmax) {
+      d.collapse(nroots, phase == 1);
+      wh = d.ritz(nroots);
+    }
+    ADC_CUDA(cudaMemcpyAsync(d.rowsb.p, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice, ex.stream));
+    k_precondition<<<grid1d((int64_t)rows.size() * N, 256), 256, 0, ex.stream>>>(
+        d.R.c(), d.w.d(), (const int *)d.rowsb.p, c->diag.d(), (int64_t)rows.size(), N, d.T.c());
+    ADC_CHECK_LAUNCH();
+    int na = d.orthonormalise((int)rows.size());
+    if (na == 0) break;
+    ADC_CUDA(cudaMemcpyAsync(d.V.c() + (int64_t)d.m * N, d.T.c(), (int64_t)na * N * sizeof(cplx),
+                             cudaMemcpyDeviceToDevice, ex.stream));
+    prec_new = (phase == 2) ? ADC_PREC_FP64 : ADC_PREC_BF16X3;
+    d.apply_sigma(d.V.c() + (int64_t)d.m * N, d.AV.c() + (int64_t)d.m * N, na, prec_new);
+    d.extend_projection(d.m, na);
+    d.m += na;
+  }
+  if (it > max_iter) it = max_iter;
+  if (!converged && phase != 2) {
+    // report FP64 residuals of the best vectors
+    d.collapse(nroots, true);
+    wh = d.ritz(nroots);
+    rn = d.row_norms(d.R.c(), nroots);
+  }
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+  for (int r = 0; r < nroots; ++r) {
+    omega[r] = wh[r];
+    if (err64) err64[r] = rn[r];
+  }
+  if (Yout)
+    ADC_CUDA(cudaMemcpyAsync(Yout, d.Y.c(), (int64_t)nroots * N * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                             ex.stream));
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+  d.st.time_total_s = total.s();
+  d.st.time_sigma_s = d.tsig;
+  d.st.max_residual = *std::max_element(rn.begin(), rn.end());
+  if (st_out) *st_out = d.st;
+  (void)nr;
+  return converged ? ADC_OK : ADC_ERR_NOCONV;
+}
+
+}  // namespace adc

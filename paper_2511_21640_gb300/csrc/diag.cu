@@ -1,0 +1,95 @@
+// Diagnostics of the contraction kernels (see include/adc_gb300_diag.h).
+#include <cmath>
+
+#include "ctx.cuh"
+#include "tc_gemm.cuh"
+#include "../../include/adc_gb300_diag.h"
+
+using namespace adc;
+
+namespace {
+__global__ void k_fill_random(cplx *x, int64_t n, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    // splitmix64 of (seed, i)
+    uint64_t z = seed * 0x9E3779B97F4A7C15ull + (uint64_t)i * 0xBF58476D1CE4E5B9ull + 0x94D049BB133111EBull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    double a = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    uint64_t w = z * 0xD1342543DE82EF95ull + 1;
+    w ^= w >> 29;
+    double b = (double)(w >> 11) * (1.0 / 9007199254740992.0);
+    x[i] = cmake(2.0 * a - 1.0, 2.0 * b - 1.0);
+  }
+}
+__global__ void k_diff(const cplx *a, const cplx *b, int64_t n, double *out) {
+  double d = 0.0, r = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double dx = a[i].x - b[i].x, dy = a[i].y - b[i].y;
+    d += dx * dx + dy * dy;
+    r += b[i].x * b[i].x + b[i].y * b[i].y;
+  }
+  atomicAdd(out, d);
+  atomicAdd(out + 1, r);
+}
+}  // namespace
+
+extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_t seed, int reps,
+                             double *rel_err, double *ms) {
+  if (M <= 0 || N <= 0 || K <= 0 || reps < 1 || (which != 0 && which != 1)) return ADC_ERR_ARG;
+  Exec ex;
+  try {
+    ADC_CUDA(cudaStreamCreateWithFlags(&ex.stream, cudaStreamNonBlocking));
+    {
+      DBuf A = cbuf(ex, M * K), B = cbuf(ex, N * K), C = cbuf(ex, M * N), R = cbuf(ex, M * N);
+      DBuf acc(ex, 2 * sizeof(double)), err(ex, sizeof(int));
+      fill_zero(ex, err.p, sizeof(int));
+      k_fill_random<<<grid1d(M * K, 256), 256, 0, ex.stream>>>(A.c(), M * K, seed);
+      k_fill_random<<<grid1d(N * K, 256), 256, 0, ex.stream>>>(B.c(), N * K, seed + 7);
+      ADC_CHECK_LAUNCH();
+      zgemm(ex, M, N, K, 1, C1(), A.c(), 0, K, 1, false, B.c(), 0, 1, K, false, C0(), R.c(), 0, N, 1);
+      TcMat Ta, Tb;
+      auto run = [&]() {
+        if (which == 0) {
+          zgemm(ex, M, N, K, 1, C1(), A.c(), 0, K, 1, false, B.c(), 0, 1, K, false, C0(), C.c(), 0, N, 1);
+        } else {
+          tc_gemm(ex, Ta, Tb, M, N, C1(), C0(), C.c(), N, 1, 0, 1, (int *)err.p);
+        }
+      };
+      if (which == 1) {
+        tc_pack_A(ex, Ta, A.c(), M, K, K, 1, false);
+        tc_pack_B(ex, Tb, B.c(), N, K, K, 0, 1, 1, false);
+      }
+      run();
+      cudaEvent_t e0, e1;
+      ADC_CUDA(cudaEventCreate(&e0));
+      ADC_CUDA(cudaEventCreate(&e1));
+      ADC_CUDA(cudaEventRecord(e0, ex.stream));
+      for (int r = 0; r < reps; ++r) run();
+      ADC_CUDA(cudaEventRecord(e1, ex.stream));
+      ADC_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (ms) *ms = t / reps;
+      fill_zero(ex, acc.p, acc.bytes);
+      k_diff<<<256, 256, 0, ex.stream>>>(C.c(), R.c(), M * N, acc.d());
+      ADC_CHECK_LAUNCH();
+      double h[2];
+      int he = 0;
+      ADC_CUDA(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, ex.stream));
+      ADC_CUDA(cudaMemcpyAsync(&he, err.p, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));
+      ADC_CUDA(cudaStreamSynchronize(ex.stream));
+      if (rel_err) *rel_err = std::sqrt(h[0] / std::max(h[1], 1e-300));
+      if (he) throw Error(ADC_ERR_TIMEOUT, "tensor-core GEMM wait gave up");
+    }
+    cudaStreamSynchronize(ex.stream);
+    cudaStreamDestroy(ex.stream);
+    return ADC_OK;
+  } catch (const Error &e) {
+    if (ex.stream) { cudaStreamSynchronize(ex.stream); cudaStreamDestroy(ex.stream); }
+    fprintf(stderr, "adc_diag_gemm: %s\n", e.what());
+    return e.code;
+  }
+}

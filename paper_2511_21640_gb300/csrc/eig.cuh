@@ -1,0 +1,9 @@
+#pragma once
+#include "tensor.cuh"
+
+namespace adc {
+// Eigen-decomposition of the Hermitian n x n matrix A (overwritten): eigenvalues
+// ascending in w[n], eigenvectors in the columns of V (leading dimension ldv).
+// info_dev[0] receives the sweep count, or -1 if not converged.
+void jacobi_eigh(Exec &ex, cplx *A, int n, int lda, double *w, cplx *V, int ldv, int *info_dev);
+}  // namespace adc

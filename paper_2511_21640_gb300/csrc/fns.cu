@@ -1,0 +1,69 @@
+// Frozen natural spinors from the MP2 virtual density (Sec. 2.4, Eqs. 25-30).
+//   Eq. 25: D_ab = 1/2 sum_cij <ac||ij><ij||bc> / (eps_ij^ac eps_ij^bc)
+//               = 1/2 sum_ijc t_ij^ac conj(t_ij^bc)
+//   Eq. 26: D V = V eta (eta descending);  Eq. 27: keep eta_i >= eta_crit
+//   Eq. 28-29: F~ = V~^H diag(eps_vir) V~,  F~ Z~ = Z~ eps~
+//   Eq. 30: U = V~ Z~
+#include "ctx.cuh"
+#include "eig.cuh"
+
+namespace adc {
+
+namespace {
+// reverse the column order (ascending -> descending) of V and w
+__global__ void k_reverse(const double *w, const cplx *V, int n, double *wo, cplx *Vo) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n) wo[idx] = w[n - 1 - idx];
+  if (idx < n * n) {
+    int r = idx / n, col = idx % n;
+    Vo[r * n + col] = V[r * n + (n - 1 - col)];
+  }
+}
+}  // namespace
+
+void fns_run(adc_ctx *c, cplx *D, double *eta, cplx *Vout, double eta_crit, int64_t *n_keep, cplx *U,
+             double *eps_new) {
+  Exec &ex = c->ex;
+  const int64_t o = c->o, v = c->v;
+  TV t1 = TV::dense(c->t1.c(), {o, o, v, v});
+  DBuf Db = cbuf(ex, v * v);
+  einsum(ex, CR(0.5), t1, "ijac", t1.cj(), "ijbc", C0(), TV::dense(Db.c(), {v, v}), "ab");
+  if (D) ADC_CUDA(cudaMemcpyAsync(D, Db.c(), v * v * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
+  DBuf A = cbuf(ex, v * v), Vasc = cbuf(ex, v * v), Vd = cbuf(ex, v * v);
+  DBuf wasc(ex, v * sizeof(double)), wd(ex, v * sizeof(double)), info(ex, 16);
+  ADC_CUDA(cudaMemcpyAsync(A.c(), Db.c(), v * v * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
+  jacobi_eigh(ex, A.c(), (int)v, (int)v, wasc.d(), Vasc.c(), (int)v, (int *)info.p);
+  k_reverse<<<grid1d(v * v, 256), 256, 0, ex.stream>>>(wasc.d(), Vasc.c(), (int)v, wd.d(), Vd.c());
+  ADC_CHECK_LAUNCH();
+  std::vector<double> wh(v);
+  ADC_CUDA(cudaMemcpyAsync(wh.data(), wd.d(), v * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+  int64_t nk = 0;
+  while (nk < v && wh[nk] >= eta_crit) ++nk;
+  *n_keep = nk;
+  if (eta) ADC_CUDA(cudaMemcpyAsync(eta, wd.d(), v * sizeof(double), cudaMemcpyDeviceToDevice, ex.stream));
+  if (Vout) ADC_CUDA(cudaMemcpyAsync(Vout, Vd.c(), v * v * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
+  if (nk > 0 && (U || eps_new)) {
+    // F~ = V~^H diag(eps) V~ : scale rows of V~ by eps, then V~^H (eps V~)
+    DBuf EV = cbuf(ex, v * nk), F = cbuf(ex, nk * nk), Z = cbuf(ex, nk * nk);
+    DBuf ew(ex, nk * sizeof(double));
+    {
+      // EV[a][k] = eps_a V~[a][k], as diag(eps) times V~
+      DBuf Dg = cbuf(ex, v * v);
+      fill_zero(ex, Dg.p, Dg.bytes);
+      add_diag(ex, Dg.c(), c->ev.d(), v, 1.0);
+      zgemm(ex, v, nk, v, 1, C1(), Dg.c(), 0, v, 1, false, Vd.c(), 0, v, 1, false, C0(), EV.c(), 0, nk, 1);
+    }
+    // F[k][l] = sum_a conj(V~[a][k]) EV[a][l]
+    zgemm(ex, nk, nk, v, 1, C1(), Vd.c(), 0, 1, v, true, EV.c(), 0, nk, 1, false, C0(), F.c(), 0, nk, 1);
+    jacobi_eigh(ex, F.c(), (int)nk, (int)nk, ew.d(), Z.c(), (int)nk, (int *)info.p);
+    if (eps_new) ADC_CUDA(cudaMemcpyAsync(eps_new, ew.d(), nk * sizeof(double), cudaMemcpyDeviceToDevice, ex.stream));
+    if (U) {
+      // U[a][l] = sum_k V~[a][k] Z[k][l], written with leading dimension v
+      zgemm(ex, v, nk, nk, 1, C1(), Vd.c(), 0, v, 1, false, Z.c(), 0, nk, 1, false, C0(), U, 0, v, 1);
+    }
+  }
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+}
+
+}  // namespace adc

@@ -1,0 +1,76 @@
+// Matrix-free sigma product S = M X in FP64 with the cached operators.
+//
+// EA, X = [X_a | X_j,(a<b)]:
+//   S1 = M11 X1 + Cpl X2
+//   S2 = Cpl^H X1 + d2 * X2
+//        + x [ sum_{c<d} <ab||cd> X_j,cd  -  P(ab) sum_kc <ak||cj> X_k,cb ]
+// IP, X = [X_i | X_(i<j),a]:
+//   S1 = M11 X1 + Cpl X2
+//   S2 = Cpl^H X1 + d2 * X2
+//        + x [ sum_{k<l} <kl||ij> X_(kl),a  +  P(ij) sum_kb <ak||bj> X_k,i,b ]
+// (Sec. 2.1 Eqs. 10-12; integrals from Eq. 43.) The satellite terms of
+// first order are the ladder (packed GEMM) and the ring (GEMM over (k,c)).
+#include "ctx.cuh"
+
+namespace adc {
+
+cplx *scratch(adc_ctx *c, int64_t ncplx) {
+  size_t need = (size_t)ncplx * sizeof(cplx);
+  if (c->scratch.bytes < need) {
+    c->scratch.reset();
+    c->scratch = DBuf(c->ex, need);
+  }
+  return c->scratch.c();
+}
+
+void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
+  Exec &ex = c->ex;
+  const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N;
+  const bool sat = (c->order == 3 && c->x != 0.0);
+  const double x = sat ? c->x : 0.0;
+  // S1 = X1 M11^T  (S1[r][p] = sum_q M11[p][q] X1[r][q])
+  zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, c->M11.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
+  // S1 += X2 Cpl^T
+  zgemm(ex, k, n1, n2, 1, C1(), X + n1, 0, N, 1, false, c->Cpl.c(), 0, 1, n2, false, C1(), S, 0, N, 1);
+  // S2 = X1 conj(Cpl)
+  zgemm(ex, k, n2, n1, 1, C1(), X, 0, N, 1, false, c->Cpl.c(), 0, n2, 1, true, C0(), S + n1, 0, N, 1);
+  // S2 += d2 * X2
+  diag_mul_add(ex, k, n2, c->d2.d(), X + n1, N, S + n1, N, 1.0);
+  if (!sat) return;
+  if (c->kind == ADC_EA) {
+    const int64_t pv = npairs(v);
+    // ladder: S2[r][j][(ab)] += x sum_(cd) X2[r][j][(cd)] Glad[(ab)][(cd)]
+    zgemm(ex, o, pv, pv, k, CR(x), X + n1, N, pv, 1, false, c->Glad.c(), 0, 1, pv, false, C1(),
+          S + n1, N, pv, 1);
+    // ring: Xf[r][k][c][b] (antisymmetric in c,b); T[r][(j,a)][b] = sum_(kc) W[(j,a)][(kc)] Xf[r][(kc)][b]
+    cplx *Xf = scratch(c, 2 * k * o * v * v);
+    cplx *T = Xf + k * o * v * v;
+    pair_unpack(ex, X + n1, k, o, N, pv, v, 1, Xf);
+    zgemm(ex, o * v, v, o * v, k, C1(), c->W.c(), 0, o * v, 1, false, Xf, o * v * v, v, 1, false, C0(),
+          T, o * v * v, v, 1);
+    // S2[r][j][(a<b)] -= x (T[r][j][a][b] - T[r][j][b][a])
+    pair_pack(ex, T, o * v * v, v * v, v, 1, 0, 1.0, k, o, v, 1, S + n1, N, pv, CR(-x), C1());
+  } else {
+    const int64_t po = npairs(o);
+    // ladder: S2[r][(ij)][a] += x sum_(kl) Glad[(ij)][(kl)] X2[r][(kl)][a]
+    zgemm(ex, po, v, po, k, CR(x), c->Glad.c(), 0, po, 1, false, X + n1, N, v, 1, false, C1(),
+          S + n1, N, v, 1);
+    // ring: Xf[r][i][k][b]; T[r][(j,a)][i] = -sum_(kb) W[(j,a)][(kb)] Xf[r][i][(kb)]
+    cplx *Xf = scratch(c, 2 * k * o * o * v);
+    cplx *T = Xf + k * o * o * v;
+    pair_unpack(ex, X + n1, k, 1, N, 0, o, v, Xf);
+    zgemm(ex, o * v, o, o * v, k, CR(-1.0), c->W.c(), 0, o * v, 1, false, Xf, o * o * v, 1, o * v,
+          false, C0(), T, o * v * o, o, 1);
+    // S2[r][(i<j)][a] += x (T[r][j][a][i] - T[r][i][a][j]); view T'(p=i, q=j, in=a) = T[q][in][p]
+    pair_pack(ex, T, o * v * o, 0, 1, v * o, o, 1.0, k, 1, o, v, S + n1, N, 0, CR(x), C1());
+  }
+}
+
+void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision) {
+  if (k <= 0) return;
+  if (precision == ADC_PREC_FP64) sigma_fp64(c, X, S, k);
+  else if (precision == ADC_PREC_BF16X3) sigma_bf16x3(c, X, S, k);
+  else throw Error(ADC_ERR_ARG, "unknown precision");
+}
+
+}  // namespace adc

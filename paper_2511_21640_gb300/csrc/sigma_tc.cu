@@ -1,0 +1,78 @@
+// Sigma product with the dense contractions on the tensor cores (BF16x3).
+// Same terms as sigma.cu (Sec. 2.1 Eqs. 10-12); the coupling, ladder and ring
+// contractions run through tc_gemm, the main block (n1 x n1) and the
+// zeroth-order diagonal stay FP64.
+#include "ctx.cuh"
+#include "tc_gemm.cuh"
+
+namespace adc {
+
+static void build_cache(adc_ctx *c) {
+  Exec &ex = c->ex;
+  auto &tc = *c->tc;
+  const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2;
+  tc_pack_A(ex, tc.Cpl, c->Cpl.c(), n1, n2, n2, 1, false);
+  tc_pack_A(ex, tc.CplT, c->Cpl.c(), n2, n1, 1, n2, true);
+  if (c->order == 3 && c->x != 0.0) {
+    const int64_t P = (c->kind == ADC_EA) ? npairs(v) : npairs(o);
+    tc_pack_A(ex, tc.Glad, c->Glad.c(), P, P, P, 1, false);
+    tc_pack_A(ex, tc.W, c->W.c(), o * v, o * v, o * v, 1, false);
+  }
+  tc.err = DBuf(ex, sizeof(int));
+  fill_zero(ex, tc.err.p, sizeof(int));
+  tc.ready = true;
+}
+
+void release_tc(adc_ctx *c) { c->tc.reset(); }
+
+void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
+  Exec &ex = c->ex;
+  if (!c->tc) c->tc.reset(new TcCache());
+  if (!c->tc->ready) build_cache(c);
+  auto &tc = *c->tc;
+  int *err = (int *)tc.err.p;
+  const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N;
+  const bool sat = (c->order == 3 && c->x != 0.0);
+  const double x = sat ? c->x : 0.0;
+  // S1 = X1 M11^T (FP64, n1 x n1)
+  zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, c->M11.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
+  // S1 += Cpl X2  : out[c][r] = sum_K Cpl[c][K] X2[r][K]
+  tc_pack_B(ex, tc.Bx, X + n1, k, n2, N, 0, 1, 1, false);
+  tc_gemm(ex, tc.Cpl, tc.Bx, n1, k, C1(), C1(), S, 1, N, 0, 1, err);
+  // S2 = Cpl^H X1 : out[K][r] = sum_c conj(Cpl[c][K]) X1[r][c]
+  tc_pack_B(ex, tc.Bx, X, k, n1, N, 0, 1, 1, false);
+  tc_gemm(ex, tc.CplT, tc.Bx, n2, k, C1(), C0(), S + n1, 1, N, 0, 1, err);
+  diag_mul_add(ex, k, n2, c->d2.d(), X + n1, N, S + n1, N, 1.0);
+  if (sat) {
+    if (c->kind == ADC_EA) {
+      const int64_t pv = npairs(v);
+      // ladder: out[(ab)][(r,j)] = sum_(cd) Glad[(ab)][(cd)] X2[r][j][(cd)]
+      tc_pack_B(ex, tc.Bx, X + n1, k * o, pv, N, pv, o, 1, false);
+      tc_gemm(ex, tc.Glad, tc.Bx, pv, k * o, CR(x), C1(), S + n1, 1, N, pv, o, err);
+      // ring: T[r][j][a][b] = sum_(kc) W[(j,a)][(kc)] Xf[r][k][c][b]
+      cplx *T = scratch(c, k * o * v * v);
+      tc_pack_B_ring(ex, tc.Bx, c, X, k);
+      tc_gemm(ex, tc.W, tc.Bx, o * v, k * v, C1(), C0(), T, v, o * v * v, 1, v, err);
+      pair_pack(ex, T, o * v * v, v * v, v, 1, 0, 1.0, k, o, v, 1, S + n1, N, pv, CR(-x), C1());
+    } else {
+      const int64_t po = npairs(o);
+      // ladder: out[(ij)][(r,a)] = sum_(kl) Glad[(ij)][(kl)] X2[r][(kl)][a]
+      tc_pack_B(ex, tc.Bx, X + n1, k * v, po, N, 1, v, v, false);
+      tc_gemm(ex, tc.Glad, tc.Bx, po, k * v, CR(x), C1(), S + n1, v, N, 1, v, err);
+      // ring: T[r][j][a][i] = -sum_(kb) W[(j,a)][(kb)] Xf[r][i][k][b]
+      cplx *T = scratch(c, k * o * v * o);
+      tc_pack_B_ring(ex, tc.Bx, c, X, k);
+      tc_gemm(ex, tc.W, tc.Bx, o * v, k * o, CR(-1.0), C0(), T, o, o * v * o, 1, o, err);
+      pair_pack(ex, T, o * v * o, 0, 1, v * o, o, 1.0, k, 1, o, v, S + n1, N, 0, CR(x), C1());
+    }
+  }
+  int h = 0;
+  ADC_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+  if (h != 0) {
+    fill_zero(ex, err, sizeof(int));
+    throw Error(ADC_ERR_TIMEOUT, "tensor-core GEMM wait gave up (code " + std::to_string(h) + ")");
+  }
+}
+
+}  // namespace adc

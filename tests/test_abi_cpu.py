@@ -1,0 +1,78 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The shared library must load and export every function declared in
+include/*.h; argument validation that happens before any device work must
+return the documented error codes.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_21640_gb300.build import build
+    build()
+    import paper_2511_21640_gb300 as m
+    return m
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"\b(adc_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert {"adc_init", "adc_sigma", "adc_davidson", "adc_fns_density", "adc_free"} <= names
+    raw = ctypes.CDLL(lib.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(raw, n), n
+
+
+def test_error_strings_and_defaults(lib):
+    for code in range(0, -9, -1):
+        s = lib.lib.adc_strerror(code).decode()
+        assert s.startswith("ADC_")
+    o = lib.adc_opts()
+    assert lib.lib.adc_opts_default(ctypes.byref(o)) == 0
+    assert o.precision == 0 and abs(o.herm_tol - 1e-12) < 1e-30 and o.stream is None
+    assert lib.lib.adc_dims(None, None, None) == -7
+    assert lib.lib.adc_sigma(None, None, None, 1, 0) == -7
+    assert lib.lib.adc_opts_default(None) == -1
+
+
+@pytest.mark.parametrize("kind,order,nocc,nvir,code", [
+    (2, 3, 3, 5, -6),   # EE not built
+    (7, 3, 3, 5, -1),   # unknown kind
+    (0, 4, 3, 5, -1),   # bad order
+    (0, 3, 1, 5, -1),   # IP needs two occupied spinors
+    (1, 2, 3, 1, -1),   # EA needs two virtual spinors
+])
+def test_init_rejects_bad_arguments_before_device_work(lib, kind, order, nocc, nvir, code):
+    nmo = nocc + nvir
+    B = np.zeros((2, nmo, nmo), np.complex128)
+    eo = -np.ones(nocc)
+    ev = np.ones(nvir)
+    h = ctypes.c_void_p()
+    rc = lib.lib.adc_init(ctypes.byref(h), B.ctypes.data, 2, eo.ctypes.data, nocc, ev.ctypes.data, nvir,
+                          kind, order, 1.0, None)
+    assert rc == code
+    assert not h.value
+    assert lib.lib.adc_last_error(None)
+
+
+def test_binding_rejects_wrong_dtypes(lib):
+    with pytest.raises(TypeError):
+        lib._ptr(np.zeros(3, np.complex64), np.complex128)
+    with pytest.raises(TypeError):
+        lib._ptr(np.zeros((3, 3), np.complex128)[:, 0], np.complex128)

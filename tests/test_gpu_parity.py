@@ -1,0 +1,181 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances:
+* FP64 sigma: ||S - S_ref|| / ||S_ref|| <= 1e-12 per vector.
+* BF16x3 sigma: <= 1e-4 per vector. Each FP64 operand is split into two BF16
+  numbers (about 2^-17 relative representation error), three of the four
+  partial products are kept (dropped term 2^-16 * 2^-16), and the tensor
+  cores accumulate in FP32, whose rounding grows like sqrt(K) * 2^-24 for
+  the longest inner sizes here (K <= 2e5 embedded terms): about 2e-5 in all,
+  so 1e-4 leaves a factor of five.
+* Eigenvalues: 1e-8 Eh (FP64 Davidson), 1e-6 Eh (mixed Davidson with FP64
+  refinement).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from synthetic import make_problem, random_vectors  # noqa: E402
+from oracle import adc as oadc  # noqa: E402
+from oracle.fns import fns_density, fns_basis  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_21640_gb300.build import build
+    build()
+    import paper_2511_21640_gb300 as m
+    return m
+
+
+def _rel(S, R):
+    return np.linalg.norm(S - R, axis=-1) / np.linalg.norm(R, axis=-1)
+
+
+# ---------------------------------------------------------------- GEMM kernels
+@pytest.mark.parametrize("M,N,K", [(300, 70, 1000), (1, 1, 1), (65, 129, 17)])
+def test_fp64_gemm(gpu, M, N, K):
+    err, ms = gpu.diag_gemm(0, M, N, K, seed=3)
+    assert err < 1e-14
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 16, 64), (200, 40, 1000), (129, 130, 70), (1000, 300, 5000),
+                                   (64, 8, 20000)])
+def test_bf16x3_gemm(gpu, M, N, K):
+    err, ms = gpu.diag_gemm(1, M, N, K, seed=5)
+    assert err < 5e-5, err
+
+
+# ---------------------------------------------------------------- sigma parity
+CASES = [
+    ("IP", 5, 37, 40, 3, 0.5, 11),
+    ("IP", 2, 9, 7, 3, 1.0, 12),     # one occupied pair
+    ("IP", 9, 20, 30, 2, 0.0, 13),
+    ("IP", 8, 24, 96, 3, 1.0, 0),    # the small IP-ADC(3) workload
+    ("EA", 6, 30, 64, 3, 0.5, 14),
+    ("EA", 3, 2, 5, 3, 1.0, 15),     # one virtual pair
+    ("EA", 4, 45, 50, 2, 0.0, 16),
+    ("EA", 7, 33, 70, 3, 1.0, 17),
+]
+
+
+@pytest.mark.parametrize("kind,o,v,Q,order,x,seed", CASES)
+def test_sigma_parity(gpu, kind, o, v, Q, order, x, seed):
+    p = make_problem(o, v, Q, seed=seed, sigma=0.08)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=order, x=x) as ctx:
+        n1, n2 = oadc.dims(kind, o, v)
+        assert (ctx.n1, ctx.n2) == (n1, n2)
+        X = random_vectors(ctx.N, 3, seed=seed + 100)
+        amp = oadc.Amplitudes(p.B, p.eps_occ, p.eps_vir, second_order=(order == 3))
+        ref = oadc.sigma_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, X, amp=amp)
+        # host pointers
+        S = ctx.sigma(X, "fp64")
+        assert _rel(S, ref).max() < 1e-12
+        # device pointers, single vector
+        Xd = torch.from_numpy(X[1:2].copy()).cuda()
+        Sd = ctx.sigma(Xd, "fp64").cpu().numpy()
+        assert _rel(Sd, ref[1:2]).max() < 1e-12
+        Sm = ctx.sigma(X, "bf16x3")
+        assert _rel(Sm, ref).max() < 1e-4
+        d = ctx.diagonal()
+        dref = oadc.diagonal_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, amp=amp)
+        assert np.abs(d - dref).max() < 1e-12 * max(1.0, np.abs(dref).max())
+        mb = oadc.main_block(kind, amp) if order == 3 else None
+        M11 = ctx.main_block()
+        if mb is not None:
+            ref11 = mb[0] + mb[2] + x * mb[3]
+            assert np.abs(M11 - ref11).max() < 1e-12 * np.abs(ref11).max()
+
+
+def test_sigma_zero_vectors_and_k0(gpu):
+    p = make_problem(4, 10, 12, seed=2, sigma=0.1)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EA", order=3, x=1.0) as ctx:
+        X = np.zeros((2, ctx.N), np.complex128)
+        assert np.abs(ctx.sigma(X, "fp64")).max() == 0.0
+        assert np.abs(ctx.sigma(X, "bf16x3")).max() == 0.0
+        assert gpu.lib.adc_sigma(ctx._h, None, None, 0, 0) == 0
+
+
+# ---------------------------------------------------------------- eigenvalues
+def test_ip_adc3_small_workload_davidson(gpu):
+    p = make_problem(8, 24, 96, seed=0, sigma=0.05, occ_range=(-2.0, -0.5), vir_range=(0.2, 3.0))
+    M = oadc.explicit_matrix("IP", 3, 1.0, p.B, p.eps_occ, p.eps_vir)
+    w = np.linalg.eigvalsh(M)[:4]
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP", order=3, x=1.0) as ctx:
+        om, Y, e64, st, rc = ctx.davidson(4, tol=1e-8, precision="fp64")
+        assert rc == 0
+        assert np.abs(om - w).max() < 1e-8
+        assert np.all(e64 <= 1e-8)
+        assert np.abs(Y.conj() @ Y.T - np.eye(4)).max() < 1e-10
+        R = Y @ M.T - om[:, None] * Y
+        assert np.linalg.norm(R, axis=1).max() < 1e-7
+        om2, _, e2, st2, rc2 = ctx.davidson(4, tol=1e-8, precision="bf16x3", want_vectors=False)
+        assert rc2 == 0 and np.abs(om2 - w).max() < 1e-8
+        assert st2["sigma_calls_fp64"] > 0
+
+
+@pytest.mark.parametrize("kind,o,v,Q,x", [("EA", 6, 30, 64, 0.5), ("IP", 7, 26, 50, 0.5)])
+def test_mixed_davidson_refined(gpu, kind, o, v, Q, x):
+    p = make_problem(o, v, Q, seed=21, sigma=0.06, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    M = oadc.explicit_matrix(kind, 3, x, p.B, p.eps_occ, p.eps_vir)
+    w = np.linalg.eigvalsh(M)[:4]
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=3, x=x) as ctx:
+        om, Y, e64, st, rc = ctx.davidson(4, tol=1e-7, precision="bf16x3")
+        assert rc == 0
+        assert np.abs(om - w).max() < 1e-6
+        assert np.all(e64 <= 1e-7)
+        R = Y @ M.T - om[:, None] * Y
+        assert np.linalg.norm(R, axis=1).max() < 1e-6
+
+
+def test_davidson_noconv_returns_best(gpu):
+    p = make_problem(5, 12, 20, seed=3, sigma=0.08)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP", order=3, x=1.0) as ctx:
+        om, _, e64, st, rc = ctx.davidson(3, tol=1e-12, max_iter=1, precision="fp64", raise_on_noconv=False)
+        assert rc == -4
+        assert np.all(np.isfinite(om)) and np.all(e64 > 0)
+
+
+# ---------------------------------------------------------------- natural spinors (Eqs. 25-30)
+def test_fns_density_and_truncation(gpu):
+    o, v, Q = 6, 30, 64
+    p = make_problem(o, v, Q, seed=31, sigma=0.06)
+    Dref = fns_density(p.B, p.eps_occ, p.eps_vir)
+    eta_r, V_r, nk_r, U_r, e_r = fns_basis(Dref, p.eps_vir, -1.0)
+    crit = float(np.sqrt(eta_r[9] * eta_r[10]))  # inside the gap between the 10th and 11th
+    eta_r, V_r, nk_r, U_r, e_r = fns_basis(Dref, p.eps_vir, crit)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EA", order=2) as ctx:
+        r = ctx.fns_density(crit)
+    assert np.abs(r["D"] - Dref).max() < 1e-12 * np.abs(Dref).max()
+    assert np.abs(r["eta"] - eta_r).max() < 1e-12 * eta_r.max()
+    assert r["n_keep"] == nk_r == 10
+    assert np.abs(r["eps_new"] - e_r).max() < 1e-10
+    P_gpu = r["U"] @ r["U"].conj().T
+    P_ref = U_r @ U_r.conj().T
+    assert np.abs(P_gpu - P_ref).max() < 1e-9
+    V = r["V"]
+    assert np.abs(V.conj().T @ V - np.eye(v)).max() < 1e-10
+
+
+# ---------------------------------------------------------------- errors
+def test_error_codes(gpu):
+    p = make_problem(4, 10, 8, seed=4, sigma=0.1)
+    Bbad = p.B.copy()
+    Bbad[0, 1, 2] += 0.01
+    with pytest.raises(gpu.AdcError) as e:
+        gpu.Context(Bbad, p.eps_occ, p.eps_vir, kind="IP")
+    assert e.value.code == -1
+    with pytest.raises(gpu.AdcError) as e:
+        gpu.Context(p.B, p.eps_occ + 10.0, p.eps_vir, kind="IP")
+    assert e.value.code == -1
+    with pytest.raises(gpu.AdcError) as e:
+        gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP", mem_limit=1024)
+    assert e.value.code == -2
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP") as ctx:
+        with pytest.raises(gpu.AdcError) as e:
+            ctx.sigma(np.zeros((1, ctx.N), np.complex128), precision=7)
+        assert e.value.code == -1
