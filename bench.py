@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 CD-ADC hot path; prints one JSON line.
+
+Workload (default): EA-ADC(2)+x(3) with x = 0.5, nocc = 40, nvir = 200,
+naux = 1200, complex128 Cholesky vectors (synthetic, seeded), 8 lowest roots.
+A step is one complete Davidson solve of those roots with tensor-core (BF16x3)
+sigma products refined by FP64 sigma products until every FP64 residual norm
+is below tol; the setup of the operators (adc_init) is timed separately.
+
+Metric: Davidson seconds per root (lower is better); the line also carries
+the sigma TFLOP/s of the mixed and FP64 products, the FP64 Davidson s/root,
+the eigenvalue difference between the two, a live roofline of the dominant
+kernel, clocks, an end-to-end number through the public API with host
+buffers, the number of library kernels launched, and the CPU oracle timed on
+a bounded sample of the same workload.
+
+--impl reference times the CPU oracle (the only reference there is) on the
+same workload and prints the same metric for it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synthetic import CONFIGS, config_problem, random_vectors  # noqa: E402
+
+METRIC = "Davidson s/root and sigma TFLOP/s: mixed vs FP64 on GPU at 1e-6 Eh error"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    def __init__(self):
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", os.environ.get("LOCAL_RANK", "0"),
+                                          f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def sigma_flops_formula(o, v, Q, k):
+    """Algorithmic flops of one EA sigma block of k vectors as the library forms it
+    (8 per complex multiply-add): coupling both ways (2 v n2 k), ladder over packed
+    pairs (Pv^2 o k), ring over (k, c) (o v * o v * v k)."""
+    pv = v * (v - 1) // 2
+    n2 = o * pv
+    cmac = 2 * v * n2 * k + pv * pv * o * k + (o * v) * (o * v) * (v * k) + v * v * k
+    return 8.0 * cmac
+
+
+def cpu_oracle_sample(p, x, n_rows=6, seed=5):
+    """Seconds per satellite sigma row (one vector) of the oracle on this workload."""
+    from oracle.rows import ea_satellite_rows
+    rng = np.random.default_rng(seed)
+    o, v = p.nocc, p.nvir
+    N = v + o * v * (v - 1) // 2
+    X = random_vectors(N, 1, seed=seed)
+    rows = []
+    for _ in range(n_rows):
+        k = int(rng.integers(o))
+        d, e = sorted(rng.choice(v, 2, replace=False))
+        rows.append((k, int(d), int(e)))
+    t0 = time.perf_counter()
+    ea_satellite_rows(p.B, p.eps_occ, p.eps_vir, 3, x, X, rows)
+    t = time.perf_counter() - t0
+    return t / n_rows, f"{n_rows} satellite rows of S = M X for one vector, each row from Eq. 43 integrals"
+
+
+def run_reference(args, cfgname):
+    """CPU oracle arm: each step evaluates a bounded sample of sigma rows."""
+    c = CONFIGS[cfgname]
+    p = config_problem(cfgname)
+    o, v = p.nocc, p.nvir
+    N = v + o * v * (v - 1) // 2
+    sig_vecs_per_root = args.ref_sigma_vectors_per_root
+    for _ in range(args.warmup):
+        cpu_oracle_sample(p, c["x"], n_rows=2)
+    ts = []
+    for s in range(args.steps):
+        t_row, what = cpu_oracle_sample(p, c["x"], n_rows=args.ref_rows, seed=10 + s)
+        ts.append(t_row)
+    t_row = float(np.mean(ts))
+    value = t_row * N * sig_vecs_per_root
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/root", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_row * args.ref_rows,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": cfgname, "nocc": o, "nvir": v, "naux": p.naux,
+                                            "kind": c["kind"], "order": c["order"], "x": c["x"],
+                                            "nroots": c["nroots"]},
+            "cpu_baseline": {"value": value, "unit": "s/root", "cores": cores, "kind": "oracle",
+                             "sample": f"{what}; seconds per row x N={N} rows x {sig_vecs_per_root} sigma "
+                                       "vectors per root"},
+            "e2e": {"value": value, "unit": "s/root", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="ea2x3_o40_v200_q1200")
+    ap.add_argument("--tol", type=float, default=None)
+    ap.add_argument("--no-fp64-davidson", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-rows", type=int, default=6)
+    ap.add_argument("--ref-sigma-vectors-per-root", type=float, default=8.0)
+    ap.add_argument("--cpu-rows", type=int, default=6)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, args.config)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import paper_2511_21640_gb300 as adcgpu
+
+    cfg = dict(CONFIGS[args.config])
+    kind, order, x, nroots = cfg["kind"], cfg["order"], cfg["x"], cfg["nroots"]
+    tol = args.tol if args.tol is not None else 1e-5
+    p = config_problem(args.config)
+    o, v, Q = p.nocc, p.nvir, p.naux
+    # replicas: every rank solves its own instance of the workload
+    B = torch.from_numpy(p.B).cuda()
+    eo = torch.from_numpy(p.eps_occ).cuda()
+    ev = torch.from_numpy(p.eps_vir).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = adcgpu.Context(B, eo, ev, kind=kind, order=order, x=x, stream="torch")
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+
+    def solve(prec, t=tol):
+        return ctx.davidson(nroots, tol=t, max_iter=300, precision=prec, want_vectors=False)
+
+    for _ in range(args.warmup):
+        om, _, e64, st, rc = solve("bf16x3")
+    # ---- timed region
+    clocks = Clocks()
+    clocks.start()
+    ctx.profile(True)
+    l0 = adcgpu.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        om, _, e64, st, rc = solve("bf16x3")
+        stats.append(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = adcgpu.launch_count() - l0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    ms_per_step = ms / args.steps
+    value = ms_per_step / 1e3 / (nroots * world)
+
+    pk, pk_kind = peaks()
+
+    def roofline_of(name, e):
+        avg_ms = e["total_ms"] / e["launches"]
+        alg = e["flops"] / e["launches"]
+        if name.startswith("tc_gemm"):
+            mma = 3.0 * alg  # three split products per complex product in the real embedding
+            ach = mma / (avg_ms * 1e-3) / 1e12
+            peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+            return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None, "peak_kind": f"bf16 dense sustained ({pk_kind})",
+                    "flops_per_launch": mma, "avg_launch_ms": avg_ms, "launches": e["launches"]}
+        ach = alg / (avg_ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": ach / 1.25, "traffic": None, "peak_kind": "fp64 FMA nominal 1.25 TFLOP/s",
+                "flops_per_launch": alg, "avg_launch_ms": avg_ms, "launches": e["launches"]}
+
+    by_kernel = sorted((roofline_of(k, e) for k, e in prof.items() if e["launches"] > 0),
+                       key=lambda r: -r["avg_launch_ms"] * r["launches"])
+    roof = by_kernel[0]
+    tc_rows = [r for r in by_kernel if r["kernel"].startswith("tc_gemm")]
+    roof_tc = tc_rows[0] if tc_rows else None
+
+    # ---- sigma TFLOP/s, mixed vs FP64 (one block of nroots vectors each)
+    Xs = torch.from_numpy(random_vectors(ctx.N, nroots, seed=7)).cuda()
+    sig = {}
+    for prec in ("bf16x3", "fp64"):
+        ctx.sigma(Xs, prec)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        reps = 3 if prec == "bf16x3" else 1
+        for _ in range(reps):
+            ctx.sigma(Xs, prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / reps
+        pr = ctx.profile_read()
+        ctx.profile(False)
+        fl = sum(e["flops"] for e in pr.values()) / reps
+        sig[prec] = {"ms": t, "tflops": fl / (t * 1e-3) / 1e12, "flops": fl}
+    S64 = ctx.sigma(Xs, "fp64")
+    Smx = ctx.sigma(Xs, "bf16x3")
+    sig_rel = float(((Smx - S64).abs().pow(2).sum(1).sqrt() / S64.abs().pow(2).sum(1).sqrt()).max().item())
+
+    # ---- FP64 Davidson for the comparison and the 1e-6 Eh check
+    fp64 = None
+    if not args.no_fp64_davidson:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        om64, _, e6, st6, rc6 = ctx.davidson(nroots, tol=tol, max_iter=300, precision="fp64", want_vectors=False)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t1
+        fp64 = {"s_per_root": t64 / nroots, "iterations": st6["iterations"], "sigma_calls": st6["sigma_calls"],
+                "max_eig_diff_vs_mixed": float(np.abs(om64 - om).max()), "rc": rc6}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Bh = torch.from_numpy(p.B).pin_memory()
+        eoh, evh = torch.from_numpy(p.eps_occ), torch.from_numpy(p.eps_vir)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        with adcgpu.Context(Bh, eoh, evh, kind=kind, order=order, x=x) as c2:
+            om2, _, e2, st2, rc2 = c2.davidson(nroots, tol=tol, max_iter=300, precision="bf16x3",
+                                               want_vectors=False)
+        te2e = time.perf_counter() - t2
+        e2e = {"value": te2e / nroots, "unit": "s/root", "h2d_bytes_per_step": int(p.B.nbytes + 8 * (o + v)),
+               "d2h_bytes_per_step": int(16 * nroots), "includes": "adc_init (H2D copy + operator setup) + adc_davidson"}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_rows > 0:
+        t_row, what = cpu_oracle_sample(p, x, n_rows=args.cpu_rows)
+        per_root = np.mean([s["sigma_calls"] for s in stats]) / nroots
+        N = ctx.N
+        cpu = {"value": t_row * N * per_root, "unit": "s/root", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{what}; scaled by N={N} rows and {per_root:.1f} sigma vectors per root "
+                         "(as used by the GPU run)"}
+
+    last = stats[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "s/root", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
+        "config": {"workload": args.config, "kind": kind, "order": order, "x": x, "nocc": o, "nvir": v, "naux": Q,
+                   "nroots": nroots, "tol_fp64_residual": tol, "N": ctx.N, "replicas": world,
+                   "l2": "operators larger than L2 (packed <ab||cd> 6.3 GB FP64, 3.2 GB BF16 planes)"},
+        "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "roofline_tensor_core": roof_tc,
+        "roofline_by_kernel": by_kernel,
+        "sigma": {"bf16x3": sig["bf16x3"], "fp64": sig["fp64"], "speedup": sig["fp64"]["ms"] / sig["bf16x3"]["ms"],
+                  "rel_diff_bf16x3_vs_fp64": sig_rel, "vectors": nroots},
+        "fp64_davidson": fp64,
+        "mixed_davidson": {"omega": [float(w) for w in om], "err64": [float(e) for e in e64],
+                           "iterations": last["iterations"], "sigma_calls": last["sigma_calls"],
+                           "sigma_calls_fp64": last["sigma_calls_fp64"], "rc": int(rc)},
+        "init_s": init_s, "e2e": e2e, "cpu_baseline": cpu,
+    }
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -156,6 +156,11 @@ int adc_fns_density(adc_ctx *ctx, adc_c128 *D, double *eta, adc_c128 *V,
                     double eta_crit, int64_t *n_keep, adc_c128 *U,
                     double *eps_new);
 
+/* Blocks until all work the context has queued on its stream is done. Needed
+ * after an asynchronous call with device pointers before another stream (or
+ * the host) reads the outputs. */
+int adc_sync(adc_ctx *ctx);
+
 /* Releases every resource of the context (NULL is accepted). */
 void adc_free(adc_ctx *ctx);
 

@@ -12,6 +12,9 @@
 extern "C" {
 #endif
 
+/* the context type of adc_gb300.h */
+typedef struct adc_ctx adc_ctx_opaque;
+
 /* Random complex A [M][K] and B [N][K] (seeded, uniform in [-1,1) per
  * component) are multiplied as C = A B^T by the kernel `which`
  * (0 = FP64 CUDA-core GEMM, 1 = BF16x3 tensor-core GEMM) and compared with
@@ -21,6 +24,26 @@ extern "C" {
  * Returns ADC_OK or a negative ADC_ERR_* code. */
 int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_t seed, int reps,
                   double *rel_err, double *ms);
+
+/* Per-kernel timing of one context. adc_profile_enable(ctx, 1) clears the
+ * record and starts recording a CUDA event pair around every GEMM launch on
+ * the context's stream (0 stops). adc_profile_read() synchronises the stream
+ * and returns one entry per kernel and sigma term ("tc_gemm_bf16x3/ladder",
+ * "zgemm_fp64/ring", ...): launches, total device milliseconds and the
+ * algorithmic flops of those launches (8 per complex multiply-add, no
+ * padding). *n receives the number of entries (at most max). */
+typedef struct {
+  char name[48];
+  int64_t launches;
+  double total_ms;
+  double flops;
+} adc_kernel_stat;
+
+int adc_profile_enable(adc_ctx_opaque *ctx, int on);
+int adc_profile_read(adc_ctx_opaque *ctx, adc_kernel_stat *out, int max, int *n);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+int64_t adc_launch_count(void);
 
 #ifdef __cplusplus
 }

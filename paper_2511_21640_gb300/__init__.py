@@ -50,6 +50,11 @@ class adc_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class adc_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("flops", ctypes.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
@@ -65,7 +70,11 @@ def _load():
         "adc_main_block": (I, [P, P]),
         "adc_davidson": (I, [P, I, D, I, I, P, I64, P, P, P, ctypes.POINTER(adc_stats)]),
         "adc_fns_density": (I, [P, P, P, P, D, ctypes.POINTER(I64), P, P]),
+        "adc_sync": (I, [P]),
         "adc_free": (None, [P]),
+        "adc_profile_enable": (I, [P, I]),
+        "adc_profile_read": (I, [P, ctypes.POINTER(adc_kernel_stat), I, ctypes.POINTER(I)]),
+        "adc_launch_count": (I64, []),
         "adc_strerror": (ctypes.c_char_p, [I]),
         "adc_last_error": (ctypes.c_char_p, [P]),
         "adc_diag_gemm": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
@@ -105,6 +114,15 @@ def _ptr(a, dtype):
     return ctypes.c_void_p(a.ctypes.data)
 
 
+def _on_cuda(*arrays):
+    return any(a is not None and _is_torch(a) and a.is_cuda for a in arrays)
+
+
+def _torch_sync():
+    import torch
+    torch.cuda.current_stream().synchronize()
+
+
 def _empty_like_kind(ref, shape, dtype):
     if ref is not None and _is_torch(ref):
         import torch
@@ -121,6 +139,10 @@ class Context:
         o = adc_opts()
         lib.adc_opts_default(ctypes.byref(o))
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if isinstance(stream, str) and stream == "torch":
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._shared_stream = stream is not None
         o.stream = stream
         o.block = block
         o.max_subspace = max_subspace
@@ -134,6 +156,8 @@ class Context:
         self._h = ctypes.c_void_p()
         self.kind = kind
         self.nocc, self.nvir, self.naux = nocc, nvir, naux
+        if _on_cuda(B, eps_occ, eps_vir) and not self._shared_stream:
+            _torch_sync()
         rc = lib.adc_init(ctypes.byref(self._h), _ptr(B, np.complex128), naux, _ptr(eps_occ, np.float64), nocc,
                           _ptr(eps_vir, np.float64), nvir, KINDS[kind] if isinstance(kind, str) else kind,
                           order, float(x), ctypes.byref(o))
@@ -167,8 +191,28 @@ class Context:
             raise ValueError("last dimension of X must be N")
         S = out if out is not None else _empty_like_kind(X, tuple(X.shape), np.complex128)
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        dev = _on_cuda(X, S)
+        if dev and not self._shared_stream:
+            _torch_sync()  # X was written on torch's stream
         _check(lib.adc_sigma(self._h, _ptr(X, np.complex128), _ptr(S, np.complex128), k, p), self._h)
+        if dev and not self._shared_stream:
+            _check(lib.adc_sync(self._h), self._h)  # S is read on torch's stream
         return S
+
+    def sync(self):
+        _check(lib.adc_sync(self._h), self._h)
+
+    def profile(self, on=True):
+        """Start (clear) or stop per-kernel CUDA-event timing (``adc_profile_enable``)."""
+        _check(lib.adc_profile_enable(self._h, 1 if on else 0), self._h)
+
+    def profile_read(self):
+        """Per kernel and sigma term: launches, total device ms, algorithmic flops."""
+        buf = (adc_kernel_stat * 64)()
+        n = ctypes.c_int()
+        _check(lib.adc_profile_read(self._h, buf, 64, ctypes.byref(n)), self._h)
+        return {buf[i].name.decode(): {"launches": buf[i].launches, "total_ms": buf[i].total_ms,
+                                       "flops": buf[i].flops} for i in range(n.value)}
 
     def diagonal(self):
         d = np.empty(self.N, dtype=np.float64)
@@ -221,5 +265,10 @@ def diag_gemm(which, M, N, K, seed=1, reps=3):
     return e.value, t.value
 
 
-__all__ = ["Context", "AdcError", "diag_gemm", "lib", "LIB_PATH", "ADC_IP", "ADC_EA", "ADC_EE",
+def launch_count():
+    """Kernels launched by the library in this process (``adc_launch_count``)."""
+    return int(lib.adc_launch_count())
+
+
+__all__ = ["Context", "AdcError", "diag_gemm", "launch_count", "lib", "LIB_PATH", "ADC_IP", "ADC_EA", "ADC_EE",
            "ADC_PREC_FP64", "ADC_PREC_BF16X3"]

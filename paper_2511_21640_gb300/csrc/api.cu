@@ -287,6 +287,16 @@ int adc_fns_density(adc_ctx *c, adc_c128 *D, double *eta, adc_c128 *V, double et
   ADC_API_CATCH(c)
 }
 
+int adc_sync(adc_ctx *c) {
+  if (!c) return ADC_ERR_STATE;
+  cudaError_t e = cudaStreamSynchronize(c->ex.stream);
+  if (e != cudaSuccess) {
+    c->err = cudaGetErrorString(e);
+    return ADC_ERR_CUDA;
+  }
+  return ADC_OK;
+}
+
 void adc_free(adc_ctx *c) { delete c; }
 
 const char *adc_strerror(int code) {

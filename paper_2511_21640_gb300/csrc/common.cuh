@@ -31,7 +31,13 @@ struct Error : public std::runtime_error {
                                            __FILE__ + ":" + std::to_string(__LINE__)); \
   } while (0)
 
-#define ADC_CHECK_LAUNCH() ADC_CUDA(cudaGetLastError())
+// every kernel launch site calls ADC_CHECK_LAUNCH(), which also counts it
+extern long long g_launches;
+#define ADC_CHECK_LAUNCH()                               \
+  do {                                                   \
+    __atomic_add_fetch(&::adc::g_launches, 1, __ATOMIC_RELAXED); \
+    ADC_CUDA(cudaGetLastError());                        \
+  } while (0)
 
 #define ADC_REQUIRE(cond, code, msg)                 \
   do {                                               \

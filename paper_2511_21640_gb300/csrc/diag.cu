@@ -93,3 +93,46 @@ extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_
     return e.code;
   }
 }
+
+extern "C" int adc_profile_enable(adc_ctx *c, int on) {
+  if (!c) return ADC_ERR_STATE;
+  try {
+    cudaStreamSynchronize(c->ex.stream);
+    c->ex.prof_clear();
+    c->ex.prof = (on != 0);
+    return ADC_OK;
+  } catch (const Error &e) {
+    return e.code;
+  }
+}
+
+extern "C" int adc_profile_read(adc_ctx *c, adc_kernel_stat *out, int max, int *n) {
+  if (!c || !n) return c ? ADC_ERR_ARG : ADC_ERR_STATE;
+  try {
+    ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+    std::vector<adc_kernel_stat> agg;
+    for (auto &r : c->ex.recs) {
+      float ms = 0.f;
+      ADC_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+      adc_kernel_stat *s = nullptr;
+      for (auto &a : agg)
+        if (r.name == a.name) s = &a;
+      if (!s) {
+        adc_kernel_stat z{};
+        snprintf(z.name, sizeof(z.name), "%s", r.name.c_str());
+        agg.push_back(z);
+        s = &agg.back();
+      }
+      s->launches += 1;
+      s->total_ms += ms;
+      s->flops += r.flops;
+    }
+    *n = (int)std::min<size_t>(agg.size(), (size_t)std::max(max, 0));
+    for (int i = 0; i < *n; ++i) out[i] = agg[i];
+    return ADC_OK;
+  } catch (const Error &e) {
+    return e.code;
+  }
+}
+
+extern "C" int64_t adc_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }

@@ -29,8 +29,10 @@ void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
   const bool sat = (c->order == 3 && c->x != 0.0);
   const double x = sat ? c->x : 0.0;
   // S1 = X1 M11^T  (S1[r][p] = sum_q M11[p][q] X1[r][q])
+  TagScope tg(ex, "main");
   zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, c->M11.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
   // S1 += X2 Cpl^T
+  ex.tag = "coupling";
   zgemm(ex, k, n1, n2, 1, C1(), X + n1, 0, N, 1, false, c->Cpl.c(), 0, 1, n2, false, C1(), S, 0, N, 1);
   // S2 = X1 conj(Cpl)
   zgemm(ex, k, n2, n1, 1, C1(), X, 0, N, 1, false, c->Cpl.c(), 0, n2, 1, true, C0(), S + n1, 0, N, 1);
@@ -40,9 +42,11 @@ void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
   if (c->kind == ADC_EA) {
     const int64_t pv = npairs(v);
     // ladder: S2[r][j][(ab)] += x sum_(cd) X2[r][j][(cd)] Glad[(ab)][(cd)]
+    ex.tag = "ladder";
     zgemm(ex, o, pv, pv, k, CR(x), X + n1, N, pv, 1, false, c->Glad.c(), 0, 1, pv, false, C1(),
           S + n1, N, pv, 1);
     // ring: Xf[r][k][c][b] (antisymmetric in c,b); T[r][(j,a)][b] = sum_(kc) W[(j,a)][(kc)] Xf[r][(kc)][b]
+    ex.tag = "ring";
     cplx *Xf = scratch(c, 2 * k * o * v * v);
     cplx *T = Xf + k * o * v * v;
     pair_unpack(ex, X + n1, k, o, N, pv, v, 1, Xf);
@@ -53,9 +57,11 @@ void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
   } else {
     const int64_t po = npairs(o);
     // ladder: S2[r][(ij)][a] += x sum_(kl) Glad[(ij)][(kl)] X2[r][(kl)][a]
+    ex.tag = "ladder";
     zgemm(ex, po, v, po, k, CR(x), c->Glad.c(), 0, po, 1, false, X + n1, N, v, 1, false, C1(),
           S + n1, N, v, 1);
     // ring: Xf[r][i][k][b]; T[r][(j,a)][i] = -sum_(kb) W[(j,a)][(kb)] Xf[r][i][(kb)]
+    ex.tag = "ring";
     cplx *Xf = scratch(c, 2 * k * o * o * v);
     cplx *T = Xf + k * o * o * v;
     pair_unpack(ex, X + n1, k, 1, N, 0, o, v, Xf);

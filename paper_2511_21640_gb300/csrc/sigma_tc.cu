@@ -35,8 +35,10 @@ void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
   const bool sat = (c->order == 3 && c->x != 0.0);
   const double x = sat ? c->x : 0.0;
   // S1 = X1 M11^T (FP64, n1 x n1)
+  TagScope tg(ex, "main");
   zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, c->M11.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
   // S1 += Cpl X2  : out[c][r] = sum_K Cpl[c][K] X2[r][K]
+  ex.tag = "coupling";
   tc_pack_B(ex, tc.Bx, X + n1, k, n2, N, 0, 1, 1, false);
   tc_gemm(ex, tc.Cpl, tc.Bx, n1, k, C1(), C1(), S, 1, N, 0, 1, err);
   // S2 = Cpl^H X1 : out[K][r] = sum_c conj(Cpl[c][K]) X1[r][c]
@@ -47,9 +49,11 @@ void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
     if (c->kind == ADC_EA) {
       const int64_t pv = npairs(v);
       // ladder: out[(ab)][(r,j)] = sum_(cd) Glad[(ab)][(cd)] X2[r][j][(cd)]
+      ex.tag = "ladder";
       tc_pack_B(ex, tc.Bx, X + n1, k * o, pv, N, pv, o, 1, false);
       tc_gemm(ex, tc.Glad, tc.Bx, pv, k * o, CR(x), C1(), S + n1, 1, N, pv, o, err);
       // ring: T[r][j][a][b] = sum_(kc) W[(j,a)][(kc)] Xf[r][k][c][b]
+      ex.tag = "ring";
       cplx *T = scratch(c, k * o * v * v);
       tc_pack_B_ring(ex, tc.Bx, c, X, k);
       tc_gemm(ex, tc.W, tc.Bx, o * v, k * v, C1(), C0(), T, v, o * v * v, 1, v, err);
@@ -57,9 +61,11 @@ void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
     } else {
       const int64_t po = npairs(o);
       // ladder: out[(ij)][(r,a)] = sum_(kl) Glad[(ij)][(kl)] X2[r][(kl)][a]
+      ex.tag = "ladder";
       tc_pack_B(ex, tc.Bx, X + n1, k * v, po, N, 1, v, v, false);
       tc_gemm(ex, tc.Glad, tc.Bx, po, k * v, CR(x), C1(), S + n1, v, N, 1, v, err);
       // ring: T[r][j][a][i] = -sum_(kb) W[(j,a)][(kb)] Xf[r][i][k][b]
+      ex.tag = "ring";
       cplx *T = scratch(c, k * o * v * o);
       tc_pack_B_ring(ex, tc.Bx, c, X, k);
       tc_gemm(ex, tc.W, tc.Bx, o * v, k * o, CR(-1.0), C0(), T, o, o * v * o, 1, o, err);

@@ -417,6 +417,8 @@ void launch_tc(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N2, 
   dim3 grid((unsigned)((N2 + BN - 1) / BN), (unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)ksplit);
   DBuf part;
   if (ksplit > 1) part = DBuf(ex, (size_t)ksplit * M * N2 * sizeof(float));
+  const int64_t Kc = A.kreal > 0 ? A.kreal : A.kp;
+  int pr = ex.prof_begin("tc_gemm_bf16x3", 8.0 * (double)M * (double)(N2 / 2) * (double)Kc);
   k_tc_gemm<BN, ST><<<grid, 192, L::SMEM, ex.stream>>>(mAh, mAl, mBh, mBl, (int)M, (int)N2, kps, kb_per_split,
                                                       out, s_m, s_nh, s_nl, n_in, alpha, beta,
                                                       ksplit > 1 ? (float *)part.p : nullptr, err);
@@ -426,12 +428,14 @@ void launch_tc(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N2, 
                                                                   s_nh, s_nl, n_in, alpha, beta);
     ADC_CHECK_LAUNCH();
   }
+  ex.prof_end(pr);
 }
 
 }  // namespace
 
 void tc_pack_A(Exec &ex, TcMat &dst, const cplx *src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, bool conj) {
   dst.rows = M;
+  dst.kreal = K;
   dst.kp = (K + TC_BK - 1) / TC_BK * TC_BK;
   if (dst.kp == 0) dst.kp = TC_BK;
   const size_t bytes = (size_t)M * 2 * dst.kp * sizeof(__nv_bfloat16);
@@ -447,6 +451,7 @@ void tc_pack_A(Exec &ex, TcMat &dst, const cplx *src, int64_t M, int64_t K, int6
 
 static void pack_B_impl(Exec &ex, TcMat &dst, const BSrc &s, int64_t Nc, int64_t K, bool conj) {
   dst.rows = 2 * Nc;
+  dst.kreal = K;
   dst.kp = (K + TC_BK - 1) / TC_BK * TC_BK;
   if (dst.kp == 0) dst.kp = TC_BK;
   const size_t bytes = (size_t)dst.rows * 2 * dst.kp * sizeof(__nv_bfloat16);

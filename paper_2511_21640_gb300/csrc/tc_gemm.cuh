@@ -10,7 +10,7 @@ namespace adc {
 // [rows][2*kp] (kp = K rounded up to 64). For A, rows = M; for B, rows = 2N.
 struct TcMat {
   DBuf hi, lo;
-  int64_t rows = 0, kp = 0;
+  int64_t rows = 0, kp = 0, kreal = 0;
 };
 
 // A[m][k] = op(src[m*s_m + k*s_k]) (op = conj when conj is set)

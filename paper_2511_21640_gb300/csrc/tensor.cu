@@ -32,6 +32,43 @@ void Exec::release(void *p, size_t bytes) {
   mem_used -= (int64_t)bytes;
 }
 
+long long g_launches = 0;
+
+cudaEvent_t Exec::event() {
+  if (!event_pool.empty()) {
+    cudaEvent_t e = event_pool.back();
+    event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  ADC_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+int Exec::prof_begin(const char *kernel, double flops) {
+  if (!prof) return -1;
+  ProfRec r;
+  r.name = std::string(kernel) + (tag.empty() ? "" : "/" + tag);
+  r.a = event();
+  r.b = event();
+  r.flops = flops;
+  ADC_CUDA(cudaEventRecord(r.a, stream));
+  recs.push_back(r);
+  return (int)recs.size() - 1;
+}
+
+void Exec::prof_end(int r) {
+  if (r >= 0) ADC_CUDA(cudaEventRecord(recs[r].b, stream));
+}
+
+void Exec::prof_clear() {
+  for (auto &r : recs) {
+    event_pool.push_back(r.a);
+    event_pool.push_back(r.b);
+  }
+  recs.clear();
+}
+
 void fill_zero(Exec &ex, void *p, size_t bytes) {
   if (bytes) ADC_CUDA(cudaMemsetAsync(p, 0, bytes, ex.stream));
 }
@@ -188,6 +225,7 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
     ksplit = (int)std::max<int64_t>(1, s);
   }
   const int64_t bmax = 65535 / ksplit;
+  int pr = ex.prof_begin("zgemm_fp64", 8.0 * (double)M * N * K * batch);
   for (int64_t b0 = 0; b0 < batch; b0 += bmax) {
     int64_t nb = std::min<int64_t>(bmax, batch - b0);
     dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)(nb * ksplit));
@@ -209,6 +247,7 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
       ADC_CHECK_LAUNCH();
     }
   }
+  ex.prof_end(pr);
 }
 
 // ------------------------------------------------------------------ permute

@@ -9,11 +9,26 @@ namespace adc {
 
 // Execution environment of one context: its stream and a byte budget for
 // every device allocation the context makes.
+struct ProfRec {
+  std::string name;
+  cudaEvent_t a = nullptr, b = nullptr;
+  double flops = 0.0;  // algorithmic flops of the launch (8 per complex multiply-add)
+};
+
 struct Exec {
   cudaStream_t stream = nullptr;
   int64_t mem_limit = 0;  // 0 = unlimited
   int64_t mem_used = 0;
   int64_t mem_peak = 0;
+  // per-kernel timing with CUDA events on this stream (off unless enabled)
+  bool prof = false;
+  std::string tag;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> event_pool;
+  cudaEvent_t event();
+  int prof_begin(const char *kernel, double flops);  // record index, -1 when off
+  void prof_end(int r);
+  void prof_clear();
 
   void *alloc(size_t bytes);           // cudaMallocAsync on the stream, counted
   void release(void *p, size_t bytes);  // cudaFreeAsync on the stream
@@ -43,6 +58,14 @@ struct DBuf {
   }
   cplx *c() const { return (cplx *)p; }
   double *d() const { return (double *)p; }
+};
+
+// names the sigma term whose kernels are being launched (for the profile)
+struct TagScope {
+  Exec &ex;
+  std::string old;
+  TagScope(Exec &e, const char *t) : ex(e), old(e.tag) { ex.tag = t; }
+  ~TagScope() { ex.tag = old; }
 };
 
 inline DBuf cbuf(Exec &e, int64_t n) { return DBuf(e, (size_t)n * sizeof(cplx)); }

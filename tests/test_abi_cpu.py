@@ -16,8 +16,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2511_21640_gb300.build import build
-    build()
+    from conftest import build_library
+    build_library()
     import paper_2511_21640_gb300 as m
     return m
 

@@ -26,8 +26,8 @@ from oracle.fns import fns_density, fns_basis  # noqa: E402
 def gpu():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_2511_21640_gb300.build import build
-    build()
+    from conftest import build_library
+    build_library()
     import paper_2511_21640_gb300 as m
     return m
 
