@@ -37,6 +37,10 @@ from synthetic import CONFIGS, config_problem, random_vectors  # noqa: E402
 METRIC = "Davidson s/root and sigma TFLOP/s: mixed vs FP64 on GPU at 1e-6 Eh error"
 
 
+def log(*a):
+    print(f"[bench {time.strftime('%H:%M:%S')}]", *a, file=sys.stderr, flush=True)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -191,6 +195,7 @@ def main():
     ctx = adcgpu.Context(B, eo, ev, kind=kind, order=order, x=x, stream="torch")
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
+    log(f"init {init_s:.1f} s, N = {ctx.N}")
     stream = torch.cuda.current_stream()
 
     def solve(prec, t=tol):
@@ -198,6 +203,7 @@ def main():
 
     for _ in range(args.warmup):
         om, _, e64, st, rc = solve("bf16x3")
+        log("warmup solve", st)
     # ---- timed region
     clocks = Clocks()
     clocks.start()
@@ -221,6 +227,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     launches = adcgpu.launch_count() - l0
+    log(f"timed {ms:.1f} ms for {args.steps} steps")
     prof = ctx.profile_read()
     ctx.profile(False)
     clk = clocks.stop()
@@ -270,6 +277,7 @@ def main():
         ctx.profile(False)
         fl = sum(e["flops"] for e in pr.values()) / reps
         sig[prec] = {"ms": t, "tflops": fl / (t * 1e-3) / 1e12, "flops": fl}
+    log("sigma", sig)
     S64 = ctx.sigma(Xs, "fp64")
     Smx = ctx.sigma(Xs, "bf16x3")
     sig_rel = float(((Smx - S64).abs().pow(2).sum(1).sqrt() / S64.abs().pow(2).sum(1).sqrt()).max().item())
@@ -282,6 +290,7 @@ def main():
         om64, _, e6, st6, rc6 = ctx.davidson(nroots, tol=tol, max_iter=300, precision="fp64", want_vectors=False)
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t1
+        log(f"fp64 davidson {t64:.1f} s", st6)
         fp64 = {"s_per_root": t64 / nroots, "iterations": st6["iterations"], "sigma_calls": st6["sigma_calls"],
                 "max_eig_diff_vs_mixed": float(np.abs(om64 - om).max()), "rc": rc6}
 
@@ -296,6 +305,7 @@ def main():
             om2, _, e2, st2, rc2 = c2.davidson(nroots, tol=tol, max_iter=300, precision="bf16x3",
                                                want_vectors=False)
         te2e = time.perf_counter() - t2
+        log(f"e2e {te2e:.1f} s")
         e2e = {"value": te2e / nroots, "unit": "s/root", "h2d_bytes_per_step": int(p.B.nbytes + 8 * (o + v)),
                "d2h_bytes_per_step": int(16 * nroots), "includes": "adc_init (H2D copy + operator setup) + adc_davidson"}
 

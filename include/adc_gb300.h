@@ -127,16 +127,18 @@ int adc_diagonal(adc_ctx *ctx, double *diag);
 int adc_main_block(adc_ctx *ctx, adc_c128 *M11);
 
 /* Lowest nroots eigenpairs of M (Eq. 10: M X = X Omega, X^H X = 1) by a
- * block Davidson method. Subspace matrices, Rayleigh-Ritz, residual norms,
- * orthogonalisation and denominators are always FP64. With
- * precision = ADC_PREC_BF16X3 the trial-vector sigma products run on the
- * tensor cores until the residuals stall near the split-precision floor;
- * the method then switches to FP64 sigma products, keeping the subspace,
- * until every FP64 residual norm is <= tol.
- *   guess   NULL, or [nguess][N] starting vectors (orthonormalised inside).
+ * block Davidson method. Subspace matrices, Rayleigh-Ritz (device Jacobi),
+ * residual norms, Gram-Schmidt and the diagonal preconditioner are always
+ * FP64. With precision = ADC_PREC_BF16X3 the trial-vector sigma products run
+ * on the tensor cores; when the residuals stop decreasing the subspace is
+ * collapsed onto the Ritz vectors and their sigma is recomputed in FP64
+ * (sigma(y + d) = sigma64(y) + sigma_bf16x3(d)); couplings between those FP64
+ * base vectors and later corrections come from the FP64 products. A result
+ * is accepted only when every FP64 residual norm ||M y - omega y|| <= tol.
+ *   guess   NULL, or [nguess][N] starting vectors (nguess >= nroots).
  *   omega   [nroots] eigenvalues, ascending (host or device).
  *   Y       NULL or [nroots][N] eigenvectors.
- *   err64   NULL or [nroots] FP64 residual norms ||M y - omega y||.
+ *   err64   NULL or [nroots] FP64 residual norms.
  *   st      NULL or statistics.
  * Returns ADC_ERR_NOCONV (with the best results written) if max_iter is hit. */
 int adc_davidson(adc_ctx *ctx, int nroots, double tol, int max_iter,

@@ -8,9 +8,13 @@
 //   2. refinement: the subspace is collapsed onto the current Ritz vectors and
 //      their sigma is recomputed in FP64, so that sigma(y + delta) =
 //      sigma64(y) + sigma_mixed(delta); new correction vectors keep using the
-//      tensor-core product. Every collapse (subspace full, stall, or apparent
-//      convergence) recomputes sigma64 of the Ritz vectors, and convergence is
-//      only accepted on FP64 residuals ||sigma64(y) - omega y|| <= tol.
+//      tensor-core product. The projected couplings between an FP64 base
+//      vector b and a correction t are taken as <sigma64(b)|t> (M is
+//      Hermitian), so split-precision noise enters only the correction-
+//      correction block, whose weight shrinks with the residual. Every
+//      collapse (subspace full, stall, or apparent convergence) recomputes
+//      sigma64 of the Ritz vectors, and convergence is only accepted on FP64
+//      residuals ||sigma64(y) - omega y|| <= tol.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -111,13 +115,15 @@ struct Davidson {
   adc_ctx *c;
   Exec &ex;
   int64_t N;
-  int nroots, mmax;
+  int nroots, mmax, krmax;
   DBuf V, AV, G, H, Cv, w, T, Y, SY, R, nrm, rowsb, info, tmp;
   adc_stats st{};
   double tsig = 0.0;
   int m = 0;
+  int nb = 0;  // leading subspace vectors whose sigma is FP64
 
-  Davidson(adc_ctx *c_, int nr, int mmax_) : c(c_), ex(c_->ex), N(c_->N), nroots(nr), mmax(mmax_) {
+  Davidson(adc_ctx *c_, int nr, int mmax_, int krmax_)
+      : c(c_), ex(c_->ex), N(c_->N), nroots(nr), mmax(mmax_), krmax(krmax_) {
     V = cbuf(ex, (int64_t)mmax * N);
     AV = cbuf(ex, (int64_t)mmax * N);
     G = cbuf(ex, (int64_t)mmax * mmax);
@@ -125,8 +131,8 @@ struct Davidson {
     Cv = cbuf(ex, (int64_t)mmax * mmax);
     w = DBuf(ex, mmax * sizeof(double));
     T = cbuf(ex, (int64_t)nr * N);
-    Y = cbuf(ex, (int64_t)nr * N);
-    SY = cbuf(ex, (int64_t)nr * N);
+    Y = cbuf(ex, (int64_t)krmax * N);
+    SY = cbuf(ex, (int64_t)krmax * N);
     R = cbuf(ex, (int64_t)nr * N);
     nrm = DBuf(ex, mmax * sizeof(double));
     rowsb = DBuf(ex, mmax * sizeof(int));
@@ -148,6 +154,11 @@ struct Davidson {
     int mt = m0 + na;
     zgemm(ex, mt, na, N, 1, C1(), V.c(), 0, N, 1, true, AV.c() + (int64_t)m0 * N, 0, 1, N, false,
           C0(), G.c() + m0, 0, mmax, 1);
+    if (nb > 0 && m0 >= nb) {
+      // rows of the FP64 base: <b|M|t> = <sigma64(b)|t>
+      zgemm(ex, nb, na, N, 1, C1(), AV.c(), 0, N, 1, true, V.c() + (int64_t)m0 * N, 0, 1, N, false, C0(),
+            G.c() + m0, 0, mmax, 1);
+    }
     if (m0 > 0) {
       k_fill_lower<<<(na * m0 + 255) / 256, 256, 0, ex.stream>>>(G.c(), mmax, m0, na);
       ADC_CHECK_LAUNCH();
@@ -199,15 +210,16 @@ struct Davidson {
     return acc;
   }
 
-  // Rayleigh-Ritz on V[0:m]: w (host copy), Y, SY, R for the lowest nroots
+  // Rayleigh-Ritz on V[0:m]: w (host copy), Y, SY for the lowest kr, R for nroots
   std::vector<double> ritz(int nr) {
+    nr = std::min(std::max(nr, nroots), std::min(m, krmax));
     k_hermitize<<<(m * m + 255) / 256, 256, 0, ex.stream>>>(G.c(), mmax, m, H.c(), mmax);
     ADC_CHECK_LAUNCH();
     jacobi_eigh(ex, H.c(), m, mmax, w.d(), Cv.c(), mmax, (int *)info.p);
     // Y[r][n] = sum_i Cv[i][r] V[i][n]
     zgemm(ex, nr, N, m, 1, C1(), Cv.c(), 0, 1, mmax, false, V.c(), 0, N, 1, false, C0(), Y.c(), 0, N, 1);
     zgemm(ex, nr, N, m, 1, C1(), Cv.c(), 0, 1, mmax, false, AV.c(), 0, N, 1, false, C0(), SY.c(), 0, N, 1);
-    k_residual<<<grid1d((int64_t)nr * N, 256), 256, 0, ex.stream>>>(SY.c(), Y.c(), w.d(), nr, N, R.c());
+    k_residual<<<grid1d((int64_t)nroots * N, 256), 256, 0, ex.stream>>>(SY.c(), Y.c(), w.d(), nroots, N, R.c());
     ADC_CHECK_LAUNCH();
     std::vector<double> wh(m);
     ADC_CUDA(cudaMemcpyAsync(wh.data(), w.d(), m * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
@@ -222,8 +234,10 @@ struct Davidson {
     else
       ADC_CUDA(cudaMemcpyAsync(AV.c(), SY.c(), (int64_t)nr * N * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
     m = 0;
+    nb = 0;
     extend_projection(0, nr);
     m = nr;
+    nb = fp64_sigma ? nr : 0;
   }
 };
 
@@ -235,10 +249,11 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   ADC_REQUIRE(tol > 0.0, ADC_ERR_ARG, "tol must be positive");
   ADC_REQUIRE(precision == ADC_PREC_FP64 || precision == ADC_PREC_BF16X3, ADC_ERR_ARG, "precision");
   const int kb = std::max(nroots, c->opts.block);
-  int mmax = c->opts.max_subspace > 0 ? c->opts.max_subspace : std::max(6 * kb, 3 * kb + 2 * nroots);
+  int mmax = c->opts.max_subspace > 0 ? c->opts.max_subspace : std::max(8 * kb, 40);
   mmax = (int)std::min<int64_t>(std::min<int64_t>(mmax, N), 1024);
   mmax = std::max(mmax, std::min<int>((int)N, nroots + 1));
-  Davidson d(c, nroots, mmax);
+  const int krmax = std::min(mmax, std::max(2 * nroots, kb));
+  Davidson d(c, nroots, mmax, krmax);
   Exec &ex = c->ex;
 
   // ---- starting space
@@ -278,59 +293,55 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   int prec_new = (phase == 2) ? ADC_PREC_FP64 : ADC_PREC_BF16X3;
   d.apply_sigma(d.V.c(), d.AV.c(), m0, prec_new);
   d.m = 0;
+  d.nb = 0;
   d.extend_projection(0, m0);
   d.m = m0;
 
-  std::vector<double> wh, rn(nroots, 0.0), hist;
+  std::vector<double> wh, rn(nroots, 0.0);
   bool converged = false;
+  double best = 1e300;
+  int since = 0;
+  const int stall_window = 5;
   int it = 0;
-  const int nr = std::min<int>(nroots, d.m);
   for (it = 1; it <= max_iter; ++it) {
-    wh = d.ritz(std::min(nroots, d.m));
+    const int kr = std::min(d.m, krmax);
+    wh = d.ritz(kr);
     rn = d.row_norms(d.R.c(), nroots);
     double mx = *std::max_element(rn.begin(), rn.end());
     ADC_REQUIRE(std::isfinite(mx), ADC_ERR_NUMERIC, "non-finite residual norm in Davidson");
     if (c->opts.verbose)
-      fprintf(stderr, "[davidson] it %d phase %d m %d max|r| %.3e w0 %.12f\n", it, phase, d.m, mx, wh[0]);
-    hist.push_back(mx);
+      fprintf(stderr, "[davidson] it %d phase %d m %d nb %d max|r| %.3e w0 %.12f\n", it, phase, d.m, d.nb, mx, wh[0]);
     d.st.iterations = it;
-    if (phase == 1) d.st.iterations_fp64++;
-    if (phase == 2) d.st.iterations_fp64++;
+    if (phase != 0) d.st.iterations_fp64++;
+    if (mx < 0.7 * best) { best = mx; since = 0; }
+    else ++since;
     if (mx <= tol) {
       if (phase == 2) { converged = true; break; }
-      // verify on FP64 residuals: collapse with sigma64
-      d.collapse(nroots, true);
+      // accept only on FP64 residuals: collapse with sigma64 and re-check
+      d.collapse(kr, true);
       phase = 1;
-      wh = d.ritz(nroots);
+      wh = d.ritz(kr);
       rn = d.row_norms(d.R.c(), nroots);
       mx = *std::max_element(rn.begin(), rn.end());
       if (c->opts.verbose) fprintf(stderr, "[davidson] fp64 check max|r| %.3e\n", mx);
       if (mx <= tol) { converged = true; break; }
-      hist.clear();
-    } else if (phase == 0) {
-      // stall of the mixed phase: no 2x improvement over the last 3 iterations
-      size_t h = hist.size();
-      if (h >= 4 && hist[h - 1] > 0.5 * hist[h - 4]) {
-        d.collapse(nroots, true);
-        phase = 1;
-        hist.clear();
-        continue;
-      }
-    } else if (phase == 1) {
-      size_t h = hist.size();
-      if (h >= 4 && hist[h - 1] > 0.5 * hist[h - 4]) {
-        d.collapse(nroots, true);
-        hist.clear();
-        continue;
-      }
+      best = mx;
+      since = 0;
+    } else if (phase != 2 && since >= stall_window) {
+      // stalled at the split-precision floor: FP64 base for the current Ritz vectors
+      d.collapse(kr, true);
+      phase = 1;
+      best = 1e300;
+      since = 0;
+      continue;
     }
     // new correction vectors for the unconverged roots
     std::vector<int> rows;
     for (int r = 0; r < nroots; ++r)
       if (rn[r] > tol) rows.push_back(r);
     if (d.m + (int)rows.size() > d.mmax) {
-      d.collapse(nroots, phase == 1);
-      wh = d.ritz(nroots);
+      d.collapse(kr, phase == 1);
+      wh = d.ritz(kr);
     }
     ADC_CUDA(cudaMemcpyAsync(d.rowsb.p, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice, ex.stream));
     k_precondition<<<grid1d((int64_t)rows.size() * N, 256), 256, 0, ex.stream>>>(
@@ -348,8 +359,9 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   if (it > max_iter) it = max_iter;
   if (!converged && phase != 2) {
     // report FP64 residuals of the best vectors
-    d.collapse(nroots, true);
-    wh = d.ritz(nroots);
+    const int kr = std::min(d.m, krmax);
+    d.collapse(kr, true);
+    wh = d.ritz(kr);
     rn = d.row_norms(d.R.c(), nroots);
   }
   ADC_CUDA(cudaStreamSynchronize(ex.stream));
@@ -365,7 +377,6 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   d.st.time_sigma_s = d.tsig;
   d.st.max_residual = *std::max_element(rn.begin(), rn.end());
   if (st_out) *st_out = d.st;
-  (void)nr;
   return converged ? ADC_OK : ADC_ERR_NOCONV;
 }
 
