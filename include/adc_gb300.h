@@ -158,6 +158,17 @@ int adc_fns_density(adc_ctx *ctx, adc_c128 *D, double *eta, adc_c128 *V,
                     double eta_crit, int64_t *n_keep, adc_c128 *U,
                     double *eps_new);
 
+/* Cholesky vectors in the truncated natural-spinor basis (Eq. 30 applied as
+ * the MO transformation of Eq. 42 to the virtual block):
+ *   B'_oo = B_oo,  B'_ov = B_ov U,  B'_vo = U^H B_vo,  B'_vv = U^H B_vv U.
+ *   U     [nvir][ldu], its first n_keep columns used (as written by
+ *         adc_fns_density with ldu = nvir); host or device.
+ *   Bout  [naux][nocc + n_keep][nocc + n_keep]; host or device, caller-owned.
+ * With the eps_new of adc_fns_density, (Bout, eps_occ, eps_new) define the
+ * ADC problem in the FNS basis (a new context). */
+int adc_fns_transform(adc_ctx *ctx, const adc_c128 *U, int64_t ldu,
+                      int64_t n_keep, adc_c128 *Bout);
+
 /* Blocks until all work the context has queued on its stream is done. Needed
  * after an asynchronous call with device pointers before another stream (or
  * the host) reads the outputs. */

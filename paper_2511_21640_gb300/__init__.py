@@ -71,6 +71,7 @@ def _load():
         "adc_davidson": (I, [P, I, D, I, I, P, I64, P, P, P, ctypes.POINTER(adc_stats)]),
         "adc_fns_density": (I, [P, P, P, P, D, ctypes.POINTER(I64), P, P]),
         "adc_sync": (I, [P]),
+        "adc_fns_transform": (I, [P, P, I64, I64, P]),
         "adc_free": (None, [P]),
         "adc_profile_enable": (I, [P, I]),
         "adc_profile_read": (I, [P, ctypes.POINTER(adc_kernel_stat), I, ctypes.POINTER(I)]),
@@ -198,6 +199,19 @@ class Context:
         if dev and not self._shared_stream:
             _check(lib.adc_sync(self._h), self._h)  # S is read on torch's stream
         return S
+
+    def fns_transform(self, U, n_keep=None):
+        """Cholesky vectors in the truncated natural-spinor basis (``adc_fns_transform``)."""
+        U = np.ascontiguousarray(U, dtype=np.complex128) if not _is_torch(U) else U
+        nk = U.shape[1] if n_keep is None else int(n_keep)
+        n2 = self.nocc + nk
+        Bo = _empty_like_kind(U, (self.naux, n2, n2), np.complex128)
+        dev = _on_cuda(U, Bo)
+        if dev and not self._shared_stream:
+            _torch_sync()
+        _check(lib.adc_fns_transform(self._h, _ptr(U, np.complex128), U.shape[1], nk, _ptr(Bo, np.complex128)),
+               self._h)
+        return Bo
 
     def sync(self):
         _check(lib.adc_sync(self._h), self._h)

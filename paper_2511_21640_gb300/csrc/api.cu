@@ -12,6 +12,7 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
                  int64_t nguess, double *omega, cplx *Yout, double *err64, adc_stats *st_out);
 void fns_run(adc_ctx *c, cplx *D, double *eta, cplx *Vout, double eta_crit, int64_t *n_keep, cplx *U,
              double *eps_new);
+void fns_transform(adc_ctx *c, const cplx *U, int64_t ldu, int64_t nk, cplx *Bout);
 }  // namespace adc
 
 using namespace adc;
@@ -283,6 +284,20 @@ int adc_fns_density(adc_ctx *c, adc_c128 *D, double *eta, adc_c128 *V, double et
   dD.finish(c->ex); dE.finish(c->ex); dV.finish(c->ex); dU.finish(c->ex); dN.finish(c->ex);
   ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
   *n_keep = nk;
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
+int adc_fns_transform(adc_ctx *c, const adc_c128 *U, int64_t ldu, int64_t n_keep, adc_c128 *Bout) {
+  if (!c) return ADC_ERR_STATE;
+  if (!Bout || n_keep < 0 || n_keep > c->v || (n_keep > 0 && (!U || ldu < n_keep))) return ADC_ERR_ARG;
+  ADC_API_TRY
+  const int64_t n2 = c->o + n_keep;
+  DevIn uin(c->ex, U, n_keep > 0 ? (size_t)c->v * ldu * sizeof(cplx) : 0);
+  DevOut bout(c->ex, Bout, (size_t)c->Q * n2 * n2 * sizeof(cplx));
+  fns_transform(c, (const cplx *)uin.p, ldu, n_keep, (cplx *)bout.p);
+  bout.finish(c->ex);
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
   return ADC_OK;
   ADC_API_CATCH(c)
 }

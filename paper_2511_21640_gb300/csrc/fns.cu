@@ -66,4 +66,26 @@ void fns_run(adc_ctx *c, cplx *D, double *eta, cplx *Vout, double eta_crit, int6
   ADC_CUDA(cudaStreamSynchronize(ex.stream));
 }
 
+// B' in the truncated basis: oo copied, ov = B_ov U, vo = U^H B_vo, vv = U^H B_vv U
+void fns_transform(adc_ctx *c, const cplx *U, int64_t ldu, int64_t nk, cplx *Bout) {
+  Exec &ex = c->ex;
+  const int64_t o = c->o, v = c->v, Q = c->Q, nmo = c->nmo, n2 = o + nk;
+  const cplx *B = c->B.c();
+  const int64_t sQ = nmo * nmo, sQo = n2 * n2;
+  // oo block: one strided 2-D copy per Cholesky vector
+  for (int64_t q = 0; q < Q; ++q)
+    ADC_CUDA(cudaMemcpy2DAsync(Bout + q * sQo, n2 * sizeof(cplx), B + q * sQ, nmo * sizeof(cplx), o * sizeof(cplx),
+                               o, cudaMemcpyDeviceToDevice, ex.stream));
+  if (nk == 0) return;
+  // ov: Bout[Q][i][o+l] = sum_a B[Q][i][o+a] U[a][l]
+  zgemm(ex, o, nk, v, Q, C1(), B + o, sQ, nmo, 1, false, U, 0, ldu, 1, false, C0(), Bout + o, sQo, n2, 1);
+  // vo: Bout[Q][o+l][i] = sum_a conj(U[a][l]) B[Q][o+a][i]
+  zgemm(ex, nk, o, v, Q, C1(), U, 0, 1, ldu, true, B + o * nmo, sQ, nmo, 1, false, C0(), Bout + o * n2, sQo, n2, 1);
+  // vv: T[Q][a][m] = sum_b B[Q][o+a][o+b] U[b][m]; Bout[Q][o+l][o+m] = sum_a conj(U[a][l]) T[Q][a][m]
+  DBuf T = cbuf(ex, Q * v * nk);
+  zgemm(ex, v, nk, v, Q, C1(), B + o * nmo + o, sQ, nmo, 1, false, U, 0, ldu, 1, false, C0(), T.c(), v * nk, nk, 1);
+  zgemm(ex, nk, nk, v, Q, C1(), U, 0, 1, ldu, true, T.c(), v * nk, nk, 1, false, C0(), Bout + o * n2 + o, sQo, n2, 1);
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+}
+
 }  // namespace adc

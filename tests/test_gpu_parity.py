@@ -179,3 +179,26 @@ def test_error_codes(gpu):
         with pytest.raises(gpu.AdcError) as e:
             ctx.sigma(np.zeros((1, ctx.N), np.complex128), precision=7)
         assert e.value.code == -1
+
+
+def test_fns_transform_and_invariance(gpu):
+    from oracle.fns import transform_cholesky
+    o, v, Q = 5, 22, 40
+    p = make_problem(o, v, Q, seed=33, sigma=0.07)
+    Dref = fns_density(p.B, p.eps_occ, p.eps_vir)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP", order=3, x=1.0) as ctx:
+        full = ctx.fns_density(-1.0)      # keep every natural spinor
+        assert full["n_keep"] == v
+        Bf = ctx.fns_transform(full["U"])
+        trunc = ctx.fns_density(float(np.sort(full["eta"])[::-1][11]))
+        Bt = ctx.fns_transform(trunc["U"])
+        w_can, _, _, _, _ = ctx.davidson(3, tol=1e-9, precision="fp64", want_vectors=False)
+    # transformation matches the oracle for the same U
+    assert np.abs(Bf - transform_cholesky(p.B, o, full["U"])).max() < 1e-13
+    assert np.abs(Bt - transform_cholesky(p.B, o, trunc["U"])).max() < 1e-13
+    assert Bt.shape == (Q, o + 12, o + 12)
+    # keeping every natural spinor is a unitary rotation of the virtuals with the
+    # Fock matrix semicanonical (diagonal), so the IP spectrum is unchanged
+    with gpu.Context(Bf, p.eps_occ, full["eps_new"], kind="IP", order=3, x=1.0) as c2:
+        w_fns, _, _, _, _ = c2.davidson(3, tol=1e-9, precision="fp64", want_vectors=False)
+    assert np.abs(w_fns - w_can).max() < 1e-8
