@@ -120,6 +120,26 @@ int adc_dims(const adc_ctx *ctx, int64_t *n1, int64_t *n2);
 int adc_sigma(adc_ctx *ctx, const adc_c128 *X, adc_c128 *S, int64_t k,
               int precision);
 
+/* The FP64 product of adc_sigma for callers that cannot allocate GPU memory
+ * during the call (device memory owned by another allocator, regions where
+ * cudaMalloc is forbidden or would synchronise the device, code that must not
+ * fail with out-of-memory halfway). No counterpart in the paper: it is a
+ * variant of adc_sigma's FP64 path. It calls no cudaMalloc, cudaFree or
+ * allocating library routine; every per-call intermediate lives in one
+ * file-scope __device__ array of 64 MiB that each GPU loading the library
+ * holds until the process exits.
+ *   X, S   [k][N] device pointers (host pointers give ADC_ERR_ARG).
+ *   Sizes whose intermediates exceed the array (2 k o v^2 complex elements
+ *   for EA, 2 k o^2 v for IP, order 3) give ADC_ERR_ARG with the required
+ *   size; call again with fewer vectors.
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture. Every call shares the array and overwrites what it needs
+ * (nothing is assumed to start at zero), so calls whose work overlaps on the
+ * GPU (other streams, other contexts, other threads) race: serialise them.
+ * Asynchronous on the context's stream. */
+int adc_sigma_noalloc(adc_ctx *ctx, const adc_c128 *X, adc_c128 *S, int64_t k);
+
 /* Exact diagonal of M as real numbers, [N] (host or device). */
 int adc_diagonal(adc_ctx *ctx, double *diag);
 

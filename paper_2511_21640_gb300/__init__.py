@@ -66,6 +66,7 @@ def _load():
         "adc_init": (I, [ctypes.POINTER(P), P, I64, P, I64, P, I64, I, I, D, ctypes.POINTER(adc_opts)]),
         "adc_dims": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "adc_sigma": (I, [P, P, P, I64, I]),
+        "adc_sigma_noalloc": (I, [P, P, P, I64]),
         "adc_diagonal": (I, [P, P]),
         "adc_main_block": (I, [P, P]),
         "adc_davidson": (I, [P, I, D, I, I, P, I64, P, P, P, ctypes.POINTER(adc_stats)]),

@@ -250,6 +250,52 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
   ex.prof_end(pr);
 }
 
+void zgemm_ws(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha, const cplx *A,
+              int64_t sAb, int64_t sAm, int64_t sAk, bool conjA, const cplx *B, int64_t sBb, int64_t sBk,
+              int64_t sBn, bool conjB, cplx beta, cplx *C, int64_t sCb, int64_t sCm, int64_t sCn, cplx *ws,
+              int64_t ws_elems) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  if (K < 0) K = 0;
+  ADC_REQUIRE((M + BM - 1) / BM <= 65535, ADC_ERR_UNSUPPORTED, "zgemm: M too large");
+  int a_kfast = (sAk == 1) ? 1 : 0;
+  int b_nfast = (sBn == 1) ? 1 : 0;
+  dim3 block(256);
+  const int64_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  // same split-K choice as zgemm, capped by the workspace the caller provides
+  int ksplit = 1;
+  const int64_t want = 2 * (int64_t)num_sms();
+  if (tiles * batch < want && K > 2048) {
+    int64_t s = (want + tiles * batch - 1) / (tiles * batch);
+    s = std::min<int64_t>(s, K / 1024);
+    s = std::min<int64_t>(s, 256);
+    ksplit = (int)std::max<int64_t>(1, s);
+  }
+  const int64_t bmax = 65535 / ksplit;
+  for (int64_t b0 = 0; b0 < batch; b0 += bmax) {
+    int64_t nb = std::min<int64_t>(bmax, batch - b0);
+    int ks = ksplit;
+    if (ks > 1 && ws) ks = (int)std::max<int64_t>(1, std::min<int64_t>(ks, ws_elems / std::max<int64_t>(1, nb * M * N)));
+    if (!ws) ks = 1;
+    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)(nb * ks));
+    if (ks == 1) {
+      k_zgemm<<<grid, block, 0, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B, sBb, sBk, sBn,
+                                             conjB ? 1 : 0, b_nfast, C, sCb, sCm, sCn, alpha, beta, b0, 1, K,
+                                             nullptr, nb);
+      ADC_CHECK_LAUNCH();
+    } else {
+      int64_t kchunk = (K + ks - 1) / ks;
+      kchunk = (kchunk + BKK - 1) / BKK * BKK;
+      k_zgemm<<<grid, block, 0, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B, sBb, sBk, sBn,
+                                             conjB ? 1 : 0, b_nfast, C, sCb, sCm, sCn, alpha, beta, b0, ks, kchunk,
+                                             ws, nb);
+      ADC_CHECK_LAUNCH();
+      k_splitk_reduce<<<grid1d(nb * M * N, 256), 256, 0, ex.stream>>>(ws, ks, nb, M, N, C, sCb, sCm, sCn, alpha,
+                                                                      beta, b0);
+      ADC_CHECK_LAUNCH();
+    }
+  }
+}
+
 // ------------------------------------------------------------------ permute
 namespace {
 constexpr int MAXD = 8;

@@ -96,6 +96,13 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
            const cplx *B, int64_t sBb, int64_t sBk, int64_t sBn, bool conjB, cplx beta,
            cplx *C, int64_t sCb, int64_t sCm, int64_t sCn);
 
+// zgemm without any allocation: split-K partial sums go to ws (ws_elems complex
+// elements; fewer splits when it is small, none when ws is NULL)
+void zgemm_ws(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
+              const cplx *A, int64_t sAb, int64_t sAm, int64_t sAk, bool conjA,
+              const cplx *B, int64_t sBb, int64_t sBk, int64_t sBn, bool conjB, cplx beta,
+              cplx *C, int64_t sCb, int64_t sCm, int64_t sCn, cplx *ws, int64_t ws_elems);
+
 // dst (contiguous, extents ext) = alpha * op(src at strides sstr) + beta * dst
 void permute(Exec &ex, const cplx *src, const std::vector<int64_t> &ext,
              const std::vector<int64_t> &sstr, bool conj, cplx *dst, cplx alpha, cplx beta);
