@@ -179,6 +179,8 @@ def main():
         dist.init_process_group("nccl")
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    # a dedicated stream shared with the library, so CUDA events on it bracket the library's kernels
+    torch.cuda.set_stream(torch.cuda.Stream())
     import paper_2511_21640_gb300 as adcgpu
 
     cfg = dict(CONFIGS[args.config])
