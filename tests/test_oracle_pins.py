@@ -223,3 +223,75 @@ def test_p8_davidson_matches_dense(kind):
     assert np.all(rn <= 1e-9)
     assert np.abs(Y.conj() @ Y.T - np.eye(4)).max() < 1e-10
     assert np.abs(Y @ M.T - wd[:, None] * Y).max() < 1e-8
+
+
+# ---------------------------------------------------------------- EE (Eq. 2 manifold)
+from oracle import adc_ee  # noqa: E402
+
+
+@pytest.mark.parametrize("o,v,seed", [(3, 4, 3), (2, 5, 7), (4, 3, 9)])
+def test_p5_ee_blocks_equal_brute_force_isr_series(o, v, seed):
+    p = make_problem(o, v, 6, seed=seed, sigma=0.3)
+    r = isr_series(_eps(p), p.B, o, "EE", nord=4)
+    M, n1 = r["M"], r["n1"]
+    bl = adc_ee.Blocks(p.B, p.eps_occ, p.eps_vir)
+    scale = np.abs(M).max()
+    for n in range(4):
+        assert np.abs(M[n][:n1, :n1] - bl.MSS[n]).max() < 1e-13 * scale, ("SS", n)
+    for n in range(3):
+        assert np.abs(M[n][:n1, n1:] - bl.MSD[n]).max() < 1e-13 * scale, ("SD", n)
+    for n in range(2):
+        assert np.abs(M[n][n1:, n1:] - bl.MDD[n]).max() < 1e-13 * scale, ("DD", n)
+    assert np.abs(M[3][:n1, n1:]).max() > 1e-6 and np.abs(M[2][n1:, n1:]).max() > 1e-6
+
+
+def test_p4_ee_error_order_against_fci():
+    o, v = 3, 4
+    p = make_problem(o, v, 5, seed=21, sigma=0.35)
+    eps = _eps(p)
+    lams = np.array([0.02, 0.04, 0.08])
+    errs = {2: [], 3: [], "x": []}
+    for lam in lams:
+        w = fci_energies(eps, p.B, o, lam, o, nroots=2)
+        exact = w[1] - w[0]
+        Bl = np.sqrt(lam) * p.B
+        for key, (order, x) in {2: (2, 0.0), 3: (3, 1.0), "x": (3, 0.5)}.items():
+            M = adc_ee.explicit_matrix(order, x, Bl, p.eps_occ, p.eps_vir)
+            errs[key].append(abs(np.linalg.eigvalsh(M)[0] - exact))
+    assert 2.8 < np.polyfit(np.log(lams), np.log(errs[2]), 1)[0] < 3.2
+    assert 3.7 < np.polyfit(np.log(lams), np.log(errs[3]), 1)[0] < 4.3
+    assert abs(errs["x"][0] / errs[2][0] - 0.5) < 0.05
+
+
+@pytest.mark.parametrize("order,x,dd", [(3, 1.0, 1), (3, 0.4, 1), (3, 1.0, 0), (2, 0.0, 1)])
+def test_p6_ee_sigma_diagonal_hermitian(order, x, dd):
+    o, v = 4, 6
+    p = make_problem(o, v, 10, seed=13, sigma=0.2)
+    M = adc_ee.explicit_matrix(order, x, p.B, p.eps_occ, p.eps_vir, dd_order=dd)
+    assert np.abs(M - M.conj().T).max() < 1e-13 * np.abs(M).max()
+    N = M.shape[0]
+    S = adc_ee.sigma_ref(order, x, p.B, p.eps_occ, p.eps_vir, np.eye(N, dtype=np.complex128), dd_order=dd)
+    assert np.abs(S.T - M).max() < 1e-13 * np.abs(M).max()
+    d = adc_ee.diagonal_ref(order, x, p.B, p.eps_occ, p.eps_vir, dd_order=dd)
+    assert np.abs(d - np.diag(M).real).max() < 1e-13 * np.abs(M).max()
+    if order == 3 and dd == 1 and x == 0.4:
+        M0 = adc_ee.explicit_matrix(3, 0.0, p.B, p.eps_occ, p.eps_vir)
+        M1 = adc_ee.explicit_matrix(3, 1.0, p.B, p.eps_occ, p.eps_vir)
+        assert np.abs(M - (0.6 * M0 + 0.4 * M1)).max() < 1e-14 * np.abs(M).max()
+
+
+def test_p6a_ee_unitary_invariance_within_degenerate_groups():
+    o, v, Q = 4, 6, 9
+    rng = np.random.default_rng(5)
+    p = make_problem(o, v, Q, seed=17, sigma=0.2)
+    eo = np.repeat(np.sort(rng.uniform(-2, -0.5, o // 2)), 2)
+    ev = np.repeat(np.sort(rng.uniform(0.2, 3.0, v // 2)), 2)
+    nmo = o + v
+    W = np.zeros((nmo, nmo), dtype=np.complex128)
+    for g0 in range(0, nmo, 2):
+        q, _ = np.linalg.qr(rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2)))
+        W[g0:g0 + 2, g0:g0 + 2] = q
+    Br = np.einsum("pi,Qpq,qj->Qij", W.conj(), p.B, W)
+    w0 = np.linalg.eigvalsh(adc_ee.explicit_matrix(3, 0.5, p.B, eo, ev))
+    w1 = np.linalg.eigvalsh(adc_ee.explicit_matrix(3, 0.5, Br, eo, ev))
+    assert np.abs(w0 - w1).max() < 1e-12
