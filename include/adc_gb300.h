@@ -24,11 +24,14 @@
  * code; no call aborts, traps or exits the process. adc_strerror() names
  * the code and adc_last_error() gives the context's last message.
  *
- * Vector layout (dimension N = n1 + n2, basis-state phases of Eqs. 3-4):
+ * Vector layout (dimension N = n1 + n2, basis-state phases of Eqs. 2-4):
  *   IP: [ X_i (n1 = nocc) | X_(i<j),a (n2 = nocc(nocc-1)/2 * nvir) ]
  *       state a+_a a_i a_j |Psi0>, a fastest, pairs row-major over i<j.
  *   EA: [ X_a (n1 = nvir) | X_j,(a<b) (n2 = nocc * nvir(nvir-1)/2) ]
  *       state a+_a a+_b a_j |Psi0>, pair fastest, pairs row-major over a<b.
+ *   EE: [ X_(i,a) (n1 = nocc*nvir) | X_(i<j),(a<b) (n2 = npairs_o * npairs_v) ]
+ *       states a+_a a_i |Psi0> and a+_a a_i a+_b a_j |Psi0>, a and the virtual
+ *       pair fastest.
  * Blocks of k vectors are row-major [k][N].
  */
 #ifndef ADC_GB300_H
@@ -76,6 +79,9 @@ typedef struct {
   double herm_tol;      /* relative tolerance of the Hermiticity check of B */
   int64_t mem_limit;    /* bytes the context may allocate, 0 = no limit */
   int verbose;          /* 1 = per-iteration lines on stderr */
+  int dd_order;         /* EE only: order of the doubles-doubles block at third
+                           order, 1 (full ADC(3), default) or 0 (kept at the
+                           ADC(2) level, zeroth order) */
 } adc_opts;
 
 typedef struct {
@@ -101,7 +107,8 @@ int adc_opts_default(adc_opts *opts);
  *            checked to opts->herm_tol * max|B|, else ADC_ERR_ARG.
  *   eps_occ  [nocc], eps_vir [nvir]: orbital energies (Hartree); every
  *            eps_occ must lie below every eps_vir, else ADC_ERR_ARG.
- *   kind     ADC_IP or ADC_EA (ADC_EE gives ADC_ERR_UNSUPPORTED).
+ *   kind     ADC_IP, ADC_EA or ADC_EE (EE: FP64 sigma products only; the
+ *            tensor-core precision gives ADC_ERR_UNSUPPORTED).
  *   order    2 (ADC(2)) or 3 (ADC(2)+x(3); x = 1 is ADC(3), x = 0 is ADC(2)).
  *   x        scale of every term ADC(3) adds to ADC(2) (used when order == 3).
  *   opts     NULL for the defaults.

@@ -37,7 +37,7 @@ class AdcError(RuntimeError):
 class adc_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("block", ctypes.c_int),
                 ("max_subspace", ctypes.c_int), ("herm_tol", ctypes.c_double),
-                ("mem_limit", ctypes.c_int64), ("verbose", ctypes.c_int)]
+                ("mem_limit", ctypes.c_int64), ("verbose", ctypes.c_int), ("dd_order", ctypes.c_int)]
 
 
 class adc_stats(ctypes.Structure):
@@ -137,7 +137,7 @@ class Context:
     """One ADC problem on the GPU (``adc_init``)."""
 
     def __init__(self, B, eps_occ, eps_vir, kind="IP", order=3, x=1.0, precision="fp64", stream=None,
-                 block=0, max_subspace=0, herm_tol=1e-12, mem_limit=0, verbose=False):
+                 block=0, max_subspace=0, herm_tol=1e-12, mem_limit=0, verbose=False, dd_order=1):
         o = adc_opts()
         lib.adc_opts_default(ctypes.byref(o))
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -151,6 +151,7 @@ class Context:
         o.herm_tol = herm_tol
         o.mem_limit = mem_limit
         o.verbose = 1 if verbose else 0
+        o.dd_order = int(dd_order)
         naux, nmo, nmo2 = B.shape
         nocc, nvir = eps_occ.shape[0], eps_vir.shape[0]
         if nmo != nmo2 or nmo != nocc + nvir:

@@ -6,6 +6,7 @@
 
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
+#include "ee.cuh"
 
 namespace adc {
 int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision, const cplx *guess,
@@ -102,6 +103,7 @@ int fail(adc_ctx *c, const std::exception &e, int code) {
 
 adc_ctx::~adc_ctx() {
   release_tc(this);
+  ee.reset();
   scratch.reset();
   t1.reset(); W.reset(); Glad.reset(); diag.reset(); d2.reset(); Cpl.reset(); M11.reset();
   B.reset(); eo.reset(); ev.reset();
@@ -116,6 +118,7 @@ int adc_opts_default(adc_opts *o) {
   std::memset(o, 0, sizeof(*o));
   o->precision = ADC_PREC_FP64;
   o->herm_tol = 1e-12;
+  o->dd_order = 1;
   return ADC_OK;
 }
 
@@ -126,8 +129,7 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
   *out = nullptr;
   adc_ctx *c = nullptr;
   try {
-    if (kind == ADC_EE) throw Error(ADC_ERR_UNSUPPORTED, "EE-ADC is not built");
-    if (kind != ADC_IP && kind != ADC_EA) throw Error(ADC_ERR_ARG, "kind must be ADC_IP or ADC_EA");
+    if (kind != ADC_IP && kind != ADC_EA && kind != ADC_EE) throw Error(ADC_ERR_ARG, "kind must be ADC_IP, ADC_EA or ADC_EE");
     if (order != 2 && order != 3) throw Error(ADC_ERR_ARG, "order must be 2 or 3");
     if (!B || !eps_occ || !eps_vir) throw Error(ADC_ERR_ARG, "NULL input");
     if (naux < 1 || nocc < 1 || nvir < 1) throw Error(ADC_ERR_ARG, "sizes must be positive");
@@ -143,7 +145,9 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
     c->x = (order == 3) ? x : 0.0;
     c->o = nocc; c->v = nvir; c->Q = naux; c->nmo = nocc + nvir;
     if (kind == ADC_IP) { c->n1 = nocc; c->n2 = npairs(nocc) * nvir; }
-    else { c->n1 = nvir; c->n2 = nocc * npairs(nvir); }
+    else if (kind == ADC_EA) { c->n1 = nvir; c->n2 = nocc * npairs(nvir); }
+    else { c->n1 = nocc * nvir; c->n2 = npairs(nocc) * npairs(nvir); }
+    c->dd_order = (c->opts.dd_order == 0) ? 0 : 1;
     c->N = c->n1 + c->n2;
     c->ex.mem_limit = c->opts.mem_limit;
     if (c->opts.stream) {
@@ -185,7 +189,8 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
         throw Error(ADC_ERR_ARG, "B is not Hermitian in (p,q) (max deviation " + std::to_string(h[0]) +
                                      ", max |B| " + std::to_string(h[1]) + ")");
     }
-    setup_operators(c);
+    if (kind == ADC_EE) setup_ee(c);
+    else setup_operators(c);
     *out = c;
     return ADC_OK;
   } catch (const adc::Error &e) {
@@ -214,6 +219,10 @@ int adc_sigma(adc_ctx *c, const adc_c128 *X, adc_c128 *S, int64_t k, int precisi
   if (!c) return ADC_ERR_STATE;
   if (k < 0 || (k > 0 && (!X || !S))) return ADC_ERR_ARG;
   if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3) return ADC_ERR_ARG;
+  if (c->kind == ADC_EE && precision != ADC_PREC_FP64) {
+    c->err = "EE-ADC runs FP64 sigma products only";
+    return ADC_ERR_UNSUPPORTED;
+  }
   if (k == 0) return ADC_OK;
   ADC_API_TRY
   const size_t bytes = (size_t)k * c->N * sizeof(cplx);
@@ -250,6 +259,10 @@ int adc_davidson(adc_ctx *c, int nroots, double tol, int max_iter, int precision
                  int64_t nguess, double *omega, adc_c128 *Y, double *err64, adc_stats *st) {
   if (!c) return ADC_ERR_STATE;
   if (!omega || nroots < 1 || max_iter < 1) return ADC_ERR_ARG;
+  if (c->kind == ADC_EE && precision != ADC_PREC_FP64) {
+    c->err = "EE-ADC runs FP64 sigma products only";
+    return ADC_ERR_UNSUPPORTED;
+  }
   ADC_API_TRY
   const size_t vb = (size_t)nroots * c->N * sizeof(cplx);
   DevIn gin(c->ex, guess, guess ? (size_t)nguess * c->N * sizeof(cplx) : 0);

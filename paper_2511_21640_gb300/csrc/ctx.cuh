@@ -7,6 +7,7 @@
 
 namespace adc {
 struct TcCache;  // split-precision operator copies (tc_gemm.cu)
+struct EEOps;    // EE-ADC operators (ee.cu)
 }
 
 struct adc_ctx {
@@ -34,6 +35,10 @@ struct adc_ctx {
   // split-precision copies for the tensor-core sigma
   std::unique_ptr<adc::TcCache> tc;
 
+  // EE-ADC operators (kind == ADC_EE)
+  std::unique_ptr<adc::EEOps> ee;
+  int dd_order = 1;
+
   // per-call scratch, grown on demand
   adc::DBuf scratch;
 
@@ -41,7 +46,16 @@ struct adc_ctx {
 };
 
 namespace adc {
+TV Bview(adc_ctx *c, char p, char q);               // B^Q block view [Q][p][q]
+DBuf eri_block(adc_ctx *c, const char *spec);       // dense <pq||rs> of a 4-letter o/v spec
 void setup_operators(adc_ctx *c);
+// t1 (c->t1) and ring integrals (c->W) from B
+void first_order_amplitudes(adc_ctx *c);
+// second-order doubles and singles, packed <ab||cd> and the ladder intermediate
+// Lad_ij^ab = 1/2 sum_cd <ab||cd> t_ij^cd (needs c->t1 and c->W)
+void second_order_amplitudes(adc_ctx *c, DBuf &G_vv, DBuf &Lad, DBuf &t2d, DBuf &t2s);
+void setup_ee(adc_ctx *c);
+void sigma_ee_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision);

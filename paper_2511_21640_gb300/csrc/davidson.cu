@@ -21,6 +21,7 @@
 #include <numeric>
 
 #include "ctx.cuh"
+#include "blockops.cuh"
 #include "eig.cuh"
 
 namespace adc {
@@ -102,6 +103,17 @@ __global__ void k_unit_vectors(cplx *V, int64_t n, const int64_t *idx, int k) {
   if (threadIdx.x == 0) V[(int64_t)r * n + idx[r]] = cmake(1.0, 0.0);
 }
 
+// W[:, c] = Z[:, keep[c]] / sqrt(lam[keep[c]])  (nt x nk, row-major, ld nk)
+__global__ void k_lowdin(const cplx *Z, int nt, const double *lam, const int *keep, int nk, cplx *W) {
+  for (int idx = threadIdx.x; idx < nt * nk; idx += blockDim.x) {
+    int i = idx / nk, cI = idx % nk;
+    int j = keep[cI];
+    double s = 1.0 / sqrt(lam[j]);
+    cplx z = Z[(int64_t)i * nt + j];
+    W[(int64_t)i * nk + cI] = cmake(z.x * s, z.y * s);
+  }
+}
+
 struct Timer {
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
   double s() const {
@@ -116,7 +128,7 @@ struct Davidson {
   Exec &ex;
   int64_t N;
   int nroots, mmax, krmax;
-  DBuf V, AV, G, H, Cv, w, T, Y, SY, R, nrm, rowsb, info, tmp;
+  DBuf V, AV, G, H, Cv, w, T, Tn, Y, SY, R, nrm, rowsb, info, tmp, Gs, Zs, Ws, w2;
   adc_stats st{};
   double tsig = 0.0;
   int m = 0;
@@ -131,13 +143,18 @@ struct Davidson {
     Cv = cbuf(ex, (int64_t)mmax * mmax);
     w = DBuf(ex, mmax * sizeof(double));
     T = cbuf(ex, (int64_t)nr * N);
+    Tn = cbuf(ex, (int64_t)nr * N);
+    Gs = cbuf(ex, (int64_t)nr * nr);
+    Zs = cbuf(ex, (int64_t)nr * nr);
+    Ws = cbuf(ex, (int64_t)nr * nr);
+    w2 = DBuf(ex, nr * sizeof(double));
     Y = cbuf(ex, (int64_t)krmax * N);
     SY = cbuf(ex, (int64_t)krmax * N);
     R = cbuf(ex, (int64_t)nr * N);
     nrm = DBuf(ex, mmax * sizeof(double));
     rowsb = DBuf(ex, mmax * sizeof(int));
     info = DBuf(ex, 16);
-    tmp = cbuf(ex, (int64_t)mmax * mmax);
+    tmp = cbuf(ex, (int64_t)mmax * std::max(mmax, nr));
   }
 
   void apply_sigma(const cplx *X, cplx *S, int64_t k, int prec) {
@@ -152,12 +169,10 @@ struct Davidson {
   // G[0:m+na][m:m+na] = V^H AV[m:m+na], lower part by Hermiticity
   void extend_projection(int m0, int na) {
     int mt = m0 + na;
-    zgemm(ex, mt, na, N, 1, C1(), V.c(), 0, N, 1, true, AV.c() + (int64_t)m0 * N, 0, 1, N, false,
-          C0(), G.c() + m0, 0, mmax, 1);
+    gram(ex, V.c(), N, mt, AV.c() + (int64_t)m0 * N, N, na, N, C1(), G.c() + m0, mmax);
     if (nb > 0 && m0 >= nb) {
       // rows of the FP64 base: <b|M|t> = <sigma64(b)|t>
-      zgemm(ex, nb, na, N, 1, C1(), AV.c(), 0, N, 1, true, V.c() + (int64_t)m0 * N, 0, 1, N, false, C0(),
-            G.c() + m0, 0, mmax, 1);
+      gram(ex, AV.c(), N, nb, V.c() + (int64_t)m0 * N, N, na, N, C1(), G.c() + m0, mmax);
     }
     if (m0 > 0) {
       k_fill_lower<<<(na * m0 + 255) / 256, 256, 0, ex.stream>>>(G.c(), mmax, m0, na);
@@ -175,39 +190,37 @@ struct Davidson {
     return h;
   }
 
-  // project out span(V[0:m]) from T[0:nt] twice, then MGS within T; returns the
-  // number of accepted (orthonormal) vectors, compacted to the front of T
+  // project out span(V[0:m]) from T[0:nt] twice (block classical Gram-Schmidt),
+  // then orthonormalise the block symmetrically (Loewdin, as in Eq. 6): with
+  // <t_a|t_b> = Z diag(l) Z^H, the kept directions are T' = (Z l^-1/2)^T T for
+  // eigenvalues l above the rank threshold. Returns the number of vectors kept,
+  // stored at the front of T.
   int orthonormalise(int nt) {
+    if (nt <= 0) return 0;
     std::vector<double> n0 = row_norms(T.c(), nt);
+    double nmax = *std::max_element(n0.begin(), n0.end());
+    if (!(nmax > 1e-300) || !std::isfinite(nmax)) return 0;
     for (int pass = 0; pass < 2 && m > 0; ++pass) {
-      // P = T V^H (nt x m), T -= P V
-      zgemm(ex, nt, m, N, 1, C1(), T.c(), 0, N, 1, false, V.c(), 0, 1, N, true, C0(), tmp.c(), 0, m, 1);
-      zgemm(ex, nt, N, m, 1, CR(-1.0), tmp.c(), 0, m, 1, false, V.c(), 0, N, 1, false, C1(), T.c(), 0, N, 1);
+      gram(ex, V.c(), N, m, T.c(), N, nt, N, C1(), tmp.c(), nt);
+      combine(ex, tmp.c(), nt, m, nt, V.c(), N, N, CR(-1.0), C1(), T.c(), N);
     }
-    int acc = 0;
-    for (int i = 0; i < nt; ++i) {
-      cplx *ti = T.c() + (int64_t)i * N;
-      for (int pass = 0; pass < 2; ++pass) {
-        if (acc > 0) {  // against the accepted new vectors
-          zgemm(ex, 1, acc, N, 1, C1(), ti, 0, N, 1, false, T.c(), 0, 1, N, true, C0(), tmp.c(), 0, acc, 1);
-          zgemm(ex, 1, N, acc, 1, CR(-1.0), tmp.c(), 0, acc, 1, false, T.c(), 0, N, 1, false, C1(), ti, 0, N, 1);
-        }
-        if (m > 0 && pass == 1) {
-          zgemm(ex, 1, m, N, 1, C1(), ti, 0, N, 1, false, V.c(), 0, 1, N, true, C0(), tmp.c(), 0, m, 1);
-          zgemm(ex, 1, N, m, 1, CR(-1.0), tmp.c(), 0, m, 1, false, V.c(), 0, N, 1, false, C1(), ti, 0, N, 1);
-        }
-      }
-      std::vector<double> ni = row_norms(ti, 1);
-      if (!(ni[0] > 1e-8 * std::max(n0[i], 1e-300)) || !(ni[0] > 1e-14) || !std::isfinite(ni[0]))
-        continue;
-      k_scale_row<<<grid1d(N, 256), 256, 0, ex.stream>>>(ti, N, nrm.d());
-      ADC_CHECK_LAUNCH();
-      if (acc != i)
-        ADC_CUDA(cudaMemcpyAsync(T.c() + (int64_t)acc * N, ti, N * sizeof(cplx), cudaMemcpyDeviceToDevice,
-                                 ex.stream));
-      ++acc;
-    }
-    return acc;
+    gram(ex, T.c(), N, nt, T.c(), N, nt, N, C1(), Gs.c(), nt);
+    jacobi_eigh(ex, Gs.c(), nt, nt, w2.d(), Zs.c(), nt, (int *)info.p);
+    std::vector<double> lam(nt);
+    ADC_CUDA(cudaMemcpyAsync(lam.data(), w2.d(), nt * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
+    ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    const double thr = std::max(1e-28, (1e-8 * nmax) * (1e-8 * nmax));
+    std::vector<int> keep;
+    for (int j = nt - 1; j >= 0; --j)
+      if (lam[j] > thr && std::isfinite(lam[j])) keep.push_back(j);
+    const int nk = (int)keep.size();
+    if (nk == 0) return 0;
+    ADC_CUDA(cudaMemcpyAsync(rowsb.p, keep.data(), nk * sizeof(int), cudaMemcpyHostToDevice, ex.stream));
+    k_lowdin<<<1, 256, 0, ex.stream>>>(Zs.c(), nt, w2.d(), (const int *)rowsb.p, nk, Ws.c());
+    ADC_CHECK_LAUNCH();
+    combine(ex, Ws.c(), nk, nt, nk, T.c(), N, N, C1(), C0(), Tn.c(), N);
+    ADC_CUDA(cudaMemcpyAsync(T.c(), Tn.c(), (int64_t)nk * N * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
+    return nk;
   }
 
   // Rayleigh-Ritz on V[0:m]: w (host copy), Y, SY for the lowest kr, R for nroots
@@ -216,9 +229,9 @@ struct Davidson {
     k_hermitize<<<(m * m + 255) / 256, 256, 0, ex.stream>>>(G.c(), mmax, m, H.c(), mmax);
     ADC_CHECK_LAUNCH();
     jacobi_eigh(ex, H.c(), m, mmax, w.d(), Cv.c(), mmax, (int *)info.p);
-    // Y[r][n] = sum_i Cv[i][r] V[i][n]
-    zgemm(ex, nr, N, m, 1, C1(), Cv.c(), 0, 1, mmax, false, V.c(), 0, N, 1, false, C0(), Y.c(), 0, N, 1);
-    zgemm(ex, nr, N, m, 1, C1(), Cv.c(), 0, 1, mmax, false, AV.c(), 0, N, 1, false, C0(), SY.c(), 0, N, 1);
+    // Y[r][n] = sum_i Cv[i][r] V[i][n], SY likewise from AV
+    combine(ex, Cv.c(), mmax, m, nr, V.c(), N, N, C1(), C0(), Y.c(), N);
+    combine(ex, Cv.c(), mmax, m, nr, AV.c(), N, N, C1(), C0(), SY.c(), N);
     k_residual<<<grid1d((int64_t)nroots * N, 256), 256, 0, ex.stream>>>(SY.c(), Y.c(), w.d(), nroots, N, R.c());
     ADC_CHECK_LAUNCH();
     std::vector<double> wh(m);

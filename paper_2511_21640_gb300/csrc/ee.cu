@@ -1,0 +1,348 @@
+// EE-ADC(2), ADC(2)+x(3) and ADC(3): operators and FP64 sigma product.
+//
+// Manifold (Sec. 2.1, Eq. 2): singles a+_a a_i |Psi0>, doubles
+// a+_a a_i a+_b a_j |Psi0> (i<j, a<b); vector layout [X_(i,a) | X_(i<j),(a<b)],
+// the virtual pair fastest. The singles are orthogonalised against Psi0
+// (Eq. 5), so M_SS = S^-1/2 K S^-1/2 with S_ia,jb = <E_ai^+ E_bj> - <E_ai^+><E_bj>
+// and K_ia,jb = <E_ai^+ [H, E_bj]> (Eqs. 6-7). With W_ia,jb =
+// ((eps_b - eps_j) - (eps_a - eps_i))/2 and the connected parts of the
+// expectation values (Wick's theorem on the MP ground state):
+//
+//   M_SS = diag(eps_a - eps_i) + K1 + W o S2 + Y2
+//          + x [ W o S3 + Y3 - 1/2 (S2 K1 + K1 S2) ]
+//   M_SD = M1_SD + x [ (Delta_K - Delta_S) O2 + Z1 ]
+//   M_DD = diag(eps_a + eps_b - eps_i - eps_j) + x dd M1_DD
+//
+// The tables below list every connected term (disconnected pieces cancel
+// against the normalisation of Psi0). The static singles block is assembled
+// once; the coupling and the doubles block are applied matrix-free.
+#include "ctx.cuh"
+#include "ee.cuh"
+
+namespace adc {
+
+namespace {
+
+using Rows = std::vector<std::pair<const char *, const char *>>;
+
+// singles-singles, first order: K1_ia,jb = -<aj||bi>
+const Rows kK1 = {{"-1", "v(aj,bi)"}};
+// connected second-order overlap <E_ai^+ E_bj>
+const Rows kS2 = {{"1", "t1(aA,iM) t1c(bA,jM)"},
+                  {"-1/2", "t1(aA,MN) t1c(bA,MN) d(ij)"},
+                  {"-1/2", "t1(AB,iM) t1c(AB,jM) d(ab)"}};
+// first-order expectation of E_ai^+ [V_N, E_bj]
+const Rows kY2 = {{"1", "t1(aA,iM) v(jM,bA)"},
+                  {"-1/2", "t1(aA,MN) v(MN,bA) d(ij)"},
+                  {"-1/2", "t1(AB,iM) v(jM,AB) d(ab)"}};
+// connected third-order overlap (t1 with the second-order doubles t2)
+const Rows kS3 = {{"1", "t1(aA,iM) t2c(bA,jM)"},
+                  {"1", "t1c(bA,jM) t2(aA,iM)"},
+                  {"-1/2", "t1(aA,MN) t2c(bA,MN) d(ij)"},
+                  {"-1/2", "t1(AB,iM) t2c(AB,jM) d(ab)"},
+                  {"-1/2", "t1c(bA,MN) t2(aA,MN) d(ij)"},
+                  {"-1/2", "t1c(AB,jM) t2(AB,iM) d(ab)"}};
+// connected second-order expectation of E_ai^+ [V_N, E_bj]: Psi1 x Psi1 ...
+const Rows kY3 = {{"1", "t1(aA,iM) t1c(AB,jN) v(BM,bN)"},
+                  {"1", "t1(aA,iM) t1c(AB,MN) v(jB,bN)"},
+                  {"1/2", "t1(aA,iM) t1c(bA,NO) v(jM,NO)"},
+                  {"1/2", "t1(aA,iM) t1c(BC,jM) v(BC,bA)"},
+                  {"1/2", "t1(aA,MN) t1c(bB,MN) v(jB,iA)"},
+                  {"1/2", "t1(aA,MN) t1c(AB,MN) v(jB,bi)"},
+                  {"1/2", "t1(AB,iM) t1c(AB,jN) v(aM,bN)"},
+                  {"1/2", "t1(AB,MN) t1c(bA,MN) v(aj,iB)"},
+                  {"-1", "t1(aA,iM) t1c(bB,MN) v(jB,AN)"},
+                  {"-1", "t1(aA,MN) t1c(bA,MO) v(jN,iO)"},
+                  {"-1", "t1(aA,MN) t1c(AB,jM) v(BN,bi)"},
+                  {"-1", "t1(AB,iM) t1c(bA,MN) v(aj,BN)"},
+                  {"-1", "t1(AB,iM) t1c(AC,jM) v(aC,bB)"},
+                  {"-1/2", "t1(AB,iM) t1c(AB,MN) v(aj,bN)"},
+                  {"-1/2", "t1(AB,MN) t1c(AB,jM) v(aN,bi)"},
+                  {"1", "t1(AB,iM) t1c(AC,MN) v(jC,BN) d(ab)"},
+                  {"1/2", "t1(AB,MN) t1c(AB,MO) v(jN,iO) d(ab)"},
+                  {"1/2", "t1(AB,MN) t1c(AC,MN) v(aC,bB) d(ij)"},
+                  {"-1", "t1(aA,MN) t1c(AB,MO) v(BN,bO) d(ij)"},
+                  {"-1/2", "t1(AB,MN) t1c(AB,MO) v(aN,bO) d(ij)"},
+                  {"-1/2", "t1(AB,MN) t1c(AC,MN) v(jC,iB) d(ab)"},
+                  {"-1/4", "t1(aA,MN) t1c(BC,MN) v(BC,bA) d(ij)"},
+                  {"-1/4", "t1(AB,iM) t1c(AB,NO) v(jM,NO) d(ab)"},
+                  // ... and Psi2 (doubles t2, singles s2) with Phi
+                  {"1", "t2(aA,iM) v(jM,bA)"},
+                  {"-1", "s2(a,M) v(jM,bi)"},
+                  {"-1", "s2(A,i) v(aj,bA)"},
+                  {"-1", "s2c(b,M) v(aj,iM)"},
+                  {"-1", "s2c(A,j) v(aA,bi)"},
+                  {"1", "s2(A,M) v(aM,bA) d(ij)"},
+                  {"1", "s2c(A,M) v(aA,bM) d(ij)"},
+                  {"-1", "s2(A,M) v(jM,iA) d(ab)"},
+                  {"-1", "s2c(A,M) v(jA,iM) d(ab)"},
+                  {"-1/2", "t2(aA,MN) v(MN,bA) d(ij)"},
+                  {"-1/2", "t2(AB,iM) v(jM,AB) d(ab)"}};
+// singles-doubles, first order <Phi| E_ia^+ [V_N, C_klcd] |Phi>
+const Rows kSD1 = {{"1", "v(al,cd) d(ik)"}, {"1", "v(kl,di) d(ac)"},
+                   {"-1", "v(ak,cd) d(il)"}, {"-1", "v(kl,ci) d(ad)"}};
+// second-order overlap <E_ia^+ C_klcd> (second-order singles)
+const Rows kO2 = {{"1", "s2c(c,k) d(ad) d(il)"}, {"1", "s2c(d,l) d(ac) d(ik)"},
+                  {"-1", "s2c(c,l) d(ad) d(ik)"}, {"-1", "s2c(d,k) d(ac) d(il)"}};
+// first-order expectation of E_ia^+ [V_N, C_klcd]
+const Rows kZ1 = {{"1", "t1c(cd,lM) v(ak,iM)"},
+                  {"1", "t1c(dA,kl) v(aA,ci)"},
+                  {"-1", "t1c(cd,kM) v(al,iM)"},
+                  {"-1", "t1c(cA,kl) v(aA,di)"},
+                  {"1", "t1c(cA,kM) v(aA,dM) d(il)"},
+                  {"1", "t1c(cA,lM) v(kA,iM) d(ad)"},
+                  {"1", "t1c(dA,kM) v(lA,iM) d(ac)"},
+                  {"1", "t1c(dA,lM) v(aA,cM) d(ik)"},
+                  {"1/2", "t1c(cd,MN) v(al,MN) d(ik)"},
+                  {"1/2", "t1c(AB,kl) v(AB,di) d(ac)"},
+                  {"-1", "t1c(cA,kM) v(lA,iM) d(ad)"},
+                  {"-1", "t1c(cA,lM) v(aA,dM) d(ik)"},
+                  {"-1", "t1c(dA,kM) v(aA,cM) d(il)"},
+                  {"-1", "t1c(dA,lM) v(kA,iM) d(ac)"},
+                  {"-1/2", "t1c(cd,MN) v(ak,MN) d(il)"},
+                  {"-1/2", "t1c(AB,kl) v(AB,ci) d(ad)"},
+                  {"1/2", "t1c(cA,MN) v(lA,MN) d(ad) d(ik)"},
+                  {"1/2", "t1c(dA,MN) v(kA,MN) d(ac) d(il)"},
+                  {"1/2", "t1c(AB,kM) v(AB,cM) d(ad) d(il)"},
+                  {"1/2", "t1c(AB,lM) v(AB,dM) d(ac) d(ik)"},
+                  {"-1/2", "t1c(cA,MN) v(kA,MN) d(ad) d(il)"},
+                  {"-1/2", "t1c(dA,MN) v(lA,MN) d(ac) d(ik)"},
+                  {"-1/2", "t1c(AB,kM) v(AB,dM) d(ac) d(il)"},
+                  {"-1/2", "t1c(AB,lM) v(AB,cM) d(ad) d(ik)"}};
+// doubles-doubles, first order <Phi_ijab| V_N |Phi_klcd>
+const Rows kDD1 = {{"1", "v(ab,cd) d(ik) d(jl)"}, {"1", "v(kl,ij) d(ac) d(bd)"},
+                   {"-1", "v(ab,cd) d(il) d(jk)"}, {"-1", "v(kl,ij) d(ad) d(bc)"},
+                   {"1", "v(ak,cj) d(bd) d(il)"},  {"1", "v(ak,di) d(bc) d(jl)"},
+                   {"1", "v(al,ci) d(bd) d(jk)"},  {"1", "v(al,dj) d(bc) d(ik)"},
+                   {"1", "v(bk,ci) d(ad) d(jl)"},  {"1", "v(bk,dj) d(ac) d(il)"},
+                   {"1", "v(bl,cj) d(ad) d(ik)"},  {"1", "v(bl,di) d(ac) d(jk)"},
+                   {"-1", "v(ak,ci) d(bd) d(jl)"}, {"-1", "v(ak,dj) d(bc) d(il)"},
+                   {"-1", "v(al,cj) d(bd) d(ik)"}, {"-1", "v(al,di) d(bc) d(jk)"},
+                   {"-1", "v(bk,cj) d(ad) d(il)"}, {"-1", "v(bk,di) d(ac) d(jl)"},
+                   {"-1", "v(bl,ci) d(ad) d(jk)"}, {"-1", "v(bl,dj) d(ac) d(ik)"}};
+
+// M[ia][jb] += s ((eps_b - eps_j) - (eps_a - eps_i)) / 2 * S[ia][jb]
+__global__ void k_wmul_add(cplx *M, const cplx *S, const double *eo, const double *ev, int64_t o, int64_t v,
+                           double s) {
+  const int64_t n1 = o * v;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n1 * n1;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = idx % n1, row = idx / n1;
+    const int64_t i = row / v, a = row % v, j = col / v, b = col % v;
+    const double w = s * 0.5 * ((ev[b] - eo[j]) - (ev[a] - eo[i]));
+    M[idx].x += w * S[idx].x;
+    M[idx].y += w * S[idx].y;
+  }
+}
+
+// dst[z][k][l][c][d] = src[z][k][l][c][d] * (eps_c + eps_d - eps_k - eps_l)
+__global__ void k_dk_mul(const cplx *src, const double *eo, const double *ev, int64_t k, int64_t o, int64_t v,
+                         cplx *dst) {
+  const int64_t total = k * o * o * v * v;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t d = idx % v, r = idx / v;
+    int64_t c = r % v; r /= v;
+    int64_t l = r % o; r /= o;
+    int64_t kk = r % o;
+    const double f = ev[c] + ev[d] - eo[kk] - eo[l];
+    dst[idx] = cmake(src[idx].x * f, src[idx].y * f);
+  }
+}
+
+__global__ void k_ee_diag(const cplx *MSS, const double *g, const double *eo, const double *ev, int64_t o,
+                          int64_t v, double xd, double *diag, double *d2) {
+  const int64_t nmo = o + v, n1 = o * v, po = o * (o - 1) / 2, pv = v * (v - 1) / 2;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n1 + po * pv;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    if (idx < n1) { diag[idx] = MSS[idx * n1 + idx].x; continue; }
+    const int64_t r = idx - n1;
+    const int64_t pij = r / pv, pab = r % pv;
+    int64_t i = 0;
+    while ((i + 1) * o - (i + 1) * (i + 2) / 2 <= pij) ++i;
+    const int64_t j = pij - (i * o - i * (i + 1) / 2) + i + 1;
+    int64_t a = 0;
+    while ((a + 1) * v - (a + 1) * (a + 2) / 2 <= pab) ++a;
+    const int64_t b = pab - (a * v - a * (a + 1) / 2) + a + 1;
+    const double z = ev[a] + ev[b] - eo[i] - eo[j];
+    const int64_t A = o + a, Bv = o + b;
+    const double f = g[A * nmo + Bv] + g[i * nmo + j] - g[A * nmo + i] - g[A * nmo + j] - g[Bv * nmo + i] -
+                     g[Bv * nmo + j];
+    d2[r] = z;
+    diag[idx] = z + xd * f;
+  }
+}
+
+}  // namespace
+
+
+static TermSource make_source(adc_ctx *c) {
+  TermSource s;
+  s.o = c->o;
+  s.v = c->v;
+  s.get = [c](const std::string &name, const std::string &lab) -> TV {
+    const int64_t o = c->o, v = c->v;
+    auto type = [](char ch) { return std::string("ijklMNOPRSTW").find(ch) != std::string::npos ? 'o' : 'v'; };
+    if (name == "v") {
+      std::string spec;
+      for (char ch : lab) spec.push_back(type(ch));
+      auto &m = c->ee->eri;
+      if (!m.count(spec)) m[spec] = eri_block(c, spec.c_str());
+      std::vector<int64_t> e;
+      for (char ch : spec) e.push_back(ch == 'o' ? o : v);
+      return TV::dense(m[spec].c(), e);
+    }
+    if (name == "t1" || name == "t1c" || name == "t2" || name == "t2c") {
+      cplx *p = (name[1] == '1') ? c->t1.c() : c->ee->t2d.c();
+      // stored [i][j][a][b]; labels are (a, b, i, j)
+      TV t(p, {v, v, o, o}, {v, 1, o * v * v, v * v});
+      t.conj = (name.back() == 'c');
+      return t;
+    }
+    if (name == "s2" || name == "s2c") {
+      TV t(c->ee->t2s.c(), {v, o}, {1, v});
+      t.conj = (name == "s2c");
+      return t;
+    }
+    throw Error(ADC_ERR_ARG, "EE terms: unknown tensor " + name);
+  };
+  return s;
+}
+
+void setup_ee(adc_ctx *c) {
+  Exec &ex = c->ex;
+  const int64_t o = c->o, v = c->v, n1 = c->n1;
+  const bool third = (c->order == 3) && (c->x != 0.0);
+  const double x = c->x;
+  c->ee.reset(new EEOps());
+  EEOps &E = *c->ee;
+  E.K1 = parse_terms(kK1); E.S2 = parse_terms(kS2); E.Y2 = parse_terms(kY2);
+  E.S3 = parse_terms(kS3); E.Y3 = parse_terms(kY3);
+  E.SD1 = parse_terms(kSD1); E.O2 = parse_terms(kO2); E.Z1 = parse_terms(kZ1); E.DD1 = parse_terms(kDD1);
+  first_order_amplitudes(c);
+  if (third) {
+    DBuf G_vv, Lad;
+    second_order_amplitudes(c, G_vv, Lad, E.t2d, E.t2s);
+  }
+  TermSource src = make_source(c);
+  const std::string L = "iajb";
+  std::vector<int64_t> e4 = {o, v, o, v};
+  E.MSS = cbuf(ex, n1 * n1);
+  TV M = TV::dense(E.MSS.c(), e4);
+  fill_zero(ex, E.MSS.p, E.MSS.bytes);
+  DBuf K1 = cbuf(ex, n1 * n1), S2 = cbuf(ex, n1 * n1);
+  fill_zero(ex, K1.p, K1.bytes);
+  fill_zero(ex, S2.p, S2.bytes);
+  eval_terms(ex, E.K1, src, {}, false, C1(), TV::dense(K1.c(), e4), L);
+  eval_terms(ex, E.S2, src, {}, false, C1(), TV::dense(S2.c(), e4), L);
+  // zeroth order on the diagonal
+  E.dS = DBuf(ex, n1 * sizeof(double));
+  {
+    std::vector<double> eo(o), ev(v), d(n1);
+    ADC_CUDA(cudaMemcpyAsync(eo.data(), c->eo.p, o * 8, cudaMemcpyDeviceToHost, ex.stream));
+    ADC_CUDA(cudaMemcpyAsync(ev.data(), c->ev.p, v * 8, cudaMemcpyDeviceToHost, ex.stream));
+    ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    for (int64_t i = 0; i < o; ++i)
+      for (int64_t a = 0; a < v; ++a) d[i * v + a] = ev[a] - eo[i];
+    ADC_CUDA(cudaMemcpyAsync(E.dS.p, d.data(), n1 * 8, cudaMemcpyHostToDevice, ex.stream));
+    ADC_CUDA(cudaStreamSynchronize(ex.stream));
+  }
+  add_diag(ex, E.MSS.c(), E.dS.d(), n1, 1.0);
+  zaxpby(ex, n1 * n1, C1(), K1.c(), C1(), E.MSS.c());
+  k_wmul_add<<<grid1d(n1 * n1, 256), 256, 0, ex.stream>>>(E.MSS.c(), S2.c(), c->eo.d(), c->ev.d(), o, v, 1.0);
+  ADC_CHECK_LAUNCH();
+  eval_terms(ex, E.Y2, src, {}, false, C1(), M, L);
+  if (third) {
+    DBuf S3 = cbuf(ex, n1 * n1);
+    fill_zero(ex, S3.p, S3.bytes);
+    eval_terms(ex, E.S3, src, {}, false, C1(), TV::dense(S3.c(), e4), L);
+    k_wmul_add<<<grid1d(n1 * n1, 256), 256, 0, ex.stream>>>(E.MSS.c(), S3.c(), c->eo.d(), c->ev.d(), o, v, x);
+    ADC_CHECK_LAUNCH();
+    eval_terms(ex, E.Y3, src, {}, false, CR(x), M, L);
+    // - x/2 (S2 K1 + K1 S2)
+    zgemm(ex, n1, n1, n1, 1, CR(-0.5 * x), S2.c(), 0, n1, 1, false, K1.c(), 0, n1, 1, false, C1(), E.MSS.c(), 0,
+          n1, 1);
+    zgemm(ex, n1, n1, n1, 1, CR(-0.5 * x), K1.c(), 0, n1, 1, false, S2.c(), 0, n1, 1, false, C1(), E.MSS.c(), 0,
+          n1, 1);
+  }
+  // a copy as the generic main block
+  c->M11 = cbuf(ex, n1 * n1);
+  ADC_CUDA(cudaMemcpyAsync(c->M11.p, E.MSS.p, n1 * n1 * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
+  // diagonal
+  c->diag = DBuf(ex, c->N * sizeof(double));
+  c->d2 = DBuf(ex, c->n2 * sizeof(double));
+  {
+    DBuf g(ex, c->nmo * c->nmo * sizeof(double));
+    antisym_diag(ex, c->B.c(), c->Q, c->nmo, g.d());
+    const double xd = (third && c->dd_order == 1) ? x : 0.0;
+    k_ee_diag<<<grid1d(c->N, 256), 256, 0, ex.stream>>>(E.MSS.c(), g.d(), c->eo.d(), c->ev.d(), o, v, xd,
+                                                        c->diag.d(), c->d2.d());
+    ADC_CHECK_LAUNCH();
+  }
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+}
+
+void sigma_ee_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
+  Exec &ex = c->ex;
+  EEOps &E = *c->ee;
+  const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N;
+  const int64_t po = npairs(o), pv = npairs(v);
+  const bool third = (c->order == 3) && (c->x != 0.0);
+  const double x = third ? c->x : 0.0;
+  TermSource src = make_source(c);
+  TagScope tg(ex, "ee");
+  // singles <- singles: static block
+  zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, E.MSS.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
+  // full antisymmetric doubles X2f[z][k][l][c][d]
+  const int64_t nf = k * o * o * v * v;
+  DBuf half = cbuf(ex, k * po * v * v), X2f = cbuf(ex, nf), S2f = cbuf(ex, nf);
+  pair_unpack(ex, X + n1, k, po, N, pv, v, 1, half.c());
+  pair_unpack(ex, half.c(), k, 1, po * v * v, 0, o, v * v, X2f.c());
+  half.reset();
+  TV Xd = TV::dense(X2f.c(), {k, o, o, v, v});
+  TV X1(const_cast<cplx *>(X), {k, o, v}, {N, v, 1});
+  TV S1(S, {k, o, v}, {N, v, 1});
+  // singles <- doubles: 1/4 sum_klcd M_SD(ia;klcd) X_klcd
+  eval_terms(ex, E.SD1, src, {{"zklcd", Xd}}, false, CR(0.25), S1, "zia");
+  // doubles <- singles and the doubles block
+  fill_zero(ex, S2f.p, S2f.bytes);
+  TV Sd = TV::dense(S2f.c(), {k, o, o, v, v});
+  eval_terms(ex, E.SD1, src, {{"zia", X1}}, true, C1(), Sd, "zklcd");
+  if (third) {
+    DBuf Xk = cbuf(ex, nf);
+    k_dk_mul<<<grid1d(nf, 256), 256, 0, ex.stream>>>(X2f.c(), c->eo.d(), c->ev.d(), k, o, v, Xk.c());
+    ADC_CHECK_LAUNCH();
+    TV Xkd = TV::dense(Xk.c(), {k, o, o, v, v});
+    // S1 += x/4 [ O2 (Delta_K X) - Delta_S o (O2 X) + Z1 X ]
+    eval_terms(ex, E.O2, src, {{"zklcd", Xkd}}, false, CR(0.25 * x), S1, "zia");
+    DBuf tmp = cbuf(ex, k * n1);
+    fill_zero(ex, tmp.p, tmp.bytes);
+    TV T1 = TV::dense(tmp.c(), {k, o, v});
+    eval_terms(ex, E.O2, src, {{"zklcd", Xd}}, false, CR(0.25 * x), T1, "zia");
+    diag_mul_add(ex, k, n1, E.dS.d(), tmp.c(), n1, S, N, -1.0);
+    eval_terms(ex, E.Z1, src, {{"zklcd", Xd}}, false, CR(0.25 * x), S1, "zia");
+    // S2 += x [ Delta_K o conj(O2) X1 - conj(O2) (Delta_S o X1) + conj(Z1) X1 ]
+    DBuf T2 = cbuf(ex, nf);
+    fill_zero(ex, T2.p, T2.bytes);
+    eval_terms(ex, E.O2, src, {{"zia", X1}}, true, CR(x), TV::dense(T2.c(), {k, o, o, v, v}), "zklcd");
+    k_dk_mul<<<grid1d(nf, 256), 256, 0, ex.stream>>>(T2.c(), c->eo.d(), c->ev.d(), k, o, v, T2.c());
+    ADC_CHECK_LAUNCH();
+    zaxpby(ex, nf, C1(), T2.c(), C1(), S2f.c());
+    DBuf Xs = cbuf(ex, k * n1);
+    fill_zero(ex, Xs.p, Xs.bytes);
+    diag_mul_add(ex, k, n1, E.dS.d(), X, N, Xs.c(), n1, 1.0);
+    eval_terms(ex, E.O2, src, {{"zia", TV::dense(Xs.c(), {k, o, v})}}, true, CR(-x), Sd, "zklcd");
+    eval_terms(ex, E.Z1, src, {{"zia", X1}}, true, CR(x), Sd, "zklcd");
+    if (c->dd_order == 1)
+      eval_terms(ex, E.DD1, src, {{"zklcd", Xd}}, false, CR(0.25 * x), TV::dense(S2f.c(), {k, o, o, v, v}),
+                 "zijab");
+  }
+  // pack the doubles: S2[z][(k<l)][(c<d)] = S2f + zeroth order
+  DBuf half2 = cbuf(ex, k * po * v * v);
+  pair_pack(ex, S2f.c(), o * o * v * v, 0, o * v * v, v * v, 1, 0.0, k, 1, o, v * v, half2.c(), po * v * v, 0, C1(),
+            C0());
+  pair_pack(ex, half2.c(), po * v * v, v * v, v, 1, 0, 0.0, k, po, v, 1, S + n1, N, pv, C1(), C0());
+  diag_mul_add(ex, k, n2, c->d2.d(), X + n1, N, S + n1, N, 1.0);
+}
+
+}  // namespace adc

@@ -102,6 +102,7 @@ extern "C" int adc_sigma_noalloc(adc_ctx *c, const adc_c128 *X, adc_c128 *S, int
   if (k < 0 || (k > 0 && (!X || !S))) return ADC_ERR_ARG;
   if (k == 0) return ADC_OK;
   try {
+    if (c->kind == ADC_EE) throw Error(ADC_ERR_UNSUPPORTED, "adc_sigma_noalloc covers IP and EA");
     if (!device_ptr(X) || !device_ptr(S))
       throw Error(ADC_ERR_ARG, "adc_sigma_noalloc takes device pointers only (a host copy would allocate)");
     const bool prof = c->ex.prof;

@@ -22,8 +22,6 @@
 
 namespace adc {
 
-namespace {
-
 TV Bview(adc_ctx *c, char p, char q) {
   int64_t p0 = (p == 'o') ? 0 : c->o, q0 = (q == 'o') ? 0 : c->o;
   int64_t np = (p == 'o') ? c->o : c->v, nq = (q == 'o') ? c->o : c->v;
@@ -33,7 +31,7 @@ TV Bview(adc_ctx *c, char p, char q) {
 int64_t dim_of(adc_ctx *c, char x) { return x == 'o' ? c->o : c->v; }
 
 // dense <pq||rs> block [p][q][r][s]
-DBuf eri(adc_ctx *c, const char *spec) {
+DBuf eri_block(adc_ctx *c, const char *spec) {
   std::vector<int64_t> e = {dim_of(c, spec[0]), dim_of(c, spec[1]), dim_of(c, spec[2]),
                             dim_of(c, spec[3])};
   DBuf out = cbuf(c->ex, e[0] * e[1] * e[2] * e[3]);
@@ -44,6 +42,10 @@ DBuf eri(adc_ctx *c, const char *spec) {
          O, "pqrs");
   return out;
 }
+
+namespace {
+
+DBuf eri(adc_ctx *c, const char *spec) { return eri_block(c, spec); }
 
 TV dense(const DBuf &b, std::vector<int64_t> e) { return TV::dense(b.c(), e); }
 
@@ -132,41 +134,32 @@ static DBuf build_vvvv_packed(adc_ctx *c) {
   return G;
 }
 
-void setup_operators(adc_ctx *c) {
+void first_order_amplitudes(adc_ctx *c) {
   Exec &ex = c->ex;
-  const int64_t o = c->o, v = c->v, Q = c->Q;
-  const bool third = (c->order == 3) && (c->x != 0.0);
-  const double x = c->x;
-  const int64_t po = npairs(o), pv = npairs(v);
-  TV Boo = Bview(c, 'o', 'o'), Bov = Bview(c, 'o', 'v'), Bvo = Bview(c, 'v', 'o'),
-     Bvv = Bview(c, 'v', 'v');
+  const int64_t o = c->o, v = c->v;
+  TV Boo = Bview(c, 'o', 'o'), Bov = Bview(c, 'o', 'v'), Bvo = Bview(c, 'v', 'o'), Bvv = Bview(c, 'v', 'v');
   const double *eo = c->eo.d(), *ev = c->ev.d();
-
-  // ---- first-order doubles t_ij^ab = <ab||ij> / D_ij^ab
+  // t_ij^ab = <ab||ij> / D_ij^ab
   c->t1 = cbuf(ex, o * o * v * v);
   TV t1 = dense(c->t1, {o, o, v, v});
   einsum(ex, C1(), Bvo, "Qai", Bvo, "Qbj", C0(), t1, "ijab");
   einsum(ex, CR(-1.0), Bvo, "Qaj", Bvo, "Qbi", C1(), t1, "ijab");
   denom2_div(ex, c->t1.c(), eo, ev, o, v);
-  DBuf oovv = cbuf(ex, o * o * v * v);
-  oovv_from_t1(ex, c->t1.c(), eo, ev, o, v, oovv.c());
-  TV Toovv = dense(oovv, {o, o, v, v});
-
-  // ---- ring integrals W[j][a][k][c] = <ak||cj>
+  // ring integrals W[j][a][k][c] = <ak||cj>
   c->W = cbuf(ex, o * v * o * v);
   TV W = dense(c->W, {o, v, o, v});
   einsum(ex, C1(), Bvv, "Qac", Boo, "Qkj", C0(), W, "jakc");
   einsum(ex, CR(-1.0), Bvo, "Qaj", Bov, "Qkc", C1(), W, "jakc");
+}
 
-  // ---- second-order densities of Psi1
-  DBuf gvv_b = cbuf(ex, v * v), hoo_b = cbuf(ex, o * o);
-  TV gvv = dense(gvv_b, {v, v}), hoo = dense(hoo_b, {o, o});
-  einsum(ex, CR(0.5), t1.cj(), "ijdf", t1, "ijef", C0(), gvv, "de");
-  einsum(ex, CR(0.5), t1.cj(), "njef", t1, "mjef", C0(), hoo, "nm");
-
-  // ---- second-order amplitudes, ladder intermediate, R (third order only)
-  DBuf t2d_b, t2s_b, R_b, Lad_b, G_vv;
-  if (third) {
+void second_order_amplitudes(adc_ctx *c, DBuf &G_vv, DBuf &Lad_b, DBuf &t2d_b, DBuf &t2s_b) {
+  Exec &ex = c->ex;
+  const int64_t o = c->o, v = c->v, Q = c->Q;
+  const int64_t po = npairs(o), pv = npairs(v);
+  TV Bov = Bview(c, 'o', 'v'), Bvv = Bview(c, 'v', 'v');
+  const double *eo = c->eo.d(), *ev = c->ev.d();
+  TV t1 = dense(c->t1, {o, o, v, v});
+  TV W = dense(c->W, {o, v, o, v});
     G_vv = build_vvvv_packed(c);
     // Lad_ij^ab = 1/2 sum_cd <ab||cd> t_ij^cd = sum_{c<d} G[(ab),(cd)] t_ij^cd
     DBuf tp1 = cbuf(ex, o * o * pv), tp2 = cbuf(ex, po * pv);
@@ -216,6 +209,35 @@ void setup_operators(adc_ctx *c) {
     }
     denom1_div(ex, t2s_b.c(), eo, ev, o, v);
 
+}
+
+void setup_operators(adc_ctx *c) {
+  Exec &ex = c->ex;
+  const int64_t o = c->o, v = c->v, Q = c->Q;
+  const bool third = (c->order == 3) && (c->x != 0.0);
+  const double x = c->x;
+  const int64_t po = npairs(o), pv = npairs(v);
+  TV Boo = Bview(c, 'o', 'o'), Bov = Bview(c, 'o', 'v'), Bvo = Bview(c, 'v', 'o'),
+     Bvv = Bview(c, 'v', 'v');
+  const double *eo = c->eo.d(), *ev = c->ev.d();
+
+  first_order_amplitudes(c);
+  TV t1 = dense(c->t1, {o, o, v, v});
+  DBuf oovv = cbuf(ex, o * o * v * v);
+  oovv_from_t1(ex, c->t1.c(), eo, ev, o, v, oovv.c());
+  TV Toovv = dense(oovv, {o, o, v, v});
+  TV W = dense(c->W, {o, v, o, v});
+
+  // ---- second-order densities of Psi1
+  DBuf gvv_b = cbuf(ex, v * v), hoo_b = cbuf(ex, o * o);
+  TV gvv = dense(gvv_b, {v, v}), hoo = dense(hoo_b, {o, o});
+  einsum(ex, CR(0.5), t1.cj(), "ijdf", t1, "ijef", C0(), gvv, "de");
+  einsum(ex, CR(0.5), t1.cj(), "njef", t1, "mjef", C0(), hoo, "nm");
+
+  // ---- second-order amplitudes, ladder intermediate, R (third order only)
+  DBuf t2d_b, t2s_b, R_b, Lad_b, G_vv;
+  if (third) {
+    second_order_amplitudes(c, G_vv, Lad_b, t2d_b, t2s_b);
     // R[c][a][n][m] = sum_jf conj(t_nj^cf) t_mj^af
     R_b = cbuf(ex, v * v * o * o);
     einsum(ex, C1(), t1.cj(), "njcf", t1, "mjaf", C0(), dense(R_b, {v, v, o, o}), "canm");

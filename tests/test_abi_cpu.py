@@ -52,7 +52,7 @@ def test_error_strings_and_defaults(lib):
 
 
 @pytest.mark.parametrize("kind,order,nocc,nvir,code", [
-    (2, 3, 3, 5, -6),   # EE not built
+    (2, 4, 3, 5, -1),   # EE, bad order
     (7, 3, 3, 5, -1),   # unknown kind
     (0, 4, 3, 5, -1),   # bad order
     (0, 3, 1, 5, -1),   # IP needs two occupied spinors

@@ -1,0 +1,64 @@
+"""EE-ADC on the GPU (FP64) against the CPU oracle: sigma, diagonal, singles
+block and lowest roots (Sec. 2.1, Eq. 2 manifold). Tolerances as in
+test_gpu_parity: 1e-12 relative per sigma vector, 1e-8 Eh for eigenvalues."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from synthetic import make_problem, random_vectors  # noqa: E402
+from oracle import adc_ee  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from conftest import build_library
+    build_library()
+    import paper_2511_21640_gb300 as m
+    return m
+
+
+def _rel(S, R):
+    return np.linalg.norm(S - R, axis=-1) / np.linalg.norm(R, axis=-1)
+
+
+@pytest.mark.parametrize("o,v,Q,order,x,dd,seed", [
+    (4, 8, 12, 3, 1.0, 1, 1),
+    (5, 11, 20, 3, 0.4, 1, 2),
+    (3, 7, 9, 3, 1.0, 0, 3),
+    (6, 9, 14, 2, 0.0, 1, 4),
+    (2, 2, 5, 3, 1.0, 1, 5),   # one occupied pair, one virtual pair
+])
+def test_ee_sigma_diag_block(gpu, o, v, Q, order, x, dd, seed):
+    p = make_problem(o, v, Q, seed=seed, sigma=0.1, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=order, x=x, dd_order=dd) as ctx:
+        n1, n2 = adc_ee.dims(o, v)
+        assert (ctx.n1, ctx.n2) == (n1, n2)
+        T = adc_ee.Tensors(p.B, p.eps_occ, p.eps_vir)
+        X = random_vectors(ctx.N, 3, seed=seed + 10)
+        ref = adc_ee.sigma_ref(order, x, p.B, p.eps_occ, p.eps_vir, X, dd_order=dd, T=T)
+        S = ctx.sigma(X, "fp64")
+        assert _rel(S, ref).max() < 1e-12
+        d = ctx.diagonal()
+        dref = adc_ee.diagonal_ref(order, x, p.B, p.eps_occ, p.eps_vir, dd_order=dd, T=T)
+        assert np.abs(d - dref).max() < 1e-12 * max(1.0, np.abs(dref).max())
+        M = adc_ee.explicit_matrix(order, x, p.B, p.eps_occ, p.eps_vir, dd_order=dd)
+        assert np.abs(ctx.main_block() - M[:n1, :n1]).max() < 1e-12 * np.abs(M).max()
+        with pytest.raises(gpu.AdcError) as e:
+            ctx.sigma(X, "bf16x3")
+        assert e.value.code == -6
+
+
+def test_ee_davidson_matches_dense(gpu):
+    o, v, Q = 4, 9, 16
+    p = make_problem(o, v, Q, seed=7, sigma=0.08, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    M = adc_ee.explicit_matrix(3, 0.4, p.B, p.eps_occ, p.eps_vir)
+    w = np.linalg.eigvalsh(M)[:4]
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=3, x=0.4) as ctx:
+        om, Y, e64, st, rc = ctx.davidson(4, tol=1e-8, precision="fp64")
+    assert rc == 0
+    assert np.abs(om - w).max() < 1e-8
+    assert np.linalg.norm(Y @ M.T - om[:, None] * Y, axis=1).max() < 1e-7
