@@ -330,10 +330,10 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
     else ++since;
     if (mx <= tol) {
       if (phase == 2) { converged = true; break; }
-      // accept only on FP64 residuals: collapse with sigma64 and re-check
-      d.collapse(kr, true);
+      // accept only on FP64 residuals: collapse onto the wanted roots with sigma64 and re-check
+      d.collapse(nroots, true);
       phase = 1;
-      wh = d.ritz(kr);
+      wh = d.ritz(nroots);
       rn = d.row_norms(d.R.c(), nroots);
       mx = *std::max_element(rn.begin(), rn.end());
       if (c->opts.verbose) fprintf(stderr, "[davidson] fp64 check max|r| %.3e\n", mx);
@@ -342,7 +342,7 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
       since = 0;
     } else if (phase != 2 && since >= stall_window) {
       // stalled at the split-precision floor: FP64 base for the current Ritz vectors
-      d.collapse(kr, true);
+      d.collapse(nroots, true);
       phase = 1;
       best = 1e300;
       since = 0;
@@ -353,8 +353,9 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
     for (int r = 0; r < nroots; ++r)
       if (rn[r] > tol) rows.push_back(r);
     if (d.m + (int)rows.size() > d.mmax) {
-      d.collapse(kr, phase == 1);
-      wh = d.ritz(kr);
+      const int kc = (phase == 1) ? nroots : kr;  // FP64 sigma only for the wanted roots
+      d.collapse(kc, phase == 1);
+      wh = d.ritz(kc);
     }
     ADC_CUDA(cudaMemcpyAsync(d.rowsb.p, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice, ex.stream));
     k_precondition<<<grid1d((int64_t)rows.size() * N, 256), 256, 0, ex.stream>>>(
@@ -372,9 +373,8 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   if (it > max_iter) it = max_iter;
   if (!converged && phase != 2) {
     // report FP64 residuals of the best vectors
-    const int kr = std::min(d.m, krmax);
-    d.collapse(kr, true);
-    wh = d.ritz(kr);
+    d.collapse(nroots, true);
+    wh = d.ritz(nroots);
     rn = d.row_norms(d.R.c(), nroots);
   }
   ADC_CUDA(cudaStreamSynchronize(ex.stream));

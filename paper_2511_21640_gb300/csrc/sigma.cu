@@ -14,6 +14,18 @@
 
 namespace adc {
 
+namespace {
+// dst rows (pitch ldd) += alpha * src rows (pitch lds), k rows of length n
+__global__ void k_rows_axpy(int64_t k, int64_t n, cplx alpha, const cplx *src, int64_t lds, cplx *dst,
+                            int64_t ldd) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < k * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / n, i = idx % n;
+    dst[r * ldd + i] = cadd(dst[r * ldd + i], cmul(alpha, src[r * lds + i]));
+  }
+}
+}  // namespace
+
 cplx *scratch(adc_ctx *c, int64_t ncplx) {
   size_t need = (size_t)ncplx * sizeof(cplx);
   if (c->scratch.bytes < need) {
@@ -41,19 +53,25 @@ void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
   if (!sat) return;
   if (c->kind == ADC_EA) {
     const int64_t pv = npairs(v);
-    // ladder: S2[r][j][(ab)] += x sum_(cd) X2[r][j][(cd)] Glad[(ab)][(cd)]
+    // ladder: S2[r][j][(ab)] += x sum_(cd) X2[r][j][(cd)] Glad[(ab)][(cd)], one GEMM over all (r, j)
     ex.tag = "ladder";
-    zgemm(ex, o, pv, pv, k, CR(x), X + n1, N, pv, 1, false, c->Glad.c(), 0, 1, pv, false, C1(),
-          S + n1, N, pv, 1);
-    // ring: Xf[r][k][c][b] (antisymmetric in c,b); T[r][(j,a)][b] = sum_(kc) W[(j,a)][(kc)] Xf[r][(kc)][b]
-    ex.tag = "ring";
-    cplx *Xf = scratch(c, 2 * k * o * v * v);
+    cplx *Xf = scratch(c, 2 * k * o * v * v + 2 * k * o * pv);
     cplx *T = Xf + k * o * v * v;
+    cplx *Xg = T + k * o * v * v, *Og = Xg + k * o * pv;
+    ADC_CUDA(cudaMemcpy2DAsync(Xg, o * pv * sizeof(cplx), X + n1, N * sizeof(cplx), o * pv * sizeof(cplx), k,
+                               cudaMemcpyDeviceToDevice, ex.stream));
+    zgemm(ex, k * o, pv, pv, 1, C1(), Xg, 0, pv, 1, false, c->Glad.c(), 0, 1, pv, false, C0(), Og, 0, pv, 1);
+    k_rows_axpy<<<grid1d(k * o * pv, 256), 256, 0, ex.stream>>>(k, o * pv, CR(x), Og, o * pv, S + n1, N);
+    ADC_CHECK_LAUNCH();
+    // ring: Xf[r][k][c][b] (antisymmetric in c,b); T[(j,a)][(r,b)] = sum_(kc) W[(j,a)][(kc)] Xt[(kc)][(r,b)]
+    ex.tag = "ring";
     pair_unpack(ex, X + n1, k, o, N, pv, v, 1, Xf);
-    zgemm(ex, o * v, v, o * v, k, C1(), c->W.c(), 0, o * v, 1, false, Xf, o * v * v, v, 1, false, C0(),
-          T, o * v * v, v, 1);
-    // S2[r][j][(a<b)] -= x (T[r][j][a][b] - T[r][j][b][a])
-    pair_pack(ex, T, o * v * v, v * v, v, 1, 0, 1.0, k, o, v, 1, S + n1, N, pv, CR(-x), C1());
+    // Xt[(kc)][r][b] = Xf[r][(kc)][b]
+    permute(ex, Xf, {o * v, k, v}, {v, o * v * v, 1}, false, T, C1(), C0());
+    zgemm(ex, o * v, k * v, o * v, 1, C1(), c->W.c(), 0, o * v, 1, false, T, 0, k * v, 1, false, C0(), Xf, 0, k * v,
+          1);
+    // Xf now holds R[(j,a)][r][b]; S2[r][j][(a<b)] -= x (R[j,a][r][b] - R[j,b][r][a])
+    pair_pack(ex, Xf, v, v * k * v, k * v, 1, 0, 1.0, k, o, v, 1, S + n1, N, pv, CR(-x), C1());
   } else {
     const int64_t po = npairs(o);
     // ladder: S2[r][(ij)][a] += x sum_(kl) Glad[(ij)][(kl)] X2[r][(kl)][a]
