@@ -32,7 +32,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synthetic import CONFIGS, config_problem, random_vectors  # noqa: E402
+from synthetic import (BATCH_CONFIGS, CONFIGS, batch_problems, batch_sizes, config_problem,  # noqa: E402
+                       random_vectors)
 
 METRIC = "Davidson s/root and sigma TFLOP/s: mixed vs FP64 on GPU at 1e-6 Eh error"
 
@@ -133,10 +134,123 @@ def cpu_oracle_sample(p, x, n_rows=6, seed=5):
     return t / n_rows, f"{n_rows} satellite rows of S = M X for one vector, each row from Eq. 43 integrals"
 
 
+def run_batch(args, cfgname):
+    """Batched IP/EA workload: the problems are planned into waves that fit the
+    device memory; each wave is initialised, its batched split-precision sigma
+    is timed (graph replays, and the grouped tensor-core kernel alone), and it
+    is solved with the batched Davidson. value = Davidson seconds per root over
+    all problems; e2e adds the adc_init calls (host inputs copied inside)."""
+    import torch
+    import paper_2511_21640_gb300 as adcgpu
+    c = BATCH_CONFIGS[cfgname]
+    nroots = c["nroots"]
+    tol = args.tol if args.tol is not None else c["tol"]
+    sizes = batch_sizes(cfgname)
+    free = torch.cuda.mem_get_info()[0]
+    nw, order, wave, mem, cost = adcgpu.batch_plan(sizes, nroots, int(0.85 * free))
+    log(f"{len(sizes)} problems in {nw} waves")
+    tot = dict(init_s=0.0, solve_s=0.0, sig_ms=0.0, sig_flops=0.0, g_ms=0.0, g_flops=0.0, g_launch=0,
+               batches=0, graph_launches=0, sigma_calls=0, sigma_calls_fp64=0, iters=[])
+    omegas, errs, status_all = {}, {}, {}
+    clocks = Clocks()
+    clocks.start()
+    for w in range(nw):
+        ids = [int(i) for i in order if wave[i] == w]
+        probs = batch_problems(cfgname, select=ids)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctxs = [adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind=p.kind, order=p.order, x=p.x) for p in probs]
+        for cx in ctxs:
+            cx.sync()
+        tot["init_s"] += time.perf_counter() - t0
+        log(f"wave {w}: {len(ids)} problems initialised in {time.perf_counter() - t0:.1f} s")
+        with adcgpu.Batch(ctxs) as b:
+            Xs = [torch.from_numpy(random_vectors(cx.N, nroots, seed=900 + i)).cuda() for i, cx in zip(ids, ctxs)]
+            Ss = [torch.empty_like(X) for X in Xs]
+            for _ in range(max(args.warmup, 2)):
+                b.sigma(Xs, "bf16x3", outs=Ss)
+            i0 = b.info()
+            for _ in range(5):
+                b.sigma(Xs, "bf16x3", outs=Ss)
+            i1 = b.info()
+            tot["sig_ms"] += i1["batch_ms"] - i0["batch_ms"]
+            tot["sig_flops"] += i1["tc_flops"] - i0["tc_flops"]
+            b.use_graphs(False)
+            for _ in range(3):
+                b.sigma(Xs, "bf16x3", outs=Ss)
+            i2 = b.info()
+            b.use_graphs(True)
+            tot["g_ms"] += i2["grouped_ms"] - i1["grouped_ms"]
+            tot["g_flops"] += i2["grouped_flops"] - i1["grouped_flops"]
+            tot["g_launch"] += i2["grouped_launches"] - i1["grouped_launches"]
+            del Xs, Ss
+            torch.cuda.synchronize()
+            l0 = adcgpu.launch_count()
+            t1 = time.perf_counter()
+            om, e64, st_codes, sts, rc = b.davidson(nroots, tol=tol, max_iter=300, precision="bf16x3")
+            tot["solve_s"] += time.perf_counter() - t1
+            tot["launches"] = tot.get("launches", 0) + adcgpu.launch_count() - l0
+            i3 = b.info()
+            tot["batches"] += i3["batches"] - i2["batches"]
+            tot["graph_launches"] += i3["graph_launches"] - i2["graph_launches"]
+            log(f"wave {w}: solved in {time.perf_counter() - t1:.1f} s, rc {rc}")
+            for j, i in enumerate(ids):
+                omegas[i] = om[j].tolist()
+                errs[i] = float(e64[j].max())
+                status_all[i] = int(st_codes[j])
+                tot["sigma_calls"] += sts[j]["sigma_calls"]
+                tot["sigma_calls_fp64"] += sts[j]["sigma_calls_fp64"]
+                tot["iters"].append(sts[j]["iterations"])
+        for cx in ctxs:
+            cx.close()
+    clk = clocks.stop()
+    nprob = len(sizes)
+    roots = nprob * nroots
+    pk, pk_kind = peaks()
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    g_ach = 3.0 * tot["g_flops"] / (tot["g_ms"] * 1e-3) / 1e12 if tot["g_ms"] > 0 else None
+    line = {
+        "metric": METRIC, "value": tot["solve_s"] / roots, "unit": "s/root", "n_gpus": 1, "steps": 1,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot["solve_s"], "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
+        "config": {"workload": cfgname, "problems": nprob, "nroots": nroots, "tol_fp64_residual": tol,
+                   "waves": nw, "sizes": "nocc U[10,40], nvir U[50,250], naux 6 nvir, IP even / EA odd, x 0.5",
+                   "l2": "operators larger than L2"},
+        "clocks": clk,
+        "roofline": {"bound": "tensor", "kernel": "k_tc_grouped (all problems' coupling, ladder, ring jobs)",
+                     "achieved": g_ach, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (g_ach / peak) if g_ach else None, "traffic": None,
+                     "peak_kind": f"bf16 dense sustained ({pk_kind}); achieved counts 3 BF16 products per "
+                                  "split-precision product", "launches_timed": tot["g_launch"],
+                     "avg_launch_ms": tot["g_ms"] / max(1, tot["g_launch"])},
+        "batched_sigma": {"tflops_algorithmic": tot["sig_flops"] / (tot["sig_ms"] * 1e-3) / 1e12,
+                          "ms_per_batch": tot["sig_ms"] / (5 * nw), "vectors_per_problem": nroots,
+                          "includes": "FP64 main block, operand packing, grouped tensor-core launch, epilogues "
+                                      "(CUDA graph replays)"},
+        "davidson": {"iterations_max": max(tot["iters"]), "iterations_mean": float(np.mean(tot["iters"])),
+                     "sigma_calls": tot["sigma_calls"], "sigma_calls_fp64": tot["sigma_calls_fp64"],
+                     "batched_products": tot["batches"], "graph_replays": tot["graph_launches"],
+                     "max_err64": max(errs.values()), "status_nonzero": [i for i, s in status_all.items() if s]},
+        "init_s": tot["init_s"],
+        "e2e": {"value": (tot["init_s"] + tot["solve_s"]) / roots, "unit": "s/root",
+                "h2d_bytes_per_step": int(sum(16 * d["naux"] * (d["nocc"] + d["nvir"]) ** 2 for d in sizes)),
+                "d2h_bytes_per_step": int(16 * roots),
+                "includes": "adc_init of every problem (H2D copy + FP64 operator setup) + batched Davidson"},
+        "gpu_launches": int(tot.get("launches", 0)), "cpu_baseline": None,
+    }
+    print(json.dumps(line))
+
+
 def run_reference(args, cfgname):
     """CPU oracle arm: each step evaluates a bounded sample of sigma rows."""
-    c = CONFIGS[cfgname]
-    p = config_problem(cfgname)
+    if cfgname in BATCH_CONFIGS:
+        # one EA problem of the batch stands for all of them (rows scaled by each problem's N)
+        sizes = batch_sizes(cfgname)
+        p = batch_problems(cfgname, select=[1])[0]
+        c = dict(kind="EA", order=3, x=BATCH_CONFIGS[cfgname]["x"], nroots=BATCH_CONFIGS[cfgname]["nroots"])
+    else:
+        c = CONFIGS[cfgname]
+        p = config_problem(cfgname)
     o, v = p.nocc, p.nvir
     N = v + o * v * (v - 1) // 2
     sig_vecs_per_root = args.ref_sigma_vectors_per_root
@@ -182,6 +296,13 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             run_reference(args, args.config)
+        return
+
+    if args.config in BATCH_CONFIGS:
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            run_batch(args, args.config)
         return
 
     import torch

@@ -211,6 +211,98 @@ const char *adc_strerror(int code);
  * NULL); valid until the next call on the same context. */
 const char *adc_last_error(const adc_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent problems (IP/EA; EE contexts take part in FP64
+ * only). The paper solves one problem at a time; batching is this library's
+ * addition for many small problems on one GPU.
+ * ---------------------------------------------------------------------- */
+typedef struct adc_batch adc_batch;
+
+/* Counters of a batch (all since adc_batch_create, or of one adc_batch_solve). */
+typedef struct {
+  int64_t batches;          /* batched split-precision sigma products executed */
+  int64_t graph_launches;   /* of those, replays of a captured CUDA graph */
+  int64_t graphs_captured;  /* graphs captured (a batch is captured at its second occurrence) */
+  int64_t direct_launches;  /* batches enqueued without a graph */
+  int64_t sigma_vectors;    /* vectors multiplied in batched products (padding included) */
+  double batch_ms;          /* device time of the batched products (CUDA events) */
+  double tc_flops;          /* algorithmic flops of their tensor-core jobs (8 per complex MAC) */
+  int64_t tuned_shapes;     /* GEMM shapes whose tile width the autotuner has timed (process-wide) */
+  int64_t waves;            /* adc_batch_solve: groups of problems resident together */
+  double init_s;            /* adc_batch_solve: wall time of the adc_init calls */
+  double solve_s;           /* adc_batch_solve: wall time of the batched Davidson runs */
+  int64_t grouped_launches; /* batches run without a graph, whose grouped kernel was timed alone */
+  double grouped_ms;        /* device time of those grouped tensor-core launches (CUDA events) */
+  double grouped_flops;     /* their algorithmic flops */
+} adc_batch_info;
+
+/* Groups n existing contexts (distinct, each in no other batch; the caller
+ * keeps ownership and frees the batch before the contexts). */
+int adc_batch_create(adc_batch **batch, adc_ctx *const *ctxs, int n);
+
+/* S[i] = M_i X[i] for every context i with k[i] > 0 vectors (X[i], S[i]:
+ * [k[i]][N_i] device arrays, same layout as adc_sigma). With
+ * ADC_PREC_BF16X3 all coupling, ladder and ring products of all problems are
+ * the jobs of one grouped persistent tensor-core launch (tile widths chosen
+ * by an autotuner that times each new GEMM shape once); a call that repeats
+ * with the same contexts, block sizes and pointers is captured as a CUDA
+ * graph at its second occurrence and replayed from then on. ADC_PREC_FP64
+ * runs the problems' FP64 products one after the other. Synchronous. EE
+ * contexts with ADC_PREC_BF16X3: ADC_ERR_UNSUPPORTED. */
+int adc_batch_sigma(adc_batch *batch, const adc_c128 *const *X, adc_c128 *const *S, const int64_t *k,
+                    int precision);
+
+/* The lowest nroots roots of every problem (adc_davidson semantics per
+ * problem, FP64 residual tolerance tol): each problem runs on its own host
+ * thread and stream, and the split-precision sigma products of the new
+ * blocks of all running problems are executed together as one batched
+ * product (nroots vectors per problem; rows beyond a problem's new block are
+ * computed and ignored). omega, err64: [n][nroots] host arrays; status[i] =
+ * the problem's return code; st: NULL or [n]. Returns ADC_OK, ADC_ERR_NOCONV
+ * if a problem did not converge, or the last other error. */
+int adc_batch_davidson(adc_batch *batch, int nroots, double tol, int max_iter, int precision, double *omega,
+                       double *err64, int *status, adc_stats *st);
+
+/* Switches graph capture of repeated batches on (default) or off. */
+int adc_batch_use_graphs(adc_batch *batch, int on);
+int adc_batch_info_get(const adc_batch *batch, adc_batch_info *info);
+void adc_batch_free(adc_batch *batch);
+const char *adc_batch_last_error(const adc_batch *batch);
+
+/* One problem given as raw inputs (the arguments of adc_init). */
+typedef struct {
+  const adc_c128 *B;
+  int64_t naux;
+  const double *eps_occ;
+  int64_t nocc;
+  const double *eps_vir;
+  int64_t nvir;
+  int kind, order;
+  double x;
+} adc_problem;
+
+typedef struct {
+  int64_t mem_budget;  /* device bytes for resident problems, 0 = 85% of the free memory */
+  int init_lanes;      /* concurrent adc_init calls, 0 = 4 */
+  int verbose;
+} adc_batch_opts;
+
+/* Host-only planner (no GPU needed): estimated device bytes mem_est[i] and
+ * work cost_est[i] (complex MACs) of every problem, the order of decreasing
+ * cost (order[0..n)), and the wave wave[i] of every problem: problems are
+ * taken in that order and each joins the first wave whose estimated memory
+ * stays within mem_budget (a problem larger than the budget gets a wave of
+ * its own). Returns the number of waves or a negative error code. Only the
+ * sizes, kind, order and x of the problems are read. */
+int adc_batch_plan(int n, const adc_problem *problems, int nroots, int64_t mem_budget, int *order, int *wave,
+                   int64_t *mem_est, double *cost_est);
+
+/* Solves n problems wave by wave: each wave's contexts are initialised on
+ * opts->init_lanes concurrent lanes, solved with adc_batch_davidson and
+ * freed. omega, err64: [n][nroots]; status: [n]; info: NULL or totals. */
+int adc_batch_solve(int n, const adc_problem *problems, int nroots, double tol, int max_iter, int precision,
+                    const adc_batch_opts *opts, double *omega, double *err64, int *status, adc_batch_info *info);
+
 #ifdef __cplusplus
 }
 #endif

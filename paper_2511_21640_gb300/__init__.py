@@ -55,6 +55,28 @@ class adc_kernel_stat(ctypes.Structure):
                 ("flops", ctypes.c_double)]
 
 
+class adc_batch_info(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
+                ("graphs_captured", ctypes.c_int64), ("direct_launches", ctypes.c_int64),
+                ("sigma_vectors", ctypes.c_int64), ("batch_ms", ctypes.c_double), ("tc_flops", ctypes.c_double),
+                ("tuned_shapes", ctypes.c_int64), ("waves", ctypes.c_int64), ("init_s", ctypes.c_double),
+                ("solve_s", ctypes.c_double), ("grouped_launches", ctypes.c_int64), ("grouped_ms", ctypes.c_double),
+                ("grouped_flops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class adc_problem(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_void_p), ("naux", ctypes.c_int64), ("eps_occ", ctypes.c_void_p),
+                ("nocc", ctypes.c_int64), ("eps_vir", ctypes.c_void_p), ("nvir", ctypes.c_int64),
+                ("kind", ctypes.c_int), ("order", ctypes.c_int), ("x", ctypes.c_double)]
+
+
+class adc_batch_opts(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_int64), ("init_lanes", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
@@ -80,6 +102,16 @@ def _load():
         "adc_strerror": (ctypes.c_char_p, [I]),
         "adc_last_error": (ctypes.c_char_p, [P]),
         "adc_diag_gemm": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "adc_batch_create": (I, [ctypes.POINTER(P), P, I]),
+        "adc_batch_sigma": (I, [P, P, P, P, I]),
+        "adc_batch_davidson": (I, [P, I, D, I, I, P, P, P, P]),
+        "adc_batch_use_graphs": (I, [P, I]),
+        "adc_batch_info_get": (I, [P, ctypes.POINTER(adc_batch_info)]),
+        "adc_batch_free": (None, [P]),
+        "adc_batch_last_error": (ctypes.c_char_p, [P]),
+        "adc_batch_plan": (I, [I, P, I, I64, P, P, P, P]),
+        "adc_batch_solve": (I, [I, P, I, D, I, I, ctypes.POINTER(adc_batch_opts), P, P, P,
+                                ctypes.POINTER(adc_batch_info)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -272,6 +304,135 @@ class Context:
         return {"D": D, "eta": eta, "V": V, "n_keep": k, "U": U[:, :k].copy(), "eps_new": en[:k].copy()}
 
 
+def _bcheck(rc, h=None):
+    if rc != 0:
+        msg = lib.adc_batch_last_error(h)
+        raise AdcError(rc, msg.decode() if msg else "")
+
+
+class Batch:
+    """Several contexts solved together (``adc_batch_*``); the contexts must outlive the batch."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        self._h = ctypes.c_void_p()
+        _bcheck(lib.adc_batch_create(ctypes.byref(self._h), arr, len(self.contexts)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.adc_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def use_graphs(self, on=True):
+        _bcheck(lib.adc_batch_use_graphs(self._h, 1 if on else 0), self._h)
+
+    def sigma(self, Xs, precision="bf16x3", outs=None):
+        """S_i = M_i X_i for device tensors X_i [k_i][N_i] (``adc_batch_sigma``)."""
+        import torch
+        n = len(self.contexts)
+        if len(Xs) != n:
+            raise ValueError("one block per context")
+        Ss = outs if outs is not None else [torch.empty_like(X) for X in Xs]
+        for X, S, c in zip(Xs, Ss, self.contexts):
+            if not (_is_torch(X) and X.is_cuda and _is_torch(S) and S.is_cuda):
+                raise TypeError("batched sigma takes CUDA tensors")
+            if X.shape[-1] != c.N or X.dtype != torch.complex128 or not X.is_contiguous():
+                raise ValueError("X_i must be contiguous complex128 [k][N_i]")
+        xp = (ctypes.c_void_p * n)(*[X.data_ptr() for X in Xs])
+        sp = (ctypes.c_void_p * n)(*[S.data_ptr() for S in Ss])
+        kk = (ctypes.c_int64 * n)(*[X.shape[0] if X.ndim == 2 else 1 for X in Xs])
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _bcheck(lib.adc_batch_sigma(self._h, xp, sp, kk, p), self._h)
+        return Ss
+
+    def davidson(self, nroots, tol=1e-8, max_iter=200, precision="bf16x3"):
+        """Lowest roots of every problem (``adc_batch_davidson``): (omega, err64, status, stats list, rc)."""
+        n = len(self.contexts)
+        omega = np.empty((n, nroots), dtype=np.float64)
+        err = np.empty((n, nroots), dtype=np.float64)
+        status = np.empty(n, dtype=np.int32)
+        st = (adc_stats * n)()
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        rc = lib.adc_batch_davidson(self._h, int(nroots), float(tol), int(max_iter), p,
+                                    omega.ctypes.data_as(ctypes.c_void_p), err.ctypes.data_as(ctypes.c_void_p),
+                                    status.ctypes.data_as(ctypes.c_void_p), st)
+        if rc not in (0, -4):
+            _bcheck(rc, self._h)
+        return omega, err, status, [s.as_dict() for s in st], rc
+
+    def info(self):
+        i = adc_batch_info()
+        _bcheck(lib.adc_batch_info_get(self._h, ctypes.byref(i)), self._h)
+        return i.as_dict()
+
+
+def _problems(problems):
+    """adc_problem array from objects with B, eps_occ, eps_vir, kind, order, x (numpy host arrays)."""
+    arr = (adc_problem * len(problems))()
+    keep = []
+    for i, q in enumerate(problems):
+        B = np.ascontiguousarray(q.B, dtype=np.complex128)
+        eo = np.ascontiguousarray(q.eps_occ, dtype=np.float64)
+        ev = np.ascontiguousarray(q.eps_vir, dtype=np.float64)
+        keep += [B, eo, ev]
+        kind = KINDS[q.kind] if isinstance(q.kind, str) else int(q.kind)
+        arr[i] = adc_problem(B.ctypes.data, B.shape[0], eo.ctypes.data, eo.shape[0], ev.ctypes.data, ev.shape[0],
+                             kind, int(q.order), float(q.x))
+    return arr, keep
+
+
+def batch_plan(problems, nroots, mem_budget):
+    """Host-only wave plan (``adc_batch_plan``): (n_waves, order, wave, mem_est, cost_est)."""
+    n = len(problems)
+    arr = (adc_problem * n)()
+    for i, q in enumerate(problems):
+        kind = KINDS[q["kind"]] if isinstance(q["kind"], str) else int(q["kind"])
+        arr[i] = adc_problem(None, int(q["naux"]), None, int(q["nocc"]), None, int(q["nvir"]), kind,
+                             int(q.get("order", 3)), float(q.get("x", 1.0)))
+    order = np.empty(n, dtype=np.int32)
+    wave = np.empty(n, dtype=np.int32)
+    mem = np.empty(n, dtype=np.int64)
+    cost = np.empty(n, dtype=np.float64)
+    rc = lib.adc_batch_plan(n, arr, int(nroots), int(mem_budget), order.ctypes.data_as(ctypes.c_void_p),
+                            wave.ctypes.data_as(ctypes.c_void_p), mem.ctypes.data_as(ctypes.c_void_p),
+                            cost.ctypes.data_as(ctypes.c_void_p))
+    if rc < 0:
+        _bcheck(rc)
+    return rc, order, wave, mem, cost
+
+
+def batch_solve(problems, nroots, tol=1e-6, max_iter=300, precision="bf16x3", mem_budget=0, init_lanes=0):
+    """Solve many problems given as host arrays (``adc_batch_solve``): (omega, err64, status, info, rc)."""
+    n = len(problems)
+    arr, keep = _problems(problems)
+    o = adc_batch_opts(int(mem_budget), int(init_lanes), 0)
+    omega = np.empty((n, nroots), dtype=np.float64)
+    err = np.empty((n, nroots), dtype=np.float64)
+    status = np.empty(n, dtype=np.int32)
+    info = adc_batch_info()
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    rc = lib.adc_batch_solve(n, arr, int(nroots), float(tol), int(max_iter), p, ctypes.byref(o),
+                             omega.ctypes.data_as(ctypes.c_void_p), err.ctypes.data_as(ctypes.c_void_p),
+                             status.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info))
+    del keep
+    if rc not in (0, -4):
+        _bcheck(rc)
+    return omega, err, status, info.as_dict(), rc
+
+
 def diag_gemm(which, M, N, K, seed=1, reps=3):
     """Accuracy and time of one contraction kernel (``adc_diag_gemm``): (rel_err, ms)."""
     e, t = ctypes.c_double(), ctypes.c_double()
@@ -286,5 +447,5 @@ def launch_count():
     return int(lib.adc_launch_count())
 
 
-__all__ = ["Context", "AdcError", "diag_gemm", "launch_count", "lib", "LIB_PATH", "ADC_IP", "ADC_EA", "ADC_EE",
+__all__ = ["Context", "Batch", "batch_plan", "batch_solve", "AdcError", "diag_gemm", "launch_count", "lib", "LIB_PATH", "ADC_IP", "ADC_EA", "ADC_EE",
            "ADC_PREC_FP64", "ADC_PREC_BF16X3"]

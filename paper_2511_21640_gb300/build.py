@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libadc_gb300.so")
 SOURCES = ["tensor.cu", "setup.cu", "sigma.cu", "sigma_tc.cu", "tc_gemm.cu", "eig.cu",
-           "davidson.cu", "fns.cu", "api.cu", "diag.cu", "noalloc.cu", "blockops.cu", "terms.cu", "ee.cu"]
+           "davidson.cu", "fns.cu", "api.cu", "diag.cu", "noalloc.cu", "blockops.cu", "terms.cu", "ee.cu",
+           "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -53,7 +54,7 @@ def build(force=False, verbose=False):
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(_compile, SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -8,6 +8,7 @@
 namespace adc {
 struct TcCache;  // split-precision operator copies (tc_gemm.cu)
 struct EEOps;    // EE-ADC operators (ee.cu)
+struct BatchCoord;  // cross-problem sigma batching (batch.cu)
 }
 
 struct adc_ctx {
@@ -42,6 +43,11 @@ struct adc_ctx {
   // per-call scratch, grown on demand
   adc::DBuf scratch;
 
+  // set while the context's Davidson runs inside a batch: its split-precision
+  // sigma products are then gathered with the other problems' into one launch
+  adc::BatchCoord *batch = nullptr;
+  int batch_slot = -1;
+
   ~adc_ctx();
 };
 
@@ -60,5 +66,12 @@ void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision);
 void release_tc(adc_ctx *c);
+void tc_ensure(adc_ctx *c);  // split-precision operator copies, built on first use
 cplx *scratch(adc_ctx *c, int64_t ncplx);
+// inside a batch (c->batch set): S = M X (split precision) of this problem's
+// block, executed together with the other problems' blocks; blocks until done
+void batch_submit(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
+// the problem stops / resumes taking part in the batched products (FP64 work)
+void batch_leave(adc_ctx *c);
+void batch_rejoin(adc_ctx *c);
 }  // namespace adc

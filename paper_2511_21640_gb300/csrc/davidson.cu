@@ -86,6 +86,15 @@ __global__ void k_precondition(const cplx *R, const double *w, const int *rows, 
   }
 }
 
+// T[t] = R[rows[t]]
+__global__ void k_gather_rows(const cplx *R, const int *rows, int64_t nt, int64_t n, cplx *T) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nt * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = idx / n, i = idx - t * n;
+    T[idx] = R[(int64_t)rows[t] * n + i];
+  }
+}
+
 __global__ void k_scale_row(cplx *X, int64_t n, const double *nrm) {
   double s = 1.0 / nrm[0];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -144,6 +153,7 @@ struct Davidson {
     w = DBuf(ex, mmax * sizeof(double));
     T = cbuf(ex, (int64_t)nr * N);
     Tn = cbuf(ex, (int64_t)nr * N);
+    fill_zero(ex, T.p, T.bytes);
     Gs = cbuf(ex, (int64_t)nr * nr);
     Zs = cbuf(ex, (int64_t)nr * nr);
     Ws = cbuf(ex, (int64_t)nr * nr);
@@ -159,11 +169,36 @@ struct Davidson {
 
   void apply_sigma(const cplx *X, cplx *S, int64_t k, int prec) {
     Timer t;
-    sigma(c, X, S, k, prec);
-    ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    // inside a batch the other problems go on without this one meanwhile
+    if (c->batch) batch_leave(c);
+    try {
+      sigma(c, X, S, k, prec);
+      ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    } catch (...) {
+      if (c->batch) batch_rejoin(c);
+      throw;
+    }
+    if (c->batch) batch_rejoin(c);
     tsig += t.s();
     st.sigma_calls += (int)k;
     if (prec == ADC_PREC_FP64) st.sigma_calls_fp64 += (int)k;
+  }
+
+  // sigma of the na new vectors (in T and in V[m:m+na]) into AV[m:m+na]. In a
+  // batch the split-precision product of the whole T block (nroots rows, the
+  // rows past na are ignored) joins the other problems' blocks; T and Tn keep
+  // their addresses, so a repeated batch replays a captured graph.
+  void apply_sigma_new(int na, int prec) {
+    if (c->batch && prec == ADC_PREC_BF16X3 && na <= nroots) {
+      Timer t;
+      batch_submit(c, T.c(), Tn.c(), nroots);
+      ADC_CUDA(cudaMemcpyAsync(AV.c() + (int64_t)m * N, Tn.c(), (int64_t)na * N * sizeof(cplx),
+                               cudaMemcpyDeviceToDevice, ex.stream));
+      tsig += t.s();
+      st.sigma_calls += na;
+      return;
+    }
+    apply_sigma(V.c() + (int64_t)m * N, AV.c() + (int64_t)m * N, na, prec);
   }
 
   // G[0:m+na][m:m+na] = V^H AV[m:m+na], lower part by Hermiticity
@@ -362,11 +397,28 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
         d.R.c(), d.w.d(), (const int *)d.rowsb.p, c->diag.d(), (int64_t)rows.size(), N, d.T.c());
     ADC_CHECK_LAUNCH();
     int na = d.orthonormalise((int)rows.size());
-    if (na == 0) break;
+    if (na == 0) {
+      // the preconditioned corrections lie in the subspace (an eigenvalue next
+      // to a diagonal element of M): take the residuals themselves
+      k_gather_rows<<<grid1d((int64_t)rows.size() * N, 256), 256, 0, ex.stream>>>(
+          d.R.c(), (const int *)d.rowsb.p, (int64_t)rows.size(), N, d.T.c());
+      ADC_CHECK_LAUNCH();
+      na = d.orthonormalise((int)rows.size());
+    }
+    if (na == 0) {
+      if (phase == 2) break;
+      // no new direction at this precision: continue from an FP64 base, and
+      // in plain FP64 when that happens again
+      d.collapse(nroots, true);
+      phase = (phase == 0) ? 1 : 2;
+      best = 1e300;
+      since = 0;
+      continue;
+    }
     ADC_CUDA(cudaMemcpyAsync(d.V.c() + (int64_t)d.m * N, d.T.c(), (int64_t)na * N * sizeof(cplx),
                              cudaMemcpyDeviceToDevice, ex.stream));
     prec_new = (phase == 2) ? ADC_PREC_FP64 : ADC_PREC_BF16X3;
-    d.apply_sigma(d.V.c() + (int64_t)d.m * N, d.AV.c() + (int64_t)d.m * N, na, prec_new);
+    d.apply_sigma_new(na, prec_new);
     d.extend_projection(d.m, na);
     d.m += na;
   }

@@ -1,5 +1,7 @@
 // Diagnostics of the contraction kernels (see include/adc_gb300_diag.h).
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
@@ -32,11 +34,88 @@ __global__ void k_diff(const cplx *a, const cplx *b, int64_t n, double *out) {
   atomicAdd(out, d);
   atomicAdd(out + 1, r);
 }
+
+// three jobs of different shapes (ragged sizes, tile widths, one long narrow
+// job that takes the split-K path) in one grouped launch; every output is
+// checked against the FP64 GEMM, rel_err is the largest of the three
+int diag_grouped(int64_t M, int64_t N, int64_t K, uint64_t seed, int reps, double *rel_err, double *ms) {
+  Exec ex;
+  try {
+    ADC_CUDA(cudaStreamCreateWithFlags(&ex.stream, cudaStreamNonBlocking));
+    {
+      const int64_t Ms[3] = {M, M / 2 + 37, 129};
+      const int64_t Ns[3] = {N, std::max<int64_t>(1, N / 3), 3};
+      const int64_t Ks[3] = {K, K / 2 + 11, 2 * K + 5};
+      DBuf A[3], B[3], C[3], R[3];
+      TcMat Ta[3], Tb[3];
+      DBuf acc(ex, 2 * sizeof(double)), err(ex, sizeof(int));
+      fill_zero(ex, err.p, sizeof(int));
+      std::vector<TcJobDesc> jobs;
+      for (int j = 0; j < 3; ++j) {
+        A[j] = cbuf(ex, Ms[j] * Ks[j]);
+        B[j] = cbuf(ex, Ns[j] * Ks[j]);
+        C[j] = cbuf(ex, Ms[j] * Ns[j]);
+        R[j] = cbuf(ex, Ms[j] * Ns[j]);
+        k_fill_random<<<grid1d(Ms[j] * Ks[j], 256), 256, 0, ex.stream>>>(A[j].c(), Ms[j] * Ks[j], seed + 13 * j);
+        k_fill_random<<<grid1d(Ns[j] * Ks[j], 256), 256, 0, ex.stream>>>(B[j].c(), Ns[j] * Ks[j], seed + 13 * j + 7);
+        ADC_CHECK_LAUNCH();
+        zgemm(ex, Ms[j], Ns[j], Ks[j], 1, C1(), A[j].c(), 0, Ks[j], 1, false, B[j].c(), 0, 1, Ks[j], false, C0(),
+              R[j].c(), 0, Ns[j], 1);
+        tc_pack_A(ex, Ta[j], A[j].c(), Ms[j], Ks[j], Ks[j], 1, false);
+        tc_pack_B(ex, Tb[j], B[j].c(), Ns[j], Ks[j], Ks[j], 0, 1, 1, false);
+        TcJobDesc d;
+        d.A = &Ta[j]; d.B = &Tb[j]; d.M = Ms[j]; d.N = Ns[j]; d.out = C[j].c();
+        d.s_m = Ns[j]; d.s_nh = 1; d.n_in = 1;
+        jobs.push_back(d);
+      }
+      TcGroup grp;
+      tc_gemm_grouped(ex, jobs, grp, (int *)err.p, true);
+      cudaEvent_t e0, e1;
+      ADC_CUDA(cudaEventCreate(&e0));
+      ADC_CUDA(cudaEventCreate(&e1));
+      ADC_CUDA(cudaEventRecord(e0, ex.stream));
+      for (int r = 0; r < reps; ++r) {
+        ADC_CUDA(cudaStreamSynchronize(ex.stream));  // the pinned job table is rewritten by each call
+        tc_gemm_grouped(ex, jobs, grp, (int *)err.p, true);
+      }
+      ADC_CUDA(cudaEventRecord(e1, ex.stream));
+      ADC_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (ms) *ms = t / reps;
+      double worst = 0.0;
+      for (int j = 0; j < 3; ++j) {
+        fill_zero(ex, acc.p, acc.bytes);
+        k_diff<<<256, 256, 0, ex.stream>>>(C[j].c(), R[j].c(), Ms[j] * Ns[j], acc.d());
+        ADC_CHECK_LAUNCH();
+        double h[2];
+        ADC_CUDA(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, ex.stream));
+        ADC_CUDA(cudaStreamSynchronize(ex.stream));
+        worst = std::max(worst, std::sqrt(h[0] / std::max(h[1], 1e-300)));
+      }
+      int he = 0;
+      ADC_CUDA(cudaMemcpyAsync(&he, err.p, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));
+      ADC_CUDA(cudaStreamSynchronize(ex.stream));
+      if (rel_err) *rel_err = worst;
+      if (he) throw Error(ADC_ERR_TIMEOUT, "tensor-core GEMM wait gave up");
+    }
+    cudaStreamSynchronize(ex.stream);
+    cudaStreamDestroy(ex.stream);
+    return ADC_OK;
+  } catch (const Error &e) {
+    if (ex.stream) { cudaStreamSynchronize(ex.stream); cudaStreamDestroy(ex.stream); }
+    fprintf(stderr, "adc_diag_gemm: %s\n", e.what());
+    return e.code;
+  }
+}
 }  // namespace
 
 extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_t seed, int reps,
                              double *rel_err, double *ms) {
-  if (M <= 0 || N <= 0 || K <= 0 || reps < 1 || (which != 0 && which != 1)) return ADC_ERR_ARG;
+  if (M <= 0 || N <= 0 || K <= 0 || reps < 1 || which < 0 || which > 3) return ADC_ERR_ARG;
+  if (which == 3) return diag_grouped(M, N, K, seed, reps, rel_err, ms);
   Exec ex;
   try {
     ADC_CUDA(cudaStreamCreateWithFlags(&ex.stream, cudaStreamNonBlocking));
@@ -49,14 +128,19 @@ extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_
       ADC_CHECK_LAUNCH();
       zgemm(ex, M, N, K, 1, C1(), A.c(), 0, K, 1, false, B.c(), 0, 1, K, false, C0(), R.c(), 0, N, 1);
       TcMat Ta, Tb;
+      TcGroup grp;
       auto run = [&]() {
         if (which == 0) {
           zgemm(ex, M, N, K, 1, C1(), A.c(), 0, K, 1, false, B.c(), 0, 1, K, false, C0(), C.c(), 0, N, 1);
-        } else {
+        } else if (which == 1) {
           tc_gemm(ex, Ta, Tb, M, N, C1(), C0(), C.c(), N, 1, 0, 1, (int *)err.p);
+        } else {
+          TcJobDesc d;
+          d.A = &Ta; d.B = &Tb; d.M = M; d.N = N; d.out = C.c(); d.s_m = N; d.s_nh = 1; d.n_in = 1;
+          tc_gemm_grouped(ex, std::vector<TcJobDesc>{d}, grp, (int *)err.p, true);
         }
       };
-      if (which == 1) {
+      if (which >= 1) {
         tc_pack_A(ex, Ta, A.c(), M, K, K, 1, false);
         tc_pack_B(ex, Tb, B.c(), N, K, K, 0, 1, 1, false);
       }

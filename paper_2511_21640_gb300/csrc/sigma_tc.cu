@@ -25,10 +25,14 @@ static void build_cache(adc_ctx *c) {
 
 void release_tc(adc_ctx *c) { c->tc.reset(); }
 
-void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
-  Exec &ex = c->ex;
+void tc_ensure(adc_ctx *c) {
   if (!c->tc) c->tc.reset(new TcCache());
   if (!c->tc->ready) build_cache(c);
+}
+
+void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
+  Exec &ex = c->ex;
+  tc_ensure(c);
   auto &tc = *c->tc;
   int *err = (int *)tc.err.p;
   const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N;

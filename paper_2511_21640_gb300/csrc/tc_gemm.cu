@@ -431,6 +431,193 @@ void launch_tc(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N2, 
   ex.prof_end(pr);
 }
 
+// ---------------------------------------------------------------- grouped persistent GEMM
+// One launch for a list of independent GEMM jobs (several problems and terms).
+// Every CTA stays resident and takes the next output tile from a global
+// counter until none is left, so uneven jobs balance across the SMs. Tiles of a
+// job are numbered (row block, column block, K split) with the K split fastest,
+// so consecutive tiles reuse the same A rows from L2. Each job carries its own
+// tensor maps, tile width (32..256 columns, runtime) and K split; the shared
+// memory ring is sized for the widest tile. The accumulator is drained by the
+// epilogue warps before the next tile's first MMA (block barrier per tile).
+constexpr int TG_ST = 4;
+struct TgLayout {
+  static constexpr int A_BYTES = TC_BM * TC_BK * 2;
+  static constexpr int B_BYTES = TC_BNMAX * TC_BK * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int BAR_OFF = TG_ST * STAGE;
+  static constexpr int SMEM = 1024 + BAR_OFF + 256;
+};
+
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m) : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1)
+k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *counter, int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(smem + TgLayout::BAR_OFF);
+  uint64_t *empty = full + TG_ST;
+  uint64_t *accum = empty + TG_ST;
+  uint32_t *tmem_slot = (uint32_t *)(accum + 1);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+  volatile int *tile_slot = (volatile int *)(tmem_slot + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TG_ST; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(accum), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)TC_BNMAX)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  uint32_t g = 0;        // k-blocks that went through the stage ring so far
+  uint32_t acc_par = 0;  // phase of the accumulator barrier
+  for (;;) {
+    if (threadIdx.x == 0) *tile_slot = atomicAdd(counter, 1);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const int t = *tile_slot;
+    if (t >= total_tiles || *abort_flag) break;
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].tile_begin <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const TcJob &J = jobs[lo];
+    const int lt = t - J.tile_begin;
+    const int per_m = J.tiles_n * J.ksplit;
+    const int tm = lt / per_m, rem = lt - tm * per_m;
+    const int tn = rem / J.ksplit, split = rem - tn * J.ksplit;
+    const int bn = J.bn;
+    const int m0 = tm * TC_BM, n0 = tn * bn;
+    const int total_kb = 3 * J.kps;
+    const int kb_beg = split * J.kb_per_split;
+    const int kb_end = min(total_kb, kb_beg + J.kb_per_split);
+    const int nkb = kb_end - kb_beg;
+
+    if (warp == 0 && lane == 0) {
+      // ---------------- producer
+      tensormap_acquire(&J.mAh);
+      tensormap_acquire(&J.mAl);
+      tensormap_acquire(&J.mBh);
+      tensormap_acquire(&J.mBl);
+      const uint32_t bytes = (uint32_t)(TgLayout::A_BYTES + bn * TC_BK * 2);
+      int issued = 0;
+      for (int i = 0; i < nkb; ++i) {
+        const uint32_t gi = g + (uint32_t)i;
+        const int s = (int)(gi % TG_ST);
+        const uint32_t r = gi / TG_ST;
+        if (r > 0 && !mbar_wait(smem_u32(&empty[s]), (r - 1) & 1, abort_flag)) {
+          if (!*abort_flag) atomicExch(err, 11);
+          *abort_flag = 1;
+          break;
+        }
+        const int kg = kb_beg + i;
+        const int seg = kg / J.kps;
+        const int kx = (kg - seg * J.kps) * TC_BK;
+        const uint32_t fb = smem_u32(&full[s]);
+        mbar_expect_tx(fb, bytes);
+        uint8_t *sa = smem + s * TgLayout::STAGE;
+        tma_load_2d(smem_u32(sa), seg == 2 ? &J.mAl : &J.mAh, kx, m0, fb);
+        tma_load_2d(smem_u32(sa + TgLayout::A_BYTES), seg == 1 ? &J.mBl : &J.mBh, kx, n0, fb);
+        issued = i + 1;
+      }
+      if (*abort_flag) {
+        // drain this CTA's copies in flight before shared memory is released
+        for (int j = (issued > TG_ST ? issued - TG_ST : 0); j < issued; ++j) {
+          const uint32_t gj = g + (uint32_t)j;
+          const int s = (int)(gj % TG_ST);
+          uint64_t t0 = gtimer();
+          while (!mbar_try(smem_u32(&full[s]), (gj / TG_ST) & 1) && gtimer() - t0 < WAIT_NS) {
+          }
+        }
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t idesc = idesc_bf16(TC_BM, bn);
+      for (int i = 0; i < nkb; ++i) {
+        const uint32_t gi = g + (uint32_t)i;
+        const int s = (int)(gi % TG_ST);
+        if (!mbar_wait(smem_u32(&full[s]), (gi / TG_ST) & 1, abort_flag)) {
+          if (!*abort_flag) atomicExch(err, 12);
+          *abort_flag = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t a0 = smem_u32(smem + s * TgLayout::STAGE);
+        const uint32_t b0 = a0 + TgLayout::A_BYTES;
+#pragma unroll
+        for (int k = 0; k < TC_BK / 16; ++k)
+          mma_bf16(tmem, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, (i > 0 || k > 0) ? 1u : 0u);
+        mma_commit(smem_u32(&empty[s]));
+      }
+      mma_commit(smem_u32(accum));
+    } else if (warp >= 2) {
+      // ---------------- epilogue
+      bool ok = mbar_wait(smem_u32(accum), acc_par, abort_flag);
+      if (!ok && !*abort_flag) { atomicExch(err, 13); *abort_flag = 1; }
+      fence_after();
+      __syncwarp();
+      const int q = warp & 3;
+      const int row = q * 32 + lane;
+      const int64_t m = (int64_t)m0 + row;
+      const bool use_beta = (J.beta.x != 0.0 || J.beta.y != 0.0);
+#pragma unroll 1
+      for (int cch = 0; cch < bn / 32; ++cch) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cch * 32), v);
+        if (!ok || *abort_flag || m >= J.M || nkb <= 0) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int64_t n2 = (int64_t)n0 + cch * 32 + 2 * j;
+          if (n2 >= J.N2) break;
+          const float re = __uint_as_float(v[2 * j]), im = __uint_as_float(v[2 * j + 1]);
+          if (J.part) {
+            float *pp = J.part + ((int64_t)split * J.M + m) * J.N2 + n2;
+            pp[0] = re;
+            pp[1] = im;
+          } else {
+            const int64_t n = n2 >> 1;
+            const int64_t nh = n / J.n_in, nl = n - nh * J.n_in;
+            cplx *dst = J.out + m * J.s_m + nh * J.s_nh + nl * J.s_nl;
+            cplx val = cmul(J.alpha, cmake((double)re, (double)im));
+            if (use_beta) val = cadd(val, cmul(J.beta, *dst));
+            *dst = val;
+          }
+        }
+      }
+    }
+    g += (uint32_t)max(nkb, 0);
+    acc_par ^= 1u;
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TC_BNMAX)
+                 : "memory");
+  }
+}
+
 }  // namespace
 
 void tc_pack_A(Exec &ex, TcMat &dst, const cplx *src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, bool conj) {
@@ -489,6 +676,252 @@ void tc_gemm(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N, cpl
   else if (N2 <= 64) launch_tc<64, 8>(ex, A, B, M, N2, alpha, beta, out, s_m, s_nh, s_nl, n_in, err);
   else if (N2 <= 128) launch_tc<128, 6>(ex, A, B, M, N2, alpha, beta, out, s_m, s_nh, s_nl, n_in, err);
   else launch_tc<256, 4>(ex, A, B, M, N2, alpha, beta, out, s_m, s_nh, s_nl, n_in, err);
+}
+
+}  // namespace adc
+
+// ---------------------------------------------------------------- grouped launch, host side
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+namespace adc {
+
+namespace {
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+// smallest tile width (multiple of 32, at most 256) covering N2 real columns
+// when it is narrow, else the widest tile
+int bn_rule(int64_t N2) {
+  if (N2 <= 32) return 32;
+  if (N2 <= 64) return 64;
+  if (N2 <= 128) return 128;
+  return 256;
+}
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int64_t, int64_t, int64_t>, int> g_tuned;
+
+}  // namespace
+
+TcGroup::~TcGroup() {
+  if (ev) {
+    cudaEventSynchronize(ev);
+    cudaEventDestroy(ev);
+  }
+  if (host) cudaFreeHost(host);
+}
+
+static int cached_bn(const TcJobDesc &d) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(std::make_tuple(d.M, 2 * d.N, d.A->kp));
+  return it == g_tuned.end() ? 0 : it->second;
+}
+
+void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &in, TcGroup &grp, int *err, bool may_tune) {
+  const int nj = (int)in.size();
+  if (nj == 0) return;
+  static bool attr = false;
+  if (!attr) {
+    ADC_CUDA(cudaFuncSetAttribute(k_tc_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, TgLayout::SMEM));
+    attr = true;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ADC_CUDA(cudaStreamIsCapturing(ex.stream, &cs));
+  const bool capturing = (cs != cudaStreamCaptureStatusNone);
+  if (capturing) may_tune = false;
+  struct Plan {
+    int idx, bn, kps, tiles_m, tiles_n, ksplit, kbps;
+    int64_t N2;
+  };
+  std::vector<Plan> pl;
+  double work = 0.0;
+  grp.flops = 0.0;
+  for (int j = 0; j < nj; ++j) {
+    const TcJobDesc &d = in[j];
+    ADC_REQUIRE(d.A && d.B && d.out, ADC_ERR_ARG, "tc_gemm_grouped: job operands");
+    ADC_REQUIRE(d.A->kp == d.B->kp, ADC_ERR_ARG, "tc_gemm_grouped: inner sizes differ");
+    ADC_REQUIRE(d.A->rows >= d.M && d.B->rows >= 2 * d.N, ADC_ERR_ARG, "tc_gemm_grouped: operand rows");
+    ADC_REQUIRE(d.M < (1ll << 31) && 2 * d.N < (1ll << 31), ADC_ERR_UNSUPPORTED, "tc_gemm_grouped: size");
+    if (d.M <= 0 || d.N <= 0) continue;
+    Plan p{};
+    p.idx = j;
+    p.N2 = 2 * d.N;
+    p.bn = d.bn;
+    if (p.bn <= 0) p.bn = may_tune ? tc_autotune_bn(ex, d, err) : cached_bn(d);
+    if (p.bn <= 0) p.bn = bn_rule(p.N2);
+    ADC_REQUIRE(p.bn >= 32 && p.bn <= TC_BNMAX && p.bn % 32 == 0, ADC_ERR_ARG, "tc_gemm_grouped: tile width");
+    p.kps = (int)(2 * d.A->kp / TC_BK);
+    p.tiles_m = (int)((d.M + TC_BM - 1) / TC_BM);
+    p.tiles_n = (int)((p.N2 + p.bn - 1) / p.bn);
+    work += (double)p.tiles_m * p.tiles_n * 3.0 * p.kps;
+    const int64_t Kc = d.A->kreal > 0 ? d.A->kreal : d.A->kp;
+    grp.flops += 8.0 * (double)d.M * (double)d.N * (double)Kc;
+    pl.push_back(p);
+  }
+  if (pl.empty()) return;
+  // split K of long, narrow jobs so that no tile is much longer than the
+  // average per-SM share of four waves
+  const int sms = sm_count();
+  const double target = std::max(16.0, work / (4.0 * sms));
+  size_t part_need = 0;
+  for (auto &p : pl) {
+    const int total_kb = 3 * p.kps;
+    int ks = 1;
+    if (total_kb > target) ks = (int)std::min<double>(128.0, std::ceil(total_kb / target));
+    p.kbps = (total_kb + ks - 1) / ks;
+    p.ksplit = (total_kb + p.kbps - 1) / p.kbps;
+    if (p.ksplit > 1) part_need += (size_t)p.ksplit * in[p.idx].M * p.N2;
+  }
+  // longest tiles first (largest k-blocks per tile), whole jobs kept together
+  std::stable_sort(pl.begin(), pl.end(), [](const Plan &a, const Plan &b) { return a.kbps > b.kbps; });
+  if (grp.part_elems < part_need) {
+    grp.part.reset();
+    grp.part = DBuf(ex, part_need * sizeof(float));
+    grp.part_elems = part_need;
+  }
+  const int np = (int)pl.size();
+  // the previous copy out of the pinned table must have finished before it is rewritten
+  if (grp.ev && !capturing) ADC_CUDA(cudaEventSynchronize(grp.ev));
+  if (grp.host_cap < (size_t)np) {
+    if (grp.host) cudaFreeHost(grp.host);
+    grp.host = nullptr;
+    ADC_CUDA(cudaMallocHost((void **)&grp.host, (size_t)np * sizeof(TcJob)));
+    grp.host_cap = np;
+    grp.jobs.reset();
+    grp.jobs = DBuf(ex, (size_t)np * sizeof(TcJob));
+  }
+  if (!grp.counter.p) grp.counter = DBuf(ex, 256);
+  int64_t tiles = 0;
+  size_t poff = 0;
+  for (int i = 0; i < np; ++i) {
+    const Plan &p = pl[i];
+    const TcJobDesc &d = in[p.idx];
+    TcJob &J = grp.host[i];
+    std::memset(&J, 0, sizeof(J));
+    const int64_t kp2 = 2 * d.A->kp;
+    make_map(&J.mAh, d.A->hi.p, d.A->rows, kp2, TC_BM);
+    make_map(&J.mAl, d.A->lo.p, d.A->rows, kp2, TC_BM);
+    make_map(&J.mBh, d.B->hi.p, d.B->rows, kp2, p.bn);
+    make_map(&J.mBl, d.B->lo.p, d.B->rows, kp2, p.bn);
+    J.out = d.out;
+    J.part = p.ksplit > 1 ? (float *)grp.part.p + poff : nullptr;
+    if (p.ksplit > 1) poff += (size_t)p.ksplit * d.M * p.N2;
+    J.s_m = d.s_m;
+    J.s_nh = d.s_nh;
+    J.s_nl = d.s_nl;
+    J.n_in = d.n_in > 0 ? d.n_in : 1;
+    J.alpha = d.alpha;
+    J.beta = d.beta;
+    J.M = (int)d.M;
+    J.N2 = (int)p.N2;
+    J.kps = p.kps;
+    J.bn = p.bn;
+    J.tiles_n = p.tiles_n;
+    J.tiles_m = p.tiles_m;
+    J.ksplit = p.ksplit;
+    J.kb_per_split = p.kbps;
+    J.tile_begin = (int)tiles;
+    tiles += (int64_t)p.tiles_m * p.tiles_n * p.ksplit;
+  }
+  ADC_REQUIRE(tiles < (1ll << 31), ADC_ERR_UNSUPPORTED, "tc_gemm_grouped: too many tiles");
+  ADC_CUDA(cudaMemcpyAsync(grp.jobs.p, grp.host, (size_t)np * sizeof(TcJob), cudaMemcpyHostToDevice, ex.stream));
+  if (!capturing) {
+    if (!grp.ev) ADC_CUDA(cudaEventCreateWithFlags(&grp.ev, cudaEventDisableTiming));
+    ADC_CUDA(cudaEventRecord(grp.ev, ex.stream));
+  }
+  ADC_CUDA(cudaMemsetAsync(grp.counter.p, 0, sizeof(int), ex.stream));
+  const int grid = (int)std::min<int64_t>(tiles, sms);
+  int pr = ex.prof_begin("tc_grouped_bf16x3", grp.flops);
+  k_tc_grouped<<<grid, 192, TgLayout::SMEM, ex.stream>>>((const TcJob *)grp.jobs.p, np, (int)tiles,
+                                                         (int *)grp.counter.p, err);
+  ADC_CHECK_LAUNCH();
+  for (int i = 0; i < np; ++i) {
+    const TcJob &J = grp.host[i];
+    if (J.ksplit <= 1) continue;
+    k_tc_reduce<<<grid1d((int64_t)J.M * (J.N2 / 2), 256), 256, 0, ex.stream>>>(
+        J.part, J.ksplit, J.M, J.N2, J.out, J.s_m, J.s_nh, J.s_nl, J.n_in, J.alpha, J.beta);
+    ADC_CHECK_LAUNCH();
+  }
+  ex.prof_end(pr);
+}
+
+int tc_autotune_bn(Exec &ex, const TcJobDesc &d, int *err) {
+  const int64_t N2 = 2 * d.N;
+  const auto key = std::make_tuple(d.M, N2, d.A->kp);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+  }
+  std::vector<int> cand;
+  for (int bn = 32; bn <= TC_BNMAX; bn *= 2) {
+    cand.push_back(bn);
+    if (bn >= N2) break;
+  }
+  int best = bn_rule(N2);
+  if (cand.size() > 1) {
+    // time each candidate as a lone job writing a scratch output (beta = 0)
+    DBuf scratch = cbuf(ex, d.M * d.N);
+    TcGroup g;
+    cudaEvent_t e0, e1;
+    ADC_CUDA(cudaEventCreate(&e0));
+    ADC_CUDA(cudaEventCreate(&e1));
+    double tbest = 1e300;
+    for (int bn : cand) {
+      TcJobDesc t = d;
+      t.bn = bn;
+      t.out = scratch.c();
+      t.s_m = d.N;
+      t.s_nh = 1;
+      t.s_nl = 0;
+      t.n_in = 1;
+      t.alpha = C1();
+      t.beta = C0();
+      std::vector<TcJobDesc> one{t};
+      tc_gemm_grouped(ex, one, g, err, false);
+      ADC_CUDA(cudaEventRecord(e0, ex.stream));
+      for (int r = 0; r < 2; ++r) tc_gemm_grouped(ex, one, g, err, false);
+      ADC_CUDA(cudaEventRecord(e1, ex.stream));
+      ADC_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      ADC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < tbest) { tbest = ms; best = bn; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = best;
+  return best;
+}
+
+int tc_autotune_table(int64_t *out, int cap) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  int n = 0;
+  for (auto &kv : g_tuned) {
+    if (out && n < cap) {
+      out[4 * n + 0] = std::get<0>(kv.first);
+      out[4 * n + 1] = std::get<1>(kv.first);
+      out[4 * n + 2] = std::get<2>(kv.first);
+      out[4 * n + 3] = kv.second;
+    }
+    ++n;
+  }
+  return n;
 }
 
 }  // namespace adc

@@ -1,5 +1,9 @@
 // Split-precision (BF16x3) complex GEMM on tcgen05; see tc_gemm.cu.
 #pragma once
+#include <cuda.h>
+
+#include <vector>
+
 #include "tensor.cuh"
 
 struct adc_ctx;
@@ -23,6 +27,55 @@ void tc_pack_B_ring(Exec &ex, TcMat &dst, const adc_ctx *c, const cplx *X, int64
 // out[m][n] (n = nh*n_in + nl at m*s_m + nh*s_nh + nl*s_nl) = alpha * A B^T + beta * out
 void tc_gemm(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N, cplx alpha, cplx beta, cplx *out,
              int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err);
+
+// ---- grouped persistent launch (several problems and terms in one kernel)
+constexpr int TC_BNMAX = 256;
+
+// one job as the kernel reads it (device memory, 128-byte aligned tensor maps)
+struct alignas(128) TcJob {
+  CUtensorMap mAh, mAl, mBh, mBl;
+  cplx *out;
+  float *part;  // split-K partials [ksplit][M][N2] or null
+  int64_t s_m, s_nh, s_nl, n_in;
+  cplx alpha, beta;
+  int M, N2, kps, bn, tiles_n, tiles_m, ksplit, kb_per_split, tile_begin, pad_[3];
+};
+
+// one job as the host describes it: out = alpha * A B^T + beta * out, same
+// output addressing as tc_gemm; bn = tile width in real columns (0: autotuned)
+struct TcJobDesc {
+  const TcMat *A = nullptr, *B = nullptr;
+  int64_t M = 0, N = 0;
+  cplx alpha{1.0, 0.0}, beta{0.0, 0.0};
+  cplx *out = nullptr;
+  int64_t s_m = 0, s_nh = 0, s_nl = 0, n_in = 1;
+  int bn = 0;
+};
+
+// device and pinned host state of a grouped launch. A captured graph copies
+// the job table out of `host` at every replay, so a TcGroup captured into a
+// graph belongs to that graph and is not reused for other launches.
+struct TcGroup {
+  DBuf jobs, counter, part;
+  cudaEvent_t ev = nullptr;  // completion of the last copy out of `host`
+  TcJob *host = nullptr;
+  size_t host_cap = 0;
+  size_t part_elems = 0;
+  double flops = 0.0;  // algorithmic flops of the jobs (8 per complex MAC)
+  TcGroup() = default;
+  TcGroup(const TcGroup &) = delete;
+  TcGroup &operator=(const TcGroup &) = delete;
+  ~TcGroup();
+};
+
+// enqueue all jobs as one persistent launch (plus split-K reductions). With
+// may_tune, jobs with bn == 0 get the autotuned tile width (timing runs need a
+// stream that is not being captured); otherwise a size rule picks it.
+void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &jobs, TcGroup &grp, int *err, bool may_tune);
+// tile width chosen by timing every candidate once per (M, N, K) shape; cached
+int tc_autotune_bn(Exec &ex, const TcJobDesc &d, int *err);
+// table of tuned shapes: (M, N2, kp, bn); returns the number of entries
+int tc_autotune_table(int64_t *out, int cap);
 
 struct TcCache {
   TcMat Glad, W, Cpl, CplT;  // static operators (A side)

@@ -80,6 +80,7 @@ void fill_zero(Exec &ex, void *p, size_t bytes) {
 // operand index has unit stride.
 namespace {
 constexpr int BM = 64, BN = 64, BKK = 16;
+constexpr int ZG_SMEM = (2 * BKK * (BM + 1) + 2 * BKK * (BN + 1) + BKK * (BM + 1) + BKK * (BN + 1)) * 8;
 
 __global__ void __launch_bounds__(256)
 k_zgemm(int64_t M, int64_t N, int64_t K, const cplx *__restrict__ A, int64_t sAb, int64_t sAm,
@@ -87,8 +88,14 @@ k_zgemm(int64_t M, int64_t N, int64_t K, const cplx *__restrict__ A, int64_t sAb
         int64_t sBk, int64_t sBn, int conjB, int b_nfast, cplx *C, int64_t sCb, int64_t sCm,
         int64_t sCn, cplx alpha, cplx beta, int64_t batch0, int ksplit, int64_t kchunk,
         cplx *part, int64_t nbatch) {
-  __shared__ cplx As[BKK][BM + 1];
-  __shared__ cplx Bs[BKK][BN + 1];
+  // 3M products: (ar + i ai)(br + i bi) = T1 - T2 + i (T3 - T1 - T2) with
+  // T1 = ar br, T2 = ai bi, T3 = (ar + ai)(br + bi): three FP64 FMAs per
+  // complex MAC instead of four. The sums are formed once per staged element.
+  extern __shared__ double zsm[];
+  cplx(*As)[BM + 1] = reinterpret_cast<cplx(*)[BM + 1]>(zsm);
+  cplx(*Bs)[BN + 1] = reinterpret_cast<cplx(*)[BN + 1]>(zsm + 2 * BKK * (BM + 1));
+  double(*Ass)[BM + 1] = reinterpret_cast<double(*)[BM + 1]>(zsm + 2 * BKK * (BM + 1) + 2 * BKK * (BN + 1));
+  double(*Bss)[BN + 1] = reinterpret_cast<double(*)[BN + 1]>(zsm + 3 * BKK * (BM + 1) + 2 * BKK * (BN + 1));
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t zl = blockIdx.z;
@@ -100,11 +107,11 @@ k_zgemm(int64_t M, int64_t N, int64_t K, const cplx *__restrict__ A, int64_t sAb
   const int64_t kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
   const cplx *Ab = A + b * sAb;
   const cplx *Bb = B + b * sBb;
-  cplx acc[4][4];
+  double t1[4][4], t2[4][4], t3[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = cmake(0.0, 0.0);
+    for (int j = 0; j < 4; ++j) t1[i][j] = t2[i][j] = t3[i][j] = 0.0;
   const double sa = conjA ? -1.0 : 1.0, sb = conjB ? -1.0 : 1.0;
   for (int64_t k0 = kbeg; k0 < kend; k0 += BKK) {
 #pragma unroll
@@ -116,6 +123,7 @@ k_zgemm(int64_t M, int64_t N, int64_t K, const cplx *__restrict__ A, int64_t sAb
       cplx val = cmake(0.0, 0.0);
       if (gm < M && gk < kend) { val = Ab[gm * sAm + gk * sAk]; val.y *= sa; }
       As[kk][mm] = val;
+      Ass[kk][mm] = val.x + val.y;
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -126,22 +134,33 @@ k_zgemm(int64_t M, int64_t N, int64_t K, const cplx *__restrict__ A, int64_t sAb
       cplx val = cmake(0.0, 0.0);
       if (gn < N && gk < kend) { val = Bb[gk * sBk + gn * sBn]; val.y *= sb; }
       Bs[kk][nn] = val;
+      Bss[kk][nn] = val.x + val.y;
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < BKK; ++kk) {
       cplx a[4], bv[4];
+      double as[4], bs[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty + 16 * i]; as[i] = Ass[kk][ty + 16 * i]; }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < 4; ++j) { bv[j] = Bs[kk][tx + 16 * j]; bs[j] = Bss[kk][tx + 16 * j]; }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], bv[j]);
+        for (int j = 0; j < 4; ++j) {
+          t1[i][j] = fma(a[i].x, bv[j].x, t1[i][j]);
+          t2[i][j] = fma(a[i].y, bv[j].y, t2[i][j]);
+          t3[i][j] = fma(as[i], bs[j], t3[i][j]);
+        }
     }
     __syncthreads();
   }
+  cplx acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = cmake(t1[i][j] - t2[i][j], t3[i][j] - t1[i][j] - t2[i][j]);
   if (part) {
     // split-K partial tile, unscaled: part[split][bl][m][n]
     cplx *P = part + ((int64_t)split * nbatch + bl) * M * N;
@@ -194,6 +213,13 @@ __global__ void k_splitk_reduce(const cplx *__restrict__ part, int ksplit, int64
 }  // namespace
 
 static int g_num_sms = 0;
+static void zgemm_attr() {
+  static bool done = false;
+  if (!done) {
+    ADC_CUDA(cudaFuncSetAttribute(k_zgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, ZG_SMEM));
+    done = true;
+  }
+}
 static int num_sms() {
   if (!g_num_sms) {
     int dev = 0;
@@ -210,6 +236,7 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
            int64_t sCn) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K < 0) K = 0;  // the kernel then writes beta * C
+  zgemm_attr();
   ADC_REQUIRE((M + BM - 1) / BM <= 65535, ADC_ERR_UNSUPPORTED, "zgemm: M too large");
   int a_kfast = (sAk == 1) ? 1 : 0;
   int b_nfast = (sBn == 1) ? 1 : 0;
@@ -230,7 +257,7 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
     int64_t nb = std::min<int64_t>(bmax, batch - b0);
     dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)(nb * ksplit));
     if (ksplit == 1) {
-      k_zgemm<<<grid, block, 0, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B,
+      k_zgemm<<<grid, block, ZG_SMEM, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B,
                                              sBb, sBk, sBn, conjB ? 1 : 0, b_nfast, C, sCb, sCm,
                                              sCn, alpha, beta, b0, 1, K, nullptr, nb);
       ADC_CHECK_LAUNCH();
@@ -238,7 +265,7 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
       int64_t kchunk = (K + ksplit - 1) / ksplit;
       kchunk = (kchunk + BKK - 1) / BKK * BKK;
       DBuf part = cbuf(ex, (int64_t)ksplit * nb * M * N);
-      k_zgemm<<<grid, block, 0, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B,
+      k_zgemm<<<grid, block, ZG_SMEM, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B,
                                              sBb, sBk, sBn, conjB ? 1 : 0, b_nfast, C, sCb, sCm,
                                              sCn, alpha, beta, b0, ksplit, kchunk, part.c(), nb);
       ADC_CHECK_LAUNCH();
@@ -256,6 +283,7 @@ void zgemm_ws(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alp
               int64_t ws_elems) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K < 0) K = 0;
+  zgemm_attr();
   ADC_REQUIRE((M + BM - 1) / BM <= 65535, ADC_ERR_UNSUPPORTED, "zgemm: M too large");
   int a_kfast = (sAk == 1) ? 1 : 0;
   int b_nfast = (sBn == 1) ? 1 : 0;
@@ -278,14 +306,14 @@ void zgemm_ws(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alp
     if (!ws) ks = 1;
     dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)(nb * ks));
     if (ks == 1) {
-      k_zgemm<<<grid, block, 0, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B, sBb, sBk, sBn,
+      k_zgemm<<<grid, block, ZG_SMEM, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B, sBb, sBk, sBn,
                                              conjB ? 1 : 0, b_nfast, C, sCb, sCm, sCn, alpha, beta, b0, 1, K,
                                              nullptr, nb);
       ADC_CHECK_LAUNCH();
     } else {
       int64_t kchunk = (K + ks - 1) / ks;
       kchunk = (kchunk + BKK - 1) / BKK * BKK;
-      k_zgemm<<<grid, block, 0, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B, sBb, sBk, sBn,
+      k_zgemm<<<grid, block, ZG_SMEM, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B, sBb, sBk, sBn,
                                              conjB ? 1 : 0, b_nfast, C, sCb, sCm, sCn, alpha, beta, b0, ks, kchunk,
                                              ws, nb);
       ADC_CHECK_LAUNCH();

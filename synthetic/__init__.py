@@ -24,7 +24,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["Problem", "make_problem", "random_vectors", "CONFIGS", "config_problem"]
+__all__ = ["Problem", "make_problem", "random_vectors", "CONFIGS", "config_problem", "batch_sizes",
+           "batch_problems", "BATCH_CONFIGS"]
 
 
 class Problem:
@@ -105,3 +106,36 @@ def config_problem(name):
     c.pop("nroots")
     c.pop("tol")
     return make_problem(name=name, **c)
+
+
+# Batched IP/EA workload: problem p draws nocc uniform in [10, 40] and nvir
+# uniform in [50, 250] (integers, both ends included) from default_rng(p), takes
+# naux = 6 nvir, is IP for even p and EA for odd p, ADC(2)+x(3) with x = 0.5,
+# and its inputs come from make_problem(..., seed=p) with the wide energy ranges.
+BATCH_CONFIGS = {
+    "batch64_ipea": dict(n=64, occ=(10, 40), vir=(50, 250), aux_per_vir=6, order=3, x=0.5, nroots=6, tol=1e-5,
+                         occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0)),
+}
+
+
+def batch_sizes(name="batch64_ipea", n=None):
+    """Sizes of the batched workload without the arrays: list of dicts."""
+    c = BATCH_CONFIGS[name]
+    out = []
+    for p in range(c["n"] if n is None else n):
+        rng = np.random.default_rng(p)
+        o = int(rng.integers(c["occ"][0], c["occ"][1] + 1))
+        v = int(rng.integers(c["vir"][0], c["vir"][1] + 1))
+        out.append(dict(kind="IP" if p % 2 == 0 else "EA", nocc=o, nvir=v, naux=c["aux_per_vir"] * v,
+                        order=c["order"], x=c["x"], seed=p))
+    return out
+
+
+def batch_problems(name="batch64_ipea", n=None, select=None):
+    """The problems of the batched workload (host arrays), optionally a subset of indices."""
+    c = BATCH_CONFIGS[name]
+    sizes = batch_sizes(name, n)
+    idx = range(len(sizes)) if select is None else select
+    return [make_problem(sizes[i]["nocc"], sizes[i]["nvir"], sizes[i]["naux"], seed=sizes[i]["seed"],
+                         occ_range=c["occ_range"], vir_range=c["vir_range"], kind=sizes[i]["kind"],
+                         order=c["order"], x=c["x"], name=f"{name}[{i}]") for i in idx]

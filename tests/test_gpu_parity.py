@@ -50,6 +50,21 @@ def test_bf16x3_gemm(gpu, M, N, K):
     assert err < 5e-5, err
 
 
+@pytest.mark.parametrize("M,N,K", [(128, 16, 64), (200, 40, 1000), (129, 130, 70), (1000, 300, 5000),
+                                   (64, 8, 20000), (300, 1, 129)])
+def test_grouped_gemm_one_job(gpu, M, N, K):
+    """The grouped persistent launch with an autotuned tile width, one job."""
+    err, ms = gpu.diag_gemm(2, M, N, K, seed=5)
+    assert err < 5e-5, err
+
+
+@pytest.mark.parametrize("M,N,K", [(1000, 300, 5000), (129, 130, 70), (4000, 64, 3000)])
+def test_grouped_gemm_three_jobs(gpu, M, N, K):
+    """Three jobs of different shapes in one launch, one of them split along K."""
+    err, ms = gpu.diag_gemm(3, M, N, K, seed=9)
+    assert err < 5e-5, err
+
+
 # ---------------------------------------------------------------- sigma parity
 CASES = [
     ("IP", 5, 37, 40, 3, 0.5, 11),
@@ -116,6 +131,18 @@ def test_ip_adc3_small_workload_davidson(gpu):
         om2, _, e2, st2, rc2 = ctx.davidson(4, tol=1e-8, precision="bf16x3", want_vectors=False)
         assert rc2 == 0 and np.abs(om2 - w).max() < 1e-8
         assert st2["sigma_calls_fp64"] > 0
+
+
+def test_mixed_davidson_preconditioned_corrections_in_subspace(gpu):
+    """IP-ADC(2) case whose preconditioned corrections fall into the subspace
+    in the split-precision phase; the solver must still reach the FP64 tolerance."""
+    p = make_problem(5, 14, 28, seed=54, sigma=0.06, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    M = oadc.explicit_matrix("IP", 2, 0.0, p.B, p.eps_occ, p.eps_vir)
+    w = np.linalg.eigvalsh(M)[:3]
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP", order=2, x=0.0) as ctx:
+        om, _, e64, st, rc = ctx.davidson(3, tol=1e-7, precision="bf16x3", want_vectors=False)
+        assert rc == 0 and np.all(e64 <= 1e-7)
+        assert np.abs(om - w).max() < 1e-8
 
 
 @pytest.mark.parametrize("kind,o,v,Q,x", [("EA", 6, 30, 64, 0.5), ("IP", 7, 26, 50, 0.5)])
