@@ -16,6 +16,11 @@ Modules
 ``davidson``    dense eigensolver and a plain Davidson for the lowest roots.
 ``fns``         frozen-natural-spinor density, truncation, semicanonicalisation
                 and transformation of the Cholesky vectors (Eqs. 25-30).
+``adc_ee``      closed-form EE-ADC blocks from Wick's theorem (term tables).
+``rows``        single satellite rows of the IP/EA sigma at full size.
+``gradients``   Hellmann-Feynman derivatives of the roots (Eq. 10) along a
+                direction of (B, eps, x), from central differences of the
+                explicit matrix.
 
 Every function is written for clarity, in FP64 complex, with no blocking or
 fusion beyond what the cited definition states.

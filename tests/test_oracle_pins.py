@@ -295,3 +295,63 @@ def test_p6a_ee_unitary_invariance_within_degenerate_groups():
     w0 = np.linalg.eigvalsh(adc_ee.explicit_matrix(3, 0.5, p.B, eo, ev))
     w1 = np.linalg.eigvalsh(adc_ee.explicit_matrix(3, 0.5, Br, eo, ev))
     assert np.abs(w0 - w1).max() < 1e-12
+
+
+# ---------------------------------------------------------------- P9: eigenvalue derivatives
+from oracle import gradients as ograd  # noqa: E402
+
+
+def _dir(p, seed, dx=0.0):
+    rng = np.random.default_rng(seed)
+    dB = ograd.random_hermitian_direction(p.B.shape, seed)
+    return (dB, rng.standard_normal(p.nocc) * 0.1, rng.standard_normal(p.nvir) * 0.1, dx)
+
+
+@pytest.mark.parametrize("kind,order,x", [("EE", 3, 0.4), ("EE", 2, 0.0), ("IP", 3, 0.5), ("EA", 3, 1.0)])
+def test_p9_hellmann_feynman_equals_eigenvalue_differences(kind, order, x):
+    """y^H dM y (central differences of M, h = 1e-5) against central
+    differences of the eigenvalues themselves (h = 1e-4): two routes to the
+    derivative of a non-degenerate root."""
+    o, v = (2, 4) if kind == "EE" else (3, 5)
+    p = make_problem(o, v, 6, seed=71, sigma=0.15, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    D = _dir(p, 5, dx=0.7)
+    dw, w, Y = ograd.hf_directional(kind, order, x, p.B, p.eps_occ, p.eps_vir, 3, D)
+    assert np.min(np.diff(np.linalg.eigvalsh(ograd.matrix(kind, order, x, p.B, p.eps_occ, p.eps_vir)))[:3]) > 1e-3
+    fd = ograd.eig_fd_directional(kind, order, x, p.B, p.eps_occ, p.eps_vir, 3, D)
+    assert np.abs(dw - fd).max() < 1e-6 * max(1.0, np.abs(fd).max())
+
+
+@pytest.mark.parametrize("kind", ["EE", "EA"])
+def test_p9_x_derivative_is_the_adc3_increment(kind):
+    """M is linear in x: d omega/dx = y^H (M(x=1) - M(x=0)) y exactly."""
+    o, v = (2, 4) if kind == "EE" else (3, 5)
+    p = make_problem(o, v, 6, seed=72, sigma=0.15, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    dw, w, Y = ograd.hf_directional(kind, 3, 0.4, p.B, p.eps_occ, p.eps_vir, 2, (None, None, None, 1.0))
+    dM = ograd.matrix(kind, 3, 1.0, p.B, p.eps_occ, p.eps_vir) - ograd.matrix(kind, 3, 0.0, p.B, p.eps_occ,
+                                                                               p.eps_vir)
+    ref = np.real(np.einsum("rp,pq,rq->r", Y.conj(), dM, Y))
+    assert np.abs(dw - ref).max() < 1e-9 * max(1.0, np.abs(ref).max())
+
+
+def test_p9_noninteracting_orbital_energy_derivatives():
+    """B = 0: the lowest EE root is eps_v[0] - eps_o[-1] and the lowest IP root
+    is -eps_o[-1], so their derivatives along (deo, dev) are closed forms."""
+    p = make_problem(3, 4, 5, seed=73, sigma=0.1, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    B0 = np.zeros_like(p.B)
+    rng = np.random.default_rng(3)
+    deo, dev = rng.standard_normal(3), rng.standard_normal(4)
+    dw, _, _ = ograd.hf_directional("EE", 3, 1.0, B0, p.eps_occ, p.eps_vir, 1, (None, deo, dev, 0.0))
+    assert abs(dw[0] - (dev[0] - deo[-1])) < 1e-9
+    dw, _, _ = ograd.hf_directional("IP", 3, 1.0, B0, p.eps_occ, p.eps_vir, 1, (None, deo, dev, 0.0))
+    assert abs(dw[0] - (-deo[-1])) < 1e-9
+
+
+def test_p9_complex_gradient_convention():
+    """directional() reads gradients as d/dRe + i d/dIm: for f(B) = sum |B|^2
+    the gradient 2B predicts the central difference along any direction."""
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((2, 3, 3)) + 1j * rng.standard_normal((2, 3, 3))
+    dB = ograd.random_hermitian_direction(B.shape, 9)
+    h = 1e-6
+    fd = (np.sum(np.abs(B + h * dB) ** 2) - np.sum(np.abs(B - h * dB) ** 2)) / (2 * h)
+    assert abs(ograd.directional(2 * B, None, None, 0.0, (dB, None, None, 0.0)) - fd) < 1e-7
