@@ -167,22 +167,27 @@ def run_batch(args, cfgname):
         with adcgpu.Batch(ctxs) as b:
             Xs = [torch.from_numpy(random_vectors(cx.N, nroots, seed=900 + i)).cuda() for i, cx in zip(ids, ctxs)]
             Ss = [torch.empty_like(X) for X in Xs]
-            for _ in range(max(args.warmup, 2)):
-                b.sigma(Xs, "bf16x3", outs=Ss)
-            i0 = b.info()
-            for _ in range(5):
-                b.sigma(Xs, "bf16x3", outs=Ss)
-            i1 = b.info()
-            tot["sig_ms"] += i1["batch_ms"] - i0["batch_ms"]
-            tot["sig_flops"] += i1["tc_flops"] - i0["tc_flops"]
+            # grouped tensor-core kernel alone (batches enqueued without a graph)
             b.use_graphs(False)
+            b.sigma(Xs, "bf16x3", outs=Ss)
+            i0 = b.info()
             for _ in range(3):
                 b.sigma(Xs, "bf16x3", outs=Ss)
-            i2 = b.info()
+            i1 = b.info()
+            tot["g_ms"] += i1["grouped_ms"] - i0["grouped_ms"]
+            tot["g_flops"] += i1["grouped_flops"] - i0["grouped_flops"]
+            tot["g_launch"] += i1["grouped_launches"] - i0["grouped_launches"]
+            # whole batched product, CUDA graph replays
             b.use_graphs(True)
-            tot["g_ms"] += i2["grouped_ms"] - i1["grouped_ms"]
-            tot["g_flops"] += i2["grouped_flops"] - i1["grouped_flops"]
-            tot["g_launch"] += i2["grouped_launches"] - i1["grouped_launches"]
+            for _ in range(max(args.warmup, 2)):
+                b.sigma(Xs, "bf16x3", outs=Ss)
+            i2 = b.info()
+            for _ in range(5):
+                b.sigma(Xs, "bf16x3", outs=Ss)
+            i3 = b.info()
+            tot["sig_ms"] += i3["batch_ms"] - i2["batch_ms"]
+            tot["sig_flops"] += i3["tc_flops"] - i2["tc_flops"]
+            i2 = i3
             del Xs, Ss
             torch.cuda.synchronize()
             l0 = adcgpu.launch_count()

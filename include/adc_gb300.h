@@ -196,6 +196,20 @@ int adc_fns_density(adc_ctx *ctx, adc_c128 *D, double *eta, adc_c128 *V,
 int adc_fns_transform(adc_ctx *ctx, const adc_c128 *U, int64_t ldu,
                       int64_t n_keep, adc_c128 *Bout);
 
+/* Backward pass of the roots (Hellmann-Feynman, Eq. 10): with Y the
+ * normalised eigenvectors of nroots non-degenerate roots ([nroots][N], host
+ * or device) and weights gomega[r] (host), writes the gradients of
+ * L = sum_r gomega[r] y_r^H M y_r = sum_r gomega[r] omega_r with respect to
+ * the inputs of adc_init: gB [naux][nmo][nmo] complex in the convention
+ * dL/dRe + i dL/dIm per element (the Hermitian structure of B is not
+ * imposed, so a Hermitian change dB changes L by sum Re(conj(gB) dB)),
+ * geps_occ [nocc], geps_vir [nvir] and *gx (host). gB and the energy
+ * gradients may be host or device arrays. The integral and amplitude
+ * intermediates are recomputed from the context's cached blocks. EE-ADC only
+ * (ADC_ERR_UNSUPPORTED otherwise). Synchronous. */
+int adc_sigma_adjoint(adc_ctx *ctx, const adc_c128 *Y, const double *gomega, int64_t nroots, adc_c128 *gB,
+                      double *geps_occ, double *geps_vir, double *gx);
+
 /* Blocks until all work the context has queued on its stream is done. Needed
  * after an asynchronous call with device pointers before another stream (or
  * the host) reads the outputs. */

@@ -102,6 +102,7 @@ def _load():
         "adc_strerror": (ctypes.c_char_p, [I]),
         "adc_last_error": (ctypes.c_char_p, [P]),
         "adc_diag_gemm": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "adc_sigma_adjoint": (I, [P, P, P, I64, P, P, P, ctypes.POINTER(D)]),
         "adc_batch_create": (I, [ctypes.POINTER(P), P, I]),
         "adc_batch_sigma": (I, [P, P, P, P, I]),
         "adc_batch_davidson": (I, [P, I, D, I, I, P, P, P, P]),
@@ -287,6 +288,27 @@ class Context:
         if rc != 0 and not (rc == -4 and not raise_on_noconv):
             _check(rc, self._h)
         return omega, Y, err, st.as_dict(), rc
+
+    def sigma_adjoint(self, Y, gomega):
+        """Gradients of sum_r gomega[r] y_r^H M y_r (``adc_sigma_adjoint``): (gB, geps_occ, geps_vir, gx).
+
+        Y: [nroots][N] eigenvectors (numpy or torch); outputs are numpy arrays,
+        or CUDA tensors when Y is a CUDA tensor."""
+        g = np.ascontiguousarray(np.asarray(gomega, dtype=np.float64).reshape(-1))
+        k = Y.shape[0] if Y.ndim == 2 else 1
+        if g.shape[0] != k:
+            raise ValueError("one weight per vector")
+        nmo = self.nocc + self.nvir
+        gB = _empty_like_kind(Y, (self.naux, nmo, nmo), np.complex128)
+        geo = _empty_like_kind(Y, (self.nocc,), np.float64)
+        gev = _empty_like_kind(Y, (self.nvir,), np.float64)
+        gx = ctypes.c_double()
+        if _on_cuda(Y) and not self._shared_stream:
+            _torch_sync()
+        _check(lib.adc_sigma_adjoint(self._h, _ptr(Y, np.complex128), g.ctypes.data_as(ctypes.c_void_p), k,
+                                     _ptr(gB, np.complex128), _ptr(geo, np.float64), _ptr(gev, np.float64),
+                                     ctypes.byref(gx)), self._h)
+        return gB, geo, gev, gx.value
 
     def fns_density(self, eta_crit):
         """MP2 virtual density and frozen natural spinors (``adc_fns_density``)."""

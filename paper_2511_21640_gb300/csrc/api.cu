@@ -14,6 +14,8 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
 void fns_run(adc_ctx *c, cplx *D, double *eta, cplx *Vout, double eta_crit, int64_t *n_keep, cplx *U,
              double *eps_new);
 void fns_transform(adc_ctx *c, const cplx *U, int64_t ldu, int64_t nk, cplx *Bout);
+void adjoint_ee(adc_ctx *c, const cplx *Y, const double *g_host, int64_t k, cplx *gB, double *geo, double *gev,
+                double *gx);
 }  // namespace adc
 
 using namespace adc;
@@ -311,6 +313,37 @@ int adc_fns_transform(adc_ctx *c, const adc_c128 *U, int64_t ldu, int64_t n_keep
   fns_transform(c, (const cplx *)uin.p, ldu, n_keep, (cplx *)bout.p);
   bout.finish(c->ex);
   ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
+int adc_sigma_adjoint(adc_ctx *c, const adc_c128 *Y, const double *gomega, int64_t nroots, adc_c128 *gB,
+                      double *geps_occ, double *geps_vir, double *gx) {
+  if (!c) return ADC_ERR_STATE;
+  if (!Y || !gomega || nroots < 1 || !gB || !geps_occ || !geps_vir || !gx) return ADC_ERR_ARG;
+  if (c->kind != ADC_EE) {
+    c->err = "adc_sigma_adjoint: implemented for EE-ADC";
+    g_last_error = c->err;
+    return ADC_ERR_UNSUPPORTED;
+  }
+  ADC_API_TRY
+  for (int64_t r = 0; r < nroots; ++r)
+    ADC_REQUIRE(std::isfinite(gomega[r]), ADC_ERR_ARG, "adc_sigma_adjoint: non-finite gomega");
+  const int64_t nb = c->Q * c->nmo * c->nmo;
+  DevIn yin(c->ex, Y, (size_t)nroots * c->N * sizeof(cplx));
+  DevOut gbo(c->ex, gB, (size_t)nb * sizeof(cplx));
+  DevOut geo(c->ex, geps_occ, (size_t)c->o * sizeof(double));
+  DevOut gev(c->ex, geps_vir, (size_t)c->v * sizeof(double));
+  fill_zero(c->ex, gbo.p, nb * sizeof(cplx));
+  fill_zero(c->ex, geo.p, c->o * sizeof(double));
+  fill_zero(c->ex, gev.p, c->v * sizeof(double));
+  double gxh = 0.0;
+  adjoint_ee(c, (const cplx *)yin.p, gomega, nroots, (cplx *)gbo.p, (double *)geo.p, (double *)gev.p, &gxh);
+  gbo.finish(c->ex);
+  geo.finish(c->ex);
+  gev.finish(c->ex);
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  *gx = gxh;
   return ADC_OK;
   ADC_API_CATCH(c)
 }

@@ -60,7 +60,8 @@ struct Scratch {
 };
 
 struct Plan {
-  TcGroup grp;
+  TcGroup grp;     // owned by the captured graph once there is one
+  TcGroup direct;  // for launches without the graph after capture
   cudaGraphExec_t exec = nullptr;
   int uses = 0;
   ~Plan() {
@@ -227,11 +228,11 @@ struct BatchCoord {
       ADC_CUDA(e);
       info.graphs_captured++;
     }
-    if (pl.exec) {
+    if (pl.exec && use_graphs) {
       ADC_CUDA(cudaGraphLaunch(pl.exec, bex.stream));
       info.graph_launches++;
     } else {
-      enqueue(reqs, pl.grp, true);
+      enqueue(reqs, pl.exec ? pl.direct : pl.grp, true);
       info.direct_launches++;
     }
     pl.uses++;

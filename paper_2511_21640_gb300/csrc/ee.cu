@@ -121,6 +121,15 @@ const Rows kDD1 = {{"1", "v(ab,cd) d(ik) d(jl)"}, {"1", "v(kl,ij) d(ac) d(bd)"},
                    {"-1", "v(bk,cj) d(ad) d(il)"}, {"-1", "v(bk,di) d(ac) d(jl)"},
                    {"-1", "v(bl,ci) d(ad) d(jk)"}, {"-1", "v(bl,dj) d(ac) d(ik)"}};
 
+// numerators of the second-order amplitudes (second_order_amplitudes in
+// setup.cu), as tables for the adjoint:
+//   t2_ij^ab D_ij^ab = 1/2 <ab||CD> t_ij^CD + 1/2 <MN||ij> t_MN^ab + P(ij)P(ab) <Mb||Cj> t_iM^aC
+//   t2_i^a (eps_i - eps_a) = 1/2 <aM||CD> t_iM^CD - 1/2 <MN||iC> t_MN^aC
+const Rows kT2N = {{"1/2", "v(ab,CD) t1(CD,ij)"},   {"1/2", "v(MN,ij) t1(ab,MN)"},
+                   {"1", "v(Mb,Cj) t1(aC,iM)"},     {"-1", "v(Mb,Ci) t1(aC,jM)"},
+                   {"-1", "v(Ma,Cj) t1(bC,iM)"},    {"1", "v(Ma,Ci) t1(bC,jM)"}};
+const Rows kS2N = {{"1/2", "v(aM,CD) t1(CD,iM)"}, {"-1/2", "v(MN,iC) t1(aC,MN)"}};
+
 // M[ia][jb] += s ((eps_b - eps_j) - (eps_a - eps_i)) / 2 * S[ia][jb]
 __global__ void k_wmul_add(cplx *M, const cplx *S, const double *eo, const double *ev, int64_t o, int64_t v,
                            double s) {
@@ -176,7 +185,7 @@ __global__ void k_ee_diag(const cplx *MSS, const double *g, const double *eo, co
 }  // namespace
 
 
-static TermSource make_source(adc_ctx *c) {
+TermSource ee_source(adc_ctx *c) {
   TermSource s;
   s.o = c->o;
   s.v = c->v;
@@ -219,12 +228,14 @@ void setup_ee(adc_ctx *c) {
   E.K1 = parse_terms(kK1); E.S2 = parse_terms(kS2); E.Y2 = parse_terms(kY2);
   E.S3 = parse_terms(kS3); E.Y3 = parse_terms(kY3);
   E.SD1 = parse_terms(kSD1); E.O2 = parse_terms(kO2); E.Z1 = parse_terms(kZ1); E.DD1 = parse_terms(kDD1);
+  E.T2N = parse_terms(kT2N); E.S2N = parse_terms(kS2N);
   first_order_amplitudes(c);
-  if (third) {
+  if (c->order == 3) {
+    // also at x = 0: the derivative with respect to x needs them
     DBuf G_vv, Lad;
     second_order_amplitudes(c, G_vv, Lad, E.t2d, E.t2s);
   }
-  TermSource src = make_source(c);
+  TermSource src = ee_source(c);
   const std::string L = "iajb";
   std::vector<int64_t> e4 = {o, v, o, v};
   E.MSS = cbuf(ex, n1 * n1);
@@ -289,7 +300,7 @@ void sigma_ee_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
   const int64_t po = npairs(o), pv = npairs(v);
   const bool third = (c->order == 3) && (c->x != 0.0);
   const double x = third ? c->x : 0.0;
-  TermSource src = make_source(c);
+  TermSource src = ee_source(c);
   TagScope tg(ex, "ee");
   // singles <- singles: static block
   zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, E.MSS.c(), 0, 1, n1, false, C0(), S, 0, N, 1);

@@ -78,6 +78,82 @@ struct Operand {
   std::string lab;
 };
 
+constexpr int RD_MAXD = 10;
+struct RDArgs {
+  int nk, ns;                                    // kept and summed axes
+  int64_t kext[RD_MAXD], kstr[RD_MAXD];
+  int64_t sext[RD_MAXD], sstr[RD_MAXD];
+  int64_t nsum;
+};
+
+// out[kept] = sum over the summed axes of (conj) src
+__global__ void k_reduce_axes(const cplx *__restrict__ src, RDArgs a, int conj, cplx *out, int64_t total) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = idx, base = 0;
+    for (int d = a.nk - 1; d >= 0; --d) {
+      base += (rem % a.kext[d]) * a.kstr[d];
+      rem /= a.kext[d];
+    }
+    cplx s = cmake(0.0, 0.0);
+    for (int64_t t = 0; t < a.nsum; ++t) {
+      int64_t r2 = t, off = 0;
+      for (int d = a.ns - 1; d >= 0; --d) {
+        off += (r2 % a.sext[d]) * a.sstr[d];
+        r2 /= a.sext[d];
+      }
+      s = cadd(s, src[base + off]);
+    }
+    out[idx] = conj ? cmake(s.x, -s.y) : s;
+  }
+}
+
+// sums out the labels of op that no other operand and not the output carry
+// (a contraction of one tensor with itself along an index it alone holds)
+void reduce_private_labels(Exec &ex, std::vector<Operand> &ops, const std::string &out_labels,
+                           std::vector<DBuf> &keep_alive) {
+  for (size_t i = 0; i < ops.size(); ++i) {
+    std::string kept, summed;
+    for (char ch : ops[i].lab) {
+      bool elsewhere = out_labels.find(ch) != std::string::npos;
+      for (size_t j = 0; j < ops.size() && !elsewhere; ++j)
+        if (j != i && ops[j].lab.find(ch) != std::string::npos) elsewhere = true;
+      (elsewhere ? kept : summed).push_back(ch);
+    }
+    if (summed.empty()) continue;
+    ADC_REQUIRE(!kept.empty() || ops.size() == 1, ADC_ERR_UNSUPPORTED, "terms: operand reduces to a scalar");
+    RDArgs a{};
+    a.nk = (int)kept.size();
+    a.ns = (int)summed.size();
+    ADC_REQUIRE(a.nk <= RD_MAXD && a.ns <= RD_MAXD, ADC_ERR_UNSUPPORTED, "terms: rank");
+    std::vector<int64_t> kext;
+    int64_t total = 1;
+    a.nsum = 1;
+    int nk = 0, ns = 0;
+    for (size_t d = 0; d < ops[i].lab.size(); ++d) {
+      const char ch = ops[i].lab[d];
+      if (kept.find(ch) != std::string::npos) {
+        a.kext[nk] = ops[i].t.ext[d];
+        a.kstr[nk] = ops[i].t.str[d];
+        kext.push_back(ops[i].t.ext[d]);
+        total *= ops[i].t.ext[d];
+        ++nk;
+      } else {
+        a.sext[ns] = ops[i].t.ext[d];
+        a.sstr[ns] = ops[i].t.str[d];
+        a.nsum *= ops[i].t.ext[d];
+        ++ns;
+      }
+    }
+    keep_alive.push_back(cbuf(ex, std::max<int64_t>(total, 1)));
+    cplx *dst = keep_alive.back().c();
+    k_reduce_axes<<<grid1d(total, 256), 256, 0, ex.stream>>>(ops[i].t.p, a, ops[i].t.conj ? 1 : 0, dst, total);
+    ADC_CHECK_LAUNCH();
+    ops[i].t = TV::dense(dst, kext);
+    ops[i].lab = kept;
+  }
+}
+
 double prod_ext(const std::string &labs, const std::map<char, int64_t> &ext) {
   double p = 1.0;
   for (char c : labs) p *= (double)ext.at(c);
@@ -162,6 +238,8 @@ void eval_terms(Exec &ex, const std::vector<Term> &terms, const TermSource &src,
       }
     }
     for (auto &op : ops) merge_duplicates(op.t, op.lab);
+    std::vector<DBuf> reduced;
+    reduce_private_labels(ex, ops, olab, reduced);
     std::map<char, int64_t> ext;
     for (auto &op : ops)
       for (size_t i = 0; i < op.lab.size(); ++i) ext[op.lab[i]] = op.t.ext[i];
@@ -220,6 +298,34 @@ void eval_terms(Exec &ex, const std::vector<Term> &terms, const TermSource &src,
       if (p != std::string::npos) sstr[q] = R.str[p];
     }
     strided_add(ex, res.c(), sstr, ov, coef);
+  }
+}
+
+void eval_terms_grad(Exec &ex, const std::vector<Term> &terms, const TermSource &src, const TermSource &grad,
+                     const std::vector<std::pair<std::string, TV>> &extra, bool conj, cplx alpha) {
+  for (const Term &term : terms) {
+    for (size_t j = 0; j < term.f.size(); ++j) {
+      const Factor &f = term.f[j];
+      if (f.name == "d") continue;
+      TV G = grad.get(f.name, f.labels);
+      if (!G.p) continue;  // no gradient wanted for this tensor
+      const bool appears_conj = (G.conj != conj);
+      G.conj = false;
+      Term rest;
+      rest.coef = term.coef;
+      for (size_t i = 0; i < term.f.size(); ++i)
+        if (i != j) rest.f.push_back(term.f[i]);
+      const std::vector<Term> one{rest};
+      if (appears_conj) {
+        // the factor enters as conj(T): G_T += dC/d conj(T)
+        eval_terms(ex, one, src, extra, conj, alpha, G, f.labels);
+      } else {
+        // the factor enters as T: G_T += conj(dC/dT), i.e. every operand conjugated
+        std::vector<std::pair<std::string, TV>> ex2 = extra;
+        for (auto &e : ex2) e.second.conj = !e.second.conj;
+        eval_terms(ex, one, src, ex2, !conj, cmake(alpha.x, -alpha.y), G, f.labels);
+      }
+    }
   }
 }
 

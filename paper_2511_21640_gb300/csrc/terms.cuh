@@ -45,4 +45,16 @@ void eval_terms(Exec &ex, const std::vector<Term> &terms, const TermSource &src,
                 const std::vector<std::pair<std::string, TV>> &extra, bool conj, cplx alpha,
                 const TV &out, const std::string &out_labels);
 
+// Adjoint of eval_terms for a real target f = Re C, where C is what
+// eval_terms would sum over every label (the extras carry the output side,
+// e.g. a density or the conjugated left vectors). For every factor whose
+// tensor has a gradient buffer (grad.get returns a view in the same label
+// convention as src, with conj set for the conjugated names, or a null view),
+// G_T += dC/d conj(T) where the factor enters as conj(T) and conj(dC/dT)
+// where it enters as T: the gradient in the convention d/dRe + i d/dIm. Each
+// derivative is the same contraction with the factor left out and its labels
+// as the output.
+void eval_terms_grad(Exec &ex, const std::vector<Term> &terms, const TermSource &src, const TermSource &grad,
+                     const std::vector<std::pair<std::string, TV>> &extra, bool conj, cplx alpha);
+
 }  // namespace adc
