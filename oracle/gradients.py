@@ -92,4 +92,4 @@ def random_hermitian_direction(shape, seed):
     rng = np.random.default_rng(seed)
     A = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
     A = 0.5 * (A + np.conj(np.swapaxes(A, 1, 2)))
-    return A / np.linalg.norm(A)
+    return np.ascontiguousarray(A / np.linalg.norm(A))

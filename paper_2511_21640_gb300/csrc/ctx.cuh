@@ -54,6 +54,7 @@ struct adc_ctx {
 namespace adc {
 TV Bview(adc_ctx *c, char p, char q);               // B^Q block view [Q][p][q]
 DBuf eri_block(adc_ctx *c, const char *spec);       // dense <pq||rs> of a 4-letter o/v spec
+DBuf build_vvvv_packed(adc_ctx *c);                 // [Pv][Pv] <ab||cd>, a<b, c<d
 void setup_operators(adc_ctx *c);
 // t1 (c->t1) and ring integrals (c->W) from B
 void first_order_amplitudes(adc_ctx *c);

@@ -293,6 +293,9 @@ void setup_ee(adc_ctx *c) {
   ADC_CUDA(cudaStreamSynchronize(ex.stream));
 }
 
+void ee_struct_build(adc_ctx *c, bool dd);
+void ee_struct_apply(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, double sdd);
+
 void sigma_ee_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
   Exec &ex = c->ex;
   EEOps &E = *c->ee;
@@ -300,60 +303,22 @@ void sigma_ee_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
   const int64_t po = npairs(o), pv = npairs(v);
   const bool third = (c->order == 3) && (c->x != 0.0);
   const double x = third ? c->x : 0.0;
-  TermSource src = ee_source(c);
+  const double sdd = (third && c->dd_order == 1) ? x : 0.0;
+  ee_struct_build(c, sdd != 0.0);
   TagScope tg(ex, "ee");
-  // singles <- singles: static block
+  // singles <- singles: static block; doubles: zeroth order
   zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, E.MSS.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
-  // full antisymmetric doubles X2f[z][k][l][c][d]
-  const int64_t nf = k * o * o * v * v;
-  DBuf half = cbuf(ex, k * po * v * v), X2f = cbuf(ex, nf), S2f = cbuf(ex, nf);
-  pair_unpack(ex, X + n1, k, po, N, pv, v, 1, half.c());
-  pair_unpack(ex, half.c(), k, 1, po * v * v, 0, o, v * v, X2f.c());
-  half.reset();
-  TV Xd = TV::dense(X2f.c(), {k, o, o, v, v});
-  TV X1(const_cast<cplx *>(X), {k, o, v}, {N, v, 1});
-  TV S1(S, {k, o, v}, {N, v, 1});
-  // singles <- doubles: 1/4 sum_klcd M_SD(ia;klcd) X_klcd
-  eval_terms(ex, E.SD1, src, {{"zklcd", Xd}}, false, CR(0.25), S1, "zia");
-  // doubles <- singles and the doubles block
-  fill_zero(ex, S2f.p, S2f.bytes);
-  TV Sd = TV::dense(S2f.c(), {k, o, o, v, v});
-  eval_terms(ex, E.SD1, src, {{"zia", X1}}, true, C1(), Sd, "zklcd");
-  if (third) {
-    DBuf Xk = cbuf(ex, nf);
-    k_dk_mul<<<grid1d(nf, 256), 256, 0, ex.stream>>>(X2f.c(), c->eo.d(), c->ev.d(), k, o, v, Xk.c());
-    ADC_CHECK_LAUNCH();
-    TV Xkd = TV::dense(Xk.c(), {k, o, o, v, v});
-    // S1 += x/4 [ O2 (Delta_K X) - Delta_S o (O2 X) + Z1 X ]
-    eval_terms(ex, E.O2, src, {{"zklcd", Xkd}}, false, CR(0.25 * x), S1, "zia");
-    DBuf tmp = cbuf(ex, k * n1);
-    fill_zero(ex, tmp.p, tmp.bytes);
-    TV T1 = TV::dense(tmp.c(), {k, o, v});
-    eval_terms(ex, E.O2, src, {{"zklcd", Xd}}, false, CR(0.25 * x), T1, "zia");
-    diag_mul_add(ex, k, n1, E.dS.d(), tmp.c(), n1, S, N, -1.0);
-    eval_terms(ex, E.Z1, src, {{"zklcd", Xd}}, false, CR(0.25 * x), S1, "zia");
-    // S2 += x [ Delta_K o conj(O2) X1 - conj(O2) (Delta_S o X1) + conj(Z1) X1 ]
-    DBuf T2 = cbuf(ex, nf);
-    fill_zero(ex, T2.p, T2.bytes);
-    eval_terms(ex, E.O2, src, {{"zia", X1}}, true, CR(x), TV::dense(T2.c(), {k, o, o, v, v}), "zklcd");
-    k_dk_mul<<<grid1d(nf, 256), 256, 0, ex.stream>>>(T2.c(), c->eo.d(), c->ev.d(), k, o, v, T2.c());
-    ADC_CHECK_LAUNCH();
-    zaxpby(ex, nf, C1(), T2.c(), C1(), S2f.c());
-    DBuf Xs = cbuf(ex, k * n1);
-    fill_zero(ex, Xs.p, Xs.bytes);
-    diag_mul_add(ex, k, n1, E.dS.d(), X, N, Xs.c(), n1, 1.0);
-    eval_terms(ex, E.O2, src, {{"zia", TV::dense(Xs.c(), {k, o, v})}}, true, CR(-x), Sd, "zklcd");
-    eval_terms(ex, E.Z1, src, {{"zia", X1}}, true, CR(x), Sd, "zklcd");
-    if (c->dd_order == 1)
-      eval_terms(ex, E.DD1, src, {{"zklcd", Xd}}, false, CR(0.25 * x), TV::dense(S2f.c(), {k, o, o, v, v}),
-                 "zijab");
-  }
-  // pack the doubles: S2[z][(k<l)][(c<d)] = S2f + zeroth order
-  DBuf half2 = cbuf(ex, k * po * v * v);
-  pair_pack(ex, S2f.c(), o * o * v * v, 0, o * v * v, v * v, 1, 0.0, k, 1, o, v * v, half2.c(), po * v * v, 0, C1(),
-            C0());
-  pair_pack(ex, half2.c(), po * v * v, v * v, v, 1, 0, 0.0, k, po, v, 1, S + n1, N, pv, C1(), C0());
+  ADC_CUDA(cudaMemset2DAsync(S + n1, N * sizeof(cplx), 0, n2 * sizeof(cplx), k, ex.stream));
   diag_mul_add(ex, k, n2, c->d2.d(), X + n1, N, S + n1, N, 1.0);
+  // chunks of vectors whose scratch stays within about 4 GiB
+  int64_t per = std::max<int64_t>(o * o * pv, po * v * v);
+  if (sdd != 0.0) per = std::max<int64_t>(per, 2 * o * v * o * v);
+  per *= (int64_t)sizeof(cplx);
+  const int64_t kc = std::max<int64_t>(1, std::min<int64_t>(k, (4ll << 30) / std::max<int64_t>(per, 1)));
+  for (int64_t z0 = 0; z0 < k; z0 += kc) {
+    const int64_t kk = std::min(kc, k - z0);
+    ee_struct_apply(c, X + z0 * N, S + z0 * N, kk, sdd);
+  }
 }
 
 }  // namespace adc

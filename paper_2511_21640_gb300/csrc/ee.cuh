@@ -14,6 +14,12 @@ struct EEOps {
   std::map<std::string, DBuf> eri;  // dense integral blocks by o/v spec
   DBuf MSS;                         // [n1][n1] static singles block
   DBuf dS;                          // [n1] eps_a - eps_i
+  // packed operands of the structured sigma (ee_struct.cu)
+  DBuf pair_o, pair_v;              // pair tables (p, q) of the occupied and virtual pairs
+  DBuf Va, Vb, Goo, Gvv;            // <al||cd> [(l,cd)][a], <kl||di> [i][(kl,d)], <kl||ij>, <ab||cd> packed
+                                    // (Va, Vb with the folded second-order coupling at third order)
+  DBuf T1p, T2p, V1, V2;            // conj(t_lM^cd) [(l,cd)][M], conj(t_kl^dA) [(kl,d)][A],
+                                    // <ak||iM> [(i,a)][(k,M)], <aA||ci> [(i,a)][(c,A)]
 };
 // tensors of the EE term tables (v blocks cached in EEOps::eri)
 TermSource ee_source(adc_ctx *c);

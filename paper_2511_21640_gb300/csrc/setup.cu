@@ -109,7 +109,7 @@ __global__ void k_diag_ip(const cplx *M11, const double *g, const double *eo, co
 }  // namespace
 
 // packed ladder integrals <ab||cd> (a<b, c<d) of the virtual block
-static DBuf build_vvvv_packed(adc_ctx *c) {
+DBuf build_vvvv_packed(adc_ctx *c) {
   const int64_t v = c->v, Q = c->Q, pv = npairs(v);
   DBuf G = cbuf(c->ex, pv * pv);
   if (pv == 0) return G;

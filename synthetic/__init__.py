@@ -98,6 +98,9 @@ CONFIGS = {
                                vir_range=(0.1, 5.0), kind="EE", order=3, x=1.0, nroots=6, tol=1e-6),
     "ee2x3_o30_v150_q900": dict(nocc=30, nvir=150, naux=900, seed=0, occ_range=(-3.0, -0.3),
                                 vir_range=(0.1, 5.0), kind="EE", order=3, x=0.4, nroots=4, tol=1e-8),
+    # a smaller case of the same family, for quick runs of the same measurement
+    "ee2x3_o12_v60_q360": dict(nocc=12, nvir=60, naux=360, seed=0, occ_range=(-3.0, -0.3),
+                               vir_range=(0.1, 5.0), kind="EE", order=3, x=0.4, nroots=4, tol=1e-8),
 }
 
 
