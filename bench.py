@@ -247,9 +247,11 @@ def run_batch(args, cfgname):
 
 
 def run_ee(args, cfgname):
-    """EE-ADC workload (FP64 path): Davidson seconds per root, one FP64 sigma
-    block, and the gradients of the roots (adjoint) with a central-difference
-    check along one random direction (dB Hermitian, deps, dx), h = 1e-5."""
+    """EE-ADC workload: mixed-precision Davidson seconds per root (FP64
+    residuals), the FP64 Davidson for comparison (unless --no-fp64-davidson),
+    one sigma block in each precision, and the gradients of the roots (adjoint)
+    with a central-difference check along one random direction (dB Hermitian,
+    deps, dx), h = 1e-5, from two more mixed-precision solves."""
     import torch
     import paper_2511_21640_gb300 as adcgpu
     from oracle.gradients import directional, random_hermitian_direction
@@ -262,27 +264,38 @@ def run_ee(args, cfgname):
     ctx = adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=cfg["order"], x=x)
     init_s = time.perf_counter() - t0
     log(f"init {init_s:.1f} s, N = {ctx.N}")
+    ctx.sigma(random_vectors(ctx.N, 1, seed=3), "bf16x3")  # builds the split-precision operators
     clocks = Clocks()
     clocks.start()
     ctx.profile(True)
     l0 = adcgpu.launch_count()
     t1 = time.perf_counter()
-    om, Y, e64, st, rc = ctx.davidson(nroots, tol=tol, max_iter=300, precision="fp64")
+    om, Y, e64, st, rc = ctx.davidson(nroots, tol=tol, max_iter=400, precision="bf16x3")
     solve_s = time.perf_counter() - t1
     launches = adcgpu.launch_count() - l0
     prof = ctx.profile_read()
     ctx.profile(False)
     clk = clocks.stop()
-    log(f"davidson {solve_s:.1f} s", st)
+    log(f"mixed davidson {solve_s:.1f} s", st)
+    fp64 = None
+    if not args.no_fp64_davidson:
+        t2 = time.perf_counter()
+        om64, _, e6, st6, rc6 = ctx.davidson(nroots, tol=tol, max_iter=400, precision="fp64", want_vectors=False)
+        t64 = time.perf_counter() - t2
+        log(f"fp64 davidson {t64:.1f} s", st6)
+        fp64 = {"s_per_root": t64 / nroots, "iterations": st6["iterations"], "sigma_calls": st6["sigma_calls"],
+                "max_eig_diff_vs_mixed": float(np.abs(om64 - om).max()), "rc": int(rc6)}
     Xs = random_vectors(ctx.N, nroots, seed=7)
-    ctx.sigma(Xs, "fp64")
-    ctx.profile(True)
-    t2 = time.perf_counter()
-    ctx.sigma(Xs, "fp64")
-    sig_s = time.perf_counter() - t2
-    sp = ctx.profile_read()
-    ctx.profile(False)
-    sig_flops = sum(e["flops"] for e in sp.values())
+    sig = {}
+    for prec in ("bf16x3", "fp64"):
+        ctx.sigma(Xs, prec)
+        ctx.profile(True)
+        t2 = time.perf_counter()
+        ctx.sigma(Xs, prec)
+        ts = time.perf_counter() - t2
+        sp = ctx.profile_read()
+        ctx.profile(False)
+        sig[prec] = {"ms": 1e3 * ts, "flops_timed_kernels": sum(e["flops"] for e in sp.values())}
     rng = np.random.default_rng(11)
     wts = rng.standard_normal(nroots)
     t3 = time.perf_counter()
@@ -297,29 +310,44 @@ def run_ee(args, cfgname):
     for sgn in (1, -1):
         with adcgpu.Context(p.B + sgn * h * D[0], p.eps_occ + sgn * h * D[1], p.eps_vir + sgn * h * D[2],
                             kind="EE", order=cfg["order"], x=x + sgn * h * D[3]) as c2:
-            w, _, _, _, rcf = c2.davidson(nroots, tol=min(tol, 1e-8), max_iter=300, precision="fp64",
+            w, _, _, _, rcf = c2.davidson(nroots, tol=min(tol, 1e-8), max_iter=400, precision="bf16x3",
                                           want_vectors=False)
             ws.append(w)
     fd = float(np.dot(wts, (ws[0] - ws[1]) / (2 * h)))
     log(f"gradient check: adjoint {pred:.10e} fd {fd:.10e}")
     by = sorted(((k, e) for k, e in prof.items() if e["launches"] > 0), key=lambda t: -t[1]["total_ms"])
-    top_name, top = by[0]
-    ach = top["flops"] / (top["total_ms"] * 1e-3) / 1e12 if top["total_ms"] > 0 else None
+    pk, pk_kind = peaks()
+
+    def roof(name, e):
+        avg = e["total_ms"] / e["launches"]
+        alg = e["flops"] / e["launches"]
+        if name.startswith("tc_gemm"):
+            mma = 3.0 * alg
+            peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+            ach = mma / (avg * 1e-3) / 1e12
+            return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None, "peak_kind": f"bf16 dense sustained ({pk_kind})",
+                    "launches": e["launches"], "avg_launch_ms": avg}
+        ach = alg / (avg * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                "traffic": None, "peak_kind": "fp64 FMA nominal 1.25 TFLOP/s", "launches": e["launches"],
+                "avg_launch_ms": avg}
+
+    by_kernel = [roof(k, e) for k, e in by]
     line = {
         "metric": METRIC, "value": solve_s / nroots, "unit": "s/root", "n_gpus": 1, "steps": 1,
         "warmup": 0, "ms_per_step": 1e3 * solve_s, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
         "config": {"workload": cfgname, "kind": "EE", "order": cfg["order"], "x": x, "nocc": o, "nvir": v,
                    "naux": Q, "nroots": nroots, "tol_fp64_residual": tol, "N": int(Y.shape[1]),
                    "l2": "operators larger than L2"},
-        "clocks": clk, "gpu_launches": int(launches),
-        "roofline": {"bound": "alu", "kernel": top_name, "achieved": ach, "peak": 1.25, "unit": "TFLOP/s",
-                     "frac": ach / 1.25 if ach else None, "traffic": None,
-                     "peak_kind": "fp64 FMA nominal 1.25 TFLOP/s (3M products: 6 flops per 8 counted)",
-                     "launches": top["launches"], "avg_launch_ms": top["total_ms"] / top["launches"]},
-        "davidson": {"iterations": st["iterations"], "sigma_calls": st["sigma_calls"], "rc": int(rc),
-                     "omega": [float(w) for w in om], "err64": [float(e) for e in e64]},
-        "sigma_fp64": {"ms": 1e3 * sig_s, "vectors": nroots, "tflops_algorithmic": sig_flops / sig_s / 1e12},
+        "clocks": clk, "gpu_launches": int(launches), "roofline": by_kernel[0], "roofline_by_kernel": by_kernel,
+        "mixed_davidson": {"iterations": st["iterations"], "sigma_calls": st["sigma_calls"],
+                           "sigma_calls_fp64": st["sigma_calls_fp64"], "rc": int(rc),
+                           "omega": [float(w) for w in om], "err64": [float(e) for e in e64]},
+        "fp64_davidson": fp64,
+        "sigma": {"vectors": nroots, "bf16x3_ms": sig["bf16x3"]["ms"], "fp64_ms": sig["fp64"]["ms"],
+                  "speedup": sig["fp64"]["ms"] / sig["bf16x3"]["ms"]},
         "gradient": {"adjoint_s": adj_s, "directional_adjoint": pred, "directional_fd": fd,
                      "rel_diff": abs(pred - fd) / max(1.0, abs(fd)), "fd_step": h,
                      "weights": [float(w) for w in wts]},

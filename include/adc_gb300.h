@@ -66,7 +66,7 @@ enum {
   ADC_ERR_CUDA = -3,        /* a CUDA runtime call failed */
   ADC_ERR_NOCONV = -4,      /* Davidson did not converge; best results returned */
   ADC_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
-  ADC_ERR_UNSUPPORTED = -6, /* combination not built (e.g. EE) */
+  ADC_ERR_UNSUPPORTED = -6, /* combination not built (e.g. the adjoint of IP/EA) */
   ADC_ERR_STATE = -7,       /* context not initialised / unusable */
   ADC_ERR_NUMERIC = -8      /* NaN or Inf met in a residual or input */
 };
@@ -107,8 +107,7 @@ int adc_opts_default(adc_opts *opts);
  *            checked to opts->herm_tol * max|B|, else ADC_ERR_ARG.
  *   eps_occ  [nocc], eps_vir [nvir]: orbital energies (Hartree); every
  *            eps_occ must lie below every eps_vir, else ADC_ERR_ARG.
- *   kind     ADC_IP, ADC_EA or ADC_EE (EE: FP64 sigma products only; the
- *            tensor-core precision gives ADC_ERR_UNSUPPORTED).
+ *   kind     ADC_IP, ADC_EA or ADC_EE.
  *   order    2 (ADC(2)) or 3 (ADC(2)+x(3); x = 1 is ADC(3), x = 0 is ADC(2)).
  *   x        scale of every term ADC(3) adds to ADC(2) (used when order == 3).
  *   opts     NULL for the defaults.

@@ -221,10 +221,6 @@ int adc_sigma(adc_ctx *c, const adc_c128 *X, adc_c128 *S, int64_t k, int precisi
   if (!c) return ADC_ERR_STATE;
   if (k < 0 || (k > 0 && (!X || !S))) return ADC_ERR_ARG;
   if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3) return ADC_ERR_ARG;
-  if (c->kind == ADC_EE && precision != ADC_PREC_FP64) {
-    c->err = "EE-ADC runs FP64 sigma products only";
-    return ADC_ERR_UNSUPPORTED;
-  }
   if (k == 0) return ADC_OK;
   ADC_API_TRY
   const size_t bytes = (size_t)k * c->N * sizeof(cplx);
@@ -261,10 +257,6 @@ int adc_davidson(adc_ctx *c, int nroots, double tol, int max_iter, int precision
                  int64_t nguess, double *omega, adc_c128 *Y, double *err64, adc_stats *st) {
   if (!c) return ADC_ERR_STATE;
   if (!omega || nroots < 1 || max_iter < 1) return ADC_ERR_ARG;
-  if (c->kind == ADC_EE && precision != ADC_PREC_FP64) {
-    c->err = "EE-ADC runs FP64 sigma products only";
-    return ADC_ERR_UNSUPPORTED;
-  }
   ADC_API_TRY
   const size_t vb = (size_t)nroots * c->N * sizeof(cplx);
   DevIn gin(c->ex, guess, guess ? (size_t)nguess * c->N * sizeof(cplx) : 0);

@@ -63,6 +63,7 @@ void first_order_amplitudes(adc_ctx *c);
 void second_order_amplitudes(adc_ctx *c, DBuf &G_vv, DBuf &Lad, DBuf &t2d, DBuf &t2s);
 void setup_ee(adc_ctx *c);
 void sigma_ee_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
+void sigma_ee_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision);

@@ -350,6 +350,7 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   double best = 1e300;
   int since = 0;
   const int stall_window = 5;
+  int refine_stalls = 0;
   int it = 0;
   for (it = 1; it <= max_iter; ++it) {
     const int kr = std::min(d.m, krmax);
@@ -376,9 +377,11 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
       best = mx;
       since = 0;
     } else if (phase != 2 && since >= stall_window) {
-      // stalled at the split-precision floor: FP64 base for the current Ritz vectors
+      // stalled at the split-precision floor: FP64 base for the current Ritz vectors;
+      // when the refinement itself keeps stalling, the corrections go FP64 too
       d.collapse(nroots, true);
-      phase = 1;
+      if (phase == 1) ++refine_stalls;
+      phase = (phase == 1 && refine_stalls >= 2) ? 2 : 1;
       best = 1e300;
       since = 0;
       continue;

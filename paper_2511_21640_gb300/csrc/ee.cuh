@@ -4,6 +4,7 @@
 #include <map>
 
 #include "ctx.cuh"
+#include "tc_gemm.cuh"
 #include "terms.cuh"
 
 namespace adc {
@@ -20,6 +21,10 @@ struct EEOps {
                                     // (Va, Vb with the folded second-order coupling at third order)
   DBuf T1p, T2p, V1, V2;            // conj(t_lM^cd) [(l,cd)][M], conj(t_kl^dA) [(kl,d)][A],
                                     // <ak||iM> [(i,a)][(k,M)], <aA||ci> [(i,a)][(c,A)]
+  // split-precision copies for the tensor-core sigma (A operands) and the per-call B operand
+  TcMat tVaT, tVaC, tVb, tVbC, tGvv, tGoo, tW, bx;
+  DBuf tcerr;
+  bool tc_ready = false;
 };
 // tensors of the EE term tables (v blocks cached in EEOps::eri)
 TermSource ee_source(adc_ctx *c);

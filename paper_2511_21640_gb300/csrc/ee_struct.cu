@@ -111,6 +111,30 @@ __global__ void k_gather_xt(const cplx *X, int64_t ldx, int64_t kc, int64_t o, i
   }
 }
 
+// XbT[z][a][((k<l), d)] = X_z(kl, ad)
+__global__ void k_gather_xbt(const cplx *X, int64_t ldx, int64_t kc, const int *pk, const int *pl, int64_t o,
+                             int64_t v, int64_t po, int64_t pv, cplx *Xb) {
+  const int64_t total = kc * v * po * v;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = idx % v, r = idx / v;
+    const int64_t pkl = r % po, r2 = r / po;
+    const int64_t a = r2 % v, z = r2 / v;
+    Xb[idx] = xel(X + z * ldx, pk[pkl], pl[pkl], a, d, o, v, pv);
+  }
+}
+// XtT[(z, i, b)][(k, c)] = X_z(ki, cb)
+__global__ void k_gather_xtt(const cplx *X, int64_t ldx, int64_t kc, int64_t o, int64_t v, int64_t pv, cplx *Xt) {
+  const int64_t ov = o * v, total = kc * ov * ov;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t kcol = idx % ov, row = idx / ov;
+    const int64_t c = kcol % v, kk = kcol / v;
+    const int64_t b = row % v, i = (row / v) % o, z = row / ov;
+    Xt[idx] = xel(X + z * ldx, kk, i, c, b, o, v, pv);
+  }
+}
+
 // S2_z[(i<l)][(cd)] += F_z[i][l][(cd)] - F_z[l][i][(cd)]
 __global__ void k_scatter_f(const cplx *F, int64_t kc, const int *pi, const int *pj, int64_t o, int64_t po,
                             int64_t pv, cplx *S2, int64_t lds) {
@@ -390,6 +414,138 @@ void ee_struct_apply(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, double sdd)
   k_scatter_ring<<<grid1d(kc * po * pv, 256), 256, 0, ex.stream>>>(R.c(), kc, pio, pjo, pav, pbv, o, v, po, pv, sdd,
                                                                    S + n1, N);
   ADC_CHECK_LAUNCH();
+}
+
+// split-precision copies of the static operators (after ee_struct_build)
+static void ee_tc_build(adc_ctx *c, bool dd) {
+  Exec &ex = c->ex;
+  EEOps &E = *c->ee;
+  const int64_t o = c->o, v = c->v, po = npairs(o), pv = npairs(v), ov = o * v;
+  tc_pack_A(ex, E.tVaT, E.Va.c(), v, o * pv, 1, v, false);
+  tc_pack_A(ex, E.tVaC, E.Va.c(), o * pv, v, v, 1, true);
+  tc_pack_A(ex, E.tVb, E.Vb.c(), o, po * v, po * v, 1, false);
+  tc_pack_A(ex, E.tVbC, E.Vb.c(), po * v, o, 1, po * v, true);
+  if (dd) {
+    tc_pack_A(ex, E.tGvv, E.Gvv.c(), pv, pv, pv, 1, false);
+    tc_pack_A(ex, E.tGoo, E.Goo.c(), po, po, po, 1, false);
+    tc_pack_A(ex, E.tW, c->W.c(), ov, ov, ov, 1, false);
+  }
+  E.tcerr = DBuf(ex, sizeof(int));
+  fill_zero(ex, E.tcerr.p, sizeof(int));
+  E.tc_ready = true;
+}
+
+// ee_struct_apply with the GEMMs over the doubles on the tensor cores (BF16x3);
+// the separable second-order pieces (o x o and v x v intermediates) stay FP64
+static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, double sdd) {
+  Exec &ex = c->ex;
+  EEOps &E = *c->ee;
+  const int64_t o = c->o, v = c->v, n1 = c->n1, N = c->N, po = npairs(o), pv = npairs(v), ov = o * v;
+  if (po == 0 || pv == 0 || kc <= 0) return;
+  const int *pio = (const int *)E.pair_o.p, *pjo = pio + std::max<int64_t>(po, 1);
+  const int *pav = (const int *)E.pair_v.p, *pbv = pav + std::max<int64_t>(pv, 1);
+  const bool second = (c->order == 3 && c->x != 0.0);
+  const double x = second ? c->x : 0.0;
+  int *err = (int *)E.tcerr.p;
+  TagScope tg(ex, "ee_coupling");
+  {
+    DBuf Xa = cbuf(ex, kc * o * o * pv);
+    k_gather_xa<<<grid1d(kc * o * o * pv, 256), 256, 0, ex.stream>>>(X + n1, N, kc, pav, pbv, o, v, pv, Xa.c());
+    ADC_CHECK_LAUNCH();
+    // S1[z][i][a] += sum_(l,cd) Va[(l,cd)][a] Xa[z][i][(l,cd)]
+    tc_pack_B(ex, E.bx, Xa.c(), kc * o, o * pv, o * pv, 0, 1, 1, false);
+    tc_gemm(ex, E.tVaT, E.bx, v, kc * o, C1(), C1(), S, 1, N, v, o, err);
+    DBuf U;
+    if (second) {
+      DBuf Y1 = cbuf(ex, kc * o * o);
+      zgemm(ex, o, o, o * pv, kc, C1(), Xa.c(), o * o * pv, o * pv, 1, false, E.T1p.c(), 0, o, 1, false, C0(),
+            Y1.c(), o * o, o, 1);
+      zgemm(ex, kc, n1, o * o, 1, CR(x), Y1.c(), 0, o * o, 1, false, E.V1.c(), 0, 1, o * o, false, C1(), S, 0, N, 1);
+      U = cbuf(ex, kc * o * o);
+      zgemm(ex, kc, o * o, n1, 1, C1(), X, 0, N, 1, false, E.V1.c(), 0, o * o, 1, true, C0(), U.c(), 0, o * o, 1);
+    }
+    // F[z][i][(l,cd)] = sum_a conj(Va[(l,cd)][a]) X1[z][i][a]
+    tc_pack_B(ex, E.bx, X, kc * o, v, N, v, o, 1, false);
+    tc_gemm(ex, E.tVaC, E.bx, o * pv, kc * o, C1(), C0(), Xa.c(), 1, o * o * pv, o * pv, o, err);
+    if (second)
+      zgemm(ex, o, o * pv, o, kc, CR(x), U.c(), o * o, o, 1, false, E.T1p.c(), 0, 1, o, true, C1(), Xa.c(),
+            o * o * pv, o * pv, 1);
+    k_scatter_f<<<grid1d(kc * po * pv, 256), 256, 0, ex.stream>>>(Xa.c(), kc, pio, pjo, o, po, pv, S + n1, N);
+    ADC_CHECK_LAUNCH();
+  }
+  {
+    DBuf Xb = cbuf(ex, kc * v * po * v);
+    k_gather_xbt<<<grid1d(kc * v * po * v, 256), 256, 0, ex.stream>>>(X + n1, N, kc, pio, pjo, o, v, po, pv,
+                                                                     Xb.c());
+    ADC_CHECK_LAUNCH();
+    // S1[z][i][a] += sum_((kl),d) Vb[i][((kl),d)] XbT[z][a][((kl),d)]
+    tc_pack_B(ex, E.bx, Xb.c(), kc * v, po * v, po * v, 0, 1, 1, false);
+    tc_gemm(ex, E.tVb, E.bx, o, kc * v, C1(), C1(), S, v, N, 1, v, err);
+    DBuf U2;
+    if (second) {
+      DBuf Y2 = cbuf(ex, kc * v * v);
+      zgemm(ex, v, v, po * v, kc, C1(), Xb.c(), v * po * v, po * v, 1, false, E.T2p.c(), 0, v, 1, false, C0(),
+            Y2.c(), v * v, v, 1);
+      zgemm(ex, kc, n1, v * v, 1, CR(x), Y2.c(), 0, v * v, 1, false, E.V2.c(), 0, 1, v * v, false, C1(), S, 0, N, 1);
+      U2 = cbuf(ex, kc * v * v);
+      zgemm(ex, kc, v * v, n1, 1, C1(), X, 0, N, 1, false, E.V2.c(), 0, v * v, 1, true, C0(), U2.c(), 0, v * v, 1);
+    }
+    // G[z][((kl),d)][a] = sum_i conj(Vb[i][((kl),d)]) X1[z][i][a]  (reusing the buffer)
+    tc_pack_B(ex, E.bx, X, kc * v, o, N, 1, v, v, false);
+    tc_gemm(ex, E.tVbC, E.bx, po * v, kc * v, C1(), C0(), Xb.c(), v, po * v * v, 1, v, err);
+    if (second)
+      zgemm(ex, po * v, v, v, kc, CR(x), E.T2p.c(), 0, v, 1, true, U2.c(), v * v, 1, v, false, C1(), Xb.c(),
+            po * v * v, v, 1);
+    k_scatter_g<<<grid1d(kc * po * pv, 256), 256, 0, ex.stream>>>(Xb.c(), kc, pav, pbv, v, po, pv, S + n1, N);
+    ADC_CHECK_LAUNCH();
+  }
+  if (sdd == 0.0) return;
+  ex.tag = "ee_ladder";
+  tc_pack_B(ex, E.bx, X + n1, kc * po, pv, N, pv, po, 1, false);
+  tc_gemm(ex, E.tGvv, E.bx, pv, kc * po, CR(sdd), C1(), S + n1, 1, N, pv, po, err);
+  tc_pack_B(ex, E.bx, X + n1, kc * pv, po, N, 1, pv, pv, false);
+  tc_gemm(ex, E.tGoo, E.bx, po, kc * pv, CR(sdd), C1(), S + n1, pv, N, 1, pv, err);
+  ex.tag = "ee_ring";
+  const int64_t ncol = kc * ov;
+  DBuf Xt = cbuf(ex, ncol * ov), R = cbuf(ex, ov * ncol);
+  k_gather_xtt<<<grid1d(ncol * ov, 256), 256, 0, ex.stream>>>(X + n1, N, kc, o, v, pv, Xt.c());
+  ADC_CHECK_LAUNCH();
+  tc_pack_B(ex, E.bx, Xt.c(), ncol, ov, ov, 0, 1, 1, false);
+  Xt.reset();
+  tc_gemm(ex, E.tW, E.bx, ov, ncol, C1(), C0(), R.c(), ncol, 1, 0, 1, err);
+  k_scatter_ring<<<grid1d(kc * po * pv, 256), 256, 0, ex.stream>>>(R.c(), kc, pio, pjo, pav, pbv, o, v, po, pv, sdd,
+                                                                   S + n1, N);
+  ADC_CHECK_LAUNCH();
+}
+
+void sigma_ee_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
+  Exec &ex = c->ex;
+  EEOps &E = *c->ee;
+  const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N;
+  const int64_t po = npairs(o), pv = npairs(v);
+  const bool third = (c->order == 3) && (c->x != 0.0);
+  const double sdd = (third && c->dd_order == 1) ? c->x : 0.0;
+  ee_struct_build(c, sdd != 0.0);
+  if (!E.tc_ready) ee_tc_build(c, sdd != 0.0);
+  TagScope tg(ex, "ee");
+  zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, E.MSS.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
+  ADC_CUDA(cudaMemset2DAsync(S + n1, N * sizeof(cplx), 0, n2 * sizeof(cplx), k, ex.stream));
+  diag_mul_add(ex, k, n2, c->d2.d(), X + n1, N, S + n1, N, 1.0);
+  int64_t per = std::max<int64_t>(o * o * pv, po * v * v);
+  if (sdd != 0.0) per = std::max<int64_t>(per, 3 * o * v * o * v);
+  per *= (int64_t)sizeof(cplx);
+  const int64_t kc = std::max<int64_t>(1, std::min<int64_t>(k, (4ll << 30) / std::max<int64_t>(per, 1)));
+  for (int64_t z0 = 0; z0 < k; z0 += kc) {
+    const int64_t kk = std::min(kc, k - z0);
+    ee_struct_apply_tc(c, X + z0 * N, S + z0 * N, kk, sdd);
+  }
+  int h = 0;
+  ADC_CUDA(cudaMemcpyAsync(&h, E.tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+  if (h != 0) {
+    fill_zero(ex, E.tcerr.p, sizeof(int));
+    throw Error(ADC_ERR_TIMEOUT, "tensor-core GEMM wait gave up (code " + std::to_string(h) + ")");
+  }
 }
 
 }  // namespace adc

@@ -93,8 +93,9 @@ void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision) {
   if (k <= 0) return;
   if (c->kind == ADC_EE) {
-    if (precision != ADC_PREC_FP64) throw Error(ADC_ERR_UNSUPPORTED, "EE-ADC runs FP64 sigma products only");
-    sigma_ee_fp64(c, X, S, k);
+    if (precision == ADC_PREC_FP64) sigma_ee_fp64(c, X, S, k);
+    else if (precision == ADC_PREC_BF16X3) sigma_ee_bf16x3(c, X, S, k);
+    else throw Error(ADC_ERR_ARG, "unknown precision");
   } else if (precision == ADC_PREC_FP64) sigma_fp64(c, X, S, k);
   else if (precision == ADC_PREC_BF16X3) sigma_bf16x3(c, X, S, k);
   else throw Error(ADC_ERR_ARG, "unknown precision");

@@ -1,6 +1,8 @@
-"""EE-ADC on the GPU (FP64) against the CPU oracle: sigma, diagonal, singles
-block and lowest roots (Sec. 2.1, Eq. 2 manifold). Tolerances as in
-test_gpu_parity: 1e-12 relative per sigma vector, 1e-8 Eh for eigenvalues."""
+"""EE-ADC on the GPU against the CPU oracle: sigma (FP64 and BF16x3), diagonal,
+singles block and lowest roots (Sec. 2.1, Eq. 2 manifold). Tolerances as in
+test_gpu_parity: 1e-12 relative per FP64 sigma vector, 1e-4 for the
+split-precision one, 1e-8 Eh for eigenvalues (also after the mixed-precision
+Davidson's FP64 refinement)."""
 import numpy as np
 import pytest
 
@@ -47,9 +49,8 @@ def test_ee_sigma_diag_block(gpu, o, v, Q, order, x, dd, seed):
         assert np.abs(d - dref).max() < 1e-12 * max(1.0, np.abs(dref).max())
         M = adc_ee.explicit_matrix(order, x, p.B, p.eps_occ, p.eps_vir, dd_order=dd)
         assert np.abs(ctx.main_block() - M[:n1, :n1]).max() < 1e-12 * np.abs(M).max()
-        with pytest.raises(gpu.AdcError) as e:
-            ctx.sigma(X, "bf16x3")
-        assert e.value.code == -6
+        Sm = ctx.sigma(X, "bf16x3")
+        assert _rel(Sm, ref).max() < 1e-4
 
 
 def test_ee_davidson_matches_dense(gpu):
@@ -62,3 +63,15 @@ def test_ee_davidson_matches_dense(gpu):
     assert rc == 0
     assert np.abs(om - w).max() < 1e-8
     assert np.linalg.norm(Y @ M.T - om[:, None] * Y, axis=1).max() < 1e-7
+
+
+def test_ee_mixed_davidson_refined(gpu):
+    o, v, Q = 4, 10, 16
+    p = make_problem(o, v, Q, seed=9, sigma=0.08, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    M = adc_ee.explicit_matrix(3, 0.4, p.B, p.eps_occ, p.eps_vir)
+    w = np.linalg.eigvalsh(M)[:4]
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=3, x=0.4) as ctx:
+        om, _, e64, st, rc = ctx.davidson(4, tol=1e-8, precision="bf16x3", want_vectors=False)
+    assert rc == 0 and np.all(e64 <= 1e-8)
+    assert np.abs(om - w).max() < 1e-8
+    assert st["sigma_calls_fp64"] < st["sigma_calls"]
