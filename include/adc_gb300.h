@@ -56,8 +56,13 @@ enum { ADC_IP = 0, ADC_EA = 1, ADC_EE = 2 };
  * ADC_PREC_BF16X3: the dense contractions on the tensor cores (tcgen05) with
  *   each FP64 operand split into two BF16 parts (hi + lo) and the three
  *   products hi*hi + hi*lo + lo*hi accumulated in FP32; complex arithmetic by
- *   the real 2x2 embedding. Diagonal terms stay FP64. */
-enum { ADC_PREC_FP64 = 0, ADC_PREC_BF16X3 = 1 };
+ *   the real 2x2 embedding. Diagonal terms stay FP64.
+ * ADC_PREC_BF16X6: as BF16X3 with three BF16 parts (hi, lo = bf16(x - hi),
+ *   lo2 = bf16(x - hi - lo)) and the six products of combined order up to
+ *   2^-16 (hh, hl, lh, hl2, ll, l2h): about 2^-24 per operand, limited by
+ *   the FP32 accumulation; twice the tensor-core work of BF16X3. Batches
+ *   (adc_batch_*) use BF16X3. */
+enum { ADC_PREC_FP64 = 0, ADC_PREC_BF16X3 = 1, ADC_PREC_BF16X6 = 2 };
 
 enum {
   ADC_OK = 0,
@@ -121,7 +126,7 @@ int adc_init(adc_ctx **ctx, const adc_c128 *B, int64_t naux,
 int adc_dims(const adc_ctx *ctx, int64_t *n1, int64_t *n2);
 
 /* S[r] = M X[r] for r < k (Eqs. 10-12). X, S: [k][N], host or device, not
- * overlapping. precision: ADC_PREC_FP64 or ADC_PREC_BF16X3. Uses scratch
+ * overlapping. precision: ADC_PREC_FP64, ADC_PREC_BF16X3 or ADC_PREC_BF16X6. Uses scratch
  * device memory owned by the context (grown on demand). */
 int adc_sigma(adc_ctx *ctx, const adc_c128 *X, adc_c128 *S, int64_t k,
               int precision);

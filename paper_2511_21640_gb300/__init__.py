@@ -21,9 +21,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libadc_gb300.so")
 
 ADC_IP, ADC_EA, ADC_EE = 0, 1, 2
-ADC_PREC_FP64, ADC_PREC_BF16X3 = 0, 1
+ADC_PREC_FP64, ADC_PREC_BF16X3, ADC_PREC_BF16X6 = 0, 1, 2
 KINDS = {"IP": ADC_IP, "EA": ADC_EA, "EE": ADC_EE}
-PRECISIONS = {"fp64": ADC_PREC_FP64, "bf16x3": ADC_PREC_BF16X3}
+PRECISIONS = {"fp64": ADC_PREC_FP64, "bf16x3": ADC_PREC_BF16X3, "bf16x6": ADC_PREC_BF16X6}
 ERRORS = {0: "ADC_OK", -1: "ADC_ERR_ARG", -2: "ADC_ERR_OOM", -3: "ADC_ERR_CUDA", -4: "ADC_ERR_NOCONV",
           -5: "ADC_ERR_TIMEOUT", -6: "ADC_ERR_UNSUPPORTED", -7: "ADC_ERR_STATE", -8: "ADC_ERR_NUMERIC"}
 
@@ -470,4 +470,4 @@ def launch_count():
 
 
 __all__ = ["Context", "Batch", "batch_plan", "batch_solve", "AdcError", "diag_gemm", "launch_count", "lib", "LIB_PATH", "ADC_IP", "ADC_EA", "ADC_EE",
-           "ADC_PREC_FP64", "ADC_PREC_BF16X3"]
+           "ADC_PREC_FP64", "ADC_PREC_BF16X3", "ADC_PREC_BF16X6"]

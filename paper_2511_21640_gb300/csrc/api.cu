@@ -220,7 +220,8 @@ int adc_dims(const adc_ctx *c, int64_t *n1, int64_t *n2) {
 int adc_sigma(adc_ctx *c, const adc_c128 *X, adc_c128 *S, int64_t k, int precision) {
   if (!c) return ADC_ERR_STATE;
   if (k < 0 || (k > 0 && (!X || !S))) return ADC_ERR_ARG;
-  if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3) return ADC_ERR_ARG;
+  if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3 && precision != ADC_PREC_BF16X6)
+    return ADC_ERR_ARG;
   if (k == 0) return ADC_OK;
   ADC_API_TRY
   const size_t bytes = (size_t)k * c->N * sizeof(cplx);

@@ -63,12 +63,13 @@ void first_order_amplitudes(adc_ctx *c);
 void second_order_amplitudes(adc_ctx *c, DBuf &G_vv, DBuf &Lad, DBuf &t2d, DBuf &t2s);
 void setup_ee(adc_ctx *c);
 void sigma_ee_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
-void sigma_ee_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
+void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg);
 void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
-void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
+// split-precision sigma on the tensor cores: nseg = 3 (BF16x3) or 6 (BF16x6) products
+void sigma_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg);
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision);
 void release_tc(adc_ctx *c);
-void tc_ensure(adc_ctx *c);  // split-precision operator copies, built on first use
+void tc_ensure(adc_ctx *c, int planes = 2);  // split-precision operator copies, built on first use
 cplx *scratch(adc_ctx *c, int64_t ncplx);
 // inside a batch (c->batch set): S = M X (split precision) of this problem's
 // block, executed together with the other problems' blocks; blocks until done

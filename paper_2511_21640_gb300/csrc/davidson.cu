@@ -295,7 +295,9 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   const int64_t N = c->N;
   ADC_REQUIRE(nroots >= 1 && nroots <= N, ADC_ERR_ARG, "nroots out of range");
   ADC_REQUIRE(tol > 0.0, ADC_ERR_ARG, "tol must be positive");
-  ADC_REQUIRE(precision == ADC_PREC_FP64 || precision == ADC_PREC_BF16X3, ADC_ERR_ARG, "precision");
+  ADC_REQUIRE(precision == ADC_PREC_FP64 || precision == ADC_PREC_BF16X3 || precision == ADC_PREC_BF16X6,
+              ADC_ERR_ARG, "precision");
+  const int mixed = (precision == ADC_PREC_FP64) ? ADC_PREC_BF16X3 : precision;
   const int kb = std::max(nroots, c->opts.block);
   int mmax = c->opts.max_subspace > 0 ? c->opts.max_subspace : std::max(8 * kb, 40);
   mmax = (int)std::min<int64_t>(std::min<int64_t>(mmax, N), 1024);
@@ -338,7 +340,7 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
     m0 = acc;
   }
   int phase = (precision == ADC_PREC_FP64) ? 2 : 0;  // 0 mixed, 1 refine, 2 plain FP64
-  int prec_new = (phase == 2) ? ADC_PREC_FP64 : ADC_PREC_BF16X3;
+  int prec_new = (phase == 2) ? ADC_PREC_FP64 : mixed;
   d.apply_sigma(d.V.c(), d.AV.c(), m0, prec_new);
   d.m = 0;
   d.nb = 0;
@@ -420,7 +422,7 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
     }
     ADC_CUDA(cudaMemcpyAsync(d.V.c() + (int64_t)d.m * N, d.T.c(), (int64_t)na * N * sizeof(cplx),
                              cudaMemcpyDeviceToDevice, ex.stream));
-    prec_new = (phase == 2) ? ADC_PREC_FP64 : ADC_PREC_BF16X3;
+    prec_new = (phase == 2) ? ADC_PREC_FP64 : mixed;
     d.apply_sigma_new(na, prec_new);
     d.extend_projection(d.m, na);
     d.m += na;

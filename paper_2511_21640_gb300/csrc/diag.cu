@@ -114,7 +114,7 @@ int diag_grouped(int64_t M, int64_t N, int64_t K, uint64_t seed, int reps, doubl
 
 extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_t seed, int reps,
                              double *rel_err, double *ms) {
-  if (M <= 0 || N <= 0 || K <= 0 || reps < 1 || which < 0 || which > 3) return ADC_ERR_ARG;
+  if (M <= 0 || N <= 0 || K <= 0 || reps < 1 || which < 0 || which > 4) return ADC_ERR_ARG;
   if (which == 3) return diag_grouped(M, N, K, seed, reps, rel_err, ms);
   Exec ex;
   try {
@@ -132,8 +132,8 @@ extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_
       auto run = [&]() {
         if (which == 0) {
           zgemm(ex, M, N, K, 1, C1(), A.c(), 0, K, 1, false, B.c(), 0, 1, K, false, C0(), C.c(), 0, N, 1);
-        } else if (which == 1) {
-          tc_gemm(ex, Ta, Tb, M, N, C1(), C0(), C.c(), N, 1, 0, 1, (int *)err.p);
+        } else if (which == 1 || which == 4) {
+          tc_gemm(ex, Ta, Tb, M, N, C1(), C0(), C.c(), N, 1, 0, 1, (int *)err.p, which == 4 ? 6 : 3);
         } else {
           TcJobDesc d;
           d.A = &Ta; d.B = &Tb; d.M = M; d.N = N; d.out = C.c(); d.s_m = N; d.s_nh = 1; d.n_in = 1;
@@ -141,8 +141,9 @@ extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_
         }
       };
       if (which >= 1) {
-        tc_pack_A(ex, Ta, A.c(), M, K, K, 1, false);
-        tc_pack_B(ex, Tb, B.c(), N, K, K, 0, 1, 1, false);
+        const int planes = which == 4 ? 3 : 2;
+        tc_pack_A(ex, Ta, A.c(), M, K, K, 1, false, planes);
+        tc_pack_B(ex, Tb, B.c(), N, K, K, 0, 1, 1, false, planes);
       }
       run();
       cudaEvent_t e0, e1;

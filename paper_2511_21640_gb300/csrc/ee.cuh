@@ -25,6 +25,7 @@ struct EEOps {
   TcMat tVaT, tVaC, tVb, tVbC, tGvv, tGoo, tW, bx;
   DBuf tcerr;
   bool tc_ready = false;
+  int tc_planes = 0;
 };
 // tensors of the EE term tables (v blocks cached in EEOps::eri)
 TermSource ee_source(adc_ctx *c);

@@ -417,19 +417,20 @@ void ee_struct_apply(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, double sdd)
 }
 
 // split-precision copies of the static operators (after ee_struct_build)
-static void ee_tc_build(adc_ctx *c, bool dd) {
+static void ee_tc_build(adc_ctx *c, bool dd, int planes) {
   Exec &ex = c->ex;
   EEOps &E = *c->ee;
   const int64_t o = c->o, v = c->v, po = npairs(o), pv = npairs(v), ov = o * v;
-  tc_pack_A(ex, E.tVaT, E.Va.c(), v, o * pv, 1, v, false);
-  tc_pack_A(ex, E.tVaC, E.Va.c(), o * pv, v, v, 1, true);
-  tc_pack_A(ex, E.tVb, E.Vb.c(), o, po * v, po * v, 1, false);
-  tc_pack_A(ex, E.tVbC, E.Vb.c(), po * v, o, 1, po * v, true);
+  tc_pack_A(ex, E.tVaT, E.Va.c(), v, o * pv, 1, v, false, planes);
+  tc_pack_A(ex, E.tVaC, E.Va.c(), o * pv, v, v, 1, true, planes);
+  tc_pack_A(ex, E.tVb, E.Vb.c(), o, po * v, po * v, 1, false, planes);
+  tc_pack_A(ex, E.tVbC, E.Vb.c(), po * v, o, 1, po * v, true, planes);
   if (dd) {
-    tc_pack_A(ex, E.tGvv, E.Gvv.c(), pv, pv, pv, 1, false);
-    tc_pack_A(ex, E.tGoo, E.Goo.c(), po, po, po, 1, false);
-    tc_pack_A(ex, E.tW, c->W.c(), ov, ov, ov, 1, false);
+    tc_pack_A(ex, E.tGvv, E.Gvv.c(), pv, pv, pv, 1, false, planes);
+    tc_pack_A(ex, E.tGoo, E.Goo.c(), po, po, po, 1, false, planes);
+    tc_pack_A(ex, E.tW, c->W.c(), ov, ov, ov, 1, false, planes);
   }
+  E.tc_planes = planes;
   E.tcerr = DBuf(ex, sizeof(int));
   fill_zero(ex, E.tcerr.p, sizeof(int));
   E.tc_ready = true;
@@ -437,7 +438,7 @@ static void ee_tc_build(adc_ctx *c, bool dd) {
 
 // ee_struct_apply with the GEMMs over the doubles on the tensor cores (BF16x3);
 // the separable second-order pieces (o x o and v x v intermediates) stay FP64
-static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, double sdd) {
+static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, double sdd, int nseg) {
   Exec &ex = c->ex;
   EEOps &E = *c->ee;
   const int64_t o = c->o, v = c->v, n1 = c->n1, N = c->N, po = npairs(o), pv = npairs(v), ov = o * v;
@@ -447,14 +448,15 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
   const bool second = (c->order == 3 && c->x != 0.0);
   const double x = second ? c->x : 0.0;
   int *err = (int *)E.tcerr.p;
+  const int planes = (nseg == 6) ? 3 : 2;
   TagScope tg(ex, "ee_coupling");
   {
     DBuf Xa = cbuf(ex, kc * o * o * pv);
     k_gather_xa<<<grid1d(kc * o * o * pv, 256), 256, 0, ex.stream>>>(X + n1, N, kc, pav, pbv, o, v, pv, Xa.c());
     ADC_CHECK_LAUNCH();
     // S1[z][i][a] += sum_(l,cd) Va[(l,cd)][a] Xa[z][i][(l,cd)]
-    tc_pack_B(ex, E.bx, Xa.c(), kc * o, o * pv, o * pv, 0, 1, 1, false);
-    tc_gemm(ex, E.tVaT, E.bx, v, kc * o, C1(), C1(), S, 1, N, v, o, err);
+    tc_pack_B(ex, E.bx, Xa.c(), kc * o, o * pv, o * pv, 0, 1, 1, false, planes);
+    tc_gemm(ex, E.tVaT, E.bx, v, kc * o, C1(), C1(), S, 1, N, v, o, err, nseg);
     DBuf U;
     if (second) {
       DBuf Y1 = cbuf(ex, kc * o * o);
@@ -465,8 +467,8 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
       zgemm(ex, kc, o * o, n1, 1, C1(), X, 0, N, 1, false, E.V1.c(), 0, o * o, 1, true, C0(), U.c(), 0, o * o, 1);
     }
     // F[z][i][(l,cd)] = sum_a conj(Va[(l,cd)][a]) X1[z][i][a]
-    tc_pack_B(ex, E.bx, X, kc * o, v, N, v, o, 1, false);
-    tc_gemm(ex, E.tVaC, E.bx, o * pv, kc * o, C1(), C0(), Xa.c(), 1, o * o * pv, o * pv, o, err);
+    tc_pack_B(ex, E.bx, X, kc * o, v, N, v, o, 1, false, planes);
+    tc_gemm(ex, E.tVaC, E.bx, o * pv, kc * o, C1(), C0(), Xa.c(), 1, o * o * pv, o * pv, o, err, nseg);
     if (second)
       zgemm(ex, o, o * pv, o, kc, CR(x), U.c(), o * o, o, 1, false, E.T1p.c(), 0, 1, o, true, C1(), Xa.c(),
             o * o * pv, o * pv, 1);
@@ -479,8 +481,8 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
                                                                      Xb.c());
     ADC_CHECK_LAUNCH();
     // S1[z][i][a] += sum_((kl),d) Vb[i][((kl),d)] XbT[z][a][((kl),d)]
-    tc_pack_B(ex, E.bx, Xb.c(), kc * v, po * v, po * v, 0, 1, 1, false);
-    tc_gemm(ex, E.tVb, E.bx, o, kc * v, C1(), C1(), S, v, N, 1, v, err);
+    tc_pack_B(ex, E.bx, Xb.c(), kc * v, po * v, po * v, 0, 1, 1, false, planes);
+    tc_gemm(ex, E.tVb, E.bx, o, kc * v, C1(), C1(), S, v, N, 1, v, err, nseg);
     DBuf U2;
     if (second) {
       DBuf Y2 = cbuf(ex, kc * v * v);
@@ -491,8 +493,8 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
       zgemm(ex, kc, v * v, n1, 1, C1(), X, 0, N, 1, false, E.V2.c(), 0, v * v, 1, true, C0(), U2.c(), 0, v * v, 1);
     }
     // G[z][((kl),d)][a] = sum_i conj(Vb[i][((kl),d)]) X1[z][i][a]  (reusing the buffer)
-    tc_pack_B(ex, E.bx, X, kc * v, o, N, 1, v, v, false);
-    tc_gemm(ex, E.tVbC, E.bx, po * v, kc * v, C1(), C0(), Xb.c(), v, po * v * v, 1, v, err);
+    tc_pack_B(ex, E.bx, X, kc * v, o, N, 1, v, v, false, planes);
+    tc_gemm(ex, E.tVbC, E.bx, po * v, kc * v, C1(), C0(), Xb.c(), v, po * v * v, 1, v, err, nseg);
     if (second)
       zgemm(ex, po * v, v, v, kc, CR(x), E.T2p.c(), 0, v, 1, true, U2.c(), v * v, 1, v, false, C1(), Xb.c(),
             po * v * v, v, 1);
@@ -501,32 +503,33 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
   }
   if (sdd == 0.0) return;
   ex.tag = "ee_ladder";
-  tc_pack_B(ex, E.bx, X + n1, kc * po, pv, N, pv, po, 1, false);
-  tc_gemm(ex, E.tGvv, E.bx, pv, kc * po, CR(sdd), C1(), S + n1, 1, N, pv, po, err);
-  tc_pack_B(ex, E.bx, X + n1, kc * pv, po, N, 1, pv, pv, false);
-  tc_gemm(ex, E.tGoo, E.bx, po, kc * pv, CR(sdd), C1(), S + n1, pv, N, 1, pv, err);
+  tc_pack_B(ex, E.bx, X + n1, kc * po, pv, N, pv, po, 1, false, planes);
+  tc_gemm(ex, E.tGvv, E.bx, pv, kc * po, CR(sdd), C1(), S + n1, 1, N, pv, po, err, nseg);
+  tc_pack_B(ex, E.bx, X + n1, kc * pv, po, N, 1, pv, pv, false, planes);
+  tc_gemm(ex, E.tGoo, E.bx, po, kc * pv, CR(sdd), C1(), S + n1, pv, N, 1, pv, err, nseg);
   ex.tag = "ee_ring";
   const int64_t ncol = kc * ov;
   DBuf Xt = cbuf(ex, ncol * ov), R = cbuf(ex, ov * ncol);
   k_gather_xtt<<<grid1d(ncol * ov, 256), 256, 0, ex.stream>>>(X + n1, N, kc, o, v, pv, Xt.c());
   ADC_CHECK_LAUNCH();
-  tc_pack_B(ex, E.bx, Xt.c(), ncol, ov, ov, 0, 1, 1, false);
+  tc_pack_B(ex, E.bx, Xt.c(), ncol, ov, ov, 0, 1, 1, false, planes);
   Xt.reset();
-  tc_gemm(ex, E.tW, E.bx, ov, ncol, C1(), C0(), R.c(), ncol, 1, 0, 1, err);
+  tc_gemm(ex, E.tW, E.bx, ov, ncol, C1(), C0(), R.c(), ncol, 1, 0, 1, err, nseg);
   k_scatter_ring<<<grid1d(kc * po * pv, 256), 256, 0, ex.stream>>>(R.c(), kc, pio, pjo, pav, pbv, o, v, po, pv, sdd,
                                                                    S + n1, N);
   ADC_CHECK_LAUNCH();
 }
 
-void sigma_ee_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
+void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
   Exec &ex = c->ex;
   EEOps &E = *c->ee;
   const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N;
   const int64_t po = npairs(o), pv = npairs(v);
   const bool third = (c->order == 3) && (c->x != 0.0);
   const double sdd = (third && c->dd_order == 1) ? c->x : 0.0;
+  const int planes = (nseg == 6) ? 3 : 2;
   ee_struct_build(c, sdd != 0.0);
-  if (!E.tc_ready) ee_tc_build(c, sdd != 0.0);
+  if (!E.tc_ready || E.tc_planes < planes) ee_tc_build(c, sdd != 0.0, planes);
   TagScope tg(ex, "ee");
   zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, E.MSS.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
   ADC_CUDA(cudaMemset2DAsync(S + n1, N * sizeof(cplx), 0, n2 * sizeof(cplx), k, ex.stream));
@@ -537,7 +540,7 @@ void sigma_ee_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
   const int64_t kc = std::max<int64_t>(1, std::min<int64_t>(k, (4ll << 30) / std::max<int64_t>(per, 1)));
   for (int64_t z0 = 0; z0 < k; z0 += kc) {
     const int64_t kk = std::min(kc, k - z0);
-    ee_struct_apply_tc(c, X + z0 * N, S + z0 * N, kk, sdd);
+    ee_struct_apply_tc(c, X + z0 * N, S + z0 * N, kk, sdd, nseg);
   }
   int h = 0;
   ADC_CUDA(cudaMemcpyAsync(&h, E.tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));

@@ -7,16 +7,17 @@
 
 namespace adc {
 
-static void build_cache(adc_ctx *c) {
+static void build_cache(adc_ctx *c, int planes) {
   Exec &ex = c->ex;
   auto &tc = *c->tc;
   const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2;
-  tc_pack_A(ex, tc.Cpl, c->Cpl.c(), n1, n2, n2, 1, false);
-  tc_pack_A(ex, tc.CplT, c->Cpl.c(), n2, n1, 1, n2, true);
+  tc.planes = planes;
+  tc_pack_A(ex, tc.Cpl, c->Cpl.c(), n1, n2, n2, 1, false, planes);
+  tc_pack_A(ex, tc.CplT, c->Cpl.c(), n2, n1, 1, n2, true, planes);
   if (c->order == 3 && c->x != 0.0) {
     const int64_t P = (c->kind == ADC_EA) ? npairs(v) : npairs(o);
-    tc_pack_A(ex, tc.Glad, c->Glad.c(), P, P, P, 1, false);
-    tc_pack_A(ex, tc.W, c->W.c(), o * v, o * v, o * v, 1, false);
+    tc_pack_A(ex, tc.Glad, c->Glad.c(), P, P, P, 1, false, planes);
+    tc_pack_A(ex, tc.W, c->W.c(), o * v, o * v, o * v, 1, false, planes);
   }
   tc.err = DBuf(ex, sizeof(int));
   fill_zero(ex, tc.err.p, sizeof(int));
@@ -25,14 +26,16 @@ static void build_cache(adc_ctx *c) {
 
 void release_tc(adc_ctx *c) { c->tc.reset(); }
 
-void tc_ensure(adc_ctx *c) {
+void tc_ensure(adc_ctx *c, int planes) {
+  if (c->tc && c->tc->ready && c->tc->planes < planes) c->tc.reset();  // rebuild with more planes
   if (!c->tc) c->tc.reset(new TcCache());
-  if (!c->tc->ready) build_cache(c);
+  if (!c->tc->ready) build_cache(c, planes);
 }
 
-void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
+void sigma_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
   Exec &ex = c->ex;
-  tc_ensure(c);
+  const int planes = (nseg == 6) ? 3 : 2;
+  tc_ensure(c, planes);
   auto &tc = *c->tc;
   int *err = (int *)tc.err.p;
   const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N;
@@ -43,36 +46,36 @@ void sigma_bf16x3(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
   zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, c->M11.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
   // S1 += Cpl X2  : out[c][r] = sum_K Cpl[c][K] X2[r][K]
   ex.tag = "coupling";
-  tc_pack_B(ex, tc.Bx, X + n1, k, n2, N, 0, 1, 1, false);
-  tc_gemm(ex, tc.Cpl, tc.Bx, n1, k, C1(), C1(), S, 1, N, 0, 1, err);
+  tc_pack_B(ex, tc.Bx, X + n1, k, n2, N, 0, 1, 1, false, planes);
+  tc_gemm(ex, tc.Cpl, tc.Bx, n1, k, C1(), C1(), S, 1, N, 0, 1, err, nseg);
   // S2 = Cpl^H X1 : out[K][r] = sum_c conj(Cpl[c][K]) X1[r][c]
-  tc_pack_B(ex, tc.Bx, X, k, n1, N, 0, 1, 1, false);
-  tc_gemm(ex, tc.CplT, tc.Bx, n2, k, C1(), C0(), S + n1, 1, N, 0, 1, err);
+  tc_pack_B(ex, tc.Bx, X, k, n1, N, 0, 1, 1, false, planes);
+  tc_gemm(ex, tc.CplT, tc.Bx, n2, k, C1(), C0(), S + n1, 1, N, 0, 1, err, nseg);
   diag_mul_add(ex, k, n2, c->d2.d(), X + n1, N, S + n1, N, 1.0);
   if (sat) {
     if (c->kind == ADC_EA) {
       const int64_t pv = npairs(v);
       // ladder: out[(ab)][(r,j)] = sum_(cd) Glad[(ab)][(cd)] X2[r][j][(cd)]
       ex.tag = "ladder";
-      tc_pack_B(ex, tc.Bx, X + n1, k * o, pv, N, pv, o, 1, false);
-      tc_gemm(ex, tc.Glad, tc.Bx, pv, k * o, CR(x), C1(), S + n1, 1, N, pv, o, err);
+      tc_pack_B(ex, tc.Bx, X + n1, k * o, pv, N, pv, o, 1, false, planes);
+      tc_gemm(ex, tc.Glad, tc.Bx, pv, k * o, CR(x), C1(), S + n1, 1, N, pv, o, err, nseg);
       // ring: T[r][j][a][b] = sum_(kc) W[(j,a)][(kc)] Xf[r][k][c][b]
       ex.tag = "ring";
       cplx *T = scratch(c, k * o * v * v);
-      tc_pack_B_ring(ex, tc.Bx, c, X, k);
-      tc_gemm(ex, tc.W, tc.Bx, o * v, k * v, C1(), C0(), T, v, o * v * v, 1, v, err);
+      tc_pack_B_ring(ex, tc.Bx, c, X, k, planes);
+      tc_gemm(ex, tc.W, tc.Bx, o * v, k * v, C1(), C0(), T, v, o * v * v, 1, v, err, nseg);
       pair_pack(ex, T, o * v * v, v * v, v, 1, 0, 1.0, k, o, v, 1, S + n1, N, pv, CR(-x), C1());
     } else {
       const int64_t po = npairs(o);
       // ladder: out[(ij)][(r,a)] = sum_(kl) Glad[(ij)][(kl)] X2[r][(kl)][a]
       ex.tag = "ladder";
-      tc_pack_B(ex, tc.Bx, X + n1, k * v, po, N, 1, v, v, false);
-      tc_gemm(ex, tc.Glad, tc.Bx, po, k * v, CR(x), C1(), S + n1, v, N, 1, v, err);
+      tc_pack_B(ex, tc.Bx, X + n1, k * v, po, N, 1, v, v, false, planes);
+      tc_gemm(ex, tc.Glad, tc.Bx, po, k * v, CR(x), C1(), S + n1, v, N, 1, v, err, nseg);
       // ring: T[r][j][a][i] = -sum_(kb) W[(j,a)][(kb)] Xf[r][i][k][b]
       ex.tag = "ring";
       cplx *T = scratch(c, k * o * v * o);
-      tc_pack_B_ring(ex, tc.Bx, c, X, k);
-      tc_gemm(ex, tc.W, tc.Bx, o * v, k * o, CR(-1.0), C0(), T, o, o * v * o, 1, o, err);
+      tc_pack_B_ring(ex, tc.Bx, c, X, k, planes);
+      tc_gemm(ex, tc.W, tc.Bx, o * v, k * o, CR(-1.0), C0(), T, o, o * v * o, 1, o, err, nseg);
       pair_pack(ex, T, o * v * o, 0, 1, v * o, o, 1.0, k, 1, o, v, S + n1, N, 0, CR(x), C1());
     }
   }

@@ -133,7 +133,8 @@ struct TcLayout {
 template <int BN, int ST>
 __global__ void __launch_bounds__(192, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
-          const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, int M,
+          const __grid_constant__ CUtensorMap mAl2, const __grid_constant__ CUtensorMap mBh,
+          const __grid_constant__ CUtensorMap mBl, const __grid_constant__ CUtensorMap mBl2, int nseg, int M,
           int N2, int kps, int kb_per_split, cplx *out, int64_t s_m, int64_t s_nh, int64_t s_nl,
           int64_t n_in, cplx alpha, cplx beta, float *part, int *err) {
   using L = TcLayout<BN, ST>;
@@ -148,7 +149,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * BN;
   const int split = blockIdx.z;
-  const int total_kb = 3 * kps;
+  const int total_kb = nseg * kps;
   const int kb_beg = split * kb_per_split;
   const int kb_end = min(total_kb, kb_beg + kb_per_split);
   const int nkb = kb_end - kb_beg;
@@ -190,8 +191,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
       const uint32_t fb = smem_u32(&full[s]);
       mbar_expect_tx(fb, L::STAGE);
       uint8_t *sa = smem + s * L::STAGE;
-      tma_load_2d(smem_u32(sa), seg == 2 ? &mAl : &mAh, kx, m0, fb);
-      tma_load_2d(smem_u32(sa + L::A_BYTES), seg == 1 ? &mBl : &mBh, kx, n0, fb);
+      // segments: (hi,hi) (hi,lo) (lo,hi) (hi,lo2) (lo,lo) (lo2,hi)
+      const CUtensorMap *am = (seg == 2 || seg == 4) ? &mAl : (seg == 5 ? &mAl2 : &mAh);
+      const CUtensorMap *bm = (seg == 1 || seg == 4) ? &mBl : (seg == 3 ? &mBl2 : &mBh);
+      tma_load_2d(smem_u32(sa), am, kx, m0, fb);
+      tma_load_2d(smem_u32(sa + L::A_BYTES), bm, kx, n0, fb);
       issued = i + 1;
     }
     if (*abort_flag) {
@@ -289,15 +293,19 @@ __global__ void k_tc_reduce(const float *__restrict__ part, int ksplit, int64_t 
 }
 
 // ---------------------------------------------------------------- operand packing
-__device__ __forceinline__ void split_store(double x, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+// hi = bf16(x), lo = bf16(x - hi), lo2 = bf16(x - hi - lo) (the differences are exact in FP64)
+__device__ __forceinline__ void split_store(double x, __nv_bfloat16 *hi, __nv_bfloat16 *lo, __nv_bfloat16 *lo2) {
   __nv_bfloat16 h = __double2bfloat16(x);
   *hi = h;
-  *lo = __double2bfloat16(x - (double)__bfloat162float(h));
+  const double r = x - (double)__bfloat162float(h);
+  __nv_bfloat16 l = __double2bfloat16(r);
+  *lo = l;
+  if (lo2) *lo2 = __double2bfloat16(r - (double)__bfloat162float(l));
 }
 
 // A rows: [Re | Im] (conj negates Im); element (m, k) at src[m*s_m + k*s_k]
 __global__ void k_emb_A(const cplx *__restrict__ src, int64_t M, int64_t K, int64_t s_m, int64_t s_k,
-                        int conj, int64_t kp, __nv_bfloat16 *hi, __nv_bfloat16 *lo) {
+                        int conj, int64_t kp, __nv_bfloat16 *hi, __nv_bfloat16 *lo, __nv_bfloat16 *lo2) {
   const int64_t total = M * kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -306,8 +314,8 @@ __global__ void k_emb_A(const cplx *__restrict__ src, int64_t M, int64_t K, int6
     if (k < K) x = src[m * s_m + k * s_k];
     const double im = conj ? -x.y : x.y;
     const int64_t base = m * 2 * kp;
-    split_store(x.x, hi + base + k, lo + base + k);
-    split_store(im, hi + base + kp + k, lo + base + kp + k);
+    split_store(x.x, hi + base + k, lo + base + k, lo2 ? lo2 + base + k : nullptr);
+    split_store(im, hi + base + kp + k, lo + base + kp + k, lo2 ? lo2 + base + kp + k : nullptr);
   }
 }
 
@@ -342,7 +350,7 @@ struct BSrc {
 
 // B rows: row 2n = [Re | -Im], row 2n+1 = [Im | Re] (conj negates Im first)
 __global__ void k_emb_B(BSrc src, int64_t Nc, int64_t K, int conj, int64_t kp, __nv_bfloat16 *hi,
-                        __nv_bfloat16 *lo) {
+                        __nv_bfloat16 *lo, __nv_bfloat16 *lo2) {
   const int64_t total = Nc * kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -351,10 +359,10 @@ __global__ void k_emb_B(BSrc src, int64_t Nc, int64_t K, int conj, int64_t kp, _
     if (k < K) x = src.get(n, k);
     const double im = conj ? -x.y : x.y;
     const int64_t r0 = (2 * n) * 2 * kp, r1 = (2 * n + 1) * 2 * kp;
-    split_store(x.x, hi + r0 + k, lo + r0 + k);
-    split_store(-im, hi + r0 + kp + k, lo + r0 + kp + k);
-    split_store(im, hi + r1 + k, lo + r1 + k);
-    split_store(x.x, hi + r1 + kp + k, lo + r1 + kp + k);
+    split_store(x.x, hi + r0 + k, lo + r0 + k, lo2 ? lo2 + r0 + k : nullptr);
+    split_store(-im, hi + r0 + kp + k, lo + r0 + kp + k, lo2 ? lo2 + r0 + kp + k : nullptr);
+    split_store(im, hi + r1 + k, lo + r1 + k, lo2 ? lo2 + r1 + k : nullptr);
+    split_store(x.x, hi + r1 + kp + k, lo + r1 + kp + k, lo2 ? lo2 + r1 + kp + k : nullptr);
   }
 }
 
@@ -383,7 +391,7 @@ int g_sms = 0;
 
 template <int BN, int ST>
 void launch_tc(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N2, cplx alpha, cplx beta,
-               cplx *out, int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err) {
+               cplx *out, int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, int nseg) {
   using L = TcLayout<BN, ST>;
   static bool attr = false;
   if (!attr) {
@@ -396,14 +404,21 @@ void launch_tc(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N2, 
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_sms <= 0) g_sms = 148;
   }
-  CUtensorMap mAh, mAl, mBh, mBl;
+  CUtensorMap mAh, mAl, mAl2, mBh, mBl, mBl2;
   const int64_t kp2 = 2 * A.kp;
   make_map(&mAh, A.hi.p, A.rows, kp2, TC_BM);
   make_map(&mAl, A.lo.p, A.rows, kp2, TC_BM);
   make_map(&mBh, B.hi.p, B.rows, kp2, BN);
   make_map(&mBl, B.lo.p, B.rows, kp2, BN);
+  if (nseg == 6) {
+    make_map(&mAl2, A.lo2.p, A.rows, kp2, TC_BM);
+    make_map(&mBl2, B.lo2.p, B.rows, kp2, BN);
+  } else {
+    mAl2 = mAl;  // not read with three segments
+    mBl2 = mBl;
+  }
   const int kps = (int)(kp2 / TC_BK);
-  const int total_kb = 3 * kps;
+  const int total_kb = nseg * kps;
   const int64_t tiles = ((N2 + BN - 1) / BN) * ((M + TC_BM - 1) / TC_BM);
   int ksplit = 1;
   if (tiles < g_sms) {
@@ -418,8 +433,10 @@ void launch_tc(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N2, 
   DBuf part;
   if (ksplit > 1) part = DBuf(ex, (size_t)ksplit * M * N2 * sizeof(float));
   const int64_t Kc = A.kreal > 0 ? A.kreal : A.kp;
-  int pr = ex.prof_begin("tc_gemm_bf16x3", 8.0 * (double)M * (double)(N2 / 2) * (double)Kc);
-  k_tc_gemm<BN, ST><<<grid, 192, L::SMEM, ex.stream>>>(mAh, mAl, mBh, mBl, (int)M, (int)N2, kps, kb_per_split,
+  int pr = ex.prof_begin(nseg == 6 ? "tc_gemm_bf16x6" : "tc_gemm_bf16x3",
+                         8.0 * (double)M * (double)(N2 / 2) * (double)Kc);
+  k_tc_gemm<BN, ST><<<grid, 192, L::SMEM, ex.stream>>>(mAh, mAl, mAl2, mBh, mBl, mBl2, nseg, (int)M, (int)N2, kps,
+                                                      kb_per_split,
                                                       out, s_m, s_nh, s_nl, n_in, alpha, beta,
                                                       ksplit > 1 ? (float *)part.p : nullptr, err);
   ADC_CHECK_LAUNCH();
@@ -620,62 +637,69 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
 
 }  // namespace
 
-void tc_pack_A(Exec &ex, TcMat &dst, const cplx *src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, bool conj) {
+static void alloc_planes(Exec &ex, TcMat &dst, size_t bytes, int planes) {
+  if (dst.hi.bytes < bytes || (planes == 3 && dst.lo2.bytes < bytes)) {
+    dst.hi.reset(); dst.lo.reset(); dst.lo2.reset();
+    dst.hi = DBuf(ex, bytes);
+    dst.lo = DBuf(ex, bytes);
+    if (planes == 3) dst.lo2 = DBuf(ex, bytes);
+  }
+  dst.planes = (planes == 3 && dst.lo2.p) ? 3 : 2;
+}
+
+void tc_pack_A(Exec &ex, TcMat &dst, const cplx *src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, bool conj,
+               int planes) {
   dst.rows = M;
   dst.kreal = K;
   dst.kp = (K + TC_BK - 1) / TC_BK * TC_BK;
   if (dst.kp == 0) dst.kp = TC_BK;
   const size_t bytes = (size_t)M * 2 * dst.kp * sizeof(__nv_bfloat16);
-  if (dst.hi.bytes < bytes) {
-    dst.hi.reset(); dst.lo.reset();
-    dst.hi = DBuf(ex, bytes);
-    dst.lo = DBuf(ex, bytes);
-  }
+  alloc_planes(ex, dst, bytes, planes);
   k_emb_A<<<grid1d(M * dst.kp, 256), 256, 0, ex.stream>>>(src, M, K, s_m, s_k, conj ? 1 : 0, dst.kp,
-                                                          (__nv_bfloat16 *)dst.hi.p, (__nv_bfloat16 *)dst.lo.p);
+                                                          (__nv_bfloat16 *)dst.hi.p, (__nv_bfloat16 *)dst.lo.p,
+                                                          planes == 3 ? (__nv_bfloat16 *)dst.lo2.p : nullptr);
   ADC_CHECK_LAUNCH();
 }
 
-static void pack_B_impl(Exec &ex, TcMat &dst, const BSrc &s, int64_t Nc, int64_t K, bool conj) {
+static void pack_B_impl(Exec &ex, TcMat &dst, const BSrc &s, int64_t Nc, int64_t K, bool conj, int planes) {
   dst.rows = 2 * Nc;
   dst.kreal = K;
   dst.kp = (K + TC_BK - 1) / TC_BK * TC_BK;
   if (dst.kp == 0) dst.kp = TC_BK;
   const size_t bytes = (size_t)dst.rows * 2 * dst.kp * sizeof(__nv_bfloat16);
-  if (dst.hi.bytes < bytes) {
-    dst.hi.reset(); dst.lo.reset();
-    dst.hi = DBuf(ex, bytes);
-    dst.lo = DBuf(ex, bytes);
-  }
+  alloc_planes(ex, dst, bytes, planes);
   k_emb_B<<<grid1d(Nc * dst.kp, 256), 256, 0, ex.stream>>>(s, Nc, K, conj ? 1 : 0, dst.kp,
-                                                           (__nv_bfloat16 *)dst.hi.p, (__nv_bfloat16 *)dst.lo.p);
+                                                           (__nv_bfloat16 *)dst.hi.p, (__nv_bfloat16 *)dst.lo.p,
+                                                           planes == 3 ? (__nv_bfloat16 *)dst.lo2.p : nullptr);
   ADC_CHECK_LAUNCH();
 }
 
 void tc_pack_B(Exec &ex, TcMat &dst, const cplx *src, int64_t Nc, int64_t K, int64_t s_nh, int64_t s_nl,
-               int64_t n_in, int64_t s_k, bool conj) {
+               int64_t n_in, int64_t s_k, bool conj, int planes) {
   BSrc s{src, 0, s_nh, s_nl, n_in, s_k, 0, 0, 0, 0};
-  pack_B_impl(ex, dst, s, Nc, K, conj);
+  pack_B_impl(ex, dst, s, Nc, K, conj, planes);
 }
 
-void tc_pack_B_ring(Exec &ex, TcMat &dst, const adc_ctx *c, const cplx *X, int64_t k) {
+void tc_pack_B_ring(Exec &ex, TcMat &dst, const adc_ctx *c, const cplx *X, int64_t k, int planes) {
   BSrc s{X, c->kind == ADC_EA ? 1 : 2, 0, 0, 1, 0, c->o, c->v, c->N, c->n1};
   const int64_t Nc = (c->kind == ADC_EA) ? k * c->v : k * c->o;
-  pack_B_impl(ex, dst, s, Nc, c->o * c->v, false);
+  pack_B_impl(ex, dst, s, Nc, c->o * c->v, false, planes);
 }
 
 void tc_gemm(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N, cplx alpha, cplx beta, cplx *out,
-             int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err) {
+             int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, int nseg) {
   ADC_REQUIRE(A.kp == B.kp, ADC_ERR_ARG, "tc_gemm: inner sizes differ");
   ADC_REQUIRE(A.rows >= M && B.rows >= 2 * N, ADC_ERR_ARG, "tc_gemm: operand rows");
+  ADC_REQUIRE(nseg == 3 || (nseg == 6 && A.planes == 3 && B.planes == 3), ADC_ERR_ARG,
+              "tc_gemm: six products need three planes on both operands");
   if (M <= 0 || N <= 0) return;
   ADC_REQUIRE(M < (1ll << 31) && 2 * N < (1ll << 31), ADC_ERR_UNSUPPORTED, "tc_gemm: size");
   if (n_in <= 0) n_in = 1;
   const int64_t N2 = 2 * N;
-  if (N2 <= 32) launch_tc<32, 8>(ex, A, B, M, N2, alpha, beta, out, s_m, s_nh, s_nl, n_in, err);
-  else if (N2 <= 64) launch_tc<64, 8>(ex, A, B, M, N2, alpha, beta, out, s_m, s_nh, s_nl, n_in, err);
-  else if (N2 <= 128) launch_tc<128, 6>(ex, A, B, M, N2, alpha, beta, out, s_m, s_nh, s_nl, n_in, err);
-  else launch_tc<256, 4>(ex, A, B, M, N2, alpha, beta, out, s_m, s_nh, s_nl, n_in, err);
+  if (N2 <= 32) launch_tc<32, 8>(ex, A, B, M, N2, alpha, beta, out, s_m, s_nh, s_nl, n_in, err, nseg);
+  else if (N2 <= 64) launch_tc<64, 8>(ex, A, B, M, N2, alpha, beta, out, s_m, s_nh, s_nl, n_in, err, nseg);
+  else if (N2 <= 128) launch_tc<128, 6>(ex, A, B, M, N2, alpha, beta, out, s_m, s_nh, s_nl, n_in, err, nseg);
+  else launch_tc<256, 4>(ex, A, B, M, N2, alpha, beta, out, s_m, s_nh, s_nl, n_in, err, nseg);
 }
 
 }  // namespace adc

@@ -10,23 +10,29 @@ struct adc_ctx;
 
 namespace adc {
 
-// An operand in the real embedding, split into BF16 hi and lo planes of shape
-// [rows][2*kp] (kp = K rounded up to 64). For A, rows = M; for B, rows = 2N.
+// An operand in the real embedding, split into BF16 planes of shape
+// [rows][2*kp] (kp = K rounded up to 64): hi = bf16(x), lo = bf16(x - hi) and,
+// for the six-product split, lo2 = bf16(x - hi - lo). For A, rows = M; for B,
+// rows = 2N.
 struct TcMat {
-  DBuf hi, lo;
+  DBuf hi, lo, lo2;
+  int planes = 2;
   int64_t rows = 0, kp = 0, kreal = 0;
 };
 
-// A[m][k] = op(src[m*s_m + k*s_k]) (op = conj when conj is set)
-void tc_pack_A(Exec &ex, TcMat &dst, const cplx *src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, bool conj);
+// A[m][k] = op(src[m*s_m + k*s_k]) (op = conj when conj is set); planes 2 or 3
+void tc_pack_A(Exec &ex, TcMat &dst, const cplx *src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, bool conj,
+               int planes = 2);
 // B[n][k] = op(src[(n / n_in)*s_nh + (n % n_in)*s_nl + k*s_k]), Nc complex rows
 void tc_pack_B(Exec &ex, TcMat &dst, const cplx *src, int64_t Nc, int64_t K, int64_t s_nh, int64_t s_nl,
-               int64_t n_in, int64_t s_k, bool conj);
+               int64_t n_in, int64_t s_k, bool conj, int planes = 2);
 // B operand of the ring term, gathered from the packed satellite block of X
-void tc_pack_B_ring(Exec &ex, TcMat &dst, const adc_ctx *c, const cplx *X, int64_t k);
-// out[m][n] (n = nh*n_in + nl at m*s_m + nh*s_nh + nl*s_nl) = alpha * A B^T + beta * out
+void tc_pack_B_ring(Exec &ex, TcMat &dst, const adc_ctx *c, const cplx *X, int64_t k, int planes = 2);
+// out[m][n] (n = nh*n_in + nl at m*s_m + nh*s_nh + nl*s_nl) = alpha * A B^T + beta * out,
+// with nseg = 3 products (hi hi, hi lo, lo hi) or 6 (plus hi lo2, lo lo, lo2 hi;
+// both operands need three planes)
 void tc_gemm(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N, cplx alpha, cplx beta, cplx *out,
-             int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err);
+             int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, int nseg = 3);
 
 // ---- grouped persistent launch (several problems and terms in one kernel)
 constexpr int TC_BNMAX = 256;
@@ -78,6 +84,7 @@ int tc_autotune_bn(Exec &ex, const TcJobDesc &d, int *err);
 int tc_autotune_table(int64_t *out, int cap);
 
 struct TcCache {
+  int planes = 2;            // BF16 planes of the copies (3 for the six-product split)
   TcMat Glad, W, Cpl, CplT;  // static operators (A side)
   TcMat Bx;                  // per-call B operand
   DBuf err;                  // device error word of the tensor-core kernels

@@ -51,6 +51,8 @@ def test_ee_sigma_diag_block(gpu, o, v, Q, order, x, dd, seed):
         assert np.abs(ctx.main_block() - M[:n1, :n1]).max() < 1e-12 * np.abs(M).max()
         Sm = ctx.sigma(X, "bf16x3")
         assert _rel(Sm, ref).max() < 1e-4
+        Sm6 = ctx.sigma(X, "bf16x6")
+        assert _rel(Sm6, ref).max() < 2e-6
 
 
 def test_ee_davidson_matches_dense(gpu):
@@ -65,13 +67,14 @@ def test_ee_davidson_matches_dense(gpu):
     assert np.linalg.norm(Y @ M.T - om[:, None] * Y, axis=1).max() < 1e-7
 
 
-def test_ee_mixed_davidson_refined(gpu):
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+def test_ee_mixed_davidson_refined(gpu, prec):
     o, v, Q = 4, 10, 16
     p = make_problem(o, v, Q, seed=9, sigma=0.08, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
     M = adc_ee.explicit_matrix(3, 0.4, p.B, p.eps_occ, p.eps_vir)
     w = np.linalg.eigvalsh(M)[:4]
     with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=3, x=0.4) as ctx:
-        om, _, e64, st, rc = ctx.davidson(4, tol=1e-8, precision="bf16x3", want_vectors=False)
+        om, _, e64, st, rc = ctx.davidson(4, tol=1e-8, precision=prec, want_vectors=False)
     assert rc == 0 and np.all(e64 <= 1e-8)
     assert np.abs(om - w).max() < 1e-8
     assert st["sigma_calls_fp64"] < st["sigma_calls"]

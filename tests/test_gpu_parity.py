@@ -51,6 +51,15 @@ def test_bf16x3_gemm(gpu, M, N, K):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 16, 64), (200, 40, 1000), (129, 130, 70), (1000, 300, 5000),
+                                   (64, 8, 20000)])
+def test_bf16x6_gemm(gpu, M, N, K):
+    """Six-product split: about 2^-24 per operand, FP32 accumulation."""
+    err, ms = gpu.diag_gemm(4, M, N, K, seed=5)
+    err3, _ = gpu.diag_gemm(1, M, N, K, seed=5)
+    assert err < 2e-6 and err < 0.1 * err3, (err, err3)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 16, 64), (200, 40, 1000), (129, 130, 70), (1000, 300, 5000),
                                    (64, 8, 20000), (300, 1, 129)])
 def test_grouped_gemm_one_job(gpu, M, N, K):
     """The grouped persistent launch with an autotuned tile width, one job."""
@@ -96,6 +105,8 @@ def test_sigma_parity(gpu, kind, o, v, Q, order, x, seed):
         assert _rel(Sd, ref[1:2]).max() < 1e-12
         Sm = ctx.sigma(X, "bf16x3")
         assert _rel(Sm, ref).max() < 1e-4
+        Sm6 = ctx.sigma(X, "bf16x6")
+        assert _rel(Sm6, ref).max() < 2e-6
         d = ctx.diagonal()
         dref = oadc.diagonal_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, amp=amp)
         assert np.abs(d - dref).max() < 1e-12 * max(1.0, np.abs(dref).max())
@@ -145,13 +156,14 @@ def test_mixed_davidson_preconditioned_corrections_in_subspace(gpu):
         assert np.abs(om - w).max() < 1e-8
 
 
-@pytest.mark.parametrize("kind,o,v,Q,x", [("EA", 6, 30, 64, 0.5), ("IP", 7, 26, 50, 0.5)])
-def test_mixed_davidson_refined(gpu, kind, o, v, Q, x):
+@pytest.mark.parametrize("kind,o,v,Q,x,prec", [("EA", 6, 30, 64, 0.5, "bf16x3"), ("IP", 7, 26, 50, 0.5, "bf16x3"),
+                                              ("EA", 6, 30, 64, 0.5, "bf16x6")])
+def test_mixed_davidson_refined(gpu, kind, o, v, Q, x, prec):
     p = make_problem(o, v, Q, seed=21, sigma=0.06, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
     M = oadc.explicit_matrix(kind, 3, x, p.B, p.eps_occ, p.eps_vir)
     w = np.linalg.eigvalsh(M)[:4]
     with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=3, x=x) as ctx:
-        om, Y, e64, st, rc = ctx.davidson(4, tol=1e-7, precision="bf16x3")
+        om, Y, e64, st, rc = ctx.davidson(4, tol=1e-7, precision=prec)
         assert rc == 0
         assert np.abs(om - w).max() < 1e-6
         assert np.all(e64 <= 1e-7)
