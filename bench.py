@@ -264,13 +264,13 @@ def run_ee(args, cfgname):
     ctx = adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=cfg["order"], x=x)
     init_s = time.perf_counter() - t0
     log(f"init {init_s:.1f} s, N = {ctx.N}")
-    ctx.sigma(random_vectors(ctx.N, 1, seed=3), "bf16x3")  # builds the split-precision operators
+    ctx.sigma(random_vectors(ctx.N, 1, seed=3), args.mixed)  # builds the split-precision operators
     clocks = Clocks()
     clocks.start()
     ctx.profile(True)
     l0 = adcgpu.launch_count()
     t1 = time.perf_counter()
-    om, Y, e64, st, rc = ctx.davidson(nroots, tol=tol, max_iter=400, precision="bf16x3")
+    om, Y, e64, st, rc = ctx.davidson(nroots, tol=tol, max_iter=400, precision=args.mixed)
     solve_s = time.perf_counter() - t1
     launches = adcgpu.launch_count() - l0
     prof = ctx.profile_read()
@@ -287,7 +287,7 @@ def run_ee(args, cfgname):
                 "max_eig_diff_vs_mixed": float(np.abs(om64 - om).max()), "rc": int(rc6)}
     Xs = random_vectors(ctx.N, nroots, seed=7)
     sig = {}
-    for prec in ("bf16x3", "fp64"):
+    for prec in (args.mixed, "fp64"):
         ctx.sigma(Xs, prec)
         ctx.profile(True)
         t2 = time.perf_counter()
@@ -296,25 +296,31 @@ def run_ee(args, cfgname):
         sp = ctx.profile_read()
         ctx.profile(False)
         sig[prec] = {"ms": 1e3 * ts, "flops_timed_kernels": sum(e["flops"] for e in sp.values())}
-    rng = np.random.default_rng(11)
-    wts = rng.standard_normal(nroots)
-    t3 = time.perf_counter()
-    gB, geo, gev, gx = ctx.sigma_adjoint(Y, wts)
-    adj_s = time.perf_counter() - t3
-    log(f"adjoint {adj_s:.1f} s")
-    ctx.close()
-    D = (random_hermitian_direction(p.B.shape, 12), rng.standard_normal(o), rng.standard_normal(v), 0.7)
-    pred = directional(gB, geo, gev, gx, D)
-    h = 1e-5
-    ws = []
-    for sgn in (1, -1):
-        with adcgpu.Context(p.B + sgn * h * D[0], p.eps_occ + sgn * h * D[1], p.eps_vir + sgn * h * D[2],
-                            kind="EE", order=cfg["order"], x=x + sgn * h * D[3]) as c2:
-            w, _, _, _, rcf = c2.davidson(nroots, tol=min(tol, 1e-8), max_iter=400, precision="bf16x3",
-                                          want_vectors=False)
-            ws.append(w)
-    fd = float(np.dot(wts, (ws[0] - ws[1]) / (2 * h)))
-    log(f"gradient check: adjoint {pred:.10e} fd {fd:.10e}")
+    grad = None
+    if args.no_gradient:
+        ctx.close()
+    else:
+        rng = np.random.default_rng(11)
+        wts = rng.standard_normal(nroots)
+        t3 = time.perf_counter()
+        gB, geo, gev, gx = ctx.sigma_adjoint(Y, wts)
+        adj_s = time.perf_counter() - t3
+        log(f"adjoint {adj_s:.1f} s")
+        ctx.close()
+        D = (random_hermitian_direction(p.B.shape, 12), rng.standard_normal(o), rng.standard_normal(v), 0.7)
+        pred = directional(gB, geo, gev, gx, D)
+        h = 1e-5
+        ws = []
+        for sgn in (1, -1):
+            with adcgpu.Context(p.B + sgn * h * D[0], p.eps_occ + sgn * h * D[1], p.eps_vir + sgn * h * D[2],
+                                kind="EE", order=cfg["order"], x=x + sgn * h * D[3]) as c2:
+                w, _, _, _, rcf = c2.davidson(nroots, tol=min(tol, 1e-8), max_iter=400, precision=args.mixed,
+                                              want_vectors=False)
+                ws.append(w)
+        fd = float(np.dot(wts, (ws[0] - ws[1]) / (2 * h)))
+        log(f"gradient check: adjoint {pred:.10e} fd {fd:.10e}")
+        grad = {"adjoint_s": adj_s, "directional_adjoint": pred, "directional_fd": fd,
+                "rel_diff": abs(pred - fd) / max(1.0, abs(fd)), "fd_step": h, "weights": [float(w) for w in wts]}
     by = sorted(((k, e) for k, e in prof.items() if e["launches"] > 0), key=lambda t: -t[1]["total_ms"])
     pk, pk_kind = peaks()
 
@@ -346,11 +352,9 @@ def run_ee(args, cfgname):
                            "sigma_calls_fp64": st["sigma_calls_fp64"], "rc": int(rc),
                            "omega": [float(w) for w in om], "err64": [float(e) for e in e64]},
         "fp64_davidson": fp64,
-        "sigma": {"vectors": nroots, "bf16x3_ms": sig["bf16x3"]["ms"], "fp64_ms": sig["fp64"]["ms"],
-                  "speedup": sig["fp64"]["ms"] / sig["bf16x3"]["ms"]},
-        "gradient": {"adjoint_s": adj_s, "directional_adjoint": pred, "directional_fd": fd,
-                     "rel_diff": abs(pred - fd) / max(1.0, abs(fd)), "fd_step": h,
-                     "weights": [float(w) for w in wts]},
+        "sigma": {"vectors": nroots, "mixed": args.mixed, "mixed_ms": sig[args.mixed]["ms"],
+                  "fp64_ms": sig["fp64"]["ms"], "speedup": sig["fp64"]["ms"] / sig[args.mixed]["ms"]},
+        "gradient": grad,
         "init_s": init_s, "e2e": None, "cpu_baseline": None,
     }
     print(json.dumps(line))
@@ -400,6 +404,9 @@ def main():
     ap.add_argument("--config", default="ea2x3_o40_v200_q1200")
     ap.add_argument("--tol", type=float, default=None)
     ap.add_argument("--no-fp64-davidson", action="store_true")
+    ap.add_argument("--no-gradient", action="store_true", help="EE workloads: skip the adjoint and its check")
+    ap.add_argument("--mixed", default="bf16x3", choices=["bf16x3", "bf16x6"],
+                    help="split precision of the mixed Davidson")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=6)
     ap.add_argument("--ref-sigma-vectors-per-root", type=float, default=8.0)
@@ -458,7 +465,7 @@ def main():
         return ctx.davidson(nroots, tol=t, max_iter=300, precision=prec, want_vectors=False)
 
     for _ in range(args.warmup):
-        om, _, e64, st, rc = solve("bf16x3")
+        om, _, e64, st, rc = solve(args.mixed)
         log("warmup solve", st)
     # ---- timed region
     clocks = Clocks()
@@ -474,7 +481,7 @@ def main():
     ev0.record(stream)
     stats = []
     for _ in range(args.steps):
-        om, _, e64, st, rc = solve("bf16x3")
+        om, _, e64, st, rc = solve(args.mixed)
         stats.append(st)
     ev1.record(stream)
     nvtx_range("timed", False)
@@ -521,14 +528,14 @@ def main():
     # ---- sigma TFLOP/s, mixed vs FP64 (one block of nroots vectors each)
     Xs = torch.from_numpy(random_vectors(ctx.N, nroots, seed=7)).cuda()
     sig = {}
-    for prec in ("bf16x3", "fp64"):
+    for prec in (args.mixed, "fp64"):
         ctx.sigma(Xs, prec)
         torch.cuda.synchronize()
         ctx.profile(True)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        reps = 3 if prec == "bf16x3" else 1
+        reps = 3 if prec != "fp64" else 1
         for _ in range(reps):
             ctx.sigma(Xs, prec)
         b.record(stream)
@@ -540,7 +547,7 @@ def main():
         sig[prec] = {"ms": t, "tflops": fl / (t * 1e-3) / 1e12, "flops": fl}
     log("sigma", sig)
     S64 = ctx.sigma(Xs, "fp64")
-    Smx = ctx.sigma(Xs, "bf16x3")
+    Smx = ctx.sigma(Xs, args.mixed)
     sig_rel = float(((Smx - S64).abs().pow(2).sum(1).sqrt() / S64.abs().pow(2).sum(1).sqrt()).max().item())
 
     # ---- FP64 Davidson for the comparison and the 1e-6 Eh check
@@ -563,7 +570,7 @@ def main():
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         with adcgpu.Context(Bh, eoh, evh, kind=kind, order=order, x=x) as c2:
-            om2, _, e2, st2, rc2 = c2.davidson(nroots, tol=tol, max_iter=300, precision="bf16x3",
+            om2, _, e2, st2, rc2 = c2.davidson(nroots, tol=tol, max_iter=300, precision=args.mixed,
                                                want_vectors=False)
         te2e = time.perf_counter() - t2
         log(f"e2e {te2e:.1f} s")
@@ -583,14 +590,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "s/root", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": f"{args.mixed}+f64", "data": "synthetic",
         "config": {"workload": args.config, "kind": kind, "order": order, "x": x, "nocc": o, "nvir": v, "naux": Q,
                    "nroots": nroots, "tol_fp64_residual": tol, "N": ctx.N, "replicas": world,
                    "l2": "operators larger than L2 (packed <ab||cd> 6.3 GB FP64, 3.2 GB BF16 planes)"},
         "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "roofline_tensor_core": roof_tc,
         "roofline_by_kernel": by_kernel,
-        "sigma": {"bf16x3": sig["bf16x3"], "fp64": sig["fp64"], "speedup": sig["fp64"]["ms"] / sig["bf16x3"]["ms"],
-                  "rel_diff_bf16x3_vs_fp64": sig_rel, "vectors": nroots},
+        "sigma": {args.mixed: sig[args.mixed], "fp64": sig["fp64"], "speedup": sig["fp64"]["ms"] / sig[args.mixed]["ms"],
+                  "rel_diff_mixed_vs_fp64": sig_rel, "vectors": nroots},
         "fp64_davidson": fp64,
         "mixed_davidson": {"omega": [float(w) for w in om], "err64": [float(e) for e in e64],
                            "iterations": last["iterations"], "sigma_calls": last["sigma_calls"],
