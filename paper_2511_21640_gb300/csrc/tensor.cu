@@ -87,7 +87,7 @@ k_zgemm(int64_t M, int64_t N, int64_t K, const cplx *__restrict__ A, int64_t sAb
         int64_t sAk, int conjA, int a_kfast, const cplx *__restrict__ B, int64_t sBb,
         int64_t sBk, int64_t sBn, int conjB, int b_nfast, cplx *C, int64_t sCb, int64_t sCm,
         int64_t sCn, cplx alpha, cplx beta, int64_t batch0, int ksplit, int64_t kchunk,
-        cplx *part, int64_t nbatch) {
+        cplx *part, int64_t nbatch, int mfast) {
   // 3M products: (ar + i ai)(br + i bi) = T1 - T2 + i (T3 - T1 - T2) with
   // T1 = ar br, T2 = ai bi, T3 = (ar + ai)(br + bi): three FP64 FMAs per
   // complex MAC instead of four. The sums are formed once per staged element.
@@ -102,7 +102,10 @@ k_zgemm(int64_t M, int64_t N, int64_t K, const cplx *__restrict__ A, int64_t sAb
   const int64_t split = zl % ksplit;
   const int64_t bl = zl / ksplit;
   const int64_t b = bl + batch0;
-  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  // with mfast the row tiles vary fastest, so the CTAs that read one column
+  // tile of B (the large operand of the skinny shapes) run together and share it in L2
+  const int64_t m0 = (int64_t)(mfast ? blockIdx.x : blockIdx.y) * BM;
+  const int64_t n0 = (int64_t)(mfast ? blockIdx.y : blockIdx.x) * BN;
   const int64_t kbeg = split * kchunk;
   const int64_t kend = (kbeg + kchunk < K) ? kbeg + kchunk : K;
   const cplx *Ab = A + b * sAb;
@@ -237,7 +240,9 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K < 0) K = 0;  // the kernel then writes beta * C
   zgemm_attr();
-  ADC_REQUIRE((M + BM - 1) / BM <= 65535, ADC_ERR_UNSUPPORTED, "zgemm: M too large");
+  const int64_t mt_ = (M + BM - 1) / BM, nt_ = (N + BN - 1) / BN;
+  const int mfast = (nt_ <= 65535) ? 1 : 0;
+  ADC_REQUIRE(mfast || mt_ <= 65535, ADC_ERR_UNSUPPORTED, "zgemm: shape too large");
   int a_kfast = (sAk == 1) ? 1 : 0;
   int b_nfast = (sBn == 1) ? 1 : 0;
   dim3 block(256);
@@ -255,11 +260,11 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
   int pr = ex.prof_begin("zgemm_fp64", 8.0 * (double)M * N * K * batch);
   for (int64_t b0 = 0; b0 < batch; b0 += bmax) {
     int64_t nb = std::min<int64_t>(bmax, batch - b0);
-    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)(nb * ksplit));
+    dim3 grid(mfast ? (unsigned)mt_ : (unsigned)nt_, mfast ? (unsigned)nt_ : (unsigned)mt_, (unsigned)(nb * ksplit));
     if (ksplit == 1) {
       k_zgemm<<<grid, block, ZG_SMEM, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B,
                                              sBb, sBk, sBn, conjB ? 1 : 0, b_nfast, C, sCb, sCm,
-                                             sCn, alpha, beta, b0, 1, K, nullptr, nb);
+                                             sCn, alpha, beta, b0, 1, K, nullptr, nb, mfast);
       ADC_CHECK_LAUNCH();
     } else {
       int64_t kchunk = (K + ksplit - 1) / ksplit;
@@ -267,7 +272,7 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
       DBuf part = cbuf(ex, (int64_t)ksplit * nb * M * N);
       k_zgemm<<<grid, block, ZG_SMEM, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B,
                                              sBb, sBk, sBn, conjB ? 1 : 0, b_nfast, C, sCb, sCm,
-                                             sCn, alpha, beta, b0, ksplit, kchunk, part.c(), nb);
+                                             sCn, alpha, beta, b0, ksplit, kchunk, part.c(), nb, mfast);
       ADC_CHECK_LAUNCH();
       k_splitk_reduce<<<grid1d(nb * M * N, 256), 256, 0, ex.stream>>>(
           part.c(), ksplit, nb, M, N, C, sCb, sCm, sCn, alpha, beta, b0);
@@ -284,7 +289,9 @@ void zgemm_ws(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alp
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K < 0) K = 0;
   zgemm_attr();
-  ADC_REQUIRE((M + BM - 1) / BM <= 65535, ADC_ERR_UNSUPPORTED, "zgemm: M too large");
+  const int64_t mt_ = (M + BM - 1) / BM, nt_ = (N + BN - 1) / BN;
+  const int mfast = (nt_ <= 65535) ? 1 : 0;
+  ADC_REQUIRE(mfast || mt_ <= 65535, ADC_ERR_UNSUPPORTED, "zgemm: shape too large");
   int a_kfast = (sAk == 1) ? 1 : 0;
   int b_nfast = (sBn == 1) ? 1 : 0;
   dim3 block(256);
@@ -304,18 +311,18 @@ void zgemm_ws(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alp
     int ks = ksplit;
     if (ks > 1 && ws) ks = (int)std::max<int64_t>(1, std::min<int64_t>(ks, ws_elems / std::max<int64_t>(1, nb * M * N)));
     if (!ws) ks = 1;
-    dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)(nb * ks));
+    dim3 grid(mfast ? (unsigned)mt_ : (unsigned)nt_, mfast ? (unsigned)nt_ : (unsigned)mt_, (unsigned)(nb * ks));
     if (ks == 1) {
       k_zgemm<<<grid, block, ZG_SMEM, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B, sBb, sBk, sBn,
                                              conjB ? 1 : 0, b_nfast, C, sCb, sCm, sCn, alpha, beta, b0, 1, K,
-                                             nullptr, nb);
+                                             nullptr, nb, mfast);
       ADC_CHECK_LAUNCH();
     } else {
       int64_t kchunk = (K + ks - 1) / ks;
       kchunk = (kchunk + BKK - 1) / BKK * BKK;
       k_zgemm<<<grid, block, ZG_SMEM, ex.stream>>>(M, N, K, A, sAb, sAm, sAk, conjA ? 1 : 0, a_kfast, B, sBb, sBk, sBn,
                                              conjB ? 1 : 0, b_nfast, C, sCb, sCm, sCn, alpha, beta, b0, ks, kchunk,
-                                             ws, nb);
+                                             ws, nb, mfast);
       ADC_CHECK_LAUNCH();
       k_splitk_reduce<<<grid1d(nb * M * N, 256), 256, 0, ex.stream>>>(ws, ks, nb, M, N, C, sCb, sCm, sCn, alpha,
                                                                       beta, b0);
