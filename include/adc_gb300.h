@@ -59,9 +59,10 @@ enum { ADC_IP = 0, ADC_EA = 1, ADC_EE = 2 };
  *   the real 2x2 embedding. Diagonal terms stay FP64.
  * ADC_PREC_BF16X6: as BF16X3 with three BF16 parts (hi, lo = bf16(x - hi),
  *   lo2 = bf16(x - hi - lo)) and the six products of combined order up to
- *   2^-16 (hh, hl, lh, hl2, ll, l2h): about 2^-24 per operand, limited by
- *   the FP32 accumulation; twice the tensor-core work of BF16X3. Batches
- *   (adc_batch_*) use BF16X3. */
+ *   2^-16 (hh, hl, lh, hl2, ll, l2h): about 2^-24 per operand at twice the
+ *   tensor-core work of BF16X3. The tensor cores' FP32 accumulation, not the
+ *   split, limits both (1e-6 to 1e-5 relative measured), so BF16X6 is rarely
+ *   more accurate. Batches (adc_batch_*) use BF16X3. */
 enum { ADC_PREC_FP64 = 0, ADC_PREC_BF16X3 = 1, ADC_PREC_BF16X6 = 2 };
 
 enum {
