@@ -455,9 +455,13 @@ void launch_tc(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N2, 
 // job are numbered (row block, column block, K split) with the K split fastest,
 // so consecutive tiles reuse the same A rows from L2. Each job carries its own
 // tensor maps, tile width (32..256 columns, runtime) and K split; the shared
-// memory ring is sized for the widest tile. The accumulator is drained by the
-// epilogue warps before the next tile's first MMA (block barrier per tile).
-constexpr int TG_ST = 4;
+// memory ring is sized for the widest tile.
+// Roles run decoupled: warp 0 takes tile numbers from the counter into a small
+// shared ring and issues the TMA loads, warp 1 issues the MMAs into one of two
+// TMEM accumulators (2 x 256 columns), warps 2-5 drain the other accumulator,
+// so the epilogue of one tile overlaps the main loop of the next.
+constexpr int TG_ST = 4;  // shared-memory stages
+constexpr int TG_TQ = 4;  // tile-number ring
 struct TgLayout {
   static constexpr int A_BYTES = TC_BM * TC_BK * 2;
   static constexpr int B_BYTES = TC_BNMAX * TC_BK * 2;
@@ -469,6 +473,36 @@ struct TgLayout {
 __device__ __forceinline__ void tensormap_acquire(const CUtensorMap *m) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+struct TgTile {
+  const TcJob *J;
+  int m0, n0, bn, split, kb_beg, nkb;
+};
+__device__ __forceinline__ TgTile tg_decode(const TcJob *__restrict__ jobs, int njobs, int t) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  TgTile d;
+  d.J = &jobs[lo];
+  const TcJob &J = *d.J;
+  const int lt = t - J.tile_begin;
+  const int per_m = J.tiles_n * J.ksplit;
+  const int tm = lt / per_m, rem = lt - tm * per_m;
+  const int tn = rem / J.ksplit;
+  d.split = rem - tn * J.ksplit;
+  d.bn = J.bn;
+  d.m0 = tm * TC_BM;
+  d.n0 = tn * J.bn;
+  d.kb_beg = d.split * J.kb_per_split;
+  d.nkb = min(3 * J.kps, d.kb_beg + J.kb_per_split) - d.kb_beg;
+  return d;
+}
 
 __global__ void __launch_bounds__(192, 1)
 k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *counter, int *err) {
@@ -476,10 +510,13 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + TgLayout::BAR_OFF);
   uint64_t *empty = full + TG_ST;
-  uint64_t *accum = empty + TG_ST;
-  uint32_t *tmem_slot = (uint32_t *)(accum + 1);
+  uint64_t *accf = empty + TG_ST;   // accumulator b holds a finished tile (MMA -> epilogue)
+  uint64_t *acce = accf + 2;        // accumulator b drained (epilogue -> MMA)
+  uint64_t *tfull = acce + 2;       // tile number published (producer -> consumers)
+  uint64_t *tempty = tfull + TG_TQ;  // tile number read by the MMA warp and the 4 epilogue warps
+  uint32_t *tmem_slot = (uint32_t *)(tempty + TG_TQ);
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-  volatile int *tile_slot = (volatile int *)(tmem_slot + 2);
+  volatile int *ring = (volatile int *)(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -487,14 +524,21 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
-    mbar_init(smem_u32(accum), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf[b]), 1);
+      mbar_init(smem_u32(&acce[b]), 4);
+    }
+    for (int q = 0; q < TG_TQ; ++q) {
+      mbar_init(smem_u32(&tfull[q]), 1);
+      mbar_init(smem_u32(&tempty[q]), 5);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)TC_BNMAX)
+                 "r"((uint32_t)(2 * TC_BNMAX))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -503,79 +547,92 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  uint32_t g = 0;        // k-blocks that went through the stage ring so far
-  uint32_t acc_par = 0;  // phase of the accumulator barrier
-  for (;;) {
-    if (threadIdx.x == 0) *tile_slot = atomicAdd(counter, 1);
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const int t = *tile_slot;
-    if (t >= total_tiles || *abort_flag) break;
-    int lo = 0, hi = njobs - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (jobs[mid].tile_begin <= t) lo = mid;
-      else hi = mid - 1;
-    }
-    const TcJob &J = jobs[lo];
-    const int lt = t - J.tile_begin;
-    const int per_m = J.tiles_n * J.ksplit;
-    const int tm = lt / per_m, rem = lt - tm * per_m;
-    const int tn = rem / J.ksplit, split = rem - tn * J.ksplit;
-    const int bn = J.bn;
-    const int m0 = tm * TC_BM, n0 = tn * bn;
-    const int total_kb = 3 * J.kps;
-    const int kb_beg = split * J.kb_per_split;
-    const int kb_end = min(total_kb, kb_beg + J.kb_per_split);
-    const int nkb = kb_end - kb_beg;
-
-    if (warp == 0 && lane == 0) {
-      // ---------------- producer
+  if (warp == 0 && lane == 0) {
+    // ---------------- tile scheduler and TMA producer
+    uint32_t g = 0, g_issued = 0;
+    for (uint32_t q = 0;; ++q) {
+      const int slot = (int)(q % TG_TQ);
+      const uint32_t r = q / TG_TQ;
+      if (r > 0 && !mbar_wait(smem_u32(&tempty[slot]), (r - 1) & 1, abort_flag)) {
+        if (!*abort_flag) atomicExch(err, 14);
+        *abort_flag = 1;
+        break;
+      }
+      const int t = *abort_flag ? total_tiles : atomicAdd(counter, 1);
+      ring[slot] = t;
+      mbar_arrive(smem_u32(&tfull[slot]));
+      if (t >= total_tiles) break;
+      const TgTile d = tg_decode(jobs, njobs, t);
+      const TcJob &J = *d.J;
       tensormap_acquire(&J.mAh);
       tensormap_acquire(&J.mAl);
       tensormap_acquire(&J.mBh);
       tensormap_acquire(&J.mBl);
-      const uint32_t bytes = (uint32_t)(TgLayout::A_BYTES + bn * TC_BK * 2);
-      int issued = 0;
-      for (int i = 0; i < nkb; ++i) {
+      const uint32_t bytes = (uint32_t)(TgLayout::A_BYTES + d.bn * TC_BK * 2);
+      bool stop = false;
+      for (int i = 0; i < d.nkb; ++i) {
         const uint32_t gi = g + (uint32_t)i;
         const int s = (int)(gi % TG_ST);
-        const uint32_t r = gi / TG_ST;
-        if (r > 0 && !mbar_wait(smem_u32(&empty[s]), (r - 1) & 1, abort_flag)) {
+        const uint32_t rr = gi / TG_ST;
+        if (rr > 0 && !mbar_wait(smem_u32(&empty[s]), (rr - 1) & 1, abort_flag)) {
           if (!*abort_flag) atomicExch(err, 11);
           *abort_flag = 1;
+          stop = true;
           break;
         }
-        const int kg = kb_beg + i;
+        const int kg = d.kb_beg + i;
         const int seg = kg / J.kps;
         const int kx = (kg - seg * J.kps) * TC_BK;
         const uint32_t fb = smem_u32(&full[s]);
         mbar_expect_tx(fb, bytes);
         uint8_t *sa = smem + s * TgLayout::STAGE;
-        tma_load_2d(smem_u32(sa), seg == 2 ? &J.mAl : &J.mAh, kx, m0, fb);
-        tma_load_2d(smem_u32(sa + TgLayout::A_BYTES), seg == 1 ? &J.mBl : &J.mBh, kx, n0, fb);
-        issued = i + 1;
+        tma_load_2d(smem_u32(sa), seg == 2 ? &J.mAl : &J.mAh, kx, d.m0, fb);
+        tma_load_2d(smem_u32(sa + TgLayout::A_BYTES), seg == 1 ? &J.mBl : &J.mBh, kx, d.n0, fb);
+        g_issued = gi + 1;
       }
-      if (*abort_flag) {
-        // drain this CTA's copies in flight before shared memory is released
-        for (int j = (issued > TG_ST ? issued - TG_ST : 0); j < issued; ++j) {
-          const uint32_t gj = g + (uint32_t)j;
-          const int s = (int)(gj % TG_ST);
-          uint64_t t0 = gtimer();
-          while (!mbar_try(smem_u32(&full[s]), (gj / TG_ST) & 1) && gtimer() - t0 < WAIT_NS) {
-          }
+      if (stop) break;
+      g += (uint32_t)d.nkb;
+    }
+    if (*abort_flag) {
+      // drain this CTA's copies in flight before shared memory is released
+      for (uint32_t gj = (g_issued > TG_ST ? g_issued - TG_ST : 0); gj < g_issued; ++gj) {
+        const int s = (int)(gj % TG_ST);
+        uint64_t t0 = gtimer();
+        while (!mbar_try(smem_u32(&full[s]), (gj / TG_ST) & 1) && gtimer() - t0 < WAIT_NS) {
         }
       }
-    } else if (warp == 1 && lane == 0) {
-      // ---------------- MMA issuer
-      const uint32_t idesc = idesc_bf16(TC_BM, bn);
-      for (int i = 0; i < nkb; ++i) {
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer, accumulators alternating
+    uint32_t g = 0;
+    for (uint32_t q = 0;; ++q) {
+      const int slot = (int)(q % TG_TQ);
+      if (!mbar_wait(smem_u32(&tfull[slot]), (q / TG_TQ) & 1, abort_flag)) {
+        if (!*abort_flag) atomicExch(err, 15);
+        *abort_flag = 1;
+        break;
+      }
+      const int t = ring[slot];
+      mbar_arrive(smem_u32(&tempty[slot]));
+      if (t >= total_tiles) break;
+      const TgTile d = tg_decode(jobs, njobs, t);
+      const uint32_t b = q & 1u, use = q >> 1;
+      if (use > 0 && !mbar_wait(smem_u32(&acce[b]), (use - 1) & 1, abort_flag)) {
+        if (!*abort_flag) atomicExch(err, 16);
+        *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      const uint32_t dacc = tmem + b * (uint32_t)TC_BNMAX;
+      const uint32_t idesc = idesc_bf16(TC_BM, d.bn);
+      bool stop = false;
+      for (int i = 0; i < d.nkb; ++i) {
         const uint32_t gi = g + (uint32_t)i;
         const int s = (int)(gi % TG_ST);
         if (!mbar_wait(smem_u32(&full[s]), (gi / TG_ST) & 1, abort_flag)) {
           if (!*abort_flag) atomicExch(err, 12);
           *abort_flag = 1;
+          stop = true;
           break;
         }
         fence_after();
@@ -583,32 +640,54 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
         const uint32_t b0 = a0 + TgLayout::A_BYTES;
 #pragma unroll
         for (int k = 0; k < TC_BK / 16; ++k)
-          mma_bf16(tmem, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, (i > 0 || k > 0) ? 1u : 0u);
+          mma_bf16(dacc, sdesc(a0 + 32 * k), sdesc(b0 + 32 * k), idesc, (i > 0 || k > 0) ? 1u : 0u);
         mma_commit(smem_u32(&empty[s]));
       }
-      mma_commit(smem_u32(accum));
-    } else if (warp >= 2) {
-      // ---------------- epilogue
-      bool ok = mbar_wait(smem_u32(accum), acc_par, abort_flag);
-      if (!ok && !*abort_flag) { atomicExch(err, 13); *abort_flag = 1; }
+      if (stop) break;
+      mma_commit(smem_u32(&accf[b]));
+      g += (uint32_t)d.nkb;
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue: TMEM -> registers -> complex128, one accumulator at a time
+    const int qq = warp & 3;
+    const int row = qq * 32 + lane;
+    for (uint32_t q = 0;; ++q) {
+      const int slot = (int)(q % TG_TQ);
+      bool ok = mbar_wait(smem_u32(&tfull[slot]), (q / TG_TQ) & 1, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0 && !*abort_flag) { atomicExch(err, 17); *abort_flag = 1; }
+        break;
+      }
+      const int t = ring[slot];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[slot]));
+      if (t >= total_tiles) break;
+      const TgTile d = tg_decode(jobs, njobs, t);
+      const TcJob &J = *d.J;
+      const uint32_t b = q & 1u, use = q >> 1;
+      ok = mbar_wait(smem_u32(&accf[b]), use & 1, abort_flag);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0 && !*abort_flag) { atomicExch(err, 13); *abort_flag = 1; }
+        break;
+      }
       fence_after();
       __syncwarp();
-      const int q = warp & 3;
-      const int row = q * 32 + lane;
-      const int64_t m = (int64_t)m0 + row;
+      const int64_t m = (int64_t)d.m0 + row;
       const bool use_beta = (J.beta.x != 0.0 || J.beta.y != 0.0);
 #pragma unroll 1
-      for (int cch = 0; cch < bn / 32; ++cch) {
+      for (int cch = 0; cch < d.bn / 32; ++cch) {
         uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cch * 32), v);
-        if (!ok || *abort_flag || m >= J.M || nkb <= 0) continue;
+        tmem_ld32(tmem + b * (uint32_t)TC_BNMAX + ((uint32_t)(qq * 32) << 16) + (uint32_t)(cch * 32), v);
+        if (m >= J.M || d.nkb <= 0) continue;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int64_t n2 = (int64_t)n0 + cch * 32 + 2 * j;
+          const int64_t n2 = (int64_t)d.n0 + cch * 32 + 2 * j;
           if (n2 >= J.N2) break;
           const float re = __uint_as_float(v[2 * j]), im = __uint_as_float(v[2 * j + 1]);
           if (J.part) {
-            float *pp = J.part + ((int64_t)split * J.M + m) * J.N2 + n2;
+            float *pp = J.part + ((int64_t)d.split * J.M + m) * J.N2 + n2;
             pp[0] = re;
             pp[1] = im;
           } else {
@@ -621,16 +700,17 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
           }
         }
       }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acce[b]));
     }
-    g += (uint32_t)max(nkb, 0);
-    acc_par ^= 1u;
   }
   fence_before();
   __syncthreads();
   if (warp == 1) {
     __syncwarp();
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TC_BNMAX)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * TC_BNMAX))
                  : "memory");
   }
 }
