@@ -210,8 +210,11 @@ int adc_fns_transform(adc_ctx *ctx, const adc_c128 *U, int64_t ldu,
  * imposed, so a Hermitian change dB changes L by sum Re(conj(gB) dB)),
  * geps_occ [nocc], geps_vir [nvir] and *gx (host). gB and the energy
  * gradients may be host or device arrays. The integral and amplitude
- * intermediates are recomputed from the context's cached blocks. EE-ADC only
- * (ADC_ERR_UNSUPPORTED otherwise). Synchronous. */
+ * intermediates are recomputed from the context's cached blocks (the
+ * second-order amplitudes of IP/EA-ADC(3) anew). All kinds (IP, EA, EE) and
+ * orders; at order 3 *gx is dL/dx even for x = 0. Memory: the dense integral
+ * blocks the term tables name and their gradients, up to two v^4 arrays for
+ * EA and EE at third order. Synchronous. */
 int adc_sigma_adjoint(adc_ctx *ctx, const adc_c128 *Y, const double *gomega, int64_t nroots, adc_c128 *gB,
                       double *geps_occ, double *geps_vir, double *gx);
 

@@ -16,6 +16,8 @@ void fns_run(adc_ctx *c, cplx *D, double *eta, cplx *Vout, double eta_crit, int6
 void fns_transform(adc_ctx *c, const cplx *U, int64_t ldu, int64_t nk, cplx *Bout);
 void adjoint_ee(adc_ctx *c, const cplx *Y, const double *g_host, int64_t k, cplx *gB, double *geo, double *gev,
                 double *gx);
+void adjoint_ipea(adc_ctx *c, const cplx *Y, const double *g_host, int64_t k, cplx *gB, double *geo, double *gev,
+                  double *gx);
 }  // namespace adc
 
 using namespace adc;
@@ -314,11 +316,6 @@ int adc_sigma_adjoint(adc_ctx *c, const adc_c128 *Y, const double *gomega, int64
                       double *geps_occ, double *geps_vir, double *gx) {
   if (!c) return ADC_ERR_STATE;
   if (!Y || !gomega || nroots < 1 || !gB || !geps_occ || !geps_vir || !gx) return ADC_ERR_ARG;
-  if (c->kind != ADC_EE) {
-    c->err = "adc_sigma_adjoint: implemented for EE-ADC";
-    g_last_error = c->err;
-    return ADC_ERR_UNSUPPORTED;
-  }
   ADC_API_TRY
   for (int64_t r = 0; r < nroots; ++r)
     ADC_REQUIRE(std::isfinite(gomega[r]), ADC_ERR_ARG, "adc_sigma_adjoint: non-finite gomega");
@@ -331,7 +328,10 @@ int adc_sigma_adjoint(adc_ctx *c, const adc_c128 *Y, const double *gomega, int64
   fill_zero(c->ex, geo.p, c->o * sizeof(double));
   fill_zero(c->ex, gev.p, c->v * sizeof(double));
   double gxh = 0.0;
-  adjoint_ee(c, (const cplx *)yin.p, gomega, nroots, (cplx *)gbo.p, (double *)geo.p, (double *)gev.p, &gxh);
+  if (c->kind == ADC_EE)
+    adjoint_ee(c, (const cplx *)yin.p, gomega, nroots, (cplx *)gbo.p, (double *)geo.p, (double *)gev.p, &gxh);
+  else
+    adjoint_ipea(c, (const cplx *)yin.p, gomega, nroots, (cplx *)gbo.p, (double *)geo.p, (double *)gev.p, &gxh);
   gbo.finish(c->ex);
   geo.finish(c->ex);
   gev.finish(c->ex);

@@ -185,6 +185,11 @@ __global__ void k_ee_diag(const cplx *MSS, const double *g, const double *eo, co
 }  // namespace
 
 
+void amplitude_tables(std::vector<Term> &t2n, std::vector<Term> &s2n) {
+  t2n = parse_terms(kT2N);
+  s2n = parse_terms(kS2N);
+}
+
 TermSource ee_source(adc_ctx *c) {
   TermSource s;
   s.o = c->o;
@@ -228,7 +233,7 @@ void setup_ee(adc_ctx *c) {
   E.K1 = parse_terms(kK1); E.S2 = parse_terms(kS2); E.Y2 = parse_terms(kY2);
   E.S3 = parse_terms(kS3); E.Y3 = parse_terms(kY3);
   E.SD1 = parse_terms(kSD1); E.O2 = parse_terms(kO2); E.Z1 = parse_terms(kZ1); E.DD1 = parse_terms(kDD1);
-  E.T2N = parse_terms(kT2N); E.S2N = parse_terms(kS2N);
+  amplitude_tables(E.T2N, E.S2N);
   first_order_amplitudes(c);
   if (c->order == 3) {
     // also at x = 0: the derivative with respect to x needs them

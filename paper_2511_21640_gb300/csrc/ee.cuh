@@ -27,6 +27,9 @@ struct EEOps {
   bool tc_ready = false;
   int tc_planes = 0;
 };
+// numerators of the second-order doubles and singles (second_order_amplitudes in
+// setup.cu) as term tables: t2_ij^ab D_ij^ab and t2_i^a (eps_i - eps_a)
+void amplitude_tables(std::vector<Term> &t2n, std::vector<Term> &s2n);
 // tensors of the EE term tables (v blocks cached in EEOps::eri)
 TermSource ee_source(adc_ctx *c);
 }  // namespace adc
