@@ -62,8 +62,16 @@ enum { ADC_IP = 0, ADC_EA = 1, ADC_EE = 2 };
  *   2^-16 (hh, hl, lh, hl2, ll, l2h): about 2^-24 per operand at twice the
  *   tensor-core work of BF16X3. The tensor cores' FP32 accumulation, not the
  *   split, limits both (1e-6 to 1e-5 relative measured), so BF16X6 is rarely
- *   more accurate. Batches (adc_batch_*) use BF16X3. */
-enum { ADC_PREC_FP64 = 0, ADC_PREC_BF16X3 = 1, ADC_PREC_BF16X6 = 2 };
+ *   more accurate. Batches (adc_batch_*) use BF16X3.
+ * ADC_PREC_SLICED: FP64-accurate products on the tensor cores (IP and EA).
+ *   Each operand row is scaled by a power of two and written as a sum of
+ *   integer BF16 digits of 4 to 7 bits; every digit product is summed exactly
+ *   in the FP32 accumulator (the inner size is split so that the sums stay
+ *   below 2^24) and the pair products are combined in FP64, for about 40
+ *   significant bits relative to the row and column maxima (about 1e-11
+ *   relative to the largest output). Used for the refinement products of the
+ *   mixed Davidson when opts.refine selects it. */
+enum { ADC_PREC_FP64 = 0, ADC_PREC_BF16X3 = 1, ADC_PREC_BF16X6 = 2, ADC_PREC_SLICED = 3 };
 
 enum {
   ADC_OK = 0,
@@ -88,6 +96,9 @@ typedef struct {
   int dd_order;         /* EE only: order of the doubles-doubles block at third
                            order, 1 (full ADC(3), default) or 0 (kept at the
                            ADC(2) level, zeroth order) */
+  int refine;           /* products of adc_davidson's refinement (the FP64 base
+                           of the Ritz vectors and the final residual check):
+                           ADC_PREC_FP64 (default) or ADC_PREC_SLICED (IP/EA) */
 } adc_opts;
 
 typedef struct {

@@ -22,7 +22,9 @@ typedef struct adc_ctx adc_ctx_opaque;
  * tile width, 3 = three jobs of different shapes in one grouped launch:
  * (M, N, K), (M/2+37, max(1, N/3), K/2+11) and (129, 3, 2K+5), the last one
  * long and narrow so that it is split along K; rel_err is then the largest of
- * the three), 4 = the six-product (BF16x6) tensor-core GEMM) and compared with
+ * the three), 4 = the six-product (BF16x6) tensor-core GEMM, 5 = the sliced
+ * FP64-accurate tensor-core product of ADC_PREC_SLICED, including the slicing
+ * of both operands) and compared with
  * the FP64 GEMM. Outputs: rel_err = ||C - C_fp64||_F / ||C_fp64||_F,
  * ms = average time of one launch sequence over `reps` repetitions (CUDA
  * events, after one warm-up). Allocates and frees its own device memory.

@@ -21,9 +21,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libadc_gb300.so")
 
 ADC_IP, ADC_EA, ADC_EE = 0, 1, 2
-ADC_PREC_FP64, ADC_PREC_BF16X3, ADC_PREC_BF16X6 = 0, 1, 2
+ADC_PREC_FP64, ADC_PREC_BF16X3, ADC_PREC_BF16X6, ADC_PREC_SLICED = 0, 1, 2, 3
 KINDS = {"IP": ADC_IP, "EA": ADC_EA, "EE": ADC_EE}
-PRECISIONS = {"fp64": ADC_PREC_FP64, "bf16x3": ADC_PREC_BF16X3, "bf16x6": ADC_PREC_BF16X6}
+PRECISIONS = {"fp64": ADC_PREC_FP64, "bf16x3": ADC_PREC_BF16X3, "bf16x6": ADC_PREC_BF16X6,
+              "sliced": ADC_PREC_SLICED}
 ERRORS = {0: "ADC_OK", -1: "ADC_ERR_ARG", -2: "ADC_ERR_OOM", -3: "ADC_ERR_CUDA", -4: "ADC_ERR_NOCONV",
           -5: "ADC_ERR_TIMEOUT", -6: "ADC_ERR_UNSUPPORTED", -7: "ADC_ERR_STATE", -8: "ADC_ERR_NUMERIC"}
 
@@ -37,7 +38,8 @@ class AdcError(RuntimeError):
 class adc_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("block", ctypes.c_int),
                 ("max_subspace", ctypes.c_int), ("herm_tol", ctypes.c_double),
-                ("mem_limit", ctypes.c_int64), ("verbose", ctypes.c_int), ("dd_order", ctypes.c_int)]
+                ("mem_limit", ctypes.c_int64), ("verbose", ctypes.c_int), ("dd_order", ctypes.c_int),
+                ("refine", ctypes.c_int)]
 
 
 class adc_stats(ctypes.Structure):
@@ -170,7 +172,8 @@ class Context:
     """One ADC problem on the GPU (``adc_init``)."""
 
     def __init__(self, B, eps_occ, eps_vir, kind="IP", order=3, x=1.0, precision="fp64", stream=None,
-                 block=0, max_subspace=0, herm_tol=1e-12, mem_limit=0, verbose=False, dd_order=1):
+                 block=0, max_subspace=0, herm_tol=1e-12, mem_limit=0, verbose=False, dd_order=1,
+                 refine="fp64"):
         o = adc_opts()
         lib.adc_opts_default(ctypes.byref(o))
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -185,6 +188,7 @@ class Context:
         o.mem_limit = mem_limit
         o.verbose = 1 if verbose else 0
         o.dd_order = int(dd_order)
+        o.refine = PRECISIONS[refine] if isinstance(refine, str) else int(refine)
         naux, nmo, nmo2 = B.shape
         nocc, nvir = eps_occ.shape[0], eps_vir.shape[0]
         if nmo != nmo2 or nmo != nocc + nvir:

@@ -6,6 +6,7 @@
 
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
+#include "tc_slice.cuh"
 #include "ee.cuh"
 
 namespace adc {
@@ -144,6 +145,8 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
     if (opts) c->opts = *opts;
     else adc_opts_default(&c->opts);
     if (c->opts.herm_tol <= 0.0) c->opts.herm_tol = 1e-12;
+    ADC_REQUIRE(c->opts.refine == ADC_PREC_FP64 || c->opts.refine == ADC_PREC_SLICED, ADC_ERR_ARG,
+                "opts.refine: ADC_PREC_FP64 or ADC_PREC_SLICED");
     c->kind = kind;
     c->order = order;
     c->x = (order == 3) ? x : 0.0;
@@ -222,7 +225,8 @@ int adc_dims(const adc_ctx *c, int64_t *n1, int64_t *n2) {
 int adc_sigma(adc_ctx *c, const adc_c128 *X, adc_c128 *S, int64_t k, int precision) {
   if (!c) return ADC_ERR_STATE;
   if (k < 0 || (k > 0 && (!X || !S))) return ADC_ERR_ARG;
-  if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3 && precision != ADC_PREC_BF16X6)
+  if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3 && precision != ADC_PREC_BF16X6 &&
+      precision != ADC_PREC_SLICED)
     return ADC_ERR_ARG;
   if (k == 0) return ADC_OK;
   ADC_API_TRY

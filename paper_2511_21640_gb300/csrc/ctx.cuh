@@ -7,6 +7,7 @@
 
 namespace adc {
 struct TcCache;  // split-precision operator copies (tc_gemm.cu)
+struct SlCache;  // sliced (FP64-accurate) operator copies (tc_slice.cu)
 struct EEOps;    // EE-ADC operators (ee.cu)
 struct BatchCoord;  // cross-problem sigma batching (batch.cu)
 }
@@ -35,6 +36,8 @@ struct adc_ctx {
 
   // split-precision copies for the tensor-core sigma
   std::unique_ptr<adc::TcCache> tc;
+  // integer-digit slices for the FP64-accurate tensor-core sigma
+  std::unique_ptr<adc::SlCache> sl;
 
   // EE-ADC operators (kind == ADC_EE)
   std::unique_ptr<adc::EEOps> ee;
@@ -67,6 +70,8 @@ void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg);
 void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 // split-precision sigma on the tensor cores: nseg = 3 (BF16x3) or 6 (BF16x6) products
 void sigma_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg);
+// FP64-accurate sigma with the dense contractions as sliced tensor-core products (IP/EA)
+void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision);
 void release_tc(adc_ctx *c);
 void tc_ensure(adc_ctx *c, int planes = 2);  // split-precision operator copies, built on first use

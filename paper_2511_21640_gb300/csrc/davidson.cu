@@ -15,6 +15,8 @@
 //      collapse (subspace full, stall, or apparent convergence) recomputes
 //      sigma64 of the Ritz vectors, and convergence is only accepted on FP64
 //      residuals ||sigma64(y) - omega y|| <= tol.
+// The refinement products (sigma64) are FP64, or with opts.refine the sliced
+// tensor-core product of tc_slice.cu, exact digit products combined in FP64.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -142,6 +144,7 @@ struct Davidson {
   double tsig = 0.0;
   int m = 0;
   int nb = 0;  // leading subspace vectors whose sigma is FP64
+  int prec64 = ADC_PREC_FP64;  // precision of the refinement products (FP64 or the sliced FP64-accurate product)
 
   Davidson(adc_ctx *c_, int nr, int mmax_, int krmax_)
       : c(c_), ex(c_->ex), N(c_->N), nroots(nr), mmax(mmax_), krmax(krmax_) {
@@ -181,7 +184,7 @@ struct Davidson {
     if (c->batch) batch_rejoin(c);
     tsig += t.s();
     st.sigma_calls += (int)k;
-    if (prec == ADC_PREC_FP64) st.sigma_calls_fp64 += (int)k;
+    if (prec == ADC_PREC_FP64 || prec == ADC_PREC_SLICED) st.sigma_calls_fp64 += (int)k;
   }
 
   // sigma of the na new vectors (in T and in V[m:m+na]) into AV[m:m+na]. In a
@@ -278,7 +281,7 @@ struct Davidson {
   // V <- Y (orthonormal Ritz vectors), AV <- sigma64(Y) or SY, G <- Y^H AV
   void collapse(int nr, bool fp64_sigma) {
     ADC_CUDA(cudaMemcpyAsync(V.c(), Y.c(), (int64_t)nr * N * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
-    if (fp64_sigma) apply_sigma(V.c(), AV.c(), nr, ADC_PREC_FP64);
+    if (fp64_sigma) apply_sigma(V.c(), AV.c(), nr, prec64);
     else
       ADC_CUDA(cudaMemcpyAsync(AV.c(), SY.c(), (int64_t)nr * N * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
     m = 0;
@@ -304,6 +307,9 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   mmax = std::max(mmax, std::min<int>((int)N, nroots + 1));
   const int krmax = std::min(mmax, std::max(2 * nroots, kb));
   Davidson d(c, nroots, mmax, krmax);
+  // refinement products: FP64, or the sliced FP64-accurate tensor-core product (IP/EA)
+  if (precision != ADC_PREC_FP64 && c->opts.refine == ADC_PREC_SLICED && c->kind != ADC_EE)
+    d.prec64 = ADC_PREC_SLICED;
   Exec &ex = c->ex;
 
   // ---- starting space
@@ -422,7 +428,7 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
     }
     ADC_CUDA(cudaMemcpyAsync(d.V.c() + (int64_t)d.m * N, d.T.c(), (int64_t)na * N * sizeof(cplx),
                              cudaMemcpyDeviceToDevice, ex.stream));
-    prec_new = (phase == 2) ? ADC_PREC_FP64 : mixed;
+    prec_new = (phase == 2) ? d.prec64 : mixed;
     d.apply_sigma_new(na, prec_new);
     d.extend_projection(d.m, na);
     d.m += na;

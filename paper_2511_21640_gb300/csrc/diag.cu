@@ -5,6 +5,7 @@
 
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
+#include "tc_slice.cuh"
 #include "../../include/adc_gb300_diag.h"
 
 using namespace adc;
@@ -114,7 +115,7 @@ int diag_grouped(int64_t M, int64_t N, int64_t K, uint64_t seed, int reps, doubl
 
 extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_t seed, int reps,
                              double *rel_err, double *ms) {
-  if (M <= 0 || N <= 0 || K <= 0 || reps < 1 || which < 0 || which > 4) return ADC_ERR_ARG;
+  if (M <= 0 || N <= 0 || K <= 0 || reps < 1 || which < 0 || which > 5) return ADC_ERR_ARG;
   if (which == 3) return diag_grouped(M, N, K, seed, reps, rel_err, ms);
   Exec ex;
   try {
@@ -129,8 +130,12 @@ extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_
       zgemm(ex, M, N, K, 1, C1(), A.c(), 0, K, 1, false, B.c(), 0, 1, K, false, C0(), R.c(), 0, N, 1);
       TcMat Ta, Tb;
       TcGroup grp;
+      SlMat Sa, Sb;
+      SlWork sw;
       auto run = [&]() {
-        if (which == 0) {
+        if (which == 5) {
+          sl_gemm(ex, Sa, Sb, M, N, C1(), C0(), C.c(), N, 1, 0, 1, (int *)err.p, sw);
+        } else if (which == 0) {
           zgemm(ex, M, N, K, 1, C1(), A.c(), 0, K, 1, false, B.c(), 0, 1, K, false, C0(), C.c(), 0, N, 1);
         } else if (which == 1 || which == 4) {
           tc_gemm(ex, Ta, Tb, M, N, C1(), C0(), C.c(), N, 1, 0, 1, (int *)err.p, which == 4 ? 6 : 3);
@@ -140,7 +145,10 @@ extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_
           tc_gemm_grouped(ex, std::vector<TcJobDesc>{d}, grp, (int *)err.p, true);
         }
       };
-      if (which >= 1) {
+      if (which == 5) {
+        sl_pack_A(ex, Sa, A.c(), M, K, K, 1, false, 40);
+        sl_pack_B(ex, Sb, B.c(), N, K, K, 0, 1, 1, false, Sa);
+      } else if (which >= 1) {
         const int planes = which == 4 ? 3 : 2;
         tc_pack_A(ex, Ta, A.c(), M, K, K, 1, false, planes);
         tc_pack_B(ex, Tb, B.c(), N, K, K, 0, 1, 1, false, planes);

@@ -92,10 +92,13 @@ void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
 
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision) {
   if (k <= 0) return;
-  if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3 && precision != ADC_PREC_BF16X6)
+  if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3 && precision != ADC_PREC_BF16X6 &&
+      precision != ADC_PREC_SLICED)
     throw Error(ADC_ERR_ARG, "unknown precision");
   const int nseg = (precision == ADC_PREC_BF16X6) ? 6 : 3;
-  if (c->kind == ADC_EE) {
+  if (precision == ADC_PREC_SLICED) {
+    sigma_sliced(c, X, S, k);
+  } else if (c->kind == ADC_EE) {
     if (precision == ADC_PREC_FP64) sigma_ee_fp64(c, X, S, k);
     else sigma_ee_split(c, X, S, k, nseg);
   } else if (precision == ADC_PREC_FP64) {

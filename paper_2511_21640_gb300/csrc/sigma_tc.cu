@@ -4,6 +4,7 @@
 // zeroth-order diagonal stay FP64.
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
+#include "tc_slice.cuh"
 
 namespace adc {
 
@@ -24,7 +25,10 @@ static void build_cache(adc_ctx *c, int planes) {
   tc.ready = true;
 }
 
-void release_tc(adc_ctx *c) { c->tc.reset(); }
+void release_tc(adc_ctx *c) {
+  c->tc.reset();
+  c->sl.reset();
+}
 
 void tc_ensure(adc_ctx *c, int planes) {
   if (c->tc && c->tc->ready && c->tc->planes < planes) c->tc.reset();  // rebuild with more planes
@@ -76,6 +80,78 @@ void sigma_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
       cplx *T = scratch(c, k * o * v * o);
       tc_pack_B_ring(ex, tc.Bx, c, X, k, planes);
       tc_gemm(ex, tc.W, tc.Bx, o * v, k * o, CR(-1.0), C0(), T, o, o * v * o, 1, o, err, nseg);
+      pair_pack(ex, T, o * v * o, 0, 1, v * o, o, 1.0, k, 1, o, v, S + n1, N, 0, CR(x), C1());
+    }
+  }
+  int h = 0;
+  ADC_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+  if (h != 0) {
+    fill_zero(ex, err, sizeof(int));
+    throw Error(ADC_ERR_TIMEOUT, "tensor-core GEMM wait gave up (code " + std::to_string(h) + ")");
+  }
+}
+
+// ---- FP64-accurate sigma: the same contractions as sliced tensor-core products
+constexpr int kSliceBits = 40;
+
+static void build_sl(adc_ctx *c) {
+  Exec &ex = c->ex;
+  c->sl.reset(new SlCache());
+  SlCache &sl = *c->sl;
+  const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2;
+  sl.bits = kSliceBits;
+  sl_pack_A(ex, sl.Cpl, c->Cpl.c(), n1, n2, n2, 1, false, sl.bits);
+  sl_pack_A(ex, sl.CplT, c->Cpl.c(), n2, n1, 1, n2, true, sl.bits);
+  if (c->order == 3 && c->x != 0.0) {
+    const int64_t P = (c->kind == ADC_EA) ? npairs(v) : npairs(o);
+    sl_pack_A(ex, sl.Glad, c->Glad.c(), P, P, P, 1, false, sl.bits);
+    sl_pack_A(ex, sl.W, c->W.c(), o * v, o * v, o * v, 1, false, sl.bits);
+  }
+  sl.err = DBuf(ex, sizeof(int));
+  fill_zero(ex, sl.err.p, sizeof(int));
+  sl.ready = true;
+}
+
+void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
+  ADC_REQUIRE(c->kind != ADC_EE, ADC_ERR_UNSUPPORTED, "sliced sigma: IP and EA only");
+  Exec &ex = c->ex;
+  if (!c->sl || !c->sl->ready) build_sl(c);
+  SlCache &sl = *c->sl;
+  int *err = (int *)sl.err.p;
+  const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N;
+  const bool sat = (c->order == 3 && c->x != 0.0);
+  const double x = sat ? c->x : 0.0;
+  // S1 = X1 M11^T (FP64, n1 x n1)
+  TagScope tg(ex, "main");
+  zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, c->M11.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
+  // S1 += Cpl X2, S2 = Cpl^H X1
+  ex.tag = "coupling";
+  sl_pack_B(ex, sl.Bx, X + n1, k, n2, N, 0, 1, 1, false, sl.Cpl);
+  sl_gemm(ex, sl.Cpl, sl.Bx, n1, k, C1(), C1(), S, 1, N, 0, 1, err, sl.w);
+  sl_pack_B(ex, sl.Bx, X, k, n1, N, 0, 1, 1, false, sl.CplT);
+  sl_gemm(ex, sl.CplT, sl.Bx, n2, k, C1(), C0(), S + n1, 1, N, 0, 1, err, sl.w);
+  diag_mul_add(ex, k, n2, c->d2.d(), X + n1, N, S + n1, N, 1.0);
+  if (sat) {
+    if (c->kind == ADC_EA) {
+      const int64_t pv = npairs(v);
+      ex.tag = "ladder";
+      sl_pack_B(ex, sl.Bx, X + n1, k * o, pv, N, pv, o, 1, false, sl.Glad);
+      sl_gemm(ex, sl.Glad, sl.Bx, pv, k * o, CR(x), C1(), S + n1, 1, N, pv, o, err, sl.w);
+      ex.tag = "ring";
+      cplx *T = scratch(c, k * o * v * v);
+      sl_pack_B_ring(ex, sl.Bx, c, X, k, sl.W);
+      sl_gemm(ex, sl.W, sl.Bx, o * v, k * v, C1(), C0(), T, v, o * v * v, 1, v, err, sl.w);
+      pair_pack(ex, T, o * v * v, v * v, v, 1, 0, 1.0, k, o, v, 1, S + n1, N, pv, CR(-x), C1());
+    } else {
+      const int64_t po = npairs(o);
+      ex.tag = "ladder";
+      sl_pack_B(ex, sl.Bx, X + n1, k * v, po, N, 1, v, v, false, sl.Glad);
+      sl_gemm(ex, sl.Glad, sl.Bx, po, k * v, CR(x), C1(), S + n1, v, N, 1, v, err, sl.w);
+      ex.tag = "ring";
+      cplx *T = scratch(c, k * o * v * o);
+      sl_pack_B_ring(ex, sl.Bx, c, X, k, sl.W);
+      sl_gemm(ex, sl.W, sl.Bx, o * v, k * o, CR(-1.0), C0(), T, o, o * v * o, 1, o, err, sl.w);
       pair_pack(ex, T, o * v * o, 0, 1, v * o, o, 1.0, k, 1, o, v, S + n1, N, 0, CR(x), C1());
     }
   }

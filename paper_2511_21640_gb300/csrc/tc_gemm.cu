@@ -319,34 +319,6 @@ __global__ void k_emb_A(const cplx *__restrict__ src, int64_t M, int64_t K, int6
   }
 }
 
-// value of B[n][k] for the three gather patterns
-struct BSrc {
-  const cplx *p;
-  int mode;        // 0 strided, 1 EA ring from packed X2, 2 IP ring from packed X2
-  int64_t s_nh, s_nl, n_in, s_k;
-  int64_t o, v, N, n1;
-  __device__ __forceinline__ cplx get(int64_t n, int64_t k) const {
-    if (mode == 0) {
-      const int64_t nh = n / n_in, nl = n - nh * n_in;
-      return p[nh * s_nh + nl * s_nl + k * s_k];
-    }
-    if (mode == 1) {  // n = (vec, b), k = (kk, c): Xf[vec][kk][c][b]
-      const int64_t vec = n / v, b = n - vec * v;
-      const int64_t kk = k / v, cc = k - kk * v;
-      if (cc == b) return cmake(0.0, 0.0);
-      const int64_t lo_ = cc < b ? cc : b, hi_ = cc < b ? b : cc;
-      cplx x = p[n1 + vec * N + kk * (v * (v - 1) / 2) + pair_index(lo_, hi_, v)];
-      return cc < b ? x : cmake(-x.x, -x.y);
-    }
-    // mode 2: n = (vec, i), k = (kp_, b): Xf[vec][i][kp_][b]
-    const int64_t vec = n / o, i = n - vec * o;
-    const int64_t kq = k / v, b = k - kq * v;
-    if (kq == i) return cmake(0.0, 0.0);
-    const int64_t lo_ = i < kq ? i : kq, hi_ = i < kq ? kq : i;
-    cplx x = p[n1 + vec * N + pair_index(lo_, hi_, o) * v + b];
-    return i < kq ? x : cmake(-x.x, -x.y);
-  }
-};
 
 // B rows: row 2n = [Re | -Im], row 2n+1 = [Im | Re] (conj negates Im first)
 __global__ void k_emb_B(BSrc src, int64_t Nc, int64_t K, int conj, int64_t kp, __nv_bfloat16 *hi,
@@ -500,7 +472,7 @@ __device__ __forceinline__ TgTile tg_decode(const TcJob *__restrict__ jobs, int 
   d.m0 = tm * TC_BM;
   d.n0 = tn * J.bn;
   d.kb_beg = d.split * J.kb_per_split;
-  d.nkb = min(3 * J.kps, d.kb_beg + J.kb_per_split) - d.kb_beg;
+  d.nkb = min(J.nseg * J.kps, d.kb_beg + J.kb_per_split) - d.kb_beg;
   return d;
 }
 
@@ -848,7 +820,7 @@ void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &in, TcGroup &grp, i
   const bool capturing = (cs != cudaStreamCaptureStatusNone);
   if (capturing) may_tune = false;
   struct Plan {
-    int idx, bn, kps, tiles_m, tiles_n, ksplit, kbps;
+    int idx, bn, kps, tiles_m, tiles_n, ksplit, kbps, nseg;
     int64_t N2;
   };
   std::vector<Plan> pl;
@@ -856,7 +828,9 @@ void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &in, TcGroup &grp, i
   grp.flops = 0.0;
   for (int j = 0; j < nj; ++j) {
     const TcJobDesc &d = in[j];
-    ADC_REQUIRE(d.A && d.B && d.out, ADC_ERR_ARG, "tc_gemm_grouped: job operands");
+    ADC_REQUIRE(d.A && d.B && (d.out || d.out32), ADC_ERR_ARG, "tc_gemm_grouped: job operands");
+    ADC_REQUIRE(d.nseg == 3 || d.nseg == 1, ADC_ERR_ARG, "tc_gemm_grouped: products per tile");
+    ADC_REQUIRE(!d.out32 || d.kb_split > 0, ADC_ERR_ARG, "tc_gemm_grouped: raw output needs kb_split");
     ADC_REQUIRE(d.A->kp == d.B->kp, ADC_ERR_ARG, "tc_gemm_grouped: inner sizes differ");
     ADC_REQUIRE(d.A->rows >= d.M && d.B->rows >= 2 * d.N, ADC_ERR_ARG, "tc_gemm_grouped: operand rows");
     ADC_REQUIRE(d.M < (1ll << 31) && 2 * d.N < (1ll << 31), ADC_ERR_UNSUPPORTED, "tc_gemm_grouped: size");
@@ -869,9 +843,10 @@ void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &in, TcGroup &grp, i
     if (p.bn <= 0) p.bn = bn_rule(p.N2);
     ADC_REQUIRE(p.bn >= 32 && p.bn <= TC_BNMAX && p.bn % 32 == 0, ADC_ERR_ARG, "tc_gemm_grouped: tile width");
     p.kps = (int)(2 * d.A->kp / TC_BK);
+    p.nseg = d.nseg;
     p.tiles_m = (int)((d.M + TC_BM - 1) / TC_BM);
     p.tiles_n = (int)((p.N2 + p.bn - 1) / p.bn);
-    work += (double)p.tiles_m * p.tiles_n * 3.0 * p.kps;
+    work += (double)p.tiles_m * p.tiles_n * (double)p.nseg * p.kps;
     const int64_t Kc = d.A->kreal > 0 ? d.A->kreal : d.A->kp;
     grp.flops += 8.0 * (double)d.M * (double)d.N * (double)Kc;
     pl.push_back(p);
@@ -883,7 +858,13 @@ void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &in, TcGroup &grp, i
   const double target = std::max(16.0, work / (4.0 * sms));
   size_t part_need = 0;
   for (auto &p : pl) {
-    const int total_kb = 3 * p.kps;
+    const int total_kb = p.nseg * p.kps;
+    if (in[p.idx].out32) {
+      // raw output: the caller fixes the split (exact FP32 sums need short splits)
+      p.kbps = std::min(in[p.idx].kb_split, total_kb);
+      p.ksplit = (total_kb + p.kbps - 1) / p.kbps;
+      continue;
+    }
     int ks = 1;
     if (total_kb > target) ks = (int)std::min<double>(128.0, std::ceil(total_kb / target));
     p.kbps = (total_kb + ks - 1) / ks;
@@ -917,13 +898,20 @@ void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &in, TcGroup &grp, i
     TcJob &J = grp.host[i];
     std::memset(&J, 0, sizeof(J));
     const int64_t kp2 = 2 * d.A->kp;
+    // one-product jobs read only the hi planes (a single-plane operand has no lo)
     make_map(&J.mAh, d.A->hi.p, d.A->rows, kp2, TC_BM);
-    make_map(&J.mAl, d.A->lo.p, d.A->rows, kp2, TC_BM);
+    make_map(&J.mAl, d.A->lo.p ? d.A->lo.p : d.A->hi.p, d.A->rows, kp2, TC_BM);
     make_map(&J.mBh, d.B->hi.p, d.B->rows, kp2, p.bn);
-    make_map(&J.mBl, d.B->lo.p, d.B->rows, kp2, p.bn);
+    make_map(&J.mBl, d.B->lo.p ? d.B->lo.p : d.B->hi.p, d.B->rows, kp2, p.bn);
+    ADC_REQUIRE(p.nseg == 1 || (d.A->lo.p && d.B->lo.p), ADC_ERR_ARG, "tc_gemm_grouped: three products need lo planes");
     J.out = d.out;
-    J.part = p.ksplit > 1 ? (float *)grp.part.p + poff : nullptr;
-    if (p.ksplit > 1) poff += (size_t)p.ksplit * d.M * p.N2;
+    J.nseg = p.nseg;
+    if (d.out32) {
+      J.part = d.out32;
+    } else {
+      J.part = p.ksplit > 1 ? (float *)grp.part.p + poff : nullptr;
+      if (p.ksplit > 1) poff += (size_t)p.ksplit * d.M * p.N2;
+    }
     J.s_m = d.s_m;
     J.s_nh = d.s_nh;
     J.s_nl = d.s_nl;
@@ -955,7 +943,7 @@ void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &in, TcGroup &grp, i
   ADC_CHECK_LAUNCH();
   for (int i = 0; i < np; ++i) {
     const TcJob &J = grp.host[i];
-    if (J.ksplit <= 1) continue;
+    if (J.ksplit <= 1 || in[pl[i].idx].out32) continue;
     k_tc_reduce<<<grid1d((int64_t)J.M * (J.N2 / 2), 256), 256, 0, ex.stream>>>(
         J.part, J.ksplit, J.M, J.N2, J.out, J.s_m, J.s_nh, J.s_nl, J.n_in, J.alpha, J.beta);
     ADC_CHECK_LAUNCH();

@@ -10,6 +10,36 @@ struct adc_ctx;
 
 namespace adc {
 
+// value of B[n][k] for the three gather patterns of the B operands:
+// strided, the EA ring and the IP ring gathered from the packed satellite block
+struct BSrc {
+  const cplx *p;
+  int mode;        // 0 strided, 1 EA ring from packed X2, 2 IP ring from packed X2
+  int64_t s_nh, s_nl, n_in, s_k;
+  int64_t o, v, N, n1;
+  __device__ __forceinline__ cplx get(int64_t n, int64_t k) const {
+    if (mode == 0) {
+      const int64_t nh = n / n_in, nl = n - nh * n_in;
+      return p[nh * s_nh + nl * s_nl + k * s_k];
+    }
+    if (mode == 1) {  // n = (vec, b), k = (kk, c): Xf[vec][kk][c][b]
+      const int64_t vec = n / v, b = n - vec * v;
+      const int64_t kk = k / v, cc = k - kk * v;
+      if (cc == b) return cmake(0.0, 0.0);
+      const int64_t lo_ = cc < b ? cc : b, hi_ = cc < b ? b : cc;
+      cplx x = p[n1 + vec * N + kk * (v * (v - 1) / 2) + pair_index(lo_, hi_, v)];
+      return cc < b ? x : cmake(-x.x, -x.y);
+    }
+    // mode 2: n = (vec, i), k = (kp_, b): Xf[vec][i][kp_][b]
+    const int64_t vec = n / o, i = n - vec * o;
+    const int64_t kq = k / v, b = k - kq * v;
+    if (kq == i) return cmake(0.0, 0.0);
+    const int64_t lo_ = i < kq ? i : kq, hi_ = i < kq ? kq : i;
+    cplx x = p[n1 + vec * N + pair_index(lo_, hi_, o) * v + b];
+    return i < kq ? x : cmake(-x.x, -x.y);
+  }
+};
+
 // An operand in the real embedding, split into BF16 planes of shape
 // [rows][2*kp] (kp = K rounded up to 64): hi = bf16(x), lo = bf16(x - hi) and,
 // for the six-product split, lo2 = bf16(x - hi - lo). For A, rows = M; for B,
@@ -44,7 +74,7 @@ struct alignas(128) TcJob {
   float *part;  // split-K partials [ksplit][M][N2] or null
   int64_t s_m, s_nh, s_nl, n_in;
   cplx alpha, beta;
-  int M, N2, kps, bn, tiles_n, tiles_m, ksplit, kb_per_split, tile_begin, pad_[3];
+  int M, N2, kps, bn, tiles_n, tiles_m, ksplit, kb_per_split, tile_begin, nseg, pad_[2];
 };
 
 // one job as the host describes it: out = alpha * A B^T + beta * out, same
@@ -56,6 +86,14 @@ struct TcJobDesc {
   cplx *out = nullptr;
   int64_t s_m = 0, s_nh = 0, s_nl = 0, n_in = 1;
   int bn = 0;
+  // products per tile: 3 (hi hi, hi lo, lo hi) or 1 (hi hi: one plane of each
+  // operand, e.g. one pair of slices of the sliced FP64 product)
+  int nseg = 3;
+  // raw mode: when set, the FP32 sums of each K split s are written to
+  // out32[s][M][2N] (real columns) and out/alpha/beta are unused; every split
+  // holds at most kb_split k-blocks of 64 (required in raw mode)
+  float *out32 = nullptr;
+  int kb_split = 0;
 };
 
 // device and pinned host state of a grouped launch. A captured graph copies

@@ -1,0 +1,309 @@
+// FP64-accurate complex GEMM from BF16 slices on the tensor cores.
+//
+// out[m][n] = alpha * sum_k A[m][k] B[n][k] + beta * out[m][n]   (complex)
+//
+// The operands use the real embedding of tc_gemm.cu (an A row is [Re | Im], a
+// complex B row n becomes [Re | -Im] and [Im | Re]). Every row of an operand
+// is scaled by a power of two, 2^E with max |row| < 2^E, and each scaled value
+// y (|y| < 1) is written as a sum of slices y = sum_i d_i 2^(-b i), i = 1..ns,
+// with integer digits d_i = rint((y - d_1 2^-b - ... - d_(i-1) 2^(-b (i-1))) 2^(b i)),
+// so |d_1| <= 2^b and |d_i| <= 2^(b-1) for i >= 2: integers of at most b + 1
+// bits, exact in BF16 for b <= 7. The product of slice i of A and slice j of B
+// over K2 embedded terms is a sum of integers whose partial sums stay below
+// K2 2^(2b); with K2 <= 2^(24 - 2b) (longer inner sizes are split) every
+// partial sum is an integer below 2^24 and the tensor cores' FP32 accumulator
+// holds it exactly. The pairs i + j <= ns + 1 run as one grouped tcgen05 launch
+// (tc_gemm_grouped, one product per tile, raw FP32 outputs) and a combine
+// kernel forms, in FP64, sum over pairs and splits of 2^(E_m + F_n - b (i + j)) P_ij.
+// The error comes only from the dropped slice digits and pairs, about 2^(-b ns)
+// relative to the row and column maxima, whatever K is: an error-free
+// splitting of the products in the manner of Ozaki, Ogita, Oishi and Rump
+// ("Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication", Numer. Algorithms 59, 2012), on BF16
+// tensor cores with integer digits.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "ctx.cuh"
+#include "tc_gemm.cuh"
+#include "tc_slice.cuh"
+
+namespace adc {
+
+namespace {
+
+constexpr int SL_MAXPAIRS = 160;
+
+__device__ __forceinline__ double amax2(cplx x) { return fmax(fabs(x.x), fabs(x.y)); }
+
+// block-wide maximum (blockDim.x a multiple of 32, at most 1024)
+__device__ double block_max(double v) {
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+  }
+  return v;  // valid in thread 0
+}
+
+// exponent E with max < 2^E (0 for an all-zero row)
+__device__ __forceinline__ int exp_above(double amax) {
+  if (!(amax > 0.0)) return 0;
+  int e;
+  frexp(amax, &e);  // amax = f 2^e, f in [0.5, 1)
+  return e;
+}
+
+// E[m] for the rows of A (element (m, k) at src[m*s_m + k*s_k]), one block per row
+__global__ void k_sl_exp_A(const cplx *__restrict__ src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, int *E) {
+  for (int64_t m = blockIdx.x; m < M; m += gridDim.x) {
+    double v = 0.0;
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) v = fmax(v, amax2(src[m * s_m + k * s_k]));
+    v = block_max(v);
+    if (threadIdx.x == 0) E[m] = exp_above(v);
+    __syncthreads();
+  }
+}
+
+// F[n] for the complex rows of B, one block per row
+__global__ void k_sl_exp_B(BSrc src, int64_t Nc, int64_t K, int *F) {
+  for (int64_t n = blockIdx.x; n < Nc; n += gridDim.x) {
+    double v = 0.0;
+    for (int64_t k = threadIdx.x; k < K; k += blockDim.x) v = fmax(v, amax2(src.get(n, k)));
+    v = block_max(v);
+    if (threadIdx.x == 0) F[n] = exp_above(v);
+    __syncthreads();
+  }
+}
+
+// the ns digits of y = x 2^-E, written to planes[i][pos] (plane stride pe) with sign s
+__device__ __forceinline__ void digits(double x, int E, int ns, int b, __nv_bfloat16 *base, int64_t pe,
+                                       int64_t pos0, int64_t pos1) {
+  double y = ldexp(x, -E);
+  for (int i = 1; i <= ns; ++i) {
+    const double d = rint(ldexp(y, b * i));
+    y -= ldexp(d, -b * i);  // exact: the remainder has at most 53 significant bits
+    const __nv_bfloat16 h = __double2bfloat16(d);
+    base[(int64_t)(i - 1) * pe + pos0] = h;
+    if (pos1 >= 0) base[(int64_t)(i - 1) * pe + pos1] = __double2bfloat16(-d);
+  }
+}
+
+// A rows [Re | Im] (conj negates Im), padded to kp with zeros
+__global__ void k_sl_slice_A(const cplx *__restrict__ src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, int conj,
+                             int64_t kp, const int *__restrict__ E, int ns, int b, __nv_bfloat16 *base, int64_t pe) {
+  const int64_t total = M * kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = idx % kp, m = idx / kp;
+    cplx x = cmake(0.0, 0.0);
+    if (k < K) x = src[m * s_m + k * s_k];
+    const double im = conj ? -x.y : x.y;
+    const int64_t row = m * 2 * kp;
+    digits(x.x, E[m], ns, b, base, pe, row + k, -1);
+    digits(im, E[m], ns, b, base, pe, row + kp + k, -1);
+  }
+}
+
+// B rows 2n = [Re | -Im], 2n+1 = [Im | Re] (conj negates Im first)
+__global__ void k_sl_slice_B(BSrc src, int64_t Nc, int64_t K, int conj, int64_t kp, const int *__restrict__ F,
+                             int ns, int b, __nv_bfloat16 *base, int64_t pe) {
+  const int64_t total = Nc * kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = idx % kp, n = idx / kp;
+    cplx x = cmake(0.0, 0.0);
+    if (k < K) x = src.get(n, k);
+    const double im = conj ? -x.y : x.y;
+    const int64_t r0 = (2 * n) * 2 * kp, r1 = (2 * n + 1) * 2 * kp;
+    digits(x.x, F[n], ns, b, base, pe, r0 + k, -1);
+    digits(x.x, F[n], ns, b, base, pe, r1 + kp + k, -1);
+    // row 2n holds -Im, row 2n+1 holds Im: the digits of -y are the negated digits of y
+    digits(im, F[n], ns, b, base, pe, r1 + k, r0 + kp + k);
+  }
+}
+
+struct SlCombine {
+  int npair, ksplit;
+  int sh[SL_MAXPAIRS];  // b (i + j) of each pair, pairs in ascending order
+};
+
+// out[m][n] = alpha 2^(E_m + F_n) sum_p sum_s 2^-sh_p P[p][s][m][2n..2n+1] + beta out
+__global__ void k_sl_combine(const float *__restrict__ P, SlCombine cfg, int64_t M, int64_t N2,
+                             const int *__restrict__ E, const int *__restrict__ F, cplx alpha, cplx beta, cplx *out,
+                             int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in) {
+  const int64_t Nc = N2 / 2, total = M * Nc, per = M * N2;
+  const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = idx % Nc, m = idx / Nc;
+    double re = 0.0, im = 0.0;
+    for (int p = cfg.npair - 1; p >= 0; --p) {  // smallest terms first
+      double pr = 0.0, pi = 0.0;
+      for (int s = 0; s < cfg.ksplit; ++s) {
+        const float2 v = *(const float2 *)(P + ((int64_t)p * cfg.ksplit + s) * per + m * N2 + 2 * n);
+        pr += (double)v.x;
+        pi += (double)v.y;
+      }
+      re += ldexp(pr, -cfg.sh[p]);
+      im += ldexp(pi, -cfg.sh[p]);
+    }
+    const int e = E[m] + F[n];
+    const cplx val0 = cmake(ldexp(re, e), ldexp(im, e));
+    const int64_t nh = n / n_in, nl = n - nh * n_in;
+    cplx *dst = out + m * s_m + nh * s_nh + nl * s_nl;
+    cplx val = cmul(alpha, val0);
+    if (use_beta) val = cadd(val, cmul(beta, *dst));
+    *dst = val;
+  }
+}
+
+int ceil_log2(int64_t x) {
+  int l = 0;
+  while ((1ll << l) < x) ++l;
+  return l;
+}
+
+void set_views(SlMat &d) {
+  const int64_t pe = d.rows * 2 * d.kp;
+  d.s.resize(d.ns);
+  for (int i = 0; i < d.ns; ++i) {
+    TcMat &t = d.s[i];
+    t.hi.ex = nullptr;  // a view into d.planes
+    t.hi.p = (__nv_bfloat16 *)d.planes.p + (int64_t)i * pe;
+    t.hi.bytes = (size_t)pe * sizeof(__nv_bfloat16);
+    t.planes = 1;
+    t.rows = d.rows;
+    t.kp = d.kp;
+    t.kreal = d.kreal;
+  }
+}
+
+void alloc_sl(Exec &ex, SlMat &d, int64_t rows, int64_t expn) {
+  const size_t bytes = (size_t)d.ns * rows * 2 * d.kp * sizeof(__nv_bfloat16);
+  if (d.planes.bytes < bytes) {
+    d.s.clear();
+    d.planes.reset();
+    d.planes = DBuf(ex, bytes);
+  }
+  if (d.exps.bytes < (size_t)expn * sizeof(int)) {
+    d.exps.reset();
+    d.exps = DBuf(ex, (size_t)std::max<int64_t>(expn, 1) * sizeof(int));
+  }
+  d.rows = rows;
+  set_views(d);
+}
+
+}  // namespace
+
+SlParams sl_params(int64_t K, int bits) {
+  SlParams p;
+  p.kp = (K + 63) / 64 * 64;
+  if (p.kp == 0) p.kp = 64;
+  const int64_t K2 = 2 * p.kp;
+  int b = (24 - ceil_log2(K2)) / 2;
+  b = std::max(4, std::min(7, b));
+  p.b = b;
+  p.ns = (bits + b - 1) / b;
+  p.kb_split = (int)((1ll << (24 - 2 * b)) / 64);
+  return p;
+}
+
+void sl_pack_A(Exec &ex, SlMat &dst, const cplx *src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, bool conj,
+               int bits) {
+  const SlParams p = sl_params(K, bits);
+  dst.kp = p.kp;
+  dst.kreal = K;
+  dst.ns = p.ns;
+  dst.bits = p.b;
+  dst.kb_split = p.kb_split;
+  alloc_sl(ex, dst, M, M);
+  if (M <= 0) return;
+  k_sl_exp_A<<<(unsigned)std::min<int64_t>(M, 65535), 256, 0, ex.stream>>>(src, M, K, s_m, s_k, (int *)dst.exps.p);
+  ADC_CHECK_LAUNCH();
+  k_sl_slice_A<<<grid1d(M * dst.kp, 256), 256, 0, ex.stream>>>(src, M, K, s_m, s_k, conj ? 1 : 0, dst.kp,
+                                                               (const int *)dst.exps.p, dst.ns, dst.bits,
+                                                               (__nv_bfloat16 *)dst.planes.p, M * 2 * dst.kp);
+  ADC_CHECK_LAUNCH();
+}
+
+static void sl_pack_B_impl(Exec &ex, SlMat &dst, const BSrc &s, int64_t Nc, int64_t K, bool conj, const SlMat &like) {
+  ADC_REQUIRE(like.kreal == K, ADC_ERR_ARG, "sl_pack_B: inner size differs from the A operand");
+  dst.kp = like.kp;
+  dst.kreal = K;
+  dst.ns = like.ns;
+  dst.bits = like.bits;
+  dst.kb_split = like.kb_split;
+  alloc_sl(ex, dst, 2 * Nc, Nc);
+  if (Nc <= 0) return;
+  k_sl_exp_B<<<(unsigned)std::min<int64_t>(Nc, 65535), 256, 0, ex.stream>>>(s, Nc, K, (int *)dst.exps.p);
+  ADC_CHECK_LAUNCH();
+  k_sl_slice_B<<<grid1d(Nc * dst.kp, 256), 256, 0, ex.stream>>>(s, Nc, K, conj ? 1 : 0, dst.kp,
+                                                                (const int *)dst.exps.p, dst.ns, dst.bits,
+                                                                (__nv_bfloat16 *)dst.planes.p, 2 * Nc * 2 * dst.kp);
+  ADC_CHECK_LAUNCH();
+}
+
+void sl_pack_B(Exec &ex, SlMat &dst, const cplx *src, int64_t Nc, int64_t K, int64_t s_nh, int64_t s_nl,
+               int64_t n_in, int64_t s_k, bool conj, const SlMat &like) {
+  BSrc s{src, 0, s_nh, s_nl, n_in, s_k, 0, 0, 0, 0};
+  sl_pack_B_impl(ex, dst, s, Nc, K, conj, like);
+}
+
+void sl_pack_B_ring(Exec &ex, SlMat &dst, const adc_ctx *c, const cplx *X, int64_t k, const SlMat &like) {
+  BSrc s{X, c->kind == ADC_EA ? 1 : 2, 0, 0, 1, 0, c->o, c->v, c->N, c->n1};
+  const int64_t Nc = (c->kind == ADC_EA) ? k * c->v : k * c->o;
+  sl_pack_B_impl(ex, dst, s, Nc, c->o * c->v, false, like);
+}
+
+void sl_gemm(Exec &ex, const SlMat &A, const SlMat &B, int64_t M, int64_t N, cplx alpha, cplx beta, cplx *out,
+             int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, SlWork &w) {
+  ADC_REQUIRE(A.kp == B.kp && A.ns == B.ns && A.bits == B.bits, ADC_ERR_ARG, "sl_gemm: operands sliced differently");
+  ADC_REQUIRE(A.rows >= M && B.rows >= 2 * N, ADC_ERR_ARG, "sl_gemm: operand rows");
+  if (M <= 0 || N <= 0) return;
+  if (n_in <= 0) n_in = 1;
+  const int64_t N2 = 2 * N;
+  const int kps = (int)(2 * A.kp / 64);
+  const int kbs = std::min(A.kb_split, kps);
+  const int ksplit = (kps + kbs - 1) / kbs;
+  SlCombine cfg{};
+  std::vector<std::pair<int, int>> pairs;
+  for (int g = 2; g <= A.ns + 1; ++g)
+    for (int i = 1; i < g; ++i)
+      if (i <= A.ns && g - i <= A.ns) pairs.push_back({i, g - i});
+  ADC_REQUIRE((int)pairs.size() <= SL_MAXPAIRS, ADC_ERR_UNSUPPORTED, "sl_gemm: too many slice pairs");
+  cfg.npair = (int)pairs.size();
+  cfg.ksplit = ksplit;
+  const size_t per = (size_t)ksplit * M * N2;
+  const size_t need = per * pairs.size() * sizeof(float);
+  if (w.part.bytes < need) {
+    w.part.reset();
+    w.part = DBuf(ex, need);
+  }
+  std::vector<TcJobDesc> jobs(pairs.size());
+  for (size_t q = 0; q < pairs.size(); ++q) {
+    TcJobDesc &d = jobs[q];
+    d.A = &A.s[pairs[q].first - 1];
+    d.B = &B.s[pairs[q].second - 1];
+    d.M = M;
+    d.N = N;
+    d.nseg = 1;
+    d.out32 = (float *)w.part.p + q * per;
+    d.kb_split = kbs;
+    d.bn = N2 <= 32 ? 32 : N2 <= 64 ? 64 : N2 <= 128 ? 128 : 256;
+    cfg.sh[q] = A.bits * (pairs[q].first + pairs[q].second);
+  }
+  tc_gemm_grouped(ex, jobs, w.grp, err, false);
+  int pr = ex.prof_begin("sl_combine", 0.0);
+  k_sl_combine<<<grid1d(M * N, 256), 256, 0, ex.stream>>>((const float *)w.part.p, cfg, M, N2, (const int *)A.exps.p,
+                                                          (const int *)B.exps.p, alpha, beta, out, s_m, s_nh, s_nl,
+                                                          n_in);
+  ADC_CHECK_LAUNCH();
+  ex.prof_end(pr);
+}
+
+}  // namespace adc

@@ -8,8 +8,12 @@ Tolerances:
   cores accumulate in FP32, whose rounding grows like sqrt(K) * 2^-24 for
   the longest inner sizes here (K <= 2e5 embedded terms): about 2e-5 in all,
   so 1e-4 leaves a factor of five.
+* Sliced (FP64-accurate) tensor-core product and sigma: 1e-10. The digit
+  products are exact in FP32; what remains is the truncation after about 40
+  bits relative to the row and column maxima, about 1e-11 of the output norm
+  for these value distributions, plus the FP64 combination.
 * Eigenvalues: 1e-8 Eh (FP64 Davidson), 1e-6 Eh (mixed Davidson with FP64
-  refinement).
+  or sliced refinement).
 """
 import numpy as np
 import pytest
@@ -61,6 +65,15 @@ def test_bf16x6_gemm(gpu, M, N, K):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 16, 64), (200, 40, 1000), (129, 130, 70), (1000, 300, 5000),
+                                   (130, 3, 70000), (300, 1, 129)])
+def test_sliced_gemm(gpu, M, N, K):
+    """Sliced FP64-accurate product (exact digit products in FP32, FP64
+    combination); (130, 3, 70000) splits K for exactness."""
+    err, ms = gpu.diag_gemm(5, M, N, K, seed=7)
+    assert err < 1e-10, err
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 16, 64), (200, 40, 1000), (129, 130, 70), (1000, 300, 5000),
                                    (64, 8, 20000), (300, 1, 129)])
 def test_grouped_gemm_one_job(gpu, M, N, K):
     """The grouped persistent launch with an autotuned tile width, one job."""
@@ -108,6 +121,8 @@ def test_sigma_parity(gpu, kind, o, v, Q, order, x, seed):
         assert _rel(Sm, ref).max() < 1e-4
         Sm6 = ctx.sigma(X, "bf16x6")
         assert _rel(Sm6, ref).max() < 1e-4, _rel(Sm6, ref).max()
+        Ss = ctx.sigma(X, "sliced")
+        assert _rel(Ss, ref).max() < 1e-10, _rel(Ss, ref).max()
         d = ctx.diagonal()
         dref = oadc.diagonal_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, amp=amp)
         assert np.abs(d - dref).max() < 1e-12 * max(1.0, np.abs(dref).max())
@@ -124,7 +139,13 @@ def test_sigma_zero_vectors_and_k0(gpu):
         X = np.zeros((2, ctx.N), np.complex128)
         assert np.abs(ctx.sigma(X, "fp64")).max() == 0.0
         assert np.abs(ctx.sigma(X, "bf16x3")).max() == 0.0
+        assert np.abs(ctx.sigma(X, "sliced")).max() == 0.0
         assert gpu.lib.adc_sigma(ctx._h, None, None, 0, 0) == 0
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=2) as ctx:
+        X = np.zeros((1, ctx.N), np.complex128)
+        with pytest.raises(gpu.AdcError) as e:
+            ctx.sigma(X, "sliced")
+        assert e.value.code == -6
 
 
 # ---------------------------------------------------------------- eigenvalues
@@ -166,6 +187,23 @@ def test_mixed_davidson_refined(gpu, kind, o, v, Q, x, prec):
     with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=3, x=x) as ctx:
         om, Y, e64, st, rc = ctx.davidson(4, tol=1e-7, precision=prec)
         assert rc == 0
+        assert np.abs(om - w).max() < 1e-6
+        assert np.all(e64 <= 1e-7)
+        R = Y @ M.T - om[:, None] * Y
+        assert np.linalg.norm(R, axis=1).max() < 1e-6
+
+
+@pytest.mark.parametrize("kind,o,v,Q,x", [("EA", 6, 30, 64, 0.5), ("IP", 7, 26, 50, 0.5), ("EA", 5, 24, 40, 1.0)])
+def test_mixed_davidson_sliced_refinement(gpu, kind, o, v, Q, x):
+    """Mixed Davidson whose refinement products (FP64 base of the Ritz vectors,
+    final residual check) are the sliced tensor-core product."""
+    p = make_problem(o, v, Q, seed=22, sigma=0.06, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    M = oadc.explicit_matrix(kind, 3, x, p.B, p.eps_occ, p.eps_vir)
+    w = np.linalg.eigvalsh(M)[:4]
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=3, x=x, refine="sliced") as ctx:
+        om, Y, e64, st, rc = ctx.davidson(4, tol=1e-7, precision="bf16x3")
+        assert rc == 0
+        assert st["sigma_calls_fp64"] > 0
         assert np.abs(om - w).max() < 1e-6
         assert np.all(e64 <= 1e-7)
         R = Y @ M.T - om[:, None] * Y
