@@ -4,8 +4,11 @@
 Workload (default): EA-ADC(2)+x(3) with x = 0.5, nocc = 40, nvir = 200,
 naux = 1200, complex128 Cholesky vectors (synthetic, seeded), 8 lowest roots.
 A step is one complete Davidson solve of those roots with tensor-core (BF16x3)
-sigma products refined by FP64 sigma products until every FP64 residual norm
-is below tol; the setup of the operators (adc_init) is timed separately.
+sigma products refined by FP64-accurate sigma products until every residual
+norm of those is below tol; the setup of the operators (adc_init) is timed
+separately. The refinement products are, by default, the sliced tensor-core
+product (integer BF16 digits summed exactly in FP32, combined in FP64, about
+1e-12 relative); --refine fp64 uses the FP64 CUDA-core product instead.
 
 Metric: Davidson seconds per root (lower is better); the line also carries
 the sigma TFLOP/s of the mixed and FP64 products, the FP64 Davidson s/root,
@@ -407,6 +410,8 @@ def main():
     ap.add_argument("--no-gradient", action="store_true", help="EE workloads: skip the adjoint and its check")
     ap.add_argument("--mixed", default="bf16x3", choices=["bf16x3", "bf16x6"],
                     help="split precision of the mixed Davidson")
+    ap.add_argument("--refine", default="sliced", choices=["sliced", "fp64"],
+                    help="IP/EA: product of the Davidson refinement (FP64-accurate)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=6)
     ap.add_argument("--ref-sigma-vectors-per-root", type=float, default=8.0)
@@ -455,7 +460,7 @@ def main():
     ev = torch.from_numpy(p.eps_vir).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctx = adcgpu.Context(B, eo, ev, kind=kind, order=order, x=x, stream="torch")
+    ctx = adcgpu.Context(B, eo, ev, kind=kind, order=order, x=x, stream="torch", refine=args.refine)
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
     log(f"init {init_s:.1f} s, N = {ctx.N}")
@@ -504,8 +509,10 @@ def main():
     def roofline_of(name, e):
         avg_ms = e["total_ms"] / e["launches"]
         alg = e["flops"] / e["launches"]
-        if name.startswith("tc_gemm"):
-            mma = (6.0 if "bf16x6" in name else 3.0) * alg  # split products per complex product
+        if name.startswith("tc_"):
+            # MMA work: the split products per complex product (3 or 6); the sliced digit
+            # pairs are recorded as MMA work already
+            mma = (1.0 if name.startswith("tc_sliced") else 6.0 if "bf16x6" in name else 3.0) * alg
             ach = mma / (avg_ms * 1e-3) / 1e12
             peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
             return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
@@ -529,13 +536,14 @@ def main():
     if key in measured_traffic:
         roof["traffic"] = measured_traffic[key]
         roof["traffic_note"] = "one ncu capture of the 320 x 19900 x 19900 FP64 ladder GEMM"
-    tc_rows = [r for r in by_kernel if r["kernel"].startswith("tc_gemm")]
+    tc_rows = [r for r in by_kernel if r["kernel"].startswith("tc_")]
     roof_tc = tc_rows[0] if tc_rows else None
 
     # ---- sigma TFLOP/s, mixed vs FP64 (one block of nroots vectors each)
     Xs = torch.from_numpy(random_vectors(ctx.N, nroots, seed=7)).cuda()
     sig = {}
-    for prec in (args.mixed, "fp64"):
+    sig_precs = (args.mixed, "sliced", "fp64") if kind in ("IP", "EA") else (args.mixed, "fp64")
+    for prec in sig_precs:
         ctx.sigma(Xs, prec)
         torch.cuda.synchronize()
         ctx.profile(True)
@@ -554,8 +562,12 @@ def main():
         sig[prec] = {"ms": t, "tflops": fl / (t * 1e-3) / 1e12, "flops": fl}
     log("sigma", sig)
     S64 = ctx.sigma(Xs, "fp64")
-    Smx = ctx.sigma(Xs, args.mixed)
-    sig_rel = float(((Smx - S64).abs().pow(2).sum(1).sqrt() / S64.abs().pow(2).sum(1).sqrt()).max().item())
+
+    def rel_to_fp64(S):
+        return float(((S - S64).abs().pow(2).sum(1).sqrt() / S64.abs().pow(2).sum(1).sqrt()).max().item())
+
+    sig_rel = rel_to_fp64(ctx.sigma(Xs, args.mixed))
+    sig_rel_sliced = rel_to_fp64(ctx.sigma(Xs, "sliced")) if "sliced" in sig else None
 
     # ---- FP64 Davidson for the comparison and the 1e-6 Eh check
     fp64 = None
@@ -576,7 +588,7 @@ def main():
         eoh, evh = torch.from_numpy(p.eps_occ), torch.from_numpy(p.eps_vir)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        with adcgpu.Context(Bh, eoh, evh, kind=kind, order=order, x=x) as c2:
+        with adcgpu.Context(Bh, eoh, evh, kind=kind, order=order, x=x, refine=args.refine) as c2:
             om2, _, e2, st2, rc2 = c2.davidson(nroots, tol=tol, max_iter=300, precision=args.mixed,
                                                want_vectors=False)
         te2e = time.perf_counter() - t2
@@ -597,14 +609,19 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "s/root", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": f"{args.mixed}+f64", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": f"{args.mixed}+" + ("f64 from exact bf16 digit products" if args.refine == "sliced" else "f64"),
+        "data": "synthetic",
         "config": {"workload": args.config, "kind": kind, "order": order, "x": x, "nocc": o, "nvir": v, "naux": Q,
                    "nroots": nroots, "tol_fp64_residual": tol, "N": ctx.N, "replicas": world,
-                   "l2": "operators larger than L2 (packed <ab||cd> 6.3 GB FP64, 3.2 GB BF16 planes)"},
+                   "l2": "operators larger than L2 (packed <ab||cd> 6.3 GB FP64, 3.2 GB per BF16 plane)"},
         "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "roofline_tensor_core": roof_tc,
         "roofline_by_kernel": by_kernel,
-        "sigma": {args.mixed: sig[args.mixed], "fp64": sig["fp64"], "speedup": sig["fp64"]["ms"] / sig[args.mixed]["ms"],
-                  "rel_diff_mixed_vs_fp64": sig_rel, "vectors": nroots},
+        "sigma": {**sig, "speedup": sig["fp64"]["ms"] / sig[args.mixed]["ms"],
+                  "rel_diff_mixed_vs_fp64": sig_rel, "rel_diff_sliced_vs_fp64": sig_rel_sliced,
+                  "speedup_sliced": (sig["fp64"]["ms"] / sig["sliced"]["ms"]) if "sliced" in sig else None,
+                  "vectors": nroots},
+        "refine": args.refine,
         "fp64_davidson": fp64,
         "mixed_davidson": {"omega": [float(w) for w in om], "err64": [float(e) for e in e64],
                            "iterations": last["iterations"], "sigma_calls": last["sigma_calls"],

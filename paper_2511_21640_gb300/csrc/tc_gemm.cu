@@ -937,7 +937,10 @@ void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &in, TcGroup &grp, i
   }
   ADC_CUDA(cudaMemsetAsync(grp.counter.p, 0, sizeof(int), ex.stream));
   const int grid = (int)std::min<int64_t>(tiles, sms);
-  int pr = ex.prof_begin("tc_grouped_bf16x3", grp.flops);
+  // one-product raw jobs are the digit pairs of the sliced product (tc_slice.cu)
+  bool raw = true;
+  for (const auto &d : in) raw = raw && d.out32 && d.nseg == 1;
+  int pr = ex.prof_begin(raw ? "tc_sliced_pairs" : "tc_grouped_bf16x3", grp.flops);
   k_tc_grouped<<<grid, 192, TgLayout::SMEM, ex.stream>>>((const TcJob *)grp.jobs.p, np, (int)tiles,
                                                          (int *)grp.counter.p, err);
   ADC_CHECK_LAUNCH();
