@@ -412,6 +412,8 @@ def main():
                     help="split precision of the mixed Davidson")
     ap.add_argument("--refine", default="sliced", choices=["sliced", "fp64"],
                     help="IP/EA: product of the Davidson refinement (FP64-accurate)")
+    ap.add_argument("--e2e-setup", default="sliced", choices=["sliced", "fp64"],
+                    help="IP/EA/EE: adc_init contractions of the end-to-end run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=6)
     ap.add_argument("--ref-sigma-vectors-per-root", type=float, default=8.0)
@@ -588,13 +590,20 @@ def main():
         eoh, evh = torch.from_numpy(p.eps_occ), torch.from_numpy(p.eps_vir)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        with adcgpu.Context(Bh, eoh, evh, kind=kind, order=order, x=x, refine=args.refine) as c2:
+        with adcgpu.Context(Bh, eoh, evh, kind=kind, order=order, x=x, refine=args.refine,
+                            setup=args.e2e_setup) as c2:
+            t3 = time.perf_counter()
             om2, _, e2, st2, rc2 = c2.davidson(nroots, tol=tol, max_iter=300, precision=args.mixed,
                                                want_vectors=False)
         te2e = time.perf_counter() - t2
-        log(f"e2e {te2e:.1f} s")
+        log(f"e2e {te2e:.1f} s (init {t3 - t2:.1f} s)")
+        ref_om = om64 if fp64 is not None else om
         e2e = {"value": te2e / nroots, "unit": "s/root", "h2d_bytes_per_step": int(p.B.nbytes + 8 * (o + v)),
-               "d2h_bytes_per_step": int(16 * nroots), "includes": "adc_init (H2D copy + operator setup) + adc_davidson"}
+               "d2h_bytes_per_step": int(16 * nroots),
+               "includes": "adc_init (H2D copy + operator setup) + adc_davidson",
+               "setup": args.e2e_setup, "init_s": t3 - t2, "rc": int(rc2),
+               "max_eig_diff_vs_" + ("fp64_davidson" if fp64 is not None else "timed_solve"):
+                   float(np.abs(np.asarray(om2) - np.asarray(ref_om)).max())}
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_rows > 0:

@@ -99,6 +99,11 @@ typedef struct {
   int refine;           /* products of adc_davidson's refinement (the FP64 base
                            of the Ritz vectors and the final residual check):
                            ADC_PREC_FP64 (default) or ADC_PREC_SLICED (IP/EA) */
+  int setup;            /* dense contractions of adc_init: ADC_PREC_FP64
+                           (default) or ADC_PREC_SLICED (those of at least 2^24
+                           flops as the sliced product with about 48
+                           significant bits; the operators then differ from
+                           the FP64 ones by about 1e-13 relative) */
 } adc_opts;
 
 typedef struct {

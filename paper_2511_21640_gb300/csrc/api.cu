@@ -147,6 +147,8 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
     if (c->opts.herm_tol <= 0.0) c->opts.herm_tol = 1e-12;
     ADC_REQUIRE(c->opts.refine == ADC_PREC_FP64 || c->opts.refine == ADC_PREC_SLICED, ADC_ERR_ARG,
                 "opts.refine: ADC_PREC_FP64 or ADC_PREC_SLICED");
+    ADC_REQUIRE(c->opts.setup == ADC_PREC_FP64 || c->opts.setup == ADC_PREC_SLICED, ADC_ERR_ARG,
+                "opts.setup: ADC_PREC_FP64 or ADC_PREC_SLICED");
     c->kind = kind;
     c->order = order;
     c->x = (order == 3) ? x : 0.0;
@@ -196,8 +198,11 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
         throw Error(ADC_ERR_ARG, "B is not Hermitian in (p,q) (max deviation " + std::to_string(h[0]) +
                                      ", max |B| " + std::to_string(h[1]) + ")");
     }
+    // the setup's large contractions as the sliced tensor-core product when asked for
+    c->ex.sliced_bits = (c->opts.setup == ADC_PREC_SLICED) ? 48 : 0;
     if (kind == ADC_EE) setup_ee(c);
     else setup_operators(c);
+    c->ex.sliced_bits = 0;
     *out = c;
     return ADC_OK;
   } catch (const adc::Error &e) {

@@ -9,22 +9,23 @@ namespace adc {
 
 namespace {
 
-constexpr int GA = 64;   // rows of A per CTA (gram)
 constexpr int GK = 16;   // K staged per step (gram)
 
-// part[chunk][a][b] = sum_{k in chunk} conj(A[a][k]) B[b][k], GB rows of B per
-// CTA. Three FP64 products per complex product (3M): with a' = conj(a),
-// T1 = a'r br, T2 = a'i bi, T3 = (a'r + a'i)(br + bi); the sums are formed
-// once per staged element.
-template <int GB>
+// part[chunk][a][b] = sum_{k in chunk} conj(A[a][k]) B[b][k], GA rows of A
+// (64, or 32 for short subspaces) and GB rows of B per CTA. Three FP64
+// products per complex product (3M): with a' = conj(a), T1 = a'r br,
+// T2 = a'i bi, T3 = (a'r + a'i)(br + bi); the sums are formed once per staged
+// element.
+template <int GA, int GB>
 __global__ void __launch_bounds__(256)
 k_gram(const cplx *__restrict__ A, int64_t lda, int na, const cplx *__restrict__ B, int64_t ldb, int nb,
        int64_t n, int64_t chunk, cplx *part) {
-  constexpr int PB = GB / 4;  // b rows per thread
+  constexpr int NG = 256 / GA;  // groups of threads sharing a row of A
+  constexpr int PB = GB / NG;   // b rows per thread
   __shared__ double Ar[GK][GA + 1], Ai[GK][GA + 1], As[GK][GA + 1];
   __shared__ double Br[GK][GB + 1], Bi[GK][GB + 1], Bs[GK][GB + 1];
   const int t = threadIdx.x;
-  const int al = t & 63, bg = t >> 6;
+  const int al = t % GA, bg = t / GA;
   const int a0 = blockIdx.y * GA, b0 = blockIdx.z * GB;
   const int64_t k_beg = (int64_t)blockIdx.x * chunk;
   const int64_t k_end = min(n, k_beg + chunk);
@@ -151,6 +152,7 @@ void gram(Exec &ex, const cplx *A, int64_t lda, int na, const cplx *B, int64_t l
     if (g_sms_blockops <= 0) g_sms_blockops = 148;
   }
   const int GB = nb <= 8 ? 8 : 16;
+  const int GA = na <= 32 ? 32 : 64;
   const int gy = (na + GA - 1) / GA, gz = (nb + GB - 1) / GB;
   int64_t nchunk = std::max<int64_t>(1, (4 * (int64_t)g_sms_blockops) / (gy * gz));
   nchunk = std::min<int64_t>(nchunk, std::max<int64_t>(1, n / (4 * GK)));
@@ -160,10 +162,15 @@ void gram(Exec &ex, const cplx *A, int64_t lda, int na, const cplx *B, int64_t l
   ADC_REQUIRE(nchunk < (1ll << 31) && gy <= 65535 && gz <= 65535, ADC_ERR_UNSUPPORTED, "gram: shape");
   DBuf part = cbuf(ex, nchunk * (int64_t)na * nb);
   int pr = ex.prof_begin("gram_fp64", 8.0 * (double)na * nb * (double)n);
-  if (GB == 8)
-    k_gram<8><<<dim3((unsigned)nchunk, gy, gz), 256, 0, ex.stream>>>(A, lda, na, B, ldb, nb, n, chunk, part.c());
+  const dim3 grid((unsigned)nchunk, gy, gz);
+  if (GA == 32 && GB == 8)
+    k_gram<32, 8><<<grid, 256, 0, ex.stream>>>(A, lda, na, B, ldb, nb, n, chunk, part.c());
+  else if (GA == 32)
+    k_gram<32, 16><<<grid, 256, 0, ex.stream>>>(A, lda, na, B, ldb, nb, n, chunk, part.c());
+  else if (GB == 8)
+    k_gram<64, 8><<<grid, 256, 0, ex.stream>>>(A, lda, na, B, ldb, nb, n, chunk, part.c());
   else
-    k_gram<16><<<dim3((unsigned)nchunk, gy, gz), 256, 0, ex.stream>>>(A, lda, na, B, ldb, nb, n, chunk, part.c());
+    k_gram<64, 16><<<grid, 256, 0, ex.stream>>>(A, lda, na, B, ldb, nb, n, chunk, part.c());
   ADC_CHECK_LAUNCH();
   k_gram_reduce<<<(na * nb + 255) / 256, 256, 0, ex.stream>>>(part.c(), (int)nchunk, na, nb, alpha, G, ldg);
   ADC_CHECK_LAUNCH();

@@ -261,15 +261,24 @@ struct Davidson {
     return nk;
   }
 
-  // Rayleigh-Ritz on V[0:m]: w (host copy), Y, SY for the lowest kr, R for nroots
+  // Rayleigh-Ritz on V[0:m]: w (host copy), Y and SY for the nroots lowest
+  // (more columns only when a collapse asks for them: ritz_vectors), R for nroots
+  int ycols = 0;  // columns of Y and SY formed from the current eigenvectors Cv
+  void ritz_vectors(int nr) {
+    nr = std::min(nr, std::min(m, krmax));
+    if (nr <= ycols) return;
+    // Y[r][n] = sum_i Cv[i][r] V[i][n], SY likewise from AV (columns ycols .. nr)
+    combine(ex, Cv.c() + ycols, mmax, m, nr - ycols, V.c(), N, N, C1(), C0(), Y.c() + (int64_t)ycols * N, N);
+    combine(ex, Cv.c() + ycols, mmax, m, nr - ycols, AV.c(), N, N, C1(), C0(), SY.c() + (int64_t)ycols * N, N);
+    ycols = nr;
+  }
   std::vector<double> ritz(int nr) {
     nr = std::min(std::max(nr, nroots), std::min(m, krmax));
     k_hermitize<<<(m * m + 255) / 256, 256, 0, ex.stream>>>(G.c(), mmax, m, H.c(), mmax);
     ADC_CHECK_LAUNCH();
     jacobi_eigh(ex, H.c(), m, mmax, w.d(), Cv.c(), mmax, (int *)info.p);
-    // Y[r][n] = sum_i Cv[i][r] V[i][n], SY likewise from AV
-    combine(ex, Cv.c(), mmax, m, nr, V.c(), N, N, C1(), C0(), Y.c(), N);
-    combine(ex, Cv.c(), mmax, m, nr, AV.c(), N, N, C1(), C0(), SY.c(), N);
+    ycols = 0;
+    ritz_vectors(std::min(nr, nroots));
     k_residual<<<grid1d((int64_t)nroots * N, 256), 256, 0, ex.stream>>>(SY.c(), Y.c(), w.d(), nroots, N, R.c());
     ADC_CHECK_LAUNCH();
     std::vector<double> wh(m);
@@ -280,6 +289,7 @@ struct Davidson {
 
   // V <- Y (orthonormal Ritz vectors), AV <- sigma64(Y) or SY, G <- Y^H AV
   void collapse(int nr, bool fp64_sigma) {
+    ritz_vectors(nr);
     ADC_CUDA(cudaMemcpyAsync(V.c(), Y.c(), (int64_t)nr * N * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
     if (fp64_sigma) apply_sigma(V.c(), AV.c(), nr, prec64);
     else

@@ -29,9 +29,11 @@ __device__ inline double block_sum(double v, double *red) {
 // A (n x n, leading dimension lda) is overwritten; eigenvalues ascending into
 // w, eigenvectors as columns of Vout (leading dimension ldv). Vwork n x n.
 // info[0] = sweeps used, or -1 when the sweep limit was reached.
+// With in_smem the matrix and the eigenvector work array live in shared
+// memory for the whole iteration (n up to about 80), else in global memory.
 __global__ void __launch_bounds__(1024)
-k_jacobi(cplx *A, int n, int lda, cplx *Vwork, double *w, cplx *Vout, int ldv, int *info,
-         int max_sweeps, double rel_tol) {
+k_jacobi(cplx *Ag, int n, int ldag, cplx *Vg, double *w, cplx *Vout, int ldv, int *info,
+         int max_sweeps, double rel_tol, int in_smem) {
   extern __shared__ double sm[];
   const int np = n + (n & 1);       // even number of players
   const int npairs = np / 2;
@@ -43,6 +45,17 @@ k_jacobi(cplx *A, int n, int lda, cplx *Vwork, double *w, cplx *Vout, int ldv, i
   int *pq = pp + npairs;
   double *red = (double *)(pq + npairs);
   const int tid = threadIdx.x, nt = blockDim.x;
+  cplx *A = Ag, *Vwork = Vg;
+  int lda = ldag;
+  if (in_smem) {
+    // after the 64 reduction slots, 16-byte aligned
+    uintptr_t base = ((uintptr_t)(red + 64) + 15) & ~(uintptr_t)15;
+    A = (cplx *)base;
+    Vwork = A + (int64_t)n * n;
+    lda = n;
+    for (int idx = tid; idx < n * n; idx += nt) A[idx] = Ag[(int64_t)(idx / n) * ldag + idx % n];
+    __syncthreads();
+  }
 
   for (int idx = tid; idx < n * n; idx += nt) {
     int r = idx / n, cI = idx % n;
@@ -138,6 +151,11 @@ k_jacobi(cplx *A, int n, int lda, cplx *Vwork, double *w, cplx *Vout, int ldv, i
     w[rank] = di;
     for (int r = 0; r < n; ++r) Vout[(int64_t)r * ldv + rank] = Vwork[(int64_t)r * n + i];
   }
+  if (in_smem) {
+    __syncthreads();
+    // the diagonalised matrix back to the caller's array (its diagonal holds the eigenvalues)
+    for (int idx = tid; idx < n * n; idx += nt) Ag[(int64_t)(idx / n) * ldag + idx % n] = A[idx];
+  }
   if (tid == 0) info[0] = done ? sweeps : -1;
 }
 
@@ -150,12 +168,16 @@ void jacobi_eigh(Exec &ex, cplx *A, int n, int lda, double *w, cplx *V, int ldv,
   int np = n + (n & 1), npairs = np / 2;
   size_t smem = (size_t)npairs * 4 * sizeof(double) + (size_t)(2 * npairs + 2) * sizeof(int) +
                 64 * sizeof(double);
+  constexpr size_t kMaxSmem = 200 * 1024;
+  const size_t mats = 16 + 2 * (size_t)n * n * sizeof(cplx);
+  const int in_smem = (smem + mats <= kMaxSmem) ? 1 : 0;
+  if (in_smem) smem += mats;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    ADC_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem));
     attr_set = true;
   }
-  k_jacobi<<<1, 1024, smem, ex.stream>>>(A, n, lda, work.c(), w, V, ldv, info_dev, 40, 1e-14);
+  k_jacobi<<<1, 1024, smem, ex.stream>>>(A, n, lda, work.c(), w, V, ldv, info_dev, 40, 1e-14, in_smem);
   ADC_CHECK_LAUNCH();
 }
 

@@ -278,32 +278,74 @@ void sl_gemm(Exec &ex, const SlMat &A, const SlMat &B, int64_t M, int64_t N, cpl
   ADC_REQUIRE((int)pairs.size() <= SL_MAXPAIRS, ADC_ERR_UNSUPPORTED, "sl_gemm: too many slice pairs");
   cfg.npair = (int)pairs.size();
   cfg.ksplit = ksplit;
-  const size_t per = (size_t)ksplit * M * N2;
-  const size_t need = per * pairs.size() * sizeof(float);
+  for (size_t q = 0; q < pairs.size(); ++q) cfg.sh[q] = A.bits * (pairs[q].first + pairs[q].second);
+  // output rows in chunks whose FP32 pair products stay within about 2 GiB
+  const size_t per_row = (size_t)ksplit * N2 * pairs.size() * sizeof(float);
+  const size_t budget = (size_t)2 << 30;
+  int64_t mc = M;
+  if ((size_t)M * per_row > budget) mc = std::max<int64_t>(128, (int64_t)(budget / per_row) / 128 * 128);
+  const size_t need = per_row * (size_t)std::min(mc, M);
   if (w.part.bytes < need) {
     w.part.reset();
     w.part = DBuf(ex, need);
   }
-  std::vector<TcJobDesc> jobs(pairs.size());
-  for (size_t q = 0; q < pairs.size(); ++q) {
-    TcJobDesc &d = jobs[q];
-    d.A = &A.s[pairs[q].first - 1];
-    d.B = &B.s[pairs[q].second - 1];
-    d.M = M;
-    d.N = N;
-    d.nseg = 1;
-    d.out32 = (float *)w.part.p + q * per;
-    d.kb_split = kbs;
-    d.bn = N2 <= 32 ? 32 : N2 <= 64 ? 64 : N2 <= 128 ? 128 : 256;
-    cfg.sh[q] = A.bits * (pairs[q].first + pairs[q].second);
+  const int bn = N2 <= 32 ? 32 : N2 <= 64 ? 64 : N2 <= 128 ? 128 : 256;
+  std::vector<TcMat> av(A.ns);
+  for (int64_t m0 = 0; m0 < M; m0 += mc) {
+    const int64_t mm = std::min(mc, M - m0);
+    const size_t per = (size_t)ksplit * mm * N2;
+    for (int i = 0; i < A.ns; ++i) {  // views of rows m0 .. m0 + mm of every A slice
+      TcMat &t = av[i];
+      t.hi.ex = nullptr;
+      t.hi.p = (__nv_bfloat16 *)A.s[i].hi.p + m0 * 2 * A.kp;
+      t.hi.bytes = (size_t)mm * 2 * A.kp * sizeof(__nv_bfloat16);
+      t.planes = 1;
+      t.rows = mm;
+      t.kp = A.kp;
+      t.kreal = A.kreal;
+    }
+    std::vector<TcJobDesc> jobs(pairs.size());
+    for (size_t q = 0; q < pairs.size(); ++q) {
+      TcJobDesc &d = jobs[q];
+      d.A = &av[pairs[q].first - 1];
+      d.B = &B.s[pairs[q].second - 1];
+      d.M = mm;
+      d.N = N;
+      d.nseg = 1;
+      d.out32 = (float *)w.part.p + q * per;
+      d.kb_split = kbs;
+      d.bn = bn;
+    }
+    tc_gemm_grouped(ex, jobs, w.grp, err, false);
+    int pr = ex.prof_begin("sl_combine", 0.0);
+    k_sl_combine<<<grid1d(mm * N, 256), 256, 0, ex.stream>>>((const float *)w.part.p, cfg, mm, N2,
+                                                             (const int *)A.exps.p + m0, (const int *)B.exps.p,
+                                                             alpha, beta, out + m0 * s_m, s_m, s_nh, s_nl, n_in);
+    ADC_CHECK_LAUNCH();
+    ex.prof_end(pr);
+    for (auto &t : av) { t.hi.p = nullptr; t.hi.bytes = 0; }
   }
-  tc_gemm_grouped(ex, jobs, w.grp, err, false);
-  int pr = ex.prof_begin("sl_combine", 0.0);
-  k_sl_combine<<<grid1d(M * N, 256), 256, 0, ex.stream>>>((const float *)w.part.p, cfg, M, N2, (const int *)A.exps.p,
-                                                          (const int *)B.exps.p, alpha, beta, out, s_m, s_nh, s_nl,
-                                                          n_in);
-  ADC_CHECK_LAUNCH();
-  ex.prof_end(pr);
+  for (auto &t : av) { t.hi.p = nullptr; t.hi.bytes = 0; }
+}
+
+// zgemm's operands and output (element strides, conj flags, batch) through
+// the sliced product: used for large contractions when Exec::sliced_bits > 0
+void zgemm_sliced(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha, const cplx *A, int64_t sAb,
+                  int64_t sAm, int64_t sAk, bool conjA, const cplx *B, int64_t sBb, int64_t sBk, int64_t sBn,
+                  bool conjB, cplx beta, cplx *C, int64_t sCb, int64_t sCm, int64_t sCn) {
+  SlMat Sa, Sb;
+  SlWork w;
+  DBuf err(ex, sizeof(int));
+  fill_zero(ex, err.p, sizeof(int));
+  for (int64_t b = 0; b < batch; ++b) {
+    sl_pack_A(ex, Sa, A + b * sAb, M, K, sAm, sAk, conjA, ex.sliced_bits);
+    sl_pack_B(ex, Sb, B + b * sBb, N, K, sBn, 0, 1, sBk, conjB, Sa);
+    sl_gemm(ex, Sa, Sb, M, N, alpha, beta, C + b * sCb, sCm, sCn, 0, 1, (int *)err.p, w);
+  }
+  int h = 0;
+  ADC_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+  ADC_REQUIRE(h == 0, ADC_ERR_TIMEOUT, "sliced GEMM: a tensor-core wait gave up (code " + std::to_string(h) + ")");
 }
 
 }  // namespace adc

@@ -48,6 +48,10 @@ void sl_pack_B(Exec &ex, SlMat &dst, const cplx *src, int64_t Nc, int64_t K, int
                int64_t n_in, int64_t s_k, bool conj, const SlMat &like);
 // B operand of the ring term, gathered from the packed satellite block of X
 void sl_pack_B_ring(Exec &ex, SlMat &dst, const adc_ctx *c, const cplx *X, int64_t k, const SlMat &like);
+// zgemm's contract (tensor.cuh) computed as the sliced product with ex.sliced_bits bits
+void zgemm_sliced(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha, const cplx *A, int64_t sAb,
+                  int64_t sAm, int64_t sAk, bool conjA, const cplx *B, int64_t sBb, int64_t sBk, int64_t sBn,
+                  bool conjB, cplx beta, cplx *C, int64_t sCb, int64_t sCm, int64_t sCn);
 // out = alpha A B^T + beta out, addressing as tc_gemm
 void sl_gemm(Exec &ex, const SlMat &A, const SlMat &B, int64_t M, int64_t N, cplx alpha, cplx beta, cplx *out,
              int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, SlWork &w);

@@ -4,6 +4,7 @@
 #include <map>
 
 #include "tensor.cuh"
+#include "tc_slice.cuh"
 
 namespace adc {
 
@@ -239,6 +240,11 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
            int64_t sCn) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K < 0) K = 0;  // the kernel then writes beta * C
+  if (ex.sliced_bits > 0 && K > 0 && 8.0 * (double)M * N * K * batch >= (double)(1 << 24)) {
+    zgemm_sliced(ex, M, N, K, batch, alpha, A, sAb, sAm, sAk, conjA, B, sBb, sBk, sBn, conjB, beta, C, sCb, sCm,
+                 sCn);
+    return;
+  }
   zgemm_attr();
   const int64_t mt_ = (M + BM - 1) / BM, nt_ = (N + BN - 1) / BN;
   const int mfast = (nt_ <= 65535) ? 1 : 0;

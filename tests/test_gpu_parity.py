@@ -210,6 +210,31 @@ def test_mixed_davidson_sliced_refinement(gpu, kind, o, v, Q, x):
         assert np.linalg.norm(R, axis=1).max() < 1e-6
 
 
+@pytest.mark.parametrize("kind,o,v,Q,order,x,seed", [("EA", 8, 40, 80, 3, 0.5, 41), ("IP", 12, 30, 80, 3, 1.0, 42),
+                                                     ("EE", 6, 20, 40, 3, 0.4, 43), ("EA", 6, 36, 60, 2, 0.0, 44)])
+def test_sliced_setup(gpu, kind, o, v, Q, order, x, seed):
+    """adc_init with opts.setup = ADC_PREC_SLICED: the setup's contractions of at
+    least 2^24 flops run as the sliced product (about 48 bits); the operators
+    match the oracle to 1e-11 relative (FP64 setup: 1e-12)."""
+    p = make_problem(o, v, Q, seed=seed, sigma=0.08)
+    kw = dict(kind=kind, order=order, x=x)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, setup="sliced", **kw) as ctx:
+        X = random_vectors(ctx.N, 2, seed=seed + 1)
+        S = ctx.sigma(X, "fp64")
+        d = ctx.diagonal()
+    if kind == "EE":
+        from oracle import adc_ee
+        M = adc_ee.explicit_matrix(order, x, p.B, p.eps_occ, p.eps_vir)
+        ref = X @ M.T
+        dref = np.real(np.diag(M))
+    else:
+        amp = oadc.Amplitudes(p.B, p.eps_occ, p.eps_vir, second_order=(order == 3))
+        ref = oadc.sigma_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, X, amp=amp)
+        dref = oadc.diagonal_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, amp=amp)
+    assert _rel(S, ref).max() < 1e-11, _rel(S, ref).max()
+    assert np.abs(d - dref).max() < 1e-11 * max(1.0, np.abs(dref).max())
+
+
 def test_davidson_noconv_returns_best(gpu):
     p = make_problem(5, 12, 20, seed=3, sigma=0.08)
     with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP", order=3, x=1.0) as ctx:
