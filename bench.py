@@ -264,7 +264,7 @@ def run_ee(args, cfgname):
     p = config_problem(cfgname)
     o, v, Q = p.nocc, p.nvir, p.naux
     t0 = time.perf_counter()
-    ctx = adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=cfg["order"], x=x)
+    ctx = adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=cfg["order"], x=x, refine=args.refine)
     init_s = time.perf_counter() - t0
     log(f"init {init_s:.1f} s, N = {ctx.N}")
     ctx.sigma(random_vectors(ctx.N, 1, seed=3), args.mixed)  # builds the split-precision operators
@@ -290,7 +290,7 @@ def run_ee(args, cfgname):
                 "max_eig_diff_vs_mixed": float(np.abs(om64 - om).max()), "rc": int(rc6)}
     Xs = random_vectors(ctx.N, nroots, seed=7)
     sig = {}
-    for prec in (args.mixed, "fp64"):
+    for prec in (args.mixed, "sliced", "fp64"):
         ctx.sigma(Xs, prec)
         ctx.profile(True)
         t2 = time.perf_counter()
@@ -316,7 +316,7 @@ def run_ee(args, cfgname):
         ws = []
         for sgn in (1, -1):
             with adcgpu.Context(p.B + sgn * h * D[0], p.eps_occ + sgn * h * D[1], p.eps_vir + sgn * h * D[2],
-                                kind="EE", order=cfg["order"], x=x + sgn * h * D[3]) as c2:
+                                kind="EE", order=cfg["order"], x=x + sgn * h * D[3], refine=args.refine) as c2:
                 w, _, _, _, rcf = c2.davidson(nroots, tol=min(tol, 1e-8), max_iter=400, precision=args.mixed,
                                               want_vectors=False)
                 ws.append(w)
@@ -330,8 +330,8 @@ def run_ee(args, cfgname):
     def roof(name, e):
         avg = e["total_ms"] / e["launches"]
         alg = e["flops"] / e["launches"]
-        if name.startswith("tc_gemm"):
-            mma = (6.0 if "bf16x6" in name else 3.0) * alg
+        if name.startswith("tc_"):
+            mma = (1.0 if name.startswith("tc_sliced") else 6.0 if "bf16x6" in name else 3.0) * alg
             peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
             ach = mma / (avg * 1e-3) / 1e12
             return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
@@ -346,7 +346,9 @@ def run_ee(args, cfgname):
     line = {
         "metric": METRIC, "value": solve_s / nroots, "unit": "s/root", "n_gpus": 1, "steps": 1,
         "warmup": 0, "ms_per_step": 1e3 * solve_s, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": f"{args.mixed}+" + ("f64 from exact bf16 digit products" if args.refine == "sliced" else "f64"),
+        "data": "synthetic",
         "config": {"workload": cfgname, "kind": "EE", "order": cfg["order"], "x": x, "nocc": o, "nvir": v,
                    "naux": Q, "nroots": nroots, "tol_fp64_residual": tol, "N": int(Y.shape[1]),
                    "l2": "operators larger than L2"},
@@ -356,7 +358,10 @@ def run_ee(args, cfgname):
                            "omega": [float(w) for w in om], "err64": [float(e) for e in e64]},
         "fp64_davidson": fp64,
         "sigma": {"vectors": nroots, "mixed": args.mixed, "mixed_ms": sig[args.mixed]["ms"],
-                  "fp64_ms": sig["fp64"]["ms"], "speedup": sig["fp64"]["ms"] / sig[args.mixed]["ms"]},
+                  "sliced_ms": sig["sliced"]["ms"], "fp64_ms": sig["fp64"]["ms"],
+                  "speedup": sig["fp64"]["ms"] / sig[args.mixed]["ms"],
+                  "speedup_sliced": sig["fp64"]["ms"] / sig["sliced"]["ms"]},
+        "refine": args.refine,
         "gradient": grad,
         "init_s": init_s, "e2e": None, "cpu_baseline": None,
     }
@@ -411,7 +416,7 @@ def main():
     ap.add_argument("--mixed", default="bf16x3", choices=["bf16x3", "bf16x6"],
                     help="split precision of the mixed Davidson")
     ap.add_argument("--refine", default="sliced", choices=["sliced", "fp64"],
-                    help="IP/EA: product of the Davidson refinement (FP64-accurate)")
+                    help="product of the Davidson refinement (both FP64-accurate)")
     ap.add_argument("--e2e-setup", default="sliced", choices=["sliced", "fp64"],
                     help="IP/EA/EE: adc_init contractions of the end-to-end run")
     ap.add_argument("--no-e2e", action="store_true")

@@ -63,7 +63,7 @@ enum { ADC_IP = 0, ADC_EA = 1, ADC_EE = 2 };
  *   tensor-core work of BF16X3. The tensor cores' FP32 accumulation, not the
  *   split, limits both (1e-6 to 1e-5 relative measured), so BF16X6 is rarely
  *   more accurate. Batches (adc_batch_*) use BF16X3.
- * ADC_PREC_SLICED: FP64-accurate products on the tensor cores (IP and EA).
+ * ADC_PREC_SLICED: FP64-accurate products on the tensor cores.
  *   Each operand row is scaled by a power of two and written as a sum of
  *   integer BF16 digits of 4 to 7 bits; every digit product is summed exactly
  *   in the FP32 accumulator (the inner size is split so that the sums stay
@@ -98,7 +98,7 @@ typedef struct {
                            ADC(2) level, zeroth order) */
   int refine;           /* products of adc_davidson's refinement (the FP64 base
                            of the Ritz vectors and the final residual check):
-                           ADC_PREC_FP64 (default) or ADC_PREC_SLICED (IP/EA) */
+                           ADC_PREC_FP64 (default) or ADC_PREC_SLICED */
   int setup;            /* dense contractions of adc_init: ADC_PREC_FP64
                            (default) or ADC_PREC_SLICED (those of at least 2^24
                            flops as the sliced product with about 48

@@ -317,9 +317,8 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   mmax = std::max(mmax, std::min<int>((int)N, nroots + 1));
   const int krmax = std::min(mmax, std::max(2 * nroots, kb));
   Davidson d(c, nroots, mmax, krmax);
-  // refinement products: FP64, or the sliced FP64-accurate tensor-core product (IP/EA)
-  if (precision != ADC_PREC_FP64 && c->opts.refine == ADC_PREC_SLICED && c->kind != ADC_EE)
-    d.prec64 = ADC_PREC_SLICED;
+  // refinement products: FP64, or the sliced FP64-accurate tensor-core product
+  if (precision != ADC_PREC_FP64 && c->opts.refine == ADC_PREC_SLICED) d.prec64 = ADC_PREC_SLICED;
   Exec &ex = c->ex;
 
   // ---- starting space

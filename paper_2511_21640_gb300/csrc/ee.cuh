@@ -4,10 +4,13 @@
 #include <map>
 
 #include "ctx.cuh"
-#include "tc_gemm.cuh"
+#include "tc_slice.cuh"
 #include "terms.cuh"
 
 namespace adc {
+// operators of the structured EE sigma that run as tensor-core products
+enum { EE_VAT = 0, EE_VAC, EE_VB, EE_VBC, EE_GVV, EE_GOO, EE_W, EE_NOPS };
+
 struct EEOps {
   std::vector<Term> K1, S2, Y2, S3, Y3, SD1, O2, Z1, DD1;
   std::vector<Term> T2N, S2N;  // numerators of the second-order doubles and singles (adjoint only)
@@ -26,6 +29,11 @@ struct EEOps {
   DBuf tcerr;
   bool tc_ready = false;
   int tc_planes = 0;
+  // sliced copies (FP64-accurate products), indexed by EE_VAT .. EE_W, and the per-call B operand
+  SlMat sop[EE_NOPS];
+  SlMat sbx;
+  SlWork slw;
+  bool sl_ready = false, sl_dd = false;
 };
 // numerators of the second-order doubles and singles (second_order_amplitudes in
 // setup.cu) as term tables: t2_ij^ab D_ij^ab and t2_i^a (eps_i - eps_a)

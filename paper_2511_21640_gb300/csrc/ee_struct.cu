@@ -436,8 +436,33 @@ static void ee_tc_build(adc_ctx *c, bool dd, int planes) {
   E.tc_ready = true;
 }
 
-// ee_struct_apply with the GEMMs over the doubles on the tensor cores (BF16x3);
-// the separable second-order pieces (o x o and v x v intermediates) stay FP64
+// sliced copies of the same operators (FP64-accurate tensor-core products)
+static void ee_sl_build(adc_ctx *c, bool dd) {
+  Exec &ex = c->ex;
+  EEOps &E = *c->ee;
+  const int64_t o = c->o, v = c->v, po = npairs(o), pv = npairs(v), ov = o * v;
+  constexpr int bits = 40;
+  sl_pack_A(ex, E.sop[EE_VAT], E.Va.c(), v, o * pv, 1, v, false, bits);
+  sl_pack_A(ex, E.sop[EE_VAC], E.Va.c(), o * pv, v, v, 1, true, bits);
+  sl_pack_A(ex, E.sop[EE_VB], E.Vb.c(), o, po * v, po * v, 1, false, bits);
+  sl_pack_A(ex, E.sop[EE_VBC], E.Vb.c(), po * v, o, 1, po * v, true, bits);
+  if (dd) {
+    sl_pack_A(ex, E.sop[EE_GVV], E.Gvv.c(), pv, pv, pv, 1, false, bits);
+    sl_pack_A(ex, E.sop[EE_GOO], E.Goo.c(), po, po, po, 1, false, bits);
+    sl_pack_A(ex, E.sop[EE_W], c->W.c(), ov, ov, ov, 1, false, bits);
+  }
+  if (!E.tcerr.p) {
+    E.tcerr = DBuf(ex, sizeof(int));
+    fill_zero(ex, E.tcerr.p, sizeof(int));
+  }
+  E.sl_dd = dd;
+  E.sl_ready = true;
+}
+
+// ee_struct_apply with the GEMMs over the doubles on the tensor cores, as the
+// BF16x3/BF16x6 split (nseg 3 or 6) or as the sliced FP64-accurate product
+// (nseg 0); the separable second-order pieces (o x o and v x v intermediates)
+// stay FP64
 static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, double sdd, int nseg) {
   Exec &ex = c->ex;
   EEOps &E = *c->ee;
@@ -448,15 +473,29 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
   const bool second = (c->order == 3 && c->x != 0.0);
   const double x = second ? c->x : 0.0;
   int *err = (int *)E.tcerr.p;
+  const bool sliced = (nseg == 0);
   const int planes = (nseg == 6) ? 3 : 2;
+  const TcMat *tops[EE_NOPS] = {&E.tVaT, &E.tVaC, &E.tVb, &E.tVbC, &E.tGvv, &E.tGoo, &E.tW};
+  // out = alpha op B^T + beta out, B[n][k] = src[(n / b_in) b_nh + (n % b_in) b_nl + k b_k]
+  auto mul = [&](int op, const cplx *src, int64_t Nc, int64_t K, int64_t b_nh, int64_t b_nl, int64_t b_in,
+                 int64_t b_k, int64_t M, cplx alpha, cplx beta, cplx *out, int64_t s_m, int64_t s_nh, int64_t s_nl,
+                 int64_t n_in) {
+    if (sliced) {
+      const SlMat &A = E.sop[op];
+      sl_pack_B(ex, E.sbx, src, Nc, K, b_nh, b_nl, b_in, b_k, false, A);
+      sl_gemm(ex, A, E.sbx, M, Nc, alpha, beta, out, s_m, s_nh, s_nl, n_in, err, E.slw);
+    } else {
+      tc_pack_B(ex, E.bx, src, Nc, K, b_nh, b_nl, b_in, b_k, false, planes);
+      tc_gemm(ex, *tops[op], E.bx, M, Nc, alpha, beta, out, s_m, s_nh, s_nl, n_in, err, nseg);
+    }
+  };
   TagScope tg(ex, "ee_coupling");
   {
     DBuf Xa = cbuf(ex, kc * o * o * pv);
     k_gather_xa<<<grid1d(kc * o * o * pv, 256), 256, 0, ex.stream>>>(X + n1, N, kc, pav, pbv, o, v, pv, Xa.c());
     ADC_CHECK_LAUNCH();
     // S1[z][i][a] += sum_(l,cd) Va[(l,cd)][a] Xa[z][i][(l,cd)]
-    tc_pack_B(ex, E.bx, Xa.c(), kc * o, o * pv, o * pv, 0, 1, 1, false, planes);
-    tc_gemm(ex, E.tVaT, E.bx, v, kc * o, C1(), C1(), S, 1, N, v, o, err, nseg);
+    mul(EE_VAT, Xa.c(), kc * o, o * pv, o * pv, 0, 1, 1, v, C1(), C1(), S, 1, N, v, o);
     DBuf U;
     if (second) {
       DBuf Y1 = cbuf(ex, kc * o * o);
@@ -467,8 +506,7 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
       zgemm(ex, kc, o * o, n1, 1, C1(), X, 0, N, 1, false, E.V1.c(), 0, o * o, 1, true, C0(), U.c(), 0, o * o, 1);
     }
     // F[z][i][(l,cd)] = sum_a conj(Va[(l,cd)][a]) X1[z][i][a]
-    tc_pack_B(ex, E.bx, X, kc * o, v, N, v, o, 1, false, planes);
-    tc_gemm(ex, E.tVaC, E.bx, o * pv, kc * o, C1(), C0(), Xa.c(), 1, o * o * pv, o * pv, o, err, nseg);
+    mul(EE_VAC, X, kc * o, v, N, v, o, 1, o * pv, C1(), C0(), Xa.c(), 1, o * o * pv, o * pv, o);
     if (second)
       zgemm(ex, o, o * pv, o, kc, CR(x), U.c(), o * o, o, 1, false, E.T1p.c(), 0, 1, o, true, C1(), Xa.c(),
             o * o * pv, o * pv, 1);
@@ -481,8 +519,7 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
                                                                      Xb.c());
     ADC_CHECK_LAUNCH();
     // S1[z][i][a] += sum_((kl),d) Vb[i][((kl),d)] XbT[z][a][((kl),d)]
-    tc_pack_B(ex, E.bx, Xb.c(), kc * v, po * v, po * v, 0, 1, 1, false, planes);
-    tc_gemm(ex, E.tVb, E.bx, o, kc * v, C1(), C1(), S, v, N, 1, v, err, nseg);
+    mul(EE_VB, Xb.c(), kc * v, po * v, po * v, 0, 1, 1, o, C1(), C1(), S, v, N, 1, v);
     DBuf U2;
     if (second) {
       DBuf Y2 = cbuf(ex, kc * v * v);
@@ -493,8 +530,7 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
       zgemm(ex, kc, v * v, n1, 1, C1(), X, 0, N, 1, false, E.V2.c(), 0, v * v, 1, true, C0(), U2.c(), 0, v * v, 1);
     }
     // G[z][((kl),d)][a] = sum_i conj(Vb[i][((kl),d)]) X1[z][i][a]  (reusing the buffer)
-    tc_pack_B(ex, E.bx, X, kc * v, o, N, 1, v, v, false, planes);
-    tc_gemm(ex, E.tVbC, E.bx, po * v, kc * v, C1(), C0(), Xb.c(), v, po * v * v, 1, v, err, nseg);
+    mul(EE_VBC, X, kc * v, o, N, 1, v, v, po * v, C1(), C0(), Xb.c(), v, po * v * v, 1, v);
     if (second)
       zgemm(ex, po * v, v, v, kc, CR(x), E.T2p.c(), 0, v, 1, true, U2.c(), v * v, 1, v, false, C1(), Xb.c(),
             po * v * v, v, 1);
@@ -503,18 +539,15 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
   }
   if (sdd == 0.0) return;
   ex.tag = "ee_ladder";
-  tc_pack_B(ex, E.bx, X + n1, kc * po, pv, N, pv, po, 1, false, planes);
-  tc_gemm(ex, E.tGvv, E.bx, pv, kc * po, CR(sdd), C1(), S + n1, 1, N, pv, po, err, nseg);
-  tc_pack_B(ex, E.bx, X + n1, kc * pv, po, N, 1, pv, pv, false, planes);
-  tc_gemm(ex, E.tGoo, E.bx, po, kc * pv, CR(sdd), C1(), S + n1, pv, N, 1, pv, err, nseg);
+  mul(EE_GVV, X + n1, kc * po, pv, N, pv, po, 1, pv, CR(sdd), C1(), S + n1, 1, N, pv, po);
+  mul(EE_GOO, X + n1, kc * pv, po, N, 1, pv, pv, po, CR(sdd), C1(), S + n1, pv, N, 1, pv);
   ex.tag = "ee_ring";
   const int64_t ncol = kc * ov;
   DBuf Xt = cbuf(ex, ncol * ov), R = cbuf(ex, ov * ncol);
   k_gather_xtt<<<grid1d(ncol * ov, 256), 256, 0, ex.stream>>>(X + n1, N, kc, o, v, pv, Xt.c());
   ADC_CHECK_LAUNCH();
-  tc_pack_B(ex, E.bx, Xt.c(), ncol, ov, ov, 0, 1, 1, false, planes);
+  mul(EE_W, Xt.c(), ncol, ov, ov, 0, 1, 1, ov, C1(), C0(), R.c(), ncol, 1, 0, 1);
   Xt.reset();
-  tc_gemm(ex, E.tW, E.bx, ov, ncol, C1(), C0(), R.c(), ncol, 1, 0, 1, err, nseg);
   k_scatter_ring<<<grid1d(kc * po * pv, 256), 256, 0, ex.stream>>>(R.c(), kc, pio, pjo, pav, pbv, o, v, po, pv, sdd,
                                                                    S + n1, N);
   ADC_CHECK_LAUNCH();
@@ -529,7 +562,11 @@ void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
   const double sdd = (third && c->dd_order == 1) ? c->x : 0.0;
   const int planes = (nseg == 6) ? 3 : 2;
   ee_struct_build(c, sdd != 0.0);
-  if (!E.tc_ready || E.tc_planes < planes) ee_tc_build(c, sdd != 0.0, planes);
+  if (nseg == 0) {
+    if (!E.sl_ready) ee_sl_build(c, sdd != 0.0);
+  } else if (!E.tc_ready || E.tc_planes < planes) {
+    ee_tc_build(c, sdd != 0.0, planes);
+  }
   TagScope tg(ex, "ee");
   zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, E.MSS.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
   ADC_CUDA(cudaMemset2DAsync(S + n1, N * sizeof(cplx), 0, n2 * sizeof(cplx), k, ex.stream));

@@ -97,7 +97,8 @@ void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision) {
     throw Error(ADC_ERR_ARG, "unknown precision");
   const int nseg = (precision == ADC_PREC_BF16X6) ? 6 : 3;
   if (precision == ADC_PREC_SLICED) {
-    sigma_sliced(c, X, S, k);
+    if (c->kind == ADC_EE) sigma_ee_split(c, X, S, k, 0);  // nseg 0: sliced products
+    else sigma_sliced(c, X, S, k);
   } else if (c->kind == ADC_EE) {
     if (precision == ADC_PREC_FP64) sigma_ee_fp64(c, X, S, k);
     else sigma_ee_split(c, X, S, k, nseg);

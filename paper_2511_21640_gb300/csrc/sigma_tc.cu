@@ -114,7 +114,7 @@ static void build_sl(adc_ctx *c) {
 }
 
 void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
-  ADC_REQUIRE(c->kind != ADC_EE, ADC_ERR_UNSUPPORTED, "sliced sigma: IP and EA only");
+  ADC_REQUIRE(c->kind != ADC_EE, ADC_ERR_ARG, "sigma_sliced: IP and EA (EE goes through sigma_ee_split)");
   Exec &ex = c->ex;
   if (!c->sl || !c->sl->ready) build_sl(c);
   SlCache &sl = *c->sl;

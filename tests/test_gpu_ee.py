@@ -53,6 +53,8 @@ def test_ee_sigma_diag_block(gpu, o, v, Q, order, x, dd, seed):
         assert _rel(Sm, ref).max() < 1e-4
         Sm6 = ctx.sigma(X, "bf16x6")
         assert _rel(Sm6, ref).max() < 1e-4, _rel(Sm6, ref).max()
+        Ss = ctx.sigma(X, "sliced")
+        assert _rel(Ss, ref).max() < 1e-10, _rel(Ss, ref).max()
 
 
 def test_ee_davidson_matches_dense(gpu):
@@ -67,13 +69,13 @@ def test_ee_davidson_matches_dense(gpu):
     assert np.linalg.norm(Y @ M.T - om[:, None] * Y, axis=1).max() < 1e-7
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
-def test_ee_mixed_davidson_refined(gpu, prec):
+@pytest.mark.parametrize("prec,refine", [("bf16x3", "fp64"), ("bf16x6", "fp64"), ("bf16x3", "sliced")])
+def test_ee_mixed_davidson_refined(gpu, prec, refine):
     o, v, Q = 4, 10, 16
     p = make_problem(o, v, Q, seed=9, sigma=0.08, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
     M = adc_ee.explicit_matrix(3, 0.4, p.B, p.eps_occ, p.eps_vir)
     w = np.linalg.eigvalsh(M)[:4]
-    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=3, x=0.4) as ctx:
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=3, x=0.4, refine=refine) as ctx:
         om, _, e64, st, rc = ctx.davidson(4, tol=1e-8, precision=prec, want_vectors=False)
     assert rc == 0 and np.all(e64 <= 1e-8)
     assert np.abs(om - w).max() < 1e-8
