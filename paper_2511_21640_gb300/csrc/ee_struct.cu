@@ -462,7 +462,7 @@ static void ee_sl_build(adc_ctx *c, bool dd) {
 // ee_struct_apply with the GEMMs over the doubles on the tensor cores, as the
 // BF16x3/BF16x6 split (nseg 3 or 6) or as the sliced FP64-accurate product
 // (nseg 0); the separable second-order pieces (o x o and v x v intermediates)
-// stay FP64
+// go through zgemm, which the caller switches to the sliced product
 static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, double sdd, int nseg) {
   Exec &ex = c->ex;
   EEOps &E = *c->ee;
@@ -575,10 +575,20 @@ void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
   if (sdd != 0.0) per = std::max<int64_t>(per, 3 * o * v * o * v);
   per *= (int64_t)sizeof(cplx);
   const int64_t kc = std::max<int64_t>(1, std::min<int64_t>(k, (4ll << 30) / std::max<int64_t>(per, 1)));
-  for (int64_t z0 = 0; z0 < k; z0 += kc) {
-    const int64_t kk = std::min(kc, k - z0);
-    ee_struct_apply_tc(c, X + z0 * N, S + z0 * N, kk, sdd, nseg);
+  // the separable second-order pieces (zgemm over the long (l, c<d) and
+  // ((k<l), d) indices) as sliced tensor-core products too
+  const int old_bits = ex.sliced_bits;
+  ex.sliced_bits = 40;
+  try {
+    for (int64_t z0 = 0; z0 < k; z0 += kc) {
+      const int64_t kk = std::min(kc, k - z0);
+      ee_struct_apply_tc(c, X + z0 * N, S + z0 * N, kk, sdd, nseg);
+    }
+  } catch (...) {
+    ex.sliced_bits = old_bits;
+    throw;
   }
+  ex.sliced_bits = old_bits;
   int h = 0;
   ADC_CUDA(cudaMemcpyAsync(&h, E.tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));
   ADC_CUDA(cudaStreamSynchronize(ex.stream));

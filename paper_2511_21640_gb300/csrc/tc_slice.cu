@@ -129,10 +129,15 @@ __global__ void k_sl_slice_B(BSrc src, int64_t Nc, int64_t K, int conj, int64_t 
 
 struct SlCombine {
   int npair, ksplit;
-  int sh[SL_MAXPAIRS];  // b (i + j) of each pair, pairs in ascending order
+  int sh[SL_MAXPAIRS];     // b (i + j) of each pair; pairs ordered by i + j
+  double sc[SL_MAXPAIRS];  // 2^-sh (exact)
 };
 
-// out[m][n] = alpha 2^(E_m + F_n) sum_p sum_s 2^-sh_p P[p][s][m][2n..2n+1] + beta out
+// out[m][n] = alpha 2^(E_m + F_n) sum_p sum_s 2^-sh_p P[p][s][m][2n..2n+1] + beta out.
+// Every P is an integer below 2^24 held exactly in FP32; the pairs of one
+// shift (same i + j) and their K splits are summed exactly as 64-bit integers,
+// and only one FP64 conversion and product per shift remains (the FP64 pipe is
+// the scarce one).
 __global__ void k_sl_combine(const float *__restrict__ P, SlCombine cfg, int64_t M, int64_t N2,
                              const int *__restrict__ E, const int *__restrict__ F, cplx alpha, cplx beta, cplx *out,
                              int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in) {
@@ -141,16 +146,21 @@ __global__ void k_sl_combine(const float *__restrict__ P, SlCombine cfg, int64_t
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = idx % Nc, m = idx / Nc;
+    const float *base = P + m * N2 + 2 * n;
     double re = 0.0, im = 0.0;
+    long long ar = 0, ai = 0;
     for (int p = cfg.npair - 1; p >= 0; --p) {  // smallest terms first
-      double pr = 0.0, pi = 0.0;
       for (int s = 0; s < cfg.ksplit; ++s) {
-        const float2 v = *(const float2 *)(P + ((int64_t)p * cfg.ksplit + s) * per + m * N2 + 2 * n);
-        pr += (double)v.x;
-        pi += (double)v.y;
+        const float2 v = *(const float2 *)(base + ((int64_t)p * cfg.ksplit + s) * per);
+        ar += __float2int_rn(v.x);
+        ai += __float2int_rn(v.y);
       }
-      re += ldexp(pr, -cfg.sh[p]);
-      im += ldexp(pi, -cfg.sh[p]);
+      if (p == 0 || cfg.sh[p - 1] != cfg.sh[p]) {  // last pair of this shift
+        re = fma((double)ar, cfg.sc[p], re);
+        im = fma((double)ai, cfg.sc[p], im);
+        ar = 0;
+        ai = 0;
+      }
     }
     const int e = E[m] + F[n];
     const cplx val0 = cmake(ldexp(re, e), ldexp(im, e));
@@ -278,7 +288,10 @@ void sl_gemm(Exec &ex, const SlMat &A, const SlMat &B, int64_t M, int64_t N, cpl
   ADC_REQUIRE((int)pairs.size() <= SL_MAXPAIRS, ADC_ERR_UNSUPPORTED, "sl_gemm: too many slice pairs");
   cfg.npair = (int)pairs.size();
   cfg.ksplit = ksplit;
-  for (size_t q = 0; q < pairs.size(); ++q) cfg.sh[q] = A.bits * (pairs[q].first + pairs[q].second);
+  for (size_t q = 0; q < pairs.size(); ++q) {
+    cfg.sh[q] = A.bits * (pairs[q].first + pairs[q].second);
+    cfg.sc[q] = std::ldexp(1.0, -cfg.sh[q]);
+  }
   // output rows in chunks whose FP32 pair products stay within about 2 GiB
   const size_t per_row = (size_t)ksplit * N2 * pairs.size() * sizeof(float);
   const size_t budget = (size_t)2 << 30;
