@@ -101,7 +101,7 @@ typedef struct {
                            ADC_PREC_FP64 (default) or ADC_PREC_SLICED */
   int setup;            /* dense contractions of adc_init: ADC_PREC_FP64
                            (default) or ADC_PREC_SLICED (those of at least 2^24
-                           flops as the sliced product with about 48
+                           flops and inner size 512 as the sliced product with about 48
                            significant bits; the operators then differ from
                            the FP64 ones by about 1e-13 relative) */
 } adc_opts;

@@ -240,7 +240,9 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
            int64_t sCn) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K < 0) K = 0;  // the kernel then writes beta * C
-  if (ex.sliced_bits > 0 && K > 0 && 8.0 * (double)M * N * K * batch >= (double)(1 << 24)) {
+  // (short inner sizes stay here: there the product is bound by memory, and the
+  // sliced form reads and writes several times more)
+  if (ex.sliced_bits > 0 && K >= 512 && 8.0 * (double)M * N * K * batch >= (double)(1 << 24)) {
     zgemm_sliced(ex, M, N, K, batch, alpha, A, sAb, sAm, sAk, conjA, B, sBb, sBk, sBn, conjB, beta, C, sCb, sCm,
                  sCn);
     return;

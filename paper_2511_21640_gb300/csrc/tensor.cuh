@@ -17,8 +17,9 @@ struct ProfRec {
 
 struct Exec {
   cudaStream_t stream = nullptr;
-  // > 0: zgemm runs large products (at least 2^24 flops) as the sliced
-  // tensor-core product with about this many significant bits (tc_slice.cu)
+  // > 0: zgemm runs large products (at least 2^24 flops, inner size at least
+  // 512) as the sliced tensor-core product with about this many significant
+  // bits (tc_slice.cu)
   int sliced_bits = 0;
   int64_t mem_limit = 0;  // 0 = unlimited
   int64_t mem_used = 0;
