@@ -575,10 +575,11 @@ void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
   if (sdd != 0.0) per = std::max<int64_t>(per, 3 * o * v * o * v);
   per *= (int64_t)sizeof(cplx);
   const int64_t kc = std::max<int64_t>(1, std::min<int64_t>(k, (4ll << 30) / std::max<int64_t>(per, 1)));
-  // the separable second-order pieces (zgemm over the long (l, c<d) and
-  // ((k<l), d) indices) as sliced tensor-core products too
+  // with the sliced products, the separable second-order pieces (zgemm over
+  // the long (l, c<d) and ((k<l), d) indices) run as sliced products too; next
+  // to the BF16 split they stay FP64 (measured: faster there)
   const int old_bits = ex.sliced_bits;
-  ex.sliced_bits = 40;
+  if (nseg == 0) ex.sliced_bits = 40;
   try {
     for (int64_t z0 = 0; z0 < k; z0 += kc) {
       const int64_t kk = std::min(kc, k - z0);
