@@ -21,6 +21,9 @@ Modules
 ``gradients``   Hellmann-Feynman derivatives of the roots (Eq. 10) along a
                 direction of (B, eps, x), from central differences of the
                 explicit matrix.
+``ssfns``       state-specific natural spinors for EA and EE (Eqs. 31-32):
+                state density of the zeroth-order intermediate states, guess
+                transformation, root-specific solves, corrected energies.
 
 Every function is written for clarity, in FP64 complex, with no blocking or
 fusion beyond what the cited definition states.
