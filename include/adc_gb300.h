@@ -217,6 +217,66 @@ int adc_fns_density(adc_ctx *ctx, adc_c128 *D, double *eta, adc_c128 *V,
 int adc_fns_transform(adc_ctx *ctx, const adc_c128 *U, int64_t ldu,
                       int64_t n_keep, adc_c128 *Bout);
 
+/* ------------------------------------------------------------------------
+ * State-specific frozen natural spinors (Sec. 2.3, Eqs. 31-32), EA and EE.
+ * ---------------------------------------------------------------------- */
+
+/* Virtual density of one state, D_ab = <Psi| a+_b a_a |Psi>, with |Psi> the
+ * excited configurations weighted by y (the zeroth-order intermediate states
+ * of Eq. 31): EA D_ab = y_a conj(y_b) + sum_jc Y_jac conj(Y_jbc), EE D_ab =
+ * sum_i y_ia conj(y_ib) + 1/2 sum_ijc Y_ijac conj(Y_ijbc), Y the doubles as
+ * full antisymmetric arrays. y [N] (packed layout of adc_dims), D [nvir][nvir];
+ * host or device. EA and EE contexts (else ADC_ERR_UNSUPPORTED). Synchronous. */
+int adc_state_density(adc_ctx *ctx, const adc_c128 *y, adc_c128 *D);
+
+/* adc_fns_density with the state density of y added to the MP2 density
+ * before Eq. 26 (Eq. 31): the state-specific natural spinors of that state.
+ * Arguments as adc_fns_density; y [N] host or device. */
+int adc_ssfns_density(adc_ctx *ctx, const adc_c128 *y, double eta_crit, adc_c128 *D, double *eta,
+                      int64_t *n_keep, adc_c128 *U, double *eps_new);
+
+/* A vector of this context carried into the truncated basis of U ([nvir][ldu],
+ * its first n_keep columns): y'_a' = sum_a conj(U_aa') y_a on every virtual
+ * index, written packed for nocc occupied and n_keep virtual spinors into
+ * g (EA: n_keep + nocc n_keep (n_keep - 1)/2 entries; EE: nocc n_keep +
+ * nocc (nocc - 1)/2 n_keep (n_keep - 1)/2). Host or device. Synchronous. */
+int adc_fns_vector(adc_ctx *ctx, const adc_c128 *y, const adc_c128 *U, int64_t ldu, int64_t n_keep,
+                   adc_c128 *g);
+
+/* Root-specific Davidson: the eigenpair whose vector overlaps `guess` [N]
+ * most, followed through the iterations (at every Rayleigh-Ritz step the Ritz
+ * vector with the largest |<guess|y>| is the one refined). Precision and
+ * refinement as adc_davidson; Y [N] or NULL. ADC_ERR_NOCONV with the best
+ * result when max_iter is reached. */
+int adc_davidson_follow(adc_ctx *ctx, const adc_c128 *guess, double tol, int max_iter, int precision,
+                        double *omega, adc_c128 *Y, double *err64, adc_stats *st);
+
+/* One root of adc_ssfns. */
+typedef struct {
+  double omega_corrected;  /* Eq. 32: omega_fns + omega2_canonical - omega2_fns */
+  double omega_fns;        /* ADC(order) root in the state-specific basis (root-specific solve) */
+  double omega2_canonical; /* ADC(2) root k in the canonical basis */
+  double omega2_fns;       /* ADC(2) root in the state-specific basis (root-specific solve) */
+  double err64;            /* residual norm of the ADC(order) solve */
+  int64_t n_keep;          /* natural spinors kept */
+  int status;              /* ADC_OK, ADC_ERR_NOCONV (a solve did not converge) or ADC_ERR_ARG
+                              (too few natural spinors kept: EA needs 2, EE 1) */
+  int pad_;
+} adc_ssfns_root;
+
+/* The state-specific natural-spinor procedure for the nroots lowest roots of
+ * EA- or EE-ADC: canonical ADC(2) roots and vectors; per root the density of
+ * Eq. 31, natural spinors with occupation >= eta_crit and their
+ * semicanonical energies (Eqs. 26-30), the Cholesky vectors in that basis,
+ * root-specific ADC(2) and ADC(order) (x as in adc_init) solves from the
+ * carried-over canonical vector, and the corrected energy of Eq. 32. Inputs
+ * as adc_init (host or device); out [nroots] (host). Every solve uses
+ * `precision` and `tol`; opts (or NULL) applies to every context. Returns
+ * ADC_OK when every root has a result (see status), else an error code. */
+int adc_ssfns(const adc_c128 *B, int64_t naux, const double *eps_occ, int64_t nocc, const double *eps_vir,
+              int64_t nvir, int kind, int order, double x, int nroots, double eta_crit, double tol, int max_iter,
+              int precision, const adc_opts *opts, adc_ssfns_root *out);
+
 /* Backward pass of the roots (Hellmann-Feynman, Eq. 10): with Y the
  * normalised eigenvectors of nroots non-degenerate roots ([nroots][N], host
  * or device) and weights gomega[r] (host), writes the gradients of

@@ -8,7 +8,7 @@ importing this package fails when the compiled library is missing.
 The C ABI is declared in ``include/adc_gb300.h``; the names here mirror it:
 ``Context(...)`` wraps ``adc_init``/``adc_free``, ``Context.sigma`` wraps
 ``adc_sigma``, ``Context.davidson`` wraps ``adc_davidson``,
-``Context.fns_density`` wraps ``adc_fns_density``.
+``Context.fns_density`` wraps ``adc_fns_density``; ``ssfns`` wraps ``adc_ssfns``.
 """
 from __future__ import annotations
 
@@ -55,6 +55,16 @@ class adc_stats(ctypes.Structure):
 class adc_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("flops", ctypes.c_double)]
+
+
+class adc_ssfns_root(ctypes.Structure):
+    _fields_ = [("omega_corrected", ctypes.c_double), ("omega_fns", ctypes.c_double),
+                ("omega2_canonical", ctypes.c_double), ("omega2_fns", ctypes.c_double),
+                ("err64", ctypes.c_double), ("n_keep", ctypes.c_int64), ("status", ctypes.c_int),
+                ("pad_", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
 class adc_batch_info(ctypes.Structure):
@@ -105,6 +115,11 @@ def _load():
         "adc_last_error": (ctypes.c_char_p, [P]),
         "adc_diag_gemm": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_sigma_adjoint": (I, [P, P, P, I64, P, P, P, ctypes.POINTER(D)]),
+        "adc_state_density": (I, [P, P, P]),
+        "adc_ssfns_density": (I, [P, P, D, P, P, ctypes.POINTER(I64), P, P]),
+        "adc_fns_vector": (I, [P, P, P, I64, I64, P]),
+        "adc_davidson_follow": (I, [P, P, D, I, I, ctypes.POINTER(D), P, ctypes.POINTER(D), P]),
+        "adc_ssfns": (I, [P, I64, P, I64, P, I64, I, I, D, I, D, D, I, I, P, P]),
         "adc_batch_create": (I, [ctypes.POINTER(P), P, I]),
         "adc_batch_sigma": (I, [P, P, P, P, I]),
         "adc_batch_davidson": (I, [P, I, D, I, I, P, P, P, P]),
@@ -315,6 +330,53 @@ class Context:
                                      ctypes.byref(gx)), self._h)
         return gB, geo, gev, gx.value
 
+    def state_density(self, y):
+        """Virtual density of the configurations weighted by y (``adc_state_density``, Eq. 31)."""
+        y = np.ascontiguousarray(y, dtype=np.complex128).reshape(-1)
+        D = np.empty((self.nvir, self.nvir), dtype=np.complex128)
+        _check(lib.adc_state_density(self._h, _ptr(y, np.complex128), _ptr(D, np.complex128)), self._h)
+        return D
+
+    def ssfns_density(self, y, eta_crit):
+        """State-specific natural spinors of the state y (``adc_ssfns_density``, Eqs. 31, 26-30)."""
+        y = np.ascontiguousarray(y, dtype=np.complex128).reshape(-1)
+        nvir = self.nvir
+        D = np.empty((nvir, nvir), dtype=np.complex128)
+        eta = np.empty(nvir, dtype=np.float64)
+        U = np.empty((nvir, nvir), dtype=np.complex128)
+        en = np.empty(nvir, dtype=np.float64)
+        nk = ctypes.c_int64()
+        _check(lib.adc_ssfns_density(self._h, _ptr(y, np.complex128), float(eta_crit), _ptr(D, np.complex128),
+                                     _ptr(eta, np.float64), ctypes.byref(nk), _ptr(U, np.complex128),
+                                     _ptr(en, np.float64)), self._h)
+        k = nk.value
+        return {"D": D, "eta": eta, "n_keep": k, "U": U[:, :k].copy(), "eps_new": en[:k].copy()}
+
+    def fns_vector(self, y, U):
+        """y carried into the truncated basis of U [nvir][n_keep] (``adc_fns_vector``)."""
+        y = np.ascontiguousarray(y, dtype=np.complex128).reshape(-1)
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        nk = U.shape[1]
+        o = self.nocc
+        n = nk + o * (nk * (nk - 1) // 2) if self.kind == "EA" else o * nk + (o * (o - 1) // 2) * (nk * (nk - 1) // 2)
+        g = np.empty(n, dtype=np.complex128)
+        _check(lib.adc_fns_vector(self._h, _ptr(y, np.complex128), _ptr(U, np.complex128), nk, nk,
+                                  _ptr(g, np.complex128)), self._h)
+        return g
+
+    def davidson_follow(self, guess, tol=1e-8, max_iter=300, precision="fp64", raise_on_noconv=True):
+        """Root-specific solve (``adc_davidson_follow``): (omega, y, err64, stats dict, rc)."""
+        g = np.ascontiguousarray(guess, dtype=np.complex128).reshape(-1)
+        y = np.empty(self.N, dtype=np.complex128)
+        om, err = ctypes.c_double(), ctypes.c_double()
+        st = adc_stats()
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        rc = lib.adc_davidson_follow(self._h, _ptr(g, np.complex128), float(tol), int(max_iter), p, ctypes.byref(om),
+                                     _ptr(y, np.complex128), ctypes.byref(err), ctypes.byref(st))
+        if rc != 0 and not (rc == -4 and not raise_on_noconv):
+            _check(rc, self._h)
+        return om.value, y, err.value, st.as_dict(), rc
+
     def fns_density(self, eta_crit):
         """MP2 virtual density and frozen natural spinors (``adc_fns_density``)."""
         nvir = self.nvir
@@ -458,6 +520,26 @@ def batch_solve(problems, nroots, tol=1e-6, max_iter=300, precision="bf16x3", me
     if rc not in (0, -4):
         _bcheck(rc)
     return omega, err, status, info.as_dict(), rc
+
+
+def ssfns(B, eps_occ, eps_vir, kind="EA", order=3, x=1.0, nroots=1, eta_crit=1e-5, tol=1e-8, max_iter=300,
+          precision="fp64", refine="fp64"):
+    """State-specific natural-spinor energies of the nroots lowest EA/EE roots (``adc_ssfns``,
+    Sec. 2.3, Eqs. 31-32): a list of dicts (omega_corrected, omega_fns, omega2_canonical, omega2_fns,
+    err64, n_keep, status)."""
+    B = np.ascontiguousarray(B, dtype=np.complex128)
+    eo = np.ascontiguousarray(eps_occ, dtype=np.float64)
+    ev = np.ascontiguousarray(eps_vir, dtype=np.float64)
+    o = adc_opts()
+    lib.adc_opts_default(ctypes.byref(o))
+    o.refine = PRECISIONS[refine] if isinstance(refine, str) else int(refine)
+    out = (adc_ssfns_root * int(nroots))()
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    rc = lib.adc_ssfns(B.ctypes.data, B.shape[0], eo.ctypes.data, eo.shape[0], ev.ctypes.data, ev.shape[0],
+                       KINDS[kind], int(order), float(x), int(nroots), float(eta_crit), float(tol), int(max_iter), p,
+                       ctypes.byref(o), out)
+    _check(rc)
+    return [r.as_dict() for r in out]
 
 
 def diag_gemm(which, M, N, K, seed=1, reps=3):

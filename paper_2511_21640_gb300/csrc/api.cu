@@ -10,11 +10,6 @@
 #include "ee.cuh"
 
 namespace adc {
-int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision, const cplx *guess,
-                 int64_t nguess, double *omega, cplx *Yout, double *err64, adc_stats *st_out);
-void fns_run(adc_ctx *c, cplx *D, double *eta, cplx *Vout, double eta_crit, int64_t *n_keep, cplx *U,
-             double *eps_new);
-void fns_transform(adc_ctx *c, const cplx *U, int64_t ldu, int64_t nk, cplx *Bout);
 void adjoint_ee(adc_ctx *c, const cplx *Y, const double *g_host, int64_t k, cplx *gB, double *geo, double *gev,
                 double *gx);
 void adjoint_ipea(adc_ctx *c, const cplx *Y, const double *g_host, int64_t k, cplx *gB, double *geo, double *gev,
@@ -319,6 +314,104 @@ int adc_fns_transform(adc_ctx *c, const adc_c128 *U, int64_t ldu, int64_t n_keep
   ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
   return ADC_OK;
   ADC_API_CATCH(c)
+}
+
+int adc_state_density(adc_ctx *c, const adc_c128 *y, adc_c128 *D) {
+  if (!c) return ADC_ERR_STATE;
+  if (!y || !D) return ADC_ERR_ARG;
+  if (c->kind != ADC_EA && c->kind != ADC_EE) return ADC_ERR_UNSUPPORTED;
+  ADC_API_TRY
+  const int64_t v = c->v;
+  DevIn yin(c->ex, y, (size_t)c->N * sizeof(cplx));
+  DevOut dD(c->ex, D, (size_t)v * v * sizeof(cplx));
+  state_density(c, (const cplx *)yin.p, (cplx *)dD.p);
+  dD.finish(c->ex);
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
+int adc_ssfns_density(adc_ctx *c, const adc_c128 *y, double eta_crit, adc_c128 *D, double *eta, int64_t *n_keep,
+                      adc_c128 *U, double *eps_new) {
+  if (!c) return ADC_ERR_STATE;
+  if (!y || !n_keep) return ADC_ERR_ARG;
+  if (c->kind != ADC_EA && c->kind != ADC_EE) return ADC_ERR_UNSUPPORTED;
+  ADC_API_TRY
+  const int64_t v = c->v;
+  DevIn yin(c->ex, y, (size_t)c->N * sizeof(cplx));
+  DBuf Dst = cbuf(c->ex, v * v);
+  state_density(c, (const cplx *)yin.p, Dst.c());
+  DevOut dD(c->ex, D, D ? v * v * sizeof(cplx) : 0);
+  DevOut dE(c->ex, eta, eta ? v * sizeof(double) : 0);
+  DevOut dU(c->ex, U, U ? v * v * sizeof(cplx) : 0);
+  DevOut dN(c->ex, eps_new, eps_new ? v * sizeof(double) : 0);
+  if (dU.p) fill_zero(c->ex, dU.p, dU.bytes);
+  if (dN.p) fill_zero(c->ex, dN.p, dN.bytes);
+  int64_t nk = 0;
+  fns_run(c, (cplx *)dD.p, (double *)dE.p, nullptr, eta_crit, &nk, (cplx *)dU.p, (double *)dN.p, Dst.c());
+  dD.finish(c->ex); dE.finish(c->ex); dU.finish(c->ex); dN.finish(c->ex);
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  *n_keep = nk;
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
+int adc_fns_vector(adc_ctx *c, const adc_c128 *y, const adc_c128 *U, int64_t ldu, int64_t n_keep, adc_c128 *g) {
+  if (!c) return ADC_ERR_STATE;
+  if (!y || !U || !g || n_keep < 1 || n_keep > c->v || ldu < n_keep) return ADC_ERR_ARG;
+  if (c->kind != ADC_EA && c->kind != ADC_EE) return ADC_ERR_UNSUPPORTED;
+  ADC_API_TRY
+  DevIn yin(c->ex, y, (size_t)c->N * sizeof(cplx));
+  DevIn uin(c->ex, U, (size_t)c->v * ldu * sizeof(cplx));
+  DevOut gout(c->ex, g, (size_t)fns_dim(c->kind, c->o, n_keep) * sizeof(cplx));
+  to_fns_basis(c, (const cplx *)yin.p, (const cplx *)uin.p, ldu, n_keep, (cplx *)gout.p);
+  gout.finish(c->ex);
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
+int adc_davidson_follow(adc_ctx *c, const adc_c128 *guess, double tol, int max_iter, int precision, double *omega,
+                        adc_c128 *Y, double *err64, adc_stats *st) {
+  if (!c) return ADC_ERR_STATE;
+  if (!guess || !omega || max_iter < 1) return ADC_ERR_ARG;
+  ADC_API_TRY
+  const int64_t N = c->N;
+  DevIn gin(c->ex, guess, (size_t)N * sizeof(cplx));
+  DevOut yout(c->ex, Y, Y ? (size_t)N * sizeof(cplx) : 0);
+  double e = 0.0;
+  int rc = davidson_run(c, 1, tol, max_iter, precision, (const cplx *)gin.p, 1, omega, (cplx *)yout.p, &e, st,
+                        true);
+  yout.finish(c->ex);
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  if (err64) *err64 = e;
+  if (rc == ADC_ERR_NOCONV) {
+    c->err = "davidson: not converged within max_iter";
+    g_last_error = c->err;
+  }
+  return rc;
+  ADC_API_CATCH(c)
+}
+
+int adc_ssfns(const adc_c128 *B, int64_t naux, const double *eps_occ, int64_t nocc, const double *eps_vir,
+              int64_t nvir, int kind, int order, double x, int nroots, double eta_crit, double tol, int max_iter,
+              int precision, const adc_opts *opts, adc_ssfns_root *out) {
+  if (!B || !eps_occ || !eps_vir || !out || nroots < 1 || max_iter < 1 || !(tol > 0.0)) return ADC_ERR_ARG;
+  if (kind != ADC_EA && kind != ADC_EE) return ADC_ERR_UNSUPPORTED;
+  if (order != 2 && order != 3) return ADC_ERR_ARG;
+  try {
+    return ssfns_run(B, naux, eps_occ, nocc, eps_vir, nvir, kind, order, x, nroots, eta_crit, tol, max_iter,
+                     precision, opts, out);
+  } catch (const adc::Error &e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc &e) {
+    g_last_error = e.what();
+    return ADC_ERR_OOM;
+  } catch (const std::exception &e) {
+    g_last_error = e.what();
+    return ADC_ERR_CUDA;
+  }
 }
 
 int adc_sigma_adjoint(adc_ctx *c, const adc_c128 *Y, const double *gomega, int64_t nroots, adc_c128 *gB,

@@ -30,8 +30,6 @@
 #include "../../include/adc_gb300.h"
 
 namespace adc {
-int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision, const cplx *guess,
-                 int64_t nguess, double *omega, cplx *Yout, double *err64, adc_stats *st_out);
 
 namespace {
 // dst rows (pitch ldd) += src rows (pitch lds), k rows of n elements

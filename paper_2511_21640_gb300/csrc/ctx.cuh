@@ -65,6 +65,25 @@ void first_order_amplitudes(adc_ctx *c);
 // Lad_ij^ab = 1/2 sum_cd <ab||cd> t_ij^cd (needs c->t1 and c->W)
 void second_order_amplitudes(adc_ctx *c, DBuf &G_vv, DBuf &Lad, DBuf &t2d, DBuf &t2s);
 void setup_ee(adc_ctx *c);
+// block Davidson for the lowest nroots roots (davidson.cu); with follow, one
+// root: the Ritz vector with the largest overlap with the (single) guess at
+// every iteration, instead of the lowest (root-specific solve)
+int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision, const cplx *guess,
+                 int64_t nguess, double *omega, cplx *Yout, double *err64, adc_stats *st_out, bool follow = false);
+// natural spinors (Eqs. 25-30): D^MP2 (+ Dadd, device v x v, Eq. 31), eta descending, V, U = V~ Z~
+// ([v][v], leading dimension v), eps~; all outputs device pointers or null
+void fns_run(adc_ctx *c, cplx *D, double *eta, cplx *Vout, double eta_crit, int64_t *n_keep, cplx *U,
+             double *eps_new, const cplx *Dadd = nullptr);
+// Cholesky vectors in the occupied + truncated-virtual basis (U [v][ldu], first nk columns)
+void fns_transform(adc_ctx *c, const cplx *U, int64_t ldu, int64_t nk, cplx *Bout);
+// state-specific natural spinors (ssfns.cu): state density (device y [N], D [v][v]),
+// a vector in the truncated basis (g packed for o, nk), its length, the whole procedure
+void state_density(adc_ctx *c, const cplx *y, cplx *D);
+void to_fns_basis(adc_ctx *c, const cplx *y, const cplx *U, int64_t ldu, int64_t nk, cplx *g);
+int64_t fns_dim(int kind, int64_t o, int64_t nk);
+int ssfns_run(const adc_c128 *B, int64_t naux, const double *eps_occ, int64_t nocc, const double *eps_vir,
+              int64_t nvir, int kind, int order, double x, int nroots, double eta_crit, double tol, int max_iter,
+              int precision, const adc_opts *opts, adc_ssfns_root *out);
 void sigma_ee_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg);
 void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);

@@ -47,6 +47,20 @@ __global__ void k_fill_lower(cplx *G, int ldg, int m0, int na) {
   G[(int64_t)(m0 + i) * ldg + j] = cmake(a.x, -a.y);
 }
 
+// swap column 0 and column r of C (rows 0..m-1, leading dimension ldc) and w[0], w[r]
+__global__ void k_swap_first(cplx *C, int ldc, int m, double *w, int r) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const cplx t = C[(int64_t)i * ldc];
+    C[(int64_t)i * ldc] = C[(int64_t)i * ldc + r];
+    C[(int64_t)i * ldc + r] = t;
+  }
+  if (threadIdx.x == 0) {
+    const double t = w[0];
+    w[0] = w[r];
+    w[r] = t;
+  }
+}
+
 // R[r] = SY[r] - w[r] Y[r]
 __global__ void k_residual(const cplx *SY, const cplx *Y, const double *w, int64_t k, int64_t n,
                            cplx *R) {
@@ -144,6 +158,8 @@ struct Davidson {
   double tsig = 0.0;
   int m = 0;
   int nb = 0;  // leading subspace vectors whose sigma is FP64
+  bool follow = false;  // root-specific: track the Ritz vector closest to gfol
+  DBuf gfol, ovl;
   int prec64 = ADC_PREC_FP64;  // precision of the refinement products (FP64 or the sliced FP64-accurate product)
 
   Davidson(adc_ctx *c_, int nr, int mmax_, int krmax_)
@@ -272,11 +288,39 @@ struct Davidson {
     combine(ex, Cv.c() + ycols, mmax, m, nr - ycols, AV.c(), N, N, C1(), C0(), SY.c() + (int64_t)ycols * N, N);
     ycols = nr;
   }
+  // root-specific step: the Ritz vector with the largest |<g|y_r>| (y_r = sum_i Cv[i][r] v_i)
+  // becomes column 0 of Cv and w
+  void pick_followed() {
+    gram(ex, gfol.c(), N, 1, V.c(), N, m, N, C1(), ovl.c(), m);
+    std::vector<cplx> s(m), cv((size_t)m * m);
+    ADC_CUDA(cudaMemcpyAsync(s.data(), ovl.p, m * sizeof(cplx), cudaMemcpyDeviceToHost, ex.stream));
+    ADC_CUDA(cudaMemcpy2DAsync(cv.data(), m * sizeof(cplx), Cv.p, mmax * sizeof(cplx), m * sizeof(cplx), m,
+                               cudaMemcpyDeviceToHost, ex.stream));
+    ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    int best = 0;
+    double bo = -1.0;
+    for (int r = 0; r < m; ++r) {
+      double re = 0.0, im = 0.0;
+      for (int i = 0; i < m; ++i) {
+        const cplx a = cv[(size_t)i * m + r], b = s[i];
+        re += a.x * b.x - a.y * b.y;
+        im += a.x * b.y + a.y * b.x;
+      }
+      const double o2 = re * re + im * im;
+      if (o2 > bo) { bo = o2; best = r; }
+    }
+    if (best != 0) {
+      k_swap_first<<<1, 256, 0, ex.stream>>>(Cv.c(), mmax, m, w.d(), best);
+      ADC_CHECK_LAUNCH();
+    }
+  }
+
   std::vector<double> ritz(int nr) {
     nr = std::min(std::max(nr, nroots), std::min(m, krmax));
     k_hermitize<<<(m * m + 255) / 256, 256, 0, ex.stream>>>(G.c(), mmax, m, H.c(), mmax);
     ADC_CHECK_LAUNCH();
     jacobi_eigh(ex, H.c(), m, mmax, w.d(), Cv.c(), mmax, (int *)info.p);
+    if (follow) pick_followed();
     ycols = 0;
     ritz_vectors(std::min(nr, nroots));
     k_residual<<<grid1d((int64_t)nroots * N, 256), 256, 0, ex.stream>>>(SY.c(), Y.c(), w.d(), nroots, N, R.c());
@@ -303,7 +347,7 @@ struct Davidson {
 };
 
 int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision, const cplx *guess,
-                 int64_t nguess, double *omega, cplx *Yout, double *err64, adc_stats *st_out) {
+                 int64_t nguess, double *omega, cplx *Yout, double *err64, adc_stats *st_out, bool follow) {
   Timer total;
   const int64_t N = c->N;
   ADC_REQUIRE(nroots >= 1 && nroots <= N, ADC_ERR_ARG, "nroots out of range");
@@ -316,7 +360,15 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   mmax = (int)std::min<int64_t>(std::min<int64_t>(mmax, N), 1024);
   mmax = std::max(mmax, std::min<int>((int)N, nroots + 1));
   const int krmax = std::min(mmax, std::max(2 * nroots, kb));
+  ADC_REQUIRE(!follow || (nroots == 1 && guess && nguess >= 1), ADC_ERR_ARG,
+              "root-specific Davidson: one root and a guess vector");
   Davidson d(c, nroots, mmax, krmax);
+  if (follow) {
+    d.follow = true;
+    d.gfol = cbuf(c->ex, N);
+    d.ovl = cbuf(c->ex, mmax);
+    ADC_CUDA(cudaMemcpyAsync(d.gfol.p, guess, N * sizeof(cplx), cudaMemcpyDeviceToDevice, c->ex.stream));
+  }
   // refinement products: FP64, or the sliced FP64-accurate tensor-core product
   if (precision != ADC_PREC_FP64 && c->opts.refine == ADC_PREC_SLICED) d.prec64 = ADC_PREC_SLICED;
   Exec &ex = c->ex;

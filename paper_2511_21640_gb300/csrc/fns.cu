@@ -1,4 +1,5 @@
-// Frozen natural spinors from the MP2 virtual density (Sec. 2.4, Eqs. 25-30).
+// Frozen natural spinors from the MP2 virtual density (Sec. 2.4, Eqs. 25-30),
+// optionally plus a state density (Eq. 31, state-specific natural spinors).
 //   Eq. 25: D_ab = 1/2 sum_cij <ac||ij><ij||bc> / (eps_ij^ac eps_ij^bc)
 //               = 1/2 sum_ijc t_ij^ac conj(t_ij^bc)
 //   Eq. 26: D V = V eta (eta descending);  Eq. 27: keep eta_i >= eta_crit
@@ -21,13 +22,16 @@ __global__ void k_reverse(const double *w, const cplx *V, int n, double *wo, cpl
 }
 }  // namespace
 
+// Dadd (device, v x v, or null) is added to the MP2 density before Eq. 26: the
+// state density of a root for the state-specific natural spinors (Eq. 31)
 void fns_run(adc_ctx *c, cplx *D, double *eta, cplx *Vout, double eta_crit, int64_t *n_keep, cplx *U,
-             double *eps_new) {
+             double *eps_new, const cplx *Dadd) {
   Exec &ex = c->ex;
   const int64_t o = c->o, v = c->v;
   TV t1 = TV::dense(c->t1.c(), {o, o, v, v});
   DBuf Db = cbuf(ex, v * v);
   einsum(ex, CR(0.5), t1, "ijac", t1.cj(), "ijbc", C0(), TV::dense(Db.c(), {v, v}), "ab");
+  if (Dadd) zaxpby(ex, v * v, C1(), Dadd, C1(), Db.c());
   if (D) ADC_CUDA(cudaMemcpyAsync(D, Db.c(), v * v * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
   DBuf A = cbuf(ex, v * v), Vasc = cbuf(ex, v * v), Vd = cbuf(ex, v * v);
   DBuf wasc(ex, v * sizeof(double)), wd(ex, v * sizeof(double)), info(ex, 16);
