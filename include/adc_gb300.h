@@ -183,6 +183,8 @@ int adc_main_block(adc_ctx *ctx, adc_c128 *M11);
  * (sigma(y + d) = sigma64(y) + sigma_bf16x3(d)); couplings between those FP64
  * base vectors and later corrections come from the FP64 products. A result
  * is accepted only when every FP64 residual norm ||M y - omega y|| <= tol.
+ * With opts.refine = ADC_PREC_SLICED those FP64 products (base, check) are
+ * the sliced FP64-accurate tensor-core products instead.
  *   guess   NULL, or [nguess][N] starting vectors (nguess >= nroots).
  *   omega   [nroots] eigenvalues, ascending (host or device).
  *   Y       NULL or [nroots][N] eigenvectors.

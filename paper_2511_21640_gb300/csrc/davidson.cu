@@ -111,15 +111,6 @@ __global__ void k_gather_rows(const cplx *R, const int *rows, int64_t nt, int64_
   }
 }
 
-__global__ void k_scale_row(cplx *X, int64_t n, const double *nrm) {
-  double s = 1.0 / nrm[0];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    X[i].x *= s;
-    X[i].y *= s;
-  }
-}
-
 __global__ void k_unit_vectors(cplx *V, int64_t n, const int64_t *idx, int k) {
   int r = blockIdx.x;
   if (r >= k) return;

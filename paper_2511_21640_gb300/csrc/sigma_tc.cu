@@ -1,7 +1,8 @@
-// Sigma product with the dense contractions on the tensor cores (BF16x3).
-// Same terms as sigma.cu (Sec. 2.1 Eqs. 10-12); the coupling, ladder and ring
-// contractions run through tc_gemm, the main block (n1 x n1) and the
-// zeroth-order diagonal stay FP64.
+// Sigma product with the dense contractions on the tensor cores: the BF16x3
+// (BF16x6) split (sigma_split) or the sliced FP64-accurate product
+// (sigma_sliced, tc_slice.cu). Same terms as sigma.cu (Sec. 2.1 Eqs. 10-12);
+// the coupling, ladder and ring contractions run on the tensor cores, the main
+// block (n1 x n1) and the zeroth-order diagonal stay FP64.
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
 #include "tc_slice.cuh"

@@ -80,7 +80,8 @@ __global__ void k_sl_exp_B(BSrc src, int64_t Nc, int64_t K, int *F) {
   }
 }
 
-// the ns digits of y = x 2^-E, written to planes[i][pos] (plane stride pe) with sign s
+// the ns digits of y = x 2^-E into plane i (planes pe elements apart) at pos0,
+// and their negations at pos1 when pos1 >= 0
 __device__ __forceinline__ void digits(double x, int E, int ns, int b, __nv_bfloat16 *base, int64_t pe,
                                        int64_t pos0, int64_t pos1) {
   double y = ldexp(x, -E);
