@@ -382,7 +382,7 @@ def run_reference(args, cfgname):
     N = v + o * v * (v - 1) // 2
     sig_vecs_per_root = args.ref_sigma_vectors_per_root
     for _ in range(args.warmup):
-        cpu_oracle_sample(p, c["x"], n_rows=2)
+        cpu_oracle_sample(p, c["x"], n_rows=1)
     ts = []
     for s in range(args.steps):
         t_row, what = cpu_oracle_sample(p, c["x"], n_rows=args.ref_rows, seed=10 + s)
@@ -420,9 +420,9 @@ def main():
     ap.add_argument("--e2e-setup", default="sliced", choices=["sliced", "fp64"],
                     help="IP/EA/EE: adc_init contractions of the end-to-end run")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-rows", type=int, default=6)
+    ap.add_argument("--ref-rows", type=int, default=1, help="reference arm: satellite rows per step (~20-35 s each)")
     ap.add_argument("--ref-sigma-vectors-per-root", type=float, default=8.0)
-    ap.add_argument("--cpu-rows", type=int, default=6)
+    ap.add_argument("--cpu-rows", type=int, default=1, help="CPU baseline: satellite rows timed (~20-35 s each)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
