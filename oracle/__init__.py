@@ -21,6 +21,10 @@ Modules
 ``gradients``   Hellmann-Feynman derivatives of the roots (Eq. 10) along a
                 direction of (B, eps, x), from central differences of the
                 explicit matrix.
+``properties``  EE ground-to-excited transition densities from the ISR
+                transition moments (Sec. 2.2), singles to second and doubles
+                to first order; ``isr_series.transition_moments_series`` is
+                their brute-force pin.
 ``ssfns``       state-specific natural spinors for EA and EE (Eqs. 31-32):
                 state density of the zeroth-order intermediate states, guess
                 transformation, root-specific solves, corrected energies.

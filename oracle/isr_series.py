@@ -35,7 +35,7 @@ import numpy as np
 import scipy.sparse as sp
 
 __all__ = ["FockSpace", "antisym_eri_dense", "rspt_ground_state", "isr_series",
-           "class_indices", "fci_energies", "mp1_density_bruteforce"]
+           "class_indices", "fci_energies", "mp1_density_bruteforce", "transition_moments_series"]
 
 
 def antisym_eri_dense(B):
@@ -277,8 +277,12 @@ def _class_operator(fs, kind, cls, label, nel):
     raise ValueError(kind)
 
 
-def isr_series(eps, B, nocc, kind, nord=4):
+def isr_series(eps, B, nocc, kind, nord=4, want_states=False):
     """Exact perturbation orders of the ISR secular matrix for a tiny case.
+
+    With want_states the intermediate states themselves are returned instead
+    (``states`` [nord, N, dim] in the target sector, and for EE the
+    normalised ground-state series ``psi0`` [nord, dim]).
 
     Returns dict with
       ``M``: [nord, N, N] series (class 1 states first, then class 2),
@@ -324,6 +328,9 @@ def isr_series(eps, B, nocc, kind, nord=4):
         ortho.append(tilde)
         excited.append(tilde)
     states = np.concatenate(excited, axis=1)
+    if want_states:
+        return {"states": states, "psi0": ortho[0][:, 0, :] if kind == "EE" else None, "fs": fs,
+                "nel": tgt, "n1": len(classes[0]), "labels": classes}
     # (H - E0) applied to the state series
     h0 = sec_t.h0
     HS = np.zeros_like(states)
@@ -366,3 +373,23 @@ def mp1_density_bruteforce(eps, B, nocc):
         for q in range(nmo):
             rho[p, q] = np.vdot(p1, fs.excitation(p, q, nocc) @ p1)
     return rho, psi
+
+
+def transition_moments_series(eps, B, nocc, nord=3):
+    """EE transition moments f_I(pq) = <Psi~_I| a+_p a_q |Psi0> as a series.
+
+    Intermediate states of the ISR (Eqs. 5-6, as in isr_series) and the
+    normalised ground state, both as perturbation series; returns
+    f [nord, N, nmo, nmo] (class 1 first, labels as class_indices).
+    """
+    r = isr_series(eps, B, nocc, "EE", nord=nord, want_states=True)
+    fs, nel, states, psi0 = r["fs"], r["nel"], r["states"], r["psi0"]
+    nmo = fs.nmo
+    N = states.shape[1]
+    f = np.zeros((nord, N, nmo, nmo), dtype=np.complex128)
+    for p in range(nmo):
+        for q in range(nmo):
+            E = fs.excitation(p, q, nel)
+            Epsi = np.stack([E @ psi0[n] for n in range(nord)])  # [nord, dim]
+            f[:, :, p, q] = _sdot(states, Epsi[:, None, :])[:, :, 0]
+    return f, r["n1"], r["labels"]

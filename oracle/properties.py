@@ -1,0 +1,69 @@
+"""Ground-to-excited transition densities of EE-ADC (oracle), Sec. 2.2.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+The transition density of state K is rho_pq = <Psi_K| a+_p a_q |Psi0> =
+sum_I conj(Y_IK) f_I(pq), with the ISR transition moments
+f_I(pq) = <Psi~_I| a+_p a_q |Psi0> (Psi~_I the intermediate states of Eqs.
+5-6, Psi0 the normalised MP ground state); a transition moment of a
+one-particle operator d is T = sum_pq d_pq rho_pq.
+
+Through the orders used with ADC(2) and ADC(3) eigenvectors (singles to
+second, doubles to first order), with S the singles label (i, a), D the
+doubles label (i<j, a<b), t / t2 the first- / second-order doubles
+amplitudes, s2 the second-order singles and S2 the second-order overlap of
+the orthogonalised singles precursors (the singles f is S^{1/2} on its
+excitation block):
+
+  f_S(b, j) = d_ab d_ij + 1/2 S2_{ia,jb}           (p = b virtual, q = j occupied)
+  f_S(j, b) = t_ij^ab + t2_ij^ab                    (p = j occupied, q = b virtual)
+  f_S(k, l) = -d_li s2_k^a,    f_S(e, f) = d_ae s2_i^f
+  f_D(k, l) = -d_li t_kj^ab - d_lj t_ik^ab,    f_D(e, f) = d_ae t_ij^fb + d_be t_ij^af
+
+(every term pinned against the brute-force ISR series in determinant space).
+Summed over the packed doubles with the full antisymmetric Y:
+
+  rho_bj = conj(y_jb) + 1/2 sum_ia conj(y_ia) S2_{ia,jb}
+  rho_jb = sum_ia conj(y_ia) (t_ij^ab + t2_ij^ab)
+  rho_kl = -sum_a conj(y_la) s2_k^a - 1/2 sum_jab conj(Y_ljab) t_kj^ab
+  rho_ef = sum_i conj(y_ie) s2_i^f + 1/2 sum_ijb conj(Y_ijeb) t_ij^fb
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import adc_ee as _ee
+from .integrals import Amplitudes
+
+__all__ = ["singles_overlap2", "transition_density", "transition_moment"]
+
+
+def singles_overlap2(B, eps_occ, eps_vir, amp=None):
+    """S2_{ia,jb}: second-order overlap of the orthogonalised singles precursors."""
+    T = _ee.Tensors(B, eps_occ, eps_vir, amp=amp)
+    o, v = T.o, T.v
+    N2 = 0.25 * np.sum(np.abs(T.amp.t1) ** 2)
+    return T.evaluate("SS_S2", "iajb") - N2 * np.einsum("ij,ab->iajb", np.eye(o), np.eye(v))
+
+
+def transition_density(y, B, eps_occ, eps_vir, amp=None, S2=None):
+    """rho [nmo][nmo] of one EE vector y (packed singles + doubles)."""
+    amp = amp if amp is not None else Amplitudes(B, eps_occ, eps_vir)
+    o, v = amp.nocc, amp.nvir
+    S2 = S2 if S2 is not None else singles_overlap2(B, eps_occ, eps_vir, amp=amp)
+    y = np.asarray(y, np.complex128).reshape(-1)
+    n1 = o * v
+    y1c = y[:n1].reshape(o, v).conj()
+    Yc = _ee.unpack2(y[n1:][None], o, v)[0].conj()
+    t, t2, s2 = amp.t1, amp.t2d, amp.t2s
+    rho = np.zeros((o + v, o + v), np.complex128)
+    rho[o:, :o] = y1c.T + 0.5 * np.einsum("ia,iajb->bj", y1c, S2)
+    rho[:o, o:] = np.einsum("ia,ijab->jb", y1c, t + t2)
+    rho[:o, :o] = -np.einsum("la,ka->kl", y1c, s2) - 0.5 * np.einsum("ljab,kjab->kl", Yc, t)
+    rho[o:, o:] = np.einsum("ie,if->ef", y1c, s2) + 0.5 * np.einsum("ijeb,ijfb->ef", Yc, t)
+    return rho
+
+
+def transition_moment(rho, d):
+    """T = sum_pq d_pq rho_pq for a one-particle operator d [nmo][nmo] (or [3][nmo][nmo])."""
+    return np.einsum("...pq,pq->...", np.asarray(d), rho)
