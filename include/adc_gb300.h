@@ -219,6 +219,23 @@ int adc_fns_density(adc_ctx *ctx, adc_c128 *D, double *eta, adc_c128 *V,
 int adc_fns_transform(adc_ctx *ctx, const adc_c128 *U, int64_t ldu,
                       int64_t n_keep, adc_c128 *Bout);
 
+/* Ground-to-excited transition densities of EE-ADC (Sec. 2.2):
+ * rho_pq = <Psi_K| a+_p a_q |Psi0> = sum_I conj(Y_I) <Psi~_I| a+_p a_q |Psi0>
+ * for each of the k vectors Y [k][N] (normally eigenvectors), with the ISR
+ * transition moments through second order for the singles and first order
+ * for the doubles:
+ *   rho_bj = conj(y_jb) + 1/2 sum_ia conj(y_ia) S2_{ia,jb}   (b virtual, j occupied)
+ *   rho_jb = sum_ia conj(y_ia) (t_ij^ab + t2_ij^ab)
+ *   rho_kl = -sum_a conj(y_la) s2_k^a - 1/2 sum_jab conj(Y_ljab) t_kj^ab
+ *   rho_ef = sum_i conj(y_ie) s2_i^f + 1/2 sum_ijb conj(Y_ijeb) t_ij^fb
+ * (t, t2: first- and second-order doubles, s2: second-order singles, S2: the
+ * second-order overlap of the orthogonalised singles precursors, Y the
+ * doubles as a full antisymmetric array). rho [k][nmo][nmo], orbitals in
+ * the order of B (occupied first); host or device. A transition moment of a
+ * one-particle operator d is sum_pq d_pq rho_pq. EE contexts only
+ * (ADC_ERR_UNSUPPORTED otherwise). Synchronous. */
+int adc_transition_density(adc_ctx *ctx, const adc_c128 *Y, int64_t k, adc_c128 *rho);
+
 /* ------------------------------------------------------------------------
  * State-specific frozen natural spinors (Sec. 2.3, Eqs. 31-32), EA and EE.
  * ---------------------------------------------------------------------- */

@@ -116,6 +116,7 @@ def _load():
         "adc_diag_gemm": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_sigma_adjoint": (I, [P, P, P, I64, P, P, P, ctypes.POINTER(D)]),
         "adc_state_density": (I, [P, P, P]),
+        "adc_transition_density": (I, [P, P, I64, P]),
         "adc_ssfns_density": (I, [P, P, D, P, P, ctypes.POINTER(I64), P, P]),
         "adc_fns_vector": (I, [P, P, P, I64, I64, P]),
         "adc_davidson_follow": (I, [P, P, D, I, I, ctypes.POINTER(D), P, ctypes.POINTER(D), P]),
@@ -329,6 +330,16 @@ class Context:
                                      _ptr(gB, np.complex128), _ptr(geo, np.float64), _ptr(gev, np.float64),
                                      ctypes.byref(gx)), self._h)
         return gB, geo, gev, gx.value
+
+    def transition_density(self, Y):
+        """Ground-to-excited transition densities [k][nmo][nmo] of EE vectors Y [k][N]
+        (``adc_transition_density``, Sec. 2.2)."""
+        Y = np.ascontiguousarray(np.atleast_2d(Y), dtype=np.complex128)
+        nmo = self.nocc + self.nvir
+        rho = np.empty((Y.shape[0], nmo, nmo), dtype=np.complex128)
+        _check(lib.adc_transition_density(self._h, _ptr(Y, np.complex128), Y.shape[0], _ptr(rho, np.complex128)),
+               self._h)
+        return rho
 
     def state_density(self, y):
         """Virtual density of the configurations weighted by y (``adc_state_density``, Eq. 31)."""

@@ -1,0 +1,83 @@
+// EE ground-to-excited transition densities (Sec. 2.2).
+//
+// rho_pq = <Psi_K| a+_p a_q |Psi0> = sum_I conj(Y_I) f_I(pq) with the ISR
+// transition moments f_I(pq) = <Psi~_I| a+_p a_q |Psi0>, singles to second
+// and doubles to first order (t / t2: first- / second-order doubles, s2:
+// second-order singles, S2: second-order overlap of the orthogonalised
+// singles precursors, Y the doubles as a full antisymmetric array):
+//   rho_bj = conj(y_jb) + 1/2 sum_ia conj(y_ia) S2_{ia,jb}
+//   rho_jb = sum_ia conj(y_ia) (t_ij^ab + t2_ij^ab)
+//   rho_kl = -sum_a conj(y_la) s2_k^a - 1/2 sum_jab conj(Y_ljab) t_kj^ab
+//   rho_ef = sum_i conj(y_ie) s2_i^f + 1/2 sum_ijb conj(Y_ijeb) t_ij^fb
+// A transition moment of a one-particle operator d is sum_pq d_pq rho_pq.
+#include "ctx.cuh"
+#include "ee.cuh"
+
+namespace adc {
+
+namespace {
+// dst[(r0 + r) * ld + c0 + c] = src[r * cols + c]
+__global__ void k_put_block(const cplx *__restrict__ src, int64_t rows, int64_t cols, cplx *dst, int64_t ld,
+                            int64_t r0, int64_t c0) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < rows * cols;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / cols, cc = idx - r * cols;
+    dst[(r0 + r) * ld + c0 + cc] = src[idx];
+  }
+}
+}  // namespace
+
+void transition_density(adc_ctx *c, const cplx *Y, int64_t k, cplx *rho) {
+  ADC_REQUIRE(c->kind == ADC_EE && c->ee, ADC_ERR_UNSUPPORTED, "transition densities: EE-ADC");
+  Exec &ex = c->ex;
+  EEOps &E = *c->ee;
+  const int64_t o = c->o, v = c->v, n1 = c->n1, N = c->N, nmo = c->nmo;
+  const int64_t po = npairs(o), pv = npairs(v);
+  TagScope tg(ex, "properties");
+  // second-order amplitudes (the setup keeps them at third order only)
+  if (!E.t2d.p || !E.t2s.p) {
+    DBuf Gvv, Lad;
+    second_order_amplitudes(c, Gvv, Lad, E.t2d, E.t2s);
+  }
+  DBuf S2 = cbuf(ex, n1 * n1);
+  fill_zero(ex, S2.p, S2.bytes);
+  eval_terms(ex, E.S2, ee_source(c), {}, false, C1(), TV::dense(S2.c(), {o, v, o, v}), "iajb");
+  DBuf tt = cbuf(ex, o * o * v * v);
+  ADC_CUDA(cudaMemcpyAsync(tt.p, c->t1.p, tt.bytes, cudaMemcpyDeviceToDevice, ex.stream));
+  zaxpby(ex, o * o * v * v, C1(), E.t2d.c(), C1(), tt.c());
+  const TV t1 = TV::dense(c->t1.c(), {o, o, v, v}), T12 = TV::dense(tt.c(), {o, o, v, v});
+  const TV s2 = TV::dense(E.t2s.c(), {o, v}), S2v = TV::dense(S2.c(), {o, v, o, v});
+  DBuf Yf = cbuf(ex, o * o * v * v), half = cbuf(ex, std::max<int64_t>(po, 1) * v * v);
+  DBuf Bvo = cbuf(ex, v * o), Bov = cbuf(ex, o * v), Boo = cbuf(ex, o * o), Bvv = cbuf(ex, v * v);
+  for (int64_t z = 0; z < k; ++z) {
+    const cplx *y = Y + z * N;
+    cplx *R = rho + z * nmo * nmo;
+    const TV y1c(const_cast<cplx *>(y), {o, v}, {v, 1}, true);
+    if (po > 0 && pv > 0) {
+      pair_unpack(ex, y + n1, 1, po, 0, pv, v, 1, half.c());
+      pair_unpack(ex, half.c(), 1, 1, po * v * v, 0, o, v * v, Yf.c());
+    } else {
+      fill_zero(ex, Yf.p, Yf.bytes);
+    }
+    const TV Yc = TV::dense(Yf.c(), {o, o, v, v}).cj();
+    // excitation block rho[o+b][j]
+    permute(ex, y, {v, o}, {1, v}, true, Bvo.c(), C1(), C0());
+    einsum(ex, CR(0.5), y1c, "ia", S2v, "iajb", C1(), TV::dense(Bvo.c(), {v, o}), "bj");
+    // de-excitation block rho[j][o+b]
+    einsum(ex, C1(), y1c, "ia", T12, "ijab", C0(), TV::dense(Bov.c(), {o, v}), "jb");
+    // occupied block rho[k][l]
+    einsum(ex, CR(-1.0), y1c, "la", s2, "ka", C0(), TV::dense(Boo.c(), {o, o}), "kl");
+    einsum(ex, CR(-0.5), Yc, "ljab", t1, "kjab", C1(), TV::dense(Boo.c(), {o, o}), "kl");
+    // virtual block rho[o+e][o+f]
+    einsum(ex, C1(), y1c, "ie", s2, "if", C0(), TV::dense(Bvv.c(), {v, v}), "ef");
+    einsum(ex, CR(0.5), Yc, "ijeb", t1, "ijfb", C1(), TV::dense(Bvv.c(), {v, v}), "ef");
+    k_put_block<<<grid1d(v * o, 256), 256, 0, ex.stream>>>(Bvo.c(), v, o, R, nmo, o, 0);
+    k_put_block<<<grid1d(o * v, 256), 256, 0, ex.stream>>>(Bov.c(), o, v, R, nmo, 0, o);
+    k_put_block<<<grid1d(o * o, 256), 256, 0, ex.stream>>>(Boo.c(), o, o, R, nmo, 0, 0);
+    k_put_block<<<grid1d(v * v, 256), 256, 0, ex.stream>>>(Bvv.c(), v, v, R, nmo, o, o);
+    ADC_CHECK_LAUNCH();
+  }
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+}
+
+}  // namespace adc
