@@ -236,6 +236,19 @@ int adc_fns_transform(adc_ctx *ctx, const adc_c128 *U, int64_t ldu,
  * (ADC_ERR_UNSUPPORTED otherwise). Synchronous. */
 int adc_transition_density(adc_ctx *ctx, const adc_c128 *Y, int64_t k, adc_c128 *rho);
 
+/* Excited-state one-particle densities of EE-ADC states (Sec. 2.2), at the
+ * level stated for ADC(2) states: rho^K_pq = <a+_p a_q> = rho0_pq (the MP
+ * ground-state density through second order: rho0_ij = d_ij - 1/2 sum_kab
+ * conj(t_jk^ab) t_ik^ab, rho0_ab = 1/2 sum_ijc conj(t_ij^ac) t_ij^bc, rho0_jb =
+ * s2_j^b, rho0_bj = conj(s2_j^b)) plus Y^H G Y with G the zeroth-order
+ * intermediate-state representation of a+_p a_q - rho0 (the configurations):
+ *   rho_kl += -sum_a conj(y_la) y_ka - 1/2 sum_jab conj(Y_ljab) Y_kjab,
+ *   rho_ef += sum_i conj(y_ie) y_if + 1/2 sum_ijc conj(Y_ijec) Y_ijfc,
+ *   rho_jb += sum_ia conj(y_ia) Y_ijab,  rho_bj += sum_ia conj(Y_ijab) y_ia.
+ * Y [k][N] normalised vectors, rho [k][nmo][nmo]; host or device. Expectation
+ * values are sum_pq d_pq rho_pq. EE contexts only. Synchronous. */
+int adc_excited_density(adc_ctx *ctx, const adc_c128 *Y, int64_t k, adc_c128 *rho);
+
 /* ------------------------------------------------------------------------
  * State-specific frozen natural spinors (Sec. 2.3, Eqs. 31-32), EA and EE.
  * ---------------------------------------------------------------------- */

@@ -27,6 +27,19 @@ Summed over the packed doubles with the full antisymmetric Y:
   rho_jb = sum_ia conj(y_ia) (t_ij^ab + t2_ij^ab)
   rho_kl = -sum_a conj(y_la) s2_k^a - 1/2 sum_jab conj(Y_ljab) t_kj^ab
   rho_ef = sum_i conj(y_ie) s2_i^f + 1/2 sum_ijb conj(Y_ijeb) t_ij^fb
+
+Excited-state density (the level the paper states for ADC(2) states: the
+ground-state density through second order plus the zeroth-order
+intermediate-state representation of D - D0, i.e. the configurations
+weighted by the eigenvector), rho^K_pq = <a+_p a_q>:
+
+  ground state  rho0_ij = d_ij - 1/2 sum_kab conj(t_jk^ab) t_ik^ab,
+                rho0_ab = 1/2 sum_ijc conj(t_ij^ac) t_ij^bc,
+                rho0_jb = s2_j^b,  rho0_bj = conj(s2_j^b);
+  difference    rho_kl += -sum_a conj(y_la) y_ka - 1/2 sum_jab conj(Y_ljab) Y_kjab,
+                rho_ef += sum_i conj(y_ie) y_if + 1/2 sum_ijc conj(Y_ijec) Y_ijfc,
+                rho_jb += sum_ia conj(y_ia) Y_ijab,  rho_bj += sum_ia conj(Y_ijab) y_ia
+(pinned against the same quantities in determinant space).
 """
 from __future__ import annotations
 
@@ -35,7 +48,7 @@ import numpy as np
 from . import adc_ee as _ee
 from .integrals import Amplitudes
 
-__all__ = ["singles_overlap2", "transition_density", "transition_moment"]
+__all__ = ["singles_overlap2", "transition_density", "transition_moment", "excited_state_density"]
 
 
 def singles_overlap2(B, eps_occ, eps_vir, amp=None):
@@ -67,3 +80,24 @@ def transition_density(y, B, eps_occ, eps_vir, amp=None, S2=None):
 def transition_moment(rho, d):
     """T = sum_pq d_pq rho_pq for a one-particle operator d [nmo][nmo] (or [3][nmo][nmo])."""
     return np.einsum("...pq,pq->...", np.asarray(d), rho)
+
+
+def excited_state_density(y, B, eps_occ, eps_vir, amp=None):
+    """rho^K [nmo][nmo] of one EE vector y: ground state to second order + zeroth-order ISR difference."""
+    amp = amp if amp is not None else Amplitudes(B, eps_occ, eps_vir)
+    o, v = amp.nocc, amp.nvir
+    y = np.asarray(y, np.complex128).reshape(-1)
+    n1 = o * v
+    y1 = y[:n1].reshape(o, v)
+    Y = _ee.unpack2(y[n1:][None], o, v)[0]
+    t, s2 = amp.t1, amp.t2s
+    rho = np.zeros((o + v, o + v), np.complex128)
+    rho[:o, :o] = np.eye(o) - 0.5 * np.einsum("jkab,ikab->ij", t.conj(), t)
+    rho[o:, o:] = 0.5 * np.einsum("ijac,ijbc->ab", t.conj(), t)
+    rho[:o, o:] = s2
+    rho[o:, :o] = s2.conj().T
+    rho[:o, :o] += -np.einsum("la,ka->kl", y1.conj(), y1) - 0.5 * np.einsum("ljab,kjab->kl", Y.conj(), Y)
+    rho[o:, o:] += np.einsum("ie,if->ef", y1.conj(), y1) + 0.5 * np.einsum("ijec,ijfc->ef", Y.conj(), Y)
+    rho[:o, o:] += np.einsum("ia,ijab->jb", y1.conj(), Y)
+    rho[o:, :o] += np.einsum("ijab,ia->bj", Y.conj(), y1)
+    return rho

@@ -117,6 +117,7 @@ def _load():
         "adc_sigma_adjoint": (I, [P, P, P, I64, P, P, P, ctypes.POINTER(D)]),
         "adc_state_density": (I, [P, P, P]),
         "adc_transition_density": (I, [P, P, I64, P]),
+        "adc_excited_density": (I, [P, P, I64, P]),
         "adc_ssfns_density": (I, [P, P, D, P, P, ctypes.POINTER(I64), P, P]),
         "adc_fns_vector": (I, [P, P, P, I64, I64, P]),
         "adc_davidson_follow": (I, [P, P, D, I, I, ctypes.POINTER(D), P, ctypes.POINTER(D), P]),
@@ -338,6 +339,15 @@ class Context:
         nmo = self.nocc + self.nvir
         rho = np.empty((Y.shape[0], nmo, nmo), dtype=np.complex128)
         _check(lib.adc_transition_density(self._h, _ptr(Y, np.complex128), Y.shape[0], _ptr(rho, np.complex128)),
+               self._h)
+        return rho
+
+    def excited_density(self, Y):
+        """Excited-state densities [k][nmo][nmo] of EE vectors Y [k][N] (``adc_excited_density``)."""
+        Y = np.ascontiguousarray(np.atleast_2d(Y), dtype=np.complex128)
+        nmo = self.nocc + self.nvir
+        rho = np.empty((Y.shape[0], nmo, nmo), dtype=np.complex128)
+        _check(lib.adc_excited_density(self._h, _ptr(Y, np.complex128), Y.shape[0], _ptr(rho, np.complex128)),
                self._h)
         return rho
 

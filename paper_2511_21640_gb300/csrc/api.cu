@@ -428,6 +428,20 @@ int adc_transition_density(adc_ctx *c, const adc_c128 *Y, int64_t k, adc_c128 *r
   ADC_API_CATCH(c)
 }
 
+int adc_excited_density(adc_ctx *c, const adc_c128 *Y, int64_t k, adc_c128 *rho) {
+  if (!c) return ADC_ERR_STATE;
+  if (!Y || !rho || k < 1) return ADC_ERR_ARG;
+  if (c->kind != ADC_EE) return ADC_ERR_UNSUPPORTED;
+  ADC_API_TRY
+  DevIn yin(c->ex, Y, (size_t)k * c->N * sizeof(cplx));
+  DevOut rout(c->ex, rho, (size_t)k * c->nmo * c->nmo * sizeof(cplx));
+  excited_density(c, (const cplx *)yin.p, k, (cplx *)rout.p);
+  rout.finish(c->ex);
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
 int adc_sigma_adjoint(adc_ctx *c, const adc_c128 *Y, const double *gomega, int64_t nroots, adc_c128 *gB,
                       double *geps_occ, double *geps_vir, double *gx) {
   if (!c) return ADC_ERR_STATE;

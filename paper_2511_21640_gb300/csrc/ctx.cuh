@@ -83,6 +83,8 @@ void to_fns_basis(adc_ctx *c, const cplx *y, const cplx *U, int64_t ldu, int64_t
 int64_t fns_dim(int kind, int64_t o, int64_t nk);
 // EE ground-to-excited transition densities rho [k][nmo][nmo] of the vectors Y [k][N] (properties.cu)
 void transition_density(adc_ctx *c, const cplx *Y, int64_t k, cplx *rho);
+// EE excited-state densities rho [k][nmo][nmo]: ground state to second order + zeroth-order ISR difference
+void excited_density(adc_ctx *c, const cplx *Y, int64_t k, cplx *rho);
 int ssfns_run(const adc_c128 *B, int64_t naux, const double *eps_occ, int64_t nocc, const double *eps_vir,
               int64_t nvir, int kind, int order, double x, int nroots, double eta_crit, double tol, int max_iter,
               int precision, const adc_opts *opts, adc_ssfns_root *out);

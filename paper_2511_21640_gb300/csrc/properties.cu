@@ -10,6 +10,18 @@
 //   rho_kl = -sum_a conj(y_la) s2_k^a - 1/2 sum_jab conj(Y_ljab) t_kj^ab
 //   rho_ef = sum_i conj(y_ie) s2_i^f + 1/2 sum_ijb conj(Y_ijeb) t_ij^fb
 // A transition moment of a one-particle operator d is sum_pq d_pq rho_pq.
+//
+// Excited-state densities rho^K_pq = <a+_p a_q> at the level stated for ADC(2)
+// states: the ground-state density through second order plus the
+// configurations weighted by the eigenvector (zeroth-order intermediate
+// states) for D - D0:
+//   rho0_ij = d_ij - 1/2 sum_kab conj(t_jk^ab) t_ik^ab,  rho0_ab = 1/2 sum_ijc conj(t_ij^ac) t_ij^bc,
+//   rho0_jb = s2_j^b,  rho0_bj = conj(s2_j^b);
+//   rho_kl += -sum_a conj(y_la) y_ka - 1/2 sum_jab conj(Y_ljab) Y_kjab,
+//   rho_ef += sum_i conj(y_ie) y_if + 1/2 sum_ijc conj(Y_ijec) Y_ijfc,
+//   rho_jb += sum_ia conj(y_ia) Y_ijab,  rho_bj += sum_ia conj(Y_ijab) y_ia.
+#include <vector>
+
 #include "ctx.cuh"
 #include "ee.cuh"
 
@@ -75,6 +87,61 @@ void transition_density(adc_ctx *c, const cplx *Y, int64_t k, cplx *rho) {
     k_put_block<<<grid1d(o * v, 256), 256, 0, ex.stream>>>(Bov.c(), o, v, R, nmo, 0, o);
     k_put_block<<<grid1d(o * o, 256), 256, 0, ex.stream>>>(Boo.c(), o, o, R, nmo, 0, 0);
     k_put_block<<<grid1d(v * v, 256), 256, 0, ex.stream>>>(Bvv.c(), v, v, R, nmo, o, o);
+    ADC_CHECK_LAUNCH();
+  }
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+}
+
+void excited_density(adc_ctx *c, const cplx *Y, int64_t k, cplx *rho) {
+  ADC_REQUIRE(c->kind == ADC_EE && c->ee, ADC_ERR_UNSUPPORTED, "excited-state densities: EE-ADC");
+  Exec &ex = c->ex;
+  EEOps &E = *c->ee;
+  const int64_t o = c->o, v = c->v, n1 = c->n1, N = c->N, nmo = c->nmo;
+  const int64_t po = npairs(o), pv = npairs(v);
+  TagScope tg(ex, "properties");
+  if (!E.t2d.p || !E.t2s.p) {
+    DBuf Gvv, Lad;
+    second_order_amplitudes(c, Gvv, Lad, E.t2d, E.t2s);
+  }
+  const TV t1 = TV::dense(c->t1.c(), {o, o, v, v});
+  // ground-state density through second order, blocks
+  DBuf G0oo = cbuf(ex, o * o), G0vv = cbuf(ex, v * v), G0vo = cbuf(ex, v * o);
+  {
+    std::vector<cplx> id((size_t)(o * o), cmake(0.0, 0.0));
+    for (int64_t i = 0; i < o; ++i) id[(size_t)(i * o + i)] = cmake(1.0, 0.0);
+    ADC_CUDA(cudaMemcpyAsync(G0oo.p, id.data(), G0oo.bytes, cudaMemcpyHostToDevice, ex.stream));
+    ADC_CUDA(cudaStreamSynchronize(ex.stream));  // the host vector goes out of scope
+  }
+  einsum(ex, CR(-0.5), t1.cj(), "jkab", t1, "ikab", C1(), TV::dense(G0oo.c(), {o, o}), "ij");
+  einsum(ex, CR(0.5), t1.cj(), "ijac", t1, "ijbc", C0(), TV::dense(G0vv.c(), {v, v}), "ab");
+  permute(ex, E.t2s.c(), {v, o}, {1, v}, true, G0vo.c(), C1(), C0());
+  DBuf Yf = cbuf(ex, o * o * v * v), half = cbuf(ex, std::max<int64_t>(po, 1) * v * v);
+  DBuf Boo = cbuf(ex, o * o), Bvv = cbuf(ex, v * v), Bov = cbuf(ex, o * v), Bvo = cbuf(ex, v * o);
+  for (int64_t z = 0; z < k; ++z) {
+    const cplx *y = Y + z * N;
+    cplx *R = rho + z * nmo * nmo;
+    const TV y1(const_cast<cplx *>(y), {o, v}, {v, 1});
+    if (po > 0 && pv > 0) {
+      pair_unpack(ex, y + n1, 1, po, 0, pv, v, 1, half.c());
+      pair_unpack(ex, half.c(), 1, 1, po * v * v, 0, o, v * v, Yf.c());
+    } else {
+      fill_zero(ex, Yf.p, Yf.bytes);
+    }
+    const TV Yv = TV::dense(Yf.c(), {o, o, v, v});
+    ADC_CUDA(cudaMemcpyAsync(Boo.p, G0oo.p, Boo.bytes, cudaMemcpyDeviceToDevice, ex.stream));
+    einsum(ex, CR(-1.0), y1.cj(), "la", y1, "ka", C1(), TV::dense(Boo.c(), {o, o}), "kl");
+    einsum(ex, CR(-0.5), Yv.cj(), "ljab", Yv, "kjab", C1(), TV::dense(Boo.c(), {o, o}), "kl");
+    ADC_CUDA(cudaMemcpyAsync(Bvv.p, G0vv.p, Bvv.bytes, cudaMemcpyDeviceToDevice, ex.stream));
+    einsum(ex, C1(), y1.cj(), "ie", y1, "if", C1(), TV::dense(Bvv.c(), {v, v}), "ef");
+    einsum(ex, CR(0.5), Yv.cj(), "ijec", Yv, "ijfc", C1(), TV::dense(Bvv.c(), {v, v}), "ef");
+    ADC_CUDA(cudaMemcpyAsync(Bov.p, E.t2s.p, Bov.bytes, cudaMemcpyDeviceToDevice, ex.stream));
+    einsum(ex, C1(), y1.cj(), "ia", Yv, "ijab", C1(), TV::dense(Bov.c(), {o, v}), "jb");
+    ADC_CUDA(cudaMemcpyAsync(Bvo.p, G0vo.p, Bvo.bytes, cudaMemcpyDeviceToDevice, ex.stream));
+    einsum(ex, C1(), Yv.cj(), "ijab", y1, "ia", C1(), TV::dense(Bvo.c(), {v, o}), "bj");
+    k_put_block<<<grid1d(o * o, 256), 256, 0, ex.stream>>>(Boo.c(), o, o, R, nmo, 0, 0);
+    k_put_block<<<grid1d(v * v, 256), 256, 0, ex.stream>>>(Bvv.c(), v, v, R, nmo, o, o);
+    k_put_block<<<grid1d(o * v, 256), 256, 0, ex.stream>>>(Bov.c(), o, v, R, nmo, 0, o);
+    k_put_block<<<grid1d(v * o, 256), 256, 0, ex.stream>>>(Bvo.c(), v, o, R, nmo, o, 0);
     ADC_CHECK_LAUNCH();
   }
   ADC_CUDA(cudaStreamSynchronize(ex.stream));

@@ -1,7 +1,8 @@
-"""EE ground-to-excited transition densities on the GPU (adc_transition_density,
-Sec. 2.2) against the oracle: the closed forms of oracle/properties.py (1e-12
-relative, ADC(2) and ADC(3) contexts) and, on a tiny case, the brute-force ISR
-transition moments in determinant space directly (1e-12).
+"""EE ground-to-excited transition densities (adc_transition_density) and
+excited-state densities (adc_excited_density) on the GPU (Sec. 2.2) against the
+oracle: the closed forms of oracle/properties.py (1e-12 relative, ADC(2) and
+ADC(3) contexts) and, on a tiny case, the brute-force ISR transition moments in
+determinant space directly (1e-12).
 """
 import numpy as np
 import pytest
@@ -36,9 +37,12 @@ def test_transition_density_matches_oracle(gpu, o, v, Q, order, x, seed):
     with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=order, x=x) as c:
         Y = _vectors(c.N, 2, seed + 1)
         rho = c.transition_density(Y)
+        rk = c.excited_density(Y)
     for z in range(2):
         ref = oprop.transition_density(Y[z], p.B, p.eps_occ, p.eps_vir)
         assert np.abs(rho[z] - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+        refk = oprop.excited_state_density(Y[z], p.B, p.eps_occ, p.eps_vir)
+        assert np.abs(rk[z] - refk).max() < 1e-12 * max(1.0, np.abs(refk).max())
 
 
 def test_transition_density_matches_isr_series(gpu):

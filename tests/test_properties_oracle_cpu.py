@@ -8,6 +8,9 @@
 * Each block's leading order separately: the zeroth-order excitation block
   is conj(y), the first-order de-excitation block is sum conj(y_ia) t_ij^ab.
 * B = 0: rho is conj(y1) on the excitation block and zero elsewhere.
+* The excited-state density (ground state through second order plus the
+  configurations weighted by y) equals the same expectation values in
+  determinant space; its trace is the electron count and it is Hermitian.
 """
 import numpy as np
 import pytest
@@ -16,7 +19,7 @@ from synthetic import make_problem
 from oracle import adc_ee
 from oracle import properties as oprop
 from oracle.integrals import Amplitudes
-from oracle.isr_series import transition_moments_series
+from oracle.isr_series import _class_operator, class_indices, isr_series, transition_moments_series
 
 
 def _unit(n, seed):
@@ -55,3 +58,29 @@ def test_transition_density_without_interaction():
     ref = np.zeros_like(rho)
     ref[o:, :o] = y[:n1].reshape(o, v).conj().T
     assert np.abs(rho - ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("o,v,Q,seed", [(2, 3, 4, 1), (3, 3, 5, 2), (2, 4, 5, 3)])
+def test_excited_state_density_matches_determinant_space(o, v, Q, seed):
+    p = make_problem(o, v, Q, seed=seed, sigma=0.2, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    eps = np.concatenate([p.eps_occ, p.eps_vir])
+    r = isr_series(eps, p.B, o, "EE", nord=3, want_states=True)
+    fs, nel, psi0 = r["fs"], r["nel"], r["psi0"]
+    nmo = o + v
+    ref = np.zeros(fs.dim(o), np.complex128)
+    ref[fs.det_index(o, tuple(range(o)))] = 1.0
+    labels = class_indices("EE", o, v)
+    Phi = np.array([_class_operator(fs, "EE", c, lab, o) @ ref for c in range(2) for lab in labels[c]])
+    y = _unit(Phi.shape[0], seed)
+    psi = y @ Phi
+    rho_b = np.zeros((nmo, nmo), np.complex128)
+    for p_ in range(nmo):
+        for q in range(nmo):
+            E = fs.excitation(p_, q, nel)
+            rho_b[p_, q] = np.vdot(psi, E @ psi) - (1.0 if (p_ == q and p_ < o) else 0.0)
+            rho_b[p_, q] += sum(np.vdot(psi0[n], E @ psi0[m]) for n in range(3) for m in range(3 - n))
+    rho = oprop.excited_state_density(y, p.B, p.eps_occ, p.eps_vir)
+    assert np.abs(rho - rho_b).max() < 1e-13
+    assert np.abs(rho - rho.conj().T).max() < 1e-14
+    assert abs(np.trace(rho).real - o) < 1e-12
+
