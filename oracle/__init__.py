@@ -25,6 +25,8 @@ Modules
                 transition moments (Sec. 2.2), singles to second and doubles
                 to first order; ``isr_series.transition_moments_series`` is
                 their brute-force pin.
+``cholesky``    one-step pivoted Cholesky decomposition of the two-electron
+                integrals and the MO transformation of the vectors (Eqs. 41-42).
 ``ssfns``       state-specific natural spinors for EA and EE (Eqs. 31-32):
                 state density of the zeroth-order intermediate states, guess
                 transformation, root-specific solves, corrected energies.

@@ -79,6 +79,30 @@ def make_problem(nocc, nvir, naux, seed=0, sigma=0.05, occ_range=(-2.0, -0.5),
     return Problem(B, eps_occ, eps_vir, kind, order, x, seed, name)
 
 
+def make_eri(nao, rank, seed=0, decay=0.7):
+    """Synthetic AO two-electron integrals as the PSD matrix V[(mu nu)][(kappa lambda)].
+
+    V = sum_g w_g G_g G_g^T with real symmetric G_g (mu <-> nu), weights
+    w_g = decay^g: real, symmetric in each index pair and between the pairs,
+    positive semidefinite of rank <= `rank`, with the decaying spectrum a
+    Cholesky decomposition of integrals meets. Returns V [nao*nao][nao*nao].
+    """
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((rank, nao, nao))
+    G = 0.5 * (G + G.transpose(0, 2, 1))
+    w = decay ** np.arange(rank)
+    Gf = G.reshape(rank, nao * nao)
+    return np.ascontiguousarray((Gf.T * w) @ Gf)
+
+
+def random_unitary(n, seed=0):
+    """Haar-random complex unitary n x n (QR of a complex Gaussian, phases fixed)."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    Qm, R = np.linalg.qr(A)
+    return Qm * (np.diag(R) / np.abs(np.diag(R)))[None, :]
+
+
 def random_vectors(n, k, seed=1):
     """``k`` complex unit vectors of length ``n`` as a ``[k][n]`` complex128 array."""
     rng = np.random.default_rng(seed)
