@@ -250,6 +250,28 @@ int adc_transition_density(adc_ctx *ctx, const adc_c128 *Y, int64_t k, adc_c128 
 int adc_excited_density(adc_ctx *ctx, const adc_c128 *Y, int64_t k, adc_c128 *rho);
 
 /* ------------------------------------------------------------------------
+ * Cholesky vectors from two-electron integrals (Sec. 2.5, Eqs. 41-42).
+ * ---------------------------------------------------------------------- */
+
+/* One-step pivoted Cholesky decomposition (Eq. 41) of the symmetric positive
+ * semidefinite V [n][n] (n = nao^2, V[(mu nu)][(kappa lambda)] = (mu nu|kappa
+ * lambda), real): at each step the largest remaining diagonal element is the
+ * pivot; the decomposition stops when it is below tau (or not positive) or
+ * after max_rank vectors. Every residual element is then below tau.
+ *   L      [max_rank][n] (host or device): the vectors, rows beyond the rank zero.
+ *   pivots NULL or [max_rank] (host): pivot of each vector.
+ *   rank   (host): number of vectors.
+ * Synchronous; runs on a stream of its own. */
+int adc_cholesky(const double *V, int64_t n, double tau, int64_t max_rank, double *L, int64_t *pivots,
+                 int64_t *rank);
+
+/* Eq. 42: B[P] = C^H L^P C, the Cholesky vectors in the molecular spinor
+ * basis (the B of adc_init; Hermitian per P when each L^P is symmetric).
+ * L [rank][nao][nao] real, C [nao][nmo] complex (columns: spinors), B
+ * [rank][nmo][nmo]; host or device. Synchronous. */
+int adc_cholesky_mo(const double *L, int64_t rank, int64_t nao, const adc_c128 *C, int64_t nmo, adc_c128 *B);
+
+/* ------------------------------------------------------------------------
  * State-specific frozen natural spinors (Sec. 2.3, Eqs. 31-32), EA and EE.
  * ---------------------------------------------------------------------- */
 

@@ -118,6 +118,8 @@ def _load():
         "adc_state_density": (I, [P, P, P]),
         "adc_transition_density": (I, [P, P, I64, P]),
         "adc_excited_density": (I, [P, P, I64, P]),
+        "adc_cholesky": (I, [P, I64, D, I64, P, P, ctypes.POINTER(I64)]),
+        "adc_cholesky_mo": (I, [P, I64, I64, P, I64, P]),
         "adc_ssfns_density": (I, [P, P, D, P, P, ctypes.POINTER(I64), P, P]),
         "adc_fns_vector": (I, [P, P, P, I64, I64, P]),
         "adc_davidson_follow": (I, [P, P, D, I, I, ctypes.POINTER(D), P, ctypes.POINTER(D), P]),
@@ -561,6 +563,28 @@ def ssfns(B, eps_occ, eps_vir, kind="EA", order=3, x=1.0, nroots=1, eta_crit=1e-
                        ctypes.byref(o), out)
     _check(rc)
     return [r.as_dict() for r in out]
+
+
+def cholesky(V, tau, max_rank=None):
+    """Pivoted Cholesky vectors of the PSD matrix V [n][n] (``adc_cholesky``, Eq. 41): (L [rank][n], pivots)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    n = V.shape[0]
+    mr = n if max_rank is None else int(max_rank)
+    L = np.zeros((mr, n), dtype=np.float64)
+    piv = np.zeros(mr, dtype=np.int64)
+    r = ctypes.c_int64()
+    _check(lib.adc_cholesky(V.ctypes.data, n, float(tau), mr, L.ctypes.data, piv.ctypes.data, ctypes.byref(r)))
+    return L[:r.value].copy(), piv[:r.value].copy()
+
+
+def cholesky_mo(L, nao, C):
+    """Cholesky vectors in the spinor basis C [nao][nmo] (``adc_cholesky_mo``, Eq. 42): B [rank][nmo][nmo]."""
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    C = np.ascontiguousarray(C, dtype=np.complex128)
+    rank, nmo = L.shape[0], C.shape[1]
+    B = np.empty((rank, nmo, nmo), dtype=np.complex128)
+    _check(lib.adc_cholesky_mo(L.ctypes.data, rank, int(nao), C.ctypes.data, nmo, B.ctypes.data))
+    return B
 
 
 def diag_gemm(which, M, N, K, seed=1, reps=3):

@@ -442,6 +442,61 @@ int adc_excited_density(adc_ctx *c, const adc_c128 *Y, int64_t k, adc_c128 *rho)
   ADC_API_CATCH(c)
 }
 
+int adc_cholesky(const double *V, int64_t n, double tau, int64_t max_rank, double *L, int64_t *pivots,
+                 int64_t *rank) {
+  if (!V || !L || !rank || n < 1 || max_rank < 1 || !(tau >= 0.0)) return ADC_ERR_ARG;
+  Exec ex;
+  try {
+    ADC_CUDA(cudaStreamCreateWithFlags(&ex.stream, cudaStreamNonBlocking));
+    int64_t r = 0;
+    {
+      DevIn vin(ex, V, (size_t)n * n * sizeof(double));
+      DevOut lout(ex, L, (size_t)max_rank * n * sizeof(double));
+      fill_zero(ex, lout.p, lout.bytes);
+      r = cholesky_run(ex, (const double *)vin.p, n, tau, max_rank, (double *)lout.p, pivots);
+      lout.finish(ex);
+      ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    }
+    cudaStreamDestroy(ex.stream);
+    *rank = r;
+    return ADC_OK;
+  } catch (const adc::Error &e) {
+    if (ex.stream) { cudaStreamSynchronize(ex.stream); cudaStreamDestroy(ex.stream); }
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc &e) {
+    if (ex.stream) { cudaStreamSynchronize(ex.stream); cudaStreamDestroy(ex.stream); }
+    g_last_error = e.what();
+    return ADC_ERR_OOM;
+  }
+}
+
+int adc_cholesky_mo(const double *L, int64_t rank, int64_t nao, const adc_c128 *C, int64_t nmo, adc_c128 *B) {
+  if (!L || !C || !B || rank < 1 || nao < 1 || nmo < 1) return ADC_ERR_ARG;
+  Exec ex;
+  try {
+    ADC_CUDA(cudaStreamCreateWithFlags(&ex.stream, cudaStreamNonBlocking));
+    {
+      DevIn lin(ex, L, (size_t)rank * nao * nao * sizeof(double));
+      DevIn cin(ex, C, (size_t)nao * nmo * sizeof(cplx));
+      DevOut bout(ex, B, (size_t)rank * nmo * nmo * sizeof(cplx));
+      cholesky_mo(ex, (const double *)lin.p, rank, nao, (const cplx *)cin.p, nmo, (cplx *)bout.p);
+      bout.finish(ex);
+      ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    }
+    cudaStreamDestroy(ex.stream);
+    return ADC_OK;
+  } catch (const adc::Error &e) {
+    if (ex.stream) { cudaStreamSynchronize(ex.stream); cudaStreamDestroy(ex.stream); }
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc &e) {
+    if (ex.stream) { cudaStreamSynchronize(ex.stream); cudaStreamDestroy(ex.stream); }
+    g_last_error = e.what();
+    return ADC_ERR_OOM;
+  }
+}
+
 int adc_sigma_adjoint(adc_ctx *c, const adc_c128 *Y, const double *gomega, int64_t nroots, adc_c128 *gB,
                       double *geps_occ, double *geps_vir, double *gx) {
   if (!c) return ADC_ERR_STATE;

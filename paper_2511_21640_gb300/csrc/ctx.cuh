@@ -83,6 +83,11 @@ void to_fns_basis(adc_ctx *c, const cplx *y, const cplx *U, int64_t ldu, int64_t
 int64_t fns_dim(int kind, int64_t o, int64_t nk);
 // EE ground-to-excited transition densities rho [k][nmo][nmo] of the vectors Y [k][N] (properties.cu)
 void transition_density(adc_ctx *c, const cplx *Y, int64_t k, cplx *rho);
+// pivoted Cholesky of the PSD V [n][n] (device) into L [max_rank][n] (device); pivots (host) or null;
+// returns the rank (cholesky.cu)
+int64_t cholesky_run(Exec &ex, const double *V, int64_t n, double tau, int64_t max_rank, double *L, int64_t *pivots);
+// B[P] = C^H L^P C for real L [rank][nao][nao] and C [nao][nmo] (all device)
+void cholesky_mo(Exec &ex, const double *L, int64_t rank, int64_t nao, const cplx *C, int64_t nmo, cplx *B);
 // EE excited-state densities rho [k][nmo][nmo]: ground state to second order + zeroth-order ISR difference
 void excited_density(adc_ctx *c, const cplx *Y, int64_t k, cplx *rho);
 int ssfns_run(const adc_c128 *B, int64_t naux, const double *eps_occ, int64_t nocc, const double *eps_vir,
