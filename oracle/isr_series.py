@@ -35,7 +35,8 @@ import numpy as np
 import scipy.sparse as sp
 
 __all__ = ["FockSpace", "antisym_eri_dense", "rspt_ground_state", "isr_series",
-           "class_indices", "fci_energies", "mp1_density_bruteforce", "transition_moments_series"]
+           "class_indices", "fci_energies", "mp1_density_bruteforce", "transition_moments_series",
+           "spectroscopic_series"]
 
 
 def antisym_eri_dense(B):
@@ -393,3 +394,29 @@ def transition_moments_series(eps, B, nocc, nord=3):
             Epsi = np.stack([E @ psi0[n] for n in range(nord)])  # [nord, dim]
             f[:, :, p, q] = _sdot(states, Epsi[:, None, :])[:, :, 0]
     return f, r["n1"], r["labels"]
+
+
+def spectroscopic_series(eps, B, nocc, kind, nord=3):
+    """IP/EA transition moments f_I(p) = <Psi~_I| a_p |Psi0> (IP) or <Psi~_I| a+_p |Psi0> (EA).
+
+    Intermediate states of the (N-1)/(N+1) ISR (as in isr_series) and the
+    normalised N-electron ground state, both perturbation series; returns
+    f [nord, N, nmo] (class 1 first, labels as class_indices).
+    """
+    eps = np.asarray(eps, dtype=np.float64)
+    r = isr_series(eps, B, nocc, kind, nord=nord, want_states=True)
+    fs, nel, states = r["fs"], r["nel"], r["states"]
+    g = antisym_eri_dense(B)
+    secN = _Sector(fs, eps, g, nocc)
+    phi = fs.det_index(nocc, tuple(range(nocc)))
+    psi, _ = rspt_ground_state(secN, phi, nord)
+    nrm = _sdot(psi[:, None, :], psi[:, None, :])
+    psi0 = _scombine(psi[:, None, :], _inv_sqrt(nrm))[:, 0, :]
+    nmo = fs.nmo
+    f = np.zeros((nord, states.shape[1], nmo), dtype=np.complex128)
+    for p in range(nmo):
+        op = fs.ann(p, nocc) if kind == "IP" else fs.cre(p, nocc)
+        ops = np.stack([op @ psi0[n] for n in range(nord)])
+        f[:, :, p] = _sdot(states, ops[:, None, :])[:, :, 0]
+    return f, r["n1"], r["labels"]
+

@@ -40,15 +40,35 @@ weighted by the eigenvector), rho^K_pq = <a+_p a_q>:
                 rho_ef += sum_i conj(y_ie) y_if + 1/2 sum_ijc conj(Y_ijec) Y_ijfc,
                 rho_jb += sum_ia conj(y_ia) Y_ijab,  rho_bj += sum_ia conj(Y_ijab) y_ia
 (pinned against the same quantities in determinant space).
+
+Spectroscopic amplitudes of IP/EA states (the ISR transition moments of the
+one-particle operators a_p / a+_p), x_p = <Psi_n| a_p |Psi0> (IP) or
+<Psi_n| a+_p |Psi0> (EA) = sum_I conj(Y_In) f_I(p), main class through second
+and satellite class through first order (the same orders as the EE moments):
+
+  IP, main i:        f_i(k) = d_ik - 1/4 sum_jab conj(t_kj^ab) t_ij^ab,  f_i(b) = s2_i^b
+  IP, sat (i<j, a):  f(b) = t_ij^ab
+  EA, main a:        f_a(b) = d_ab - 1/4 sum_ijc conj(t_ij^bc) t_ij^ac,  f_a(k) = -s2_k^a
+  EA, sat (j, a<b):  f(k) = t_jk^ab
+
+so, with Y the satellite amplitudes as a full antisymmetric array,
+
+  IP  x_k = conj(y_k) - 1/4 sum_ijab conj(y_i) conj(t_kj^ab) t_ij^ab
+      x_b = sum_i conj(y_i) s2_i^b + 1/2 sum_ija conj(Y_ija) t_ij^ab
+  EA  x_b = conj(y_b) - 1/4 sum_aijc conj(y_a) conj(t_ij^bc) t_ij^ac
+      x_k = -sum_a conj(y_a) s2_k^a + 1/2 sum_jab conj(Y_jab) t_jk^ab
+(pinned against the brute-force (N-1)/(N+1)-electron ISR series).
 """
 from __future__ import annotations
 
 import numpy as np
 
+from . import adc as _ipea
 from . import adc_ee as _ee
 from .integrals import Amplitudes
 
-__all__ = ["singles_overlap2", "transition_density", "transition_moment", "excited_state_density"]
+__all__ = ["singles_overlap2", "transition_density", "transition_moment", "excited_state_density",
+           "spectroscopic_amplitudes"]
 
 
 def singles_overlap2(B, eps_occ, eps_vir, amp=None):
@@ -101,3 +121,24 @@ def excited_state_density(y, B, eps_occ, eps_vir, amp=None):
     rho[:o, o:] += np.einsum("ia,ijab->jb", y1.conj(), Y)
     rho[o:, :o] += np.einsum("ijab,ia->bj", Y.conj(), y1)
     return rho
+
+
+def spectroscopic_amplitudes(y, kind, B, eps_occ, eps_vir, amp=None):
+    """x [nmo] of one IP or EA vector y (packed main + satellite)."""
+    amp = amp if amp is not None else Amplitudes(B, eps_occ, eps_vir)
+    o, v = amp.nocc, amp.nvir
+    n1, _ = _ipea.dims(kind, o, v)
+    y = np.asarray(y, np.complex128).reshape(-1)
+    y1c = y[:n1].conj()
+    Yc = _ipea.unpack2(kind, y[n1:][None], o, v)[0].conj()
+    t, s2 = amp.t1, amp.t2s
+    x = np.zeros(o + v, np.complex128)
+    if kind == "IP":
+        x[:o] = y1c - 0.25 * np.einsum("i,kjab,ijab->k", y1c, t.conj(), t)
+        x[o:] = np.einsum("i,ib->b", y1c, s2) + 0.5 * np.einsum("ija,ijab->b", Yc, t)
+    elif kind == "EA":
+        x[o:] = y1c - 0.25 * np.einsum("a,ijbc,ijac->b", y1c, t.conj(), t)
+        x[:o] = -np.einsum("a,ka->k", y1c, s2) + 0.5 * np.einsum("jab,jkab->k", Yc, t)
+    else:
+        raise ValueError(kind)
+    return x

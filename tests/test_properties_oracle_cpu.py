@@ -19,7 +19,9 @@ from synthetic import make_problem
 from oracle import adc_ee
 from oracle import properties as oprop
 from oracle.integrals import Amplitudes
-from oracle.isr_series import _class_operator, class_indices, isr_series, transition_moments_series
+from oracle import adc as oadc
+from oracle.isr_series import (_class_operator, class_indices, isr_series, spectroscopic_series,
+                               transition_moments_series)
 
 
 def _unit(n, seed):
@@ -84,3 +86,63 @@ def test_excited_state_density_matches_determinant_space(o, v, Q, seed):
     assert np.abs(rho - rho.conj().T).max() < 1e-14
     assert abs(np.trace(rho).real - o) < 1e-12
 
+
+
+@pytest.mark.parametrize("kind", ["IP", "EA"])
+@pytest.mark.parametrize("o,v,Q,seed", [(2, 3, 4, 1), (3, 3, 5, 2), (3, 2, 4, 3)])
+def test_spectroscopic_amplitudes_match_isr_series(kind, o, v, Q, seed):
+    p = make_problem(o, v, Q, seed=seed, sigma=0.2, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    eps = np.concatenate([p.eps_occ, p.eps_vir])
+    f, n1, _ = spectroscopic_series(eps, p.B, o, kind, nord=3)
+    y = _unit(f.shape[1], seed + 10)
+    fb = f[0] + f[1] + f[2]
+    fb[n1:] = f[0, n1:] + f[1, n1:]  # satellites through first order
+    x_b = y.conj() @ fb
+    x = oprop.spectroscopic_amplitudes(y, kind, p.B, p.eps_occ, p.eps_vir)
+    assert np.abs(x - x_b).max() < 1e-14 * max(1.0, np.abs(x_b).max())
+    # the orders separately: zeroth is conj(y) on the main orbitals, first is
+    # the satellites' t contraction, nothing else
+    main = slice(0, o) if kind == "IP" else slice(o, o + v)
+    x0 = y.conj() @ f[0]
+    ref0 = np.zeros_like(x0)
+    ref0[main] = y[:n1].conj()
+    assert np.abs(x0 - ref0).max() < 1e-15
+    x1 = y.conj() @ f[1]
+    assert np.abs(x1[main]).max() < 1e-15
+    assert np.abs(x1).max() > 1e-3
+
+
+@pytest.mark.parametrize("kind", ["IP", "EA"])
+def test_spectroscopic_amplitudes_without_interaction(kind):
+    o, v = 3, 4
+    p = make_problem(o, v, 5, seed=6, sigma=0.2)
+    B0 = np.zeros_like(p.B)
+    n1, n2 = oadc.dims(kind, o, v)
+    y = _unit(n1 + n2, 7)
+    x = oprop.spectroscopic_amplitudes(y, kind, B0, p.eps_occ, p.eps_vir)
+    ref = np.zeros(o + v, np.complex128)
+    ref[slice(0, o) if kind == "IP" else slice(o, o + v)] = y[:n1].conj()
+    assert np.abs(x - ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("kind", ["IP", "EA"])
+def test_spectroscopic_strength_sum(kind):
+    """Through second order the pole strengths of all states of one class-1
+    orbital sum to its occupation (IP: <a+_k a_k>, EA: <a_b a+_b>) of the
+    second-order ground state: sum_n |x_p(n)|^2 over a complete set of
+    orthonormal y equals (f^H f)_pp, which the series evaluates by brute force."""
+    o, v, Q = 2, 3, 4
+    p = make_problem(o, v, Q, seed=8, sigma=0.2, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    n1, n2 = oadc.dims(kind, o, v)
+    Y = np.linalg.qr(np.random.default_rng(9).standard_normal((n1 + n2, n1 + n2))
+                     + 1j * np.random.default_rng(10).standard_normal((n1 + n2, n1 + n2)))[0].T
+    X = np.array([oprop.spectroscopic_amplitudes(y, kind, p.B, p.eps_occ, p.eps_vir) for y in Y])
+    amp = Amplitudes(p.B, p.eps_occ, p.eps_vir)
+    t = amp.t1
+    strength = np.sum(np.abs(X) ** 2, axis=0)
+    if kind == "IP":
+        occ2 = 1.0 - 0.5 * np.einsum("kjab,kjab->k", t.conj(), t).real  # 1 - n_k^(2) hole depletion
+        assert np.abs(strength[:o] - occ2).max() < 5e-3 * np.abs(1 - occ2).max() + 1e-12
+    else:
+        vir2 = 1.0 - 0.5 * np.einsum("ijbc,ijbc->b", t.conj(), t).real
+        assert np.abs(strength[o:] - vir2).max() < 5e-3 * np.abs(1 - vir2).max() + 1e-12
