@@ -249,6 +249,20 @@ int adc_transition_density(adc_ctx *ctx, const adc_c128 *Y, int64_t k, adc_c128 
  * values are sum_pq d_pq rho_pq. EE contexts only. Synchronous. */
 int adc_excited_density(adc_ctx *ctx, const adc_c128 *Y, int64_t k, adc_c128 *rho);
 
+/* Spectroscopic amplitudes of IP/EA-ADC states (Sec. 2.2, the ISR transition
+ * moments of a_p and a+_p): x_p = <Psi_n| a_p |Psi0> (IP) or
+ * <Psi_n| a+_p |Psi0> (EA) = sum_I conj(Y_I) f_I(p), main class through
+ * second and satellites through first order (t: first-order doubles, s2:
+ * second-order singles, Y the satellites as a full antisymmetric array):
+ *   IP  x_k = conj(y_k) - 1/4 sum_ijab conj(y_i) conj(t_kj^ab) t_ij^ab,
+ *       x_b = sum_i conj(y_i) s2_i^b + 1/2 sum_ija conj(Y_ija) t_ij^ab
+ *   EA  x_b = conj(y_b) - 1/4 sum_aijc conj(y_a) conj(t_ij^bc) t_ij^ac,
+ *       x_k = -sum_a conj(y_a) s2_k^a + 1/2 sum_jab conj(Y_jab) t_jk^ab
+ * Pole strengths are |x_p|^2. Y [k][N], x [k][nmo] (orbitals in the order of
+ * B, occupied first); host or device. IP and EA contexts only
+ * (ADC_ERR_UNSUPPORTED otherwise). Synchronous. */
+int adc_spectroscopic_amplitudes(adc_ctx *ctx, const adc_c128 *Y, int64_t k, adc_c128 *x);
+
 /* ------------------------------------------------------------------------
  * Cholesky vectors from two-electron integrals (Sec. 2.5, Eqs. 41-42).
  * ---------------------------------------------------------------------- */

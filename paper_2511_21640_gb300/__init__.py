@@ -118,6 +118,7 @@ def _load():
         "adc_state_density": (I, [P, P, P]),
         "adc_transition_density": (I, [P, P, I64, P]),
         "adc_excited_density": (I, [P, P, I64, P]),
+        "adc_spectroscopic_amplitudes": (I, [P, P, I64, P]),
         "adc_cholesky": (I, [P, I64, D, I64, P, P, ctypes.POINTER(I64)]),
         "adc_cholesky_mo": (I, [P, I64, I64, P, I64, P]),
         "adc_ssfns_density": (I, [P, P, D, P, P, ctypes.POINTER(I64), P, P]),
@@ -352,6 +353,14 @@ class Context:
         _check(lib.adc_excited_density(self._h, _ptr(Y, np.complex128), Y.shape[0], _ptr(rho, np.complex128)),
                self._h)
         return rho
+
+    def spectroscopic_amplitudes(self, Y):
+        """Spectroscopic amplitudes [k][nmo] of IP/EA vectors Y [k][N] (``adc_spectroscopic_amplitudes``)."""
+        Y = np.ascontiguousarray(np.atleast_2d(Y), dtype=np.complex128)
+        x = np.empty((Y.shape[0], self.nocc + self.nvir), dtype=np.complex128)
+        _check(lib.adc_spectroscopic_amplitudes(self._h, _ptr(Y, np.complex128), Y.shape[0],
+                                                _ptr(x, np.complex128)), self._h)
+        return x
 
     def state_density(self, y):
         """Virtual density of the configurations weighted by y (``adc_state_density``, Eq. 31)."""

@@ -428,6 +428,20 @@ int adc_transition_density(adc_ctx *c, const adc_c128 *Y, int64_t k, adc_c128 *r
   ADC_API_CATCH(c)
 }
 
+int adc_spectroscopic_amplitudes(adc_ctx *c, const adc_c128 *Y, int64_t k, adc_c128 *x) {
+  if (!c) return ADC_ERR_STATE;
+  if (!Y || !x || k < 1) return ADC_ERR_ARG;
+  if (c->kind != ADC_IP && c->kind != ADC_EA) return ADC_ERR_UNSUPPORTED;
+  ADC_API_TRY
+  DevIn yin(c->ex, Y, (size_t)k * c->N * sizeof(cplx));
+  DevOut xout(c->ex, x, (size_t)k * c->nmo * sizeof(cplx));
+  spectroscopic_amplitudes(c, (const cplx *)yin.p, k, (cplx *)xout.p);
+  xout.finish(c->ex);
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
 int adc_excited_density(adc_ctx *c, const adc_c128 *Y, int64_t k, adc_c128 *rho) {
   if (!c) return ADC_ERR_STATE;
   if (!Y || !rho || k < 1) return ADC_ERR_ARG;

@@ -64,6 +64,8 @@ void first_order_amplitudes(adc_ctx *c);
 // second-order doubles and singles, packed <ab||cd> and the ladder intermediate
 // Lad_ij^ab = 1/2 sum_cd <ab||cd> t_ij^cd (needs c->t1 and c->W)
 void second_order_amplitudes(adc_ctx *c, DBuf &G_vv, DBuf &Lad, DBuf &t2d, DBuf &t2s);
+// the second-order singles t2_i^a alone (needs c->t1)
+DBuf second_order_singles(adc_ctx *c);
 void setup_ee(adc_ctx *c);
 // block Davidson for the lowest nroots roots (davidson.cu); with follow, one
 // root: the Ritz vector with the largest overlap with the (single) guess at
@@ -90,6 +92,8 @@ int64_t cholesky_run(Exec &ex, const double *V, int64_t n, double tau, int64_t m
 void cholesky_mo(Exec &ex, const double *L, int64_t rank, int64_t nao, const cplx *C, int64_t nmo, cplx *B);
 // EE excited-state densities rho [k][nmo][nmo]: ground state to second order + zeroth-order ISR difference
 void excited_density(adc_ctx *c, const cplx *Y, int64_t k, cplx *rho);
+// IP/EA spectroscopic amplitudes x [k][nmo] of the vectors Y [k][N] (properties.cu)
+void spectroscopic_amplitudes(adc_ctx *c, const cplx *Y, int64_t k, cplx *x);
 int ssfns_run(const adc_c128 *B, int64_t naux, const double *eps_occ, int64_t nocc, const double *eps_vir,
               int64_t nvir, int kind, int order, double x, int nroots, double eta_crit, double tol, int max_iter,
               int precision, const adc_opts *opts, adc_ssfns_root *out);

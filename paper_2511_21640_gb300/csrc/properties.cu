@@ -20,6 +20,15 @@
 //   rho_kl += -sum_a conj(y_la) y_ka - 1/2 sum_jab conj(Y_ljab) Y_kjab,
 //   rho_ef += sum_i conj(y_ie) y_if + 1/2 sum_ijc conj(Y_ijec) Y_ijfc,
 //   rho_jb += sum_ia conj(y_ia) Y_ijab,  rho_bj += sum_ia conj(Y_ijab) y_ia.
+//
+// Spectroscopic amplitudes of IP/EA states, x_p = <Psi_n| a_p |Psi0> (IP) or
+// <Psi_n| a+_p |Psi0> (EA) = sum_I conj(Y_I) f_I(p), main class through
+// second and satellites through first order (Y the satellites as a full
+// antisymmetric array, H the second-order hole / particle density pieces):
+//   IP  x_k = conj(y_k) - 1/4 sum_i conj(y_i) H_ik,  H_ik = sum_jab t_ij^ab conj(t_kj^ab)
+//       x_b = sum_i conj(y_i) s2_i^b + 1/2 sum_ija conj(Y_ija) t_ij^ab
+//   EA  x_b = conj(y_b) - 1/4 sum_a conj(y_a) H_ab,  H_ab = sum_ijc t_ij^ac conj(t_ij^bc)
+//       x_k = -sum_a conj(y_a) s2_k^a + 1/2 sum_jab conj(Y_jab) t_jk^ab
 #include <vector>
 
 #include "ctx.cuh"
@@ -35,6 +44,17 @@ __global__ void k_put_block(const cplx *__restrict__ src, int64_t rows, int64_t 
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = idx / cols, cc = idx - r * cols;
     dst[(r0 + r) * ld + c0 + cc] = src[idx];
+  }
+}
+
+// dst[r * ld + c0 + c] = conj(src[r * lds + c]), r < rows, c < cols
+__global__ void k_put_conj(const cplx *__restrict__ src, int64_t lds, int64_t rows, int64_t cols, cplx *dst,
+                           int64_t ld, int64_t c0) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < rows * cols;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / cols, cc = idx - r * cols;
+    const cplx a = src[r * lds + cc];
+    dst[r * ld + c0 + cc] = cmake(a.x, -a.y);
   }
 }
 }  // namespace
@@ -143,6 +163,42 @@ void excited_density(adc_ctx *c, const cplx *Y, int64_t k, cplx *rho) {
     k_put_block<<<grid1d(o * v, 256), 256, 0, ex.stream>>>(Bov.c(), o, v, R, nmo, 0, o);
     k_put_block<<<grid1d(v * o, 256), 256, 0, ex.stream>>>(Bvo.c(), v, o, R, nmo, o, 0);
     ADC_CHECK_LAUNCH();
+  }
+  ADC_CUDA(cudaStreamSynchronize(ex.stream));
+}
+
+void spectroscopic_amplitudes(adc_ctx *c, const cplx *Y, int64_t k, cplx *x) {
+  ADC_REQUIRE(c->kind == ADC_IP || c->kind == ADC_EA, ADC_ERR_UNSUPPORTED, "spectroscopic amplitudes: IP/EA-ADC");
+  Exec &ex = c->ex;
+  const bool ea = (c->kind == ADC_EA);
+  const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N, nmo = c->nmo;
+  const int64_t pv = npairs(v);
+  TagScope tg(ex, "properties");
+  DBuf s2b = second_order_singles(c);
+  const TV t1 = TV::dense(c->t1.c(), {o, o, v, v}), s2 = TV::dense(s2b.c(), {o, v});
+  const TV y1c(const_cast<cplx *>(Y), {k, n1}, {N, 1}, true);
+  const TV xo(x, {k, o}, {nmo, 1}), xv(x + o, {k, v}, {nmo, 1});
+  const std::vector<int64_t> ef = ea ? std::vector<int64_t>{k, o, v, v} : std::vector<int64_t>{k, o, o, v};
+  DBuf Y2f = cbuf(ex, ef[0] * ef[1] * ef[2] * ef[3]);
+  if (n2 == 0) fill_zero(ex, Y2f.p, Y2f.bytes);
+  else if (ea) pair_unpack(ex, Y + n1, k, o, N, pv, v, 1, Y2f.c());
+  else pair_unpack(ex, Y + n1, k, 1, N, 0, o, v, Y2f.c());
+  const TV Y2c = TV::dense(Y2f.c(), ef).cj();
+  // the main orbitals: conj(y) at zeroth order
+  k_put_conj<<<grid1d(k * n1, 256), 256, 0, ex.stream>>>(Y, N, k, n1, x, nmo, ea ? o : 0);
+  ADC_CHECK_LAUNCH();
+  if (!ea) {
+    DBuf H = cbuf(ex, o * o);
+    einsum(ex, C1(), t1, "ijab", t1.cj(), "kjab", C0(), TV::dense(H.c(), {o, o}), "ik");
+    einsum(ex, CR(-0.25), y1c, "zi", TV::dense(H.c(), {o, o}), "ik", C1(), xo, "zk");
+    einsum(ex, C1(), y1c, "zi", s2, "ib", C0(), xv, "zb");
+    einsum(ex, CR(0.5), Y2c, "zija", t1, "ijab", C1(), xv, "zb");
+  } else {
+    DBuf H = cbuf(ex, v * v);
+    einsum(ex, C1(), t1, "ijac", t1.cj(), "ijbc", C0(), TV::dense(H.c(), {v, v}), "ab");
+    einsum(ex, CR(-0.25), y1c, "za", TV::dense(H.c(), {v, v}), "ab", C1(), xv, "zb");
+    einsum(ex, CR(-1.0), y1c, "za", s2, "ka", C0(), xo, "zk");
+    einsum(ex, CR(0.5), Y2c, "zjab", t1, "jkab", C1(), xo, "zk");
   }
   ADC_CUDA(cudaStreamSynchronize(ex.stream));
 }

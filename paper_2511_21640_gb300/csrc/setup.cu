@@ -197,18 +197,26 @@ void second_order_amplitudes(adc_ctx *c, DBuf &G_vv, DBuf &Lad_b, DBuf &t2d_b, D
     }
     denom2_div(ex, t2d_b.c(), eo, ev, o, v);
 
-    // t2_i^a (eps_i - eps_a) = 1/2 sum_jcd <aj||cd> t_ij^cd - 1/2 sum_jkc <jk||ic> t_jk^ac
-    t2s_b = cbuf(ex, o * v);
-    TV t2s = dense(t2s_b, {o, v});
-    {
-      DBuf Y = cbuf(ex, Q * o * v);
-      einsum(ex, C1(), Bov, "Qjd", t1, "ijcd", C0(), dense(Y, {Q, o, v}), "Qic");
-      einsum(ex, C1(), Bvv, "Qac", dense(Y, {Q, o, v}), "Qic", C0(), t2s, "ia");
-      DBuf ooov = eri(c, "ooov");
-      einsum(ex, CR(-0.5), dense(ooov, {o, o, o, v}), "jkic", t1, "jkac", C1(), t2s, "ia");
-    }
-    denom1_div(ex, t2s_b.c(), eo, ev, o, v);
+    t2s_b = second_order_singles(c);
+}
 
+DBuf second_order_singles(adc_ctx *c) {
+  Exec &ex = c->ex;
+  const int64_t o = c->o, v = c->v, Q = c->Q;
+  TV Bov = Bview(c, 'o', 'v'), Bvv = Bview(c, 'v', 'v');
+  TV t1 = dense(c->t1, {o, o, v, v});
+  // t2_i^a (eps_i - eps_a) = 1/2 sum_jcd <aj||cd> t_ij^cd - 1/2 sum_jkc <jk||ic> t_jk^ac
+  DBuf t2s_b = cbuf(ex, o * v);
+  TV t2s = dense(t2s_b, {o, v});
+  {
+    DBuf Y = cbuf(ex, Q * o * v);
+    einsum(ex, C1(), Bov, "Qjd", t1, "ijcd", C0(), dense(Y, {Q, o, v}), "Qic");
+    einsum(ex, C1(), Bvv, "Qac", dense(Y, {Q, o, v}), "Qic", C0(), t2s, "ia");
+    DBuf ooov = eri(c, "ooov");
+    einsum(ex, CR(-0.5), dense(ooov, {o, o, o, v}), "jkic", t1, "jkac", C1(), t2s, "ia");
+  }
+  denom1_div(ex, t2s_b.c(), c->eo.d(), c->ev.d(), o, v);
+  return t2s_b;
 }
 
 void setup_operators(adc_ctx *c) {

@@ -1,5 +1,6 @@
-"""EE ground-to-excited transition densities (adc_transition_density) and
-excited-state densities (adc_excited_density) on the GPU (Sec. 2.2) against the
+"""EE ground-to-excited transition densities (adc_transition_density),
+excited-state densities (adc_excited_density) and IP/EA spectroscopic
+amplitudes (adc_spectroscopic_amplitudes) on the GPU (Sec. 2.2) against the
 oracle: the closed forms of oracle/properties.py (1e-12 relative, ADC(2) and
 ADC(3) contexts) and, on a tiny case, the brute-force ISR transition moments in
 determinant space directly (1e-12).
@@ -12,7 +13,8 @@ pytestmark = pytest.mark.gpu
 
 from synthetic import make_problem  # noqa: E402
 from oracle import properties as oprop  # noqa: E402
-from oracle.isr_series import transition_moments_series  # noqa: E402
+from oracle.integrals import Amplitudes  # noqa: E402
+from oracle.isr_series import spectroscopic_series, transition_moments_series  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -64,4 +66,40 @@ def test_transition_density_rejects_ip(gpu):
     with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP", order=2) as c:
         with pytest.raises(gpu.AdcError) as e:
             c.transition_density(np.zeros((1, c.N), np.complex128))
+        assert e.value.code == -6
+
+
+@pytest.mark.parametrize("kind,o,v,Q,order,x,seed", [("IP", 4, 9, 14, 2, 0.0, 81), ("EA", 4, 9, 14, 3, 0.5, 82),
+                                                     ("IP", 12, 40, 60, 3, 1.0, 83), ("EA", 7, 33, 50, 2, 0.0, 84),
+                                                     ("IP", 2, 5, 6, 3, 0.5, 85)])
+def test_spectroscopic_amplitudes_match_oracle(gpu, kind, o, v, Q, order, x, seed):
+    p = make_problem(o, v, Q, seed=seed, sigma=0.12, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=order, x=x) as c:
+        Y = _vectors(c.N, 3, seed + 1)
+        X = c.spectroscopic_amplitudes(Y)
+    amp = Amplitudes(p.B, p.eps_occ, p.eps_vir)
+    for z in range(3):
+        ref = oprop.spectroscopic_amplitudes(Y[z], kind, p.B, p.eps_occ, p.eps_vir, amp=amp)
+        assert np.abs(X[z] - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("kind", ["IP", "EA"])
+def test_spectroscopic_amplitudes_match_isr_series(gpu, kind):
+    o, v, Q = 2, 3, 4
+    p = make_problem(o, v, Q, seed=1, sigma=0.2, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    eps = np.concatenate([p.eps_occ, p.eps_vir])
+    f, n1, _ = spectroscopic_series(eps, p.B, o, kind, nord=3)
+    fb = f[0] + f[1] + f[2]
+    fb[n1:] = f[0, n1:] + f[1, n1:]
+    Y = _vectors(f.shape[1], 1, 3)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=2) as c:
+        X = c.spectroscopic_amplitudes(Y)[0]
+    assert np.abs(X - Y[0].conj() @ fb).max() < 1e-12
+
+
+def test_spectroscopic_amplitudes_reject_ee(gpu):
+    p = make_problem(3, 4, 6, seed=3, sigma=0.1)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=2) as c:
+        with pytest.raises(gpu.AdcError) as e:
+            c.spectroscopic_amplitudes(np.zeros((1, c.N), np.complex128))
         assert e.value.code == -6
