@@ -58,6 +58,23 @@ so, with Y the satellite amplitudes as a full antisymmetric array,
   EA  x_b = conj(y_b) - 1/4 sum_aijc conj(y_a) conj(t_ij^bc) t_ij^ac
       x_k = -sum_a conj(y_a) s2_k^a + 1/2 sum_jab conj(Y_jab) t_jk^ab
 (pinned against the brute-force (N-1)/(N+1)-electron ISR series).
+
+State and state-to-state one-particle densities of all three kinds at the
+level of the excited-state density above, rho^KL_pq = <Psi_K| a+_p a_q |Psi_L>
+= (y_K^H y_L) rho0_pq + (the configurations' difference density between K and
+L), with the configuration blocks (K on the bra, L on the ket, Y the class-2
+amplitudes as a full antisymmetric array):
+
+  EE  kl: -sum_a conj(yK_la) yL_ka - 1/2 sum_jab conj(YK_ljab) YL_kjab
+      ef:  sum_i conj(yK_ie) yL_if + 1/2 sum_ijc conj(YK_ijec) YL_ijfc
+      jb:  sum_ia conj(yK_ia) YL_ijab,   bj: sum_ia conj(YK_ijab) yL_ia
+  IP  kl: -conj(yK_l) yL_k - sum_ja conj(YK_lja) YL_kja
+      ab:  1/2 sum_ij conj(YK_ija) YL_ijb
+      jb: -sum_i conj(yK_i) YL_ijb,      bj: -sum_i conj(YK_ijb) yL_i
+  EA  kl: -1/2 sum_ab conj(YK_lab) YL_kab
+      ab:  conj(yK_a) yL_b + sum_jc conj(YK_jac) YL_jbc
+      jb:  sum_a conj(yK_a) YL_jab,      bj: sum_a conj(YK_jab) yL_a
+(pinned against the same matrix elements in determinant space).
 """
 from __future__ import annotations
 
@@ -68,7 +85,7 @@ from . import adc_ee as _ee
 from .integrals import Amplitudes
 
 __all__ = ["singles_overlap2", "transition_density", "transition_moment", "excited_state_density",
-           "spectroscopic_amplitudes"]
+           "spectroscopic_amplitudes", "ground_state_density", "state_pair_density"]
 
 
 def singles_overlap2(B, eps_occ, eps_vir, amp=None):
@@ -142,3 +159,54 @@ def spectroscopic_amplitudes(y, kind, B, eps_occ, eps_vir, amp=None):
     else:
         raise ValueError(kind)
     return x
+
+
+def ground_state_density(amp):
+    """rho0 [nmo][nmo]: the MP ground-state density through second order."""
+    o, v = amp.nocc, amp.nvir
+    t, s2 = amp.t1, amp.t2s
+    rho = np.zeros((o + v, o + v), np.complex128)
+    rho[:o, :o] = np.eye(o) - 0.5 * np.einsum("jkab,ikab->ij", t.conj(), t)
+    rho[o:, o:] = 0.5 * np.einsum("ijac,ijbc->ab", t.conj(), t)
+    rho[:o, o:] = s2
+    rho[o:, :o] = s2.conj().T
+    return rho
+
+
+def _classes(kind, y, o, v):
+    if kind == "EE":
+        n1 = o * v
+        return y[:n1].reshape(o, v), _ee.unpack2(y[n1:][None], o, v)[0]
+    n1, _ = _ipea.dims(kind, o, v)
+    return y[:n1], _ipea.unpack2(kind, y[n1:][None], o, v)[0]
+
+
+def state_pair_density(yK, yL, kind, B, eps_occ, eps_vir, amp=None):
+    """rho^KL [nmo][nmo] = <Psi_K| a+_p a_q |Psi_L> of two vectors of one kind."""
+    amp = amp if amp is not None else Amplitudes(B, eps_occ, eps_vir)
+    o, v = amp.nocc, amp.nvir
+    yK = np.asarray(yK, np.complex128).reshape(-1)
+    yL = np.asarray(yL, np.complex128).reshape(-1)
+    aK, YK = _classes(kind, yK, o, v)
+    aL, YL = _classes(kind, yL, o, v)
+    aKc, YKc = aK.conj(), YK.conj()
+    e = np.einsum
+    d = np.zeros((o + v, o + v), np.complex128)
+    if kind == "EE":
+        d[:o, :o] = -e("la,ka->kl", aKc, aL) - 0.5 * e("ljab,kjab->kl", YKc, YL)
+        d[o:, o:] = e("ie,if->ef", aKc, aL) + 0.5 * e("ijec,ijfc->ef", YKc, YL)
+        d[:o, o:] = e("ia,ijab->jb", aKc, YL)
+        d[o:, :o] = e("ijab,ia->bj", YKc, aL)
+    elif kind == "IP":
+        d[:o, :o] = -e("l,k->kl", aKc, aL) - e("lja,kja->kl", YKc, YL)
+        d[o:, o:] = 0.5 * e("ija,ijb->ab", YKc, YL)
+        d[:o, o:] = -e("i,ijb->jb", aKc, YL)
+        d[o:, :o] = -e("ijb,i->bj", YKc, aL)
+    elif kind == "EA":
+        d[:o, :o] = -0.5 * e("lab,kab->kl", YKc, YL)
+        d[o:, o:] = e("a,b->ab", aKc, aL) + e("jac,jbc->ab", YKc, YL)
+        d[:o, o:] = e("a,jab->jb", aKc, YL)
+        d[o:, :o] = e("jab,a->bj", YKc, aL)
+    else:
+        raise ValueError(kind)
+    return np.vdot(yK, yL) * ground_state_density(amp) + d

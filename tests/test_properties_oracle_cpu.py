@@ -146,3 +146,75 @@ def test_spectroscopic_strength_sum(kind):
     else:
         vir2 = 1.0 - 0.5 * np.einsum("ijbc,ijbc->b", t.conj(), t).real
         assert np.abs(strength[o:] - vir2).max() < 5e-3 * np.abs(1 - vir2).max() + 1e-12
+
+
+def _ground_series_density(eps, B, o, nord=3):
+    """sum_{n+m<nord} <psi0^(n)| a+_p a_q |psi0^(m)> of the normalised MP ground state."""
+    from oracle.isr_series import (_Sector, _build_space, _inv_sqrt, _scombine, _sdot, antisym_eri_dense,
+                                   rspt_ground_state)
+    g = antisym_eri_dense(B)
+    fs = _build_space(eps, g, o)
+    secN = _Sector(fs, eps, g, o)
+    psi, _ = rspt_ground_state(secN, fs.det_index(o, tuple(range(o))), nord)
+    psi0 = _scombine(psi[:, None, :], _inv_sqrt(_sdot(psi[:, None, :], psi[:, None, :])))[:, 0, :]
+    nmo = eps.shape[0]
+    r = np.zeros((nmo, nmo), np.complex128)
+    for p_ in range(nmo):
+        for q in range(nmo):
+            E = fs.excitation(p_, q, o)
+            r[p_, q] = sum(np.vdot(psi0[n], E @ psi0[m]) for n in range(nord) for m in range(nord - n))
+    return r, fs
+
+
+@pytest.mark.parametrize("kind", ["IP", "EA", "EE"])
+@pytest.mark.parametrize("o,v,Q,seed", [(2, 3, 4, 11), (3, 3, 5, 12)])
+def test_state_pair_density_matches_determinant_space(kind, o, v, Q, seed):
+    """<Psi_K|a+_p a_q|Psi_L> with Psi = the configurations weighted by y in the
+    target sector, minus (y_K^H y_L) times the reference density, plus
+    (y_K^H y_L) times the ground-state density series: every block, K != L."""
+    p = make_problem(o, v, Q, seed=seed, sigma=0.2, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    eps = np.concatenate([p.eps_occ, p.eps_vir])
+    rho0, fs = _ground_series_density(eps, p.B, o)
+    amp = Amplitudes(p.B, p.eps_occ, p.eps_vir)
+    assert np.abs(oprop.ground_state_density(amp) - rho0).max() < 1e-13
+    ref = np.zeros(fs.dim(o), np.complex128)
+    ref[fs.det_index(o, tuple(range(o)))] = 1.0
+    labels = class_indices(kind, o, v)
+    Phi = np.array([_class_operator(fs, kind, c, lab, o) @ ref for c in range(2) for lab in labels[c]])
+    nel = {"IP": o - 1, "EA": o + 1, "EE": o}[kind]
+    rng = np.random.default_rng(seed)
+    yK = rng.standard_normal(Phi.shape[0]) + 1j * rng.standard_normal(Phi.shape[0])
+    yL = rng.standard_normal(Phi.shape[0]) + 1j * rng.standard_normal(Phi.shape[0])
+    pK, pL = yK @ Phi, yL @ Phi
+    s = np.vdot(yK, yL)
+    nmo = o + v
+    rho_b = np.zeros((nmo, nmo), np.complex128)
+    for p_ in range(nmo):
+        for q in range(nmo):
+            E = fs.excitation(p_, q, nel)
+            rho_b[p_, q] = np.vdot(pK, E @ pL) - (s if (p_ == q and p_ < o) else 0.0)
+    rho_b += s * rho0
+    rho = oprop.state_pair_density(yK, yL, kind, p.B, p.eps_occ, p.eps_vir, amp=amp)
+    assert np.abs(rho - rho_b).max() < 1e-13 * max(1.0, np.abs(rho_b).max())
+    # rho^LK = (rho^KL)^H
+    rho_lk = oprop.state_pair_density(yL, yK, kind, p.B, p.eps_occ, p.eps_vir, amp=amp)
+    assert np.abs(rho_lk - rho.conj().T).max() < 1e-14 * np.abs(rho).max()
+
+
+@pytest.mark.parametrize("kind,dn", [("IP", -1), ("EA", 1), ("EE", 0)])
+def test_state_pair_density_traces(kind, dn):
+    """Normalised state: trace = electrons of the target sector, Hermitian,
+    equal to the EE excited-state density for EE; orthogonal pair: trace 0."""
+    o, v, Q = 3, 5, 7
+    p = make_problem(o, v, Q, seed=21, sigma=0.15, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    amp = Amplitudes(p.B, p.eps_occ, p.eps_vir)
+    n = o * v + adc_ee.dims(o, v)[1] if kind == "EE" else sum(oadc.dims(kind, o, v))
+    Yq = np.linalg.qr(np.random.default_rng(22).standard_normal((n, 2))
+                      + 1j * np.random.default_rng(23).standard_normal((n, 2)))[0].T
+    r = oprop.state_pair_density(Yq[0], Yq[0], kind, p.B, p.eps_occ, p.eps_vir, amp=amp)
+    assert abs(np.trace(r) - (o + dn)) < 1e-12
+    assert np.abs(r - r.conj().T).max() < 1e-14
+    r01 = oprop.state_pair_density(Yq[0], Yq[1], kind, p.B, p.eps_occ, p.eps_vir, amp=amp)
+    assert abs(np.trace(r01)) < 1e-12
+    if kind == "EE":
+        assert np.abs(r - oprop.excited_state_density(Yq[0], p.B, p.eps_occ, p.eps_vir, amp=amp)).max() < 1e-15
