@@ -236,18 +236,30 @@ int adc_fns_transform(adc_ctx *ctx, const adc_c128 *U, int64_t ldu,
  * (ADC_ERR_UNSUPPORTED otherwise). Synchronous. */
 int adc_transition_density(adc_ctx *ctx, const adc_c128 *Y, int64_t k, adc_c128 *rho);
 
-/* Excited-state one-particle densities of EE-ADC states (Sec. 2.2), at the
- * level stated for ADC(2) states: rho^K_pq = <a+_p a_q> = rho0_pq (the MP
- * ground-state density through second order: rho0_ij = d_ij - 1/2 sum_kab
- * conj(t_jk^ab) t_ik^ab, rho0_ab = 1/2 sum_ijc conj(t_ij^ac) t_ij^bc, rho0_jb =
- * s2_j^b, rho0_bj = conj(s2_j^b)) plus Y^H G Y with G the zeroth-order
- * intermediate-state representation of a+_p a_q - rho0 (the configurations):
- *   rho_kl += -sum_a conj(y_la) y_ka - 1/2 sum_jab conj(Y_ljab) Y_kjab,
- *   rho_ef += sum_i conj(y_ie) y_if + 1/2 sum_ijc conj(Y_ijec) Y_ijfc,
- *   rho_jb += sum_ia conj(y_ia) Y_ijab,  rho_bj += sum_ia conj(Y_ijab) y_ia.
- * Y [k][N] normalised vectors, rho [k][nmo][nmo]; host or device. Expectation
- * values are sum_pq d_pq rho_pq. EE contexts only. Synchronous. */
+/* One-particle densities of ADC states of any kind (Sec. 2.2), at the level
+ * stated for ADC(2) states: rho^KL_pq = <Psi_K| a+_p a_q |Psi_L> =
+ * (y_K^H y_L) rho0_pq + y_K^H G y_L, with rho0 the MP ground-state density
+ * through second order (rho0_ij = d_ij - 1/2 sum_kab conj(t_jk^ab) t_ik^ab,
+ * rho0_ab = 1/2 sum_ijc conj(t_ij^ac) t_ij^bc, rho0_jb = s2_j^b, rho0_bj =
+ * conj(s2_j^b)) and G the zeroth-order intermediate-state representation of
+ * a+_p a_q - rho0 (the configurations; Y the class-2 amplitudes as a full
+ * antisymmetric array):
+ *   EE  kl: -sum_a conj(yK_la) yL_ka - 1/2 sum_jab conj(YK_ljab) YL_kjab
+ *       ef:  sum_i conj(yK_ie) yL_if + 1/2 sum_ijc conj(YK_ijec) YL_ijfc
+ *       jb:  sum_ia conj(yK_ia) YL_ijab,   bj: sum_ia conj(YK_ijab) yL_ia
+ *   IP  kl: -conj(yK_l) yL_k - sum_ja conj(YK_lja) YL_kja
+ *       ab:  1/2 sum_ij conj(YK_ija) YL_ijb
+ *       jb: -sum_i conj(yK_i) YL_ijb,      bj: -sum_i conj(YK_ijb) yL_i
+ *   EA  kl: -1/2 sum_ab conj(YK_lab) YL_kab
+ *       ab:  conj(yK_a) yL_b + sum_jc conj(YK_jac) YL_jbc
+ *       jb:  sum_a conj(yK_a) YL_jab,      bj: sum_a conj(YK_jab) yL_a
+ * adc_excited_density: the state densities rho^KK of the vectors Y [k][N]
+ * (trace = electrons of the state for normalised y). adc_state_pair_density:
+ * the state-to-state densities of the pairs (YK[z], YL[z]), z < k, YK and YL
+ * [k][N]. rho [k][nmo][nmo]; all host or device. Expectation values and
+ * state-to-state transition moments are sum_pq d_pq rho_pq. Synchronous. */
 int adc_excited_density(adc_ctx *ctx, const adc_c128 *Y, int64_t k, adc_c128 *rho);
+int adc_state_pair_density(adc_ctx *ctx, const adc_c128 *YK, const adc_c128 *YL, int64_t k, adc_c128 *rho);
 
 /* Spectroscopic amplitudes of IP/EA-ADC states (Sec. 2.2, the ISR transition
  * moments of a_p and a+_p): x_p = <Psi_n| a_p |Psi0> (IP) or

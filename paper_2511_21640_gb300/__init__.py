@@ -119,6 +119,7 @@ def _load():
         "adc_transition_density": (I, [P, P, I64, P]),
         "adc_excited_density": (I, [P, P, I64, P]),
         "adc_spectroscopic_amplitudes": (I, [P, P, I64, P]),
+        "adc_state_pair_density": (I, [P, P, P, I64, P]),
         "adc_cholesky": (I, [P, I64, D, I64, P, P, ctypes.POINTER(I64)]),
         "adc_cholesky_mo": (I, [P, I64, I64, P, I64, P]),
         "adc_ssfns_density": (I, [P, P, D, P, P, ctypes.POINTER(I64), P, P]),
@@ -346,12 +347,24 @@ class Context:
         return rho
 
     def excited_density(self, Y):
-        """Excited-state densities [k][nmo][nmo] of EE vectors Y [k][N] (``adc_excited_density``)."""
+        """State densities [k][nmo][nmo] of the vectors Y [k][N], any kind (``adc_excited_density``)."""
         Y = np.ascontiguousarray(np.atleast_2d(Y), dtype=np.complex128)
         nmo = self.nocc + self.nvir
         rho = np.empty((Y.shape[0], nmo, nmo), dtype=np.complex128)
         _check(lib.adc_excited_density(self._h, _ptr(Y, np.complex128), Y.shape[0], _ptr(rho, np.complex128)),
                self._h)
+        return rho
+
+    def state_pair_density(self, YK, YL):
+        """<Psi_K|a+_p a_q|Psi_L> [k][nmo][nmo] of the pairs (YK[z], YL[z]) (``adc_state_pair_density``)."""
+        YK = np.ascontiguousarray(np.atleast_2d(YK), dtype=np.complex128)
+        YL = np.ascontiguousarray(np.atleast_2d(YL), dtype=np.complex128)
+        if YK.shape != YL.shape:
+            raise ValueError("YK and YL must have the same shape")
+        nmo = self.nocc + self.nvir
+        rho = np.empty((YK.shape[0], nmo, nmo), dtype=np.complex128)
+        _check(lib.adc_state_pair_density(self._h, _ptr(YK, np.complex128), _ptr(YL, np.complex128), YK.shape[0],
+                                          _ptr(rho, np.complex128)), self._h)
         return rho
 
     def spectroscopic_amplitudes(self, Y):

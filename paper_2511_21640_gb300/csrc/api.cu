@@ -428,6 +428,20 @@ int adc_transition_density(adc_ctx *c, const adc_c128 *Y, int64_t k, adc_c128 *r
   ADC_API_CATCH(c)
 }
 
+int adc_state_pair_density(adc_ctx *c, const adc_c128 *YK, const adc_c128 *YL, int64_t k, adc_c128 *rho) {
+  if (!c) return ADC_ERR_STATE;
+  if (!YK || !YL || !rho || k < 1) return ADC_ERR_ARG;
+  ADC_API_TRY
+  DevIn kin(c->ex, YK, (size_t)k * c->N * sizeof(cplx));
+  DevIn lin(c->ex, YL, (size_t)k * c->N * sizeof(cplx));
+  DevOut rout(c->ex, rho, (size_t)k * c->nmo * c->nmo * sizeof(cplx));
+  state_pair_density(c, (const cplx *)kin.p, (const cplx *)lin.p, k, (cplx *)rout.p);
+  rout.finish(c->ex);
+  ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
 int adc_spectroscopic_amplitudes(adc_ctx *c, const adc_c128 *Y, int64_t k, adc_c128 *x) {
   if (!c) return ADC_ERR_STATE;
   if (!Y || !x || k < 1) return ADC_ERR_ARG;
@@ -445,7 +459,6 @@ int adc_spectroscopic_amplitudes(adc_ctx *c, const adc_c128 *Y, int64_t k, adc_c
 int adc_excited_density(adc_ctx *c, const adc_c128 *Y, int64_t k, adc_c128 *rho) {
   if (!c) return ADC_ERR_STATE;
   if (!Y || !rho || k < 1) return ADC_ERR_ARG;
-  if (c->kind != ADC_EE) return ADC_ERR_UNSUPPORTED;
   ADC_API_TRY
   DevIn yin(c->ex, Y, (size_t)k * c->N * sizeof(cplx));
   DevOut rout(c->ex, rho, (size_t)k * c->nmo * c->nmo * sizeof(cplx));

@@ -90,8 +90,10 @@ void transition_density(adc_ctx *c, const cplx *Y, int64_t k, cplx *rho);
 int64_t cholesky_run(Exec &ex, const double *V, int64_t n, double tau, int64_t max_rank, double *L, int64_t *pivots);
 // B[P] = C^H L^P C for real L [rank][nao][nao] and C [nao][nmo] (all device)
 void cholesky_mo(Exec &ex, const double *L, int64_t rank, int64_t nao, const cplx *C, int64_t nmo, cplx *B);
-// EE excited-state densities rho [k][nmo][nmo]: ground state to second order + zeroth-order ISR difference
+// state densities rho [k][nmo][nmo] of any kind: ground state to second order + zeroth-order ISR
+// difference (properties.cu); state_pair_density gives <Psi_K|a+_p a_q|Psi_L> for the pairs (YK[z], YL[z])
 void excited_density(adc_ctx *c, const cplx *Y, int64_t k, cplx *rho);
+void state_pair_density(adc_ctx *c, const cplx *YK, const cplx *YL, int64_t k, cplx *rho);
 // IP/EA spectroscopic amplitudes x [k][nmo] of the vectors Y [k][N] (properties.cu)
 void spectroscopic_amplitudes(adc_ctx *c, const cplx *Y, int64_t k, cplx *x);
 int ssfns_run(const adc_c128 *B, int64_t naux, const double *eps_occ, int64_t nocc, const double *eps_vir,

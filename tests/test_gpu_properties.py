@@ -1,7 +1,7 @@
-"""EE ground-to-excited transition densities (adc_transition_density),
-excited-state densities (adc_excited_density) and IP/EA spectroscopic
-amplitudes (adc_spectroscopic_amplitudes) on the GPU (Sec. 2.2) against the
-oracle: the closed forms of oracle/properties.py (1e-12 relative, ADC(2) and
+"""EE ground-to-excited transition densities (adc_transition_density), state
+and state-to-state densities of every kind (adc_excited_density,
+adc_state_pair_density) and IP/EA spectroscopic amplitudes
+(adc_spectroscopic_amplitudes) on the GPU (Sec. 2.2) against the oracle: the closed forms of oracle/properties.py (1e-12 relative, ADC(2) and
 ADC(3) contexts) and, on a tiny case, the brute-force ISR transition moments in
 determinant space directly (1e-12).
 """
@@ -103,3 +103,23 @@ def test_spectroscopic_amplitudes_reject_ee(gpu):
         with pytest.raises(gpu.AdcError) as e:
             c.spectroscopic_amplitudes(np.zeros((1, c.N), np.complex128))
         assert e.value.code == -6
+
+
+@pytest.mark.parametrize("kind,o,v,Q,order,x,seed", [("IP", 3, 7, 10, 3, 0.5, 91), ("EA", 4, 9, 14, 2, 0.0, 92),
+                                                     ("EE", 3, 6, 10, 3, 1.0, 93), ("IP", 10, 37, 50, 2, 0.0, 94),
+                                                     ("EA", 6, 29, 40, 3, 0.5, 95)])
+def test_state_pair_density_matches_oracle(gpu, kind, o, v, Q, order, x, seed):
+    p = make_problem(o, v, Q, seed=seed, sigma=0.12, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=order, x=x) as c:
+        YK = _vectors(c.N, 2, seed + 1)
+        YL = _vectors(c.N, 2, seed + 2) * np.array([[1.3], [0.7 - 0.2j]])  # unnormalised ket
+        R = c.state_pair_density(YK, YL)
+        Rk = c.excited_density(YK)
+    amp = Amplitudes(p.B, p.eps_occ, p.eps_vir)
+    for z in range(2):
+        ref = oprop.state_pair_density(YK[z], YL[z], kind, p.B, p.eps_occ, p.eps_vir, amp=amp)
+        assert np.abs(R[z] - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+        refk = oprop.state_pair_density(YK[z], YK[z], kind, p.B, p.eps_occ, p.eps_vir, amp=amp)
+        assert np.abs(Rk[z] - refk).max() < 1e-12 * max(1.0, np.abs(refk).max())
+        dn = {"IP": -1, "EA": 1, "EE": 0}[kind]
+        assert abs(np.trace(Rk[z]) - (o + dn)) < 1e-11
