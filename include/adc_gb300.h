@@ -104,6 +104,13 @@ typedef struct {
                            flops and inner size 512 as the sliced product with about 48
                            significant bits; the operators then differ from
                            the FP64 ones by about 1e-13 relative) */
+  int ee_vvvv;          /* EE third order: the terms of the singles block
+                           with four virtual indices (<ab||cd>, or a product
+                           of two amplitudes over four virtual indices).
+                           0 = automatic: formed in chunks of the first
+                           virtual index, never whole, when the dense
+                           <ab||cd> would take more than 32 GiB; 1 = always
+                           in chunks; -1 = always from the dense block */
 } adc_opts;
 
 typedef struct {

@@ -67,6 +67,10 @@ void second_order_amplitudes(adc_ctx *c, DBuf &G_vv, DBuf &Lad, DBuf &t2d, DBuf 
 // the second-order singles t2_i^a alone (needs c->t1)
 DBuf second_order_singles(adc_ctx *c);
 void setup_ee(adc_ctx *c);
+// EE: the four-virtual rows of the third-order singles block in chunks (opts.ee_vvvv, size)
+bool ee_vvvv_chunked(adc_ctx *c);
+// EE: build the product operands (structured, split-precision planes 0/2/3, sliced) ahead of a solve
+void ee_prepare(adc_ctx *c, int planes, bool sliced);
 // block Davidson for the lowest nroots roots (davidson.cu); with follow, one
 // root: the Ritz vector with the largest overlap with the (single) guess at
 // every iteration, instead of the lowest (root-specific solve)

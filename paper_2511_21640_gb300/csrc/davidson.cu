@@ -350,6 +350,21 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   int mmax = c->opts.max_subspace > 0 ? c->opts.max_subspace : std::max(8 * kb, 40);
   mmax = (int)std::min<int64_t>(std::min<int64_t>(mmax, N), 1024);
   mmax = std::max(mmax, std::min<int>((int)N, nroots + 1));
+  if (c->opts.max_subspace <= 0) {
+    // the operators of the products first (their transient buffers never meet
+    // the subspace), then V and AV within half of the memory left
+    if (c->kind == ADC_EE && c->ee)
+      ee_prepare(c, precision == ADC_PREC_FP64 ? 0 : (mixed == ADC_PREC_BF16X6 ? 3 : 2),
+                 c->opts.refine == ADC_PREC_SLICED);
+    ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+    size_t fr = 0, tot = 0;
+    ADC_CUDA(cudaMemGetInfo(&fr, &tot));
+    double avail = (double)fr;
+    if (c->ex.mem_limit > 0) avail = std::min(avail, (double)(c->ex.mem_limit - c->ex.mem_used));
+    const int64_t fit = (int64_t)(0.5 * std::max(avail, 0.0) / (2.0 * (double)N * sizeof(cplx)));
+    const int lo = (int)std::min<int64_t>(N, std::max(2 * nroots, kb) + kb);
+    if (fit < mmax) mmax = (int)std::max<int64_t>(fit, std::max(lo, std::min<int>((int)N, nroots + 1)));
+  }
   const int krmax = std::min(mmax, std::max(2 * nroots, kb));
   ADC_REQUIRE(!follow || (nroots == 1 && guess && nguess >= 1), ADC_ERR_ARG,
               "root-specific Davidson: one root and a guess vector");

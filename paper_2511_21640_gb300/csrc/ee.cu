@@ -46,8 +46,6 @@ const Rows kS3 = {{"1", "t1(aA,iM) t2c(bA,jM)"},
 const Rows kY3 = {{"1", "t1(aA,iM) t1c(AB,jN) v(BM,bN)"},
                   {"1", "t1(aA,iM) t1c(AB,MN) v(jB,bN)"},
                   {"1/2", "t1(aA,iM) t1c(bA,NO) v(jM,NO)"},
-                  {"1/2", "t1(aA,iM) t1c(BC,jM) v(BC,bA)"},
-                  {"1/2", "t1(aA,MN) t1c(bB,MN) v(jB,iA)"},
                   {"1/2", "t1(aA,MN) t1c(AB,MN) v(jB,bi)"},
                   {"1/2", "t1(AB,iM) t1c(AB,jN) v(aM,bN)"},
                   {"1/2", "t1(AB,MN) t1c(bA,MN) v(aj,iB)"},
@@ -55,16 +53,13 @@ const Rows kY3 = {{"1", "t1(aA,iM) t1c(AB,jN) v(BM,bN)"},
                   {"-1", "t1(aA,MN) t1c(bA,MO) v(jN,iO)"},
                   {"-1", "t1(aA,MN) t1c(AB,jM) v(BN,bi)"},
                   {"-1", "t1(AB,iM) t1c(bA,MN) v(aj,BN)"},
-                  {"-1", "t1(AB,iM) t1c(AC,jM) v(aC,bB)"},
                   {"-1/2", "t1(AB,iM) t1c(AB,MN) v(aj,bN)"},
                   {"-1/2", "t1(AB,MN) t1c(AB,jM) v(aN,bi)"},
                   {"1", "t1(AB,iM) t1c(AC,MN) v(jC,BN) d(ab)"},
                   {"1/2", "t1(AB,MN) t1c(AB,MO) v(jN,iO) d(ab)"},
-                  {"1/2", "t1(AB,MN) t1c(AC,MN) v(aC,bB) d(ij)"},
                   {"-1", "t1(aA,MN) t1c(AB,MO) v(BN,bO) d(ij)"},
                   {"-1/2", "t1(AB,MN) t1c(AB,MO) v(aN,bO) d(ij)"},
                   {"-1/2", "t1(AB,MN) t1c(AC,MN) v(jC,iB) d(ab)"},
-                  {"-1/4", "t1(aA,MN) t1c(BC,MN) v(BC,bA) d(ij)"},
                   {"-1/4", "t1(AB,iM) t1c(AB,NO) v(jM,NO) d(ab)"},
                   // ... and Psi2 (doubles t2, singles s2) with Phi
                   {"1", "t2(aA,iM) v(jM,bA)"},
@@ -78,6 +73,14 @@ const Rows kY3 = {{"1", "t1(aA,iM) t1c(AB,jN) v(BM,bN)"},
                   {"-1", "s2c(A,M) v(jA,iM) d(ab)"},
                   {"-1/2", "t2(aA,MN) v(MN,bA) d(ij)"},
                   {"-1/2", "t2(AB,iM) v(jM,AB) d(ab)"}};
+// the rows of Y3 with four virtual indices: <ab||cd>, or (first row) the
+// product of two amplitudes over four virtual indices; evaluated from these rows
+// with the dense integrals, or in chunks (y3_vvvv_chunked) for large v
+const Rows kY3V = {{"1/2", "t1(aA,iM) t1c(BC,jM) v(BC,bA)"},
+                   {"1/2", "t1(aA,MN) t1c(bB,MN) v(jB,iA)"},
+                   {"-1", "t1(AB,iM) t1c(AC,jM) v(aC,bB)"},
+                   {"1/2", "t1(AB,MN) t1c(AC,MN) v(aC,bB) d(ij)"},
+                   {"-1/4", "t1(aA,MN) t1c(BC,MN) v(BC,bA) d(ij)"}};
 // singles-doubles, first order <Phi| E_ia^+ [V_N, C_klcd] |Phi>
 const Rows kSD1 = {{"1", "v(al,cd) d(ik)"}, {"1", "v(kl,di) d(ac)"},
                    {"-1", "v(ak,cd) d(il)"}, {"-1", "v(kl,ci) d(ad)"}};
@@ -223,6 +226,115 @@ TermSource ee_source(adc_ctx *c) {
   return s;
 }
 
+bool ee_vvvv_chunked(adc_ctx *c) {
+  if (c->opts.ee_vvvv == 1) return true;
+  if (c->opts.ee_vvvv == -1) return false;
+  const double v = (double)c->v;
+  return v * v * v * v * (double)sizeof(cplx) > 32.0 * (double)(1ll << 30);
+}
+
+namespace {
+// M[i][a][i][b] += s G[a][b] for every i (M is [o][v][o][v])
+__global__ void k_add_ij_diag(cplx *M, const cplx *__restrict__ G, int64_t o, int64_t v, double s) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < o * v * v;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / (v * v), r = idx - i * v * v, a = r / v, b = r - a * v;
+    cplx &m = M[((i * v + a) * o + i) * v + b];
+    m = cmake(m.x + s * G[r].x, m.y + s * G[r].y);
+  }
+}
+
+// M[i][a0 + a][j][b] += s T[i][j][a][b], a < na
+__global__ void k_add_chunk(const cplx *__restrict__ T, int64_t o, int64_t na, int64_t v, int64_t a0, double s,
+                            cplx *M) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < o * o * na * v;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = idx % v;
+    int64_t r = idx / v;
+    const int64_t a = r % na;
+    r /= na;
+    const int64_t j = r % o, i = r / o;
+    cplx &m = M[((i * v + a0 + a) * o + j) * v + b];
+    m = cmake(m.x + s * T[idx].x, m.y + s * T[idx].y);
+  }
+}
+}  // namespace
+
+// The rows of kY3V times x, added to the singles block M [o][v][o][v], without
+// the dense <ab||cd> (t: first-order doubles, Lad_ij^ab = 1/2 sum_cd <ab||cd>
+// t_ij^cd, <pq||rs>* = <rs||pq>, <pq||rs> = sum_Q (B_pr B_qs - B_ps B_qr)):
+//   1/2 t(aA,iM) t*(BC,jM) <BC||bA>        = sum_AM t_iM^aA conj(Lad_jM^bA)
+//   -1/4 t(aA,MN) t*(BC,MN) <BC||bA> d_ij  = -1/2 d_ij sum_AMN t_MN^aA conj(Lad_MN^bA)
+//   1/2 t(AB,MN) t*(AC,MN) <aC||bB> d_ij   = 1/2 d_ij sum_BC P_BC <aC||bB>,
+//        P_BC = sum_AMN t_MN^AB conj(t_MN^AC), contracted through B
+//   1/2 t(aA,MN) t*(bB,MN) <jB||iA>        = 1/2 sum_AB D[a][A][b][B] <jB||iA>
+//   -t(AB,iM) t*(AC,jM) <aC||bB>           = -sum_BC R[i][j][B][C] <aC||bB>,
+//        R = sum_AM t_iM^AB conj(t_jM^AC)
+// The last two run over chunks of a: D[a][A][b][B] = sum_MN t_MN^aA conj(t_MN^bB)
+// and <aC||bB> (assembled from B) exist for one chunk at a time.
+void y3_vvvv_chunked(adc_ctx *c, const DBuf &Lad, double x, cplx *Mp) {
+  Exec &ex = c->ex;
+  const int64_t o = c->o, v = c->v, Q = c->Q;
+  TagScope tg(ex, "ee_y3_chunked");
+  ADC_REQUIRE(Lad.p != nullptr, ADC_ERR_STATE, "EE setup: ladder intermediate missing");
+  const TV t = TV::dense(c->t1.c(), {o, o, v, v}), tc = t.cj();
+  const TV Ladc = TV::dense(Lad.c(), {o, o, v, v}).cj();
+  const TV M = TV::dense(Mp, {o, v, o, v});
+  einsum(ex, CR(x), t, "iMaA", Ladc, "jMbA", C1(), M, "iajb");
+  // the d_ij rows as one [v][v] matrix
+  {
+    DBuf G = cbuf(ex, v * v), P = cbuf(ex, v * v), pQ = cbuf(ex, Q), H = cbuf(ex, Q * v * v);
+    const TV Gv = TV::dense(G.c(), {v, v}), Pv = TV::dense(P.c(), {v, v}), pv = TV::dense(pQ.c(), {Q}),
+             Hv = TV::dense(H.c(), {Q, v, v});
+    const TV Bvv = Bview(c, 'v', 'v');
+    einsum(ex, CR(-0.5), t, "MNaA", Ladc, "MNbA", C0(), Gv, "ab");
+    einsum(ex, C1(), t, "MNAB", tc, "MNAC", C0(), Pv, "BC");
+    einsum(ex, C1(), Pv, "BC", Bvv, "QCB", C0(), pv, "Q");
+    einsum(ex, CR(0.5), pv, "Q", Bvv, "Qab", C1(), Gv, "ab");
+    einsum(ex, C1(), Bvv, "QaB", Pv, "BC", C0(), Hv, "QaC");
+    einsum(ex, CR(-0.5), Hv, "QaC", Bvv, "QCb", C1(), Gv, "ab");
+    k_add_ij_diag<<<grid1d(o * v * v, 256), 256, 0, ex.stream>>>(Mp, G.c(), o, v, x);
+    ADC_CHECK_LAUNCH();
+  }
+  // R[i][j][B][C], W[i][j][A][B] = <jB||iA>, Bt[Q][B][C] = B^Q_CB
+  DBuf R = cbuf(ex, o * o * v * v), W = cbuf(ex, o * o * v * v), Bt = cbuf(ex, Q * v * v);
+  einsum(ex, C1(), t, "iMAB", tc, "jMAC", C0(), TV::dense(R.c(), {o, o, v, v}), "ijBC");
+  {
+    DBuf ovov = eri_block(c, "ovov");  // [j][B][i][A]
+    permute(ex, ovov.c(), {o, o, v, v}, {v, v * o * v, 1, o * v}, false, W.c(), C1(), C0());
+  }
+  {
+    const TV Bvv = Bview(c, 'v', 'v');
+    permute(ex, Bvv.p, {Q, v, v}, {Bvv.str[0], 1, Bvv.str[1]}, false, Bt.c(), C1(), C0());
+  }
+  const TV Rv = TV::dense(R.c(), {o, o, v, v}), Wv = TV::dense(W.c(), {o, o, v, v});
+  // chunk of a: each of the four chunk buffers within about 2 GiB, and at
+  // least four chunks (ceil(v/4) wide) so that every size runs the chunk loop
+  const int64_t per_a = v * v * v * (int64_t)sizeof(cplx);
+  const int64_t na = std::max<int64_t>(
+      1, std::min<int64_t>((v + 3) / 4, (2ll << 30) / std::max<int64_t>(per_a, 1)));
+  DBuf D = cbuf(ex, na * v * v * v), Vc = cbuf(ex, na * v * v * v), T = cbuf(ex, o * o * na * v);
+  for (int64_t a0 = 0; a0 < v; a0 += na) {
+    const int64_t n = std::min(na, v - a0);
+    const TV Dv = TV::dense(D.c(), {n, v, v, v}), Vv = TV::dense(Vc.c(), {v, v, n, v}),
+             Tv = TV::dense(T.c(), {o, o, n, v});
+    // D[a][A][b][B] = sum_MN t_MN^aA conj(t_MN^bB), a in the chunk
+    const TV ta(c->t1.c() + a0 * v, {o, o, n, v}, {o * v * v, v * v, v, 1});
+    einsum(ex, C1(), ta, "MNaA", tc, "MNbB", C0(), Dv, "aAbB");
+    // Vc[B][C][a][b] = <aC||bB> = sum_Q (B_ab B_CB - B_aB B_Cb), a in the chunk
+    const TV Bvv = Bview(c, 'v', 'v');
+    const TV Ba(Bvv.p + a0 * Bvv.str[1], {Q, n, v}, Bvv.str);
+    const TV BtCB(Bt.c(), {Q, v, v}, {v * v, 1, v});  // labels Q, C, B
+    einsum(ex, C1(), Ba, "Qab", BtCB, "QCB", C0(), Vv, "BCab");
+    einsum(ex, CR(-1.0), Ba, "QaB", Bvv, "QCb", C1(), Vv, "BCab");
+    // T[i][j][a][b] = 1/2 sum_AB W[i][j][A][B] D[a][A][b][B] - sum_BC R[i][j][B][C] Vc[B][C][a][b]
+    einsum(ex, CR(0.5), Wv, "ijAB", Dv, "aAbB", C0(), Tv, "ijab");
+    einsum(ex, CR(-1.0), Rv, "ijBC", Vv, "BCab", C1(), Tv, "ijab");
+    k_add_chunk<<<grid1d(o * o * n * v, 256), 256, 0, ex.stream>>>(T.c(), o, n, v, a0, x, Mp);
+    ADC_CHECK_LAUNCH();
+  }
+}
+
 void setup_ee(adc_ctx *c) {
   Exec &ex = c->ex;
   const int64_t o = c->o, v = c->v, n1 = c->n1;
@@ -231,14 +343,23 @@ void setup_ee(adc_ctx *c) {
   c->ee.reset(new EEOps());
   EEOps &E = *c->ee;
   E.K1 = parse_terms(kK1); E.S2 = parse_terms(kS2); E.Y2 = parse_terms(kY2);
-  E.S3 = parse_terms(kS3); E.Y3 = parse_terms(kY3);
+  E.S3 = parse_terms(kS3);
+  E.Y3L = parse_terms(kY3);
+  E.Y3 = E.Y3L;
+  {
+    const std::vector<Term> y3v = parse_terms(kY3V);
+    E.Y3.insert(E.Y3.end(), y3v.begin(), y3v.end());
+  }
   E.SD1 = parse_terms(kSD1); E.O2 = parse_terms(kO2); E.Z1 = parse_terms(kZ1); E.DD1 = parse_terms(kDD1);
   amplitude_tables(E.T2N, E.S2N);
   first_order_amplitudes(c);
+  const bool chunked = ee_vvvv_chunked(c);
+  DBuf Lad_keep;  // the ladder intermediate, for the chunked four-virtual terms
   if (c->order == 3) {
     // also at x = 0: the derivative with respect to x needs them
     DBuf G_vv, Lad;
     second_order_amplitudes(c, G_vv, Lad, E.t2d, E.t2s);
+    if (chunked && third) Lad_keep = std::move(Lad);
   }
   TermSource src = ee_source(c);
   const std::string L = "iajb";
@@ -274,7 +395,13 @@ void setup_ee(adc_ctx *c) {
     eval_terms(ex, E.S3, src, {}, false, C1(), TV::dense(S3.c(), e4), L);
     k_wmul_add<<<grid1d(n1 * n1, 256), 256, 0, ex.stream>>>(E.MSS.c(), S3.c(), c->eo.d(), c->ev.d(), o, v, x);
     ADC_CHECK_LAUNCH();
-    eval_terms(ex, E.Y3, src, {}, false, CR(x), M, L);
+    if (chunked) {
+      eval_terms(ex, E.Y3L, src, {}, false, CR(x), M, L);
+      y3_vvvv_chunked(c, Lad_keep, x, E.MSS.c());
+      Lad_keep.reset();
+    } else {
+      eval_terms(ex, E.Y3, src, {}, false, CR(x), M, L);
+    }
     // - x/2 (S2 K1 + K1 S2)
     zgemm(ex, n1, n1, n1, 1, CR(-0.5 * x), S2.c(), 0, n1, 1, false, K1.c(), 0, n1, 1, false, C1(), E.MSS.c(), 0,
           n1, 1);
@@ -296,6 +423,9 @@ void setup_ee(adc_ctx *c) {
     ADC_CHECK_LAUNCH();
   }
   ADC_CUDA(cudaStreamSynchronize(ex.stream));
+  // at sizes where the four-virtual terms are chunked, the dense integral
+  // blocks of the tables are dropped (they are rebuilt on demand)
+  if (chunked) E.eri.clear();
 }
 
 void ee_struct_build(adc_ctx *c, bool dd);

@@ -13,6 +13,7 @@ enum { EE_VAT = 0, EE_VAC, EE_VB, EE_VBC, EE_GVV, EE_GOO, EE_W, EE_NOPS };
 
 struct EEOps {
   std::vector<Term> K1, S2, Y2, S3, Y3, SD1, O2, Z1, DD1;
+  std::vector<Term> Y3L;            // Y3 without its four-virtual rows (chunked evaluation)
   std::vector<Term> T2N, S2N;  // numerators of the second-order doubles and singles (adjoint only)
   DBuf t2d, t2s;
   std::map<std::string, DBuf> eri;  // dense integral blocks by o/v spec

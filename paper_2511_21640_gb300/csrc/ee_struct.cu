@@ -599,4 +599,15 @@ void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
   }
 }
 
+// the operands of the EE products a solve will use, built ahead of its subspace
+// (planes: 0 = no split-precision copies, 2 or 3 = BF16x3 or BF16x6)
+void ee_prepare(adc_ctx *c, int planes, bool sliced) {
+  EEOps &E = *c->ee;
+  const bool third = (c->order == 3) && (c->x != 0.0);
+  const bool dd = third && c->dd_order == 1;
+  ee_struct_build(c, dd);
+  if (planes > 0 && (!E.tc_ready || E.tc_planes < planes)) ee_tc_build(c, dd, planes);
+  if (sliced && !E.sl_ready) ee_sl_build(c, dd);
+}
+
 }  // namespace adc

@@ -57,6 +57,27 @@ def test_ee_sigma_diag_block(gpu, o, v, Q, order, x, dd, seed):
         assert _rel(Ss, ref).max() < 1e-10, _rel(Ss, ref).max()
 
 
+@pytest.mark.parametrize("o,v,Q,x,dd,seed", [(4, 10, 14, 1.0, 0, 31), (3, 7, 11, 0.6, 1, 32)])
+def test_ee_singles_block_chunked_four_virtual(gpu, o, v, Q, x, dd, seed):
+    """Third-order singles block with its four-virtual rows in chunks of the
+    first virtual index (v = 10: chunks 3, 3, 3, 1; v = 7: 2, 2, 2, 1), through
+    the ladder intermediate and the Cholesky vectors instead of the dense
+    <ab||cd>: equal to the oracle's explicit block and to the dense evaluation."""
+    p = make_problem(o, v, Q, seed=seed, sigma=0.1, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    n1 = o * v
+    M = adc_ee.explicit_matrix(3, x, p.B, p.eps_occ, p.eps_vir, dd_order=dd)
+    X = random_vectors(n1 + adc_ee.dims(o, v)[1], 2, seed=seed + 1)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=3, x=x, dd_order=dd, vvvv="chunked") as c:
+        Mc = c.main_block()
+        Sc = c.sigma(X, "fp64")
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=3, x=x, dd_order=dd, vvvv="dense") as c:
+        Md = c.main_block()
+    assert np.abs(Mc - M[:n1, :n1]).max() < 1e-12 * np.abs(M).max()
+    assert np.abs(Mc - Md).max() < 1e-13 * np.abs(Md).max()
+    ref = adc_ee.sigma_ref(3, x, p.B, p.eps_occ, p.eps_vir, X, dd_order=dd)
+    assert _rel(Sc, ref).max() < 1e-12
+
+
 def test_ee_davidson_matches_dense(gpu):
     o, v, Q = 4, 9, 16
     p = make_problem(o, v, Q, seed=7, sigma=0.08, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
