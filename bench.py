@@ -264,7 +264,10 @@ def run_ee(args, cfgname):
     p = config_problem(cfgname)
     o, v, Q = p.nocc, p.nvir, p.naux
     t0 = time.perf_counter()
-    ctx = adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=cfg["order"], x=x, refine=args.refine)
+    dd_order, block = cfg.get("dd_order", 1), cfg.get("block", 0)
+    setup = cfg.get("setup", "fp64")
+    ctx = adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=cfg["order"], x=x, refine=args.refine,
+                         dd_order=dd_order, block=block, setup=setup)
     init_s = time.perf_counter() - t0
     log(f"init {init_s:.1f} s, N = {ctx.N}")
     ctx.sigma(random_vectors(ctx.N, 1, seed=3), args.mixed)  # builds the split-precision operators
@@ -281,14 +284,15 @@ def run_ee(args, cfgname):
     clk = clocks.stop()
     log(f"mixed davidson {solve_s:.1f} s", st)
     fp64 = None
-    if not args.no_fp64_davidson:
+    if not args.no_fp64_davidson and cfg.get("fp64_davidson", True):
         t2 = time.perf_counter()
         om64, _, e6, st6, rc6 = ctx.davidson(nroots, tol=tol, max_iter=400, precision="fp64", want_vectors=False)
         t64 = time.perf_counter() - t2
         log(f"fp64 davidson {t64:.1f} s", st6)
         fp64 = {"s_per_root": t64 / nroots, "iterations": st6["iterations"], "sigma_calls": st6["sigma_calls"],
                 "max_eig_diff_vs_mixed": float(np.abs(om64 - om).max()), "rc": int(rc6)}
-    Xs = random_vectors(ctx.N, nroots, seed=7)
+    nsig = nroots if ctx.N < 20_000_000 else 1
+    Xs = random_vectors(ctx.N, nsig, seed=7)
     sig = {}
     for prec in (args.mixed, "sliced", "fp64"):
         ctx.sigma(Xs, prec)
@@ -299,8 +303,17 @@ def run_ee(args, cfgname):
         sp = ctx.profile_read()
         ctx.profile(False)
         sig[prec] = {"ms": 1e3 * ts, "flops_timed_kernels": sum(e["flops"] for e in sp.values())}
+    fns = None
+    if cfg.get("fns_eta") is not None:
+        ctx.profile(True)
+        t4 = time.perf_counter()
+        n_keep = ctx.fns_density(cfg["fns_eta"])["n_keep"]
+        fns_s = time.perf_counter() - t4
+        ctx.profile(False)
+        fns = {"s": fns_s, "eta_crit": cfg["fns_eta"], "n_keep": int(n_keep), "nvir": v}
+        log(f"fns density {fns_s:.2f} s, keep {n_keep} of {v}")
     grad = None
-    if args.no_gradient:
+    if args.no_gradient or not cfg.get("gradient", True):
         ctx.close()
     else:
         rng = np.random.default_rng(11)
@@ -351,13 +364,15 @@ def run_ee(args, cfgname):
         "data": "synthetic",
         "config": {"workload": cfgname, "kind": "EE", "order": cfg["order"], "x": x, "nocc": o, "nvir": v,
                    "naux": Q, "nroots": nroots, "tol_fp64_residual": tol, "N": int(Y.shape[1]),
+                   "dd_order": dd_order, "block": block, "setup": setup,
                    "l2": "operators larger than L2"},
         "clocks": clk, "gpu_launches": int(launches), "roofline": by_kernel[0], "roofline_by_kernel": by_kernel,
         "mixed_davidson": {"iterations": st["iterations"], "sigma_calls": st["sigma_calls"],
                            "sigma_calls_fp64": st["sigma_calls_fp64"], "rc": int(rc),
                            "omega": [float(w) for w in om], "err64": [float(e) for e in e64]},
         "fp64_davidson": fp64,
-        "sigma": {"vectors": nroots, "mixed": args.mixed, "mixed_ms": sig[args.mixed]["ms"],
+        "fns": fns,
+        "sigma": {"vectors": nsig, "mixed": args.mixed, "mixed_ms": sig[args.mixed]["ms"],
                   "sliced_ms": sig["sliced"]["ms"], "fp64_ms": sig["fp64"]["ms"],
                   "speedup": sig["fp64"]["ms"] / sig[args.mixed]["ms"],
                   "speedup_sliced": sig["fp64"]["ms"] / sig["sliced"]["ms"]},
@@ -578,7 +593,7 @@ def main():
 
     # ---- FP64 Davidson for the comparison and the 1e-6 Eh check
     fp64 = None
-    if not args.no_fp64_davidson:
+    if not args.no_fp64_davidson and cfg.get("fp64_davidson", True):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         om64, _, e6, st6, rc6 = ctx.davidson(nroots, tol=tol, max_iter=300, precision="fp64", want_vectors=False)

@@ -118,8 +118,12 @@ CONFIGS = {
                            vir_range=(0.2, 3.0), kind="IP", order=3, x=1.0, nroots=4, tol=1e-8),
     "ea2x3_o40_v200_q1200": dict(nocc=40, nvir=200, naux=1200, seed=0, occ_range=(-3.0, -0.3),
                                  vir_range=(0.1, 5.0), kind="EA", order=3, x=0.5, nroots=8, tol=1e-6),
+    # EE-ADC(3) with the doubles block at the ADC(2) level, block Davidson of 12,
+    # the FNS virtual density truncated at occupation 1e-5
     "ee3_o60_v300_q1800": dict(nocc=60, nvir=300, naux=1800, seed=0, occ_range=(-3.0, -0.3),
-                               vir_range=(0.1, 5.0), kind="EE", order=3, x=1.0, nroots=6, tol=1e-6),
+                               vir_range=(0.1, 5.0), kind="EE", order=3, x=1.0, nroots=6, tol=1e-6,
+                               dd_order=0, block=12, fns_eta=1e-5, setup="sliced", fp64_davidson=False,
+                               gradient=False),
     "ee2x3_o30_v150_q900": dict(nocc=30, nvir=150, naux=900, seed=0, occ_range=(-3.0, -0.3),
                                 vir_range=(0.1, 5.0), kind="EE", order=3, x=0.4, nroots=4, tol=1e-8),
     # a smaller case of the same family, for quick runs of the same measurement
@@ -128,10 +132,12 @@ CONFIGS = {
 }
 
 
+# solver settings of a config (not inputs of make_problem)
+SOLVER_KEYS = ("nroots", "tol", "dd_order", "block", "fns_eta", "setup", "fp64_davidson", "gradient")
+
+
 def config_problem(name):
-    c = dict(CONFIGS[name])
-    c.pop("nroots")
-    c.pop("tol")
+    c = {k: val for k, val in CONFIGS[name].items() if k not in SOLVER_KEYS}
     return make_problem(name=name, **c)
 
 
