@@ -76,3 +76,35 @@ def test_binding_rejects_wrong_dtypes(lib):
         lib._ptr(np.zeros(3, np.complex64), np.complex128)
     with pytest.raises(TypeError):
         lib._ptr(np.zeros((3, 3), np.complex128)[:, 0], np.complex128)
+
+
+STRUCTS = ["adc_opts", "adc_stats", "adc_ssfns_root", "adc_batch_info", "adc_problem", "adc_batch_opts",
+           "adc_kernel_stat"]
+
+
+def test_python_struct_mirrors_match_the_headers(lib, tmp_path):
+    """Size and field offsets of every public struct, as gcc lays it out from
+    include/*.h, equal those of the ctypes mirrors of the Python binding."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "adc_gb300.h"', '#include "adc_gb300_diag.h"',
+             "int main(void) {"]
+    for st in STRUCTS:
+        cls = getattr(lib, st)
+        lines.append(f'  printf("{st} size %zu\\n", sizeof({st}));')
+        for name, _ in cls._fields_:
+            lines.append(f'  printf("{st} {name} %zu\\n", offsetof({st}, {name}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for st in STRUCTS:
+        cls = getattr(lib, st)
+        assert c_layout[(st, "size")] == ctypes.sizeof(cls), st
+        for name, _ in cls._fields_:
+            assert c_layout[(st, name)] == getattr(cls, name).offset, (st, name)
