@@ -36,6 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from synthetic import (BATCH_CONFIGS, CONFIGS, batch_problems, batch_sizes, config_problem,  # noqa: E402
+                       random_hermitian_direction,
                        random_vectors)
 
 METRIC = "Davidson s/root and sigma TFLOP/s: mixed vs FP64 on GPU at 1e-6 Eh error"
@@ -257,7 +258,6 @@ def run_ee(args, cfgname):
     deps, dx), h = 1e-5, from two more mixed-precision solves."""
     import torch
     import paper_2511_21640_gb300 as adcgpu
-    from oracle.gradients import directional, random_hermitian_direction
     cfg = dict(CONFIGS[cfgname])
     nroots, x = cfg["nroots"], cfg["x"]
     tol = args.tol if args.tol is not None else cfg["tol"]
@@ -324,7 +324,9 @@ def run_ee(args, cfgname):
         log(f"adjoint {adj_s:.1f} s")
         ctx.close()
         D = (random_hermitian_direction(p.B.shape, 12), rng.standard_normal(o), rng.standard_normal(v), 0.7)
-        pred = directional(gB, geo, gev, gx, D)
+        # derivative along D that the gradients predict
+        pred = float(np.real(np.vdot(gB, D[0]))) + float(np.dot(geo, D[1])) + float(np.dot(gev, D[2])) \
+            + float(gx) * D[3]
         h = 1e-5
         ws = []
         for sgn in (1, -1):

@@ -25,6 +25,8 @@ from __future__ import annotations
 
 import numpy as np
 
+from synthetic import random_hermitian_direction  # noqa: F401  (seeded input generator, re-exported)
+
 from . import adc as _adc
 from . import adc_ee as _ee
 
@@ -85,11 +87,3 @@ def directional(gB, geo, gev, gx, D):
     if dev is not None:
         s += float(np.dot(gev, dev))
     return s + float(gx) * float(dx)
-
-
-def random_hermitian_direction(shape, seed):
-    """Random dB with dB[Q] Hermitian for every Q, unit Frobenius norm."""
-    rng = np.random.default_rng(seed)
-    A = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
-    A = 0.5 * (A + np.conj(np.swapaxes(A, 1, 2)))
-    return np.ascontiguousarray(A / np.linalg.norm(A))

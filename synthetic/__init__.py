@@ -172,3 +172,13 @@ def batch_problems(name="batch64_ipea", n=None, select=None):
     return [make_problem(sizes[i]["nocc"], sizes[i]["nvir"], sizes[i]["naux"], seed=sizes[i]["seed"],
                          occ_range=c["occ_range"], vir_range=c["vir_range"], kind=sizes[i]["kind"],
                          order=c["order"], x=c["x"], name=f"{name}[{i}]") for i in idx]
+
+
+def random_hermitian_direction(shape, seed):
+    """Random dB [Q][n][n] with every dB[Q] Hermitian and unit Frobenius norm (a
+    perturbation direction of Cholesky vectors)."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    A = 0.5 * (A + np.conj(np.swapaxes(A, 1, 2)))
+    return np.ascontiguousarray(A / np.linalg.norm(A))
+
