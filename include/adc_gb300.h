@@ -89,7 +89,10 @@ typedef struct {
   int precision;        /* default precision of adc_davidson's mixed phase */
   void *stream;         /* cudaStream_t to run on; NULL = the context's own */
   int block;            /* Davidson block size (new vectors per iteration), 0 = nroots */
-  int max_subspace;     /* Davidson subspace limit, 0 = automatic */
+  int max_subspace;     /* Davidson subspace limit, 0 = automatic: 8 x the
+                           block (at least 40), lowered so that the subspace
+                           and its products take at most half of the device
+                           memory free once the operators are built */
   double herm_tol;      /* relative tolerance of the Hermiticity check of B */
   int64_t mem_limit;    /* bytes the context may allocate, 0 = no limit */
   int verbose;          /* 1 = per-iteration lines on stderr */
