@@ -108,3 +108,29 @@ def test_python_struct_mirrors_match_the_headers(lib, tmp_path):
         assert c_layout[(st, "size")] == ctypes.sizeof(cls), st
         for name, _ in cls._fields_:
             assert c_layout[(st, name)] == getattr(cls, name).offset, (st, name)
+
+
+@pytest.mark.parametrize("field,value", [("ee_vvvv", 2), ("ee_vvvv", -2), ("refine", 1), ("setup", 2)])
+def test_init_rejects_bad_options_before_device_work(lib, field, value):
+    o = lib.adc_opts()
+    lib.lib.adc_opts_default(ctypes.byref(o))
+    setattr(o, field, value)
+    nocc, nvir = 3, 5
+    nmo = nocc + nvir
+    B = np.zeros((2, nmo, nmo), np.complex128)
+    eo, ev = -np.ones(nocc), np.ones(nvir)
+    h = ctypes.c_void_p()
+    rc = lib.lib.adc_init(ctypes.byref(h), B.ctypes.data, 2, eo.ctypes.data, nocc, ev.ctypes.data, nvir,
+                          2, 3, 1.0, ctypes.byref(o))
+    assert rc == -1
+    assert not h.value
+
+
+def test_property_calls_need_a_context(lib):
+    z = np.zeros(4, np.complex128)
+    p = z.ctypes.data
+    L = lib.lib
+    assert L.adc_spectroscopic_amplitudes(None, p, 1, p) == -7
+    assert L.adc_state_pair_density(None, p, p, 1, p) == -7
+    assert L.adc_excited_density(None, p, 1, p) == -7
+    assert L.adc_transition_density(None, p, 1, p) == -7
