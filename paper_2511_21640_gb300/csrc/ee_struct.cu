@@ -329,8 +329,9 @@ void ee_struct_build(adc_ctx *c, bool dd) {
     E.Goo = cbuf(ex, po * po);
     k_pack_goo<<<grid1d(po * po, 256), 256, 0, ex.stream>>>(oooo.c(), pio, pjo, o, po, E.Goo.c());
     ADC_CHECK_LAUNCH();
-    E.Gvv = build_vvvv_packed(c);
   }
+  // (rebuilt here when a solve released it, see ee_prepare)
+  if (dd && !E.Gvv.p) E.Gvv = build_vvvv_packed(c);
 }
 
 // the structured pieces for vectors [X | ...] of one chunk: S1 += SD X2,
@@ -608,6 +609,10 @@ void ee_prepare(adc_ctx *c, int planes, bool sliced) {
   ee_struct_build(c, dd);
   if (planes > 0 && (!E.tc_ready || E.tc_planes < planes)) ee_tc_build(c, dd, planes);
   if (sliced && !E.sl_ready) ee_sl_build(c, dd);
+  // a mixed solve with sliced refinement reads only the split and sliced
+  // copies of the packed <ab||cd>; above 4 GiB its FP64 copy makes room for
+  // the subspace and is assembled again by the next FP64 product
+  if (dd && planes > 0 && sliced && E.Gvv.bytes > (4ull << 30)) E.Gvv.reset();
 }
 
 }  // namespace adc
