@@ -269,7 +269,9 @@ def run_ee(args, cfgname):
     ctx = adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EE", order=cfg["order"], x=x, refine=args.refine,
                          dd_order=dd_order, block=block, setup=setup)
     init_s = time.perf_counter() - t0
-    log(f"init {init_s:.1f} s, N = {ctx.N}")
+    mem_init = ctx.memory()
+    log(f"init {init_s:.1f} s, N = {ctx.N}, device memory after init {mem_init['in_use'] / 2**30:.1f} GiB "
+        f"(peak {mem_init['peak'] / 2**30:.1f} GiB)")
     ctx.sigma(random_vectors(ctx.N, 1, seed=3), args.mixed)  # builds the split-precision operators
     clocks = Clocks()
     clocks.start()
@@ -282,7 +284,8 @@ def run_ee(args, cfgname):
     prof = ctx.profile_read()
     ctx.profile(False)
     clk = clocks.stop()
-    log(f"mixed davidson {solve_s:.1f} s", st)
+    mem_solve = ctx.memory()
+    log(f"mixed davidson {solve_s:.1f} s, peak device memory {mem_solve['peak'] / 2**30:.1f} GiB", st)
     fp64 = None
     if not args.no_fp64_davidson and cfg.get("fp64_davidson", True):
         t2 = time.perf_counter()
@@ -374,6 +377,8 @@ def run_ee(args, cfgname):
                            "omega": [float(w) for w in om], "err64": [float(e) for e in e64]},
         "fp64_davidson": fp64,
         "fns": fns,
+        "memory_gib": {"after_init": mem_init["in_use"] / 2**30, "peak_init": mem_init["peak"] / 2**30,
+                       "peak_through_solve": mem_solve["peak"] / 2**30},
         "sigma": {"vectors": nsig, "mixed": args.mixed, "mixed_ms": sig[args.mixed]["ms"],
                   "sliced_ms": sig["sliced"]["ms"], "fp64_ms": sig["fp64"]["ms"],
                   "speedup": sig["fp64"]["ms"] / sig[args.mixed]["ms"],

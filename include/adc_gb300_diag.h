@@ -49,6 +49,12 @@ typedef struct {
 int adc_profile_enable(adc_ctx_opaque *ctx, int on);
 int adc_profile_read(adc_ctx_opaque *ctx, adc_kernel_stat *out, int max, int *n);
 
+/* Device memory of one context: the bytes its allocations hold now and the
+ * largest amount they held at once since adc_init (the context's own buffers,
+ * not the CUDA runtime's). Host-side counters only, no device work.
+ * ADC_ERR_STATE for a NULL context, ADC_ERR_ARG for NULL outputs. */
+int adc_memory(const adc_ctx_opaque *ctx, int64_t *in_use, int64_t *peak);
+
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t adc_launch_count(void);
 

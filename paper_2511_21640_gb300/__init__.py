@@ -120,6 +120,7 @@ def _load():
         "adc_excited_density": (I, [P, P, I64, P]),
         "adc_spectroscopic_amplitudes": (I, [P, P, I64, P]),
         "adc_state_pair_density": (I, [P, P, P, I64, P]),
+        "adc_memory": (I, [P, P, P]),
         "adc_cholesky": (I, [P, I64, D, I64, P, P, ctypes.POINTER(I64)]),
         "adc_cholesky_mo": (I, [P, I64, I64, P, I64, P]),
         "adc_ssfns_density": (I, [P, P, D, P, P, ctypes.POINTER(I64), P, P]),
@@ -367,6 +368,12 @@ class Context:
         _check(lib.adc_state_pair_density(self._h, _ptr(YK, np.complex128), _ptr(YL, np.complex128), YK.shape[0],
                                           _ptr(rho, np.complex128)), self._h)
         return rho
+
+    def memory(self):
+        """Bytes the context's device buffers hold now and at most since init (``adc_memory``)."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.adc_memory(self._h, ctypes.byref(a), ctypes.byref(b)), self._h)
+        return {"in_use": a.value, "peak": b.value}
 
     def spectroscopic_amplitudes(self, Y):
         """Spectroscopic amplitudes [k][nmo] of IP/EA vectors Y [k][N] (``adc_spectroscopic_amplitudes``)."""

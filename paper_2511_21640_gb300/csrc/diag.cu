@@ -199,6 +199,14 @@ extern "C" int adc_profile_enable(adc_ctx *c, int on) {
   }
 }
 
+extern "C" int adc_memory(const adc_ctx *c, int64_t *in_use, int64_t *peak) {
+  if (!c) return ADC_ERR_STATE;
+  if (!in_use || !peak) return ADC_ERR_ARG;
+  *in_use = c->ex.mem_used;
+  *peak = c->ex.mem_peak;
+  return ADC_OK;
+}
+
 extern "C" int adc_profile_read(adc_ctx *c, adc_kernel_stat *out, int max, int *n) {
   if (!c || !n) return c ? ADC_ERR_ARG : ADC_ERR_STATE;
   try {

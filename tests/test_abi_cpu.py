@@ -134,3 +134,4 @@ def test_property_calls_need_a_context(lib):
     assert L.adc_state_pair_density(None, p, p, 1, p) == -7
     assert L.adc_excited_density(None, p, 1, p) == -7
     assert L.adc_transition_density(None, p, 1, p) == -7
+    assert L.adc_memory(None, p, p) == -7
