@@ -1,6 +1,8 @@
-// EE ground-to-excited transition densities (Sec. 2.2).
+// One-particle properties of ADC states from the intermediate-state
+// representation (Sec. 2.2): EE transition densities, state and
+// state-to-state densities of every kind, IP/EA spectroscopic amplitudes.
 //
-// rho_pq = <Psi_K| a+_p a_q |Psi0> = sum_I conj(Y_I) f_I(pq) with the ISR
+// EE transition densities rho_pq = <Psi_K| a+_p a_q |Psi0> = sum_I conj(Y_I) f_I(pq) with the ISR
 // transition moments f_I(pq) = <Psi~_I| a+_p a_q |Psi0>, singles to second
 // and doubles to first order (t / t2: first- / second-order doubles, s2:
 // second-order singles, S2: second-order overlap of the orthogonalised
