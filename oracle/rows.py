@@ -8,12 +8,18 @@ their definition: every integral a row needs is assembled from the Cholesky
 vectors (Eq. 43) for that row only, and every amplitude from its definition
 t_ij^ab = <ab||ij>/D_ij^ab. The terms are those of ``adc.sigma_ref`` (EA:
 coupling, zeroth-order diagonal, ladder, ring; IP likewise), Sec. 2.1.
+
+EE doubles rows evaluate the oracle's own term tables (``adc_ee.TERMS``:
+the coupling M_SD at first and second order, the second-order overlap and
+M_DD^(1)) with the row's four indices held fixed, so that every operand is
+a slice assembled from B for that row (and the second-order singles only at
+the elements the row needs).
 """
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["ea_satellite_rows", "ip_satellite_rows"]
+__all__ = ["ea_satellite_rows", "ip_satellite_rows", "ee_doubles_rows"]
 
 
 def _pair(p, q, n):
@@ -177,3 +183,170 @@ def ip_satellite_rows(B, eps_occ, eps_vir, order, x, X, rows):
             val = val + x * (lad + ring(i, j) - ring(j, i))
         out[:, r] = val
     return out
+
+
+# ---------------------------------------------------------------- EE doubles rows
+
+def _class_sel(ch, fixed, o, v, occ):
+    base, n = (0, o) if ch in occ else (o, v)
+    return base + fixed[ch] if ch in fixed else slice(base, base + n)
+
+
+def _free(labels, fixed):
+    return "".join(ch for ch in labels if ch not in fixed)
+
+
+class _FixedIndexTensors:
+    """The tensors of the EE term tables with some labels held at fixed indices
+    (index within the label's class): each array has one axis per free label,
+    in label order, and is assembled from B for that slice only."""
+
+    def __init__(self, B, eps_occ, eps_vir, fixed):
+        from .adc_ee import _OCC
+        self.B = B
+        self.eo = np.asarray(eps_occ, np.float64)
+        self.ev = np.asarray(eps_vir, np.float64)
+        self.o, self.v = self.eo.size, self.ev.size
+        self.fixed = dict(fixed)
+        self.occ = _OCC
+        self._cache = {}
+        self._s2 = {}
+
+    def _eri(self, labels):
+        """<pq||rs> = sum_Q (B_pr B_qs - B_ps B_qr) (Eq. 43) on the slice."""
+        key = ("v", labels, tuple(self.fixed.get(c) for c in labels))
+        if key in self._cache:
+            return self._cache[key]
+        p, q, r, s_ = labels
+        sel = lambda c: _class_sel(c, self.fixed, self.o, self.v, self.occ)
+        f = lambda *cs: "".join(c for c in cs if c not in self.fixed)
+        out = f(p, q, r, s_)
+        B = self.B
+        val = (np.einsum(f"Q{f(p, r)},Q{f(q, s_)}->{out}", B[:, sel(p), sel(r)], B[:, sel(q), sel(s_)],
+                         optimize="greedy")
+               - np.einsum(f"Q{f(p, s_)},Q{f(q, r)}->{out}", B[:, sel(p), sel(s_)], B[:, sel(q), sel(r)],
+                           optimize="greedy"))
+        self._cache[key] = val
+        return val
+
+    def _energy(self, ch):
+        e = self.eo if ch in self.occ else self.ev
+        return e[self.fixed[ch]] if ch in self.fixed else e
+
+    def _denominator(self, a, b, i, j):
+        """eps_i + eps_j - eps_a - eps_b on the free labels of (a, b, i, j)."""
+        free = _free(a + b + i + j, self.fixed)
+        D = np.zeros([self.o if c in self.occ else self.v for c in free]) if free else np.zeros(())
+        for ch, sgn in ((a, -1.0), (b, -1.0), (i, 1.0), (j, 1.0)):
+            e = self._energy(ch)
+            if ch in self.fixed:
+                D = D + sgn * e
+            else:
+                shape = [1] * len(free)
+                shape[free.index(ch)] = e.size
+                D = D + sgn * e.reshape(shape)
+        return D
+
+    def _s2_element(self, a, i):
+        """t2_i^a (eps_i - eps_a) = 1/2 sum_jcd <aj||cd> t_ij^cd - 1/2 sum_jkc <jk||ic> t_jk^ac, one element."""
+        if (a, i) in self._s2:
+            return self._s2[(a, i)]
+        sub = _FixedIndexTensors(self.B, self.eo, self.ev, {"a": a, "i": i})
+        t_i = sub.array("t1", "cdij")      # t_ij^cd, free c, d, j
+        v_a = sub.array("v", "ajcd")       # <aj||cd>, free j, c, d
+        t_a = sub.array("t1", "acjk")      # t_jk^ac, free c, j, k
+        v_i = sub.array("v", "jkic")       # <jk||ic>, free j, k, c
+        num = 0.5 * np.einsum("cdj,jcd->", t_i, v_a) - 0.5 * np.einsum("cjk,jkc->", t_a, v_i)
+        val = num / (self.eo[i] - self.ev[a])
+        self._s2[(a, i)] = val
+        return val
+
+    def array(self, name, labels):
+        fx = self.fixed
+        if name == "d":
+            x, y = labels
+            n = self.o if x in self.occ else self.v
+            if x in fx and y in fx:
+                return np.asarray(1.0 if fx[x] == fx[y] else 0.0)
+            if x in fx or y in fx:
+                e = np.zeros(n)
+                e[fx[x] if x in fx else fx[y]] = 1.0
+                return e
+            return np.eye(n)
+        if name == "v":
+            return self._eri(labels)
+        if name in ("t1", "t1c"):
+            a, b, i, j = labels          # t_ij^ab = <ab||ij> / D_ij^ab
+            t = self._eri(a + b + i + j) / self._denominator(a, b, i, j)
+            return t.conj() if name == "t1c" else t
+        if name in ("s2", "s2c"):
+            a, i = labels
+            free = _free(labels, fx)
+            shape = [self.v if a not in fx else None, self.o if i not in fx else None]
+            if not free:
+                val = self._s2_element(fx[a], fx[i])
+                return np.asarray(np.conj(val) if name == "s2c" else val)
+            arr = np.zeros([n for n in shape if n is not None], np.complex128)
+            for idx in np.ndindex(*arr.shape):
+                it = iter(idx)
+                aa = fx[a] if a in fx else next(it)
+                ii = fx[i] if i in fx else next(it)
+                arr[idx] = self._s2_element(aa, ii)
+            return arr.conj() if name == "s2c" else arr
+        raise KeyError(name)
+
+    def evaluate(self, key, out):
+        """sum over TERMS[key] of coef * product, on the free labels of ``out``."""
+        from .adc_ee import TERMS, _TOK
+        fout = _free(out, self.fixed)
+        total = 0.0
+        for coef, product in TERMS[key]:
+            subs, ops = [], []
+            for name, labs in _TOK.findall(product):
+                lab = labs.replace(",", "")
+                subs.append(_free(lab, self.fixed))
+                ops.append(self.array(name, lab))
+            c = float(eval(coef, {"__builtins__": {}}))
+            total = total + c * np.einsum(",".join(subs) + "->" + fout, *ops, optimize="greedy")
+        return total
+
+
+def ee_doubles_rows(B, eps_occ, eps_vir, order, x, X, rows, dd_order=1):
+    """S2 entries (k<l, c<d) of S = M X for each ``(k, l, c, d)`` in ``rows`` (EE).
+
+    S2_D = sum_S conj(M_SD[S, D]) X1_S + Delta_D X2_D + x [dd_order] sum_D' M_DD^(1)[D, D'] X2_D',
+    M_SD = M_SD^(1) + x [(Delta_D - Delta_S) O2 + Z1]  (the blocks of ``adc_ee.Blocks``),
+    Delta_S = eps_a - eps_i, Delta_D = eps_c + eps_d - eps_k - eps_l.
+    Returns [len(X), len(rows)] complex.
+    """
+    eo = np.asarray(eps_occ, np.float64)
+    ev = np.asarray(eps_vir, np.float64)
+    o, v = eo.size, ev.size
+    if order == 2:
+        x = 0.0
+    n1 = o * v
+    X = np.atleast_2d(np.asarray(X, np.complex128))
+    X1 = X[:, :n1].reshape(-1, o, v)
+    X2 = X[:, n1:]
+    io, jo = np.triu_indices(o, 1)
+    av, bv = np.triu_indices(v, 1)
+    pv = av.size
+    dS = ev[None, :] - eo[:, None]
+    out = np.zeros((X.shape[0], len(rows)), np.complex128)
+    for r, (k, l, c, d) in enumerate(rows):
+        assert k < l and c < d
+        T = _FixedIndexTensors(B, eo, ev, {"k": k, "l": l, "c": c, "d": d})
+        Msd = T.evaluate("SD_M1", "iaklcd")
+        if x != 0.0:
+            dK = ev[c] + ev[d] - eo[k] - eo[l]
+            Msd = Msd + x * ((dK - dS) * T.evaluate("SD_O2", "iaklcd") + T.evaluate("SD_Z1", "iaklcd"))
+        D = _pair(k, l, o) * pv + _pair(c, d, v)
+        val = np.einsum("ia,zia->z", Msd.conj(), X1) + (ev[c] + ev[d] - eo[k] - eo[l]) * X2[:, D]
+        if x != 0.0 and dd_order == 1:
+            Td = _FixedIndexTensors(B, eo, ev, {"i": k, "j": l, "a": c, "b": d})
+            R = Td.evaluate("DD_M1", "ijabklcd")  # [k][l][c][d] free
+            Rp = R[io[:, None], jo[:, None], av[None, :], bv[None, :]].reshape(-1)
+            val = val + x * (X2 @ Rp)
+        out[:, r] = val
+    return out
+

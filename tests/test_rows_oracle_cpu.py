@@ -1,0 +1,55 @@
+"""Pins of the row oracles (oracle/rows.py), which compute single rows of
+S = M X at sizes where the dense oracle cannot: every row equals the same
+row of the term-by-term sigma (adc.sigma_ref, adc_ee.sigma_ref; Sec. 2.1) on
+small problems, for ADC(2), ADC(2)+x(3), ADC(3) and both EE doubles-block
+orders, so the full-size sampled parity tests and the CPU baseline use rows
+that are pinned to the oracle's definition."""
+import numpy as np
+import pytest
+
+from synthetic import make_problem, random_vectors
+from oracle import adc, adc_ee, rows
+
+
+def _pair(p, q, n):
+    return p * n - p * (p + 1) // 2 + (q - p - 1)
+
+
+@pytest.mark.parametrize("order,x", [(2, 0.0), (3, 1.0), (3, 0.5)])
+def test_ea_rows_equal_sigma(order, x):
+    o, v, Q = 3, 6, 9
+    p = make_problem(o, v, Q, seed=41, sigma=0.15, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    n1, n2 = adc.dims("EA", o, v)
+    X = random_vectors(n1 + n2, 2, seed=42)
+    S = adc.sigma_ref("EA", order, x, p.B, p.eps_occ, p.eps_vir, X)
+    sel = [(0, 0, 1), (2, 3, 5), (1, 0, 4), (2, 1, 2)]
+    R = rows.ea_satellite_rows(p.B, p.eps_occ, p.eps_vir, order, x, X, sel)
+    idx = [n1 + k * (v * (v - 1) // 2) + _pair(d, e, v) for k, d, e in sel]
+    assert np.abs(R - S[:, idx]).max() < 1e-13 * max(1.0, np.abs(S).max())
+
+
+@pytest.mark.parametrize("order,x", [(2, 0.0), (3, 1.0), (3, 0.5)])
+def test_ip_rows_equal_sigma(order, x):
+    o, v, Q = 4, 5, 9
+    p = make_problem(o, v, Q, seed=43, sigma=0.15, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    n1, n2 = adc.dims("IP", o, v)
+    X = random_vectors(n1 + n2, 2, seed=44)
+    S = adc.sigma_ref("IP", order, x, p.B, p.eps_occ, p.eps_vir, X)
+    sel = [(0, 1, 0), (2, 3, 4), (1, 3, 2), (0, 2, 1)]
+    R = rows.ip_satellite_rows(p.B, p.eps_occ, p.eps_vir, order, x, X, sel)
+    idx = [n1 + _pair(i, j, o) * v + a for i, j, a in sel]
+    assert np.abs(R - S[:, idx]).max() < 1e-13 * max(1.0, np.abs(S).max())
+
+
+@pytest.mark.parametrize("order,x,dd", [(2, 0.0, 1), (3, 1.0, 1), (3, 0.7, 0), (3, 0.4, 1)])
+def test_ee_rows_equal_sigma(order, x, dd):
+    o, v, Q = 3, 5, 8
+    p = make_problem(o, v, Q, seed=45, sigma=0.15, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    n1, n2 = adc_ee.dims(o, v)
+    X = random_vectors(n1 + n2, 2, seed=46)
+    S = adc_ee.sigma_ref(order, x, p.B, p.eps_occ, p.eps_vir, X, dd_order=dd)
+    sel = [(0, 1, 0, 1), (1, 2, 2, 4), (0, 2, 1, 3)]
+    R = rows.ee_doubles_rows(p.B, p.eps_occ, p.eps_vir, order, x, X, sel, dd_order=dd)
+    pv = v * (v - 1) // 2
+    idx = [n1 + _pair(k, l, o) * pv + _pair(c, d, v) for k, l, c, d in sel]
+    assert np.abs(R - S[:, idx]).max() < 1e-13 * max(1.0, np.abs(S).max())
