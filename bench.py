@@ -120,22 +120,56 @@ def sigma_flops_formula(o, v, Q, k):
     return 8.0 * cmac
 
 
-def cpu_oracle_sample(p, x, n_rows=6, seed=5):
-    """Seconds per satellite sigma row (one vector) of the oracle on this workload."""
-    from oracle.rows import ea_satellite_rows
+def _pair(p, q, n):
+    return p * n - p * (p + 1) // 2 + (q - p - 1)
+
+
+def cpu_oracle_sample(p, x, n_rows=6, seed=5, kind="EA", want_rows=False):
+    """Seconds per satellite sigma row (one vector) of the oracle on this workload.
+
+    With want_rows, also (X, packed indices of the rows in S, the rows' values)."""
+    from oracle.rows import ea_satellite_rows, ip_satellite_rows
     rng = np.random.default_rng(seed)
     o, v = p.nocc, p.nvir
-    N = v + o * v * (v - 1) // 2
+    if kind == "EA":
+        n1, N = v, v + o * v * (v - 1) // 2
+    else:
+        n1, N = o, o + (o * (o - 1) // 2) * v
     X = random_vectors(N, 1, seed=seed)
-    rows = []
+    rows, idx = [], []
     for _ in range(n_rows):
-        k = int(rng.integers(o))
-        d, e = sorted(rng.choice(v, 2, replace=False))
-        rows.append((k, int(d), int(e)))
+        if kind == "EA":
+            k = int(rng.integers(o))
+            d, e = sorted(rng.choice(v, 2, replace=False))
+            rows.append((k, int(d), int(e)))
+            idx.append(n1 + k * (v * (v - 1) // 2) + _pair(int(d), int(e), v))
+        else:
+            i, j = sorted(rng.choice(o, 2, replace=False))
+            a = int(rng.integers(v))
+            rows.append((int(i), int(j), a))
+            idx.append(n1 + _pair(int(i), int(j), o) * v + a)
+    fn = ea_satellite_rows if kind == "EA" else ip_satellite_rows
     t0 = time.perf_counter()
-    ea_satellite_rows(p.B, p.eps_occ, p.eps_vir, 3, x, X, rows)
+    R = fn(p.B, p.eps_occ, p.eps_vir, 3, x, X, rows)
     t = time.perf_counter() - t0
-    return t / n_rows, f"{n_rows} satellite rows of S = M X for one vector, each row from Eq. 43 integrals"
+    what = f"{n_rows} satellite rows of S = M X for one vector, each row from Eq. 43 integrals"
+    if want_rows:
+        return t / n_rows, what, (X, idx, R)
+    return t / n_rows, what
+
+
+def sampled_parity(ctx, sample, precisions):
+    """The GPU sigma of the sampled vector, in each precision, at the rows the
+    oracle computed: largest absolute difference and that over the largest
+    oracle row value."""
+    X, idx, R = sample
+    scale = float(np.abs(R).max())
+    out = {"rows": len(idx), "oracle_row_max": scale}
+    for prec in precisions:
+        S = np.asarray(ctx.sigma(X, prec))
+        err = float(np.abs(S[:, idx] - R).max())
+        out[prec] = {"max_abs_err": err, "rel": err / max(scale, 1e-300)}
+    return out
 
 
 def run_batch(args, cfgname):
@@ -404,10 +438,10 @@ def run_reference(args, cfgname):
     N = v + o * v * (v - 1) // 2
     sig_vecs_per_root = args.ref_sigma_vectors_per_root
     for _ in range(args.warmup):
-        cpu_oracle_sample(p, c["x"], n_rows=1)
+        cpu_oracle_sample(p, c["x"], n_rows=1, kind=c["kind"])
     ts = []
     for s in range(args.steps):
-        t_row, what = cpu_oracle_sample(p, c["x"], n_rows=args.ref_rows, seed=10 + s)
+        t_row, what = cpu_oracle_sample(p, c["x"], n_rows=args.ref_rows, seed=10 + s, kind=c["kind"])
         ts.append(t_row)
     t_row = float(np.mean(ts))
     value = t_row * N * sig_vecs_per_root
@@ -633,8 +667,14 @@ def main():
                    float(np.abs(np.asarray(om2) - np.asarray(ref_om)).max())}
 
     cpu = None
+    parity = None
     if rank == 0 and world == 1 and args.cpu_rows > 0:
-        t_row, what = cpu_oracle_sample(p, x, n_rows=args.cpu_rows)
+        t_row, what, sample = cpu_oracle_sample(p, x, n_rows=args.cpu_rows, kind=kind, want_rows=True)
+        try:
+            parity = sampled_parity(ctx, sample, ("fp64", args.mixed, "sliced"))
+        except Exception as exc:  # the check reports, it never stops the run
+            parity = {"error": str(exc)[:200]}
+        log("sampled parity", parity)
         per_root = np.mean([s["sigma_calls"] for s in stats]) / nroots
         N = ctx.N
         cpu = {"value": t_row * N * per_root, "unit": "s/root", "cores": os.cpu_count(), "kind": "oracle",
@@ -657,6 +697,7 @@ def main():
                   "rel_diff_mixed_vs_fp64": sig_rel, "rel_diff_sliced_vs_fp64": sig_rel_sliced,
                   "speedup_sliced": (sig["fp64"]["ms"] / sig["sliced"]["ms"]) if "sliced" in sig else None,
                   "vectors": nroots},
+        "sampled_parity": parity,
         "refine": args.refine,
         "fp64_davidson": fp64,
         "mixed_davidson": {"omega": [float(w) for w in om], "err64": [float(e) for e in e64],
