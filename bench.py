@@ -158,6 +158,28 @@ def cpu_oracle_sample(p, x, n_rows=6, seed=5, kind="EA", want_rows=False):
     return t / n_rows, what
 
 
+def ee_oracle_sample(p, order, x, dd_order, n_rows=1, seed=5):
+    """Seconds per EE doubles row (one vector) of the oracle on this workload,
+    with (X, packed indices of the rows in S, the rows' values)."""
+    from oracle.rows import ee_doubles_rows
+    rng = np.random.default_rng(seed)
+    o, v = p.nocc, p.nvir
+    n1, po, pv = o * v, o * (o - 1) // 2, v * (v - 1) // 2
+    X = random_vectors(n1 + po * pv, 1, seed=seed)
+    sel, idx = [], []
+    for _ in range(n_rows):
+        k, l = sorted(int(a) for a in rng.choice(o, 2, replace=False))
+        c, d = sorted(int(a) for a in rng.choice(v, 2, replace=False))
+        sel.append((k, l, c, d))
+        idx.append(n1 + _pair(k, l, o) * pv + _pair(c, d, v))
+    t0 = time.perf_counter()
+    R = ee_doubles_rows(p.B, p.eps_occ, p.eps_vir, order, x, X, sel, dd_order=dd_order)
+    t = time.perf_counter() - t0
+    what = (f"{n_rows} doubles rows of S = M X for one vector, each row from the oracle's term tables "
+            "with its indices fixed (operands assembled from B per row)")
+    return t / n_rows, what, (X, idx, R)
+
+
 def sampled_parity(ctx, sample, precisions):
     """The GPU sigma of the sampled vector, in each precision, at the rows the
     oracle computed: largest absolute difference and that over the largest
@@ -340,6 +362,18 @@ def run_ee(args, cfgname):
         sp = ctx.profile_read()
         ctx.profile(False)
         sig[prec] = {"ms": 1e3 * ts, "flops_timed_kernels": sum(e["flops"] for e in sp.values())}
+    cpu, parity = None, None
+    if args.cpu_rows > 0:
+        t_row, what, sample = ee_oracle_sample(p, cfg["order"], x, dd_order, n_rows=args.cpu_rows)
+        try:
+            parity = sampled_parity(ctx, sample, ("fp64", args.mixed, "sliced"))
+        except Exception as exc:  # the check reports, it never stops the run
+            parity = {"error": str(exc)[:200]}
+        log("sampled parity", parity)
+        per_root = st["sigma_calls"] / nroots
+        cpu = {"value": t_row * ctx.N * per_root, "unit": "s/root", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{what}; scaled by N={ctx.N} rows and {per_root:.1f} sigma vectors per root "
+                         "(as used by the GPU run)"}
     fns = None
     if cfg.get("fns_eta") is not None:
         ctx.profile(True)
@@ -419,7 +453,7 @@ def run_ee(args, cfgname):
                   "speedup_sliced": sig["fp64"]["ms"] / sig["sliced"]["ms"]},
         "refine": args.refine,
         "gradient": grad,
-        "init_s": init_s, "e2e": None, "cpu_baseline": None,
+        "init_s": init_s, "e2e": None, "cpu_baseline": cpu, "sampled_parity": parity,
     }
     print(json.dumps(line))
 
