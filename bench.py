@@ -124,10 +124,11 @@ def _pair(p, q, n):
     return p * n - p * (p + 1) // 2 + (q - p - 1)
 
 
-def cpu_oracle_sample(p, x, n_rows=6, seed=5, kind="EA", want_rows=False):
+def cpu_oracle_sample(p, x, n_rows=6, seed=5, kind="EA", want_rows=False, X=None):
     """Seconds per satellite sigma row (one vector) of the oracle on this workload.
 
-    With want_rows, also (X, packed indices of the rows in S, the rows' values)."""
+    With want_rows, also (X, packed indices of the rows in S, the rows' values);
+    X [1][N] may be given, else it is drawn."""
     from oracle.rows import ea_satellite_rows, ip_satellite_rows
     rng = np.random.default_rng(seed)
     o, v = p.nocc, p.nvir
@@ -135,7 +136,7 @@ def cpu_oracle_sample(p, x, n_rows=6, seed=5, kind="EA", want_rows=False):
         n1, N = v, v + o * v * (v - 1) // 2
     else:
         n1, N = o, o + (o * (o - 1) // 2) * v
-    X = random_vectors(N, 1, seed=seed)
+    X = random_vectors(N, 1, seed=seed) if X is None else np.asarray(X).reshape(1, N)
     rows, idx = [], []
     for _ in range(n_rows):
         if kind == "EA":
@@ -212,6 +213,7 @@ def run_batch(args, cfgname):
     tot = dict(init_s=0.0, solve_s=0.0, sig_ms=0.0, sig_flops=0.0, g_ms=0.0, g_flops=0.0, g_launch=0,
                batches=0, graph_launches=0, sigma_calls=0, sigma_calls_fp64=0, iters=[])
     omegas, errs, status_all = {}, {}, {}
+    batch_parity = []
     clocks = Clocks()
     clocks.start()
     for w in range(nw):
@@ -230,6 +232,26 @@ def run_batch(args, cfgname):
             # grouped tensor-core kernel alone (batches enqueued without a graph)
             b.use_graphs(False)
             b.sigma(Xs, "bf16x3", outs=Ss)
+            if w == 0 and args.cpu_rows > 0:
+                # one problem of each kind: its batched product against oracle rows of the same vector
+                seen = set()
+                for j, pr in enumerate(probs):
+                    if pr.kind in seen:
+                        continue
+                    seen.add(pr.kind)
+                    try:
+                        X0 = Xs[j][:1].cpu().numpy()
+                        S0 = Ss[j][:1].cpu().numpy()
+                        _, _, (_, idx, R) = cpu_oracle_sample(pr, pr.x, n_rows=args.cpu_rows, kind=pr.kind,
+                                                              want_rows=True, X=X0)
+                        err = float(np.abs(S0[:, idx] - R).max())
+                        scale = float(np.abs(R).max())
+                        batch_parity.append({"problem": ids[j], "kind": pr.kind, "nocc": pr.nocc, "nvir": pr.nvir,
+                                             "rows": len(idx), "bf16x3_max_abs_err": err,
+                                             "rel": err / max(scale, 1e-300)})
+                    except Exception as exc:  # the check reports, it never stops the run
+                        batch_parity.append({"problem": ids[j], "error": str(exc)[:200]})
+                log("batched sampled parity", batch_parity)
             i0 = b.info()
             for _ in range(3):
                 b.sigma(Xs, "bf16x3", outs=Ss)
@@ -281,7 +303,7 @@ def run_batch(args, cfgname):
         "config": {"workload": cfgname, "problems": nprob, "nroots": nroots, "tol_fp64_residual": tol,
                    "waves": nw, "sizes": "nocc U[10,40], nvir U[50,250], naux 6 nvir, IP even / EA odd, x 0.5",
                    "l2": "operators larger than L2"},
-        "clocks": clk,
+        "clocks": clk, "sampled_parity": batch_parity,
         "roofline": {"bound": "tensor", "kernel": "k_tc_grouped (all problems' coupling, ladder, ring jobs)",
                      "achieved": g_ach, "peak": peak, "unit": "TFLOP/s",
                      "frac": (g_ach / peak) if g_ach else None, "traffic": None,
