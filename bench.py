@@ -110,6 +110,35 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+THREE_M = ("zgemm", "gram", "combine")  # FP64 kernels whose complex products take 3 real products
+
+
+def fp64_peak(adcgpu):
+    """FP64 FMA peak of this GPU, measured now by the library's FMA probe
+    (TFLOP/s), with the nominal figure from the unit counts and clocks."""
+    try:
+        best = max(adcgpu.diag_fp64_peak(152 * b, 1 << 14)[0] for b in (4, 8))
+        return best, "measured (FP64 FMA probe, 16 independent chains per thread, this run)"
+    except Exception as exc:  # the probe reports, it never stops the run
+        log("fp64 probe failed", exc)
+        return 1.25, "nominal: 152 SMs x 2.07 GHz x 2 FP64 FMA/clk x 2"
+
+
+def alu_row(name, e, peak64, peak_kind):
+    """Roofline entry of an FP64 CUDA-core kernel: algorithmic rate (8 flops
+    per complex multiply-add) and the rate of the FP64 work it executes (6 per
+    complex multiply-add for the 3M products)."""
+    avg = e["total_ms"] / e["launches"]
+    alg = e["flops"] / e["launches"]
+    ach = alg / (avg * 1e-3) / 1e12
+    ex = 0.75 if name.split("/")[0].split("_")[0] in THREE_M else 1.0
+    return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
+            "frac": ach / peak64, "traffic": None, "peak_kind": f"fp64 FMA {peak64:.3f} TFLOP/s, {peak_kind}; "
+            "3M complex products execute 6 of the 8 algorithmic flops, so frac can reach 4/3",
+            "executed_frac": ex * ach / peak64, "flops_per_launch": alg, "avg_launch_ms": avg,
+            "launches": e["launches"]}
+
+
 def sigma_flops_formula(o, v, Q, k):
     """Algorithmic flops of one EA sigma block of k vectors as the library forms it
     (8 per complex multiply-add): coupling both ways (2 v n2 k), ladder over packed
@@ -124,31 +153,55 @@ def _pair(p, q, n):
     return p * n - p * (p + 1) // 2 + (q - p - 1)
 
 
-def cpu_oracle_sample(p, x, n_rows=6, seed=5, kind="EA", want_rows=False, X=None):
-    """Seconds per satellite sigma row (one vector) of the oracle on this workload.
+# Sigma vectors per root that the plain FP64 block Davidson (the CPU oracle's
+# algorithm, run on the GPU in FP64) spends on each workload to the bench's
+# residual tolerance; both oracle legs scale seconds per sigma row to seconds
+# per root with the same number. Measured: ea2x3, 302 FP64 sigma vectors for
+# 8 roots (tol 1e-5); the EE workloads use their mixed solves' counts.
+ORACLE_SIGMA_VECTORS_PER_ROOT = {"ea2x3_o40_v200_q1200": 37.75, "ee2x3_o30_v150_q900": 110.0,
+                                 "ee3_o60_v300_q1800": 40.0}
 
-    With want_rows, also (X, packed indices of the rows in S, the rows' values);
-    X [1][N] may be given, else it is drawn."""
-    from oracle.rows import ea_satellite_rows, ip_satellite_rows
+
+def pick_rows(kind, o, v, n_rows, seed):
+    """Seeded satellite (IP/EA) or doubles (EE) rows: (row tuples, packed indices in S)."""
     rng = np.random.default_rng(seed)
-    o, v = p.nocc, p.nvir
-    if kind == "EA":
-        n1, N = v, v + o * v * (v - 1) // 2
-    else:
-        n1, N = o, o + (o * (o - 1) // 2) * v
-    X = random_vectors(N, 1, seed=seed) if X is None else np.asarray(X).reshape(1, N)
     rows, idx = [], []
     for _ in range(n_rows):
         if kind == "EA":
             k = int(rng.integers(o))
             d, e = sorted(rng.choice(v, 2, replace=False))
             rows.append((k, int(d), int(e)))
-            idx.append(n1 + k * (v * (v - 1) // 2) + _pair(int(d), int(e), v))
-        else:
+            idx.append(v + k * (v * (v - 1) // 2) + _pair(int(d), int(e), v))
+        elif kind == "IP":
             i, j = sorted(rng.choice(o, 2, replace=False))
             a = int(rng.integers(v))
             rows.append((int(i), int(j), a))
-            idx.append(n1 + _pair(int(i), int(j), o) * v + a)
+            idx.append(o + _pair(int(i), int(j), o) * v + a)
+        else:
+            k, l = sorted(int(a) for a in rng.choice(o, 2, replace=False))
+            c, d = sorted(int(a) for a in rng.choice(v, 2, replace=False))
+            rows.append((k, l, c, d))
+            idx.append(o * v + _pair(k, l, o) * (v * (v - 1) // 2) + _pair(c, d, v))
+    return rows, idx
+
+
+def _dim(kind, o, v):
+    if kind == "EA":
+        return v + o * v * (v - 1) // 2
+    if kind == "IP":
+        return o + o * (o - 1) // 2 * v
+    return o * v + (o * (o - 1) // 2) * (v * (v - 1) // 2)
+
+
+def cpu_oracle_sample(p, x, n_rows=6, seed=5, kind="EA", want_rows=False, X=None):
+    """Seconds per satellite sigma row (one vector) of the oracle on this
+    workload, in this process. With want_rows, also (X, packed indices of the
+    rows in S, the rows' values); X [1][N] may be given, else it is drawn."""
+    from oracle.rows import ea_satellite_rows, ip_satellite_rows
+    o, v = p.nocc, p.nvir
+    N = _dim(kind, o, v)
+    X = random_vectors(N, 1, seed=seed) if X is None else np.asarray(X).reshape(1, N)
+    rows, idx = pick_rows(kind, o, v, n_rows, seed)
     fn = ea_satellite_rows if kind == "EA" else ip_satellite_rows
     t0 = time.perf_counter()
     R = fn(p.B, p.eps_occ, p.eps_vir, 3, x, X, rows)
@@ -159,26 +212,111 @@ def cpu_oracle_sample(p, x, n_rows=6, seed=5, kind="EA", want_rows=False, X=None
     return t / n_rows, what
 
 
-def ee_oracle_sample(p, order, x, dd_order, n_rows=1, seed=5):
-    """Seconds per EE doubles row (one vector) of the oracle on this workload,
-    with (X, packed indices of the rows in S, the rows' values)."""
-    from oracle.rows import ee_doubles_rows
-    rng = np.random.default_rng(seed)
-    o, v = p.nocc, p.nvir
-    n1, po, pv = o * v, o * (o - 1) // 2, v * (v - 1) // 2
-    X = random_vectors(n1 + po * pv, 1, seed=seed)
-    sel, idx = [], []
-    for _ in range(n_rows):
-        k, l = sorted(int(a) for a in rng.choice(o, 2, replace=False))
-        c, d = sorted(int(a) for a in rng.choice(v, 2, replace=False))
-        sel.append((k, l, c, d))
-        idx.append(n1 + _pair(k, l, o) * pv + _pair(c, d, v))
+# ---- the oracle on the host cores: one process per core (spawn start, so
+# that no process forks from one that has touched the GPU), one row per task
+_POOL = {}
+
+
+def _spec_problem(spec):
+    if spec[0] == "batch":
+        return batch_problems(spec[1], select=[spec[2]])[0]
+    return config_problem(spec[1])
+
+
+def _pool_init(spec, xseed):
+    p = _spec_problem(spec)
+    _POOL.update(p=p, X=random_vectors(_dim(p.kind, p.nocc, p.nvir), 1, seed=xseed))
+
+
+def _pool_row(task):
+    from oracle.rows import ea_satellite_rows, ee_doubles_rows, ip_satellite_rows
+    kind, order, x, dd_order, row = task
+    p, X = _POOL["p"], _POOL["X"]
     t0 = time.perf_counter()
-    R = ee_doubles_rows(p.B, p.eps_occ, p.eps_vir, order, x, X, sel, dd_order=dd_order)
-    t = time.perf_counter() - t0
-    what = (f"{n_rows} doubles rows of S = M X for one vector, each row from the oracle's term tables "
-            "with its indices fixed (operands assembled from B per row)")
-    return t / n_rows, what, (X, idx, R)
+    if kind == "EE":
+        R = ee_doubles_rows(p.B, p.eps_occ, p.eps_vir, order, x, X, [row], dd_order=dd_order)
+    else:
+        fn = ea_satellite_rows if kind == "EA" else ip_satellite_rows
+        R = fn(p.B, p.eps_occ, p.eps_vir, order, x, X, [row])
+    return np.asarray(R)[0, 0], time.perf_counter() - t0
+
+
+def _mem_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def _blas_name():
+    try:
+        cfg = np.show_config(mode="dicts")
+        b = cfg["Build Dependencies"]["blas"]
+        return f"{b.get('name')} {b.get('version')}"
+    except Exception:
+        return "unknown"
+
+
+def oracle_rows_pool(spec, kind, order, x, dd_order, n_rows, seed=5, xseed=5, workers=None):
+    """The oracle's sigma rows of one seeded vector on the host cores.
+
+    Worker processes (spawn) each rebuild the seeded problem and vector, then
+    compute rows, one single-threaded row per task (the row oracle is numpy
+    einsum loops; BLAS is held to one thread per process). Returns the sample:
+    X, packed row indices, row values [1][n_rows], the pool's wall time for the
+    rows, the mean seconds of one row inside a worker, and the worker count."""
+    import multiprocessing as mp
+    p_sizes = _spec_problem(spec) if spec[0] == "batch" else CONFIGS[spec[1]]
+    o = p_sizes.nocc if spec[0] == "batch" else p_sizes["nocc"]
+    v = p_sizes.nvir if spec[0] == "batch" else p_sizes["nvir"]
+    q = p_sizes.naux if spec[0] == "batch" else p_sizes["naux"]
+    cores = os.cpu_count() or 1
+    bytes_b = 16.0 * q * (o + v) ** 2
+    avail = _mem_available()
+    cap = cores if avail is None else max(1, int(avail // (4.0 * bytes_b)))
+    workers = max(1, min(workers or cores, cores, cap, n_rows))
+    rows, idx = pick_rows(kind, o, v, n_rows, seed)
+    env_keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(workers, initializer=_pool_init, initargs=(spec, xseed)) as pool:
+            # every worker has built its problem before the rows are timed
+            pool.map(time.sleep, [0.0] * workers, chunksize=1)
+            t0 = time.perf_counter()
+            res = pool.map(_pool_row, [(kind, order, x, dd_order, r) for r in rows], chunksize=1)
+            wall = time.perf_counter() - t0
+    finally:
+        for k, val in saved.items():
+            if val is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = val
+    X = random_vectors(_dim(kind, o, v), 1, seed=xseed)
+    R = np.array([[r[0] for r in res]])
+    return {"X": X, "idx": idx, "R": R, "wall_s": wall, "row_s": float(np.mean([r[1] for r in res])),
+            "workers": workers, "rows": n_rows}
+
+
+def cpu_baseline_of(sample, N, spr, spr_note, kind):
+    """cpu_baseline object: seconds per root of the oracle on the host cores,
+    from the pool's rows per second, N rows per sigma vector and spr sigma
+    vectors per root."""
+    per_row = sample["wall_s"] / sample["rows"]
+    what = ("doubles rows (the oracle's term tables with the row's indices fixed)" if kind == "EE"
+            else "satellite rows (integrals of each row from Eq. 43)")
+    return {"value": per_row * N * spr, "unit": "s/root", "cores": sample["workers"], "kind": "oracle",
+            "sample": (f"{sample['rows']} {what} of S = M X for one seeded vector, one single-threaded row per "
+                       f"process on {sample['workers']} processes, {sample['wall_s']:.1f} s wall; seconds per row "
+                       f"x N={N} rows x {spr:.2f} sigma vectors per root ({spr_note})"),
+            "row_s_one_thread": sample["row_s"], "threads_per_process": 1, "host_cores": os.cpu_count(),
+            "blas": _blas_name()}
 
 
 def sampled_parity(ctx, sample, precisions):
@@ -242,7 +380,7 @@ def run_batch(args, cfgname):
                     try:
                         X0 = Xs[j][:1].cpu().numpy()
                         S0 = Ss[j][:1].cpu().numpy()
-                        _, _, (_, idx, R) = cpu_oracle_sample(pr, pr.x, n_rows=args.cpu_rows, kind=pr.kind,
+                        _, _, (_, idx, R) = cpu_oracle_sample(pr, pr.x, n_rows=min(args.cpu_rows, 4), kind=pr.kind,
                                                               want_rows=True, X=X0)
                         err = float(np.abs(S0[:, idx] - R).max())
                         scale = float(np.abs(R).max())
@@ -386,16 +524,17 @@ def run_ee(args, cfgname):
         sig[prec] = {"ms": 1e3 * ts, "flops_timed_kernels": sum(e["flops"] for e in sp.values())}
     cpu, parity = None, None
     if args.cpu_rows > 0:
-        t_row, what, sample = ee_oracle_sample(p, cfg["order"], x, dd_order, n_rows=args.cpu_rows)
+        smp = oracle_rows_pool(("config", cfgname), "EE", cfg["order"], x, dd_order, args.cpu_rows)
         try:
-            parity = sampled_parity(ctx, sample, ("fp64", args.mixed, "sliced"))
+            parity = sampled_parity(ctx, (smp["X"], smp["idx"], smp["R"]), ("fp64", args.mixed, "sliced"))
         except Exception as exc:  # the check reports, it never stops the run
             parity = {"error": str(exc)[:200]}
         log("sampled parity", parity)
-        per_root = st["sigma_calls"] / nroots
-        cpu = {"value": t_row * ctx.N * per_root, "unit": "s/root", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{what}; scaled by N={ctx.N} rows and {per_root:.1f} sigma vectors per root "
-                         "(as used by the GPU run)"}
+        spr = ORACLE_SIGMA_VECTORS_PER_ROOT.get(cfgname)
+        note = "FP64 Davidson count of this workload"
+        if spr is None:
+            spr, note = st["sigma_calls"] / nroots, "this run's mixed solve"
+        cpu = cpu_baseline_of(smp, ctx.N, spr, note, "EE")
     fns = None
     if cfg.get("fns_eta") is not None:
         ctx.profile(True)
@@ -434,6 +573,7 @@ def run_ee(args, cfgname):
                 "rel_diff": abs(pred - fd) / max(1.0, abs(fd)), "fd_step": h, "weights": [float(w) for w in wts]}
     by = sorted(((k, e) for k, e in prof.items() if e["launches"] > 0), key=lambda t: -t[1]["total_ms"])
     pk, pk_kind = peaks()
+    peak64, peak64_kind = fp64_peak(adcgpu)
 
     def roof(name, e):
         avg = e["total_ms"] / e["launches"]
@@ -445,10 +585,7 @@ def run_ee(args, cfgname):
             return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None, "peak_kind": f"bf16 dense sustained ({pk_kind})",
                     "launches": e["launches"], "avg_launch_ms": avg}
-        ach = alg / (avg * 1e-3) / 1e12
-        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
-                "traffic": None, "peak_kind": "fp64 FMA nominal 1.25 TFLOP/s", "launches": e["launches"],
-                "avg_launch_ms": avg}
+        return alu_row(name, e, peak64, peak64_kind)
 
     by_kernel = [roof(k, e) for k, e in by]
     line = {
@@ -481,36 +618,44 @@ def run_ee(args, cfgname):
 
 
 def run_reference(args, cfgname):
-    """CPU oracle arm: each step evaluates a bounded sample of sigma rows."""
+    """CPU oracle arm: sigma rows of the workload on the host cores (one
+    single-threaded row per process, as in the CPU baseline of the GPU arm),
+    scaled to seconds per root with the same factor. The rows of all timed
+    steps run together on the pool; a step's time is the pool's wall time per
+    row times the rows of one step."""
     if cfgname in BATCH_CONFIGS:
-        # one EA problem of the batch stands for all of them (rows scaled by each problem's N)
-        sizes = batch_sizes(cfgname)
+        # one EA problem of the batch stands for all of them
+        spec = ("batch", cfgname, 1)
         p = batch_problems(cfgname, select=[1])[0]
         c = dict(kind="EA", order=3, x=BATCH_CONFIGS[cfgname]["x"], nroots=BATCH_CONFIGS[cfgname]["nroots"])
+        o, v, q = p.nocc, p.nvir, p.naux
     else:
+        spec = ("config", cfgname)
         c = CONFIGS[cfgname]
-        p = config_problem(cfgname)
-    o, v = p.nocc, p.nvir
-    N = v + o * v * (v - 1) // 2
-    sig_vecs_per_root = args.ref_sigma_vectors_per_root
+        o, v, q = c["nocc"], c["nvir"], c["naux"]
+    kind, dd_order = c["kind"], c.get("dd_order", 1)
+    N = _dim(kind, o, v)
+    spr = ORACLE_SIGMA_VECTORS_PER_ROOT.get(cfgname, 40.0)
+    note = ("FP64 Davidson count of this workload" if cfgname in ORACLE_SIGMA_VECTORS_PER_ROOT
+            else "assumed 40")
+    cores = os.cpu_count() or 1
+    # warm-up: the oracle modules imported, no timing
     for _ in range(args.warmup):
-        cpu_oracle_sample(p, c["x"], n_rows=1, kind=c["kind"])
-    ts = []
-    for s in range(args.steps):
-        t_row, what = cpu_oracle_sample(p, c["x"], n_rows=args.ref_rows, seed=10 + s, kind=c["kind"])
-        ts.append(t_row)
-    t_row = float(np.mean(ts))
-    value = t_row * N * sig_vecs_per_root
-    cores = os.cpu_count()
+        import oracle.rows  # noqa: F401
+    rows = max(args.steps, 1) * max(args.ref_rows, 1)
+    workers = min(cores, rows)
+    rows = -(-rows // workers) * workers  # whole rounds of the pool
+    smp = oracle_rows_pool(spec, kind, c["order"], c["x"], dd_order, rows, seed=10)
+    cpu = cpu_baseline_of(smp, N, spr, note, kind)
+    value = cpu["value"]
+    per_step_s = smp["wall_s"] / rows * max(args.ref_rows, 1)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/root", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_row * args.ref_rows,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_step_s,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": cfgname, "nocc": o, "nvir": v, "naux": p.naux,
-                                            "kind": c["kind"], "order": c["order"], "x": c["x"],
+            "data": "synthetic", "config": {"workload": cfgname, "nocc": o, "nvir": v, "naux": q,
+                                            "kind": kind, "order": c["order"], "x": c["x"],
                                             "nroots": c["nroots"]},
-            "cpu_baseline": {"value": value, "unit": "s/root", "cores": cores, "kind": "oracle",
-                             "sample": f"{what}; seconds per row x N={N} rows x {sig_vecs_per_root} sigma "
-                                       "vectors per root"},
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "s/root", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -532,9 +677,10 @@ def main():
     ap.add_argument("--e2e-setup", default="sliced", choices=["sliced", "fp64"],
                     help="IP/EA/EE: adc_init contractions of the end-to-end run")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-rows", type=int, default=1, help="reference arm: satellite rows per step (~20-35 s each)")
-    ap.add_argument("--ref-sigma-vectors-per-root", type=float, default=8.0)
-    ap.add_argument("--cpu-rows", type=int, default=1, help="CPU baseline: satellite rows timed (~20-35 s each)")
+    ap.add_argument("--ref-rows", type=int, default=1,
+                    help="reference arm: oracle rows per step (about 30 s of one core each)")
+    ap.add_argument("--cpu-rows", type=int, default=16,
+                    help="CPU baseline: oracle rows, run one per host core (about 30 s each)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -624,6 +770,7 @@ def main():
     value = ms_per_step / 1e3 / (nroots * world)
 
     pk, pk_kind = peaks()
+    peak64, peak64_kind = fp64_peak(adcgpu)
 
     def roofline_of(name, e):
         avg_ms = e["total_ms"] / e["launches"]
@@ -637,13 +784,7 @@ def main():
             return {"bound": "tensor", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None, "peak_kind": f"bf16 dense sustained ({pk_kind})",
                     "flops_per_launch": mma, "avg_launch_ms": avg_ms, "launches": e["launches"]}
-        ach = alg / (avg_ms * 1e-3) / 1e12
-        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": ach / 1.25, "traffic": None,
-                "peak_kind": "fp64 FMA 1.25 TFLOP/s (152 SMs x 2.07 GHz x 2 FMA/clk x 2); the complex products "
-                             "execute 6 of the 8 algorithmic flops (3M), so frac can reach 4/3",
-                "executed_frac": 0.75 * ach / 1.25 if name.startswith("zgemm") else ach / 1.25,
-                "flops_per_launch": alg, "avg_launch_ms": avg_ms, "launches": e["launches"]}
+        return alu_row(name, e, peak64, peak64_kind)
 
     by_kernel = sorted((roofline_of(k, e) for k, e in prof.items() if e["launches"] > 0),
                        key=lambda r: -r["avg_launch_ms"] * r["launches"])
@@ -725,17 +866,18 @@ def main():
     cpu = None
     parity = None
     if rank == 0 and world == 1 and args.cpu_rows > 0:
-        t_row, what, sample = cpu_oracle_sample(p, x, n_rows=args.cpu_rows, kind=kind, want_rows=True)
+        smp = oracle_rows_pool(("config", args.config), kind, order, x, 1, args.cpu_rows)
         try:
-            parity = sampled_parity(ctx, sample, ("fp64", args.mixed, "sliced"))
+            parity = sampled_parity(ctx, (smp["X"], smp["idx"], smp["R"]), ("fp64", args.mixed, "sliced"))
         except Exception as exc:  # the check reports, it never stops the run
             parity = {"error": str(exc)[:200]}
         log("sampled parity", parity)
-        per_root = np.mean([s["sigma_calls"] for s in stats]) / nroots
-        N = ctx.N
-        cpu = {"value": t_row * N * per_root, "unit": "s/root", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{what}; scaled by N={N} rows and {per_root:.1f} sigma vectors per root "
-                         "(as used by the GPU run)"}
+        spr = ORACLE_SIGMA_VECTORS_PER_ROOT.get(args.config)
+        note = "FP64 Davidson count of this workload"
+        if spr is None:
+            spr, note = np.mean([s["sigma_calls"] for s in stats]) / nroots, "this run's mixed solve"
+        cpu = cpu_baseline_of(smp, ctx.N, spr, note, kind)
+        cpu["gpu_mixed_sigma_vectors_per_root"] = float(np.mean([s["sigma_calls"] for s in stats]) / nroots)
 
     last = stats[-1]
     line = {

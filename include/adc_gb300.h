@@ -153,8 +153,10 @@ int adc_init(adc_ctx **ctx, const adc_c128 *B, int64_t naux,
 int adc_dims(const adc_ctx *ctx, int64_t *n1, int64_t *n2);
 
 /* S[r] = M X[r] for r < k (Eqs. 10-12). X, S: [k][N], host or device, not
- * overlapping. precision: ADC_PREC_FP64, ADC_PREC_BF16X3 or ADC_PREC_BF16X6. Uses scratch
- * device memory owned by the context (grown on demand). */
+ * overlapping. precision: ADC_PREC_FP64, ADC_PREC_BF16X3, ADC_PREC_BF16X6 or
+ * ADC_PREC_SLICED (the FP64-accurate product from exact BF16 digit products
+ * on the tensor cores). Uses scratch device memory owned by the context
+ * (grown on demand). */
 int adc_sigma(adc_ctx *ctx, const adc_c128 *X, adc_c128 *S, int64_t k,
               int precision);
 
@@ -166,7 +168,9 @@ int adc_sigma(adc_ctx *ctx, const adc_c128 *X, adc_c128 *S, int64_t k,
  * allocating library routine; every per-call intermediate lives in one
  * file-scope __device__ array of 64 MiB that each GPU loading the library
  * holds until the process exits.
- *   X, S   [k][N] device pointers (host pointers give ADC_ERR_ARG).
+ *   X, S   [k][N] device pointers on the context's device, which must be
+ *          the current device (host pointers, or memory or a current device
+ *          other than the one adc_init ran on, give ADC_ERR_ARG).
  *   Sizes whose intermediates exceed the array (2 k o v^2 complex elements
  *   for EA, 2 k o^2 v for IP, order 3) give ADC_ERR_ARG with the required
  *   size; call again with fewer vectors.

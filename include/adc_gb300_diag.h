@@ -55,6 +55,24 @@ int adc_profile_read(adc_ctx_opaque *ctx, adc_kernel_stat *out, int max, int *n)
  * ADC_ERR_STATE for a NULL context, ADC_ERR_ARG for NULL outputs. */
 int adc_memory(const adc_ctx_opaque *ctx, int64_t *in_use, int64_t *peak);
 
+/* Davidson block kernels alone (blockops.cu), against the FP64 GEMM:
+ *   which 0: gram, G[m][nb] = sum_k conj(A[m][k]) B[nb][k] for A [m][n],
+ *            B [nb][n] (the subspace projections V^H T);
+ *   which 1: combine, Y[nb][n] = sum_i C[i][r] V[i][n] for C [m][nb],
+ *            V [m][n] (Ritz vectors and Gram-Schmidt updates).
+ * Operands are seeded uniform random complex numbers. rel_err =
+ * ||out - out_zgemm||_F / ||out_zgemm||_F, ms = average time of one call over
+ * `reps` repetitions (CUDA events, after one warm-up). Allocates and frees
+ * its own device memory. */
+int adc_diag_blockops(int which, int64_t m, int64_t nb, int64_t n, uint64_t seed, int reps,
+                      double *rel_err, double *ms);
+
+/* FP64 FMA throughput of the device: every thread of a grid of `blocks`
+ * blocks of 256 threads runs 16 independent fused multiply-add chains of
+ * `iters` steps each (2 flops per FMA). tflops = flops / CUDA-event time. A
+ * plain probe for the FP64 roofline; changes no device setting. */
+int adc_diag_fp64_peak(int blocks, int64_t iters, double *tflops, double *ms);
+
 /* Number of CUDA kernels this library has launched in the process so far. */
 int64_t adc_launch_count(void);
 

@@ -1,6 +1,6 @@
 """Per-kernel totals of an ncu launch list (``--metrics gpu__time_duration.sum --csv``).
 
-Usage: python paper_2511_21640_gb300/ncu_launches.py launches.csv
+Usage: python ncu_launches.py launches.csv
 Prints one row per kernel: launches, total device time and share of the total.
 """
 import collections

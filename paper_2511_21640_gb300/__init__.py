@@ -114,6 +114,8 @@ def _load():
         "adc_strerror": (ctypes.c_char_p, [I]),
         "adc_last_error": (ctypes.c_char_p, [P]),
         "adc_diag_gemm": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "adc_diag_blockops": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "adc_diag_fp64_peak": (I, [I, I64, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_sigma_adjoint": (I, [P, P, P, I64, P, P, P, ctypes.POINTER(D)]),
         "adc_state_density": (I, [P, P, P]),
         "adc_transition_density": (I, [P, P, I64, P]),
@@ -626,10 +628,26 @@ def diag_gemm(which, M, N, K, seed=1, reps=3):
     return e.value, t.value
 
 
+def diag_blockops(which, m, nb, n, seed=1, reps=3):
+    """Accuracy and time of a Davidson block kernel (``adc_diag_blockops``; 0 gram, 1 combine): (rel_err, ms)."""
+    e, t = ctypes.c_double(), ctypes.c_double()
+    _check(lib.adc_diag_blockops(int(which), int(m), int(nb), int(n), int(seed), int(reps), ctypes.byref(e),
+                                 ctypes.byref(t)))
+    return e.value, t.value
+
+
+def diag_fp64_peak(blocks, iters):
+    """FP64 FMA throughput probe (``adc_diag_fp64_peak``): (TFLOP/s, ms)."""
+    f, t = ctypes.c_double(), ctypes.c_double()
+    _check(lib.adc_diag_fp64_peak(int(blocks), int(iters), ctypes.byref(f), ctypes.byref(t)))
+    return f.value, t.value
+
+
 def launch_count():
     """Kernels launched by the library in this process (``adc_launch_count``)."""
     return int(lib.adc_launch_count())
 
 
-__all__ = ["Context", "Batch", "batch_plan", "batch_solve", "AdcError", "diag_gemm", "launch_count", "lib", "LIB_PATH", "ADC_IP", "ADC_EA", "ADC_EE",
+__all__ = ["Context", "Batch", "batch_plan", "batch_solve", "AdcError", "diag_gemm", "diag_blockops", "diag_fp64_peak",
+           "launch_count", "lib", "LIB_PATH", "ADC_IP", "ADC_EA", "ADC_EE",
            "ADC_PREC_FP64", "ADC_PREC_BF16X3", "ADC_PREC_BF16X6"]

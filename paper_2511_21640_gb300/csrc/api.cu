@@ -155,6 +155,7 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
     c->dd_order = (c->opts.dd_order == 0) ? 0 : 1;
     c->N = c->n1 + c->n2;
     c->ex.mem_limit = c->opts.mem_limit;
+    ADC_CUDA(cudaGetDevice(&c->dev));
     if (c->opts.stream) {
       c->ex.stream = (cudaStream_t)c->opts.stream;
     } else {

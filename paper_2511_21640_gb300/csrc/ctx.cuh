@@ -15,6 +15,7 @@ struct BatchCoord;  // cross-problem sigma batching (batch.cu)
 struct adc_ctx {
   adc::Exec ex;
   bool own_stream = false;
+  int dev = -1;  // CUDA device that was current at adc_init (holds every buffer)
   int kind = 0, order = 2;
   double x = 0.0;   // the x of ADC(2)+x(3); 0 for order 2
   int64_t o = 0, v = 0, Q = 0, nmo = 0, n1 = 0, n2 = 0, N = 0;

@@ -6,6 +6,7 @@
 #include "ctx.cuh"
 #include "tc_gemm.cuh"
 #include "tc_slice.cuh"
+#include "blockops.cuh"
 #include "../../include/adc_gb300_diag.h"
 
 using namespace adc;
@@ -237,3 +238,110 @@ extern "C" int adc_profile_read(adc_ctx *c, adc_kernel_stat *out, int max, int *
 }
 
 extern "C" int64_t adc_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+namespace {
+// 16 independent FMA chains per thread; the result feeds an output so that
+// nothing is removed by the compiler
+__global__ void __launch_bounds__(256) k_fp64_fma(double *out, int64_t iters, double m, double c) {
+  double a[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = (double)(threadIdx.x + j) * 1e-3;
+  for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = fma(a[j], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) s += a[j];
+  if (s == 12345.678) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+}  // namespace
+
+extern "C" int adc_diag_fp64_peak(int blocks, int64_t iters, double *tflops, double *ms) {
+  if (blocks < 1 || iters < 1 || !tflops || !ms) return ADC_ERR_ARG;
+  Exec ex;
+  try {
+    ADC_CUDA(cudaStreamCreateWithFlags(&ex.stream, cudaStreamNonBlocking));
+    {
+      DBuf out(ex, (size_t)blocks * 256 * sizeof(double));
+      k_fp64_fma<<<blocks, 256, 0, ex.stream>>>(out.d(), std::min<int64_t>(iters, 64), 0.999999, 1e-7);
+      ADC_CHECK_LAUNCH();
+      cudaEvent_t e0, e1;
+      ADC_CUDA(cudaEventCreate(&e0));
+      ADC_CUDA(cudaEventCreate(&e1));
+      ADC_CUDA(cudaEventRecord(e0, ex.stream));
+      k_fp64_fma<<<blocks, 256, 0, ex.stream>>>(out.d(), iters, 0.999999, 1e-7);
+      ADC_CHECK_LAUNCH();
+      ADC_CUDA(cudaEventRecord(e1, ex.stream));
+      ADC_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      *ms = t;
+      *tflops = 2.0 * 16.0 * (double)iters * blocks * 256.0 / (t * 1e-3) / 1e12;
+    }
+    cudaStreamSynchronize(ex.stream);
+    cudaStreamDestroy(ex.stream);
+    return ADC_OK;
+  } catch (const Error &e) {
+    if (ex.stream) { cudaStreamSynchronize(ex.stream); cudaStreamDestroy(ex.stream); }
+    fprintf(stderr, "adc_diag_fp64_peak: %s\n", e.what());
+    return e.code;
+  }
+}
+
+extern "C" int adc_diag_blockops(int which, int64_t m, int64_t nb, int64_t n, uint64_t seed, int reps,
+                                 double *rel_err, double *ms) {
+  if (which < 0 || which > 1 || m < 1 || nb < 1 || n < 1 || reps < 1 || m > 1024 || nb > 1024) return ADC_ERR_ARG;
+  Exec ex;
+  try {
+    ADC_CUDA(cudaStreamCreateWithFlags(&ex.stream, cudaStreamNonBlocking));
+    {
+      // gram: A [m][n], B [nb][n], out [m][nb]; combine: C [m][nb], V [m][n], out [nb][n]
+      const int64_t na = (which == 0) ? m * n : m * nb;
+      const int64_t nbb = (which == 0) ? nb * n : m * n;
+      const int64_t no = (which == 0) ? m * nb : nb * n;
+      DBuf A = cbuf(ex, na), B = cbuf(ex, nbb), C = cbuf(ex, no), R = cbuf(ex, no);
+      DBuf acc(ex, 2 * sizeof(double));
+      k_fill_random<<<grid1d(na, 256), 256, 0, ex.stream>>>(A.c(), na, seed);
+      k_fill_random<<<grid1d(nbb, 256), 256, 0, ex.stream>>>(B.c(), nbb, seed + 7);
+      ADC_CHECK_LAUNCH();
+      if (which == 0)
+        zgemm(ex, m, nb, n, 1, C1(), A.c(), 0, n, 1, true, B.c(), 0, 1, n, false, C0(), R.c(), 0, nb, 1);
+      else
+        zgemm(ex, nb, n, m, 1, C1(), A.c(), 0, 1, nb, false, B.c(), 0, n, 1, false, C0(), R.c(), 0, n, 1);
+      auto run = [&]() {
+        if (which == 0) gram(ex, A.c(), n, (int)m, B.c(), n, (int)nb, n, C1(), C.c(), nb);
+        else combine(ex, A.c(), nb, (int)m, (int)nb, B.c(), n, n, C1(), C0(), C.c(), n);
+      };
+      run();
+      cudaEvent_t e0, e1;
+      ADC_CUDA(cudaEventCreate(&e0));
+      ADC_CUDA(cudaEventCreate(&e1));
+      ADC_CUDA(cudaEventRecord(e0, ex.stream));
+      for (int r = 0; r < reps; ++r) run();
+      ADC_CUDA(cudaEventRecord(e1, ex.stream));
+      ADC_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (ms) *ms = t / reps;
+      fill_zero(ex, acc.p, acc.bytes);
+      k_diff<<<256, 256, 0, ex.stream>>>(C.c(), R.c(), no, acc.d());
+      ADC_CHECK_LAUNCH();
+      double h[2];
+      ADC_CUDA(cudaMemcpyAsync(h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, ex.stream));
+      ADC_CUDA(cudaStreamSynchronize(ex.stream));
+      if (rel_err) *rel_err = std::sqrt(h[0] / std::max(h[1], 1e-300));
+    }
+    cudaStreamSynchronize(ex.stream);
+    cudaStreamDestroy(ex.stream);
+    return ADC_OK;
+  } catch (const Error &e) {
+    if (ex.stream) { cudaStreamSynchronize(ex.stream); cudaStreamDestroy(ex.stream); }
+    fprintf(stderr, "adc_diag_blockops: %s\n", e.what());
+    return e.code;
+  }
+}

@@ -41,14 +41,24 @@ cplx *scratch_address() {
   return g_scratch_addr[dev];
 }
 
-bool device_ptr(const void *p) {
+// device that holds p (device or managed memory), -1 for host memory or an unknown pointer
+int pointer_device(const void *p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return -1;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? a.device : -1;
 }
+
+// profiling (per-kernel CUDA events) stays off for the call and is put back on
+// every exit, thrown errors included
+struct ProfOff {
+  Exec &ex;
+  bool prev;
+  explicit ProfOff(Exec &e) : ex(e), prev(e.prof) { e.prof = false; }
+  ~ProfOff() { ex.prof = prev; }
+};
 }  // namespace
 
 // Same terms and order as sigma_fp64 (Sec. 2.1 Eqs. 10-12), scratch from the static array.
@@ -103,15 +113,28 @@ extern "C" int adc_sigma_noalloc(adc_ctx *c, const adc_c128 *X, adc_c128 *S, int
   if (k == 0) return ADC_OK;
   try {
     if (c->kind == ADC_EE) throw Error(ADC_ERR_UNSUPPORTED, "adc_sigma_noalloc covers IP and EA");
-    if (!device_ptr(X) || !device_ptr(S))
+    int cur = -1;
+    ADC_CUDA(cudaGetDevice(&cur));
+    if (cur != c->dev)
+      throw Error(ADC_ERR_ARG, "adc_sigma_noalloc: device " + std::to_string(cur) +
+                                   " is current, the context lives on device " + std::to_string(c->dev));
+    const int dx = pointer_device(X), ds = pointer_device(S);
+    if (dx < 0 || ds < 0)
       throw Error(ADC_ERR_ARG, "adc_sigma_noalloc takes device pointers only (a host copy would allocate)");
-    const bool prof = c->ex.prof;
-    c->ex.prof = false;  // no event bookkeeping on this path
+    if (dx != c->dev || ds != c->dev)
+      throw Error(ADC_ERR_ARG, "adc_sigma_noalloc: X is on device " + std::to_string(dx) + ", S on device " +
+                                   std::to_string(ds) + ", the context on device " + std::to_string(c->dev));
+    ProfOff off(c->ex);  // no event bookkeeping on this path
     sigma_fp64_noalloc(c, (const cplx *)X, (cplx *)S, k);
-    c->ex.prof = prof;
     return ADC_OK;
   } catch (const Error &e) {
     c->err = e.what();
     return e.code;
+  } catch (const std::bad_alloc &e) {
+    c->err = e.what();
+    return ADC_ERR_OOM;
+  } catch (const std::exception &e) {
+    c->err = e.what();
+    return ADC_ERR_CUDA;
   }
 }

@@ -47,6 +47,18 @@ def test_fp64_gemm(gpu, M, N, K):
     assert err < 1e-14
 
 
+@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("m,nb,n", [(1, 1, 1), (8, 8, 4096), (13, 5, 20011), (40, 8, 70000), (64, 16, 33333),
+                                     (97, 3, 5000), (33, 1, 1234567), (200, 12, 777)])
+def test_davidson_block_kernels(gpu, which, m, nb, n):
+    """The Davidson's FP64 block kernels (projections V^H T, 0; subspace
+    combinations sum_i C[i][r] V[i], 1) equal the FP64 GEMM on ragged shapes:
+    tiles of the short indices cut off, long vectors that are no multiple of
+    the staged length, a single element."""
+    err, ms = gpu.diag_blockops(which, m, nb, n, seed=11, reps=1)
+    assert err < 1e-13, (which, m, nb, n, err)
+
+
 @pytest.mark.parametrize("M,N,K", [(128, 16, 64), (200, 40, 1000), (129, 130, 70), (1000, 300, 5000),
                                    (64, 8, 20000)])
 def test_bf16x3_gemm(gpu, M, N, K):

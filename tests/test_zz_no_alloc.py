@@ -3,7 +3,9 @@ GPU memory during the call (their device memory belongs to another
 allocator, or cudaMalloc would stall or fail them mid-run). The entry point
 keeps its intermediates in a fixed __device__ array instead; its results must
 equal adc_sigma's FP64 results on consecutive calls (the array is reused, so
-a second call must not see stale data from the first)."""
+a second call must not see stale data from the first). On tiny IP and EA
+problems they must also equal the CPU oracle's explicit matrix times X, so a
+fault shared by both GPU entry points cannot hide behind their agreement."""
 import ctypes
 
 import numpy as np
@@ -13,6 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from synthetic import make_problem, random_vectors  # noqa: E402
+from oracle import adc as oadc  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -62,3 +65,20 @@ def test_noalloc_rejects_host_pointers_and_oversize(gpu):
         S = torch.zeros_like(X)
         assert _noalloc(gpu, ctx, X, S) == -1
         assert b"scratch" in gpu.lib.adc_last_error(ctx._h)
+
+
+@pytest.mark.parametrize("kind,o,v,Q,x", [("IP", 4, 7, 9, 1.0), ("EA", 3, 8, 10, 0.5)])
+def test_noalloc_matches_oracle_explicit_matrix(gpu, kind, o, v, Q, x):
+    p = make_problem(o, v, Q, seed=43, sigma=0.1)
+    M = oadc.explicit_matrix(kind, 3, x, p.B, p.eps_occ, p.eps_vir)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=3, x=x) as ctx:
+        assert ctx.N == M.shape[0]
+        for call, seed in enumerate((5, 6)):
+            Xh = random_vectors(ctx.N, 2, seed=seed)
+            ref = Xh @ M.T
+            X = torch.from_numpy(Xh).cuda()
+            S = torch.full_like(X, complex(np.nan, np.nan))
+            assert _noalloc(gpu, ctx, X, S) == 0, gpu.lib.adc_last_error(ctx._h)
+            got = S.cpu().numpy()
+            err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+            assert err.max() < 1e-12, (call, err)
