@@ -677,6 +677,8 @@ def main():
     ap.add_argument("--e2e-setup", default="sliced", choices=["sliced", "fp64"],
                     help="IP/EA/EE: adc_init contractions of the end-to-end run")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--max-subspace", type=int, default=0, help="Davidson subspace limit (0: the library's default)")
+    ap.add_argument("--block", type=int, default=0, help="Davidson block size (0: the number of roots)")
     ap.add_argument("--ref-rows", type=int, default=1,
                     help="reference arm: oracle rows per step (about 30 s of one core each)")
     ap.add_argument("--cpu-rows", type=int, default=16,
@@ -725,7 +727,8 @@ def main():
     ev = torch.from_numpy(p.eps_vir).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctx = adcgpu.Context(B, eo, ev, kind=kind, order=order, x=x, stream="torch", refine=args.refine)
+    ctx = adcgpu.Context(B, eo, ev, kind=kind, order=order, x=x, stream="torch", refine=args.refine,
+                         max_subspace=args.max_subspace, block=args.block)
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
     log(f"init {init_s:.1f} s, N = {ctx.N}")
@@ -849,7 +852,7 @@ def main():
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         with adcgpu.Context(Bh, eoh, evh, kind=kind, order=order, x=x, refine=args.refine,
-                            setup=args.e2e_setup) as c2:
+                            setup=args.e2e_setup, max_subspace=args.max_subspace, block=args.block) as c2:
             t3 = time.perf_counter()
             om2, _, e2, st2, rc2 = c2.davidson(nroots, tol=tol, max_iter=300, precision=args.mixed,
                                                want_vectors=False)
@@ -888,6 +891,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.config, "kind": kind, "order": order, "x": x, "nocc": o, "nvir": v, "naux": Q,
                    "nroots": nroots, "tol_fp64_residual": tol, "N": ctx.N, "replicas": world,
+                   "max_subspace": args.max_subspace, "block": args.block,
                    "l2": "operators larger than L2 (packed <ab||cd> 6.3 GB FP64, 3.2 GB per BF16 plane)"},
         "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "roofline_tensor_core": roof_tc,
         "roofline_by_kernel": by_kernel,

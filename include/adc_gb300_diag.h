@@ -55,6 +55,24 @@ int adc_profile_read(adc_ctx_opaque *ctx, adc_kernel_stat *out, int max, int *n)
  * ADC_ERR_STATE for a NULL context, ADC_ERR_ARG for NULL outputs. */
 int adc_memory(const adc_ctx_opaque *ctx, int64_t *in_use, int64_t *peak);
 
+/* Test hook for the failure path of the tensor-core kernels: sets the limit
+ * (nanoseconds of %globaltimer) of their pipeline waits on the current device,
+ * 0 = the default of 2 s. With a limit far below a kernel's run time a wait
+ * gives up: the kernel records the error, waits (with its own fixed 2 s
+ * limit) for the copies and MMAs it has in flight, frees its tensor memory
+ * and returns, and the call that launched it returns ADC_ERR_TIMEOUT. Affects
+ * every context of the process on that device until it is set again. */
+int adc_diag_set_wait_ns(uint64_t ns);
+
+/* Routes of the complex products adc_init issued for this context: how many
+ * ran as the sliced tensor-core product (opts.setup = ADC_PREC_SLICED, inner
+ * size at least 512 and at least 2^24 flops) and how many on the FP64 CUDA
+ * cores, with their algorithmic flops (8 per complex multiply-add). Host-side
+ * counters only. ADC_ERR_STATE for a NULL context, ADC_ERR_ARG for NULL
+ * outputs. */
+int adc_setup_routes(const adc_ctx_opaque *ctx, int64_t *n_sliced, int64_t *n_fp64, double *flops_sliced,
+                     double *flops_fp64);
+
 /* Davidson block kernels alone (blockops.cu), against the FP64 GEMM:
  *   which 0: gram, G[m][nb] = sum_k conj(A[m][k]) B[nb][k] for A [m][n],
  *            B [nb][n] (the subspace projections V^H T);

@@ -116,6 +116,7 @@ def _load():
         "adc_diag_gemm": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_diag_blockops": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_diag_fp64_peak": (I, [I, I64, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "adc_diag_set_wait_ns": (I, [ctypes.c_uint64]),
         "adc_sigma_adjoint": (I, [P, P, P, I64, P, P, P, ctypes.POINTER(D)]),
         "adc_state_density": (I, [P, P, P]),
         "adc_transition_density": (I, [P, P, I64, P]),
@@ -123,6 +124,7 @@ def _load():
         "adc_spectroscopic_amplitudes": (I, [P, P, I64, P]),
         "adc_state_pair_density": (I, [P, P, P, I64, P]),
         "adc_memory": (I, [P, P, P]),
+        "adc_setup_routes": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_cholesky": (I, [P, I64, D, I64, P, P, ctypes.POINTER(I64)]),
         "adc_cholesky_mo": (I, [P, I64, I64, P, I64, P]),
         "adc_ssfns_density": (I, [P, P, D, P, P, ctypes.POINTER(I64), P, P]),
@@ -376,6 +378,14 @@ class Context:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(lib.adc_memory(self._h, ctypes.byref(a), ctypes.byref(b)), self._h)
         return {"in_use": a.value, "peak": b.value}
+
+    def setup_routes(self):
+        """Products adc_init ran as the sliced tensor-core product and on the FP64 cores (``adc_setup_routes``)."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        fa, fb = ctypes.c_double(), ctypes.c_double()
+        _check(lib.adc_setup_routes(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(fa), ctypes.byref(fb)),
+               self._h)
+        return {"n_sliced": a.value, "n_fp64": b.value, "flops_sliced": fa.value, "flops_fp64": fb.value}
 
     def spectroscopic_amplitudes(self, Y):
         """Spectroscopic amplitudes [k][nmo] of IP/EA vectors Y [k][N] (``adc_spectroscopic_amplitudes``)."""

@@ -197,9 +197,15 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
     }
     // the setup's large contractions as the sliced tensor-core product when asked for
     c->ex.sliced_bits = (c->opts.setup == ADC_PREC_SLICED) ? 48 : 0;
+    c->ex.n_sliced = c->ex.n_fp64 = 0;
+    c->ex.flops_sliced = c->ex.flops_fp64 = 0.0;
     if (kind == ADC_EE) setup_ee(c);
     else setup_operators(c);
     c->ex.sliced_bits = 0;
+    c->setup_n[0] = c->ex.n_sliced;
+    c->setup_n[1] = c->ex.n_fp64;
+    c->setup_flops[0] = c->ex.flops_sliced;
+    c->setup_flops[1] = c->ex.flops_fp64;
     *out = c;
     return ADC_OK;
   } catch (const adc::Error &e) {

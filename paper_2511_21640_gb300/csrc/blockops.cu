@@ -1,95 +1,171 @@
 // FP64 block kernels of the Davidson solver for "tall-skinny" operands: a
 // handful of long vectors (length N, up to 10^8) against a subspace of at most
-// a few hundred. A general GEMM tile (64 x 64) would waste most of its FP64
-// throughput on such shapes; these kernels keep every loaded vector element
-// busy for all the short indices it meets.
+// a few hundred. On GB300 the FP64 units execute two fused multiply-adds per
+// clock per SM, so these products are bound by the FP64 pipe, never by HBM
+// (about 3 flops per byte against a ridge near 0.2): the only thing that
+// matters is that every issued FP64 operation is useful. The tile shapes are
+// therefore chosen per call from the actual numbers of rows on both sides, so
+// that no FMA is spent on padding, and the K dimension is split across the
+// threads of a CTA (reduced by warp shuffles) instead of padding the tile.
+//
+// Complex products use three real products (3M): for conj(a) b,
+//   T1 = ar br, T2 = ai bi, T3 = (ar - ai)(br + bi),
+//   Re = T1 + T2, Im = T3 - T1 + T2,
+// with the sums ar - ai and br + bi formed once per staged element.
+#include <algorithm>
+#include <climits>
+
 #include "blockops.cuh"
 
 namespace adc {
 
 namespace {
 
-constexpr int GK = 16;   // K staged per step (gram)
+// ---------------------------------------------------------------- gram
+// smallest stride >= g (in doubles) with stride % q == r
+__host__ __device__ constexpr int stride_mod(int g, int q, int r) { return g + ((r - g % q) + q) % q; }
 
-// part[chunk][a][b] = sum_{k in chunk} conj(A[a][k]) B[b][k], GA rows of A
-// (64, or 32 for short subspaces) and GB rows of B per CTA. Three FP64
-// products per complex product (3M): with a' = conj(a), T1 = a'r br,
-// T2 = a'i bi, T3 = (a'r + a'i)(br + bi); the sums are formed once per staged
-// element.
-template <int GA, int GB>
+// part[chunk][a][b] = sum_{k in chunk} conj(A[a][k]) B[b][k] for one (GA x GB)
+// output tile per CTA. 256 threads: TA x TB register tiles of RA x RB outputs
+// (rows a0 + ta + TA i, columns b0 + tb + TB j), and KS = 256 / (TA TB)
+// adjacent lanes per register tile, each taking every KS-th staged k; their
+// sums meet by warp shuffles at the end. The staged rows are padded (in
+// doubles) so that the 16 lanes of a half-warp, which read from KS different
+// k rows, fall on distinct banks: an odd stride when a half-warp is one
+// register tile (KS >= 16), 2 mod 4 when it is two (KS = 8), 4 mod 8 when it
+// is four (KS = 4); the B side, read by one column group, takes an odd stride.
+template <int GA, int GB, int RA, int RB, int GK>
 __global__ void __launch_bounds__(256)
 k_gram(const cplx *__restrict__ A, int64_t lda, int na, const cplx *__restrict__ B, int64_t ldb, int nb,
        int64_t n, int64_t chunk, cplx *part) {
-  constexpr int NG = 256 / GA;  // groups of threads sharing a row of A
-  constexpr int PB = GB / NG;   // b rows per thread
-  __shared__ double Ar[GK][GA + 1], Ai[GK][GA + 1], As[GK][GA + 1];
-  __shared__ double Br[GK][GB + 1], Bi[GK][GB + 1], Bs[GK][GB + 1];
+  constexpr int TA = GA / RA, TB = GB / RB, KS = 256 / (TA * TB);
+  static_assert(TA * TB * KS == 256 && KS >= 4 && KS <= 32 && GK % KS == 0 && TA >= 8, "gram tile");
+  constexpr int SA = KS >= 16 ? stride_mod(GA, 2, 1) : KS == 8 ? stride_mod(GA, 4, 2) : stride_mod(GA, 8, 4);
+  constexpr int SB = stride_mod(GB, 2, 1);
+  static_assert(3 * GK * (SA + SB) * 8 <= 48 * 1024, "gram staging exceeds 48 KB");
+  __shared__ double sA[3][GK * SA];  // re, im, re - im of conj-side rows
+  __shared__ double sB[3][GK * SB];  // re, im, re + im
   const int t = threadIdx.x;
-  const int al = t % GA, bg = t / GA;
+  const int ks = t % KS, tile = t / KS;
+  const int ta = tile % TA, tb = tile / TA;
   const int a0 = blockIdx.y * GA, b0 = blockIdx.z * GB;
   const int64_t k_beg = (int64_t)blockIdx.x * chunk;
   const int64_t k_end = min(n, k_beg + chunk);
-  double t1[PB], t2[PB], t3[PB];
+  double t1[RA][RB], t2[RA][RB], t3[RA][RB];
 #pragma unroll
-  for (int j = 0; j < PB; ++j) t1[j] = t2[j] = t3[j] = 0.0;
+  for (int i = 0; i < RA; ++i)
+#pragma unroll
+    for (int j = 0; j < RB; ++j) t1[i][j] = t2[i][j] = t3[i][j] = 0.0;
   for (int64_t k0 = k_beg; k0 < k_end; k0 += GK) {
-#pragma unroll
-    for (int s = 0; s < (GA * GK) / 256; ++s) {
-      const int e = t + 256 * s;
+    for (int e = t; e < GA * GK; e += 256) {
       const int ai = e / GK, kk = e % GK;
       const int64_t k = k0 + kk;
       cplx v = cmake(0.0, 0.0);
       if (a0 + ai < na && k < k_end) v = A[(int64_t)(a0 + ai) * lda + k];
-      Ar[kk][ai] = v.x;
-      Ai[kk][ai] = -v.y;
-      As[kk][ai] = v.x - v.y;
+      sA[0][kk * SA + ai] = v.x;
+      sA[1][kk * SA + ai] = v.y;
+      sA[2][kk * SA + ai] = v.x - v.y;
     }
     for (int e = t; e < GB * GK; e += 256) {
       const int bi = e / GK, kk = e % GK;
       const int64_t k = k0 + kk;
       cplx v = cmake(0.0, 0.0);
       if (b0 + bi < nb && k < k_end) v = B[(int64_t)(b0 + bi) * ldb + k];
-      Br[kk][bi] = v.x;
-      Bi[kk][bi] = v.y;
-      Bs[kk][bi] = v.x + v.y;
+      sB[0][kk * SB + bi] = v.x;
+      sB[1][kk * SB + bi] = v.y;
+      sB[2][kk * SB + bi] = v.x + v.y;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < GK; ++kk) {
-      const double ar = Ar[kk][al], ai = Ai[kk][al], as = As[kk][al];
+    for (int kk = ks; kk < GK; kk += KS) {
+      double ar[RA], ai[RA], as[RA], br[RB], bi[RB], bs[RB];
 #pragma unroll
-      for (int j = 0; j < PB; ++j) {
-        const int bj = bg * PB + j;
-        t1[j] = fma(ar, Br[kk][bj], t1[j]);
-        t2[j] = fma(ai, Bi[kk][bj], t2[j]);
-        t3[j] = fma(as, Bs[kk][bj], t3[j]);
+      for (int i = 0; i < RA; ++i) {
+        ar[i] = sA[0][kk * SA + ta + TA * i];
+        ai[i] = sA[1][kk * SA + ta + TA * i];
+        as[i] = sA[2][kk * SA + ta + TA * i];
       }
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        br[j] = sB[0][kk * SB + tb + TB * j];
+        bi[j] = sB[1][kk * SB + tb + TB * j];
+        bs[j] = sB[2][kk * SB + tb + TB * j];
+      }
+#pragma unroll
+      for (int i = 0; i < RA; ++i)
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+          t1[i][j] = fma(ar[i], br[j], t1[i][j]);
+          t2[i][j] = fma(ai[i], bi[j], t2[i][j]);
+          t3[i][j] = fma(as[i], bs[j], t3[i][j]);
+        }
     }
     __syncthreads();
   }
-  const int a = a0 + al;
-  if (a < na) {
+  // sum over the KS lanes of each register tile
 #pragma unroll
-    for (int j = 0; j < PB; ++j) {
-      const int b = b0 + bg * PB + j;
-      if (b < nb) part[((int64_t)blockIdx.x * na + a) * nb + b] = cmake(t1[j] - t2[j], t3[j] - t1[j] - t2[j]);
+  for (int i = 0; i < RA; ++i)
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+      double re = t1[i][j] + t2[i][j];
+      double im = t3[i][j] - t1[i][j] + t2[i][j];
+#pragma unroll
+      for (int off = KS / 2; off > 0; off >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, off);
+        im += __shfl_xor_sync(0xffffffffu, im, off);
+      }
+      const int a = a0 + ta + TA * i, b = b0 + tb + TB * j;
+      if (ks == 0 && a < na && b < nb) part[((int64_t)blockIdx.x * na + a) * nb + b] = cmake(re, im);
     }
-  }
 }
 
-__global__ void k_gram_reduce(const cplx *__restrict__ part, int nchunk, int na, int nb, cplx alpha, cplx *G,
-                              int64_t ldg) {
+// G[a][b] = alpha sum_c part[c][a][b]; with trans, part holds the transposed
+// product (part[c][b][a] = sum conj(B_b) A_a) and G[a][b] = alpha conj(.)
+__global__ void k_gram_reduce(const cplx *__restrict__ part, int nchunk, int na, int nb, int trans, cplx alpha,
+                              cplx *G, int64_t ldg) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= na * nb) return;
+  const int a = idx / nb, b = idx % nb;
+  const int src = trans ? b * na + a : idx;
   cplx s = cmake(0.0, 0.0);
-  for (int c = 0; c < nchunk; ++c) s = cadd(s, part[(int64_t)c * na * nb + idx]);
-  G[(int64_t)(idx / nb) * ldg + idx % nb] = cmul(alpha, s);
+  for (int c = 0; c < nchunk; ++c) s = cadd(s, part[(int64_t)c * na * nb + src]);
+  if (trans) s = cconj(s);
+  G[(int64_t)a * ldg + b] = cmul(alpha, s);
 }
 
-constexpr int CI = 64;  // subspace rows staged per step (combine)
+typedef void (*GramFn)(const cplx *, int64_t, int, const cplx *, int64_t, int, int64_t, int64_t, cplx *);
+
+struct GramCfg {
+  int ga, gb, gk;
+  GramFn fn;
+};
+
+// register tiles: RB = 4 for 16 columns, else min(GB, 2); RA = 4 for 32 or 64
+// rows, 2 for 16, 1 for 8 (so that 4 to 32 lanes share a register tile); GK
+// staged k per step so that the staged triples stay within 48 KB
+#define GRAM_CFG(GA, GB, RA, RB, GK) {GA, GB, GK, &k_gram<GA, GB, RA, RB, GK>}
+const GramCfg kGramCfgs[] = {
+    GRAM_CFG(8, 1, 1, 1, 64),   GRAM_CFG(8, 2, 1, 2, 64),   GRAM_CFG(8, 4, 1, 2, 64),
+    GRAM_CFG(8, 8, 1, 2, 64),   GRAM_CFG(8, 16, 1, 4, 32),  GRAM_CFG(16, 1, 2, 1, 64),
+    GRAM_CFG(16, 2, 2, 2, 64),  GRAM_CFG(16, 4, 2, 2, 64),  GRAM_CFG(16, 8, 2, 2, 32),
+    GRAM_CFG(16, 16, 2, 4, 32), GRAM_CFG(32, 1, 4, 1, 32),  GRAM_CFG(32, 2, 4, 2, 32),
+    GRAM_CFG(32, 4, 4, 2, 32),  GRAM_CFG(32, 8, 4, 2, 32),  GRAM_CFG(32, 16, 4, 4, 32),
+    GRAM_CFG(64, 1, 4, 1, 16),  GRAM_CFG(64, 2, 4, 2, 16),  GRAM_CFG(64, 4, 4, 2, 16),
+    GRAM_CFG(64, 8, 4, 2, 16),  GRAM_CFG(64, 16, 4, 4, 16),
+};
+#undef GRAM_CFG
+
+// FP64 operations per staged k of the whole product with this tile: 3 FMAs per
+// padded output plus one add per staged element of each side, per tile
+int64_t gram_ops(int na, int nb, int ga, int gb) {
+  const int64_t ta = (na + ga - 1) / ga, tb = (nb + gb - 1) / gb;
+  return ta * tb * (3LL * ga * gb + ga + gb);
+}
+
+// ---------------------------------------------------------------- combine
+constexpr int CI = 64;  // subspace rows staged per step
 
 // Y[r][k] = alpha sum_i C[i][r] V[i][k] + beta Y[r][k], r in this CTA's group
-// of RR rows; 3M products as in k_gram
+// of RR rows; 3M products (as in k_gram, without the conjugate)
 template <int RR>
 __global__ void __launch_bounds__(256)
 k_combine(const cplx *__restrict__ C, int64_t ldc, int m, int nr, const cplx *__restrict__ V, int64_t ldv,
@@ -140,39 +216,56 @@ k_combine(const cplx *__restrict__ C, int64_t ldc, int m, int nr, const cplx *__
 
 int g_sms_blockops = 0;
 
+int sm_count() {
+  if (!g_sms_blockops) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int s = 0;
+    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+    g_sms_blockops = s > 0 ? s : 148;
+  }
+  return g_sms_blockops;
+}
+
 }  // namespace
 
 void gram(Exec &ex, const cplx *A, int64_t lda, int na, const cplx *B, int64_t ldb, int nb, int64_t n, cplx alpha,
           cplx *G, int64_t ldg) {
   if (na <= 0 || nb <= 0) return;
-  if (!g_sms_blockops) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms_blockops, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms_blockops <= 0) g_sms_blockops = 148;
+  if (n <= 0) {
+    for (int a = 0; a < na; ++a) ADC_CUDA(cudaMemsetAsync(G + (int64_t)a * ldg, 0, nb * sizeof(cplx), ex.stream));
+    return;
   }
-  const int GB = nb <= 8 ? 8 : 16;
-  const int GA = na <= 32 ? 32 : 64;
-  const int gy = (na + GA - 1) / GA, gz = (nb + GB - 1) / GB;
-  int64_t nchunk = std::max<int64_t>(1, (4 * (int64_t)g_sms_blockops) / (gy * gz));
-  nchunk = std::min<int64_t>(nchunk, std::max<int64_t>(1, n / (4 * GK)));
+  int pr = ex.prof_begin("gram_fp64", 8.0 * (double)na * nb * (double)n);
+  // one row against many: the transposed product has the long side in rows
+  const bool trans = (na < 8 && nb > na);
+  const cplx *P = trans ? B : A, *R = trans ? A : B;
+  const int64_t ldp = trans ? ldb : lda, ldr = trans ? lda : ldb;
+  const int np = trans ? nb : na, nr = trans ? na : nb;
+  const GramCfg *best = nullptr;
+  int64_t best_ops = LLONG_MAX;
+  for (const GramCfg &g : kGramCfgs) {
+    const int64_t ops = gram_ops(np, nr, g.ga, g.gb);
+    // ties go to the larger tile (fewer staged re-reads)
+    if (ops < best_ops || (ops == best_ops && g.ga * g.gb > best->ga * best->gb)) {
+      best_ops = ops;
+      best = &g;
+    }
+  }
+  const int gy = (np + best->ga - 1) / best->ga, gz = (nr + best->gb - 1) / best->gb;
+  // enough CTAs for four per SM, each chunk at least four staged steps
+  int64_t nchunk = std::max<int64_t>(1, (4 * (int64_t)sm_count() + gy * gz - 1) / (gy * gz));
+  nchunk = std::min<int64_t>(nchunk, std::max<int64_t>(1, n / (4 * best->gk)));
   int64_t chunk = (n + nchunk - 1) / nchunk;
-  chunk = (chunk + GK - 1) / GK * GK;
+  chunk = (chunk + best->gk - 1) / best->gk * best->gk;
   nchunk = std::max<int64_t>(1, (n + chunk - 1) / chunk);
   ADC_REQUIRE(nchunk < (1ll << 31) && gy <= 65535 && gz <= 65535, ADC_ERR_UNSUPPORTED, "gram: shape");
   DBuf part = cbuf(ex, nchunk * (int64_t)na * nb);
-  int pr = ex.prof_begin("gram_fp64", 8.0 * (double)na * nb * (double)n);
   const dim3 grid((unsigned)nchunk, gy, gz);
-  if (GA == 32 && GB == 8)
-    k_gram<32, 8><<<grid, 256, 0, ex.stream>>>(A, lda, na, B, ldb, nb, n, chunk, part.c());
-  else if (GA == 32)
-    k_gram<32, 16><<<grid, 256, 0, ex.stream>>>(A, lda, na, B, ldb, nb, n, chunk, part.c());
-  else if (GB == 8)
-    k_gram<64, 8><<<grid, 256, 0, ex.stream>>>(A, lda, na, B, ldb, nb, n, chunk, part.c());
-  else
-    k_gram<64, 16><<<grid, 256, 0, ex.stream>>>(A, lda, na, B, ldb, nb, n, chunk, part.c());
+  best->fn<<<grid, 256, 0, ex.stream>>>(P, ldp, np, R, ldr, nr, n, chunk, part.c());
   ADC_CHECK_LAUNCH();
-  k_gram_reduce<<<(na * nb + 255) / 256, 256, 0, ex.stream>>>(part.c(), (int)nchunk, na, nb, alpha, G, ldg);
+  k_gram_reduce<<<(na * nb + 255) / 256, 256, 0, ex.stream>>>(part.c(), (int)nchunk, na, nb, trans ? 1 : 0, alpha,
+                                                               G, ldg);
   ADC_CHECK_LAUNCH();
   ex.prof_end(pr);
 }
@@ -181,14 +274,20 @@ void combine(Exec &ex, const cplx *C, int64_t ldc, int m, int nr, const cplx *V,
              cplx alpha, cplx beta, cplx *Y, int64_t ldy) {
   if (nr <= 0 || n <= 0) return;
   const int64_t gx = (n + 255) / 256;
-  const int RR = nr <= 8 ? 8 : 16;
+  // rows per CTA: the smallest group that covers nr in as few padded rows as
+  // possible (16 for more than 8)
+  const int RR = nr >= 9 ? 16 : nr >= 5 ? 8 : nr >= 3 ? 4 : nr;
   const int gy = (nr + RR - 1) / RR;
   ADC_REQUIRE(gx < (1ll << 31) && gy <= 65535, ADC_ERR_UNSUPPORTED, "combine: shape");
   int pr = ex.prof_begin("combine_fp64", 8.0 * (double)nr * m * (double)n);
-  if (RR == 8)
-    k_combine<8><<<dim3((unsigned)gx, gy), 256, 0, ex.stream>>>(C, ldc, m, nr, V, ldv, n, alpha, beta, Y, ldy);
-  else
-    k_combine<16><<<dim3((unsigned)gx, gy), 256, 0, ex.stream>>>(C, ldc, m, nr, V, ldv, n, alpha, beta, Y, ldy);
+  const dim3 grid((unsigned)gx, gy);
+  switch (RR) {
+    case 1: k_combine<1><<<grid, 256, 0, ex.stream>>>(C, ldc, m, nr, V, ldv, n, alpha, beta, Y, ldy); break;
+    case 2: k_combine<2><<<grid, 256, 0, ex.stream>>>(C, ldc, m, nr, V, ldv, n, alpha, beta, Y, ldy); break;
+    case 4: k_combine<4><<<grid, 256, 0, ex.stream>>>(C, ldc, m, nr, V, ldv, n, alpha, beta, Y, ldy); break;
+    case 8: k_combine<8><<<grid, 256, 0, ex.stream>>>(C, ldc, m, nr, V, ldv, n, alpha, beta, Y, ldy); break;
+    default: k_combine<16><<<grid, 256, 0, ex.stream>>>(C, ldc, m, nr, V, ldv, n, alpha, beta, Y, ldy); break;
+  }
   ADC_CHECK_LAUNCH();
   ex.prof_end(pr);
 }

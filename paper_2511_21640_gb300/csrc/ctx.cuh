@@ -16,6 +16,9 @@ struct adc_ctx {
   adc::Exec ex;
   bool own_stream = false;
   int dev = -1;  // CUDA device that was current at adc_init (holds every buffer)
+  // zgemm routes taken by adc_init: products (sliced, FP64) and their algorithmic flops
+  int64_t setup_n[2] = {0, 0};
+  double setup_flops[2] = {0.0, 0.0};
   int kind = 0, order = 2;
   double x = 0.0;   // the x of ADC(2)+x(3); 0 for order 2
   int64_t o = 0, v = 0, Q = 0, nmo = 0, n1 = 0, n2 = 0, N = 0;

@@ -200,6 +200,26 @@ extern "C" int adc_profile_enable(adc_ctx *c, int on) {
   }
 }
 
+extern "C" int adc_diag_set_wait_ns(uint64_t ns) {
+  try {
+    tc_set_wait_ns(ns);
+    return ADC_OK;
+  } catch (const Error &e) {
+    return e.code;
+  }
+}
+
+extern "C" int adc_setup_routes(const adc_ctx *c, int64_t *n_sliced, int64_t *n_fp64, double *flops_sliced,
+                                double *flops_fp64) {
+  if (!c) return ADC_ERR_STATE;
+  if (!n_sliced || !n_fp64 || !flops_sliced || !flops_fp64) return ADC_ERR_ARG;
+  *n_sliced = c->setup_n[0];
+  *n_fp64 = c->setup_n[1];
+  *flops_sliced = c->setup_flops[0];
+  *flops_fp64 = c->setup_flops[1];
+  return ADC_OK;
+}
+
 extern "C" int adc_memory(const adc_ctx *c, int64_t *in_use, int64_t *peak) {
   if (!c) return ADC_ERR_STATE;
   if (!in_use || !peak) return ADC_ERR_ARG;

@@ -32,7 +32,11 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;
-constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr uint64_t WAIT_NS = 2000000000ull;   // limit of every pipeline wait (default)
+constexpr uint64_t DRAIN_NS = 2000000000ull;  // limit of the waits that drain work in flight after an abort
+// limit of the pipeline waits in use; a diagnostic may lower it so that a
+// wait gives up on purpose (the drains keep DRAIN_NS)
+__device__ unsigned long long g_wait_ns = WAIT_NS;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -60,12 +64,19 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
 }
 // bounded wait; false when it gave up or another role aborted
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int *abort_flag) {
-  uint64_t t0 = gtimer();
+  const uint64_t t0 = gtimer();
+  const uint64_t lim = *(volatile unsigned long long *)&g_wait_ns;
   while (!mbar_try(a, parity)) {
     if (*abort_flag) return false;
-    if (gtimer() - t0 > WAIT_NS) return false;
+    if (gtimer() - t0 > lim) return false;
   }
   return true;
+}
+// wait for work already in flight (copies, MMAs) after an abort: fixed limit
+__device__ __forceinline__ void mbar_drain(uint32_t a, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try(a, parity) && gtimer() - t0 < DRAIN_NS) {
+  }
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
                                             uint32_t mbar) {
@@ -202,9 +213,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
       // drain this CTA's copies in flight before shared memory is released
       for (int j = (issued > ST ? issued - ST : 0); j < issued; ++j) {
         const int s = j % ST, r = j / ST;
-        uint64_t t0 = gtimer();
-        while (!mbar_try(smem_u32(&full[s]), r & 1) && gtimer() - t0 < WAIT_NS) {
-        }
+        mbar_drain(smem_u32(&full[s]), r & 1);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -226,10 +235,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
       mma_commit(smem_u32(&empty[s]));
     }
     mma_commit(smem_u32(accum));
+    // after an abort the MMAs already issued finish before TMEM is freed
+    if (*abort_flag) mbar_drain(smem_u32(accum), 0);
   } else if (warp >= 2) {
     // ---------------- epilogue: TMEM -> registers -> complex128
     bool ok = mbar_wait(smem_u32(accum), 0, abort_flag);
     if (!ok && !*abort_flag) { atomicExch(err, 3); *abort_flag = 1; }
+    if (!ok) mbar_drain(smem_u32(accum), 0);
     fence_after();
     __syncwarp();
     const int q = warp & 3;
@@ -489,6 +501,7 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
   uint32_t *tmem_slot = (uint32_t *)(tempty + TG_TQ);
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
   volatile int *ring = (volatile int *)(tmem_slot + 2);
+  uint64_t *fin = (uint64_t *)(tmem_slot + 2 + TG_TQ);  // every MMA of this CTA finished
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -504,6 +517,7 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
       mbar_init(smem_u32(&tfull[q]), 1);
       mbar_init(smem_u32(&tempty[q]), 5);
     }
+    mbar_init(smem_u32(fin), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -569,9 +583,7 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
       // drain this CTA's copies in flight before shared memory is released
       for (uint32_t gj = (g_issued > TG_ST ? g_issued - TG_ST : 0); gj < g_issued; ++gj) {
         const int s = (int)(gj % TG_ST);
-        uint64_t t0 = gtimer();
-        while (!mbar_try(smem_u32(&full[s]), (gj / TG_ST) & 1) && gtimer() - t0 < WAIT_NS) {
-        }
+        mbar_drain(smem_u32(&full[s]), (gj / TG_ST) & 1);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -619,6 +631,10 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
       mma_commit(smem_u32(&accf[b]));
       g += (uint32_t)d.nkb;
     }
+    // every MMA this thread issued has finished before TMEM is freed (after an
+    // abort the epilogue no longer waits for them)
+    mma_commit(smem_u32(fin));
+    mbar_drain(smem_u32(fin), 0);
   } else if (warp >= 2) {
     // ---------------- epilogue: TMEM -> registers -> complex128, one accumulator at a time
     const int qq = warp & 3;
@@ -952,6 +968,11 @@ void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &in, TcGroup &grp, i
     ADC_CHECK_LAUNCH();
   }
   ex.prof_end(pr);
+}
+
+void tc_set_wait_ns(uint64_t ns) {
+  const unsigned long long v = ns ? (unsigned long long)ns : (unsigned long long)WAIT_NS;
+  ADC_CUDA(cudaMemcpyToSymbol(g_wait_ns, &v, sizeof(v)));
 }
 
 int tc_autotune_bn(Exec &ex, const TcJobDesc &d, int *err) {

@@ -120,6 +120,9 @@ void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &jobs, TcGroup &grp,
 int tc_autotune_bn(Exec &ex, const TcJobDesc &d, int *err);
 // table of tuned shapes: (M, N2, kp, bn); returns the number of entries
 int tc_autotune_table(int64_t *out, int cap);
+// limit (ns) of the tensor-core kernels' pipeline waits on the current device;
+// 0 restores the default of 2 s (the drains after an abort keep their own 2 s)
+void tc_set_wait_ns(uint64_t ns);
 
 struct TcCache {
   int planes = 2;            // BF16 planes of the copies (3 for the six-product split)

@@ -243,10 +243,14 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
   // (short inner sizes stay here: there the product is bound by memory, and the
   // sliced form reads and writes several times more)
   if (ex.sliced_bits > 0 && K >= 512 && 8.0 * (double)M * N * K * batch >= (double)(1 << 24)) {
+    ex.n_sliced += 1;
+    ex.flops_sliced += 8.0 * (double)M * N * K * batch;
     zgemm_sliced(ex, M, N, K, batch, alpha, A, sAb, sAm, sAk, conjA, B, sBb, sBk, sBn, conjB, beta, C, sCb, sCm,
                  sCn);
     return;
   }
+  ex.n_fp64 += 1;
+  ex.flops_fp64 += 8.0 * (double)M * N * K * batch;
   zgemm_attr();
   const int64_t mt_ = (M + BM - 1) / BM, nt_ = (N + BN - 1) / BN;
   const int mfast = (nt_ <= 65535) ? 1 : 0;

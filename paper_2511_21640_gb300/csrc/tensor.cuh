@@ -21,6 +21,11 @@ struct Exec {
   // 512) as the sliced tensor-core product with about this many significant
   // bits (tc_slice.cu)
   int sliced_bits = 0;
+  // complex GEMMs issued through zgemm since the counters were cleared: how
+  // many took the sliced tensor-core route and how many the FP64 kernel, with
+  // their algorithmic flops (host-side counts)
+  int64_t n_sliced = 0, n_fp64 = 0;
+  double flops_sliced = 0.0, flops_fp64 = 0.0;
   int64_t mem_limit = 0;  // 0 = unlimited
   int64_t mem_used = 0;
   int64_t mem_peak = 0;

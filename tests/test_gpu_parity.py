@@ -221,28 +221,67 @@ def test_mixed_davidson_sliced_refinement(gpu, kind, o, v, Q, x):
 
 
 @pytest.mark.parametrize("kind,o,v,Q,order,x,seed", [("EA", 8, 40, 80, 3, 0.5, 41), ("IP", 12, 30, 80, 3, 1.0, 42),
-                                                     ("EE", 6, 20, 40, 3, 0.4, 43), ("EA", 6, 36, 60, 2, 0.0, 44)])
+                                                     ("EE", 6, 20, 40, 3, 0.4, 43), ("EA", 6, 36, 60, 2, 0.0, 44),
+                                                     ("IP", 6, 20, 600, 3, 1.0, 45), ("EA", 5, 21, 560, 3, 0.5, 46),
+                                                     ("EE", 4, 10, 520, 3, 0.4, 47), ("EE", 4, 10, 520, 2, 0.0, 48)])
 def test_sliced_setup(gpu, kind, o, v, Q, order, x, seed):
     """adc_init with opts.setup = ADC_PREC_SLICED: the setup's contractions of at
-    least 2^24 flops run as the sliced product (about 48 bits); the operators
-    match the oracle to 1e-11 relative (FP64 setup: 1e-12)."""
+    least 2^24 flops and inner size 512 run as the sliced product (about 48
+    bits); sigma, diagonal and main block match the oracle to 1e-11 relative
+    (FP64 setup: 1e-12). The routes adc_init took are counted: with naux >= 512
+    every kind's integral assembly over the Cholesky index goes through the
+    sliced product, and most of the setup's flops with it."""
     p = make_problem(o, v, Q, seed=seed, sigma=0.08)
     kw = dict(kind=kind, order=order, x=x)
     with gpu.Context(p.B, p.eps_occ, p.eps_vir, setup="sliced", **kw) as ctx:
         X = random_vectors(ctx.N, 2, seed=seed + 1)
         S = ctx.sigma(X, "fp64")
         d = ctx.diagonal()
+        M11 = ctx.main_block()
+        routes = ctx.setup_routes()
     if kind == "EE":
         from oracle import adc_ee
         M = adc_ee.explicit_matrix(order, x, p.B, p.eps_occ, p.eps_vir)
         ref = X @ M.T
         dref = np.real(np.diag(M))
+        m11 = M[:ctx.n1, :ctx.n1]
     else:
         amp = oadc.Amplitudes(p.B, p.eps_occ, p.eps_vir, second_order=(order == 3))
         ref = oadc.sigma_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, X, amp=amp)
         dref = oadc.diagonal_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, amp=amp)
+        m11 = oadc.explicit_matrix(kind, order, x, p.B, p.eps_occ, p.eps_vir)[:ctx.n1, :ctx.n1]
     assert _rel(S, ref).max() < 1e-11, _rel(S, ref).max()
     assert np.abs(d - dref).max() < 1e-11 * max(1.0, np.abs(dref).max())
+    assert np.abs(M11 - m11).max() < 1e-11 * max(1.0, np.abs(m11).max())
+    if Q >= 512:
+        total = routes["flops_sliced"] + routes["flops_fp64"]
+        assert routes["n_sliced"] >= 1 and routes["flops_sliced"] >= 0.5 * total, routes
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-4), ("sliced", 1e-10)])
+def test_tensor_core_wait_gives_up_and_context_recovers(gpu, prec, tol):
+    """A pipeline wait of the tensor-core kernels that runs out: the wait limit
+    is lowered to 1 ns through the test hook, so a wait gives up long before
+    the copies and MMAs it waits for finish. The kernels drain what they have
+    in flight and return; the call reports ADC_ERR_TIMEOUT (-5). With the
+    limit restored the next call on the same context gives the normal result
+    (against the oracle). The operand copies and tile widths are built at the
+    normal limit first."""
+    p = make_problem(6, 60, 50, seed=51, sigma=0.08)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EA", order=3, x=0.5) as ctx:
+        X = random_vectors(ctx.N, 2, seed=52)
+        first = ctx.sigma(X, prec)
+        assert gpu.lib.adc_diag_set_wait_ns(1) == 0
+        try:
+            with pytest.raises(gpu.AdcError) as ei:
+                ctx.sigma(X, prec)
+            assert ei.value.code == -5, ei.value
+        finally:
+            assert gpu.lib.adc_diag_set_wait_ns(0) == 0
+        again = ctx.sigma(X, prec)
+    ref = oadc.sigma_ref("EA", 3, 0.5, p.B, p.eps_occ, p.eps_vir, X)
+    assert _rel(again, first).max() < 1e-14
+    assert _rel(again, ref).max() < tol
 
 
 def test_davidson_noconv_returns_best(gpu):
