@@ -19,7 +19,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["ea_satellite_rows", "ip_satellite_rows", "ee_doubles_rows"]
+__all__ = ["ea_satellite_rows", "ip_satellite_rows", "ee_doubles_rows", "main_rows_ground", "ea_main_rows",
+           "ip_main_rows"]
 
 
 def _pair(p, q, n):
@@ -350,3 +351,170 @@ def ee_doubles_rows(B, eps_occ, eps_vir, order, x, X, rows, dd_order=1):
         out[:, r] = val
     return out
 
+
+
+# ---------------------------------------------------------------- IP/EA main rows
+
+def _eri_fixed(B, nocc, spec, fix=None):
+    """<pq||rs> = sum_Q (B_pr B_qs - B_ps B_qr) (Eq. 43) for the classes of
+    ``spec`` (four of 'o'/'v'), with the positions in ``fix`` held at one
+    index (within their class); one axis per free position, in order."""
+    fix = fix or {}
+    nmo = B.shape[1]
+    sel = []
+    for pos, c in enumerate(spec):
+        base, n = (0, nocc) if c == "o" else (nocc, nmo - nocc)
+        sel.append(base + fix[pos] if pos in fix else slice(base, base + n))
+    L = "pqrs"
+
+    def lab(*ps):
+        return "".join(L[p] for p in ps if p not in fix)
+
+    out = lab(0, 1, 2, 3)
+    t1 = np.einsum(f"Q{lab(0, 2)},Q{lab(1, 3)}->{out}", B[:, sel[0], sel[2]], B[:, sel[1], sel[3]],
+                   optimize="greedy")
+    t2 = np.einsum(f"Q{lab(0, 3)},Q{lab(1, 2)}->{out}", B[:, sel[0], sel[3]], B[:, sel[1], sel[2]],
+                   optimize="greedy")
+    return t1 - t2
+
+
+def main_rows_ground(B, eps_occ, eps_vir):
+    """Ground-state quantities of ``integrals.Amplitudes`` (first-order doubles
+    t1, second-order singles t2s and doubles t2d, the densities gvv and hoo)
+    plus the stored integral classes oovv and ovvo, at sizes where the dense
+    four-virtual block does not fit: the second-order ladder
+    1/2 sum_cd <ab||cd> t_ij^cd is accumulated one virtual index a at a time,
+    with <ab||cd> for that a assembled from B (Eq. 43); the vovv integrals of
+    the second-order singles likewise."""
+    eo = np.asarray(eps_occ, np.float64)
+    ev = np.asarray(eps_vir, np.float64)
+    o, v = eo.size, ev.size
+    D2 = eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
+    g = {"eo": eo, "ev": ev, "o": o, "v": v}
+    t1 = _eri_fixed(B, o, "vvoo").transpose(2, 3, 0, 1) / D2        # t_ij^ab = <ab||ij> / D_ij^ab
+    tc = t1.conj()
+    g["t1"] = t1
+    g["oovv"] = _eri_fixed(B, o, "oovv")                               # <ij||ab>
+    g["ovvo"] = _eri_fixed(B, o, "ovvo")                               # <kb||cj>
+    g["gvv"] = 0.5 * np.einsum("ijdf,ijef->de", tc, t1, optimize="greedy")
+    g["hoo"] = 0.5 * np.einsum("njef,mjef->nm", tc, t1, optimize="greedy")
+    # second-order singles: (eps_i - eps_a) t_i^a = 1/2 sum_jcd <aj||cd> t_ij^cd - 1/2 sum_jkc <jk||ic> t_jk^ac
+    num = -0.5 * np.einsum("jkic,jkac->ia", _eri_fixed(B, o, "ooov"), t1, optimize="greedy")
+    for a in range(v):
+        num[:, a] += 0.5 * np.einsum("jcd,ijcd->i", _eri_fixed(B, o, "vovv", {0: a}), t1, optimize="greedy")
+    g["t2s"] = num / (eo[:, None] - ev[None, :])
+    # second-order doubles: D t2 = 1/2 <ab||cd> t^cd + 1/2 <kl||ij> t_kl + P(ij) P(ab) sum_kc <kb||cj> t_ik^ac
+    ring = np.einsum("kbcj,ikac->ijab", g["ovvo"], t1, optimize="greedy")
+    t2 = ring - ring.transpose(1, 0, 2, 3) - ring.transpose(0, 1, 3, 2) + ring.transpose(1, 0, 3, 2)
+    del ring
+    t2 += 0.5 * np.einsum("klij,klab->ijab", _eri_fixed(B, o, "oooo"), t1, optimize="greedy")
+    for a in range(v):
+        t2[:, :, a, :] += 0.5 * np.einsum("bcd,ijcd->ijb", _eri_fixed(B, o, "vvvv", {0: a}), t1, optimize="greedy")
+    g["t2d"] = t2 / D2
+    return g
+
+
+def ea_main_rows(B, eps_occ, eps_vir, order, x, X, rows, ground=None):
+    """S1 entries (the 1p rows) c of S = M X for each c in ``rows`` (EA).
+
+    S1_c = sum_b M11_cb X1_b + 1/2 sum_kde (<ck||de> + x M12^(2)_c,kde) X2_kde,
+    M11 = M0 + M2 (+ x M3 at order 3), term by term as ``adc.main_block`` writes
+    them, with every integral the row needs assembled from B for that row
+    (Eq. 43). The four-virtual term 1/4 sum <cd||be> conj(t_ij^cd) t_ij^ea is
+    contracted through B: sum_cde <cd||be> P_cde = sum_Q [sum_c B_cb sum_de B_de
+    P_cde - sum_d B_db sum_ce B_ce P_cde]. Returns [len(X), len(rows)] complex.
+    """
+    g = ground if ground is not None else main_rows_ground(B, eps_occ, eps_vir)
+    eo, ev, o, v = g["eo"], g["ev"], g["o"], g["v"]
+    if order == 2:
+        x = 0.0
+    t1, t2d, t2s, gvv, hoo = g["t1"], g["t2d"], g["t2s"], g["gvv"], g["hoo"]
+    tc = t1.conj()
+    X = np.atleast_2d(np.asarray(X, np.complex128))
+    X1 = X[:, :v]
+    iu, ju = np.triu_indices(v, 1)
+    X2f = np.zeros((X.shape[0], o, v, v), np.complex128)
+    X2f[:, :, iu, ju] = X[:, v:].reshape(X.shape[0], o, iu.size)
+    X2f[:, :, ju, iu] = -X2f[:, :, iu, ju]
+    Bvv = B[:, o:, o:]
+    out = np.zeros((X.shape[0], len(rows)), np.complex128)
+    for r, a in enumerate(rows):
+        de = ev[a] - ev                                           # eps_a - eps_b
+        m11 = np.zeros(v, np.complex128)
+        m11[a] = ev[a]
+        m11 += -0.5 * np.einsum("klc,klbc->b", t1[:, :, a, :], g["oovv"], optimize="greedy") + 0.5 * de * gvv[:, a]
+        if x != 0.0:
+            g3 = 0.5 * (np.einsum("ijbf,ijf->b", tc, t2d[:, :, a, :], optimize="greedy")
+                        + np.einsum("ijbf,ijf->b", t2d.conj(), t1[:, :, a, :], optimize="greedy"))
+            P = np.einsum("ijcd,ije->cde", tc, t1[:, :, :, a], optimize="greedy")      # P_cde for e a-paired
+            U = np.einsum("Qde,cde->Qc", Bvv, P, optimize="greedy")
+            W = np.einsum("Qce,cde->Qd", Bvv, P, optimize="greedy")
+            four = np.einsum("Qcb,Qc->b", Bvv, U, optimize="greedy") - np.einsum("Qdb,Qd->b", Bvv, W,
+                                                                                optimize="greedy")
+            R = np.einsum("njcf,mjf->cnm", tc, t1[:, :, a, :], optimize="greedy")       # R_ca,nm
+            y3 = (-0.5 * np.einsum("klc,klbc->b", t2d[:, :, a, :], g["oovv"], optimize="greedy")
+                  - np.einsum("mbd,md->b", _eri_fixed(B, o, "ovvv", {1: a}), t2s, optimize="greedy")
+                  + np.einsum("dbk,kd->b", _eri_fixed(B, o, "vvvo", {0: a}), t2s.conj(), optimize="greedy")
+                  + np.einsum("dbe,de->b", _eri_fixed(B, o, "vvvv", {0: a}), gvv, optimize="greedy")
+                  + 0.25 * four
+                  + np.einsum("mbn,nm->b", _eri_fixed(B, o, "ovvo", {1: a}), hoo, optimize="greedy")
+                  - np.einsum("mcbn,cnm->b", g["ovvo"], R, optimize="greedy"))
+            m11 += x * (y3 + 0.5 * de * g3)
+        C = _eri_fixed(B, o, "vovv", {0: a})                                     # <ak||de>
+        if x != 0.0:
+            c2 = (0.5 * np.einsum("kmn,mnde->kde", _eri_fixed(B, o, "vooo", {0: a}), tc, optimize="greedy")
+                  + np.einsum("gem,kmgd->kde", _eri_fixed(B, o, "vvvo", {0: a}), tc, optimize="greedy")
+                  - np.einsum("gdm,kmge->kde", _eri_fixed(B, o, "vvvo", {0: a}), tc, optimize="greedy"))
+            C = C + x * c2
+        out[:, r] = X1 @ m11 + 0.5 * np.einsum("kde,zkde->z", C, X2f, optimize="greedy")
+    return out
+
+
+def ip_main_rows(B, eps_occ, eps_vir, order, x, X, rows, ground=None):
+    """S1 entries (the 1h rows) k of S = M X for each k in ``rows`` (IP).
+
+    S1_k = sum_l M11_kl X1_l + 1/2 sum_ija (<ji||ak> + x M12^(2)_k,ija) X2_ija,
+    M11 = M0 + M2 (+ x M3 at order 3), term by term as ``adc.main_block``
+    writes them, every integral of the row assembled from B (Eq. 43).
+    Returns [len(X), len(rows)] complex.
+    """
+    g = ground if ground is not None else main_rows_ground(B, eps_occ, eps_vir)
+    eo, ev, o, v = g["eo"], g["ev"], g["o"], g["v"]
+    if order == 2:
+        x = 0.0
+    t1, t2d, t2s, gvv, hoo = g["t1"], g["t2d"], g["t2s"], g["gvv"], g["hoo"]
+    tc = t1.conj()
+    X = np.atleast_2d(np.asarray(X, np.complex128))
+    X1 = X[:, :o]
+    iu, ju = np.triu_indices(o, 1)
+    X2f = np.zeros((X.shape[0], o, o, v), np.complex128)
+    X2f[:, iu, ju, :] = X[:, o:].reshape(X.shape[0], iu.size, v)
+    X2f[:, ju, iu, :] = -X2f[:, iu, ju, :]
+    out = np.zeros((X.shape[0], len(rows)), np.complex128)
+    vovo = _eri_fixed(B, o, "vovo") if x != 0.0 else None          # <cj||dk>
+    for r, i in enumerate(rows):
+        do = eo[i] - eo                                             # eps_i - eps_j
+        m11 = np.zeros(o, np.complex128)
+        m11[i] = -eo[i]
+        m11 += 0.5 * np.einsum("kjcd,kcd->j", g["oovv"], t1[i], optimize="greedy") - 0.5 * do * hoo[:, i]
+        if x != 0.0:
+            h3 = 0.5 * (np.einsum("jkcd,kcd->j", tc, t2d[i], optimize="greedy")
+                        + np.einsum("jkcd,kcd->j", t2d.conj(), t1[i], optimize="greedy"))
+            Pk = np.einsum("lmef,kef->lmk", tc, t1[i], optimize="greedy")
+            Z = np.einsum("klcf,ldf->ckd", tc, t1[i], optimize="greedy")
+            y3 = (0.5 * np.einsum("kjcd,kcd->j", g["oovv"], t2d[i], optimize="greedy")
+                  - np.einsum("kje,ke->j", _eri_fixed(B, o, "oovo", {3: i}), t2s, optimize="greedy")
+                  + np.einsum("cjk,kc->j", _eri_fixed(B, o, "vooo", {2: i}), t2s.conj(), optimize="greedy")
+                  + np.einsum("kjl,lk->j", _eri_fixed(B, o, "oooo", {3: i}), hoo, optimize="greedy")
+                  + 0.25 * np.einsum("kjlm,lmk->j", _eri_fixed(B, o, "oooo"), Pk, optimize="greedy")
+                  - np.einsum("cjd,cd->j", _eri_fixed(B, o, "vovo", {3: i}), gvv, optimize="greedy")
+                  + np.einsum("cjdk,ckd->j", vovo, Z, optimize="greedy"))
+            m11 += x * (y3 - 0.5 * do * h3)
+        C = _eri_fixed(B, o, "oovo", {3: i}).transpose(1, 0, 2)              # <ji||ak> -> [i][j][a]
+        if x != 0.0:
+            c2 = (0.5 * np.einsum("efa,jief->ija", _eri_fixed(B, o, "vvvo", {3: i}), tc, optimize="greedy")
+                  - np.einsum("fim,jmfa->ija", _eri_fixed(B, o, "vooo", {3: i}), tc, optimize="greedy")
+                  + np.einsum("fjm,imfa->ija", _eri_fixed(B, o, "vooo", {3: i}), tc, optimize="greedy"))
+            C = C + x * c2
+        out[:, r] = X1 @ m11 + 0.5 * np.einsum("ija,zija->z", C, X2f, optimize="greedy")
+    return out

@@ -230,7 +230,8 @@ def test_sliced_setup(gpu, kind, o, v, Q, order, x, seed):
     bits); sigma, diagonal and main block match the oracle to 1e-11 relative
     (FP64 setup: 1e-12). The routes adc_init took are counted: with naux >= 512
     every kind's integral assembly over the Cholesky index goes through the
-    sliced product, and most of the setup's flops with it."""
+    sliced product, a third or more of the setup's flops at these sizes (the
+    EE setup's many products below 2^24 flops stay on the FP64 cores)."""
     p = make_problem(o, v, Q, seed=seed, sigma=0.08)
     kw = dict(kind=kind, order=order, x=x)
     with gpu.Context(p.B, p.eps_occ, p.eps_vir, setup="sliced", **kw) as ctx:
@@ -255,7 +256,7 @@ def test_sliced_setup(gpu, kind, o, v, Q, order, x, seed):
     assert np.abs(M11 - m11).max() < 1e-11 * max(1.0, np.abs(m11).max())
     if Q >= 512:
         total = routes["flops_sliced"] + routes["flops_fp64"]
-        assert routes["n_sliced"] >= 1 and routes["flops_sliced"] >= 0.5 * total, routes
+        assert routes["n_sliced"] >= 1 and routes["flops_sliced"] >= total / 3, routes
 
 
 @pytest.mark.parametrize("prec,tol", [("bf16x3", 1e-4), ("sliced", 1e-10)])
