@@ -223,7 +223,7 @@ def test_mixed_davidson_sliced_refinement(gpu, kind, o, v, Q, x):
 @pytest.mark.parametrize("kind,o,v,Q,order,x,seed", [("EA", 8, 40, 80, 3, 0.5, 41), ("IP", 12, 30, 80, 3, 1.0, 42),
                                                      ("EE", 6, 20, 40, 3, 0.4, 43), ("EA", 6, 36, 60, 2, 0.0, 44),
                                                      ("IP", 6, 20, 600, 3, 1.0, 45), ("EA", 5, 21, 560, 3, 0.5, 46),
-                                                     ("EE", 4, 10, 520, 3, 0.4, 47), ("EE", 4, 10, 520, 2, 0.0, 48)])
+                                                     ("EE", 4, 10, 520, 3, 0.4, 47), ("EE", 6, 16, 520, 2, 0.0, 48)])
 def test_sliced_setup(gpu, kind, o, v, Q, order, x, seed):
     """adc_init with opts.setup = ADC_PREC_SLICED: the setup's contractions of at
     least 2^24 flops and inner size 512 run as the sliced product (about 48
