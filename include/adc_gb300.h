@@ -182,6 +182,26 @@ int adc_sigma(adc_ctx *ctx, const adc_c128 *X, adc_c128 *S, int64_t k,
  * Asynchronous on the context's stream. */
 int adc_sigma_noalloc(adc_ctx *ctx, const adc_c128 *X, adc_c128 *S, int64_t k);
 
+/* One rank's share of the FP64 sigma product (Sec. 2.1, Eqs. 10-12) when an
+ * EA problem is split across ranks by the occupied index j of its satellite
+ * amplitudes X_j,(a<b): the rank owning j in [i0, i1) holds the satellite
+ * rows of those j and a copy of the 1p rows. The ladder term is diagonal in
+ * j; the ring and the coupling reach every j, so every rank first gathers the
+ * whole trial block.
+ *   X          [k][N] the whole trial block (host or device).
+ *   S          [k][n1 + (i1 - i0) Pv] output (host or device), Pv = nvir
+ *              (nvir - 1) / 2:
+ *              S[:, :n1]  partial 1p rows: the coupling of the share's
+ *                         satellites, plus M11 X1 when with_main != 0; the
+ *                         sum over the ranks (one of them with_main) is S1;
+ *              S[:, n1:]  the share's satellite rows of S = M X, complete.
+ *   i0, i1     occupied range of the share, 0 <= i0 <= i1 <= nocc.
+ * EA contexts only (ADC_ERR_UNSUPPORTED otherwise); ADC_ERR_ARG for a range
+ * outside [0, nocc]. Asynchronous on the context's stream unless a pointer
+ * is on the host. */
+int adc_sigma_share(adc_ctx *ctx, const adc_c128 *X, adc_c128 *S, int64_t k,
+                    int64_t i0, int64_t i1, int with_main);
+
 /* Exact diagonal of M as real numbers, [N] (host or device). */
 int adc_diagonal(adc_ctx *ctx, double *diag);
 

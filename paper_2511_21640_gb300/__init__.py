@@ -101,6 +101,7 @@ def _load():
         "adc_dims": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "adc_sigma": (I, [P, P, P, I64, I]),
         "adc_sigma_noalloc": (I, [P, P, P, I64]),
+        "adc_sigma_share": (I, [P, P, P, I64, I64, I64, I]),
         "adc_diagonal": (I, [P, P]),
         "adc_main_block": (I, [P, P]),
         "adc_davidson": (I, [P, I, D, I, I, P, I64, P, P, P, ctypes.POINTER(adc_stats)]),
@@ -265,6 +266,25 @@ class Context:
         _check(lib.adc_sigma(self._h, _ptr(X, np.complex128), _ptr(S, np.complex128), k, p), self._h)
         if dev and not self._shared_stream:
             _check(lib.adc_sync(self._h), self._h)  # S is read on torch's stream
+        return S
+
+    def sigma_share(self, X, i0, i1, with_main):
+        """One rank's share of S = M X for an EA problem split by the satellites'
+        occupied index (``adc_sigma_share``): X [k][N] whole, returns [k][n1 + (i1 - i0) Pv]
+        (partial 1p rows, then the share's satellite rows)."""
+        X2 = X if X.ndim == 2 else X.reshape(1, -1)
+        k = X2.shape[0]
+        if X2.shape[1] != self.N:
+            raise ValueError("last dimension of X must be N")
+        pv = self.nvir * (self.nvir - 1) // 2
+        S = _empty_like_kind(X2, (k, self.n1 + (int(i1) - int(i0)) * pv), np.complex128)
+        dev = _on_cuda(X2, S)
+        if dev and not self._shared_stream:
+            _torch_sync()
+        _check(lib.adc_sigma_share(self._h, _ptr(X2, np.complex128), _ptr(S, np.complex128), k, int(i0), int(i1),
+                                   1 if with_main else 0), self._h)
+        if dev and not self._shared_stream:
+            _check(lib.adc_sync(self._h), self._h)
         return S
 
     def fns_transform(self, U, n_keep=None):

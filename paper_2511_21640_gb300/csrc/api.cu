@@ -248,6 +248,26 @@ int adc_sigma(adc_ctx *c, const adc_c128 *X, adc_c128 *S, int64_t k, int precisi
   ADC_API_CATCH(c)
 }
 
+int adc_sigma_share(adc_ctx *c, const adc_c128 *X, adc_c128 *S, int64_t k, int64_t i0, int64_t i1,
+                    int with_main) {
+  if (!c) return ADC_ERR_STATE;
+  if (k < 0 || (k > 0 && (!X || !S))) return ADC_ERR_ARG;
+  ADC_API_TRY
+  if (c->kind != ADC_EA) throw Error(ADC_ERR_UNSUPPORTED, "adc_sigma_share covers EA");
+  if (i0 < 0 || i1 < i0 || i1 > c->o)
+    throw Error(ADC_ERR_ARG, "adc_sigma_share: occupied range [" + std::to_string(i0) + ", " + std::to_string(i1) +
+                                 ") outside [0, " + std::to_string(c->o) + ")");
+  if (k == 0) return ADC_OK;
+  const int64_t ls = c->n1 + (i1 - i0) * npairs(c->v);
+  DevIn xin(c->ex, X, (size_t)k * c->N * sizeof(cplx));
+  DevOut sout(c->ex, S, (size_t)k * ls * sizeof(cplx));
+  sigma_fp64_share(c, (const cplx *)xin.p, (cplx *)sout.p, k, i0, i1, with_main != 0);
+  sout.finish(c->ex);
+  if (sout.host || xin.buf.p) ADC_CUDA(cudaStreamSynchronize(c->ex.stream));
+  return ADC_OK;
+  ADC_API_CATCH(c)
+}
+
 int adc_diagonal(adc_ctx *c, double *diag) {
   if (!c) return ADC_ERR_STATE;
   if (!diag) return ADC_ERR_ARG;

@@ -110,6 +110,8 @@ int ssfns_run(const adc_c128 *B, int64_t naux, const double *eps_occ, int64_t no
 void sigma_ee_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg);
 void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
+// one rank's share of the EA sigma with the satellites split by occupied index [i0, i1) (sigma.cu)
+void sigma_fp64_share(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int64_t i0, int64_t i1, bool with_main);
 // split-precision sigma on the tensor cores: nseg = 3 (BF16x3) or 6 (BF16x6) products
 void sigma_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg);
 // FP64-accurate sigma with the dense contractions as sliced tensor-core products (IP/EA)

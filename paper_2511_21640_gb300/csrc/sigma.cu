@@ -90,6 +90,57 @@ void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
   }
 }
 
+// One rank's share of the FP64 EA sigma when the satellite space is split by
+// its occupied index j into [i0, i1) (nb = i1 - i0). X is the whole [k][N]
+// block (every rank holds it after an all-gather); S is [k][n1 + nb Pv]:
+//   S[:, :n1]  the partial main rows X2[j in share] Cpl[:, j in share]^T
+//              (plus X1 M11^T when with_main): summed over the ranks they give S1;
+//   S[:, n1:]  the satellite rows of the share, complete: coupling
+//              conj(Cpl[:, j in share])^T X1, zeroth-order diagonal, the ladder
+//              (diagonal in j: only the share's own X2 rows) and the ring (all of
+//              X2, through the all-gathered block).
+// The same terms and kernels as sigma_fp64 (Sec. 2.1 Eqs. 10-12), restricted.
+void sigma_fp64_share(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int64_t i0, int64_t i1, bool with_main) {
+  Exec &ex = c->ex;
+  ADC_REQUIRE(c->kind == ADC_EA, ADC_ERR_UNSUPPORTED, "sigma share: EA only");
+  ADC_REQUIRE(0 <= i0 && i0 <= i1 && i1 <= c->o, ADC_ERR_ARG, "sigma share: occupied range");
+  const int64_t o = c->o, v = c->v, n1 = c->n1, N = c->N;
+  const int64_t pv = npairs(v), nb = i1 - i0, ns = nb * pv, ldS = n1 + ns;
+  const bool sat = (c->order == 3 && c->x != 0.0);
+  const double x = sat ? c->x : 0.0;
+  TagScope tg(ex, "main");
+  if (with_main)
+    zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, c->M11.c(), 0, 1, n1, false, C0(), S, 0, ldS, 1);
+  ex.tag = "coupling";
+  if (ns > 0)
+    zgemm(ex, k, n1, ns, 1, C1(), X + n1 + i0 * pv, 0, N, 1, false, c->Cpl.c() + i0 * pv, 0, 1, c->n2, false,
+          with_main ? C1() : C0(), S, 0, ldS, 1);
+  else if (!with_main)
+    for (int64_t r = 0; r < k; ++r) ADC_CUDA(cudaMemsetAsync(S + r * ldS, 0, n1 * sizeof(cplx), ex.stream));
+  if (ns == 0) return;
+  zgemm(ex, k, ns, n1, 1, C1(), X, 0, N, 1, false, c->Cpl.c() + i0 * pv, 0, c->n2, 1, true, C0(), S + n1, 0, ldS,
+        1);
+  diag_mul_add(ex, k, ns, c->d2.d() + i0 * pv, X + n1 + i0 * pv, N, S + n1, ldS, 1.0);
+  if (!sat) return;
+  // ladder on the share's rows: Og[r][j][(ab)] = sum_(cd) X2[r][j][(cd)] Glad[(ab)][(cd)]
+  ex.tag = "ladder";
+  cplx *Xf = scratch(c, 2 * k * o * v * v + 2 * k * ns);
+  cplx *T = Xf + k * o * v * v;
+  cplx *Xg = T + k * o * v * v, *Og = Xg + k * ns;
+  ADC_CUDA(cudaMemcpy2DAsync(Xg, ns * sizeof(cplx), X + n1 + i0 * pv, N * sizeof(cplx), ns * sizeof(cplx), k,
+                             cudaMemcpyDeviceToDevice, ex.stream));
+  zgemm(ex, k * nb, pv, pv, 1, C1(), Xg, 0, pv, 1, false, c->Glad.c(), 0, 1, pv, false, C0(), Og, 0, pv, 1);
+  k_rows_axpy<<<grid1d(k * ns, 256), 256, 0, ex.stream>>>(k, ns, CR(x), Og, ns, S + n1, ldS);
+  ADC_CHECK_LAUNCH();
+  // ring rows (j, a) of the share: R[(j,a)][r][b] = sum_(kc) W[(j,a)][(kc)] Xt[(kc)][r][b], all k
+  ex.tag = "ring";
+  pair_unpack(ex, X + n1, k, o, N, pv, v, 1, Xf);
+  permute(ex, Xf, {o * v, k, v}, {v, o * v * v, 1}, false, T, C1(), C0());
+  zgemm(ex, nb * v, k * v, o * v, 1, C1(), c->W.c() + i0 * v * (o * v), 0, o * v, 1, false, T, 0, k * v, 1, false,
+        C0(), Xf, 0, k * v, 1);
+  pair_pack(ex, Xf, v, v * k * v, k * v, 1, 0, 1.0, k, nb, v, 1, S + n1, ldS, pv, CR(-x), C1());
+}
+
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision) {
   if (k <= 0) return;
   if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3 && precision != ADC_PREC_BF16X6 &&
