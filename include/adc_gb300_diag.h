@@ -85,6 +85,14 @@ int adc_setup_routes(const adc_ctx_opaque *ctx, int64_t *n_sliced, int64_t *n_fp
 int adc_diag_blockops(int which, int64_t m, int64_t nb, int64_t n, uint64_t seed, int reps,
                       double *rel_err, double *ms);
 
+/* The small Hermitian eigensolvers of the Davidson's Rayleigh-Ritz step on a
+ * host matrix A [n][n] (row-major, Hermitian): which 0 = FP64 cyclic Jacobi,
+ * 1 = FP32 Jacobi start refined in FP64 (n <= 128, else
+ * ADC_ERR_UNSUPPORTED). Eigenvalues ascending into w [n], eigenvectors as the
+ * columns of V [n][n] (host). ms = CUDA-event time of one solve after a
+ * warm-up (NULL allowed). Allocates and frees its own device memory. */
+int adc_diag_eigh(int which, const adc_c128 *A, int n, double *w, adc_c128 *V, double *ms);
+
 /* FP64 FMA throughput of the device: every thread of a grid of `blocks`
  * blocks of 256 threads runs 16 independent fused multiply-add chains of
  * `iters` steps each (2 flops per FMA). tflops = flops / CUDA-event time. A

@@ -384,8 +384,8 @@ def main_rows_ground(B, eps_occ, eps_vir):
     plus the stored integral classes oovv and ovvo, at sizes where the dense
     four-virtual block does not fit: the second-order ladder
     1/2 sum_cd <ab||cd> t_ij^cd is accumulated one virtual index a at a time,
-    with <ab||cd> for that a assembled from B (Eq. 43); the vovv integrals of
-    the second-order singles likewise."""
+    with <ab||cd> (b > a) for that a assembled from B (Eq. 43); the vovv
+    integrals of the second-order singles likewise."""
     eo = np.asarray(eps_occ, np.float64)
     ev = np.asarray(eps_vir, np.float64)
     o, v = eo.size, ev.size
@@ -400,17 +400,28 @@ def main_rows_ground(B, eps_occ, eps_vir):
     g["hoo"] = 0.5 * np.einsum("njef,mjef->nm", tc, t1, optimize="greedy")
     # second-order singles: (eps_i - eps_a) t_i^a = 1/2 sum_jcd <aj||cd> t_ij^cd - 1/2 sum_jkc <jk||ic> t_jk^ac
     num = -0.5 * np.einsum("jkic,jkac->ia", _eri_fixed(B, o, "ooov"), t1, optimize="greedy")
+    Bvv, Bov = B[:, o:, o:], B[:, :o, o:]
     for a in range(v):
-        num[:, a] += 0.5 * np.einsum("jcd,ijcd->i", _eri_fixed(B, o, "vovv", {0: a}), t1, optimize="greedy")
+        # <aj||cd> = sum_Q (B_ac B_jd - B_ad B_jc): the second product is the first with c, d swapped
+        h = np.einsum("Qc,Qjd->jcd", Bvv[:, a, :], Bov, optimize="greedy")
+        num[:, a] += 0.5 * np.einsum("jcd,ijcd->i", h - h.transpose(0, 2, 1), t1, optimize="greedy")
     g["t2s"] = num / (eo[:, None] - ev[None, :])
     # second-order doubles: D t2 = 1/2 <ab||cd> t^cd + 1/2 <kl||ij> t_kl + P(ij) P(ab) sum_kc <kb||cj> t_ik^ac
     ring = np.einsum("kbcj,ikac->ijab", g["ovvo"], t1, optimize="greedy")
     t2 = ring - ring.transpose(1, 0, 2, 3) - ring.transpose(0, 1, 3, 2) + ring.transpose(1, 0, 3, 2)
     del ring
     t2 += 0.5 * np.einsum("klij,klab->ijab", _eri_fixed(B, o, "oooo"), t1, optimize="greedy")
-    for a in range(v):
-        t2[:, :, a, :] += 0.5 * np.einsum("bcd,ijcd->ijb", _eri_fixed(B, o, "vvvv", {0: a}), t1, optimize="greedy")
-    g["t2d"] = t2 / D2
+    # ladder 1/2 sum_cd <ab||cd> t_ij^cd = sum_{c<d} <ab||cd> t_ij^cd (both antisymmetric in c, d),
+    # for b > a from <ab||cd> = sum_Q (B_ac B_bd - B_ad B_bc); b < a by its antisymmetry in a, b
+    iu, ju = np.triu_indices(v, 1)
+    t1p = t1[:, :, iu, ju]
+    lad = np.zeros_like(t1)
+    for a in range(v - 1):
+        h = np.einsum("Qc,Qbd->bcd", Bvv[:, a, :], Bvv[:, a + 1:, :], optimize="greedy")
+        G = h - h.transpose(0, 2, 1)
+        lad[:, :, a, a + 1:] = np.einsum("bp,ijp->ijb", G[:, iu, ju], t1p, optimize="greedy")
+    lad -= lad.transpose(0, 1, 3, 2)
+    g["t2d"] = (t2 + lad) / D2
     return g
 
 

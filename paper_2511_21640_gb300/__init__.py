@@ -118,6 +118,7 @@ def _load():
         "adc_diag_blockops": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_diag_fp64_peak": (I, [I, I64, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_diag_set_wait_ns": (I, [ctypes.c_uint64]),
+        "adc_diag_eigh": (I, [I, P, I, P, P, ctypes.POINTER(D)]),
         "adc_sigma_adjoint": (I, [P, P, P, I64, P, P, P, ctypes.POINTER(D)]),
         "adc_state_density": (I, [P, P, P]),
         "adc_transition_density": (I, [P, P, I64, P]),
@@ -666,6 +667,18 @@ def diag_blockops(which, m, nb, n, seed=1, reps=3):
     return e.value, t.value
 
 
+def diag_eigh(which, A):
+    """Small Hermitian eigensolver on the device (``adc_diag_eigh``; 0 FP64 Jacobi, 1 FP32 start + FP64
+    refinement): (w ascending, V with eigenvectors as columns, ms)."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    w = np.empty(n, dtype=np.float64)
+    V = np.empty((n, n), dtype=np.complex128)
+    t = ctypes.c_double()
+    _check(lib.adc_diag_eigh(int(which), A.ctypes.data, n, w.ctypes.data, V.ctypes.data, ctypes.byref(t)))
+    return w, V, t.value
+
+
 def diag_fp64_peak(blocks, iters):
     """FP64 FMA throughput probe (``adc_diag_fp64_peak``): (TFLOP/s, ms)."""
     f, t = ctypes.c_double(), ctypes.c_double()
@@ -678,6 +691,6 @@ def launch_count():
     return int(lib.adc_launch_count())
 
 
-__all__ = ["Context", "Batch", "batch_plan", "batch_solve", "AdcError", "diag_gemm", "diag_blockops", "diag_fp64_peak",
+__all__ = ["Context", "Batch", "batch_plan", "batch_solve", "AdcError", "diag_gemm", "diag_blockops", "diag_eigh", "diag_fp64_peak",
            "launch_count", "lib", "LIB_PATH", "ADC_IP", "ADC_EA", "ADC_EE",
            "ADC_PREC_FP64", "ADC_PREC_BF16X3", "ADC_PREC_BF16X6"]

@@ -72,20 +72,31 @@ __global__ void k_residual(const cplx *SY, const cplx *Y, const double *w, int64
   }
 }
 
-// out[r] = || X[r] ||_2, one block per row
-__global__ void k_row_norms(const cplx *X, int64_t n, int64_t ld, double *out) {
+// part[r][b] = sum of |X[r][i]|^2 over segment b of row r (gridDim.x segments per row)
+__global__ void k_row_norms_part(const cplx *X, int64_t n, int64_t ld, double *part) {
   __shared__ double red[32];
-  const cplx *x = X + blockIdx.x * ld;
+  const cplx *x = X + blockIdx.y * ld;
+  const int64_t seg = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * seg, i1 = min(n, i0 + seg);
   double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += x[i].x * x[i].x + x[i].y * x[i].y;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += x[i].x * x[i].x + x[i].y * x[i].y;
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x < 32) {
     s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
+}
+
+// out[r] = sqrt(sum_b part[r][b]), the segments in order (deterministic)
+__global__ void k_row_norms_fin(const double *part, int nseg, int k, double *out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  double s = 0.0;
+  for (int b = 0; b < nseg; ++b) s += part[(int64_t)r * nseg + b];
+  out[r] = sqrt(s);
 }
 
 // T[r] = R[r] / (w[r] - diag), |denominator| floored at 1e-4
@@ -228,7 +239,12 @@ struct Davidson {
   std::vector<double> row_norms(const cplx *X, int k) {
     std::vector<double> h(k);
     if (!k) return h;
-    k_row_norms<<<k, 512, 0, ex.stream>>>(X, N, N, nrm.d());
+    // about four CTAs per SM in all, segments of at least 4096 elements
+    const int nseg = (int)std::max<int64_t>(1, std::min<int64_t>((608 + k - 1) / k, (N + 4095) / 4096));
+    DBuf part(ex, (size_t)k * nseg * sizeof(double));
+    k_row_norms_part<<<dim3(nseg, k), 256, 0, ex.stream>>>(X, N, N, part.d());
+    ADC_CHECK_LAUNCH();
+    k_row_norms_fin<<<(k + 127) / 128, 128, 0, ex.stream>>>(part.d(), nseg, k, nrm.d());
     ADC_CHECK_LAUNCH();
     ADC_CUDA(cudaMemcpyAsync(h.data(), nrm.d(), k * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
     ADC_CUDA(cudaStreamSynchronize(ex.stream));
@@ -250,7 +266,8 @@ struct Davidson {
       combine(ex, tmp.c(), nt, m, nt, V.c(), N, N, CR(-1.0), C1(), T.c(), N);
     }
     gram(ex, T.c(), N, nt, T.c(), N, nt, N, C1(), Gs.c(), nt);
-    jacobi_eigh(ex, Gs.c(), nt, nt, w2.d(), Zs.c(), nt, (int *)info.p);
+    if (eigh_refined_fits(nt)) eigh_refined(ex, Gs.c(), nt, nt, w2.d(), Zs.c(), nt);
+    else jacobi_eigh(ex, Gs.c(), nt, nt, w2.d(), Zs.c(), nt, (int *)info.p);
     std::vector<double> lam(nt);
     ADC_CUDA(cudaMemcpyAsync(lam.data(), w2.d(), nt * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
     ADC_CUDA(cudaStreamSynchronize(ex.stream));
@@ -310,7 +327,8 @@ struct Davidson {
     nr = std::min(std::max(nr, nroots), std::min(m, krmax));
     k_hermitize<<<(m * m + 255) / 256, 256, 0, ex.stream>>>(G.c(), mmax, m, H.c(), mmax);
     ADC_CHECK_LAUNCH();
-    jacobi_eigh(ex, H.c(), m, mmax, w.d(), Cv.c(), mmax, (int *)info.p);
+    if (eigh_refined_fits(m)) eigh_refined(ex, H.c(), m, mmax, w.d(), Cv.c(), mmax);
+    else jacobi_eigh(ex, H.c(), m, mmax, w.d(), Cv.c(), mmax, (int *)info.p);
     if (follow) pick_followed();
     ycols = 0;
     ritz_vectors(std::min(nr, nroots));

@@ -7,6 +7,7 @@
 #include "tc_gemm.cuh"
 #include "tc_slice.cuh"
 #include "blockops.cuh"
+#include "eig.cuh"
 #include "../../include/adc_gb300_diag.h"
 
 using namespace adc;
@@ -362,6 +363,47 @@ extern "C" int adc_diag_blockops(int which, int64_t m, int64_t nb, int64_t n, ui
   } catch (const Error &e) {
     if (ex.stream) { cudaStreamSynchronize(ex.stream); cudaStreamDestroy(ex.stream); }
     fprintf(stderr, "adc_diag_blockops: %s\n", e.what());
+    return e.code;
+  }
+}
+
+extern "C" int adc_diag_eigh(int which, const adc_c128 *A, int n, double *w, adc_c128 *V, double *ms) {
+  if (which < 0 || which > 1 || n < 1 || !A || !w || !V) return ADC_ERR_ARG;
+  if (which == 1 && !eigh_refined_fits(n)) return ADC_ERR_UNSUPPORTED;
+  Exec ex;
+  try {
+    ADC_CUDA(cudaStreamCreateWithFlags(&ex.stream, cudaStreamNonBlocking));
+    {
+      const int64_t nn = (int64_t)n * n;
+      DBuf Ad = cbuf(ex, nn), Aw = cbuf(ex, nn), Vd = cbuf(ex, nn), wd(ex, n * sizeof(double)), info(ex, 16);
+      ADC_CUDA(cudaMemcpyAsync(Ad.p, A, nn * sizeof(cplx), cudaMemcpyHostToDevice, ex.stream));
+      auto run = [&]() {
+        ADC_CUDA(cudaMemcpyAsync(Aw.p, Ad.p, nn * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
+        if (which == 0) jacobi_eigh(ex, Aw.c(), n, n, wd.d(), Vd.c(), n, (int *)info.p);
+        else eigh_refined(ex, Aw.c(), n, n, wd.d(), Vd.c(), n);
+      };
+      run();
+      cudaEvent_t e0, e1;
+      ADC_CUDA(cudaEventCreate(&e0));
+      ADC_CUDA(cudaEventCreate(&e1));
+      ADC_CUDA(cudaEventRecord(e0, ex.stream));
+      run();
+      ADC_CUDA(cudaEventRecord(e1, ex.stream));
+      ADC_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (ms) *ms = t;
+      ADC_CUDA(cudaMemcpyAsync(w, wd.p, n * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
+      ADC_CUDA(cudaMemcpyAsync(V, Vd.p, nn * sizeof(cplx), cudaMemcpyDeviceToHost, ex.stream));
+      ADC_CUDA(cudaStreamSynchronize(ex.stream));
+    }
+    cudaStreamDestroy(ex.stream);
+    return ADC_OK;
+  } catch (const Error &e) {
+    if (ex.stream) { cudaStreamSynchronize(ex.stream); cudaStreamDestroy(ex.stream); }
+    fprintf(stderr, "adc_diag_eigh: %s\n", e.what());
     return e.code;
   }
 }

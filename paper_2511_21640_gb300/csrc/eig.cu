@@ -159,7 +159,383 @@ k_jacobi(cplx *Ag, int n, int ldag, cplx *Vg, double *w, cplx *Vout, int ldv, in
   if (tid == 0) info[0] = done ? sweeps : -1;
 }
 
+// ---------------------------------------------------------------- FP32 start + FP64 refinement
+// For the Rayleigh-Ritz steps of the Davidson solver (n up to about 100) one
+// SM's FP64 units (two FMAs per clock) make an FP64 Jacobi take milliseconds.
+// Instead: (1) cyclic Jacobi in FP32 on A - sigma I (sigma the mean diagonal),
+// one CTA in shared memory, to about 1e-7 of the spectrum's spread; (2) FP64
+// iterative refinement of the whole eigendecomposition after Ogita and Aishima
+// (2018): with X the current eigenvectors, R = I - X^H X, S = X^H A X,
+//   lambda_i = S_ii / (1 - R_ii),
+//   F_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)  if |lambda_i - lambda_j| > delta,
+//          R_ij / 2                                       otherwise (and for i = j),
+//   X <- X (I + F),
+// which converges quadratically; delta is twice the largest off-diagonal |S_ij|.
+// The n^3 products run as small FP64 GEMMs spread over many SMs.
+
+__device__ inline float2 f2mul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+__device__ inline float block_sum_f(float v, float *red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.f;
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  float r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// A (FP64, lda) -> FP32 A - sigma I in shared memory; cyclic Jacobi (round robin);
+// eigenvectors sorted by ascending eigenvalue into X (FP64, n x n, columns), sigma into *shift
+__global__ void __launch_bounds__(1024)
+k_jacobi32(const cplx *__restrict__ Ag, int n, int lda, cplx *X, double *shift, int max_sweeps) {
+  extern __shared__ float smf[];
+  const int np = n + (n & 1), npairs = np / 2;
+  float *rc = smf, *rs = rc + npairs, *rpr = rs + npairs, *rpi = rpr + npairs;
+  int *pp = (int *)(rpi + npairs), *pq = pp + npairs;
+  float *red = (float *)(pq + npairs);
+  float2 *A = (float2 *)(((uintptr_t)(red + 64) + 15) & ~(uintptr_t)15);
+  float2 *V = A + n * n;
+  __shared__ double dred[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // shift by the mean diagonal (FP64), then round
+  double ds = 0.0;
+  for (int i = tid; i < n; i += nt) ds += Ag[(int64_t)i * lda + i].x;
+  for (int off = 16; off > 0; off >>= 1) ds += __shfl_down_sync(0xffffffffu, ds, off);
+  if ((tid & 31) == 0) dred[tid >> 5] = ds;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) t += dred[w];
+    dred[0] = t / n;
+  }
+  __syncthreads();
+  const double sigma = dred[0];
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx / n, c = idx % n;
+    const cplx a = Ag[(int64_t)r * lda + c];
+    A[idx] = make_float2((float)(a.x - (r == c ? sigma : 0.0)), (float)a.y);
+    V[idx] = make_float2(r == c ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  float loc = 0.f;
+  for (int idx = tid; idx < n * n; idx += nt) loc += A[idx].x * A[idx].x + A[idx].y * A[idx].y;
+  const float fro2 = block_sum_f(loc, red);
+  bool done = (n <= 1);
+  float prev = 3.0e38f;
+  for (int sweep = 0; !done && sweep < max_sweeps; ++sweep) {
+    for (int step = 0; step < np - 1; ++step) {
+      for (int k = tid; k < npairs; k += nt) {
+        const int a = (k == 0) ? 0 : ((k - 1 + step) % (np - 1)) + 1;
+        const int kb = np - 1 - k;
+        const int b = ((kb - 1 + step) % (np - 1)) + 1;
+        const int p = min(a, b), q = max(a, b);
+        pp[k] = p;
+        pq[k] = q;
+        float cs = 1.f, sn = 0.f, er = 1.f, ei = 0.f;
+        if (q < n) {
+          const float app = A[p * n + p].x, aqq = A[q * n + q].x;
+          const float2 apq = A[p * n + q];
+          const float mag = sqrtf(apq.x * apq.x + apq.y * apq.y);
+          if (mag > 1e-30f) {
+            er = apq.x / mag;
+            ei = apq.y / mag;
+            const float tau = (aqq - app) / (2.f * mag);
+            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            cs = 1.f / sqrtf(1.f + t * t);
+            sn = t * cs;
+          }
+        }
+        rc[k] = cs; rs[k] = sn; rpr[k] = er; rpi[k] = ei;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npairs * n; idx += nt) {
+        const int k = idx / n, col = idx % n;
+        const int p = pp[k], q = pq[k];
+        if (q >= n) continue;
+        const float cs = rc[k], sn = rs[k];
+        const float2 ap = A[p * n + col], eaq = f2mul(make_float2(rpr[k], rpi[k]), A[q * n + col]);
+        A[p * n + col] = make_float2(cs * ap.x - sn * eaq.x, cs * ap.y - sn * eaq.y);
+        A[q * n + col] = make_float2(sn * ap.x + cs * eaq.x, sn * ap.y + cs * eaq.y);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npairs * n * 2; idx += nt) {
+        const int which = idx / (npairs * n), rem = idx % (npairs * n);
+        const int k = rem / n, row = rem % n;
+        const int p = pp[k], q = pq[k];
+        if (q >= n) continue;
+        const float cs = rc[k], sn = rs[k];
+        float2 *M = which ? V : A;
+        const float2 xp = M[row * n + p], exq = f2mul(make_float2(rpr[k], -rpi[k]), M[row * n + q]);
+        M[row * n + p] = make_float2(cs * xp.x - sn * exq.x, cs * xp.y - sn * exq.y);
+        M[row * n + q] = make_float2(sn * xp.x + cs * exq.x, sn * xp.y + cs * exq.y);
+      }
+      __syncthreads();
+    }
+    float off = 0.f;
+    for (int idx = tid; idx < n * n; idx += nt)
+      if (idx / n != idx % n) off += A[idx].x * A[idx].x + A[idx].y * A[idx].y;
+    off = block_sum_f(off, red);
+    // converged, or at the FP32 rounding floor (the off-diagonal norm no longer drops)
+    done = (off <= 1e-13f * fro2) || (off == 0.f) || (sweep >= 2 && off > 0.25f * prev);
+    prev = off;
+  }
+  // columns sorted by ascending eigenvalue, promoted to FP64
+  for (int i = tid; i < n; i += nt) {
+    const float di = A[i * n + i].x;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const float dj = A[j * n + j].x;
+      if (dj < di || (dj == di && j < i)) ++rank;
+    }
+    for (int r = 0; r < n; ++r) X[(int64_t)r * n + rank] = cmake((double)V[r * n + i].x, (double)V[r * n + i].y);
+  }
+  if (tid == 0) *shift = sigma;
+}
+
+// C = op(A) op(B) (n x n, FP64): 8 x 8 output tile per CTA, A rows and B
+// columns of the tile staged in shared memory; opA: 0 = A, 1 = A^H; B as is;
+// with shift, A - shift I is used for A (opA = 0). beta_one adds C0 (C = C0 + AB).
+constexpr int SG_T = 8;
+__global__ void __launch_bounds__(SG_T * SG_T)
+k_small_gemm(const cplx *__restrict__ A, int lda, int opA, const double *shift, const cplx *__restrict__ B, int ldb,
+             int n, const cplx *C0, cplx *C, int ldc) {
+  extern __shared__ double smg[];
+  cplx *sa = (cplx *)smg;            // [SG_T][n] rows i of op(A)
+  cplx *sb = sa + SG_T * n;          // [n][SG_T] columns j of B
+  const int i0 = blockIdx.y * SG_T, j0 = blockIdx.x * SG_T;
+  const double sh = shift ? *shift : 0.0;
+  for (int e = threadIdx.x; e < SG_T * n; e += blockDim.x) {
+    const int ii = e / n, k = e % n, i = i0 + ii;
+    cplx a = cmake(0.0, 0.0);
+    if (i < n) {
+      if (opA) { a = A[(int64_t)k * lda + i]; a.y = -a.y; }
+      else { a = A[(int64_t)i * lda + k]; if (k == i) a.x -= sh; }
+    }
+    sa[ii * n + k] = a;
+    const int k2 = e / SG_T, jj = e % SG_T, j = j0 + jj;
+    sb[k2 * SG_T + jj] = (j < n) ? B[(int64_t)k2 * ldb + j] : cmake(0.0, 0.0);
+  }
+  __syncthreads();
+  const int ii = threadIdx.x / SG_T, jj = threadIdx.x % SG_T;
+  const int i = i0 + ii, j = j0 + jj;
+  double re = 0.0, im = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const cplx a = sa[ii * n + k], b = sb[k * SG_T + jj];
+    re = fma(a.x, b.x, re);
+    re = fma(-a.y, b.y, re);
+    im = fma(a.x, b.y, im);
+    im = fma(a.y, b.x, im);
+  }
+  if (i < n && j < n) {
+    cplx r = cmake(re, im);
+    if (C0) r = cadd(r, C0[(int64_t)i * ldc + j]);
+    C[(int64_t)i * ldc + j] = r;
+  }
+}
+
+// One refinement step: from H = X^H X and S = X^H (A - shift) X, the eigenvalue
+// estimates lam and the correction F (F = I + F written, for X <- X (I + F)).
+__global__ void __launch_bounds__(1024)
+k_oa_step(const cplx *__restrict__ H, const cplx *__restrict__ S, int n, double *lam, cplx *F, double *offmax) {
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) lam[i] = S[(int64_t)i * n + i].x / H[(int64_t)i * n + i].x;
+  double om = 0.0;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    if (i != j) {
+      const cplx sij = S[idx];
+      om = fmax(om, sqrt(sij.x * sij.x + sij.y * sij.y));
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) om = fmax(om, __shfl_down_sync(0xffffffffu, om, off));
+  if ((tid & 31) == 0) red[tid >> 5] = om;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) t = fmax(t, red[w]);
+    red[0] = t;
+    *offmax = t;
+  }
+  __syncthreads();
+  const double delta = 2.0 * red[0];
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    // R = I - H
+    cplx r = cmake((i == j ? 1.0 : 0.0) - H[idx].x, -H[idx].y);
+    cplx f;
+    if (i == j) {
+      f = cmake(1.0 + 0.5 * r.x, 0.0);
+    } else {
+      const double li = lam[i], lj = lam[j];
+      if (fabs(lj - li) > delta) {
+        const cplx num = cmake(S[idx].x + lj * r.x, S[idx].y + lj * r.y);
+        f = cmake(num.x / (lj - li), num.y / (lj - li));
+      } else {
+        f = cmake(0.5 * r.x, 0.5 * r.y);
+      }
+    }
+    F[idx] = f;
+  }
+}
+
+// Clusters: runs of consecutive columns (the FP32 start sorts them by
+// eigenvalue) whose estimates lie within delta of their neighbour. There the
+// first-order correction only orthonormalises; each cluster of at most
+// CL_MAX columns is then diagonalised exactly: the FP64 Jacobi eigenvectors U
+// of its block of S rotate its columns of I + F (Fout = (I + F) blockdiag(U)).
+constexpr int CL_MAX = 8;
+__global__ void __launch_bounds__(1024)
+k_cluster_rotate(const cplx *__restrict__ F, const cplx *__restrict__ S, const double *lam, const double *offmax,
+                 int n, cplx *Fout) {
+  __shared__ cplx U[128 * CL_MAX];   // U of the cluster starting at column i, rows i.. of U[i*CL_MAX ...]
+  __shared__ int start[128], size[128];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double delta = 2.0 * offmax[0];
+  for (int i = tid; i < n; i += nt) {
+    const bool joins_prev = i > 0 && fabs(lam[i] - lam[i - 1]) <= delta;
+    int e = i + 1;
+    while (e < n && fabs(lam[e] - lam[e - 1]) <= delta) ++e;
+    start[i] = joins_prev ? -1 : i;
+    size[i] = e - i;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    if (start[i] != i) continue;
+    const int sc = size[i];
+    if (sc < 2 || sc > CL_MAX) continue;
+    cplx a[CL_MAX][CL_MAX], u[CL_MAX][CL_MAX];
+    for (int r = 0; r < sc; ++r)
+      for (int c = 0; c < sc; ++c) {
+        a[r][c] = S[(int64_t)(i + r) * n + i + c];
+        u[r][c] = cmake(r == c ? 1.0 : 0.0, 0.0);
+      }
+    for (int sweep = 0; sweep < 12; ++sweep) {
+      double off = 0.0, dia = 0.0;
+      for (int r = 0; r < sc; ++r)
+        for (int c = 0; c < sc; ++c) {
+          const double m2 = a[r][c].x * a[r][c].x + a[r][c].y * a[r][c].y;
+          if (r == c) dia += m2; else off += m2;
+        }
+      if (off <= 1e-32 * dia || off == 0.0) break;
+      for (int p = 0; p < sc - 1; ++p)
+        for (int q = p + 1; q < sc; ++q) {
+          const cplx apq = a[p][q];
+          const double mag = sqrt(apq.x * apq.x + apq.y * apq.y);
+          if (mag <= 1e-300) continue;
+          const cplx e = cmake(apq.x / mag, apq.y / mag), ec = cconj(e);
+          const double tau = (a[q][q].x - a[p][p].x) / (2.0 * mag);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+          for (int c = 0; c < sc; ++c) {   // rows p, q
+            const cplx ap = a[p][c], eaq = cmul(e, a[q][c]);
+            a[p][c] = cmake(cs * ap.x - sn * eaq.x, cs * ap.y - sn * eaq.y);
+            a[q][c] = cmake(sn * ap.x + cs * eaq.x, sn * ap.y + cs * eaq.y);
+          }
+          for (int r = 0; r < sc; ++r) {   // columns p, q of a and u
+            const cplx xp = a[r][p], exq = cmul(ec, a[r][q]);
+            a[r][p] = cmake(cs * xp.x - sn * exq.x, cs * xp.y - sn * exq.y);
+            a[r][q] = cmake(sn * xp.x + cs * exq.x, sn * xp.y + cs * exq.y);
+            const cplx up = u[r][p], euq = cmul(ec, u[r][q]);
+            u[r][p] = cmake(cs * up.x - sn * euq.x, cs * up.y - sn * euq.y);
+            u[r][q] = cmake(sn * up.x + cs * euq.x, sn * up.y + cs * euq.y);
+          }
+        }
+    }
+    for (int r = 0; r < sc; ++r)
+      for (int c = 0; c < sc; ++c) U[(i + r) * CL_MAX + c] = u[r][c];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx / n, j = idx % n;
+    int s0 = j;
+    while (s0 > 0 && start[s0] != s0) --s0;
+    const int sc = size[s0];
+    if (sc < 2 || sc > CL_MAX) {
+      Fout[idx] = F[idx];
+      continue;
+    }
+    const int jj = j - s0;
+    cplx acc = cmake(0.0, 0.0);
+    for (int l = 0; l < sc; ++l) acc = cadd(acc, cmul(F[(int64_t)r * n + s0 + l], U[(s0 + l) * CL_MAX + jj]));
+    Fout[idx] = acc;
+  }
+}
+
+// eigenvalues lam + shift sorted ascending into w, the columns of X likewise into V (ldv)
+__global__ void k_sort_out(const double *lam, const double *shift, const cplx *X, int n, double *w, cplx *V,
+                           int ldv) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double di = lam[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double dj = lam[j];
+      if (dj < di || (dj == di && j < i)) ++rank;
+    }
+    w[rank] = di + *shift;
+    for (int r = 0; r < n; ++r) V[(int64_t)r * ldv + rank] = X[(int64_t)r * n + i];
+  }
+}
+
 }  // namespace
+
+bool eigh_refined_fits(int n) {
+  const int np = n + (n & 1);
+  const size_t smem = (size_t)np / 2 * 4 * sizeof(float) + (size_t)np * sizeof(int) + 64 * sizeof(float) + 16 +
+                      2 * (size_t)n * n * sizeof(float2);
+  return n >= 1 && n <= 128 && smem <= 200 * 1024;
+}
+
+void eigh_refined(Exec &ex, const cplx *A, int n, int lda, double *w, cplx *V, int ldv, int nsteps) {
+  if (n <= 0) return;
+  ADC_REQUIRE(eigh_refined_fits(n), ADC_ERR_UNSUPPORTED, "eigh_refined: matrix too large");
+  const int np = n + (n & 1);
+  const size_t smem = (size_t)np / 2 * 4 * sizeof(float) + (size_t)np * sizeof(int) + 64 * sizeof(float) + 16 +
+                      2 * (size_t)n * n * sizeof(float2);
+  static bool attr32 = false;
+  if (!attr32) {
+    ADC_CUDA(cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    ADC_CUDA(cudaFuncSetAttribute(k_small_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    attr32 = true;
+  }
+  const int64_t nn = (int64_t)n * n;
+  DBuf X0 = cbuf(ex, nn), X1 = cbuf(ex, nn), T = cbuf(ex, nn), H = cbuf(ex, nn), S = cbuf(ex, nn), F = cbuf(ex, nn);
+  DBuf lam(ex, n * sizeof(double)), sc(ex, 2 * sizeof(double));
+  k_jacobi32<<<1, 1024, smem, ex.stream>>>(A, n, lda, X0.c(), sc.d(), 30);
+  ADC_CHECK_LAUNCH();
+  const dim3 g((n + SG_T - 1) / SG_T, (n + SG_T - 1) / SG_T);
+  const size_t gs = 2 * (size_t)SG_T * n * sizeof(cplx);
+  cplx *X = X0.c(), *Xn = X1.c();
+  for (int it = 0; it < nsteps; ++it) {
+    // T = (A - shift) X, S = X^H T, H = X^H X
+    k_small_gemm<<<g, SG_T * SG_T, gs, ex.stream>>>(A, lda, 0, sc.d(), X, n, n, nullptr, T.c(), n);
+    ADC_CHECK_LAUNCH();
+    k_small_gemm<<<g, SG_T * SG_T, gs, ex.stream>>>(X, n, 1, nullptr, T.c(), n, n, nullptr, S.c(), n);
+    ADC_CHECK_LAUNCH();
+    k_small_gemm<<<g, SG_T * SG_T, gs, ex.stream>>>(X, n, 1, nullptr, X, n, n, nullptr, H.c(), n);
+    ADC_CHECK_LAUNCH();
+    k_oa_step<<<1, 1024, 0, ex.stream>>>(H.c(), S.c(), n, lam.d(), F.c(), sc.d() + 1);
+    ADC_CHECK_LAUNCH();
+    k_cluster_rotate<<<1, 1024, 0, ex.stream>>>(F.c(), S.c(), lam.d(), sc.d() + 1, n, T.c());
+    ADC_CHECK_LAUNCH();
+    // X <- X (I + F) blockdiag(U)
+    k_small_gemm<<<g, SG_T * SG_T, gs, ex.stream>>>(X, n, 0, nullptr, T.c(), n, n, nullptr, Xn, n);
+    ADC_CHECK_LAUNCH();
+    std::swap(X, Xn);
+  }
+  // the eigenvalues of the last step are Rayleigh quotients of the vectors before
+  // its update, exact to the square of their error
+  k_sort_out<<<1, 256, 0, ex.stream>>>(lam.d(), sc.d(), X, n, w, V, ldv);
+  ADC_CHECK_LAUNCH();
+}
 
 void jacobi_eigh(Exec &ex, cplx *A, int n, int lda, double *w, cplx *V, int ldv, int *info_dev) {
   if (n <= 0) return;

@@ -259,13 +259,16 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
   int b_nfast = (sBn == 1) ? 1 : 0;
   dim3 block(256);
   const int64_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-  // split K when the output tiles alone cannot fill the GPU
+  // split K when the output tiles alone cannot fill the GPU (down to chunks of
+  // 16: on GB300's FP64 units a few CTAs over a short K still take far longer
+  // than the partial sums cost), the partial buffer within 2^26 elements
   int ksplit = 1;
   const int64_t want = 2 * (int64_t)num_sms();
-  if (tiles * batch < want && K > 2048) {
+  if (tiles * batch < want && K >= 32) {
     int64_t s = (want + tiles * batch - 1) / (tiles * batch);
-    s = std::min<int64_t>(s, K / 1024);
+    s = std::min<int64_t>(s, (K + BKK - 1) / BKK);
     s = std::min<int64_t>(s, 256);
+    s = std::min<int64_t>(s, std::max<int64_t>(1, ((int64_t)1 << 26) / std::max<int64_t>(1, M * N * batch)));
     ksplit = (int)std::max<int64_t>(1, s);
   }
   const int64_t bmax = 65535 / ksplit;
