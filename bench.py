@@ -679,6 +679,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-subspace", type=int, default=0, help="Davidson subspace limit (0: the library's default)")
     ap.add_argument("--block", type=int, default=0, help="Davidson block size (0: the number of roots)")
+    ap.add_argument("--correction", default="davidson", choices=["davidson", "olsen"],
+                    help="Davidson correction vectors (preconditioned residuals, or Olsen's)")
     ap.add_argument("--ref-rows", type=int, default=1,
                     help="reference arm: oracle rows per step (about 30 s of one core each)")
     ap.add_argument("--cpu-rows", type=int, default=16,
@@ -728,7 +730,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctx = adcgpu.Context(B, eo, ev, kind=kind, order=order, x=x, stream="torch", refine=args.refine,
-                         max_subspace=args.max_subspace, block=args.block)
+                         max_subspace=args.max_subspace, block=args.block, correction=args.correction)
     torch.cuda.synchronize()
     init_s = time.perf_counter() - t0
     log(f"init {init_s:.1f} s, N = {ctx.N}")
@@ -832,6 +834,14 @@ def main():
     sig_rel = rel_to_fp64(ctx.sigma(Xs, args.mixed))
     sig_rel_sliced = rel_to_fp64(ctx.sigma(Xs, "sliced")) if "sliced" in sig else None
 
+    # ---- the residuals of the timed solve's roots recomputed with the FP64 sigma
+    # (the solve itself checks them with the sliced product by default)
+    om_v, Yv, e_v, _, _ = ctx.davidson(nroots, tol=tol, max_iter=300, precision=args.mixed, want_vectors=True)
+    Yt = torch.from_numpy(Yv).cuda()
+    R64 = ctx.sigma(Yt, "fp64") - torch.from_numpy(np.asarray(om_v)).cuda()[:, None] * Yt
+    resid_fp64 = [float(r) for r in R64.abs().pow(2).sum(1).sqrt().cpu().numpy()]
+    del Yt, R64
+
     # ---- FP64 Davidson for the comparison and the 1e-6 Eh check
     fp64 = None
     if not args.no_fp64_davidson and cfg.get("fp64_davidson", True):
@@ -852,7 +862,8 @@ def main():
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         with adcgpu.Context(Bh, eoh, evh, kind=kind, order=order, x=x, refine=args.refine,
-                            setup=args.e2e_setup, max_subspace=args.max_subspace, block=args.block) as c2:
+                            setup=args.e2e_setup, max_subspace=args.max_subspace, block=args.block,
+                            correction=args.correction) as c2:
             t3 = time.perf_counter()
             om2, _, e2, st2, rc2 = c2.davidson(nroots, tol=tol, max_iter=300, precision=args.mixed,
                                                want_vectors=False)
@@ -891,7 +902,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.config, "kind": kind, "order": order, "x": x, "nocc": o, "nvir": v, "naux": Q,
                    "nroots": nroots, "tol_fp64_residual": tol, "N": ctx.N, "replicas": world,
-                   "max_subspace": args.max_subspace, "block": args.block,
+                   "max_subspace": args.max_subspace, "block": args.block, "correction": args.correction,
                    "l2": "operators larger than L2 (packed <ab||cd> 6.3 GB FP64, 3.2 GB per BF16 plane)"},
         "clocks": clk, "gpu_launches": int(launches), "roofline": roof, "roofline_tensor_core": roof_tc,
         "roofline_by_kernel": by_kernel,
@@ -903,6 +914,8 @@ def main():
         "refine": args.refine,
         "fp64_davidson": fp64,
         "mixed_davidson": {"omega": [float(w) for w in om], "err64": [float(e) for e in e64],
+                           "err64_source": "sliced product" if args.refine == "sliced" else "fp64 product",
+                           "residual_fp64_recomputed": resid_fp64,
                            "iterations": last["iterations"], "sigma_calls": last["sigma_calls"],
                            "sigma_calls_fp64": last["sigma_calls_fp64"], "rc": int(rc)},
         "init_s": init_s, "e2e": e2e, "cpu_baseline": cpu,

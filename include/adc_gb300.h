@@ -114,6 +114,11 @@ typedef struct {
                            virtual index, never whole, when the dense
                            <ab||cd> would take more than 32 GiB; 1 = always
                            in chunks; -1 = always from the dense block */
+  int correction;       /* Davidson correction vectors: 0 = the residuals
+                           preconditioned by (omega - diag M)^-1 (default);
+                           1 = Olsen's: (omega - diag M)^-1 (r - e y) with e
+                           chosen so that the correction is orthogonal to its
+                           Ritz vector y */
 } adc_opts;
 
 typedef struct {
@@ -222,7 +227,11 @@ int adc_main_block(adc_ctx *ctx, adc_c128 *M11);
  *   guess   NULL, or [nguess][N] starting vectors (nguess >= nroots).
  *   omega   [nroots] eigenvalues, ascending (host or device).
  *   Y       NULL or [nroots][N] eigenvectors.
- *   err64   NULL or [nroots] FP64 residual norms.
+ *   err64   NULL or [nroots] residual norms ||M y - omega y|| of the
+ *           returned vectors, from the refinement product: FP64 CUDA cores,
+ *           or with opts.refine = ADC_PREC_SLICED the sliced product (about
+ *           40 significant bits, well below any tolerance above 1e-10 of the
+ *           norm of M y); an FP64 check is adc_sigma(ADC_PREC_FP64) of Y.
  *   st      NULL or statistics.
  * Returns ADC_ERR_NOCONV (with the best results written) if max_iter is hit. */
 int adc_davidson(adc_ctx *ctx, int nroots, double tol, int max_iter,

@@ -39,7 +39,8 @@ class adc_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("stream", ctypes.c_void_p), ("block", ctypes.c_int),
                 ("max_subspace", ctypes.c_int), ("herm_tol", ctypes.c_double),
                 ("mem_limit", ctypes.c_int64), ("verbose", ctypes.c_int), ("dd_order", ctypes.c_int),
-                ("refine", ctypes.c_int), ("setup", ctypes.c_int), ("ee_vvvv", ctypes.c_int)]
+                ("refine", ctypes.c_int), ("setup", ctypes.c_int), ("ee_vvvv", ctypes.c_int),
+                ("correction", ctypes.c_int)]
 
 
 class adc_stats(ctypes.Structure):
@@ -201,7 +202,7 @@ class Context:
 
     def __init__(self, B, eps_occ, eps_vir, kind="IP", order=3, x=1.0, precision="fp64", stream=None,
                  block=0, max_subspace=0, herm_tol=1e-12, mem_limit=0, verbose=False, dd_order=1,
-                 refine="fp64", setup="fp64", vvvv="auto"):
+                 refine="fp64", setup="fp64", vvvv="auto", correction="davidson"):
         o = adc_opts()
         lib.adc_opts_default(ctypes.byref(o))
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -219,6 +220,7 @@ class Context:
         o.refine = PRECISIONS[refine] if isinstance(refine, str) else int(refine)
         o.setup = PRECISIONS[setup] if isinstance(setup, str) else int(setup)
         o.ee_vvvv = {"auto": 0, "chunked": 1, "dense": -1}[vvvv]
+        o.correction = {"davidson": 0, "olsen": 1}[correction]
         naux, nmo, nmo2 = B.shape
         nocc, nvir = eps_occ.shape[0], eps_vir.shape[0]
         if nmo != nmo2 or nmo != nocc + nvir:

@@ -145,6 +145,7 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
     ADC_REQUIRE(c->opts.setup == ADC_PREC_FP64 || c->opts.setup == ADC_PREC_SLICED, ADC_ERR_ARG,
                 "opts.setup: ADC_PREC_FP64 or ADC_PREC_SLICED");
     ADC_REQUIRE(c->opts.ee_vvvv >= -1 && c->opts.ee_vvvv <= 1, ADC_ERR_ARG, "opts.ee_vvvv: -1, 0 or 1");
+    ADC_REQUIRE(c->opts.correction == 0 || c->opts.correction == 1, ADC_ERR_ARG, "opts.correction: 0 or 1");
     c->kind = kind;
     c->order = order;
     c->x = (order == 3) ? x : 0.0;

@@ -214,18 +214,7 @@ k_combine(const cplx *__restrict__ C, int64_t ldc, int m, int nr, const cplx *__
   }
 }
 
-int g_sms_blockops = 0;
-
-int sm_count() {
-  if (!g_sms_blockops) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int s = 0;
-    cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-    g_sms_blockops = s > 0 ? s : 148;
-  }
-  return g_sms_blockops;
-}
+int sm_count() { return device_sm_count(); }
 
 }  // namespace
 

@@ -113,6 +113,69 @@ __global__ void k_precondition(const cplx *R, const double *w, const int *rows, 
   }
 }
 
+// Olsen's correction: for each correction t (root rows[t]), over segment b of
+// the vector, part[t][b] = (sum conj(y) r / den, sum |y|^2 / den) with the
+// preconditioner's denominators den = w - diag (|den| floored as above)
+__global__ void k_olsen_part(const cplx *R, const cplx *Y, const double *w, const int *rows, const double *diag,
+                             int64_t n, double *part) {
+  __shared__ double red[3][32];
+  const int t = blockIdx.y, r = rows[t];
+  const int64_t seg = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * seg, i1 = min(n, i0 + seg);
+  double ar = 0.0, ai = 0.0, b = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    double den = w[r] - diag[i];
+    if (fabs(den) < 1e-4) den = (den < 0.0) ? -1e-4 : 1e-4;
+    const cplx y = Y[(int64_t)r * n + i], v = R[(int64_t)r * n + i];
+    ar += (y.x * v.x + y.y * v.y) / den;
+    ai += (y.x * v.y - y.y * v.x) / den;
+    b += (y.x * y.x + y.y * y.y) / den;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    ar += __shfl_down_sync(0xffffffffu, ar, off);
+    ai += __shfl_down_sync(0xffffffffu, ai, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { red[0][wid] = ar; red[1][wid] = ai; red[2][wid] = b; }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[threadIdx.x][k];
+    part[((int64_t)t * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = s;
+  }
+}
+
+// e_t = (y^H den^-1 r) / (y^H den^-1 y), the segment sums in order
+__global__ void k_olsen_fin(const double *part, int nseg, int nt, cplx *e) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double ar = 0.0, ai = 0.0, b = 0.0;
+  for (int s = 0; s < nseg; ++s) {
+    const double *p = part + ((int64_t)t * nseg + s) * 3;
+    ar += p[0];
+    ai += p[1];
+    b += p[2];
+  }
+  e[t] = (b != 0.0) ? cmake(ar / b, ai / b) : cmake(0.0, 0.0);
+}
+
+// T[t] = (R[r] - e_t Y[r]) / den: the correction is orthogonal to its Ritz vector
+__global__ void k_olsen_apply(const cplx *R, const cplx *Y, const double *w, const int *rows, const double *diag,
+                              const cplx *ev, int64_t nt, int64_t n, cplx *T) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nt * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = idx / n, i = idx % n;
+    const int r = rows[t];
+    const cplx e = ev[t];
+    double den = w[r] - diag[i];
+    if (fabs(den) < 1e-4) den = (den < 0.0) ? -1e-4 : 1e-4;
+    const cplx v = R[(int64_t)r * n + i], y = Y[(int64_t)r * n + i];
+    const cplx u = csub(v, cmul(e, y));
+    T[idx] = cmake(u.x / den, u.y / den);
+  }
+}
+
 // T[t] = R[rows[t]]
 __global__ void k_gather_rows(const cplx *R, const int *rows, int64_t nt, int64_t n, cplx *T) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < nt * n;
@@ -489,9 +552,24 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
       wh = d.ritz(kc);
     }
     ADC_CUDA(cudaMemcpyAsync(d.rowsb.p, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice, ex.stream));
-    k_precondition<<<grid1d((int64_t)rows.size() * N, 256), 256, 0, ex.stream>>>(
-        d.R.c(), d.w.d(), (const int *)d.rowsb.p, c->diag.d(), (int64_t)rows.size(), N, d.T.c());
-    ADC_CHECK_LAUNCH();
+    if (c->opts.correction == 1) {
+      const int nt = (int)rows.size();
+      const int nseg = (int)std::max<int64_t>(1, std::min<int64_t>((608 + nt - 1) / nt, (N + 4095) / 4096));
+      DBuf part(ex, (size_t)nt * nseg * 3 * sizeof(double));
+      k_olsen_part<<<dim3(nseg, nt), 256, 0, ex.stream>>>(d.R.c(), d.Y.c(), d.w.d(), (const int *)d.rowsb.p,
+                                                           c->diag.d(), N, part.d());
+      ADC_CHECK_LAUNCH();
+      DBuf ev = cbuf(ex, nt);
+      k_olsen_fin<<<(nt + 31) / 32, 32, 0, ex.stream>>>(part.d(), nseg, nt, ev.c());
+      ADC_CHECK_LAUNCH();
+      k_olsen_apply<<<grid1d((int64_t)nt * N, 256), 256, 0, ex.stream>>>(
+          d.R.c(), d.Y.c(), d.w.d(), (const int *)d.rowsb.p, c->diag.d(), ev.c(), nt, N, d.T.c());
+      ADC_CHECK_LAUNCH();
+    } else {
+      k_precondition<<<grid1d((int64_t)rows.size() * N, 256), 256, 0, ex.stream>>>(
+          d.R.c(), d.w.d(), (const int *)d.rowsb.p, c->diag.d(), (int64_t)rows.size(), N, d.T.c());
+      ADC_CHECK_LAUNCH();
+    }
     int na = d.orthonormalise((int)rows.size());
     if (na == 0) {
       // the preconditioned corrections lie in the subspace (an eigenvalue next

@@ -500,12 +500,8 @@ void eigh_refined(Exec &ex, const cplx *A, int n, int lda, double *w, cplx *V, i
   const int np = n + (n & 1);
   const size_t smem = (size_t)np / 2 * 4 * sizeof(float) + (size_t)np * sizeof(int) + 64 * sizeof(float) + 16 +
                       2 * (size_t)n * n * sizeof(float2);
-  static bool attr32 = false;
-  if (!attr32) {
-    ADC_CUDA(cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    ADC_CUDA(cudaFuncSetAttribute(k_small_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-    attr32 = true;
-  }
+  set_smem_limit((const void *)k_jacobi32, 200 * 1024);
+  set_smem_limit((const void *)k_small_gemm, 64 * 1024);
   const int64_t nn = (int64_t)n * n;
   DBuf X0 = cbuf(ex, nn), X1 = cbuf(ex, nn), T = cbuf(ex, nn), H = cbuf(ex, nn), S = cbuf(ex, nn), F = cbuf(ex, nn);
   DBuf lam(ex, n * sizeof(double)), sc(ex, 2 * sizeof(double));
@@ -548,11 +544,7 @@ void jacobi_eigh(Exec &ex, cplx *A, int n, int lda, double *w, cplx *V, int ldv,
   const size_t mats = 16 + 2 * (size_t)n * n * sizeof(cplx);
   const int in_smem = (smem + mats <= kMaxSmem) ? 1 : 0;
   if (in_smem) smem += mats;
-  static bool attr_set = false;
-  if (!attr_set) {
-    ADC_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem));
-    attr_set = true;
-  }
+  set_smem_limit((const void *)k_jacobi, (int)kMaxSmem);
   k_jacobi<<<1, 1024, smem, ex.stream>>>(A, n, lda, work.c(), w, V, ldv, info_dev, 40, 1e-14, in_smem);
   ADC_CHECK_LAUNCH();
 }

@@ -371,23 +371,13 @@ void make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t kp2, int
   ADC_REQUIRE(r == CUDA_SUCCESS, ADC_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
 }
 
-int g_sms = 0;
 
 template <int BN, int ST>
 void launch_tc(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N2, cplx alpha, cplx beta,
                cplx *out, int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, int nseg) {
   using L = TcLayout<BN, ST>;
-  static bool attr = false;
-  if (!attr) {
-    ADC_CUDA(cudaFuncSetAttribute(k_tc_gemm<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM));
-    attr = true;
-  }
-  if (!g_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 148;
-  }
+  set_smem_limit((const void *)k_tc_gemm<BN, ST>, L::SMEM);
+  const int g_sms = device_sm_count();
   CUtensorMap mAh, mAl, mAl2, mBh, mBl, mBl2;
   const int64_t kp2 = 2 * A.kp;
   make_map(&mAh, A.hi.p, A.rows, kp2, TC_BM);
@@ -784,16 +774,7 @@ namespace adc {
 
 namespace {
 
-int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
-  return n;
-}
+int sm_count() { return device_sm_count(); }
 
 // smallest tile width (multiple of 32, at most 256) covering N2 real columns
 // when it is narrow, else the widest tile
@@ -826,11 +807,7 @@ static int cached_bn(const TcJobDesc &d) {
 void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &in, TcGroup &grp, int *err, bool may_tune) {
   const int nj = (int)in.size();
   if (nj == 0) return;
-  static bool attr = false;
-  if (!attr) {
-    ADC_CUDA(cudaFuncSetAttribute(k_tc_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, TgLayout::SMEM));
-    attr = true;
-  }
+  set_smem_limit((const void *)k_tc_grouped, TgLayout::SMEM);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   ADC_CUDA(cudaStreamIsCapturing(ex.stream, &cs));
   const bool capturing = (cs != cudaStreamCaptureStatusNone);

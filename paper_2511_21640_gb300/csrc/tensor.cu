@@ -3,6 +3,11 @@
 #include <cstring>
 #include <map>
 
+#include <map>
+#include <mutex>
+#include <set>
+#include <tuple>
+
 #include "tensor.cuh"
 #include "tc_slice.cuh"
 
@@ -216,23 +221,37 @@ __global__ void k_splitk_reduce(const cplx *__restrict__ part, int ksplit, int64
 }
 }  // namespace
 
-static int g_num_sms = 0;
-static void zgemm_attr() {
-  static bool done = false;
-  if (!done) {
-    ADC_CUDA(cudaFuncSetAttribute(k_zgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, ZG_SMEM));
-    done = true;
-  }
+namespace {
+std::mutex g_dev_mu;
+std::map<int, int> g_dev_sms;
+std::set<std::tuple<const void *, int, int>> g_smem_set;
+}  // namespace
+
+int device_sm_count() {
+  int dev = 0;
+  ADC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  auto it = g_dev_sms.find(dev);
+  if (it != g_dev_sms.end()) return it->second;
+  int s = 0;
+  ADC_CUDA(cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev));
+  if (s <= 0) s = 148;
+  g_dev_sms[dev] = s;
+  return s;
 }
-static int num_sms() {
-  if (!g_num_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 128;
-  }
-  return g_num_sms;
+
+void set_smem_limit(const void *kernel, int bytes) {
+  int dev = 0;
+  ADC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  const auto key = std::make_tuple(kernel, dev, bytes);
+  if (g_smem_set.count(key)) return;
+  ADC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  g_smem_set.insert(key);
 }
+
+static void zgemm_attr() { set_smem_limit((const void *)k_zgemm, ZG_SMEM); }
+static int num_sms() { return device_sm_count(); }
 
 void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha, const cplx *A,
            int64_t sAb, int64_t sAm, int64_t sAk, bool conjA, const cplx *B, int64_t sBb,

@@ -145,6 +145,12 @@ void zaxpby(Exec &ex, int64_t n, cplx a, const cplx *x, cplx b, cplx *y);
 void diag_mul_add(Exec &ex, int64_t k, int64_t n, const double *d, const cplx *x, int64_t ldx,
                   cplx *y, int64_t ldy, double s);
 void fill_zero(Exec &ex, void *p, size_t bytes);
+// number of SMs of the current device (looked up once per device)
+int device_sm_count();
+// raise a kernel's dynamic shared-memory limit on the current device, once per
+// (kernel, device): the attribute belongs to the device, so a process that
+// drives several GPUs sets it on each
+void set_smem_limit(const void *kernel, int bytes);
 
 // ---------------------------------------------------------------- contraction engine
 // C[lc] = alpha * sum A[la] B[lb] + beta * C[lc] with Einstein labels (one char

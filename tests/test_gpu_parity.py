@@ -285,6 +285,22 @@ def test_tensor_core_wait_gives_up_and_context_recovers(gpu, prec, tol):
     assert _rel(again, ref).max() < tol
 
 
+@pytest.mark.parametrize("kind,prec", [("EA", "fp64"), ("IP", "fp64"), ("EA", "bf16x3")])
+def test_davidson_olsen_correction(gpu, kind, prec):
+    """Olsen's correction vectors (opts.correction = 1) reach the dense oracle's
+    lowest roots like the plain preconditioned residuals."""
+    p = make_problem(5, 14, 24, seed=57, sigma=0.08, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    M = oadc.explicit_matrix(kind, 3, 0.5, p.B, p.eps_occ, p.eps_vir)
+    w = np.linalg.eigvalsh(M)[:4]
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=3, x=0.5, correction="olsen",
+                     refine="sliced") as ctx:
+        om, Y, e64, st, rc = ctx.davidson(4, tol=1e-8, precision=prec)
+    assert rc == 0
+    assert np.abs(om - w).max() < 1e-8
+    R = Y @ M.T - om[:, None] * Y
+    assert np.linalg.norm(R, axis=1).max() < 1e-7
+
+
 def test_davidson_noconv_returns_best(gpu):
     p = make_problem(5, 12, 20, seed=3, sigma=0.08)
     with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP", order=3, x=1.0) as ctx:
