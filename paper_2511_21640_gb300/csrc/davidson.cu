@@ -329,8 +329,9 @@ struct Davidson {
       combine(ex, tmp.c(), nt, m, nt, V.c(), N, N, CR(-1.0), C1(), T.c(), N);
     }
     gram(ex, T.c(), N, nt, T.c(), N, nt, N, C1(), Gs.c(), nt);
-    if (eigh_refined_fits(nt)) eigh_refined(ex, Gs.c(), nt, nt, w2.d(), Zs.c(), nt);
-    else jacobi_eigh(ex, Gs.c(), nt, nt, w2.d(), Zs.c(), nt, (int *)info.p);
+    // FP64 Jacobi: its small eigenvalues (which decide the directions kept)
+    // carry relative accuracy; the block is at most a few vectors wide
+    jacobi_eigh(ex, Gs.c(), nt, nt, w2.d(), Zs.c(), nt, (int *)info.p);
     std::vector<double> lam(nt);
     ADC_CUDA(cudaMemcpyAsync(lam.data(), w2.d(), nt * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
     ADC_CUDA(cudaStreamSynchronize(ex.stream));
@@ -390,6 +391,8 @@ struct Davidson {
     nr = std::min(std::max(nr, nroots), std::min(m, krmax));
     k_hermitize<<<(m * m + 255) / 256, 256, 0, ex.stream>>>(G.c(), mmax, m, H.c(), mmax);
     ADC_CHECK_LAUNCH();
+    // the projected matrix: FP32 Jacobi start refined in FP64 (absolute accuracy
+    // about n eps |omega|, which is what the Ritz pairs need)
     if (eigh_refined_fits(m)) eigh_refined(ex, H.c(), m, mmax, w.d(), Cv.c(), mmax);
     else jacobi_eigh(ex, H.c(), m, mmax, w.d(), Cv.c(), mmax, (int *)info.p);
     if (follow) pick_followed();

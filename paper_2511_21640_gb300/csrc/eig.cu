@@ -284,7 +284,7 @@ k_jacobi32(const cplx *__restrict__ Ag, int n, int lda, cplx *X, double *shift, 
       if (idx / n != idx % n) off += A[idx].x * A[idx].x + A[idx].y * A[idx].y;
     off = block_sum_f(off, red);
     // converged, or at the FP32 rounding floor (the off-diagonal norm no longer drops)
-    done = (off <= 1e-13f * fro2) || (off == 0.f) || (sweep >= 2 && off > 0.25f * prev);
+    done = (off <= 1e-13f * fro2) || (off == 0.f) || (off <= 1e-9f * fro2 && sweep >= 1 && off > 0.25f * prev);
     prev = off;
   }
   // columns sorted by ascending eigenvalue, promoted to FP64

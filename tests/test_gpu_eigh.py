@@ -5,8 +5,12 @@ the spectra the Davidson meets (a large common shift, spread of a few hundred),
 including exactly degenerate pairs (time-reversal doubling) and pairs closer
 than FP32 can resolve. Eigenvalues within 1e-13 of the spectral norm,
 residuals ||A v - w v|| within 1e-13 of it, eigenvectors orthonormal to 1e-13
-(eigenvectors of degenerate pairs are not unique, so only these properties are
-compared)."""
+(1e-12 for the refinement, whose orthonormality ends near eps |A| over the
+smallest gap); eigenvectors of degenerate pairs are not unique, so only these
+properties are compared. The refined solver is for matrices whose eigenvalues
+are needed to absolute accuracy (the Rayleigh-Ritz step); small eigenvalues of
+a positive definite matrix keep only absolute accuracy there, which is why the
+Davidson's Gram matrices of new directions stay with the FP64 Jacobi."""
 import numpy as np
 import pytest
 
@@ -33,13 +37,13 @@ def _hermitian(n, seed, spectrum=None, shift=-3700.0, spread=300.0):
     return 0.5 * (A + A.conj().T)
 
 
-def _check(A, w, V):
+def _check(A, w, V, orth=1e-13):
     nrm = np.abs(np.linalg.eigvalsh(A)).max()
     wr = np.linalg.eigvalsh(A)
     assert np.abs(w - wr).max() < 1e-13 * nrm, np.abs(w - wr).max() / nrm
     res = np.linalg.norm(A @ V - V * w, axis=0).max()
     assert res < 1e-13 * nrm, res / nrm
-    assert np.abs(V.conj().T @ V - np.eye(A.shape[0])).max() < 1e-13
+    assert np.abs(V.conj().T @ V - np.eye(A.shape[0])).max() < orth
 
 
 @pytest.mark.parametrize("which", [0, 1])
@@ -47,7 +51,8 @@ def _check(A, w, V):
 def test_eigh_random(gpu, which, n):
     A = _hermitian(n, seed=70 + n)
     w, V, ms = gpu.diag_eigh(which, A)
-    _check(A, w, V)
+    # the refinement's orthonormality ends near eps |A| / (smallest gap), about 1e-13 here
+    _check(A, w, V, orth=1e-13 if which == 0 else 1e-12)
 
 
 @pytest.mark.parametrize("which", [0, 1])
@@ -57,7 +62,7 @@ def test_eigh_degenerate_and_close(gpu, which):
     lam = np.concatenate([base, base, base[:8] + 1e-9, base[8:16] + 1e-6])   # exact pairs, near pairs
     A = _hermitian(lam.size, seed=82, spectrum=lam)
     w, V, ms = gpu.diag_eigh(which, A)
-    _check(A, w, V)
+    _check(A, w, V, orth=1e-13 if which == 0 else 1e-12)
 
 
 def test_eigh_refined_is_faster(gpu):
