@@ -64,6 +64,10 @@ int adc_memory(const adc_ctx_opaque *ctx, int64_t *in_use, int64_t *peak);
  * every context of the process on that device until it is set again. */
 int adc_diag_set_wait_ns(uint64_t ns);
 
+/* 1 when the context forms its EA ladder integrals inside every product
+ * (opts.ladder), else 0. ADC_ERR_STATE for a NULL context. */
+int adc_ladder_mode(const adc_ctx_opaque *ctx, int *direct);
+
 /* Routes of the complex products adc_init issued for this context: how many
  * ran as the sliced tensor-core product (opts.setup = ADC_PREC_SLICED, inner
  * size at least 512 and at least 2^24 flops) and how many on the FP64 CUDA

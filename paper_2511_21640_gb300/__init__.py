@@ -40,7 +40,7 @@ class adc_opts(ctypes.Structure):
                 ("max_subspace", ctypes.c_int), ("herm_tol", ctypes.c_double),
                 ("mem_limit", ctypes.c_int64), ("verbose", ctypes.c_int), ("dd_order", ctypes.c_int),
                 ("refine", ctypes.c_int), ("setup", ctypes.c_int), ("ee_vvvv", ctypes.c_int),
-                ("correction", ctypes.c_int)]
+                ("correction", ctypes.c_int), ("ladder", ctypes.c_int)]
 
 
 class adc_stats(ctypes.Structure):
@@ -128,6 +128,7 @@ def _load():
         "adc_state_pair_density": (I, [P, P, P, I64, P]),
         "adc_memory": (I, [P, P, P]),
         "adc_setup_routes": (I, [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "adc_ladder_mode": (I, [P, ctypes.POINTER(I)]),
         "adc_cholesky": (I, [P, I64, D, I64, P, P, ctypes.POINTER(I64)]),
         "adc_cholesky_mo": (I, [P, I64, I64, P, I64, P]),
         "adc_ssfns_density": (I, [P, P, D, P, P, ctypes.POINTER(I64), P, P]),
@@ -202,7 +203,7 @@ class Context:
 
     def __init__(self, B, eps_occ, eps_vir, kind="IP", order=3, x=1.0, precision="fp64", stream=None,
                  block=0, max_subspace=0, herm_tol=1e-12, mem_limit=0, verbose=False, dd_order=1,
-                 refine="fp64", setup="fp64", vvvv="auto", correction="davidson"):
+                 refine="fp64", setup="fp64", vvvv="auto", correction="davidson", ladder="auto"):
         o = adc_opts()
         lib.adc_opts_default(ctypes.byref(o))
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -221,6 +222,7 @@ class Context:
         o.setup = PRECISIONS[setup] if isinstance(setup, str) else int(setup)
         o.ee_vvvv = {"auto": 0, "chunked": 1, "dense": -1}[vvvv]
         o.correction = {"davidson": 0, "olsen": 1}[correction]
+        o.ladder = {"auto": 0, "direct": 1, "stored": -1}[ladder]
         naux, nmo, nmo2 = B.shape
         nocc, nvir = eps_occ.shape[0], eps_vir.shape[0]
         if nmo != nmo2 or nmo != nocc + nvir:
@@ -401,6 +403,12 @@ class Context:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(lib.adc_memory(self._h, ctypes.byref(a), ctypes.byref(b)), self._h)
         return {"in_use": a.value, "peak": b.value}
+
+    def direct_ladder(self):
+        """Whether the context forms its ladder integrals in every product (``adc_ladder_mode``)."""
+        m = ctypes.c_int()
+        _check(lib.adc_ladder_mode(self._h, ctypes.byref(m)), self._h)
+        return bool(m.value)
 
     def setup_routes(self):
         """Products adc_init ran as the sliced tensor-core product and on the FP64 cores (``adc_setup_routes``)."""

@@ -20,7 +20,7 @@ BUILD = os.path.join(os.path.dirname(HERE), "_build")
 LIB = os.path.join(HERE, "libadc_gb300.so")
 SOURCES = ["tensor.cu", "setup.cu", "sigma.cu", "sigma_tc.cu", "tc_gemm.cu", "eig.cu",
            "davidson.cu", "fns.cu", "api.cu", "diag.cu", "noalloc.cu", "blockops.cu", "terms.cu", "ee.cu",
-           "batch.cu", "adjoint.cu", "ee_struct.cu", "tc_slice.cu", "ssfns.cu", "properties.cu", "cholesky.cu"]
+           "batch.cu", "adjoint.cu", "ee_struct.cu", "tc_slice.cu", "ssfns.cu", "properties.cu", "cholesky.cu", "ladder.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

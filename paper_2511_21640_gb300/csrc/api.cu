@@ -105,7 +105,7 @@ adc_ctx::~adc_ctx() {
   release_tc(this);
   ee.reset();
   scratch.reset();
-  t1.reset(); W.reset(); Glad.reset(); diag.reset(); d2.reset(); Cpl.reset(); M11.reset();
+  t1.reset(); W.reset(); Glad.reset(); Lvv.reset(); diag.reset(); d2.reset(); Cpl.reset(); M11.reset();
   B.reset(); eo.reset(); ev.reset();
   if (ex.stream) cudaStreamSynchronize(ex.stream);
   if (own_stream && ex.stream) cudaStreamDestroy(ex.stream);
@@ -146,6 +146,7 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
                 "opts.setup: ADC_PREC_FP64 or ADC_PREC_SLICED");
     ADC_REQUIRE(c->opts.ee_vvvv >= -1 && c->opts.ee_vvvv <= 1, ADC_ERR_ARG, "opts.ee_vvvv: -1, 0 or 1");
     ADC_REQUIRE(c->opts.correction == 0 || c->opts.correction == 1, ADC_ERR_ARG, "opts.correction: 0 or 1");
+    ADC_REQUIRE(c->opts.ladder >= -1 && c->opts.ladder <= 1, ADC_ERR_ARG, "opts.ladder: -1, 0 or 1");
     c->kind = kind;
     c->order = order;
     c->x = (order == 3) ? x : 0.0;

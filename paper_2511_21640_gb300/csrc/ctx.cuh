@@ -37,6 +37,10 @@ struct adc_ctx {
   adc::DBuf Glad;  // ladder integrals, packed: EA [Pv][Pv] <ab||cd>; IP [Po][Po] <kl||ij>
   adc::DBuf W;     // ring integrals [o][v][o][v]: W[j][a][k][c] = <ak||cj>
   adc::DBuf t1;    // first-order doubles [o][o][v][v]
+  // EA at third order: the ladder integrals are formed chunk by chunk in every
+  // product (integral-direct) instead of stored in Glad
+  bool direct_ladder = false;
+  adc::DBuf Lvv;   // [(a,c)][Q] = B^Q_ac of the integral-direct ladder
 
   // split-precision copies for the tensor-core sigma
   std::unique_ptr<adc::TcCache> tc;
@@ -62,6 +66,22 @@ namespace adc {
 TV Bview(adc_ctx *c, char p, char q);               // B^Q block view [Q][p][q]
 DBuf eri_block(adc_ctx *c, const char *spec);       // dense <pq||rs> of a 4-letter o/v spec
 DBuf build_vvvv_packed(adc_ctx *c);                 // [Pv][Pv] <ab||cd>, a<b, c<d
+// integral-direct ladder pieces (setup.cu): L[(a,c)][Q] = B^Q_ac; the number of
+// virtual indices a per chunk; rows (a<b) of the packed <ab||cd> for a in
+// [a0, a1) into Gc [rows][Pv] from J = L L^T (J [(a,c)][(b,d)], b >= a0); the
+// first packed row of a given a
+DBuf vvvv_L(adc_ctx *c);
+int64_t vvvv_chunk(adc_ctx *c);
+void vvvv_rows(adc_ctx *c, const cplx *L, int64_t a0, int64_t a1, cplx *J, cplx *Gc);
+void vvvv_assemble_rows(adc_ctx *c, const cplx *J, int64_t a0, int64_t a1, cplx *Gc);
+inline int64_t ladder_row0(int64_t a, int64_t v) { return a * v - a * (a + 1) / 2; }
+// the EA ladder term, integral-direct (ladder.cu): for r < k, j < nj,
+// S2[r*ldS + j*Pv + (ab)] += x sum_(cd) <ab||cd> X2[r*ldX + j*Pv + (cd)], in the precision
+// mode (ADC_LADDER_FP64, ADC_LADDER_SLICED, or 3 / 6 for the BF16 split; err: the
+// tensor-core error word)
+enum { ADC_LADDER_SLICED = 0, ADC_LADDER_FP64 = 1 };
+void ladder_direct(adc_ctx *c, const cplx *X2, int64_t ldX, int64_t nj, cplx *S2, int64_t ldS, int64_t k,
+                   double x, int mode, int *err);
 void setup_operators(adc_ctx *c);
 // t1 (c->t1) and ring integrals (c->W) from B
 void first_order_amplitudes(adc_ctx *c);

@@ -210,6 +210,13 @@ extern "C" int adc_diag_set_wait_ns(uint64_t ns) {
   }
 }
 
+extern "C" int adc_ladder_mode(const adc_ctx *c, int *direct) {
+  if (!c) return ADC_ERR_STATE;
+  if (!direct) return ADC_ERR_ARG;
+  *direct = c->direct_ladder ? 1 : 0;
+  return ADC_OK;
+}
+
 extern "C" int adc_setup_routes(const adc_ctx *c, int64_t *n_sliced, int64_t *n_fp64, double *flops_sliced,
                                 double *flops_fp64) {
   if (!c) return ADC_ERR_STATE;

@@ -49,10 +49,10 @@ DBuf eri(adc_ctx *c, const char *spec) { return eri_block(c, spec); }
 
 TV dense(const DBuf &b, std::vector<int64_t> e) { return TV::dense(b.c(), e); }
 
-// packed <ab||cd>, a<b, c<d, [Pv][Pv], from J_(ac),(bd) = sum_Q B_ac B_bd computed
-// one block of a at a time (only b >= a0 is formed).
+// packed <ab||cd>, a<b, c<d, rows [(ab) - p0][Pv], from J_(ac),(bd) = sum_Q B_ac B_bd
+// computed one block of a at a time (only b >= a0 is formed).
 __global__ void k_assemble_ladder(const cplx *__restrict__ J, int64_t a0, int64_t ca, int64_t v,
-                                  cplx *G, int64_t total) {
+                                  cplx *G, int64_t total, int64_t p0) {
   // J layout: [a - a0][c][b - a0][d], b range v - a0
   const int64_t nb = v - a0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -65,7 +65,7 @@ __global__ void k_assemble_ladder(const cplx *__restrict__ J, int64_t a0, int64_
     if (!(a < b) || !(cc < d)) continue;
     cplx j1 = J[((aa * v + cc) * nb + bb) * v + d];
     cplx j2 = J[((aa * v + d) * nb + bb) * v + cc];
-    G[pair_index(a, b, v) * (v * (v - 1) / 2) + pair_index(cc, d, v)] = csub(j1, j2);
+    G[(pair_index(a, b, v) - p0) * (v * (v - 1) / 2) + pair_index(cc, d, v)] = csub(j1, j2);
   }
 }
 
@@ -128,10 +128,37 @@ DBuf build_vvvv_packed(adc_ctx *c) {
     zgemm(c->ex, na * v, nb * v, Q, 1, C1(), L.c() + a0 * v * Q, 0, Q, 1, false,
           L.c() + a0 * v * Q, 0, 1, Q, false, C0(), J.c(), 0, nb * v, 1);
     int64_t total = na * v * nb * v;
-    k_assemble_ladder<<<grid1d(total, 256), 256, 0, c->ex.stream>>>(J.c(), a0, na, v, G.c(), total);
+    k_assemble_ladder<<<grid1d(total, 256), 256, 0, c->ex.stream>>>(J.c(), a0, na, v, G.c(), total, 0);
     ADC_CHECK_LAUNCH();
   }
   return G;
+}
+
+DBuf vvvv_L(adc_ctx *c) {
+  const int64_t v = c->v, Q = c->Q;
+  DBuf L = cbuf(c->ex, v * v * Q);
+  permute(c->ex, c->B.c() + c->o * c->nmo + c->o, {v, v, Q}, {c->nmo, 1, c->nmo * c->nmo}, false, L.c(), C1(), C0());
+  return L;
+}
+
+int64_t vvvv_chunk(adc_ctx *c) {
+  const int64_t v = c->v;
+  return std::min<int64_t>(v, std::max<int64_t>(1, ((int64_t)1 << 26) / (v * v * v)));
+}
+
+void vvvv_assemble_rows(adc_ctx *c, const cplx *J, int64_t a0, int64_t a1, cplx *Gc) {
+  const int64_t v = c->v, na = a1 - a0, nb = v - a0;
+  const int64_t total = na * v * nb * v;
+  k_assemble_ladder<<<grid1d(total, 256), 256, 0, c->ex.stream>>>(J, a0, na, v, Gc, total, ladder_row0(a0, v));
+  ADC_CHECK_LAUNCH();
+}
+
+void vvvv_rows(adc_ctx *c, const cplx *L, int64_t a0, int64_t a1, cplx *J, cplx *Gc) {
+  const int64_t v = c->v, Q = c->Q, na = a1 - a0, nb = v - a0;
+  // J[(a,c)][(b,d)] = sum_Q L[(a,c)][Q] L[(b,d)][Q], a in [a0, a1), b >= a0
+  zgemm(c->ex, na * v, nb * v, Q, 1, C1(), L + a0 * v * Q, 0, Q, 1, false, L + a0 * v * Q, 0, 1, Q, false, C0(), J,
+        0, nb * v, 1);
+  vvvv_assemble_rows(c, J, a0, a1, Gc);
 }
 
 void first_order_amplitudes(adc_ctx *c) {
@@ -160,14 +187,27 @@ void second_order_amplitudes(adc_ctx *c, DBuf &G_vv, DBuf &Lad_b, DBuf &t2d_b, D
   const double *eo = c->eo.d(), *ev = c->ev.d();
   TV t1 = dense(c->t1, {o, o, v, v});
   TV W = dense(c->W, {o, v, o, v});
-    G_vv = build_vvvv_packed(c);
     // Lad_ij^ab = 1/2 sum_cd <ab||cd> t_ij^cd = sum_{c<d} G[(ab),(cd)] t_ij^cd
     DBuf tp1 = cbuf(ex, o * o * pv), tp2 = cbuf(ex, po * pv);
     pair_pack(ex, c->t1.c(), 0, v * v, v, 1, 0, 0.0, 1, o * o, v, 1, tp1.c(), 0, pv, C1(), C0());
     pair_pack(ex, tp1.c(), 0, 0, o * pv, pv, 1, 0.0, 1, 1, o, pv, tp2.c(), 0, 0, C1(), C0());
     DBuf lp = cbuf(ex, po * pv);
-    zgemm(ex, po, pv, pv, 1, C1(), tp2.c(), 0, pv, 1, false, G_vv.c(), 0, 1, pv, false, C0(), lp.c(),
-          0, pv, 1);
+    if (c->direct_ladder) {
+      // integral-direct: chunks of rows (a<b) of <ab||cd>, each contracted at once
+      DBuf L = vvvv_L(c);
+      const int64_t ca = vvvv_chunk(c);
+      DBuf J = cbuf(ex, ca * v * v * v), Gc = cbuf(ex, std::min<int64_t>(ca * v, pv) * pv);
+      for (int64_t a0 = 0; a0 < v - 1; a0 += ca) {
+        const int64_t a1 = std::min(v - 1, a0 + ca), r0 = ladder_row0(a0, v), r1 = ladder_row0(a1, v);
+        vvvv_rows(c, L.c(), a0, a1, J.c(), Gc.c());
+        zgemm(ex, po, r1 - r0, pv, 1, C1(), tp2.c(), 0, pv, 1, false, Gc.c(), 0, 1, pv, false, C0(), lp.c() + r0, 0,
+              pv, 1);
+      }
+    } else {
+      G_vv = build_vvvv_packed(c);
+      zgemm(ex, po, pv, pv, 1, C1(), tp2.c(), 0, pv, 1, false, G_vv.c(), 0, 1, pv, false, C0(), lp.c(),
+            0, pv, 1);
+    }
     DBuf l1 = cbuf(ex, po * v * v);
     pair_unpack(ex, lp.c(), 1, po, 0, pv, v, 1, l1.c());
     Lad_b = cbuf(ex, o * o * v * v);
@@ -229,6 +269,18 @@ void setup_operators(adc_ctx *c) {
      Bvv = Bview(c, 'v', 'v');
   const double *eo = c->eo.d(), *ev = c->ev.d();
 
+  // EA ladder: stored packed <ab||cd>, or integral-direct when that would
+  // take more than a quarter of the free device memory (opts.ladder)
+  c->direct_ladder = false;
+  if (c->kind == ADC_EA && third) {
+    if (c->opts.ladder == 1) {
+      c->direct_ladder = true;
+    } else if (c->opts.ladder == 0) {
+      size_t fr = 0, tot = 0;
+      ADC_CUDA(cudaMemGetInfo(&fr, &tot));
+      c->direct_ladder = (double)pv * (double)pv * sizeof(cplx) > 0.25 * (double)fr;
+    }
+  }
   first_order_amplitudes(c);
   TV t1 = dense(c->t1, {o, o, v, v});
   DBuf oovv = cbuf(ex, o * o * v * v);
@@ -393,7 +445,7 @@ void setup_operators(adc_ctx *c) {
   // ---- ladder integrals of the satellite block (first order, x-scaled)
   if (third && x != 0.0) {
     if (c->kind == ADC_EA) {
-      c->Glad = std::move(G_vv);
+      if (!c->direct_ladder) c->Glad = std::move(G_vv);
     } else {
       // Glad[(ij)][(kl)] = <kl||ij>
       DBuf oooo = eri(c, "oooo");

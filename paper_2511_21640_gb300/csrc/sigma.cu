@@ -58,11 +58,15 @@ void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
     cplx *Xf = scratch(c, 2 * k * o * v * v + 2 * k * o * pv);
     cplx *T = Xf + k * o * v * v;
     cplx *Xg = T + k * o * v * v, *Og = Xg + k * o * pv;
-    ADC_CUDA(cudaMemcpy2DAsync(Xg, o * pv * sizeof(cplx), X + n1, N * sizeof(cplx), o * pv * sizeof(cplx), k,
-                               cudaMemcpyDeviceToDevice, ex.stream));
-    zgemm(ex, k * o, pv, pv, 1, C1(), Xg, 0, pv, 1, false, c->Glad.c(), 0, 1, pv, false, C0(), Og, 0, pv, 1);
-    k_rows_axpy<<<grid1d(k * o * pv, 256), 256, 0, ex.stream>>>(k, o * pv, CR(x), Og, o * pv, S + n1, N);
-    ADC_CHECK_LAUNCH();
+    if (c->direct_ladder) {
+      ladder_direct(c, X + n1, N, o, S + n1, N, k, x, ADC_LADDER_FP64, nullptr);
+    } else {
+      ADC_CUDA(cudaMemcpy2DAsync(Xg, o * pv * sizeof(cplx), X + n1, N * sizeof(cplx), o * pv * sizeof(cplx), k,
+                                 cudaMemcpyDeviceToDevice, ex.stream));
+      zgemm(ex, k * o, pv, pv, 1, C1(), Xg, 0, pv, 1, false, c->Glad.c(), 0, 1, pv, false, C0(), Og, 0, pv, 1);
+      k_rows_axpy<<<grid1d(k * o * pv, 256), 256, 0, ex.stream>>>(k, o * pv, CR(x), Og, o * pv, S + n1, N);
+      ADC_CHECK_LAUNCH();
+    }
     // ring: Xf[r][k][c][b] (antisymmetric in c,b); T[(j,a)][(r,b)] = sum_(kc) W[(j,a)][(kc)] Xt[(kc)][(r,b)]
     ex.tag = "ring";
     pair_unpack(ex, X + n1, k, o, N, pv, v, 1, Xf);
@@ -127,11 +131,15 @@ void sigma_fp64_share(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int64_t i0,
   cplx *Xf = scratch(c, 2 * k * o * v * v + 2 * k * ns);
   cplx *T = Xf + k * o * v * v;
   cplx *Xg = T + k * o * v * v, *Og = Xg + k * ns;
-  ADC_CUDA(cudaMemcpy2DAsync(Xg, ns * sizeof(cplx), X + n1 + i0 * pv, N * sizeof(cplx), ns * sizeof(cplx), k,
-                             cudaMemcpyDeviceToDevice, ex.stream));
-  zgemm(ex, k * nb, pv, pv, 1, C1(), Xg, 0, pv, 1, false, c->Glad.c(), 0, 1, pv, false, C0(), Og, 0, pv, 1);
-  k_rows_axpy<<<grid1d(k * ns, 256), 256, 0, ex.stream>>>(k, ns, CR(x), Og, ns, S + n1, ldS);
-  ADC_CHECK_LAUNCH();
+  if (c->direct_ladder) {
+    ladder_direct(c, X + n1 + i0 * pv, N, nb, S + n1, ldS, k, x, ADC_LADDER_FP64, nullptr);
+  } else {
+    ADC_CUDA(cudaMemcpy2DAsync(Xg, ns * sizeof(cplx), X + n1 + i0 * pv, N * sizeof(cplx), ns * sizeof(cplx), k,
+                               cudaMemcpyDeviceToDevice, ex.stream));
+    zgemm(ex, k * nb, pv, pv, 1, C1(), Xg, 0, pv, 1, false, c->Glad.c(), 0, 1, pv, false, C0(), Og, 0, pv, 1);
+    k_rows_axpy<<<grid1d(k * ns, 256), 256, 0, ex.stream>>>(k, ns, CR(x), Og, ns, S + n1, ldS);
+    ADC_CHECK_LAUNCH();
+  }
   // ring rows (j, a) of the share: R[(j,a)][r][b] = sum_(kc) W[(j,a)][(kc)] Xt[(kc)][r][b], all k
   ex.tag = "ring";
   pair_unpack(ex, X + n1, k, o, N, pv, v, 1, Xf);

@@ -18,7 +18,7 @@ static void build_cache(adc_ctx *c, int planes) {
   tc_pack_A(ex, tc.CplT, c->Cpl.c(), n2, n1, 1, n2, true, planes);
   if (c->order == 3 && c->x != 0.0) {
     const int64_t P = (c->kind == ADC_EA) ? npairs(v) : npairs(o);
-    tc_pack_A(ex, tc.Glad, c->Glad.c(), P, P, P, 1, false, planes);
+    if (!c->direct_ladder) tc_pack_A(ex, tc.Glad, c->Glad.c(), P, P, P, 1, false, planes);
     tc_pack_A(ex, tc.W, c->W.c(), o * v, o * v, o * v, 1, false, planes);
   }
   tc.err = DBuf(ex, sizeof(int));
@@ -62,8 +62,12 @@ void sigma_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
       const int64_t pv = npairs(v);
       // ladder: out[(ab)][(r,j)] = sum_(cd) Glad[(ab)][(cd)] X2[r][j][(cd)]
       ex.tag = "ladder";
-      tc_pack_B(ex, tc.Bx, X + n1, k * o, pv, N, pv, o, 1, false, planes);
-      tc_gemm(ex, tc.Glad, tc.Bx, pv, k * o, CR(x), C1(), S + n1, 1, N, pv, o, err, nseg);
+      if (c->direct_ladder) {
+        ladder_direct(c, X + n1, N, o, S + n1, N, k, x, nseg, err);
+      } else {
+        tc_pack_B(ex, tc.Bx, X + n1, k * o, pv, N, pv, o, 1, false, planes);
+        tc_gemm(ex, tc.Glad, tc.Bx, pv, k * o, CR(x), C1(), S + n1, 1, N, pv, o, err, nseg);
+      }
       // ring: T[r][j][a][b] = sum_(kc) W[(j,a)][(kc)] Xf[r][k][c][b]
       ex.tag = "ring";
       cplx *T = scratch(c, k * o * v * v);
@@ -106,7 +110,7 @@ static void build_sl(adc_ctx *c) {
   sl_pack_A(ex, sl.CplT, c->Cpl.c(), n2, n1, 1, n2, true, sl.bits);
   if (c->order == 3 && c->x != 0.0) {
     const int64_t P = (c->kind == ADC_EA) ? npairs(v) : npairs(o);
-    sl_pack_A(ex, sl.Glad, c->Glad.c(), P, P, P, 1, false, sl.bits);
+    if (!c->direct_ladder) sl_pack_A(ex, sl.Glad, c->Glad.c(), P, P, P, 1, false, sl.bits);
     sl_pack_A(ex, sl.W, c->W.c(), o * v, o * v, o * v, 1, false, sl.bits);
   }
   sl.err = DBuf(ex, sizeof(int));
@@ -137,8 +141,12 @@ void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
     if (c->kind == ADC_EA) {
       const int64_t pv = npairs(v);
       ex.tag = "ladder";
-      sl_pack_B(ex, sl.Bx, X + n1, k * o, pv, N, pv, o, 1, false, sl.Glad);
-      sl_gemm(ex, sl.Glad, sl.Bx, pv, k * o, CR(x), C1(), S + n1, 1, N, pv, o, err, sl.w);
+      if (c->direct_ladder) {
+        ladder_direct(c, X + n1, N, o, S + n1, N, k, x, ADC_LADDER_SLICED, err);
+      } else {
+        sl_pack_B(ex, sl.Bx, X + n1, k * o, pv, N, pv, o, 1, false, sl.Glad);
+        sl_gemm(ex, sl.Glad, sl.Bx, pv, k * o, CR(x), C1(), S + n1, 1, N, pv, o, err, sl.w);
+      }
       ex.tag = "ring";
       cplx *T = scratch(c, k * o * v * v);
       sl_pack_B_ring(ex, sl.Bx, c, X, k, sl.W);

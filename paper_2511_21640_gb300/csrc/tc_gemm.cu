@@ -373,20 +373,20 @@ void make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t kp2, int
 
 
 template <int BN, int ST>
-void launch_tc(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N2, cplx alpha, cplx beta,
+void launch_tc(Exec &ex, const TcView &A, const TcView &B, int64_t M, int64_t N2, cplx alpha, cplx beta,
                cplx *out, int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, int nseg) {
   using L = TcLayout<BN, ST>;
   set_smem_limit((const void *)k_tc_gemm<BN, ST>, L::SMEM);
   const int g_sms = device_sm_count();
   CUtensorMap mAh, mAl, mAl2, mBh, mBl, mBl2;
   const int64_t kp2 = 2 * A.kp;
-  make_map(&mAh, A.hi.p, A.rows, kp2, TC_BM);
-  make_map(&mAl, A.lo.p, A.rows, kp2, TC_BM);
-  make_map(&mBh, B.hi.p, B.rows, kp2, BN);
-  make_map(&mBl, B.lo.p, B.rows, kp2, BN);
+  make_map(&mAh, A.hi, A.rows, kp2, TC_BM);
+  make_map(&mAl, A.lo, A.rows, kp2, TC_BM);
+  make_map(&mBh, B.hi, B.rows, kp2, BN);
+  make_map(&mBl, B.lo, B.rows, kp2, BN);
   if (nseg == 6) {
-    make_map(&mAl2, A.lo2.p, A.rows, kp2, TC_BM);
-    make_map(&mBl2, B.lo2.p, B.rows, kp2, BN);
+    make_map(&mAl2, A.lo2, A.rows, kp2, TC_BM);
+    make_map(&mBl2, B.lo2, B.rows, kp2, BN);
   } else {
     mAl2 = mAl;  // not read with three segments
     mBl2 = mBl;
@@ -744,7 +744,25 @@ void tc_pack_B_ring(Exec &ex, TcMat &dst, const adc_ctx *c, const cplx *X, int64
   pack_B_impl(ex, dst, s, Nc, c->o * c->v, false, planes);
 }
 
+TcView tc_view(const TcMat &m, int64_t row0, int64_t rows) {
+  TcView v;
+  const int64_t off = row0 * 2 * m.kp;  // BF16 elements; rows are 4 kp bytes, a multiple of 256
+  v.hi = m.hi.p ? (const __nv_bfloat16 *)m.hi.p + off : nullptr;
+  v.lo = m.lo.p ? (const __nv_bfloat16 *)m.lo.p + off : nullptr;
+  v.lo2 = m.lo2.p ? (const __nv_bfloat16 *)m.lo2.p + off : nullptr;
+  v.planes = m.planes;
+  v.rows = rows < 0 ? m.rows - row0 : rows;
+  v.kp = m.kp;
+  v.kreal = m.kreal;
+  return v;
+}
+
 void tc_gemm(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N, cplx alpha, cplx beta, cplx *out,
+             int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, int nseg) {
+  tc_gemm(ex, tc_view(A), tc_view(B), M, N, alpha, beta, out, s_m, s_nh, s_nl, n_in, err, nseg);
+}
+
+void tc_gemm(Exec &ex, const TcView &A, const TcView &B, int64_t M, int64_t N, cplx alpha, cplx beta, cplx *out,
              int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, int nseg) {
   ADC_REQUIRE(A.kp == B.kp, ADC_ERR_ARG, "tc_gemm: inner sizes differ");
   ADC_REQUIRE(A.rows >= M && B.rows >= 2 * N, ADC_ERR_ARG, "tc_gemm: operand rows");

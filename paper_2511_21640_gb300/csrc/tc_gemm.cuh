@@ -50,6 +50,14 @@ struct TcMat {
   int64_t rows = 0, kp = 0, kreal = 0;
 };
 
+// rows [row0, row0 + rows) of a packed operand, without owning them
+struct TcView {
+  const void *hi = nullptr, *lo = nullptr, *lo2 = nullptr;
+  int planes = 2;
+  int64_t rows = 0, kp = 0, kreal = 0;
+};
+TcView tc_view(const TcMat &m, int64_t row0 = 0, int64_t rows = -1);
+
 // A[m][k] = op(src[m*s_m + k*s_k]) (op = conj when conj is set); planes 2 or 3
 void tc_pack_A(Exec &ex, TcMat &dst, const cplx *src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, bool conj,
                int planes = 2);
@@ -62,6 +70,9 @@ void tc_pack_B_ring(Exec &ex, TcMat &dst, const adc_ctx *c, const cplx *X, int64
 // with nseg = 3 products (hi hi, hi lo, lo hi) or 6 (plus hi lo2, lo lo, lo2 hi;
 // both operands need three planes)
 void tc_gemm(Exec &ex, const TcMat &A, const TcMat &B, int64_t M, int64_t N, cplx alpha, cplx beta, cplx *out,
+             int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, int nseg = 3);
+// the same on views (row ranges of packed operands)
+void tc_gemm(Exec &ex, const TcView &A, const TcView &B, int64_t M, int64_t N, cplx alpha, cplx beta, cplx *out,
              int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, int nseg = 3);
 
 // ---- grouped persistent launch (several problems and terms in one kernel)
@@ -127,6 +138,7 @@ void tc_set_wait_ns(uint64_t ns);
 struct TcCache {
   int planes = 2;            // BF16 planes of the copies (3 for the six-product split)
   TcMat Glad, W, Cpl, CplT;  // static operators (A side)
+  TcMat LA, LB;              // B^Q_ac as both operands of the integral-direct ladder's J = L L^T
   TcMat Bx;                  // per-call B operand
   DBuf err;                  // device error word of the tensor-core kernels
   bool ready = false;
