@@ -119,13 +119,15 @@ typedef struct {
                            1 = Olsen's: (omega - diag M)^-1 (r - e y) with e
                            chosen so that the correction is orthogonal to its
                            Ritz vector y */
-  int ladder;           /* EA at third order, the ladder integrals <ab||cd> of
-                           the 2p1h block (Sec. 2.5: four-external integrals
-                           formed on the fly): 0 = automatic (integral-direct
-                           when the packed block would take more than a quarter
-                           of the free device memory), 1 = integral-direct
-                           (formed from B in chunks inside every product),
-                           -1 = stored once (the packed Pv x Pv block) */
+  int ladder;           /* third order, the four-virtual integrals <ab||cd>
+                           (Sec. 2.5: four-external integrals formed on the
+                           fly), used by the ladder intermediate of the
+                           second-order amplitudes and, for EA, by the 2p1h
+                           ladder of every product: 0 = automatic
+                           (integral-direct when the packed block would take
+                           more than a quarter of the free device memory),
+                           1 = integral-direct (formed from B in chunks where
+                           needed), -1 = stored once (the packed Pv x Pv block) */
 } adc_opts;
 
 typedef struct {

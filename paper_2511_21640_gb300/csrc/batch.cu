@@ -406,7 +406,7 @@ int adc_batch_create(adc_batch **out, adc_ctx *const *ctxs, int n) {
       ADC_REQUIRE(ctxs[i] != nullptr, ADC_ERR_ARG, "adc_batch_create: NULL context");
       ADC_REQUIRE(ctxs[i]->batch == nullptr, ADC_ERR_STATE, "adc_batch_create: context already in a batch");
       for (int j = 0; j < i; ++j) ADC_REQUIRE(ctxs[j] != ctxs[i], ADC_ERR_ARG, "adc_batch_create: repeated context");
-      ADC_REQUIRE(!ctxs[i]->direct_ladder, ADC_ERR_UNSUPPORTED,
+      ADC_REQUIRE(!(ctxs[i]->kind == ADC_EA && ctxs[i]->direct_ladder), ADC_ERR_UNSUPPORTED,
                   "adc_batch_create: contexts with the integral-direct ladder are solved one at a time");
       co.ctx.push_back(ctxs[i]);
     }

@@ -37,8 +37,9 @@ struct adc_ctx {
   adc::DBuf Glad;  // ladder integrals, packed: EA [Pv][Pv] <ab||cd>; IP [Po][Po] <kl||ij>
   adc::DBuf W;     // ring integrals [o][v][o][v]: W[j][a][k][c] = <ak||cj>
   adc::DBuf t1;    // first-order doubles [o][o][v][v]
-  // EA at third order: the ladder integrals are formed chunk by chunk in every
-  // product (integral-direct) instead of stored in Glad
+  // third order: the packed <ab||cd> is never stored; the setup's ladder
+  // intermediate and, for EA, the satellite ladder of every product form it
+  // chunk by chunk (integral-direct); IP keeps its <kl||ij> ladder in Glad
   bool direct_ladder = false;
   adc::DBuf Lvv;   // [(a,c)][Q] = B^Q_ac of the integral-direct ladder
 

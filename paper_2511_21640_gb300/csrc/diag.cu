@@ -213,7 +213,7 @@ extern "C" int adc_diag_set_wait_ns(uint64_t ns) {
 extern "C" int adc_ladder_mode(const adc_ctx *c, int *direct) {
   if (!c) return ADC_ERR_STATE;
   if (!direct) return ADC_ERR_ARG;
-  *direct = c->direct_ladder ? 1 : 0;
+  *direct = c->direct_ladder ? 1 : 0;  // setup (both kinds) and, for EA, every product
   return ADC_OK;
 }
 

@@ -113,7 +113,7 @@ extern "C" int adc_sigma_noalloc(adc_ctx *c, const adc_c128 *X, adc_c128 *S, int
   if (k == 0) return ADC_OK;
   try {
     if (c->kind == ADC_EE) throw Error(ADC_ERR_UNSUPPORTED, "adc_sigma_noalloc covers IP and EA");
-    if (c->direct_ladder)
+    if (c->kind == ADC_EA && c->direct_ladder)
       throw Error(ADC_ERR_UNSUPPORTED, "adc_sigma_noalloc needs the stored ladder integrals (opts.ladder)");
     int cur = -1;
     ADC_CUDA(cudaGetDevice(&cur));

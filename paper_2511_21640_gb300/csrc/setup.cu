@@ -269,10 +269,11 @@ void setup_operators(adc_ctx *c) {
      Bvv = Bview(c, 'v', 'v');
   const double *eo = c->eo.d(), *ev = c->ev.d();
 
-  // EA ladder: stored packed <ab||cd>, or integral-direct when that would
-  // take more than a quarter of the free device memory (opts.ladder)
+  // packed <ab||cd> (EA satellite ladder, and the ladder intermediate of the
+  // second-order amplitudes of both kinds): stored, or integral-direct when it
+  // would take more than a quarter of the free device memory (opts.ladder)
   c->direct_ladder = false;
-  if (c->kind == ADC_EA && third) {
+  if (third) {
     if (c->opts.ladder == 1) {
       c->direct_ladder = true;
     } else if (c->opts.ladder == 0) {

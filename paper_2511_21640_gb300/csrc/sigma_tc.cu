@@ -18,7 +18,7 @@ static void build_cache(adc_ctx *c, int planes) {
   tc_pack_A(ex, tc.CplT, c->Cpl.c(), n2, n1, 1, n2, true, planes);
   if (c->order == 3 && c->x != 0.0) {
     const int64_t P = (c->kind == ADC_EA) ? npairs(v) : npairs(o);
-    if (!c->direct_ladder) tc_pack_A(ex, tc.Glad, c->Glad.c(), P, P, P, 1, false, planes);
+    if (!(c->kind == ADC_EA && c->direct_ladder)) tc_pack_A(ex, tc.Glad, c->Glad.c(), P, P, P, 1, false, planes);
     tc_pack_A(ex, tc.W, c->W.c(), o * v, o * v, o * v, 1, false, planes);
   }
   tc.err = DBuf(ex, sizeof(int));
@@ -110,7 +110,7 @@ static void build_sl(adc_ctx *c) {
   sl_pack_A(ex, sl.CplT, c->Cpl.c(), n2, n1, 1, n2, true, sl.bits);
   if (c->order == 3 && c->x != 0.0) {
     const int64_t P = (c->kind == ADC_EA) ? npairs(v) : npairs(o);
-    if (!c->direct_ladder) sl_pack_A(ex, sl.Glad, c->Glad.c(), P, P, P, 1, false, sl.bits);
+    if (!(c->kind == ADC_EA && c->direct_ladder)) sl_pack_A(ex, sl.Glad, c->Glad.c(), P, P, P, 1, false, sl.bits);
     sl_pack_A(ex, sl.W, c->W.c(), o * v, o * v, o * v, 1, false, sl.bits);
   }
   sl.err = DBuf(ex, sizeof(int));

@@ -86,3 +86,17 @@ def test_direct_ladder_several_chunks_equals_stored(gpu):
     idx = [v + k * pv + _pair(d, e, v) for k, d, e in sel]
     rms = float(np.sqrt(np.mean(np.abs(S64) ** 2)))
     assert np.abs(D64[:, idx] - R).max() < 1e-10 * rms
+
+
+def test_direct_setup_ip_against_oracle(gpu):
+    """IP: the four-virtual integrals enter only the second-order amplitudes'
+    ladder intermediate, formed in chunks by the integral-direct setup."""
+    o, v, Q = 5, 11, 20
+    p = make_problem(o, v, Q, seed=105, sigma=0.1, occ_range=(-3.0, -0.3), vir_range=(0.1, 5.0))
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP", order=3, x=1.0, ladder="direct") as ctx:
+        assert ctx.direct_ladder()
+        X = random_vectors(ctx.N, 2, seed=106)
+        ref = oadc.sigma_ref("IP", 3, 1.0, p.B, p.eps_occ, p.eps_vir, X)
+        assert _rel(ctx.sigma(X, "fp64"), ref).max() < 1e-12
+        assert _rel(ctx.sigma(X, "sliced"), ref).max() < 1e-10
+        assert _rel(ctx.sigma(X, "bf16x3"), ref).max() < 1e-4
