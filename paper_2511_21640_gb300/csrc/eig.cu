@@ -160,18 +160,37 @@ k_jacobi(cplx *Ag, int n, int ldag, cplx *Vg, double *w, cplx *Vout, int ldv, in
 }
 
 // ---------------------------------------------------------------- FP32 start + FP64 refinement
-// For the Rayleigh-Ritz steps of the Davidson solver (n up to about 100) one
-// SM's FP64 units (two FMAs per clock) make an FP64 Jacobi take milliseconds.
+// For the Rayleigh-Ritz steps of the Davidson solver (n up to 128) one SM's
+// FP64 units (two FMAs per clock) make an FP64 Jacobi take milliseconds.
 // Instead: (1) cyclic Jacobi in FP32 on A - sigma I (sigma the mean diagonal),
-// one CTA in shared memory, to about 1e-7 of the spectrum's spread; (2) FP64
-// iterative refinement of the whole eigendecomposition after Ogita and Aishima
-// (2018): with X the current eigenvectors, R = I - X^H X, S = X^H A X,
-//   lambda_i = S_ii / (1 - R_ii),
-//   F_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)  if |lambda_i - lambda_j| > delta,
-//          R_ij / 2                                       otherwise (and for i = j),
+// one CTA, to about 1e-7 of the spectrum's spread; (2) FP64 iterative
+// refinement of the whole eigendecomposition after Ogita and Aishima (2018):
+// with X the current eigenvectors, H = X^H X and S = X^H (A - sigma) X (both
+// made exactly Hermitian), R = I - H,
+//   lambda_i = S_ii / H_ii,
+//   F_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)   for separated i, j,
+//          R_ij / 2                                         within a cluster and for i = j,
 //   X <- X (I + F),
-// which converges quadratically; delta is twice the largest off-diagonal |S_ij|.
-// The n^3 products run as small FP64 GEMMs spread over many SMs.
+// which converges quadratically for separated eigenvalues. Hermitian S and H
+// make F_ij + conj(F_ji) = R_ij exactly, so the update keeps X orthonormal to
+// second order whatever the gap. Columns are coupled when their gap is below
+// delta = 2 (||S - diag S||_F + max|lambda| ||R||_F) (the bound of the method),
+// below 1e-10 max|lambda| (gaps the FP64 products cannot resolve), or when the
+// first-order correction would exceed 1e-3 (its second-order error would not
+// be small); clusters are the connected components of the coupling. Each
+// cluster of at most CL_MAX columns is diagonalised exactly: the FP64 Jacobi
+// eigenvectors U of P^H S_c P (P = I + R_c / 2, the first-order Loewdin
+// factor of its non-orthonormal basis) rotate its columns of I + F, and their
+// eigenvalues replace its lambda. The host repeats steps until the
+// corrections between clusters are below 1e-8 of the gaps (beyond the
+// rounding noise of S), at least nsteps and at most nsteps + 3; otherwise
+// (a cluster wider than CL_MAX, no convergence) the FP64 Jacobi solves the
+// matrix instead. The n^3 products run as small FP64 GEMMs over many SMs.
+
+constexpr int EIG_NMAX = 128;
+constexpr int CL_MAX = 8;
+constexpr double OA_ETA = 1e-3;   // largest first-order correction between separate clusters
+constexpr double OA_TAU = 1e-10;  // gaps below this fraction of max|lambda| always couple
 
 __device__ inline float2 f2mul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
@@ -192,17 +211,42 @@ __device__ inline float block_sum_f(float v, float *red) {
   return r;
 }
 
+__device__ inline double block_max(double v, double *red) {
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// shared memory of k_jacobi32 before the matrices (rotation tables, pair lists, reduction)
+__host__ __device__ inline size_t jacobi32_head_bytes(int n) {
+  const int np = n + (n & 1);
+  return (size_t)np / 2 * 4 * sizeof(float) + (size_t)np * sizeof(int) + 64 * sizeof(float) + 16;
+}
+
 // A (FP64, lda) -> FP32 A - sigma I in shared memory; cyclic Jacobi (round robin);
-// eigenvectors sorted by ascending eigenvalue into X (FP64, n x n, columns), sigma into *shift
+// eigenvectors sorted by ascending eigenvalue into X (FP64, n x n, columns), sigma
+// into *shift. The eigenvector work array lives in shared memory, or in Vg
+// (n x n FP32 complex in global memory) when Vg is given.
 __global__ void __launch_bounds__(1024)
-k_jacobi32(const cplx *__restrict__ Ag, int n, int lda, cplx *X, double *shift, int max_sweeps) {
+k_jacobi32(const cplx *__restrict__ Ag, int n, int lda, cplx *X, double *shift, int max_sweeps, float2 *Vg) {
   extern __shared__ float smf[];
   const int np = n + (n & 1), npairs = np / 2;
   float *rc = smf, *rs = rc + npairs, *rpr = rs + npairs, *rpi = rpr + npairs;
   int *pp = (int *)(rpi + npairs), *pq = pp + npairs;
   float *red = (float *)(pq + npairs);
   float2 *A = (float2 *)(((uintptr_t)(red + 64) + 15) & ~(uintptr_t)15);
-  float2 *V = A + n * n;
+  float2 *V = Vg ? Vg : A + n * n;
   __shared__ double dred[32];
   const int tid = threadIdx.x, nt = blockDim.x;
   // shift by the mean diagonal (FP64), then round
@@ -341,82 +385,177 @@ k_small_gemm(const cplx *__restrict__ A, int lda, int opA, const double *shift, 
   }
 }
 
-// One refinement step: from H = X^H X and S = X^H (A - shift) X, the eigenvalue
-// estimates lam and the correction F (F = I + F written, for X <- X (I + F)).
+// Hermitian part of M (n x n) at (i, j)
+__device__ inline cplx herm_at(const cplx *__restrict__ M, int n, int i, int j) {
+  const cplx a = M[(int64_t)i * n + j], b = M[(int64_t)j * n + i];
+  return cmake(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+}
+
+// One refinement step: from H = X^H X and S = X^H (A - shift) X the estimates
+// lam, the clusters (label[i] = smallest column of i's cluster) and
+// F = I + correction. stat[0]: largest (|num_ij| - 1e-14 max|lam|) / |gap_ij|
+// over pairs in different clusters; stat[1]: clusters wider than CL_MAX.
 __global__ void __launch_bounds__(1024)
-k_oa_step(const cplx *__restrict__ H, const cplx *__restrict__ S, int n, double *lam, cplx *F, double *offmax) {
+k_oa_step(const cplx *__restrict__ H, const cplx *__restrict__ S, int n, double *lam, int *label, cplx *F,
+          double *stat) {
   __shared__ double red[32];
+  __shared__ unsigned int cmask[EIG_NMAX * (EIG_NMAX / 32)];
+  __shared__ int lab[EIG_NMAX];
+  __shared__ double sl[EIG_NMAX];
+  __shared__ int changed;
+  constexpr int W = EIG_NMAX / 32;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int i = tid; i < n; i += nt) lam[i] = S[(int64_t)i * n + i].x / H[(int64_t)i * n + i].x;
-  double om = 0.0;
+  for (int i = tid; i < n; i += nt) {
+    sl[i] = S[(int64_t)i * n + i].x / H[(int64_t)i * n + i].x;
+    lab[i] = i;
+  }
+  for (int w = tid; w < n * W; w += nt) cmask[w] = 0u;
+  __syncthreads();
+  double so = 0.0, rr = 0.0, lm = 0.0;
   for (int idx = tid; idx < n * n; idx += nt) {
     const int i = idx / n, j = idx % n;
+    const cplx h = herm_at(H, n, i, j);
+    const double rx = (i == j ? 1.0 : 0.0) - h.x, ry = -h.y;
+    rr += rx * rx + ry * ry;
     if (i != j) {
-      const cplx sij = S[idx];
-      om = fmax(om, sqrt(sij.x * sij.x + sij.y * sij.y));
+      const cplx sv = herm_at(S, n, i, j);
+      so += sv.x * sv.x + sv.y * sv.y;
     }
   }
-  for (int off = 16; off > 0; off >>= 1) om = fmax(om, __shfl_down_sync(0xffffffffu, om, off));
-  if ((tid & 31) == 0) red[tid >> 5] = om;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (nt >> 5); ++w) t = fmax(t, red[w]);
-    red[0] = t;
-    *offmax = t;
-  }
-  __syncthreads();
-  const double delta = 2.0 * red[0];
+  for (int i = tid; i < n; i += nt) lm = fmax(lm, fabs(sl[i]));
+  so = block_sum(so, red);
+  rr = block_sum(rr, red);
+  lm = block_max(lm, red);
+  const double thr = fmax(2.0 * (sqrt(so) + lm * sqrt(rr)), OA_TAU * lm);
   for (int idx = tid; idx < n * n; idx += nt) {
     const int i = idx / n, j = idx % n;
-    // R = I - H
-    cplx r = cmake((i == j ? 1.0 : 0.0) - H[idx].x, -H[idx].y);
+    if (j <= i) continue;
+    const cplx h = herm_at(H, n, i, j), sv = herm_at(S, n, i, j);
+    const double gap = sl[j] - sl[i];
+    const double nx = sv.x - sl[j] * h.x, ny = sv.y - sl[j] * h.y;   // S_ij + lam_j R_ij
+    if (fabs(gap) <= thr || OA_ETA * fabs(gap) <= sqrt(nx * nx + ny * ny)) {
+      atomicOr(&cmask[i * W + (j >> 5)], 1u << (j & 31));
+      atomicOr(&cmask[j * W + (i >> 5)], 1u << (i & 31));
+    }
+  }
+  __syncthreads();
+  // connected components: every column takes the smallest label among its
+  // neighbours until nothing changes (labels only decrease)
+  for (int iter = 0; iter <= n; ++iter) {
+    if (tid == 0) changed = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) {
+      int best = lab[i];
+      for (int w = 0; w < W; ++w) {
+        unsigned int m = cmask[i * W + w];
+        while (m) {
+          const int b = __ffs(m) - 1;
+          m &= m - 1u;
+          best = min(best, lab[w * 32 + b]);
+        }
+      }
+      if (best < lab[i]) { lab[i] = best; changed = 1; }
+    }
+    __syncthreads();
+    const int again = changed;
+    __syncthreads();
+    if (!again) break;
+  }
+  double fr = 0.0;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    const cplx h = herm_at(H, n, i, j);
+    const double rx = (i == j ? 1.0 : 0.0) - h.x, ry = -h.y;
     cplx f;
     if (i == j) {
-      f = cmake(1.0 + 0.5 * r.x, 0.0);
+      f = cmake(1.0 + 0.5 * rx, 0.0);
+    } else if (lab[i] == lab[j]) {
+      f = cmake(0.5 * rx, 0.5 * ry);
     } else {
-      const double li = lam[i], lj = lam[j];
-      if (fabs(lj - li) > delta) {
-        const cplx num = cmake(S[idx].x + lj * r.x, S[idx].y + lj * r.y);
-        f = cmake(num.x / (lj - li), num.y / (lj - li));
-      } else {
-        f = cmake(0.5 * r.x, 0.5 * r.y);
-      }
+      const cplx sv = herm_at(S, n, i, j);
+      const double gap = sl[j] - sl[i];
+      const double nx = sv.x + sl[j] * rx, ny = sv.y + sl[j] * ry;
+      f = cmake(nx / gap, ny / gap);
+      fr = fmax(fr, (sqrt(nx * nx + ny * ny) - 1e-14 * lm) / fabs(gap));
     }
     F[idx] = f;
   }
+  fr = block_max(fr, red);
+  int big = 0;
+  for (int i = tid; i < n; i += nt) {
+    lam[i] = sl[i];
+    label[i] = lab[i];
+    if (lab[i] == i) {
+      int cnt = 0;
+      for (int j = i; j < n; ++j) cnt += (lab[j] == i);
+      big += (cnt > CL_MAX);
+    }
+  }
+  const double bigd = block_sum((double)big, red);
+  if (tid == 0) {
+    stat[0] = fr;
+    stat[1] = bigd;
+  }
 }
 
-// Clusters: runs of consecutive columns (the FP32 start sorts them by
-// eigenvalue) whose estimates lie within delta of their neighbour. There the
-// first-order correction only orthonormalises; each cluster of at most
-// CL_MAX columns is then diagonalised exactly: the FP64 Jacobi eigenvectors U
-// of its block of S rotate its columns of I + F (Fout = (I + F) blockdiag(U)).
-constexpr int CL_MAX = 8;
+// Each cluster of 2..CL_MAX columns (label from k_oa_step) is diagonalised
+// exactly: U, w = eig(P^H S_c P), P = I + R_c / 2; its columns of F become
+// F[:, c] U and its lam the eigenvalues w. Other columns of F are copied.
 __global__ void __launch_bounds__(1024)
-k_cluster_rotate(const cplx *__restrict__ F, const cplx *__restrict__ S, const double *lam, const double *offmax,
-                 int n, cplx *Fout) {
-  __shared__ cplx U[128 * CL_MAX];   // U of the cluster starting at column i, rows i.. of U[i*CL_MAX ...]
-  __shared__ int start[128], size[128];
+k_cluster_rotate(const cplx *__restrict__ F, const cplx *__restrict__ H, const cplx *__restrict__ S,
+                 const int *__restrict__ label, int n, double *lam, cplx *Fout) {
+  __shared__ cplx U[EIG_NMAX * CL_MAX];    // row j: j's row of its cluster's U
+  __shared__ int mem[EIG_NMAX * CL_MAX];   // members of the cluster rooted at i, ascending
+  __shared__ int csize[EIG_NMAX], pos[EIG_NMAX], lab[EIG_NMAX];
   const int tid = threadIdx.x, nt = blockDim.x;
-  const double delta = 2.0 * offmax[0];
-  for (int i = tid; i < n; i += nt) {
-    const bool joins_prev = i > 0 && fabs(lam[i] - lam[i - 1]) <= delta;
-    int e = i + 1;
-    while (e < n && fabs(lam[e] - lam[e - 1]) <= delta) ++e;
-    start[i] = joins_prev ? -1 : i;
-    size[i] = e - i;
+  for (int j = tid; j < n; j += nt) lab[j] = label[j];
+  __syncthreads();
+  for (int j = tid; j < n; j += nt) {
+    const int root = lab[j];
+    int before = 0, total = 0;
+    for (int k = 0; k < n; ++k) {
+      const int in = (lab[k] == root);
+      total += in;
+      before += in && k < j;
+    }
+    pos[j] = before;
+    csize[j] = total;
+    if (before < CL_MAX) mem[root * CL_MAX + before] = j;
   }
   __syncthreads();
   for (int i = tid; i < n; i += nt) {
-    if (start[i] != i) continue;
-    const int sc = size[i];
+    if (lab[i] != i) continue;
+    const int sc = csize[i];
     if (sc < 2 || sc > CL_MAX) continue;
-    cplx a[CL_MAX][CL_MAX], u[CL_MAX][CL_MAX];
+    const int *mi = mem + i * CL_MAX;
+    cplx a[CL_MAX][CL_MAX], u[CL_MAX][CL_MAX], t[CL_MAX][CL_MAX];
+    // t = S_c P, a = P^H t with P = I + R_c / 2 (R = I - H)
     for (int r = 0; r < sc; ++r)
       for (int c = 0; c < sc; ++c) {
-        a[r][c] = S[(int64_t)(i + r) * n + i + c];
+        cplx acc = cmake(0.0, 0.0);
+        for (int l = 0; l < sc; ++l) {
+          const cplx hl = herm_at(H, n, mi[l], mi[c]);
+          const cplx p = cmake((l == c ? 1.5 : 0.0) - 0.5 * hl.x, -0.5 * hl.y);
+          acc = cadd(acc, cmul(herm_at(S, n, mi[r], mi[l]), p));
+        }
+        t[r][c] = acc;
+      }
+    for (int r = 0; r < sc; ++r)
+      for (int c = 0; c < sc; ++c) {
+        cplx acc = cmake(0.0, 0.0);
+        for (int l = 0; l < sc; ++l) {
+          const cplx hl = herm_at(H, n, mi[l], mi[r]);
+          const cplx pc = cmake((l == r ? 1.5 : 0.0) - 0.5 * hl.x, 0.5 * hl.y);   // conj(P[l][r])
+          acc = cadd(acc, cmul(pc, t[l][c]));
+        }
+        a[r][c] = acc;
         u[r][c] = cmake(r == c ? 1.0 : 0.0, 0.0);
+      }
+    for (int r = 0; r < sc; ++r)
+      for (int c = r + 1; c < sc; ++c) {   // exact Hermitian symmetry for the Jacobi sweeps
+        const cplx m = cmake(0.5 * (a[r][c].x + a[c][r].x), 0.5 * (a[r][c].y - a[c][r].y));
+        a[r][c] = m;
+        a[c][r] = cconj(m);
       }
     for (int sweep = 0; sweep < 12; ++sweep) {
       double off = 0.0, dia = 0.0;
@@ -433,8 +572,8 @@ k_cluster_rotate(const cplx *__restrict__ F, const cplx *__restrict__ S, const d
           if (mag <= 1e-300) continue;
           const cplx e = cmake(apq.x / mag, apq.y / mag), ec = cconj(e);
           const double tau = (a[q][q].x - a[p][p].x) / (2.0 * mag);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+          const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = tt * cs;
           for (int c = 0; c < sc; ++c) {   // rows p, q
             const cplx ap = a[p][c], eaq = cmul(e, a[q][c]);
             a[p][c] = cmake(cs * ap.x - sn * eaq.x, cs * ap.y - sn * eaq.y);
@@ -451,21 +590,20 @@ k_cluster_rotate(const cplx *__restrict__ F, const cplx *__restrict__ S, const d
         }
     }
     for (int r = 0; r < sc; ++r)
-      for (int c = 0; c < sc; ++c) U[(i + r) * CL_MAX + c] = u[r][c];
+      for (int c = 0; c < sc; ++c) U[mi[r] * CL_MAX + c] = u[r][c];
+    for (int c = 0; c < sc; ++c) lam[mi[c]] = a[c][c].x;
   }
   __syncthreads();
   for (int idx = tid; idx < n * n; idx += nt) {
     const int r = idx / n, j = idx % n;
-    int s0 = j;
-    while (s0 > 0 && start[s0] != s0) --s0;
-    const int sc = size[s0];
+    const int sc = csize[j];
     if (sc < 2 || sc > CL_MAX) {
       Fout[idx] = F[idx];
       continue;
     }
-    const int jj = j - s0;
+    const int *mj = mem + lab[j] * CL_MAX, jj = pos[j];
     cplx acc = cmake(0.0, 0.0);
-    for (int l = 0; l < sc; ++l) acc = cadd(acc, cmul(F[(int64_t)r * n + s0 + l], U[(s0 + l) * CL_MAX + jj]));
+    for (int l = 0; l < sc; ++l) acc = cadd(acc, cmul(F[(int64_t)r * n + mj[l]], U[mj[l] * CL_MAX + jj]));
     Fout[idx] = acc;
   }
 }
@@ -485,32 +623,38 @@ __global__ void k_sort_out(const double *lam, const double *shift, const cplx *X
   }
 }
 
+__global__ void k_copy_square(const cplx *__restrict__ A, int n, int lda, cplx *B) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * n;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    B[idx] = A[(idx / n) * lda + idx % n];
+}
+
+constexpr size_t kJacobi32Smem = 200 * 1024;
+
 }  // namespace
 
-bool eigh_refined_fits(int n) {
-  const int np = n + (n & 1);
-  const size_t smem = (size_t)np / 2 * 4 * sizeof(float) + (size_t)np * sizeof(int) + 64 * sizeof(float) + 16 +
-                      2 * (size_t)n * n * sizeof(float2);
-  return n >= 1 && n <= 128 && smem <= 200 * 1024;
-}
+bool eigh_refined_fits(int n) { return n >= 1 && n <= EIG_NMAX; }
 
 void eigh_refined(Exec &ex, const cplx *A, int n, int lda, double *w, cplx *V, int ldv, int nsteps) {
   if (n <= 0) return;
   ADC_REQUIRE(eigh_refined_fits(n), ADC_ERR_UNSUPPORTED, "eigh_refined: matrix too large");
-  const int np = n + (n & 1);
-  const size_t smem = (size_t)np / 2 * 4 * sizeof(float) + (size_t)np * sizeof(int) + 64 * sizeof(float) + 16 +
-                      2 * (size_t)n * n * sizeof(float2);
-  set_smem_limit((const void *)k_jacobi32, 200 * 1024);
-  set_smem_limit((const void *)k_small_gemm, 64 * 1024);
   const int64_t nn = (int64_t)n * n;
+  // the FP32 eigenvector work array in shared memory when both matrices fit
+  size_t smem = jacobi32_head_bytes(n) + (size_t)nn * sizeof(float2);
+  DBuf vg;
+  if (smem + (size_t)nn * sizeof(float2) <= kJacobi32Smem) smem += (size_t)nn * sizeof(float2);
+  else vg = DBuf(ex, (size_t)nn * sizeof(float2));
+  set_smem_limit((const void *)k_jacobi32, (int)kJacobi32Smem);
+  set_smem_limit((const void *)k_small_gemm, 64 * 1024);
   DBuf X0 = cbuf(ex, nn), X1 = cbuf(ex, nn), T = cbuf(ex, nn), H = cbuf(ex, nn), S = cbuf(ex, nn), F = cbuf(ex, nn);
-  DBuf lam(ex, n * sizeof(double)), sc(ex, 2 * sizeof(double));
-  k_jacobi32<<<1, 1024, smem, ex.stream>>>(A, n, lda, X0.c(), sc.d(), 30);
+  DBuf lam(ex, n * sizeof(double)), sc(ex, 4 * sizeof(double)), lab(ex, n * sizeof(int));
+  k_jacobi32<<<1, 1024, smem, ex.stream>>>(A, n, lda, X0.c(), sc.d(), 30, (float2 *)vg.p);
   ADC_CHECK_LAUNCH();
   const dim3 g((n + SG_T - 1) / SG_T, (n + SG_T - 1) / SG_T);
   const size_t gs = 2 * (size_t)SG_T * n * sizeof(cplx);
   cplx *X = X0.c(), *Xn = X1.c();
-  for (int it = 0; it < nsteps; ++it) {
+  bool ok = false;
+  for (int it = 0; it < nsteps + 3; ++it) {
     // T = (A - shift) X, S = X^H T, H = X^H X
     k_small_gemm<<<g, SG_T * SG_T, gs, ex.stream>>>(A, lda, 0, sc.d(), X, n, n, nullptr, T.c(), n);
     ADC_CHECK_LAUNCH();
@@ -518,19 +662,32 @@ void eigh_refined(Exec &ex, const cplx *A, int n, int lda, double *w, cplx *V, i
     ADC_CHECK_LAUNCH();
     k_small_gemm<<<g, SG_T * SG_T, gs, ex.stream>>>(X, n, 1, nullptr, X, n, n, nullptr, H.c(), n);
     ADC_CHECK_LAUNCH();
-    k_oa_step<<<1, 1024, 0, ex.stream>>>(H.c(), S.c(), n, lam.d(), F.c(), sc.d() + 1);
+    k_oa_step<<<1, 1024, 0, ex.stream>>>(H.c(), S.c(), n, lam.d(), (int *)lab.p, F.c(), sc.d() + 1);
     ADC_CHECK_LAUNCH();
-    k_cluster_rotate<<<1, 1024, 0, ex.stream>>>(F.c(), S.c(), lam.d(), sc.d() + 1, n, T.c());
+    k_cluster_rotate<<<1, 1024, 0, ex.stream>>>(F.c(), H.c(), S.c(), (const int *)lab.p, n, lam.d(), T.c());
     ADC_CHECK_LAUNCH();
     // X <- X (I + F) blockdiag(U)
     k_small_gemm<<<g, SG_T * SG_T, gs, ex.stream>>>(X, n, 0, nullptr, T.c(), n, n, nullptr, Xn, n);
     ADC_CHECK_LAUNCH();
     std::swap(X, Xn);
+    if (it + 1 >= nsteps) {
+      double st[2];
+      ADC_CUDA(cudaMemcpyAsync(st, sc.d() + 1, sizeof(st), cudaMemcpyDeviceToHost, ex.stream));
+      ADC_CUDA(cudaStreamSynchronize(ex.stream));
+      if (st[0] <= 1e-8 && st[1] == 0.0) { ok = true; break; }
+    }
   }
-  // the eigenvalues of the last step are Rayleigh quotients of the vectors before
-  // its update, exact to the square of their error
-  k_sort_out<<<1, 256, 0, ex.stream>>>(lam.d(), sc.d(), X, n, w, V, ldv);
+  if (ok) {
+    // eigenvalues: Rayleigh quotients of the vectors before the last update
+    // (exact to the square of their error), exact ones within clusters
+    k_sort_out<<<1, 256, 0, ex.stream>>>(lam.d(), sc.d(), X, n, w, V, ldv);
+    ADC_CHECK_LAUNCH();
+    return;
+  }
+  // a cluster too wide for the exact step, or no convergence: FP64 Jacobi
+  k_copy_square<<<(int)std::min<int64_t>((nn + 255) / 256, 1024), 256, 0, ex.stream>>>(A, n, lda, T.c());
   ADC_CHECK_LAUNCH();
+  jacobi_eigh(ex, T.c(), n, n, w, V, ldv, (int *)lab.p);
 }
 
 void jacobi_eigh(Exec &ex, cplx *A, int n, int lda, double *w, cplx *V, int ldv, int *info_dev) {

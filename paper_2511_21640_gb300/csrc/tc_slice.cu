@@ -351,10 +351,25 @@ void zgemm_sliced(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx
   SlWork w;
   DBuf err(ex, sizeof(int));
   fill_zero(ex, err.p, sizeof(int));
+  // the digit planes take 4 ns kp bytes per row of A and 8 ns kp per column
+  // of B (ns slices of the real embedding): rows and columns in chunks whose
+  // planes stay within about 4 GiB per operand
+  const SlParams sp = sl_params(K, ex.sliced_bits);
+  const size_t cap = (size_t)4 << 30;
+  const int64_t mc = std::min<int64_t>(M, std::max<int64_t>(128, (int64_t)(cap / ((size_t)4 * sp.ns * sp.kp))));
+  const int64_t nc = std::min<int64_t>(N, std::max<int64_t>(64, (int64_t)(cap / ((size_t)8 * sp.ns * sp.kp))));
   for (int64_t b = 0; b < batch; ++b) {
-    sl_pack_A(ex, Sa, A + b * sAb, M, K, sAm, sAk, conjA, ex.sliced_bits);
-    sl_pack_B(ex, Sb, B + b * sBb, N, K, sBn, 0, 1, sBk, conjB, Sa);
-    sl_gemm(ex, Sa, Sb, M, N, alpha, beta, C + b * sCb, sCm, sCn, 0, 1, (int *)err.p, w);
+    for (int64_t m0 = 0; m0 < M; m0 += mc) {
+      const int64_t mm = std::min(mc, M - m0);
+      sl_pack_A(ex, Sa, A + b * sAb + m0 * sAm, mm, K, sAm, sAk, conjA, ex.sliced_bits);
+      for (int64_t n0 = 0; n0 < N; n0 += nc) {
+        const int64_t nn = std::min(nc, N - n0);
+        // B once per batch entry when it fits in one chunk
+        if (nc < N || m0 == 0) sl_pack_B(ex, Sb, B + b * sBb + n0 * sBn, nn, K, sBn, 0, 1, sBk, conjB, Sa);
+        sl_gemm(ex, Sa, Sb, mm, nn, alpha, beta, C + b * sCb + m0 * sCm + n0 * sCn, sCm, sCn, 0, 1, (int *)err.p,
+                w);
+      }
+    }
   }
   int h = 0;
   ADC_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, ex.stream));

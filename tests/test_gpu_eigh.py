@@ -4,10 +4,11 @@ and the FP32 Jacobi start refined in FP64, on random Hermitian matrices with
 the spectra the Davidson meets (a large common shift, spread of a few hundred),
 including exactly degenerate pairs (time-reversal doubling) and pairs closer
 than FP32 can resolve. Eigenvalues within 1e-13 of the spectral norm,
-residuals ||A v - w v|| within 1e-13 of it, eigenvectors orthonormal to 1e-13
-(1e-12 for the refinement, whose orthonormality ends near eps |A| over the
-smallest gap); eigenvectors of degenerate pairs are not unique, so only these
-properties are compared. The refined solver is for matrices whose eigenvalues
+residuals ||A v - w v|| within 1e-13 of it, eigenvectors orthonormal to 1e-13;
+eigenvectors of degenerate pairs are not unique, so only these properties are
+compared. The spectra with clusters take the refinement through its coupled
+clusters (exact diagonalisation of each), through clusters that split as the
+vectors improve, and (ten-fold) to its FP64 Jacobi fallback. The refined solver is for matrices whose eigenvalues
 are needed to absolute accuracy (the Rayleigh-Ritz step); small eigenvalues of
 a positive definite matrix keep only absolute accuracy there, which is why the
 Davidson's Gram matrices of new directions stay with the FP64 Jacobi."""
@@ -51,18 +52,31 @@ def _check(A, w, V, orth=1e-13):
 def test_eigh_random(gpu, which, n):
     A = _hermitian(n, seed=70 + n)
     w, V, ms = gpu.diag_eigh(which, A)
-    # the refinement's orthonormality ends near eps |A| / (smallest gap), about 1e-13 here
-    _check(A, w, V, orth=1e-13 if which == 0 else 1e-12)
+    _check(A, w, V)
+
+
+def _spectra():
+    rng = np.random.default_rng(81)
+    base = -3700.0 + 300.0 * np.sort(rng.uniform(-1.0, 1.0, 24))
+    yield "pairs", np.concatenate([base, base, base[:8] + 1e-9, base[8:16] + 1e-6]), 82   # exact and near pairs
+    # converging Davidson roots: two near pairs below a spread of higher Ritz values
+    yield "ritz", np.concatenate([[0.8382872629, 0.8382872629 + 1e-12, 0.898, 0.898 + 1e-11],
+                                  np.sort(np.random.default_rng(5).uniform(0.9, 5.0, 28))]), 3
+    # six eigenvalues 1e-7 apart: one cluster at first, separate pairs later
+    yield "six", np.concatenate([1.0 + 1e-7 * np.arange(6), np.linspace(2.0, 3.0, 20)]), 5
+    # time-reversal pairs split by 1e-13
+    yield "kramers", np.repeat(np.linspace(-5.0, 5.0, 16), 2) + np.tile([0.0, 1e-13], 16), 6
+    # a ten-fold eigenvalue: wider than the refinement's exact cluster step (FP64 Jacobi instead)
+    yield "tenfold", np.concatenate([np.full(10, 1.0), np.linspace(2.0, 3.0, 20)]), 4
 
 
 @pytest.mark.parametrize("which", [0, 1])
-def test_eigh_degenerate_and_close(gpu, which):
-    rng = np.random.default_rng(81)
-    base = -3700.0 + 300.0 * np.sort(rng.uniform(-1.0, 1.0, 24))
-    lam = np.concatenate([base, base, base[:8] + 1e-9, base[8:16] + 1e-6])   # exact pairs, near pairs
-    A = _hermitian(lam.size, seed=82, spectrum=lam)
+@pytest.mark.parametrize("case", ["pairs", "ritz", "six", "kramers", "tenfold"])
+def test_eigh_degenerate_and_close(gpu, which, case):
+    _, lam, seed = next(c for c in _spectra() if c[0] == case)
+    A = _hermitian(lam.size, seed=seed, spectrum=lam)
     w, V, ms = gpu.diag_eigh(which, A)
-    _check(A, w, V, orth=1e-13 if which == 0 else 1e-12)
+    _check(A, w, V)
 
 
 def test_eigh_refined_is_faster(gpu):
