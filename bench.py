@@ -660,6 +660,38 @@ def run_reference(args, cfgname):
     print(json.dumps(line))
 
 
+def run_init_profile(args, name):
+    """adc_init of the workload from host buffers (the e2e leg's setup) with the
+    library's profile on from the start: wall time, the device time of each
+    setup stage and of the GEMMs inside (one JSON line)."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_2511_21640_gb300 as adcgpu
+    cfg = dict(CONFIGS[name])
+    p = config_problem(name)
+    Bh = torch.from_numpy(p.B).pin_memory()
+    eoh, evh = torch.from_numpy(p.eps_occ), torch.from_numpy(p.eps_vir)
+    torch.cuda.synchronize()
+    nvtx_range("init", True)
+    t0 = time.perf_counter()
+    ctx = adcgpu.Context(Bh, eoh, evh, kind=cfg["kind"], order=cfg["order"], x=cfg["x"], setup=args.e2e_setup,
+                         dd_order=cfg.get("dd_order", 1), profile=True)
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    nvtx_range("init", False)
+    prof = ctx.profile_read()
+    stages = {k[6:]: round(v["total_ms"], 3) for k, v in prof.items() if k.startswith("stage:")}
+    gemms = sorted(((k, v) for k, v in prof.items() if not k.startswith("stage:")), key=lambda kv: -kv[1]["total_ms"])
+    out = {"config": name, "setup": args.e2e_setup, "init_s": init_s, "stages_ms": stages,
+           "gemm_ms_total": round(sum(v["total_ms"] for _, v in gemms), 3),
+           "gemms": [{"name": k, "launches": v["launches"], "ms": round(v["total_ms"], 3),
+                      "tflops": (v["flops"] / (v["total_ms"] * 1e-3) / 1e12) if v["total_ms"] > 0 else None}
+                     for k, v in gemms[:30]],
+           "mem_peak_gib": ctx.memory()["peak"] / 2**30, "setup_routes": ctx.setup_routes()}
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -685,6 +717,8 @@ def main():
                     help="reference arm: oracle rows per step (about 30 s of one core each)")
     ap.add_argument("--cpu-rows", type=int, default=16,
                     help="CPU baseline: oracle rows, run one per host core (about 30 s each)")
+    ap.add_argument("--init-only", action="store_true",
+                    help="time adc_init alone (host inputs, the e2e setup) and print its stage and GEMM profile")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -694,6 +728,10 @@ def main():
             run_reference(args, args.config)
         return
 
+    if args.init_only:
+        if rank == 0:
+            run_init_profile(args, args.config)
+        return
     if args.config in CONFIGS and CONFIGS[args.config]["kind"] == "EE":
         if rank == 0:
             import torch

@@ -128,6 +128,11 @@ typedef struct {
                            more than a quarter of the free device memory),
                            1 = integral-direct (formed from B in chunks where
                            needed), -1 = stored once (the packed Pv x Pv block) */
+  int profile;          /* 1 = per-kernel timing from the start of adc_init, so
+                           that adc_profile_read also reports the setup's GEMMs
+                           and its stages ("stage:<name>" entries, each the
+                           device time of one step of the setup); 0 = off
+                           (default; adc_profile_enable switches it later) */
 } adc_opts;
 
 typedef struct {

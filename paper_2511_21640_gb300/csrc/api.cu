@@ -165,6 +165,7 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
       c->own_stream = true;
     }
     Exec &ex = c->ex;
+    ex.prof = (c->opts.profile != 0);
     // orbital energies
     std::vector<double> eo(nocc), ev(nvir);
     if (is_device_ptr(eps_occ)) ADC_CUDA(cudaMemcpy(eo.data(), eps_occ, nocc * 8, cudaMemcpyDeviceToHost));
@@ -201,8 +202,11 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
     c->ex.sliced_bits = (c->opts.setup == ADC_PREC_SLICED) ? 48 : 0;
     c->ex.n_sliced = c->ex.n_fp64 = 0;
     c->ex.flops_sliced = c->ex.flops_fp64 = 0.0;
-    if (kind == ADC_EE) setup_ee(c);
-    else setup_operators(c);
+    {
+      StageScope st(ex, "setup");
+      if (kind == ADC_EE) setup_ee(c);
+      else setup_operators(c);
+    }
     c->ex.sliced_bits = 0;
     c->setup_n[0] = c->ex.n_sliced;
     c->setup_n[1] = c->ex.n_fp64;

@@ -352,15 +352,18 @@ void setup_ee(adc_ctx *c) {
   }
   E.SD1 = parse_terms(kSD1); E.O2 = parse_terms(kO2); E.Z1 = parse_terms(kZ1); E.DD1 = parse_terms(kDD1);
   amplitude_tables(E.T2N, E.S2N);
+  StageScope stage(ex, "first_order_amplitudes");
   first_order_amplitudes(c);
   const bool chunked = ee_vvvv_chunked(c);
   DBuf Lad_keep;  // the ladder intermediate, for the chunked four-virtual terms
   if (c->order == 3) {
     // also at x = 0: the derivative with respect to x needs them
     DBuf G_vv, Lad;
+    stage.next("second_order_amplitudes");
     second_order_amplitudes(c, G_vv, Lad, E.t2d, E.t2s);
     if (chunked && third) Lad_keep = std::move(Lad);
   }
+  stage.next("singles_second_order");
   TermSource src = ee_source(c);
   const std::string L = "iajb";
   std::vector<int64_t> e4 = {o, v, o, v};
@@ -390,6 +393,7 @@ void setup_ee(adc_ctx *c) {
   ADC_CHECK_LAUNCH();
   eval_terms(ex, E.Y2, src, {}, false, C1(), M, L);
   if (third) {
+    stage.next("singles_third_order");
     DBuf S3 = cbuf(ex, n1 * n1);
     fill_zero(ex, S3.p, S3.bytes);
     eval_terms(ex, E.S3, src, {}, false, C1(), TV::dense(S3.c(), e4), L);
@@ -409,6 +413,7 @@ void setup_ee(adc_ctx *c) {
           n1, 1);
   }
   // a copy as the generic main block
+  stage.next("diagonal");
   c->M11 = cbuf(ex, n1 * n1);
   ADC_CUDA(cudaMemcpyAsync(c->M11.p, E.MSS.p, n1 * n1 * sizeof(cplx), cudaMemcpyDeviceToDevice, ex.stream));
   // diagonal

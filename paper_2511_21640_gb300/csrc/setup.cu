@@ -282,6 +282,7 @@ void setup_operators(adc_ctx *c) {
       c->direct_ladder = (double)pv * (double)pv * sizeof(cplx) > 0.25 * (double)fr;
     }
   }
+  StageScope stage(ex, "first_order_amplitudes");
   first_order_amplitudes(c);
   TV t1 = dense(c->t1, {o, o, v, v});
   DBuf oovv = cbuf(ex, o * o * v * v);
@@ -290,12 +291,14 @@ void setup_operators(adc_ctx *c) {
   TV W = dense(c->W, {o, v, o, v});
 
   // ---- second-order densities of Psi1
+  stage.next("densities");
   DBuf gvv_b = cbuf(ex, v * v), hoo_b = cbuf(ex, o * o);
   TV gvv = dense(gvv_b, {v, v}), hoo = dense(hoo_b, {o, o});
   einsum(ex, CR(0.5), t1.cj(), "ijdf", t1, "ijef", C0(), gvv, "de");
   einsum(ex, CR(0.5), t1.cj(), "njef", t1, "mjef", C0(), hoo, "nm");
 
   // ---- second-order amplitudes, ladder intermediate, R (third order only)
+  stage.next("second_order_amplitudes");
   DBuf t2d_b, t2s_b, R_b, Lad_b, G_vv;
   if (third) {
     second_order_amplitudes(c, G_vv, Lad_b, t2d_b, t2s_b);
@@ -305,6 +308,7 @@ void setup_operators(adc_ctx *c) {
   }
 
   // ---- main block
+  stage.next("main_block");
   c->M11 = cbuf(ex, c->n1 * c->n1);
   fill_zero(ex, c->M11.p, c->M11.bytes);
   if (c->kind == ADC_EA) {
@@ -389,6 +393,7 @@ void setup_operators(adc_ctx *c) {
   Lad_b.reset(); R_b.reset(); t2d_b.reset(); t2s_b.reset();
 
   // ---- coupling block
+  stage.next("coupling");
   c->Cpl = cbuf(ex, c->n1 * c->n2);
   if (c->kind == ADC_EA) {
     // <ck||de> = J(c,k,d,e) - J(c,k,e,d), J = sum_Q B_cd B_ke
@@ -444,6 +449,7 @@ void setup_operators(adc_ctx *c) {
   }
 
   // ---- ladder integrals of the satellite block (first order, x-scaled)
+  stage.next("satellite_ladder");
   if (third && x != 0.0) {
     if (c->kind == ADC_EA) {
       if (!c->direct_ladder) c->Glad = std::move(G_vv);
@@ -461,6 +467,7 @@ void setup_operators(adc_ctx *c) {
   G_vv.reset();
 
   // ---- diagonal
+  stage.next("diagonal");
   c->diag = DBuf(ex, c->N * sizeof(double));
   c->d2 = DBuf(ex, c->n2 * sizeof(double));
   {

@@ -69,6 +69,28 @@ struct DBuf {
   double *d() const { return (double *)p; }
 };
 
+// device time of one step of a longer procedure ("stage:<name>" in the profile)
+// (next() ends the current step and starts the following one)
+struct StageScope {
+  Exec &ex;
+  int rec = -1;
+  StageScope(Exec &e, const char *name) : ex(e) { begin(name); }
+  ~StageScope() { end(); }
+  void next(const char *name) {
+    end();
+    begin(name);
+  }
+
+ private:
+  void begin(const char *name) {
+    rec = ex.prof ? ex.prof_begin((std::string("stage:") + name).c_str(), 0.0) : -1;
+  }
+  void end() {
+    if (rec >= 0 && rec < (int)ex.recs.size()) cudaEventRecord(ex.recs[rec].b, ex.stream);
+    rec = -1;
+  }
+};
+
 // names the sigma term whose kernels are being launched (for the profile)
 struct TagScope {
   Exec &ex;
