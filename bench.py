@@ -110,7 +110,10 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-THREE_M = ("zgemm", "gram", "combine")  # FP64 kernels whose complex products take 3 real products
+THREE_M = ("zgemm", "gram", "combine")
+# k_gram<32, 8, 4, 2, 32> on 32 x 8 vectors of n = 796200 (one launch, ncu): 510,484,736 B read +
+# 4,910,080 B written against (32 + 8) * 796200 * 16 + 32 * 8 * 16 = 509,572,096 algorithmic bytes
+GRAM_DRAM_RATIO = (510484736 + 4910080) / ((32 + 8) * 796200 * 16 + 32 * 8 * 16)  # FP64 kernels whose complex products take 3 real products
 
 
 def fp64_peak(adcgpu):
@@ -136,7 +139,7 @@ def alu_row(name, e, peak64, peak_kind):
             "frac": ach / peak64, "traffic": None, "peak_kind": f"fp64 FMA {peak64:.3f} TFLOP/s, {peak_kind}; "
             "3M complex products execute 6 of the 8 algorithmic flops, so frac can reach 4/3",
             "executed_frac": ex * ach / peak64, "flops_per_launch": alg, "avg_launch_ms": avg,
-            "launches": e["launches"]}
+            "algorithmic_bytes_per_launch": e.get("bytes", 0.0) / e["launches"], "launches": e["launches"]}
 
 
 def sigma_flops_formula(o, v, Q, k):
@@ -839,6 +842,15 @@ def main():
     if key in measured_traffic:
         roof["traffic"] = measured_traffic[key]
         roof["traffic_note"] = "one ncu capture of the 320 x 19900 x 19900 FP64 ladder GEMM"
+    # kernels whose launches differ in shape: DRAM bytes over algorithmic bytes of one
+    # captured launch (ncu), times this run's algorithmic bytes per launch
+    traffic_ratio = {"gram_fp64": (GRAM_DRAM_RATIO, "ncu capture of one k_gram launch, 32 x 8 vectors of "
+                                                    "n = 796200: DRAM bytes / algorithmic bytes")}
+    base = roof["kernel"].split("/")[0]
+    if roof["traffic"] is None and base in traffic_ratio and roof.get("algorithmic_bytes_per_launch"):
+        ratio, note = traffic_ratio[base]
+        roof["traffic"] = ratio * roof["algorithmic_bytes_per_launch"]
+        roof["traffic_note"] = f"{note} = {ratio:.3f}, scaled to this run's launches"
     tc_rows = [r for r in by_kernel if r["kernel"].startswith("tc_")]
     roof_tc = tc_rows[0] if tc_rows else None
 

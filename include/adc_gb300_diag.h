@@ -36,14 +36,17 @@ int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_t seed, int
  * record and starts recording a CUDA event pair around every GEMM launch on
  * the context's stream (0 stops). adc_profile_read() synchronises the stream
  * and returns one entry per kernel and sigma term ("tc_gemm_bf16x3/ladder",
- * "zgemm_fp64/ring", ...): launches, total device milliseconds and the
+ * "zgemm_fp64/ring", ...): launches, total device milliseconds, the
  * algorithmic flops of those launches (8 per complex multiply-add, no
- * padding). *n receives the number of entries (at most max). */
+ * padding) and their algorithmic device-memory bytes (operands read once,
+ * results written once; 0 where not recorded). *n receives the number of
+ * entries (at most max). */
 typedef struct {
   char name[48];
   int64_t launches;
   double total_ms;
   double flops;
+  double bytes;
 } adc_kernel_stat;
 
 int adc_profile_enable(adc_ctx_opaque *ctx, int on);

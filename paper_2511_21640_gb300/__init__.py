@@ -55,7 +55,7 @@ class adc_stats(ctypes.Structure):
 
 class adc_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
-                ("flops", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 class adc_ssfns_root(ctypes.Structure):
@@ -320,7 +320,7 @@ class Context:
         n = ctypes.c_int()
         _check(lib.adc_profile_read(self._h, buf, 512, ctypes.byref(n)), self._h)
         return {buf[i].name.decode(): {"launches": buf[i].launches, "total_ms": buf[i].total_ms,
-                                       "flops": buf[i].flops} for i in range(n.value)}
+                                       "flops": buf[i].flops, "bytes": buf[i].bytes} for i in range(n.value)}
 
     def diagonal(self):
         d = np.empty(self.N, dtype=np.float64)

@@ -225,7 +225,8 @@ void gram(Exec &ex, const cplx *A, int64_t lda, int na, const cplx *B, int64_t l
     for (int a = 0; a < na; ++a) ADC_CUDA(cudaMemsetAsync(G + (int64_t)a * ldg, 0, nb * sizeof(cplx), ex.stream));
     return;
   }
-  int pr = ex.prof_begin("gram_fp64", 8.0 * (double)na * nb * (double)n);
+  int pr = ex.prof_begin("gram_fp64", 8.0 * (double)na * nb * (double)n,
+                         16.0 * ((double)(na + nb) * (double)n + (double)na * nb));
   // one row against many: the transposed product has the long side in rows
   const bool trans = (na < 8 && nb > na);
   const cplx *P = trans ? B : A, *R = trans ? A : B;
@@ -268,7 +269,9 @@ void combine(Exec &ex, const cplx *C, int64_t ldc, int m, int nr, const cplx *V,
   const int RR = nr >= 9 ? 16 : nr >= 5 ? 8 : nr >= 3 ? 4 : nr;
   const int gy = (nr + RR - 1) / RR;
   ADC_REQUIRE(gx < (1ll << 31) && gy <= 65535, ADC_ERR_UNSUPPORTED, "combine: shape");
-  int pr = ex.prof_begin("combine_fp64", 8.0 * (double)nr * m * (double)n);
+  const bool rd = (beta.x != 0.0 || beta.y != 0.0);
+  int pr = ex.prof_begin("combine_fp64", 8.0 * (double)nr * m * (double)n,
+                         16.0 * ((double)m + (rd ? 2.0 : 1.0) * nr) * (double)n);
   const dim3 grid((unsigned)gx, gy);
   switch (RR) {
     case 1: k_combine<1><<<grid, 256, 0, ex.stream>>>(C, ldc, m, nr, V, ldv, n, alpha, beta, Y, ldy); break;

@@ -314,11 +314,15 @@ struct Davidson {
     return h;
   }
 
-  // project out span(V[0:m]) from T[0:nt] twice (block classical Gram-Schmidt),
+  // project out span(V[0:m]) from T[0:nt] by block classical Gram-Schmidt,
+  // a second pass only when the first removed more than 1 - 1/sqrt(2) of some
+  // vector's norm (the criterion of Daniel, Gragg, Kaufman and Stewart: past
+  // it one pass leaves T orthogonal to V to the rounding of the products),
   // then orthonormalise the block symmetrically (Loewdin, as in Eq. 6): with
   // <t_a|t_b> = Z diag(l) Z^H, the kept directions are T' = (Z l^-1/2)^T T for
   // eigenvalues l above the rank threshold. Returns the number of vectors kept,
   // stored at the front of T.
+  int cgs_passes = 0;
   int orthonormalise(int nt) {
     if (nt <= 0) return 0;
     std::vector<double> n0 = row_norms(T.c(), nt);
@@ -327,6 +331,14 @@ struct Davidson {
     for (int pass = 0; pass < 2 && m > 0; ++pass) {
       gram(ex, V.c(), N, m, T.c(), N, nt, N, C1(), tmp.c(), nt);
       combine(ex, tmp.c(), nt, m, nt, V.c(), N, N, CR(-1.0), C1(), T.c(), N);
+      ++cgs_passes;
+      if (pass == 0) {
+        const std::vector<double> n1 = row_norms(T.c(), nt);
+        bool enough = true;
+        for (int j = 0; j < nt; ++j)
+          if (!(n1[j] >= 0.70710678118654752 * n0[j])) enough = false;
+        if (enough) break;
+      }
     }
     gram(ex, T.c(), N, nt, T.c(), N, nt, N, C1(), Gs.c(), nt);
     // FP64 Jacobi: its small eigenvalues (which decide the directions kept)

@@ -256,6 +256,7 @@ extern "C" int adc_profile_read(adc_ctx *c, adc_kernel_stat *out, int max, int *
       s->launches += 1;
       s->total_ms += ms;
       s->flops += r.flops;
+      s->bytes += r.bytes;
     }
     *n = (int)std::min<size_t>(agg.size(), (size_t)std::max(max, 0));
     for (int i = 0; i < *n; ++i) out[i] = agg[i];

@@ -51,13 +51,14 @@ cudaEvent_t Exec::event() {
   return e;
 }
 
-int Exec::prof_begin(const char *kernel, double flops) {
+int Exec::prof_begin(const char *kernel, double flops, double bytes) {
   if (!prof) return -1;
   ProfRec r;
   r.name = std::string(kernel) + (tag.empty() ? "" : "/" + tag);
   r.a = event();
   r.b = event();
   r.flops = flops;
+  r.bytes = bytes;
   ADC_CUDA(cudaEventRecord(r.a, stream));
   recs.push_back(r);
   return (int)recs.size() - 1;
@@ -291,7 +292,8 @@ void zgemm(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha,
     ksplit = (int)std::max<int64_t>(1, s);
   }
   const int64_t bmax = 65535 / ksplit;
-  int pr = ex.prof_begin("zgemm_fp64", 8.0 * (double)M * N * K * batch);
+  int pr = ex.prof_begin("zgemm_fp64", 8.0 * (double)M * N * K * batch,
+                         16.0 * (double)batch * ((double)M * K + (double)K * N + (double)M * N));
   for (int64_t b0 = 0; b0 < batch; b0 += bmax) {
     int64_t nb = std::min<int64_t>(bmax, batch - b0);
     dim3 grid(mfast ? (unsigned)mt_ : (unsigned)nt_, mfast ? (unsigned)nt_ : (unsigned)mt_, (unsigned)(nb * ksplit));

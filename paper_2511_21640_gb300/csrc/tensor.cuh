@@ -13,6 +13,7 @@ struct ProfRec {
   std::string name;
   cudaEvent_t a = nullptr, b = nullptr;
   double flops = 0.0;  // algorithmic flops of the launch (8 per complex multiply-add)
+  double bytes = 0.0;  // algorithmic device-memory bytes (operands read once, result written once)
 };
 
 struct Exec {
@@ -35,7 +36,7 @@ struct Exec {
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> event_pool;
   cudaEvent_t event();
-  int prof_begin(const char *kernel, double flops);  // record index, -1 when off
+  int prof_begin(const char *kernel, double flops, double bytes = 0.0);  // record index, -1 when off
   void prof_end(int r);
   void prof_clear();
 
