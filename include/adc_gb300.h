@@ -133,6 +133,10 @@ typedef struct {
                            and its stages ("stage:<name>" entries, each the
                            device time of one step of the setup); 0 = off
                            (default; adc_profile_enable switches it later) */
+  int grouped_sigma;    /* IP/EA BF16x3 products with the stored operators:
+                           0 = every tensor-core term (both coupling
+                           directions, ladder, ring) as jobs of one grouped
+                           persistent launch (default); -1 = one launch per term */
 } adc_opts;
 
 typedef struct {

@@ -40,7 +40,8 @@ class adc_opts(ctypes.Structure):
                 ("max_subspace", ctypes.c_int), ("herm_tol", ctypes.c_double),
                 ("mem_limit", ctypes.c_int64), ("verbose", ctypes.c_int), ("dd_order", ctypes.c_int),
                 ("refine", ctypes.c_int), ("setup", ctypes.c_int), ("ee_vvvv", ctypes.c_int),
-                ("correction", ctypes.c_int), ("ladder", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("correction", ctypes.c_int), ("ladder", ctypes.c_int), ("profile", ctypes.c_int),
+                ("grouped_sigma", ctypes.c_int)]
 
 
 class adc_stats(ctypes.Structure):
@@ -204,7 +205,7 @@ class Context:
     def __init__(self, B, eps_occ, eps_vir, kind="IP", order=3, x=1.0, precision="fp64", stream=None,
                  block=0, max_subspace=0, herm_tol=1e-12, mem_limit=0, verbose=False, dd_order=1,
                  refine="fp64", setup="fp64", vvvv="auto", correction="davidson", ladder="auto",
-                 profile=False):
+                 profile=False, grouped_sigma=True):
         o = adc_opts()
         lib.adc_opts_default(ctypes.byref(o))
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -225,6 +226,7 @@ class Context:
         o.correction = {"davidson": 0, "olsen": 1}[correction]
         o.ladder = {"auto": 0, "direct": 1, "stored": -1}[ladder]
         o.profile = 1 if profile else 0
+        o.grouped_sigma = 0 if grouped_sigma else -1
         naux, nmo, nmo2 = B.shape
         nocc, nvir = eps_occ.shape[0], eps_vir.shape[0]
         if nmo != nmo2 or nmo != nocc + nvir:

@@ -147,6 +147,8 @@ int adc_init(adc_ctx **out, const adc_c128 *B, int64_t naux, const double *eps_o
     ADC_REQUIRE(c->opts.ee_vvvv >= -1 && c->opts.ee_vvvv <= 1, ADC_ERR_ARG, "opts.ee_vvvv: -1, 0 or 1");
     ADC_REQUIRE(c->opts.correction == 0 || c->opts.correction == 1, ADC_ERR_ARG, "opts.correction: 0 or 1");
     ADC_REQUIRE(c->opts.ladder >= -1 && c->opts.ladder <= 1, ADC_ERR_ARG, "opts.ladder: -1, 0 or 1");
+    ADC_REQUIRE(c->opts.grouped_sigma == 0 || c->opts.grouped_sigma == -1, ADC_ERR_ARG,
+                "opts.grouped_sigma: 0 or -1");
     c->kind = kind;
     c->order = order;
     c->x = (order == 3) ? x : 0.0;

@@ -983,6 +983,12 @@ int tc_autotune_bn(Exec &ex, const TcJobDesc &d, int *err) {
     cand.push_back(bn);
     if (bn >= N2) break;
   }
+  // also the narrowest width of the fewest tiles (no padded last tile where N2 allows)
+  if (N2 > TC_BNMAX) {
+    const int64_t nt = (N2 + TC_BNMAX - 1) / TC_BNMAX;
+    const int even = (int)(((N2 + nt - 1) / nt + 31) / 32 * 32);
+    if (even < TC_BNMAX) cand.push_back(even);
+  }
   int best = bn_rule(N2);
   if (cand.size() > 1) {
     // time each candidate as a lone job writing a scratch output (beta = 0)

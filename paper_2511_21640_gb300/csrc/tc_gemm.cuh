@@ -140,6 +140,8 @@ struct TcCache {
   TcMat Glad, W, Cpl, CplT;  // static operators (A side)
   TcMat LA, LB;              // B^Q_ac as both operands of the integral-direct ladder's J = L L^T
   TcMat Bx;                  // per-call B operand
+  TcMat Bx1, Bx2, Bxl, Bxr;  // per-call B operands of the grouped product (X1, X2, ladder, ring)
+  TcGroup grp;               // job table of the grouped product
   DBuf err;                  // device error word of the tensor-core kernels
   bool ready = false;
 };

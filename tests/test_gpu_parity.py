@@ -145,6 +145,26 @@ def test_sigma_parity(gpu, kind, o, v, Q, order, x, seed):
             assert np.abs(M11 - ref11).max() < 1e-12 * np.abs(ref11).max()
 
 
+@pytest.mark.parametrize("kind,o,v,Q,order,x,seed,k", [
+    ("EA", 6, 30, 64, 3, 0.5, 14, 3), ("EA", 4, 45, 50, 2, 0.0, 16, 2), ("EA", 7, 33, 70, 3, 1.0, 17, 9),
+    ("IP", 8, 24, 96, 3, 1.0, 0, 4), ("IP", 9, 20, 30, 2, 0.0, 13, 1), ("IP", 5, 37, 40, 3, 0.5, 11, 7)])
+def test_grouped_split_sigma(gpu, kind, o, v, Q, order, x, seed, k):
+    """The BF16x3 product with all tensor-core terms in one grouped launch (default)
+    against one launch per term and against the oracle: both are the same three-product
+    split, so they differ only by the FP32 summation order of the tiles."""
+    p = make_problem(o, v, Q, seed=seed, sigma=0.08)
+    X = random_vectors(oadc.dims(kind, o, v)[0] + oadc.dims(kind, o, v)[1], k, seed=seed + 200)
+    ref = oadc.sigma_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, X)
+    out = {}
+    for grouped in (True, False):
+        with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=order, x=x, grouped_sigma=grouped) as ctx:
+            out[grouped] = ctx.sigma(X, "bf16x3")
+            # repeated calls reuse the job table and the packed operands
+            assert np.array_equal(ctx.sigma(X, "bf16x3"), out[grouped])
+    assert _rel(out[True], ref).max() < 1e-4
+    assert _rel(out[True], out[False]).max() < 1e-5
+
+
 def test_sigma_zero_vectors_and_k0(gpu):
     p = make_problem(4, 10, 12, seed=2, sigma=0.1)
     with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EA", order=3, x=1.0) as ctx:
