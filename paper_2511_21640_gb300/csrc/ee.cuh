@@ -27,6 +27,8 @@ struct EEOps {
                                     // <ak||iM> [(i,a)][(k,M)], <aA||ci> [(i,a)][(c,A)]
   // split-precision copies for the tensor-core sigma (A operands) and the per-call B operand
   TcMat tVaT, tVaC, tVb, tVbC, tGvv, tGoo, tW, bx;
+  // the second-order amplitude operands of the separable pieces: T1p^T, conj(T1p), T2p^T, conj(T2p)
+  TcMat tT1T, tT1C, tT2T, tT2C;
   DBuf tcerr;
   bool tc_ready = false;
   int tc_planes = 0;

@@ -431,6 +431,13 @@ static void ee_tc_build(adc_ctx *c, bool dd, int planes) {
     tc_pack_A(ex, E.tGoo, E.Goo.c(), po, po, po, 1, false, planes);
     tc_pack_A(ex, E.tW, c->W.c(), ov, ov, ov, 1, false, planes);
   }
+  if (c->order == 3 && c->x != 0.0) {
+    // T1p [(l,cd)][M] and T2p [((kl),d)][A] as the A side of the separable pieces
+    tc_pack_A(ex, E.tT1T, E.T1p.c(), o, o * pv, 1, o, false, planes);
+    tc_pack_A(ex, E.tT1C, E.T1p.c(), o * pv, o, o, 1, true, planes);
+    tc_pack_A(ex, E.tT2T, E.T2p.c(), v, po * v, 1, v, false, planes);
+    tc_pack_A(ex, E.tT2C, E.T2p.c(), po * v, v, v, 1, true, planes);
+  }
   E.tc_planes = planes;
   E.tcerr = DBuf(ex, sizeof(int));
   fill_zero(ex, E.tcerr.p, sizeof(int));
@@ -462,8 +469,11 @@ static void ee_sl_build(adc_ctx *c, bool dd) {
 
 // ee_struct_apply with the GEMMs over the doubles on the tensor cores, as the
 // BF16x3/BF16x6 split (nseg 3 or 6) or as the sliced FP64-accurate product
-// (nseg 0); the separable second-order pieces (o x o and v x v intermediates)
-// go through zgemm, which the caller switches to the sliced product
+// (nseg 0). The separable second-order pieces (o x o and v x v intermediates):
+// with the split, their contractions over the long (l, c<d) and ((k<l), d)
+// indices and their updates of the gathered doubles run on the tensor cores
+// as well (the small products against V1, V2 stay FP64); with the sliced
+// product they go through zgemm, which the caller switches to the sliced route
 static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, double sdd, int nseg) {
   Exec &ex = c->ex;
   EEOps &E = *c->ee;
@@ -500,17 +510,30 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
     DBuf U;
     if (second) {
       DBuf Y1 = cbuf(ex, kc * o * o);
-      zgemm(ex, o, o, o * pv, kc, C1(), Xa.c(), o * o * pv, o * pv, 1, false, E.T1p.c(), 0, o, 1, false, C0(),
-            Y1.c(), o * o, o, 1);
+      if (sliced) {
+        zgemm(ex, o, o, o * pv, kc, C1(), Xa.c(), o * o * pv, o * pv, 1, false, E.T1p.c(), 0, o, 1, false, C0(),
+              Y1.c(), o * o, o, 1);
+      } else {
+        // Y1[z][i][M] = sum_(l,cd) T1p[(l,cd)][M] Xa[z][i][(l,cd)]
+        tc_pack_B(ex, E.bx, Xa.c(), kc * o, o * pv, o * pv, 0, 1, 1, false, planes);
+        tc_gemm(ex, E.tT1T, E.bx, o, kc * o, C1(), C0(), Y1.c(), 1, o, 0, 1, err, nseg);
+      }
       zgemm(ex, kc, n1, o * o, 1, CR(x), Y1.c(), 0, o * o, 1, false, E.V1.c(), 0, 1, o * o, false, C1(), S, 0, N, 1);
       U = cbuf(ex, kc * o * o);
       zgemm(ex, kc, o * o, n1, 1, C1(), X, 0, N, 1, false, E.V1.c(), 0, o * o, 1, true, C0(), U.c(), 0, o * o, 1);
     }
     // F[z][i][(l,cd)] = sum_a conj(Va[(l,cd)][a]) X1[z][i][a]
     mul(EE_VAC, X, kc * o, v, N, v, o, 1, o * pv, C1(), C0(), Xa.c(), 1, o * o * pv, o * pv, o);
-    if (second)
-      zgemm(ex, o, o * pv, o, kc, CR(x), U.c(), o * o, o, 1, false, E.T1p.c(), 0, 1, o, true, C1(), Xa.c(),
-            o * o * pv, o * pv, 1);
+    if (second) {
+      if (sliced) {
+        zgemm(ex, o, o * pv, o, kc, CR(x), U.c(), o * o, o, 1, false, E.T1p.c(), 0, 1, o, true, C1(), Xa.c(),
+              o * o * pv, o * pv, 1);
+      } else {
+        // Xa[z][i][(l,cd)] += x sum_M conj(T1p[(l,cd)][M]) U[z][i][M]
+        tc_pack_B(ex, E.bx, U.c(), kc * o, o, o, 0, 1, 1, false, planes);
+        tc_gemm(ex, E.tT1C, E.bx, o * pv, kc * o, CR(x), C1(), Xa.c(), 1, o * pv, 0, 1, err, nseg);
+      }
+    }
     k_scatter_f<<<grid1d(kc * po * pv, 256), 256, 0, ex.stream>>>(Xa.c(), kc, pio, pjo, o, po, pv, S + n1, N);
     ADC_CHECK_LAUNCH();
   }
@@ -524,17 +547,30 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
     DBuf U2;
     if (second) {
       DBuf Y2 = cbuf(ex, kc * v * v);
-      zgemm(ex, v, v, po * v, kc, C1(), Xb.c(), v * po * v, po * v, 1, false, E.T2p.c(), 0, v, 1, false, C0(),
-            Y2.c(), v * v, v, 1);
+      if (sliced) {
+        zgemm(ex, v, v, po * v, kc, C1(), Xb.c(), v * po * v, po * v, 1, false, E.T2p.c(), 0, v, 1, false, C0(),
+              Y2.c(), v * v, v, 1);
+      } else {
+        // Y2[z][c][A] = sum_((kl),d) T2p[((kl),d)][A] XbT[z][c][((kl),d)]
+        tc_pack_B(ex, E.bx, Xb.c(), kc * v, po * v, po * v, 0, 1, 1, false, planes);
+        tc_gemm(ex, E.tT2T, E.bx, v, kc * v, C1(), C0(), Y2.c(), 1, v, 0, 1, err, nseg);
+      }
       zgemm(ex, kc, n1, v * v, 1, CR(x), Y2.c(), 0, v * v, 1, false, E.V2.c(), 0, 1, v * v, false, C1(), S, 0, N, 1);
       U2 = cbuf(ex, kc * v * v);
       zgemm(ex, kc, v * v, n1, 1, C1(), X, 0, N, 1, false, E.V2.c(), 0, v * v, 1, true, C0(), U2.c(), 0, v * v, 1);
     }
     // G[z][((kl),d)][a] = sum_i conj(Vb[i][((kl),d)]) X1[z][i][a]  (reusing the buffer)
     mul(EE_VBC, X, kc * v, o, N, 1, v, v, po * v, C1(), C0(), Xb.c(), v, po * v * v, 1, v);
-    if (second)
-      zgemm(ex, po * v, v, v, kc, CR(x), E.T2p.c(), 0, v, 1, true, U2.c(), v * v, 1, v, false, C1(), Xb.c(),
-            po * v * v, v, 1);
+    if (second) {
+      if (sliced) {
+        zgemm(ex, po * v, v, v, kc, CR(x), E.T2p.c(), 0, v, 1, true, U2.c(), v * v, 1, v, false, C1(), Xb.c(),
+              po * v * v, v, 1);
+      } else {
+        // G[z][((kl),d)][a] += x sum_A conj(T2p[((kl),d)][A]) U2[z][a][A]
+        tc_pack_B(ex, E.bx, U2.c(), kc * v, v, v, 0, 1, 1, false, planes);
+        tc_gemm(ex, E.tT2C, E.bx, po * v, kc * v, CR(x), C1(), Xb.c(), v, po * v * v, 1, v, err, nseg);
+      }
+    }
     k_scatter_g<<<grid1d(kc * po * pv, 256), 256, 0, ex.stream>>>(Xb.c(), kc, pav, pbv, v, po, pv, S + n1, N);
     ADC_CHECK_LAUNCH();
   }
