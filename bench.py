@@ -603,7 +603,8 @@ def run_ee(args, cfgname):
                    "l2": "operators larger than L2"},
         "clocks": clk, "gpu_launches": int(launches), "roofline": by_kernel[0], "roofline_by_kernel": by_kernel,
         "mixed_davidson": {"iterations": st["iterations"], "sigma_calls": st["sigma_calls"],
-                           "sigma_calls_fp64": st["sigma_calls_fp64"], "rc": int(rc),
+                           "sigma_calls_fp64": st["sigma_calls_fp64"], "sigma_calls_mid": st["sigma_calls_mid"],
+                           "rc": int(rc),
                            "omega": [float(w) for w in om], "err64": [float(e) for e in e64]},
         "fp64_davidson": fp64,
         "fns": fns,
@@ -967,7 +968,8 @@ def main():
                            "err64_source": "sliced product" if args.refine == "sliced" else "fp64 product",
                            "residual_fp64_recomputed": resid_fp64,
                            "iterations": last["iterations"], "sigma_calls": last["sigma_calls"],
-                           "sigma_calls_fp64": last["sigma_calls_fp64"], "rc": int(rc)},
+                           "sigma_calls_fp64": last["sigma_calls_fp64"], "sigma_calls_mid": last["sigma_calls_mid"],
+                           "rc": int(rc)},
         "init_s": init_s, "e2e": e2e, "cpu_baseline": cpu,
     }
     ctx.close()

@@ -70,8 +70,12 @@ enum { ADC_IP = 0, ADC_EA = 1, ADC_EE = 2 };
  *   below 2^24) and the pair products are combined in FP64, for about 40
  *   significant bits relative to the row and column maxima (about 1e-11
  *   relative to the largest output). Used for the refinement products of the
- *   mixed Davidson when opts.refine selects it. */
-enum { ADC_PREC_FP64 = 0, ADC_PREC_BF16X3 = 1, ADC_PREC_BF16X6 = 2, ADC_PREC_SLICED = 3 };
+ *   mixed Davidson when opts.refine selects it.
+ * ADC_PREC_SLICED24: the same sliced product with digits for about 24
+ *   significant bits (about 1e-7 relative to the largest output) at roughly
+ *   a third of its digit products: the intermediate step of that refinement,
+ *   for the correction vectors once the BF16x3 products stall. */
+enum { ADC_PREC_FP64 = 0, ADC_PREC_BF16X3 = 1, ADC_PREC_BF16X6 = 2, ADC_PREC_SLICED = 3, ADC_PREC_SLICED24 = 4 };
 
 enum {
   ADC_OK = 0,
@@ -143,10 +147,12 @@ typedef struct {
   int iterations;       /* Davidson iterations (mixed + FP64 phases) */
   int iterations_fp64;  /* iterations of the FP64 refinement phase */
   int sigma_calls;      /* vectors multiplied by M (all precisions) */
-  int sigma_calls_fp64; /* of those, in FP64 */
+  int sigma_calls_fp64; /* of those, in FP64 or the FP64-accurate sliced product */
   double time_total_s;  /* wall time of the call */
   double time_sigma_s;  /* time inside sigma products */
   double max_residual;  /* largest final FP64 residual norm over the roots */
+  int sigma_calls_mid;  /* vectors multiplied with ADC_PREC_SLICED24 (the
+                           intermediate refinement step) */
 } adc_stats;
 
 /* Fills *opts with the defaults (precision FP64, own stream, herm_tol 1e-12). */

@@ -21,10 +21,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libadc_gb300.so")
 
 ADC_IP, ADC_EA, ADC_EE = 0, 1, 2
-ADC_PREC_FP64, ADC_PREC_BF16X3, ADC_PREC_BF16X6, ADC_PREC_SLICED = 0, 1, 2, 3
+ADC_PREC_FP64, ADC_PREC_BF16X3, ADC_PREC_BF16X6, ADC_PREC_SLICED, ADC_PREC_SLICED24 = 0, 1, 2, 3, 4
 KINDS = {"IP": ADC_IP, "EA": ADC_EA, "EE": ADC_EE}
 PRECISIONS = {"fp64": ADC_PREC_FP64, "bf16x3": ADC_PREC_BF16X3, "bf16x6": ADC_PREC_BF16X6,
-              "sliced": ADC_PREC_SLICED}
+              "sliced": ADC_PREC_SLICED, "sliced24": ADC_PREC_SLICED24}
 ERRORS = {0: "ADC_OK", -1: "ADC_ERR_ARG", -2: "ADC_ERR_OOM", -3: "ADC_ERR_CUDA", -4: "ADC_ERR_NOCONV",
           -5: "ADC_ERR_TIMEOUT", -6: "ADC_ERR_UNSUPPORTED", -7: "ADC_ERR_STATE", -8: "ADC_ERR_NUMERIC"}
 
@@ -48,7 +48,7 @@ class adc_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("iterations_fp64", ctypes.c_int),
                 ("sigma_calls", ctypes.c_int), ("sigma_calls_fp64", ctypes.c_int),
                 ("time_total_s", ctypes.c_double), ("time_sigma_s", ctypes.c_double),
-                ("max_residual", ctypes.c_double)]
+                ("max_residual", ctypes.c_double), ("sigma_calls_mid", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

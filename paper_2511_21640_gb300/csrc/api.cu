@@ -242,7 +242,7 @@ int adc_sigma(adc_ctx *c, const adc_c128 *X, adc_c128 *S, int64_t k, int precisi
   if (!c) return ADC_ERR_STATE;
   if (k < 0 || (k > 0 && (!X || !S))) return ADC_ERR_ARG;
   if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3 && precision != ADC_PREC_BF16X6 &&
-      precision != ADC_PREC_SLICED)
+      precision != ADC_PREC_SLICED && precision != ADC_PREC_SLICED24)
     return ADC_ERR_ARG;
   if (k == 0) return ADC_OK;
   ADC_API_TRY

@@ -46,7 +46,7 @@ struct adc_ctx {
   // split-precision copies for the tensor-core sigma
   std::unique_ptr<adc::TcCache> tc;
   // integer-digit slices for the FP64-accurate tensor-core sigma
-  std::unique_ptr<adc::SlCache> sl;
+  std::unique_ptr<adc::SlCache> sl, sl24;  // sliced operator copies (40 and 24 bits)
 
   // EE-ADC operators (kind == ADC_EE)
   std::unique_ptr<adc::EEOps> ee;
@@ -129,14 +129,16 @@ int ssfns_run(const adc_c128 *B, int64_t naux, const double *eps_occ, int64_t no
               int64_t nvir, int kind, int order, double x, int nroots, double eta_crit, double tol, int max_iter,
               int precision, const adc_opts *opts, adc_ssfns_root *out);
 void sigma_ee_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
-void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg);
+// significant bits of the sliced sigma products (ADC_PREC_SLICED, ADC_PREC_SLICED24)
+constexpr int kSlicedBits = 40, kSliced24Bits = 24;
+void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg, int bits = kSlicedBits);
 void sigma_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
 // one rank's share of the EA sigma with the satellites split by occupied index [i0, i1) (sigma.cu)
 void sigma_fp64_share(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int64_t i0, int64_t i1, bool with_main);
 // split-precision sigma on the tensor cores: nseg = 3 (BF16x3) or 6 (BF16x6) products
 void sigma_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg);
 // FP64-accurate sigma with the dense contractions as sliced tensor-core products (IP/EA)
-void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
+void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int bits = kSlicedBits);
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision);
 void release_tc(adc_ctx *c);
 void tc_ensure(adc_ctx *c, int planes = 2);  // split-precision operator copies, built on first use

@@ -15,6 +15,10 @@
 //      collapse (subspace full, stall, or apparent convergence) recomputes
 //      sigma64 of the Ritz vectors, and convergence is only accepted on FP64
 //      residuals ||sigma64(y) - omega y|| <= tol.
+//   3. when the refinement itself stalls twice, the correction vectors take
+//      the next precision: with the sliced refinement first the sliced product
+//      with about 24 bits (an intermediate step at about a third of the digit
+//      products), after a further stall the refinement precision itself.
 // The refinement products (sigma64) are FP64, or with opts.refine the sliced
 // tensor-core product of tc_slice.cu, exact digit products combined in FP64.
 #include <algorithm>
@@ -266,6 +270,7 @@ struct Davidson {
     tsig += t.s();
     st.sigma_calls += (int)k;
     if (prec == ADC_PREC_FP64 || prec == ADC_PREC_SLICED) st.sigma_calls_fp64 += (int)k;
+    if (prec == ADC_PREC_SLICED24) st.sigma_calls_mid += (int)k;
   }
 
   // sigma of the na new vectors (in T and in V[m:m+na]) into AV[m:m+na]. In a
@@ -508,8 +513,15 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
                              ex.stream));
     m0 = acc;
   }
-  int phase = (precision == ADC_PREC_FP64) ? 2 : 0;  // 0 mixed, 1 refine, 2 plain FP64
-  int prec_new = (phase == 2) ? ADC_PREC_FP64 : mixed;
+  // phases: 0 mixed products; 1 FP64 base (the current Ritz vectors' products
+  // in prec64, taken at each collapse) and mixed corrections; 2 the same with
+  // the corrections in the intermediate sliced precision (only when the
+  // refinement is sliced); 3 every product in prec64, the final phase
+  const int prec_mid = (precision != ADC_PREC_FP64 && d.prec64 == ADC_PREC_SLICED) ? ADC_PREC_SLICED24 : -1;
+  auto prec_of = [&](int ph) { return ph <= 1 ? mixed : (ph == 2 ? prec_mid : d.prec64); };
+  auto next_phase = [&](int ph) { return ph == 0 ? 1 : (ph == 1 && prec_mid >= 0 ? 2 : 3); };
+  int phase = (precision == ADC_PREC_FP64) ? 3 : 0;
+  int prec_new = (phase == 3) ? ADC_PREC_FP64 : mixed;
   d.apply_sigma(d.V.c(), d.AV.c(), m0, prec_new);
   d.m = 0;
   d.nb = 0;
@@ -536,10 +548,10 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
     if (mx < 0.7 * best) { best = mx; since = 0; }
     else ++since;
     if (mx <= tol) {
-      if (phase == 2) { converged = true; break; }
+      if (phase == 3) { converged = true; break; }
       // accept only on FP64 residuals: collapse onto the wanted roots with sigma64 and re-check
       d.collapse(nroots, true);
-      phase = 1;
+      phase = std::max(phase, 1);
       wh = d.ritz(nroots);
       rn = d.row_norms(d.R.c(), nroots);
       mx = *std::max_element(rn.begin(), rn.end());
@@ -547,12 +559,13 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
       if (mx <= tol) { converged = true; break; }
       best = mx;
       since = 0;
-    } else if (phase != 2 && since >= stall_window) {
-      // stalled at the split-precision floor: FP64 base for the current Ritz vectors;
-      // when the refinement itself keeps stalling, the corrections go FP64 too
+    } else if (phase != 3 && since >= stall_window) {
+      // stalled at the floor of the corrections' precision: FP64 base for the
+      // current Ritz vectors; when the refinement itself keeps stalling, the
+      // corrections go to the next precision (intermediate, then prec64)
       d.collapse(nroots, true);
       if (phase == 1) ++refine_stalls;
-      phase = (phase == 1 && refine_stalls >= 2) ? 2 : 1;
+      if (phase == 0 || (phase == 1 && refine_stalls >= 2) || phase == 2) phase = next_phase(phase);
       best = 1e300;
       since = 0;
       continue;
@@ -562,8 +575,10 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
     for (int r = 0; r < nroots; ++r)
       if (rn[r] > tol) rows.push_back(r);
     if (d.m + (int)rows.size() > d.mmax) {
-      const int kc = (phase == 1) ? nroots : kr;  // FP64 sigma only for the wanted roots
-      d.collapse(kc, phase == 1);
+      // with products of two precisions in the subspace, prec64 for the wanted roots
+      const bool base = (phase == 1 || phase == 2);
+      const int kc = base ? nroots : kr;
+      d.collapse(kc, base);
       wh = d.ritz(kc);
     }
     ADC_CUDA(cudaMemcpyAsync(d.rowsb.p, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice, ex.stream));
@@ -595,24 +610,24 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
       na = d.orthonormalise((int)rows.size());
     }
     if (na == 0) {
-      if (phase == 2) break;
-      // no new direction at this precision: continue from an FP64 base, and
-      // in plain FP64 when that happens again
+      if (phase == 3) break;
+      // no new direction at this precision: continue from an FP64 base, with
+      // the corrections in the next precision
       d.collapse(nroots, true);
-      phase = (phase == 0) ? 1 : 2;
+      phase = next_phase(phase);
       best = 1e300;
       since = 0;
       continue;
     }
     ADC_CUDA(cudaMemcpyAsync(d.V.c() + (int64_t)d.m * N, d.T.c(), (int64_t)na * N * sizeof(cplx),
                              cudaMemcpyDeviceToDevice, ex.stream));
-    prec_new = (phase == 2) ? d.prec64 : mixed;
+    prec_new = prec_of(phase);
     d.apply_sigma_new(na, prec_new);
     d.extend_projection(d.m, na);
     d.m += na;
   }
   if (it > max_iter) it = max_iter;
-  if (!converged && phase != 2) {
+  if (!converged && phase != 3) {
     // report FP64 residuals of the best vectors
     d.collapse(nroots, true);
     wh = d.ritz(nroots);

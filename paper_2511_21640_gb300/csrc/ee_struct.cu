@@ -444,27 +444,32 @@ static void ee_tc_build(adc_ctx *c, bool dd, int planes) {
   E.tc_ready = true;
 }
 
-// sliced copies of the same operators (FP64-accurate tensor-core products)
-static void ee_sl_build(adc_ctx *c, bool dd) {
+// sliced copies of the same operators (FP64-accurate tensor-core products with
+// kSlicedBits, or kSliced24Bits for the intermediate refinement step)
+static void ee_sl_build(adc_ctx *c, bool dd, int bits) {
   Exec &ex = c->ex;
   EEOps &E = *c->ee;
   const int64_t o = c->o, v = c->v, po = npairs(o), pv = npairs(v), ov = o * v;
-  constexpr int bits = 40;
-  sl_pack_A(ex, E.sop[EE_VAT], E.Va.c(), v, o * pv, 1, v, false, bits);
-  sl_pack_A(ex, E.sop[EE_VAC], E.Va.c(), o * pv, v, v, 1, true, bits);
-  sl_pack_A(ex, E.sop[EE_VB], E.Vb.c(), o, po * v, po * v, 1, false, bits);
-  sl_pack_A(ex, E.sop[EE_VBC], E.Vb.c(), po * v, o, 1, po * v, true, bits);
+  SlMat *op = (bits == kSlicedBits) ? E.sop : E.sop24;
+  sl_pack_A(ex, op[EE_VAT], E.Va.c(), v, o * pv, 1, v, false, bits);
+  sl_pack_A(ex, op[EE_VAC], E.Va.c(), o * pv, v, v, 1, true, bits);
+  sl_pack_A(ex, op[EE_VB], E.Vb.c(), o, po * v, po * v, 1, false, bits);
+  sl_pack_A(ex, op[EE_VBC], E.Vb.c(), po * v, o, 1, po * v, true, bits);
   if (dd) {
-    sl_pack_A(ex, E.sop[EE_GVV], E.Gvv.c(), pv, pv, pv, 1, false, bits);
-    sl_pack_A(ex, E.sop[EE_GOO], E.Goo.c(), po, po, po, 1, false, bits);
-    sl_pack_A(ex, E.sop[EE_W], c->W.c(), ov, ov, ov, 1, false, bits);
+    sl_pack_A(ex, op[EE_GVV], E.Gvv.c(), pv, pv, pv, 1, false, bits);
+    sl_pack_A(ex, op[EE_GOO], E.Goo.c(), po, po, po, 1, false, bits);
+    sl_pack_A(ex, op[EE_W], c->W.c(), ov, ov, ov, 1, false, bits);
   }
   if (!E.tcerr.p) {
     E.tcerr = DBuf(ex, sizeof(int));
     fill_zero(ex, E.tcerr.p, sizeof(int));
   }
-  E.sl_dd = dd;
-  E.sl_ready = true;
+  if (bits == kSlicedBits) {
+    E.sl_dd = dd;
+    E.sl_ready = true;
+  } else {
+    E.sl24_ready = true;
+  }
 }
 
 // ee_struct_apply with the GEMMs over the doubles on the tensor cores, as the
@@ -474,7 +479,7 @@ static void ee_sl_build(adc_ctx *c, bool dd) {
 // indices and their updates of the gathered doubles run on the tensor cores
 // as well (the small products against V1, V2 stay FP64); with the sliced
 // product they go through zgemm, which the caller switches to the sliced route
-static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, double sdd, int nseg) {
+static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, double sdd, int nseg, int bits) {
   Exec &ex = c->ex;
   EEOps &E = *c->ee;
   const int64_t o = c->o, v = c->v, n1 = c->n1, N = c->N, po = npairs(o), pv = npairs(v), ov = o * v;
@@ -492,7 +497,7 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
                  int64_t b_k, int64_t M, cplx alpha, cplx beta, cplx *out, int64_t s_m, int64_t s_nh, int64_t s_nl,
                  int64_t n_in) {
     if (sliced) {
-      const SlMat &A = E.sop[op];
+      const SlMat &A = (bits == kSlicedBits) ? E.sop[op] : E.sop24[op];
       sl_pack_B(ex, E.sbx, src, Nc, K, b_nh, b_nl, b_in, b_k, false, A);
       sl_gemm(ex, A, E.sbx, M, Nc, alpha, beta, out, s_m, s_nh, s_nl, n_in, err, E.slw);
     } else {
@@ -590,7 +595,7 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
   ADC_CHECK_LAUNCH();
 }
 
-void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
+void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg, int bits) {
   Exec &ex = c->ex;
   EEOps &E = *c->ee;
   const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N;
@@ -600,7 +605,7 @@ void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
   const int planes = (nseg == 6) ? 3 : 2;
   ee_struct_build(c, sdd != 0.0);
   if (nseg == 0) {
-    if (!E.sl_ready) ee_sl_build(c, sdd != 0.0);
+    if (bits == kSlicedBits ? !E.sl_ready : !E.sl24_ready) ee_sl_build(c, sdd != 0.0, bits);
   } else if (!E.tc_ready || E.tc_planes < planes) {
     ee_tc_build(c, sdd != 0.0, planes);
   }
@@ -616,11 +621,11 @@ void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
   // the long (l, c<d) and ((k<l), d) indices) run as sliced products too; next
   // to the BF16 split they stay FP64 (measured: faster there)
   const int old_bits = ex.sliced_bits;
-  if (nseg == 0) ex.sliced_bits = 40;
+  if (nseg == 0) ex.sliced_bits = bits;
   try {
     for (int64_t z0 = 0; z0 < k; z0 += kc) {
       const int64_t kk = std::min(kc, k - z0);
-      ee_struct_apply_tc(c, X + z0 * N, S + z0 * N, kk, sdd, nseg);
+      ee_struct_apply_tc(c, X + z0 * N, S + z0 * N, kk, sdd, nseg, bits);
     }
   } catch (...) {
     ex.sliced_bits = old_bits;
@@ -644,7 +649,8 @@ void ee_prepare(adc_ctx *c, int planes, bool sliced) {
   const bool dd = third && c->dd_order == 1;
   ee_struct_build(c, dd);
   if (planes > 0 && (!E.tc_ready || E.tc_planes < planes)) ee_tc_build(c, dd, planes);
-  if (sliced && !E.sl_ready) ee_sl_build(c, dd);
+  if (sliced && !E.sl_ready) ee_sl_build(c, dd, kSlicedBits);
+  if (sliced && planes > 0 && !E.sl24_ready) ee_sl_build(c, dd, kSliced24Bits);
   // a mixed solve with sliced refinement reads only the split and sliced
   // copies of the packed <ab||cd>; above 4 GiB its FP64 copy makes room for
   // the subspace and is assembled again by the next FP64 product

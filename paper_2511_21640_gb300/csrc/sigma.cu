@@ -152,12 +152,13 @@ void sigma_fp64_share(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int64_t i0,
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision) {
   if (k <= 0) return;
   if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3 && precision != ADC_PREC_BF16X6 &&
-      precision != ADC_PREC_SLICED)
+      precision != ADC_PREC_SLICED && precision != ADC_PREC_SLICED24)
     throw Error(ADC_ERR_ARG, "unknown precision");
   const int nseg = (precision == ADC_PREC_BF16X6) ? 6 : 3;
-  if (precision == ADC_PREC_SLICED) {
-    if (c->kind == ADC_EE) sigma_ee_split(c, X, S, k, 0);  // nseg 0: sliced products
-    else sigma_sliced(c, X, S, k);
+  if (precision == ADC_PREC_SLICED || precision == ADC_PREC_SLICED24) {
+    const int bits = (precision == ADC_PREC_SLICED) ? kSlicedBits : kSliced24Bits;
+    if (c->kind == ADC_EE) sigma_ee_split(c, X, S, k, 0, bits);  // nseg 0: sliced products
+    else sigma_sliced(c, X, S, k, bits);
   } else if (c->kind == ADC_EE) {
     if (precision == ADC_PREC_FP64) sigma_ee_fp64(c, X, S, k);
     else sigma_ee_split(c, X, S, k, nseg);

@@ -29,6 +29,7 @@ static void build_cache(adc_ctx *c, int planes) {
 void release_tc(adc_ctx *c) {
   c->tc.reset();
   c->sl.reset();
+  c->sl24.reset();
 }
 
 void tc_ensure(adc_ctx *c, int planes) {
@@ -208,14 +209,13 @@ void sigma_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
 }
 
 // ---- FP64-accurate sigma: the same contractions as sliced tensor-core products
-constexpr int kSliceBits = 40;
-
-static void build_sl(adc_ctx *c) {
+// (bits = 40; 24 for the intermediate refinement step)
+static void build_sl(adc_ctx *c, std::unique_ptr<SlCache> &cache, int bits) {
   Exec &ex = c->ex;
-  c->sl.reset(new SlCache());
-  SlCache &sl = *c->sl;
+  cache.reset(new SlCache());
+  SlCache &sl = *cache;
   const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2;
-  sl.bits = kSliceBits;
+  sl.bits = bits;
   sl_pack_A(ex, sl.Cpl, c->Cpl.c(), n1, n2, n2, 1, false, sl.bits);
   sl_pack_A(ex, sl.CplT, c->Cpl.c(), n2, n1, 1, n2, true, sl.bits);
   if (c->order == 3 && c->x != 0.0) {
@@ -228,11 +228,12 @@ static void build_sl(adc_ctx *c) {
   sl.ready = true;
 }
 
-void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k) {
+void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int bits) {
   ADC_REQUIRE(c->kind != ADC_EE, ADC_ERR_ARG, "sigma_sliced: IP and EA (EE goes through sigma_ee_split)");
   Exec &ex = c->ex;
-  if (!c->sl || !c->sl->ready) build_sl(c);
-  SlCache &sl = *c->sl;
+  std::unique_ptr<SlCache> &cache = (bits == kSlicedBits) ? c->sl : c->sl24;
+  if (!cache || !cache->ready) build_sl(c, cache, bits);
+  SlCache &sl = *cache;
   int *err = (int *)sl.err.p;
   const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N;
   const bool sat = (c->order == 3 && c->x != 0.0);

@@ -55,6 +55,9 @@ def test_ee_sigma_diag_block(gpu, o, v, Q, order, x, dd, seed):
         assert _rel(Sm6, ref).max() < 1e-4, _rel(Sm6, ref).max()
         Ss = ctx.sigma(X, "sliced")
         assert _rel(Ss, ref).max() < 1e-10, _rel(Ss, ref).max()
+        # the intermediate step: digits for about 24 bits
+        Ss24 = ctx.sigma(X, "sliced24")
+        assert _rel(Ss24, ref).max() < 2e-6, _rel(Ss24, ref).max()
 
 
 @pytest.mark.parametrize("o,v,Q,x,dd,seed", [(4, 10, 14, 1.0, 0, 31), (3, 7, 11, 0.6, 1, 32)])

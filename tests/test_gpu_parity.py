@@ -135,6 +135,9 @@ def test_sigma_parity(gpu, kind, o, v, Q, order, x, seed):
         assert _rel(Sm6, ref).max() < 1e-4, _rel(Sm6, ref).max()
         Ss = ctx.sigma(X, "sliced")
         assert _rel(Ss, ref).max() < 1e-10, _rel(Ss, ref).max()
+        # the intermediate refinement step: digits for about 24 bits
+        Ss24 = ctx.sigma(X, "sliced24")
+        assert _rel(Ss24, ref).max() < 2e-6, _rel(Ss24, ref).max()
         d = ctx.diagonal()
         dref = oadc.diagonal_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, amp=amp)
         assert np.abs(d - dref).max() < 1e-12 * max(1.0, np.abs(dref).max())
