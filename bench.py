@@ -903,7 +903,9 @@ def main():
         t64 = time.perf_counter() - t1
         log(f"fp64 davidson {t64:.1f} s", st6)
         fp64 = {"s_per_root": t64 / nroots, "iterations": st6["iterations"], "sigma_calls": st6["sigma_calls"],
-                "max_eig_diff_vs_mixed": float(np.abs(om64 - om).max()), "rc": rc6}
+                "max_eig_diff_vs_mixed": float(np.abs(om64 - om).max()),
+                "eig_diff_vs_mixed": [float(d) for d in np.asarray(om) - np.asarray(om64)],
+                "err64": [float(e) for e in e6], "rc": rc6}
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -926,7 +928,10 @@ def main():
                "includes": "adc_init (H2D copy + operator setup) + adc_davidson",
                "setup": args.e2e_setup, "init_s": t3 - t2, "rc": int(rc2),
                "max_eig_diff_vs_" + ("fp64_davidson" if fp64 is not None else "timed_solve"):
-                   float(np.abs(np.asarray(om2) - np.asarray(ref_om)).max())}
+                   float(np.abs(np.asarray(om2) - np.asarray(ref_om)).max()),
+               "eig_diff": [float(d) for d in np.asarray(om2) - np.asarray(ref_om)],
+               "err64": [float(e) for e in e2], "sigma_calls": st2["sigma_calls"],
+               "sigma_calls_fp64": st2["sigma_calls_fp64"], "sigma_calls_mid": st2["sigma_calls_mid"]}
 
     cpu = None
     parity = None

@@ -97,8 +97,10 @@ int adc_diag_blockops(int which, int64_t m, int64_t nb, int64_t n, uint64_t seed
  * 1 = FP32 Jacobi start refined in FP64 (n <= 128, else
  * ADC_ERR_UNSUPPORTED). Eigenvalues ascending into w [n], eigenvectors as the
  * columns of V [n][n] (host). ms = CUDA-event time of one solve after a
- * warm-up (NULL allowed). Allocates and frees its own device memory. */
-int adc_diag_eigh(int which, const adc_c128 *A, int n, double *w, adc_c128 *V, double *ms);
+ * warm-up (NULL allowed); *steps (NULL allowed) = refinement steps taken, -1
+ * when the refinement handed the matrix to the FP64 Jacobi, 0 for which 0.
+ * Allocates and frees its own device memory. */
+int adc_diag_eigh(int which, const adc_c128 *A, int n, double *w, adc_c128 *V, double *ms, int *steps);
 
 /* FP64 FMA throughput of the device: every thread of a grid of `blocks`
  * blocks of 256 threads runs 16 independent fused multiply-add chains of

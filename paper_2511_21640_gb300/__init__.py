@@ -120,7 +120,7 @@ def _load():
         "adc_diag_blockops": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_diag_fp64_peak": (I, [I, I64, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_diag_set_wait_ns": (I, [ctypes.c_uint64]),
-        "adc_diag_eigh": (I, [I, P, I, P, P, ctypes.POINTER(D)]),
+        "adc_diag_eigh": (I, [I, P, I, P, P, ctypes.POINTER(D), ctypes.POINTER(I)]),
         "adc_sigma_adjoint": (I, [P, P, P, I64, P, P, P, ctypes.POINTER(D)]),
         "adc_state_density": (I, [P, P, P]),
         "adc_transition_density": (I, [P, P, I64, P]),
@@ -683,14 +683,17 @@ def diag_blockops(which, m, nb, n, seed=1, reps=3):
 
 def diag_eigh(which, A):
     """Small Hermitian eigensolver on the device (``adc_diag_eigh``; 0 FP64 Jacobi, 1 FP32 start + FP64
-    refinement): (w ascending, V with eigenvectors as columns, ms)."""
+    refinement): (w ascending, V with eigenvectors as columns, ms, refinement steps; -1 = the FP64 Jacobi
+    took over, 0 for which 0)."""
     A = np.ascontiguousarray(A, dtype=np.complex128)
     n = A.shape[0]
     w = np.empty(n, dtype=np.float64)
     V = np.empty((n, n), dtype=np.complex128)
     t = ctypes.c_double()
-    _check(lib.adc_diag_eigh(int(which), A.ctypes.data, n, w.ctypes.data, V.ctypes.data, ctypes.byref(t)))
-    return w, V, t.value
+    st = ctypes.c_int()
+    _check(lib.adc_diag_eigh(int(which), A.ctypes.data, n, w.ctypes.data, V.ctypes.data, ctypes.byref(t),
+                             ctypes.byref(st)))
+    return w, V, t.value, st.value
 
 
 def diag_fp64_peak(blocks, iters):

@@ -375,7 +375,7 @@ extern "C" int adc_diag_blockops(int which, int64_t m, int64_t nb, int64_t n, ui
   }
 }
 
-extern "C" int adc_diag_eigh(int which, const adc_c128 *A, int n, double *w, adc_c128 *V, double *ms) {
+extern "C" int adc_diag_eigh(int which, const adc_c128 *A, int n, double *w, adc_c128 *V, double *ms, int *steps) {
   if (which < 0 || which > 1 || n < 1 || !A || !w || !V) return ADC_ERR_ARG;
   if (which == 1 && !eigh_refined_fits(n)) return ADC_ERR_UNSUPPORTED;
   Exec ex;
@@ -403,6 +403,7 @@ extern "C" int adc_diag_eigh(int which, const adc_c128 *A, int n, double *w, adc
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       if (ms) *ms = t;
+      if (steps) *steps = (which == 1) ? eigh_refined_last_steps() : 0;
       ADC_CUDA(cudaMemcpyAsync(w, wd.p, n * sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
       ADC_CUDA(cudaMemcpyAsync(V, Vd.p, nn * sizeof(cplx), cudaMemcpyDeviceToHost, ex.stream));
       ADC_CUDA(cudaStreamSynchronize(ex.stream));

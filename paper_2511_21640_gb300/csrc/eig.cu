@@ -175,7 +175,7 @@ k_jacobi(cplx *Ag, int n, int ldag, cplx *Vg, double *w, cplx *Vout, int ldv, in
 // make F_ij + conj(F_ji) = R_ij exactly, so the update keeps X orthonormal to
 // second order whatever the gap. Columns are coupled when their gap is below
 // delta = 2 (||S - diag S||_F + max|lambda| ||R||_F) (the bound of the method),
-// below 1e-10 max|lambda| (gaps the FP64 products cannot resolve), or when the
+// below 1e-8 max|lambda| (gaps the FP64 products resolve too coarsely), or when the
 // first-order correction would exceed 1e-3 (its second-order error would not
 // be small); clusters are the connected components of the coupling. Each
 // cluster of at most CL_MAX columns is diagonalised exactly: the FP64 Jacobi
@@ -183,14 +183,19 @@ k_jacobi(cplx *Ag, int n, int ldag, cplx *Vg, double *w, cplx *Vout, int ldv, in
 // factor of its non-orthonormal basis) rotate its columns of I + F, and their
 // eigenvalues replace its lambda. The host repeats steps until the
 // corrections between clusters are below 1e-8 of the gaps (beyond the
-// rounding noise of S), at least nsteps and at most nsteps + 3; otherwise
-// (a cluster wider than CL_MAX, no convergence) the FP64 Jacobi solves the
-// matrix instead. The n^3 products run as small FP64 GEMMs over many SMs.
+// rounding noise of S) and the updated X is orthonormal to 1e-13, at least
+// nsteps and at most nsteps + 3; otherwise (a cluster wider than CL_MAX, no
+// convergence) the FP64 Jacobi solves the matrix instead. The n^3 products
+// run as small FP64 GEMMs over many SMs.
 
 constexpr int EIG_NMAX = 128;
 constexpr int CL_MAX = 8;
 constexpr double OA_ETA = 1e-3;   // largest first-order correction between separate clusters
-constexpr double OA_TAU = 1e-10;  // gaps below this fraction of max|lambda| always couple
+// gaps below this fraction of max|lambda| always couple: beyond it the rounding
+// of S (about eps |lambda|) gives first-order corrections below 1e-8, whose
+// squares stay below the rounding of an orthonormal basis
+constexpr double OA_TAU = 1e-8;
+constexpr double OA_ORTH = 1e-13;  // largest |X^H X - I| of an accepted decomposition
 
 __device__ inline float2 f2mul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
@@ -623,6 +628,19 @@ __global__ void k_sort_out(const double *lam, const double *shift, const cplx *X
   }
 }
 
+// *out = max |H - I| (H n x n)
+__global__ void k_orth_err(const cplx *__restrict__ H, int n, double *out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx % n;
+    const cplx h = H[idx];
+    m = fmax(m, fmax(fabs(h.x - (i == j ? 1.0 : 0.0)), fabs(h.y)));
+  }
+  m = block_max(m, red);
+  if (threadIdx.x == 0) *out = m;
+}
+
 __global__ void k_copy_square(const cplx *__restrict__ A, int n, int lda, cplx *B) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * n;
        idx += (int64_t)gridDim.x * blockDim.x)
@@ -632,6 +650,12 @@ __global__ void k_copy_square(const cplx *__restrict__ A, int n, int lda, cplx *
 constexpr size_t kJacobi32Smem = 200 * 1024;
 
 }  // namespace
+
+namespace {
+thread_local int last_steps_ = 0;
+}
+
+int eigh_refined_last_steps() { return last_steps_; }
 
 bool eigh_refined_fits(int n) { return n >= 1 && n <= EIG_NMAX; }
 
@@ -671,10 +695,16 @@ void eigh_refined(Exec &ex, const cplx *A, int n, int lda, double *w, cplx *V, i
     ADC_CHECK_LAUNCH();
     std::swap(X, Xn);
     if (it + 1 >= nsteps) {
-      double st[2];
+      // orthonormality of the updated vectors
+      k_small_gemm<<<g, SG_T * SG_T, gs, ex.stream>>>(X, n, 1, nullptr, X, n, n, nullptr, H.c(), n);
+      ADC_CHECK_LAUNCH();
+      k_orth_err<<<1, 1024, 0, ex.stream>>>(H.c(), n, sc.d() + 3);
+      ADC_CHECK_LAUNCH();
+      double st[3];
       ADC_CUDA(cudaMemcpyAsync(st, sc.d() + 1, sizeof(st), cudaMemcpyDeviceToHost, ex.stream));
       ADC_CUDA(cudaStreamSynchronize(ex.stream));
-      if (st[0] <= 1e-8 && st[1] == 0.0) { ok = true; break; }
+      last_steps_ = it + 1;
+      if (st[0] <= 1e-8 && st[1] == 0.0 && st[2] <= OA_ORTH) { ok = true; break; }
     }
   }
   if (ok) {
@@ -684,6 +714,7 @@ void eigh_refined(Exec &ex, const cplx *A, int n, int lda, double *w, cplx *V, i
     ADC_CHECK_LAUNCH();
     return;
   }
+  last_steps_ = -1;
   // a cluster too wide for the exact step, or no convergence: FP64 Jacobi
   k_copy_square<<<(int)std::min<int64_t>((nn + 255) / 256, 1024), 256, 0, ex.stream>>>(A, n, lda, T.c());
   ADC_CHECK_LAUNCH();

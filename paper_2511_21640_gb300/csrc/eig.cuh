@@ -12,4 +12,6 @@ void jacobi_eigh(Exec &ex, cplx *A, int n, int lda, double *w, cplx *V, int ldv,
 // A is not changed.
 bool eigh_refined_fits(int n);
 void eigh_refined(Exec &ex, const cplx *A, int n, int lda, double *w, cplx *V, int ldv, int nsteps = 3);
+// refinement steps of this thread's last eigh_refined call, -1 when it took the FP64 Jacobi
+int eigh_refined_last_steps();
 }  // namespace adc

@@ -102,7 +102,7 @@ def test_batched_davidson_matches_dense(gpu):
         pcs.append(gpu.Context(p.B, p.eps_occ, p.eps_vir, kind=kind, order=order, x=x))
     with gpu.Batch(pcs) as b:
         om, e64, status, st, rc = b.davidson(4, tol=1e-7, precision="bf16x3")
-        assert rc == 0 and np.all(status == 0)
+        assert rc == 0 and np.all(status == 0), (status, e64, st)
         for i, w in enumerate(dense):
             assert np.abs(om[i] - w).max() < 1e-8
             assert np.all(e64[i] <= 1e-7)

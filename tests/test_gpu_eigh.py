@@ -51,8 +51,10 @@ def _check(A, w, V, orth=1e-13):
 @pytest.mark.parametrize("n", [1, 2, 3, 8, 17, 33, 64, 100, 128])
 def test_eigh_random(gpu, which, n):
     A = _hermitian(n, seed=70 + n)
-    w, V, ms = gpu.diag_eigh(which, A)
+    w, V, ms, steps = gpu.diag_eigh(which, A)
     _check(A, w, V)
+    if which == 1:
+        assert steps >= 3, steps   # refined, no fallback on spectra without wide clusters
 
 
 def _spectra():
@@ -75,14 +77,17 @@ def _spectra():
 def test_eigh_degenerate_and_close(gpu, which, case):
     _, lam, seed = next(c for c in _spectra() if c[0] == case)
     A = _hermitian(lam.size, seed=seed, spectrum=lam)
-    w, V, ms = gpu.diag_eigh(which, A)
+    w, V, ms, steps = gpu.diag_eigh(which, A)
     _check(A, w, V)
+    if which == 1:
+        # only the ten-fold eigenvalue needs the FP64 Jacobi
+        assert (steps == -1) == (case == "tenfold"), steps
 
 
 def test_eigh_refined_is_faster(gpu):
     """At the Davidson's usual subspace size the refined solver beats the FP64 Jacobi."""
     A = _hermitian(64, seed=90)
-    _, _, t0 = gpu.diag_eigh(0, A)
-    _, _, t1 = gpu.diag_eigh(1, A)
+    _, _, t0, _ = gpu.diag_eigh(0, A)
+    _, _, t1, _ = gpu.diag_eigh(1, A)
     print(f"n = 64: FP64 Jacobi {t0:.3f} ms, FP32 start + FP64 refinement {t1:.3f} ms")
     assert t1 < t0
