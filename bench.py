@@ -111,9 +111,9 @@ class Clocks:
 
 
 THREE_M = ("zgemm", "gram", "combine")
-# k_gram<32, 8, 4, 2, 32> on 32 x 8 vectors of n = 796200 (one launch, ncu): 510,484,736 B read +
-# 4,910,080 B written against (32 + 8) * 796200 * 16 + 32 * 8 * 16 = 509,572,096 algorithmic bytes
-GRAM_DRAM_RATIO = (510484736 + 4910080) / ((32 + 8) * 796200 * 16 + 32 * 8 * 16)  # FP64 kernels whose complex products take 3 real products
+# k_gram<32, 8, 4, 2, 32> on 32 x 8 vectors of n = 796200 (one launch, ncu): 510,109,184 B read +
+# 4,893,696 B written against (32 + 8) * 796200 * 16 + 32 * 8 * 16 = 509,572,096 algorithmic bytes
+GRAM_DRAM_RATIO = (510109184 + 4893696) / ((32 + 8) * 796200 * 16 + 32 * 8 * 16)  # FP64 kernels whose complex products take 3 real products
 
 
 def fp64_peak(adcgpu):
