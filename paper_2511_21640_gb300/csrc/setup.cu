@@ -434,10 +434,20 @@ void setup_operators(adc_ctx *c) {
       permute(ex, oovo.c(), {o, o, o, v}, {1, o * v, o * o * v, o}, false, T.c(), C1(), C0());
     }
     if (third && x != 0.0) {
-      // + x/2 sum_ef <ef||ak> conj(t_ji^ef) = x sum_ef (ea|fk) conj(t_ji^ef)
-      DBuf J = cbuf(ex, v * o * v * v);
-      einsum(ex, C1(), Bvv, "Qea", Bvo, "Qfk", C0(), dense(J, {v, o, v, v}), "akef");
-      einsum(ex, CR(x), dense(J, {v, o, v, v}), "akef", t1.cj(), "jief", C1(), Tt, "kija");
+      // + x/2 sum_ef <ef||ak> conj(t_ji^ef) = x sum_ef (ea|fk) conj(t_ji^ef), in chunks of the
+      // virtual index a whose (ea|fk) block stays within about 4 GiB:
+      // J[a][e][k][f] = sum_Q B_ea B_fk, Tc[a][k][j][i] = sum_ef J[a][e][k][f] conj(t_ji^ef)
+      const int64_t ca = std::max<int64_t>(1, std::min<int64_t>(v, (1ll << 28) / (o * v * v)));
+      DBuf J = cbuf(ex, ca * v * o * v), Tc = cbuf(ex, ca * o * o * o);
+      for (int64_t a0 = 0; a0 < v; a0 += ca) {
+        const int64_t na = std::min(ca, v - a0);
+        TV Bea(Bvv.p + a0, {Q, v, na}, {Bvv.str[0], Bvv.str[1], 1});
+        einsum(ex, C1(), Bea, "Qea", Bvo, "Qfk", C0(), dense(J, {na, v, o, v}), "aekf");
+        einsum(ex, C1(), dense(J, {na, v, o, v}), "aekf", t1.cj(), "jief", C0(), dense(Tc, {na, o, o, o}), "akji");
+        // T[k][i][j][a0 + a] += x Tc[a][k][j][i]
+        permute(ex, Tc.c(), {o, o, o, na}, {o * o, 1, o, o * o * o}, false, T.c() + a0,
+                {o * o * v, o * v, v, 1}, CR(x), C1());
+      }
     }
     pair_pack(ex, T.c(), 0, o * o * v, o * v, v, 1, 0.0, 1, o, o, v, c->Cpl.c(), 0, po * v, C1(), C0());
     if (third && x != 0.0) {

@@ -25,7 +25,10 @@ void *Exec::alloc(size_t bytes) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     throw Error(e == cudaErrorMemoryAllocation ? ADC_ERR_OOM : ADC_ERR_CUDA,
-                std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+                std::string("cudaMallocAsync(") + std::to_string(bytes) + "): " + cudaGetErrorString(e) +
+                    " (" + std::to_string(mem_used) + " bytes held by the context" +
+                    (stage.empty() ? std::string() : ", in " + stage) + (tag.empty() ? std::string() : "/" + tag) +
+                    ")");
   }
   mem_used += (int64_t)bytes;
   mem_peak = std::max(mem_peak, mem_used);
@@ -372,32 +375,56 @@ namespace {
 constexpr int MAXD = 8;
 struct PermArgs {
   int nd;
+  int strided_dst;  // 0: dst contiguous in ext order; 1: dst at strides dstr
   int64_t ext[MAXD];
   int64_t sstr[MAXD];
+  int64_t dstr[MAXD];
 };
 
 __global__ void k_permute(const cplx *__restrict__ src, PermArgs pa, int conj, cplx *dst,
                           cplx alpha, cplx beta, int use_beta, int64_t total) {
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t rem = idx, off = 0;
+    int64_t rem = idx, off = 0, doff = 0;
     for (int d = pa.nd - 1; d >= 0; --d) {
       int64_t i = rem % pa.ext[d];
       rem /= pa.ext[d];
       off += i * pa.sstr[d];
+      doff += i * pa.dstr[d];
     }
+    if (!pa.strided_dst) doff = idx;
     cplx v = src[off];
     if (conj) v.y = -v.y;
     cplx r = cmul(alpha, v);
-    if (use_beta) r = cadd(r, cmul(beta, dst[idx]));
-    dst[idx] = r;
+    if (use_beta) r = cadd(r, cmul(beta, dst[doff]));
+    dst[doff] = r;
   }
 }
 }  // namespace
 
+void permute(Exec &ex, const cplx *src, const std::vector<int64_t> &ext, const std::vector<int64_t> &sstr,
+             bool conj, cplx *dst, const std::vector<int64_t> &dstr, cplx alpha, cplx beta) {
+  PermArgs pa{};
+  ADC_REQUIRE(ext.size() <= (size_t)MAXD && ext.size() == sstr.size() && ext.size() == dstr.size(), ADC_ERR_ARG,
+              "permute: rank");
+  pa.nd = (int)ext.size();
+  pa.strided_dst = 1;
+  int64_t total = 1;
+  for (int d = 0; d < pa.nd; ++d) {
+    pa.ext[d] = ext[d];
+    pa.sstr[d] = sstr[d];
+    pa.dstr[d] = dstr[d];
+    total *= ext[d];
+  }
+  if (total == 0) return;
+  const int use_beta = (beta.x != 0.0 || beta.y != 0.0) ? 1 : 0;
+  k_permute<<<grid1d(total, 256), 256, 0, ex.stream>>>(src, pa, conj ? 1 : 0, dst, alpha, beta, use_beta, total);
+  ADC_CHECK_LAUNCH();
+}
+
 void permute(Exec &ex, const cplx *src, const std::vector<int64_t> &ext,
              const std::vector<int64_t> &sstr, bool conj, cplx *dst, cplx alpha, cplx beta) {
-  PermArgs pa;
+  PermArgs pa{};
   ADC_REQUIRE(ext.size() <= (size_t)MAXD && ext.size() == sstr.size(), ADC_ERR_ARG, "permute: rank");
   pa.nd = (int)ext.size();
   int64_t total = 1;

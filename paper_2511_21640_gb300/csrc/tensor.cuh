@@ -33,6 +33,7 @@ struct Exec {
   // per-kernel timing with CUDA events on this stream (off unless enabled)
   bool prof = false;
   std::string tag;
+  std::string stage;  // step of a longer procedure in progress (StageScope), for error messages
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> event_pool;
   cudaEvent_t event();
@@ -84,11 +85,13 @@ struct StageScope {
 
  private:
   void begin(const char *name) {
+    ex.stage = name;
     rec = ex.prof ? ex.prof_begin((std::string("stage:") + name).c_str(), 0.0) : -1;
   }
   void end() {
     if (rec >= 0 && rec < (int)ex.recs.size()) cudaEventRecord(ex.recs[rec].b, ex.stream);
     rec = -1;
+    ex.stage.clear();
   }
 };
 
@@ -138,6 +141,9 @@ void zgemm_ws(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alp
 // dst (contiguous, extents ext) = alpha * op(src at strides sstr) + beta * dst
 void permute(Exec &ex, const cplx *src, const std::vector<int64_t> &ext,
              const std::vector<int64_t> &sstr, bool conj, cplx *dst, cplx alpha, cplx beta);
+// the same with dst at strides dstr
+void permute(Exec &ex, const cplx *src, const std::vector<int64_t> &ext, const std::vector<int64_t> &sstr,
+             bool conj, cplx *dst, const std::vector<int64_t> &dstr, cplx alpha, cplx beta);
 
 // T[o][p][q][in] (contiguous) from packed P: P addr = o1*sP1 + o0*sP0 + pair*inner + in,
 // o = o1*no0 + o0. Antisymmetric fill, zero diagonal.
