@@ -250,8 +250,11 @@ k_jacobi32(const cplx *__restrict__ Ag, int n, int lda, cplx *X, double *shift, 
   float *rc = smf, *rs = rc + npairs, *rpr = rs + npairs, *rpi = rpr + npairs;
   int *pp = (int *)(rpi + npairs), *pq = pp + npairs;
   float *red = (float *)(pq + npairs);
+  // rows padded to n + 1 elements: the column rotations walk down a column
+  // with consecutive lanes on consecutive rows, free of bank conflicts
+  const int ld = n + 1;
   float2 *A = (float2 *)(((uintptr_t)(red + 64) + 15) & ~(uintptr_t)15);
-  float2 *V = Vg ? Vg : A + n * n;
+  float2 *V = Vg ? Vg : A + n * ld;
   __shared__ double dred[32];
   const int tid = threadIdx.x, nt = blockDim.x;
   // shift by the mean diagonal (FP64), then round
@@ -270,12 +273,15 @@ k_jacobi32(const cplx *__restrict__ Ag, int n, int lda, cplx *X, double *shift, 
   for (int idx = tid; idx < n * n; idx += nt) {
     const int r = idx / n, c = idx % n;
     const cplx a = Ag[(int64_t)r * lda + c];
-    A[idx] = make_float2((float)(a.x - (r == c ? sigma : 0.0)), (float)a.y);
-    V[idx] = make_float2(r == c ? 1.f : 0.f, 0.f);
+    A[r * ld + c] = make_float2((float)(a.x - (r == c ? sigma : 0.0)), (float)a.y);
+    V[r * ld + c] = make_float2(r == c ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
   float loc = 0.f;
-  for (int idx = tid; idx < n * n; idx += nt) loc += A[idx].x * A[idx].x + A[idx].y * A[idx].y;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const float2 a = A[(idx / n) * ld + idx % n];
+    loc += a.x * a.x + a.y * a.y;
+  }
   const float fro2 = block_sum_f(loc, red);
   bool done = (n <= 1);
   float prev = 3.0e38f;
@@ -290,8 +296,8 @@ k_jacobi32(const cplx *__restrict__ Ag, int n, int lda, cplx *X, double *shift, 
         pq[k] = q;
         float cs = 1.f, sn = 0.f, er = 1.f, ei = 0.f;
         if (q < n) {
-          const float app = A[p * n + p].x, aqq = A[q * n + q].x;
-          const float2 apq = A[p * n + q];
+          const float app = A[p * ld + p].x, aqq = A[q * ld + q].x;
+          const float2 apq = A[p * ld + q];
           const float mag = sqrtf(apq.x * apq.x + apq.y * apq.y);
           if (mag > 1e-30f) {
             er = apq.x / mag;
@@ -310,9 +316,9 @@ k_jacobi32(const cplx *__restrict__ Ag, int n, int lda, cplx *X, double *shift, 
         const int p = pp[k], q = pq[k];
         if (q >= n) continue;
         const float cs = rc[k], sn = rs[k];
-        const float2 ap = A[p * n + col], eaq = f2mul(make_float2(rpr[k], rpi[k]), A[q * n + col]);
-        A[p * n + col] = make_float2(cs * ap.x - sn * eaq.x, cs * ap.y - sn * eaq.y);
-        A[q * n + col] = make_float2(sn * ap.x + cs * eaq.x, sn * ap.y + cs * eaq.y);
+        const float2 ap = A[p * ld + col], eaq = f2mul(make_float2(rpr[k], rpi[k]), A[q * ld + col]);
+        A[p * ld + col] = make_float2(cs * ap.x - sn * eaq.x, cs * ap.y - sn * eaq.y);
+        A[q * ld + col] = make_float2(sn * ap.x + cs * eaq.x, sn * ap.y + cs * eaq.y);
       }
       __syncthreads();
       for (int idx = tid; idx < npairs * n * 2; idx += nt) {
@@ -322,15 +328,17 @@ k_jacobi32(const cplx *__restrict__ Ag, int n, int lda, cplx *X, double *shift, 
         if (q >= n) continue;
         const float cs = rc[k], sn = rs[k];
         float2 *M = which ? V : A;
-        const float2 xp = M[row * n + p], exq = f2mul(make_float2(rpr[k], -rpi[k]), M[row * n + q]);
-        M[row * n + p] = make_float2(cs * xp.x - sn * exq.x, cs * xp.y - sn * exq.y);
-        M[row * n + q] = make_float2(sn * xp.x + cs * exq.x, sn * xp.y + cs * exq.y);
+        const float2 xp = M[row * ld + p], exq = f2mul(make_float2(rpr[k], -rpi[k]), M[row * ld + q]);
+        M[row * ld + p] = make_float2(cs * xp.x - sn * exq.x, cs * xp.y - sn * exq.y);
+        M[row * ld + q] = make_float2(sn * xp.x + cs * exq.x, sn * xp.y + cs * exq.y);
       }
       __syncthreads();
     }
     float off = 0.f;
-    for (int idx = tid; idx < n * n; idx += nt)
-      if (idx / n != idx % n) off += A[idx].x * A[idx].x + A[idx].y * A[idx].y;
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int r = idx / n, c = idx % n;
+      if (r != c) off += A[r * ld + c].x * A[r * ld + c].x + A[r * ld + c].y * A[r * ld + c].y;
+    }
     off = block_sum_f(off, red);
     // converged, or at the FP32 rounding floor (the off-diagonal norm no longer drops)
     done = (off <= 1e-13f * fro2) || (off == 0.f) || (off <= 1e-9f * fro2 && sweep >= 1 && off > 0.25f * prev);
@@ -338,13 +346,13 @@ k_jacobi32(const cplx *__restrict__ Ag, int n, int lda, cplx *X, double *shift, 
   }
   // columns sorted by ascending eigenvalue, promoted to FP64
   for (int i = tid; i < n; i += nt) {
-    const float di = A[i * n + i].x;
+    const float di = A[i * ld + i].x;
     int rank = 0;
     for (int j = 0; j < n; ++j) {
-      const float dj = A[j * n + j].x;
+      const float dj = A[j * ld + j].x;
       if (dj < di || (dj == di && j < i)) ++rank;
     }
-    for (int r = 0; r < n; ++r) X[(int64_t)r * n + rank] = cmake((double)V[r * n + i].x, (double)V[r * n + i].y);
+    for (int r = 0; r < n; ++r) X[(int64_t)r * n + rank] = cmake((double)V[r * ld + i].x, (double)V[r * ld + i].y);
   }
   if (tid == 0) *shift = sigma;
 }
@@ -663,11 +671,12 @@ void eigh_refined(Exec &ex, const cplx *A, int n, int lda, double *w, cplx *V, i
   if (n <= 0) return;
   ADC_REQUIRE(eigh_refined_fits(n), ADC_ERR_UNSUPPORTED, "eigh_refined: matrix too large");
   const int64_t nn = (int64_t)n * n;
-  // the FP32 eigenvector work array in shared memory when both matrices fit
-  size_t smem = jacobi32_head_bytes(n) + (size_t)nn * sizeof(float2);
+  // the FP32 eigenvector work array in shared memory when both (padded) matrices fit
+  const size_t mat = (size_t)n * (n + 1) * sizeof(float2);
+  size_t smem = jacobi32_head_bytes(n) + mat;
   DBuf vg;
-  if (smem + (size_t)nn * sizeof(float2) <= kJacobi32Smem) smem += (size_t)nn * sizeof(float2);
-  else vg = DBuf(ex, (size_t)nn * sizeof(float2));
+  if (smem + mat <= kJacobi32Smem) smem += mat;
+  else vg = DBuf(ex, mat);
   set_smem_limit((const void *)k_jacobi32, (int)kJacobi32Smem);
   set_smem_limit((const void *)k_small_gemm, 64 * 1024);
   DBuf X0 = cbuf(ex, nn), X1 = cbuf(ex, nn), T = cbuf(ex, nn), H = cbuf(ex, nn), S = cbuf(ex, nn), F = cbuf(ex, nn);
