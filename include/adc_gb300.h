@@ -72,9 +72,10 @@ enum { ADC_IP = 0, ADC_EA = 1, ADC_EE = 2 };
  *   relative to the largest output). Used for the refinement products of the
  *   mixed Davidson when opts.refine selects it.
  * ADC_PREC_SLICED24: the same sliced product with digits for about 24
- *   significant bits (about 1e-7 relative to the largest output) at roughly
- *   a third of its digit products: the intermediate step of that refinement,
- *   for the correction vectors once the BF16x3 products stall. */
+ *   significant bits (about 1e-7 relative to the largest output): the trial
+ *   vectors' leading digits against the same leading digit slices of the
+ *   operators, about 40% of the digit products. The intermediate step of that
+ *   refinement, for the correction vectors once the BF16x3 products stall. */
 enum { ADC_PREC_FP64 = 0, ADC_PREC_BF16X3 = 1, ADC_PREC_BF16X6 = 2, ADC_PREC_SLICED = 3, ADC_PREC_SLICED24 = 4 };
 
 enum {

@@ -46,7 +46,7 @@ struct adc_ctx {
   // split-precision copies for the tensor-core sigma
   std::unique_ptr<adc::TcCache> tc;
   // integer-digit slices for the FP64-accurate tensor-core sigma
-  std::unique_ptr<adc::SlCache> sl, sl24;  // sliced operator copies (40 and 24 bits)
+  std::unique_ptr<adc::SlCache> sl;
 
   // EE-ADC operators (kind == ADC_EE)
   std::unique_ptr<adc::EEOps> ee;

@@ -34,10 +34,9 @@ struct EEOps {
   int tc_planes = 0;
   // sliced copies (FP64-accurate products), indexed by EE_VAT .. EE_W, and the per-call B operand
   SlMat sop[EE_NOPS];
-  SlMat sop24[EE_NOPS];  // the same with about 24 bits (intermediate refinement step)
   SlMat sbx;
   SlWork slw;
-  bool sl_ready = false, sl_dd = false, sl24_ready = false;
+  bool sl_ready = false, sl_dd = false;
 };
 // numerators of the second-order doubles and singles (second_order_amplitudes in
 // setup.cu) as term tables: t2_ij^ab D_ij^ab and t2_i^a (eps_i - eps_a)

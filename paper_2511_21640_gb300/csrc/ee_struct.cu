@@ -444,13 +444,14 @@ static void ee_tc_build(adc_ctx *c, bool dd, int planes) {
   E.tc_ready = true;
 }
 
-// sliced copies of the same operators (FP64-accurate tensor-core products with
-// kSlicedBits, or kSliced24Bits for the intermediate refinement step)
-static void ee_sl_build(adc_ctx *c, bool dd, int bits) {
+// sliced copies of the same operators (FP64-accurate tensor-core products);
+// products with fewer bits use their leading slices
+static void ee_sl_build(adc_ctx *c, bool dd) {
   Exec &ex = c->ex;
   EEOps &E = *c->ee;
   const int64_t o = c->o, v = c->v, po = npairs(o), pv = npairs(v), ov = o * v;
-  SlMat *op = (bits == kSlicedBits) ? E.sop : E.sop24;
+  constexpr int bits = kSlicedBits;
+  SlMat *op = E.sop;
   sl_pack_A(ex, op[EE_VAT], E.Va.c(), v, o * pv, 1, v, false, bits);
   sl_pack_A(ex, op[EE_VAC], E.Va.c(), o * pv, v, v, 1, true, bits);
   sl_pack_A(ex, op[EE_VB], E.Vb.c(), o, po * v, po * v, 1, false, bits);
@@ -464,12 +465,8 @@ static void ee_sl_build(adc_ctx *c, bool dd, int bits) {
     E.tcerr = DBuf(ex, sizeof(int));
     fill_zero(ex, E.tcerr.p, sizeof(int));
   }
-  if (bits == kSlicedBits) {
-    E.sl_dd = dd;
-    E.sl_ready = true;
-  } else {
-    E.sl24_ready = true;
-  }
+  E.sl_dd = dd;
+  E.sl_ready = true;
 }
 
 // ee_struct_apply with the GEMMs over the doubles on the tensor cores, as the
@@ -497,8 +494,8 @@ static void ee_struct_apply_tc(adc_ctx *c, const cplx *X, cplx *S, int64_t kc, d
                  int64_t b_k, int64_t M, cplx alpha, cplx beta, cplx *out, int64_t s_m, int64_t s_nh, int64_t s_nl,
                  int64_t n_in) {
     if (sliced) {
-      const SlMat &A = (bits == kSlicedBits) ? E.sop[op] : E.sop24[op];
-      sl_pack_B(ex, E.sbx, src, Nc, K, b_nh, b_nl, b_in, b_k, false, A);
+      const SlMat &A = E.sop[op];
+      sl_pack_B(ex, E.sbx, src, Nc, K, b_nh, b_nl, b_in, b_k, false, A, bits);
       sl_gemm(ex, A, E.sbx, M, Nc, alpha, beta, out, s_m, s_nh, s_nl, n_in, err, E.slw);
     } else {
       tc_pack_B(ex, E.bx, src, Nc, K, b_nh, b_nl, b_in, b_k, false, planes);
@@ -605,7 +602,7 @@ void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg, int
   const int planes = (nseg == 6) ? 3 : 2;
   ee_struct_build(c, sdd != 0.0);
   if (nseg == 0) {
-    if (bits == kSlicedBits ? !E.sl_ready : !E.sl24_ready) ee_sl_build(c, sdd != 0.0, bits);
+    if (!E.sl_ready) ee_sl_build(c, sdd != 0.0);
   } else if (!E.tc_ready || E.tc_planes < planes) {
     ee_tc_build(c, sdd != 0.0, planes);
   }
@@ -649,8 +646,7 @@ void ee_prepare(adc_ctx *c, int planes, bool sliced) {
   const bool dd = third && c->dd_order == 1;
   ee_struct_build(c, dd);
   if (planes > 0 && (!E.tc_ready || E.tc_planes < planes)) ee_tc_build(c, dd, planes);
-  if (sliced && !E.sl_ready) ee_sl_build(c, dd, kSlicedBits);
-  if (sliced && planes > 0 && !E.sl24_ready) ee_sl_build(c, dd, kSliced24Bits);
+  if (sliced && !E.sl_ready) ee_sl_build(c, dd);
   // a mixed solve with sliced refinement reads only the split and sliced
   // copies of the packed <ab||cd>; above 4 GiB its FP64 copy makes room for
   // the subspace and is assembled again by the next FP64 product

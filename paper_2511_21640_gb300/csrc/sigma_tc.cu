@@ -29,7 +29,6 @@ static void build_cache(adc_ctx *c, int planes) {
 void release_tc(adc_ctx *c) {
   c->tc.reset();
   c->sl.reset();
-  c->sl24.reset();
 }
 
 void tc_ensure(adc_ctx *c, int planes) {
@@ -208,14 +207,16 @@ void sigma_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg) {
   }
 }
 
-// ---- FP64-accurate sigma: the same contractions as sliced tensor-core products
-// (bits = 40; 24 for the intermediate refinement step)
-static void build_sl(adc_ctx *c, std::unique_ptr<SlCache> &cache, int bits) {
+// ---- FP64-accurate sigma: the same contractions as sliced tensor-core products.
+// The operators are sliced once for kSlicedBits; a product with fewer bits
+// (the intermediate refinement step) slices only the leading digits of the
+// trial vectors and pairs them with the same leading slices of the operators.
+static void build_sl(adc_ctx *c) {
   Exec &ex = c->ex;
-  cache.reset(new SlCache());
-  SlCache &sl = *cache;
+  c->sl.reset(new SlCache());
+  SlCache &sl = *c->sl;
   const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2;
-  sl.bits = bits;
+  sl.bits = kSlicedBits;
   sl_pack_A(ex, sl.Cpl, c->Cpl.c(), n1, n2, n2, 1, false, sl.bits);
   sl_pack_A(ex, sl.CplT, c->Cpl.c(), n2, n1, 1, n2, true, sl.bits);
   if (c->order == 3 && c->x != 0.0) {
@@ -231,9 +232,8 @@ static void build_sl(adc_ctx *c, std::unique_ptr<SlCache> &cache, int bits) {
 void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int bits) {
   ADC_REQUIRE(c->kind != ADC_EE, ADC_ERR_ARG, "sigma_sliced: IP and EA (EE goes through sigma_ee_split)");
   Exec &ex = c->ex;
-  std::unique_ptr<SlCache> &cache = (bits == kSlicedBits) ? c->sl : c->sl24;
-  if (!cache || !cache->ready) build_sl(c, cache, bits);
-  SlCache &sl = *cache;
+  if (!c->sl || !c->sl->ready) build_sl(c);
+  SlCache &sl = *c->sl;
   int *err = (int *)sl.err.p;
   const int64_t o = c->o, v = c->v, n1 = c->n1, n2 = c->n2, N = c->N;
   const bool sat = (c->order == 3 && c->x != 0.0);
@@ -243,9 +243,9 @@ void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int bits) {
   zgemm(ex, k, n1, n1, 1, C1(), X, 0, N, 1, false, c->M11.c(), 0, 1, n1, false, C0(), S, 0, N, 1);
   // S1 += Cpl X2, S2 = Cpl^H X1
   ex.tag = "coupling";
-  sl_pack_B(ex, sl.Bx, X + n1, k, n2, N, 0, 1, 1, false, sl.Cpl);
+  sl_pack_B(ex, sl.Bx, X + n1, k, n2, N, 0, 1, 1, false, sl.Cpl, bits);
   sl_gemm(ex, sl.Cpl, sl.Bx, n1, k, C1(), C1(), S, 1, N, 0, 1, err, sl.w);
-  sl_pack_B(ex, sl.Bx, X, k, n1, N, 0, 1, 1, false, sl.CplT);
+  sl_pack_B(ex, sl.Bx, X, k, n1, N, 0, 1, 1, false, sl.CplT, bits);
   sl_gemm(ex, sl.CplT, sl.Bx, n2, k, C1(), C0(), S + n1, 1, N, 0, 1, err, sl.w);
   diag_mul_add(ex, k, n2, c->d2.d(), X + n1, N, S + n1, N, 1.0);
   if (sat) {
@@ -255,22 +255,22 @@ void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int bits) {
       if (c->direct_ladder) {
         ladder_direct(c, X + n1, N, o, S + n1, N, k, x, ADC_LADDER_SLICED, err);
       } else {
-        sl_pack_B(ex, sl.Bx, X + n1, k * o, pv, N, pv, o, 1, false, sl.Glad);
+        sl_pack_B(ex, sl.Bx, X + n1, k * o, pv, N, pv, o, 1, false, sl.Glad, bits);
         sl_gemm(ex, sl.Glad, sl.Bx, pv, k * o, CR(x), C1(), S + n1, 1, N, pv, o, err, sl.w);
       }
       ex.tag = "ring";
       cplx *T = scratch(c, k * o * v * v);
-      sl_pack_B_ring(ex, sl.Bx, c, X, k, sl.W);
+      sl_pack_B_ring(ex, sl.Bx, c, X, k, sl.W, bits);
       sl_gemm(ex, sl.W, sl.Bx, o * v, k * v, C1(), C0(), T, v, o * v * v, 1, v, err, sl.w);
       pair_pack(ex, T, o * v * v, v * v, v, 1, 0, 1.0, k, o, v, 1, S + n1, N, pv, CR(-x), C1());
     } else {
       const int64_t po = npairs(o);
       ex.tag = "ladder";
-      sl_pack_B(ex, sl.Bx, X + n1, k * v, po, N, 1, v, v, false, sl.Glad);
+      sl_pack_B(ex, sl.Bx, X + n1, k * v, po, N, 1, v, v, false, sl.Glad, bits);
       sl_gemm(ex, sl.Glad, sl.Bx, po, k * v, CR(x), C1(), S + n1, v, N, 1, v, err, sl.w);
       ex.tag = "ring";
       cplx *T = scratch(c, k * o * v * o);
-      sl_pack_B_ring(ex, sl.Bx, c, X, k, sl.W);
+      sl_pack_B_ring(ex, sl.Bx, c, X, k, sl.W, bits);
       sl_gemm(ex, sl.W, sl.Bx, o * v, k * o, CR(-1.0), C0(), T, o, o * v * o, 1, o, err, sl.w);
       pair_pack(ex, T, o * v * o, 0, 1, v * o, o, 1.0, k, 1, o, v, S + n1, N, 0, CR(x), C1());
     }

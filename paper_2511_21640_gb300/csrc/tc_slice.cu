@@ -242,11 +242,14 @@ void sl_pack_A(Exec &ex, SlMat &dst, const cplx *src, int64_t M, int64_t K, int6
   ADC_CHECK_LAUNCH();
 }
 
-static void sl_pack_B_impl(Exec &ex, SlMat &dst, const BSrc &s, int64_t Nc, int64_t K, bool conj, const SlMat &like) {
+static void sl_pack_B_impl(Exec &ex, SlMat &dst, const BSrc &s, int64_t Nc, int64_t K, bool conj, const SlMat &like,
+                           int bits) {
   ADC_REQUIRE(like.kreal == K, ADC_ERR_ARG, "sl_pack_B: inner size differs from the A operand");
   dst.kp = like.kp;
   dst.kreal = K;
-  dst.ns = like.ns;
+  // fewer significant bits: the leading digits of the same width (the product
+  // then runs over the common leading slices of both operands)
+  dst.ns = bits > 0 ? std::min(like.ns, (bits + like.bits - 1) / like.bits) : like.ns;
   dst.bits = like.bits;
   dst.kb_split = like.kb_split;
   alloc_sl(ex, dst, 2 * Nc, Nc);
@@ -260,20 +263,21 @@ static void sl_pack_B_impl(Exec &ex, SlMat &dst, const BSrc &s, int64_t Nc, int6
 }
 
 void sl_pack_B(Exec &ex, SlMat &dst, const cplx *src, int64_t Nc, int64_t K, int64_t s_nh, int64_t s_nl,
-               int64_t n_in, int64_t s_k, bool conj, const SlMat &like) {
+               int64_t n_in, int64_t s_k, bool conj, const SlMat &like, int bits) {
   BSrc s{src, 0, s_nh, s_nl, n_in, s_k, 0, 0, 0, 0};
-  sl_pack_B_impl(ex, dst, s, Nc, K, conj, like);
+  sl_pack_B_impl(ex, dst, s, Nc, K, conj, like, bits);
 }
 
-void sl_pack_B_ring(Exec &ex, SlMat &dst, const adc_ctx *c, const cplx *X, int64_t k, const SlMat &like) {
+void sl_pack_B_ring(Exec &ex, SlMat &dst, const adc_ctx *c, const cplx *X, int64_t k, const SlMat &like, int bits) {
   BSrc s{X, c->kind == ADC_EA ? 1 : 2, 0, 0, 1, 0, c->o, c->v, c->N, c->n1};
   const int64_t Nc = (c->kind == ADC_EA) ? k * c->v : k * c->o;
-  sl_pack_B_impl(ex, dst, s, Nc, c->o * c->v, false, like);
+  sl_pack_B_impl(ex, dst, s, Nc, c->o * c->v, false, like, bits);
 }
 
 void sl_gemm(Exec &ex, const SlMat &A, const SlMat &B, int64_t M, int64_t N, cplx alpha, cplx beta, cplx *out,
              int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, SlWork &w) {
-  ADC_REQUIRE(A.kp == B.kp && A.ns == B.ns && A.bits == B.bits, ADC_ERR_ARG, "sl_gemm: operands sliced differently");
+  ADC_REQUIRE(A.kp == B.kp && A.bits == B.bits, ADC_ERR_ARG, "sl_gemm: operands sliced differently");
+  const int ns = std::min(A.ns, B.ns);  // the common leading slices
   ADC_REQUIRE(A.rows >= M && B.rows >= 2 * N, ADC_ERR_ARG, "sl_gemm: operand rows");
   if (M <= 0 || N <= 0) return;
   if (n_in <= 0) n_in = 1;
@@ -283,9 +287,9 @@ void sl_gemm(Exec &ex, const SlMat &A, const SlMat &B, int64_t M, int64_t N, cpl
   const int ksplit = (kps + kbs - 1) / kbs;
   SlCombine cfg{};
   std::vector<std::pair<int, int>> pairs;
-  for (int g = 2; g <= A.ns + 1; ++g)
+  for (int g = 2; g <= ns + 1; ++g)
     for (int i = 1; i < g; ++i)
-      if (i <= A.ns && g - i <= A.ns) pairs.push_back({i, g - i});
+      if (i <= ns && g - i <= ns) pairs.push_back({i, g - i});
   ADC_REQUIRE((int)pairs.size() <= SL_MAXPAIRS, ADC_ERR_UNSUPPORTED, "sl_gemm: too many slice pairs");
   cfg.npair = (int)pairs.size();
   cfg.ksplit = ksplit;
@@ -304,11 +308,11 @@ void sl_gemm(Exec &ex, const SlMat &A, const SlMat &B, int64_t M, int64_t N, cpl
     w.part = DBuf(ex, need);
   }
   const int bn = N2 <= 32 ? 32 : N2 <= 64 ? 64 : N2 <= 128 ? 128 : 256;
-  std::vector<TcMat> av(A.ns);
+  std::vector<TcMat> av(ns);
   for (int64_t m0 = 0; m0 < M; m0 += mc) {
     const int64_t mm = std::min(mc, M - m0);
     const size_t per = (size_t)ksplit * mm * N2;
-    for (int i = 0; i < A.ns; ++i) {  // views of rows m0 .. m0 + mm of every A slice
+    for (int i = 0; i < ns; ++i) {  // views of rows m0 .. m0 + mm of the A slices used
       TcMat &t = av[i];
       t.hi.ex = nullptr;
       t.hi.p = (__nv_bfloat16 *)A.s[i].hi.p + m0 * 2 * A.kp;

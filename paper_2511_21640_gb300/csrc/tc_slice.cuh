@@ -44,10 +44,13 @@ struct SlCache {
 void sl_pack_A(Exec &ex, SlMat &dst, const cplx *src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, bool conj,
                int bits);
 // B[n][k] = op(src[(n / n_in)*s_nh + (n % n_in)*s_nl + k*s_k]), sliced like the A operand `like`
+// bits > 0: only the leading digits for about that many significant bits (the
+// product then uses the same leading slices of A)
 void sl_pack_B(Exec &ex, SlMat &dst, const cplx *src, int64_t Nc, int64_t K, int64_t s_nh, int64_t s_nl,
-               int64_t n_in, int64_t s_k, bool conj, const SlMat &like);
+               int64_t n_in, int64_t s_k, bool conj, const SlMat &like, int bits = 0);
 // B operand of the ring term, gathered from the packed satellite block of X
-void sl_pack_B_ring(Exec &ex, SlMat &dst, const adc_ctx *c, const cplx *X, int64_t k, const SlMat &like);
+void sl_pack_B_ring(Exec &ex, SlMat &dst, const adc_ctx *c, const cplx *X, int64_t k, const SlMat &like,
+                    int bits = 0);
 // zgemm's contract (tensor.cuh) computed as the sliced product with ex.sliced_bits bits
 void zgemm_sliced(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha, const cplx *A, int64_t sAb,
                   int64_t sAm, int64_t sAk, bool conjA, const cplx *B, int64_t sBb, int64_t sBk, int64_t sBn,
