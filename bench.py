@@ -553,10 +553,14 @@ def run_ee(args, cfgname):
     else:
         rng = np.random.default_rng(11)
         wts = rng.standard_normal(nroots)
+        ctx.profile(True)
         t3 = time.perf_counter()
         gB, geo, gev, gx = ctx.sigma_adjoint(Y, wts)
         adj_s = time.perf_counter() - t3
-        log(f"adjoint {adj_s:.1f} s")
+        adj_prof = ctx.profile_read()
+        ctx.profile(False)
+        adj_stages = {k[6:]: round(e["total_ms"], 1) for k, e in adj_prof.items() if k.startswith("stage:")}
+        log(f"adjoint {adj_s:.1f} s", adj_stages)
         ctx.close()
         D = (random_hermitian_direction(p.B.shape, 12), rng.standard_normal(o), rng.standard_normal(v), 0.7)
         # derivative along D that the gradients predict
@@ -572,7 +576,7 @@ def run_ee(args, cfgname):
                 ws.append(w)
         fd = float(np.dot(wts, (ws[0] - ws[1]) / (2 * h)))
         log(f"gradient check: adjoint {pred:.10e} fd {fd:.10e}")
-        grad = {"adjoint_s": adj_s, "directional_adjoint": pred, "directional_fd": fd,
+        grad = {"adjoint_s": adj_s, "adjoint_stages_ms": adj_stages, "directional_adjoint": pred, "directional_fd": fd,
                 "rel_diff": abs(pred - fd) / max(1.0, abs(fd)), "fd_step": h, "weights": [float(w) for w in wts]}
     by = sorted(((k, e) for k, e in prof.items() if e["launches"] > 0), key=lambda t: -t[1]["total_ms"])
     pk, pk_kind = peaks()

@@ -374,6 +374,7 @@ void adjoint_ee(adc_ctx *c, const cplx *Y, const double *g_host, int64_t k, cplx
   const double *eo = c->eo.d(), *ev = c->ev.d();
   TermSource src = ee_source(c);
   TagScope tg(ex, "adjoint");
+  StageScope stage(ex, "adjoint_vectors");
 
   DBuf gdev(ex, k * sizeof(double));
   ADC_CUDA(cudaMemcpyAsync(gdev.p, g_host, k * sizeof(double), cudaMemcpyHostToDevice, ex.stream));
@@ -405,6 +406,7 @@ void adjoint_ee(adc_ctx *c, const cplx *Y, const double *g_host, int64_t k, cplx
   TV tY2c = TV::dense(Y2c.c(), {k, o, o, v, v});
 
   // ---- singles block: rho[P][Q] = sum_z g_z conj(y1[z][P]) y1[z][Q]
+  stage.next("adjoint_singles");
   DBuf rho = cbuf(ex, n1 * n1);
   zgemm(ex, n1, n1, k, 1, C1(), Y1c.c(), 0, 1, n1, false, Y, 0, N, 1, false, C0(), rho.c(), 0, n1, 1);
   const std::vector<int64_t> e4 = {o, v, o, v};
@@ -473,6 +475,7 @@ void adjoint_ee(adc_ctx *c, const cplx *Y, const double *g_host, int64_t k, cplx
   rho.reset(); K1.reset(); S2.reset(); S3.reset();
 
   // ---- coupling (twice: M_SD and its Hermitian partner M_DS)
+  stage.next("adjoint_coupling");
   eval_terms_grad(ex, E.SD1, src, gsrc, {{"zia", tY1c}, {"zklcd", tY2f}}, false, CR(0.5));
   if (third) {
     DBuf Y2k = cbuf(ex, nf), Y1s = cbuf(ex, k * n1);
@@ -511,6 +514,7 @@ void adjoint_ee(adc_ctx *c, const cplx *Y, const double *g_host, int64_t k, cplx
   }
 
   // ---- doubles block: zeroth order (packed = full / 4) and, at third order, M_DD^(1)
+  stage.next("adjoint_doubles");
   k_eps_from_doubles<<<1024, 256, (o + v) * sizeof(double), ex.stream>>>(Y2c.c(), Y2f.c(), k, o, v, 0.25, geo, gev);
   ADC_CHECK_LAUNCH();
   if (third && c->dd_order == 1) {
@@ -524,6 +528,7 @@ void adjoint_ee(adc_ctx *c, const cplx *Y, const double *g_host, int64_t k, cplx
   }
   Y1c.reset(); Y2f.reset(); Y2c.reset();
 
+  stage.next("adjoint_amplitudes_integrals");
   amplitudes_and_integrals_back(c, src, gsrc, G, third, E.t2d, E.t2s, gB, geo, gev);
   double h = 0.0;
   ADC_CUDA(cudaMemcpyAsync(&h, gxp, sizeof(double), cudaMemcpyDeviceToHost, ex.stream));
