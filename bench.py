@@ -766,7 +766,7 @@ def main():
 
     cfg = dict(CONFIGS[args.config])
     kind, order, x, nroots = cfg["kind"], cfg["order"], cfg["x"], cfg["nroots"]
-    tol = args.tol if args.tol is not None else 1e-5
+    tol = args.tol if args.tol is not None else cfg.get("tol", 1e-5)
     p = config_problem(args.config)
     o, v, Q = p.nocc, p.nvir, p.naux
     # replicas: every rank solves its own instance of the workload
