@@ -318,35 +318,69 @@ __device__ __forceinline__ void split_store(double x, __nv_bfloat16 *hi, __nv_bf
 // A rows: [Re | Im] (conj negates Im); element (m, k) at src[m*s_m + k*s_k]
 __global__ void k_emb_A(const cplx *__restrict__ src, int64_t M, int64_t K, int64_t s_m, int64_t s_k,
                         int conj, int64_t kp, __nv_bfloat16 *hi, __nv_bfloat16 *lo, __nv_bfloat16 *lo2) {
-  const int64_t total = M * kp;
+  // one thread per 8 consecutive k of a row, 16-byte stores of every plane
+  const int64_t kq = kp >> 3;
+  const int64_t total = M * kq;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = idx % kp, m = idx / kp;
-    cplx x = cmake(0.0, 0.0);
-    if (k < K) x = src[m * s_m + k * s_k];
-    const double im = conj ? -x.y : x.y;
-    const int64_t base = m * 2 * kp;
-    split_store(x.x, hi + base + k, lo + base + k, lo2 ? lo2 + base + k : nullptr);
-    split_store(im, hi + base + kp + k, lo + base + kp + k, lo2 ? lo2 + base + kp + k : nullptr);
+    const int64_t m = idx / kq, k0 = (idx - m * kq) << 3;
+    const cplx *row = src + m * s_m;
+    __align__(16) __nv_bfloat16 rh[8], rl[8], rl2[8], ih[8], il[8], il2[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t k = k0 + j;
+      cplx x = cmake(0.0, 0.0);
+      if (k < K) x = row[k * s_k];
+      split_store(x.x, &rh[j], &rl[j], &rl2[j]);
+      split_store(conj ? -x.y : x.y, &ih[j], &il[j], &il2[j]);
+    }
+    const int64_t base = m * 2 * kp + k0;
+    *(uint4 *)(hi + base) = *(const uint4 *)rh;
+    *(uint4 *)(hi + base + kp) = *(const uint4 *)ih;
+    *(uint4 *)(lo + base) = *(const uint4 *)rl;
+    *(uint4 *)(lo + base + kp) = *(const uint4 *)il;
+    if (lo2) {
+      *(uint4 *)(lo2 + base) = *(const uint4 *)rl2;
+      *(uint4 *)(lo2 + base + kp) = *(const uint4 *)il2;
+    }
   }
 }
 
 
-// B rows: row 2n = [Re | -Im], row 2n+1 = [Im | Re] (conj negates Im first)
+// B rows: row 2n = [Re | -Im], row 2n+1 = [Im | Re] (conj negates Im first).
+// One thread per 8 consecutive k of a row: one row index computation per
+// thread, 16-byte stores of every plane (the splits of -Im are the negated
+// splits of Im: round to nearest is symmetric)
 __global__ void k_emb_B(BSrc src, int64_t Nc, int64_t K, int conj, int64_t kp, __nv_bfloat16 *hi,
                         __nv_bfloat16 *lo, __nv_bfloat16 *lo2) {
-  const int64_t total = Nc * kp;
+  const int64_t kq = kp >> 3;
+  const int64_t total = Nc * kq;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = idx % kp, n = idx / kp;
-    cplx x = cmake(0.0, 0.0);
-    if (k < K) x = src.get(n, k);
-    const double im = conj ? -x.y : x.y;
-    const int64_t r0 = (2 * n) * 2 * kp, r1 = (2 * n + 1) * 2 * kp;
-    split_store(x.x, hi + r0 + k, lo + r0 + k, lo2 ? lo2 + r0 + k : nullptr);
-    split_store(-im, hi + r0 + kp + k, lo + r0 + kp + k, lo2 ? lo2 + r0 + kp + k : nullptr);
-    split_store(im, hi + r1 + k, lo + r1 + k, lo2 ? lo2 + r1 + k : nullptr);
-    split_store(x.x, hi + r1 + kp + k, lo + r1 + kp + k, lo2 ? lo2 + r1 + kp + k : nullptr);
+    const int64_t n = idx / kq, k0 = (idx - n * kq) << 3;
+    cplx x[8];
+    src.get8(n, k0, K, x);
+    __align__(16) __nv_bfloat16 rh[8], rl[8], rl2[8], ih[8], il[8], il2[8], nh[8], nl[8], nl2[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const double im = conj ? -x[j].y : x[j].y;
+      split_store(x[j].x, &rh[j], &rl[j], &rl2[j]);
+      split_store(im, &ih[j], &il[j], &il2[j]);
+      nh[j] = __hneg(ih[j]);
+      nl[j] = __hneg(il[j]);
+      nl2[j] = __hneg(il2[j]);
+    }
+    const int64_t r0 = (2 * n) * 2 * kp + k0, r1 = (2 * n + 1) * 2 * kp + k0;
+    auto put = [&](__nv_bfloat16 *plane, const __nv_bfloat16 (&re)[8], const __nv_bfloat16 (&imv)[8],
+                   const __nv_bfloat16 (&nim)[8]) {
+      *(uint4 *)(plane + r0) = *(const uint4 *)re;
+      *(uint4 *)(plane + r0 + kp) = *(const uint4 *)nim;
+      *(uint4 *)(plane + r1) = *(const uint4 *)imv;
+      *(uint4 *)(plane + r1 + kp) = *(const uint4 *)re;
+    };
+    put(hi, rh, ih, nh);
+    put(lo, rl, il, nl);
+    if (lo2) put(lo2, rl2, il2, nl2);
   }
 }
 
@@ -713,7 +747,7 @@ void tc_pack_A(Exec &ex, TcMat &dst, const cplx *src, int64_t M, int64_t K, int6
   if (dst.kp == 0) dst.kp = TC_BK;
   const size_t bytes = (size_t)M * 2 * dst.kp * sizeof(__nv_bfloat16);
   alloc_planes(ex, dst, bytes, planes);
-  k_emb_A<<<grid1d(M * dst.kp, 256), 256, 0, ex.stream>>>(src, M, K, s_m, s_k, conj ? 1 : 0, dst.kp,
+  k_emb_A<<<grid1d(M * (dst.kp / 8), 256), 256, 0, ex.stream>>>(src, M, K, s_m, s_k, conj ? 1 : 0, dst.kp,
                                                           (__nv_bfloat16 *)dst.hi.p, (__nv_bfloat16 *)dst.lo.p,
                                                           planes == 3 ? (__nv_bfloat16 *)dst.lo2.p : nullptr);
   ADC_CHECK_LAUNCH();
@@ -726,7 +760,7 @@ static void pack_B_impl(Exec &ex, TcMat &dst, const BSrc &s, int64_t Nc, int64_t
   if (dst.kp == 0) dst.kp = TC_BK;
   const size_t bytes = (size_t)dst.rows * 2 * dst.kp * sizeof(__nv_bfloat16);
   alloc_planes(ex, dst, bytes, planes);
-  k_emb_B<<<grid1d(Nc * dst.kp, 256), 256, 0, ex.stream>>>(s, Nc, K, conj ? 1 : 0, dst.kp,
+  k_emb_B<<<grid1d(Nc * (dst.kp / 8), 256), 256, 0, ex.stream>>>(s, Nc, K, conj ? 1 : 0, dst.kp,
                                                            (__nv_bfloat16 *)dst.hi.p, (__nv_bfloat16 *)dst.lo.p,
                                                            planes == 3 ? (__nv_bfloat16 *)dst.lo2.p : nullptr);
   ADC_CHECK_LAUNCH();

@@ -38,6 +38,50 @@ struct BSrc {
     cplx x = p[n1 + vec * N + pair_index(lo_, hi_, o) * v + b];
     return i < kq ? x : cmake(-x.x, -x.y);
   }
+  // B[n][k0 .. k0 + 7] (zero past K): the row's index arithmetic once, the
+  // inner index walked incrementally
+  __device__ __forceinline__ void get8(int64_t n, int64_t k0, int64_t K, cplx (&x)[8]) const {
+    if (mode == 0) {
+      const int64_t nh = n / n_in, nl = n - nh * n_in;
+      const cplx *base = p + nh * s_nh + nl * s_nl;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = (k0 + j < K) ? base[(k0 + j) * s_k] : cmake(0.0, 0.0);
+      return;
+    }
+    if (mode == 1) {  // n = (vec, b), k = (kk, c)
+      const int64_t vec = n / v, b = n - vec * v;
+      int64_t kk = k0 / v, cc = k0 - kk * v;
+      const cplx *row = p + n1 + vec * N;
+      const int64_t pv = v * (v - 1) / 2;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        cplx r = cmake(0.0, 0.0);
+        if (k0 + j < K && cc != b) {
+          const int64_t lo_ = cc < b ? cc : b, hi_ = cc < b ? b : cc;
+          const cplx y = row[kk * pv + pair_index(lo_, hi_, v)];
+          r = cc < b ? y : cmake(-y.x, -y.y);
+        }
+        x[j] = r;
+        if (++cc == v) { cc = 0; ++kk; }
+      }
+      return;
+    }
+    // mode 2: n = (vec, i), k = (kq, b)
+    const int64_t vec = n / o, i = n - vec * o;
+    int64_t kq = k0 / v, b = k0 - kq * v;
+    const cplx *row = p + n1 + vec * N;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      cplx r = cmake(0.0, 0.0);
+      if (k0 + j < K && kq != i) {
+        const int64_t lo_ = i < kq ? i : kq, hi_ = i < kq ? kq : i;
+        const cplx y = row[pair_index(lo_, hi_, o) * v + b];
+        r = i < kq ? y : cmake(-y.x, -y.y);
+      }
+      x[j] = r;
+      if (++b == v) { b = 0; ++kq; }
+    }
+  }
 };
 
 // An operand in the real embedding, split into BF16 planes of shape

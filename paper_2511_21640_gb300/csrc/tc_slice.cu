@@ -111,20 +111,43 @@ __global__ void k_sl_slice_A(const cplx *__restrict__ src, int64_t M, int64_t K,
 }
 
 // B rows 2n = [Re | -Im], 2n+1 = [Im | Re] (conj negates Im first)
+// B rows: row 2n = [Re | -Im], row 2n+1 = [Im | Re]. One thread per 8
+// consecutive k of a row; every slice's digits of the 8 elements go out as
+// 16-byte stores (the digits of -Im are the negated digits of Im)
 __global__ void k_sl_slice_B(BSrc src, int64_t Nc, int64_t K, int conj, int64_t kp, const int *__restrict__ F,
                              int ns, int b, __nv_bfloat16 *base, int64_t pe) {
-  const int64_t total = Nc * kp;
+  const int64_t kq = kp >> 3;
+  const int64_t total = Nc * kq;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = idx % kp, n = idx / kp;
-    cplx x = cmake(0.0, 0.0);
-    if (k < K) x = src.get(n, k);
-    const double im = conj ? -x.y : x.y;
-    const int64_t r0 = (2 * n) * 2 * kp, r1 = (2 * n + 1) * 2 * kp;
-    digits(x.x, F[n], ns, b, base, pe, r0 + k, -1);
-    digits(x.x, F[n], ns, b, base, pe, r1 + kp + k, -1);
-    // row 2n holds -Im, row 2n+1 holds Im: the digits of -y are the negated digits of y
-    digits(im, F[n], ns, b, base, pe, r1 + k, r0 + kp + k);
+    const int64_t n = idx / kq, k0 = (idx - n * kq) << 3;
+    cplx x[8];
+    src.get8(n, k0, K, x);
+    const int E = F[n];
+    double yr[8], yi[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      yr[j] = ldexp(x[j].x, -E);
+      yi[j] = ldexp(conj ? -x[j].y : x[j].y, -E);
+    }
+    const int64_t r0 = (2 * n) * 2 * kp + k0, r1 = (2 * n + 1) * 2 * kp + k0;
+    for (int i = 1; i <= ns; ++i) {
+      __align__(16) __nv_bfloat16 dr[8], di[8], dn[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const double a = rint(ldexp(yr[j], b * i)), c = rint(ldexp(yi[j], b * i));
+        yr[j] -= ldexp(a, -b * i);  // exact: the remainder has at most 53 significant bits
+        yi[j] -= ldexp(c, -b * i);
+        dr[j] = __double2bfloat16(a);
+        di[j] = __double2bfloat16(c);
+        dn[j] = __double2bfloat16(-c);
+      }
+      __nv_bfloat16 *pl = base + (int64_t)(i - 1) * pe;
+      *(uint4 *)(pl + r0) = *(const uint4 *)dr;
+      *(uint4 *)(pl + r0 + kp) = *(const uint4 *)dn;
+      *(uint4 *)(pl + r1) = *(const uint4 *)di;
+      *(uint4 *)(pl + r1 + kp) = *(const uint4 *)dr;
+    }
   }
 }
 
@@ -256,7 +279,7 @@ static void sl_pack_B_impl(Exec &ex, SlMat &dst, const BSrc &s, int64_t Nc, int6
   if (Nc <= 0) return;
   k_sl_exp_B<<<(unsigned)std::min<int64_t>(Nc, 65535), 256, 0, ex.stream>>>(s, Nc, K, (int *)dst.exps.p);
   ADC_CHECK_LAUNCH();
-  k_sl_slice_B<<<grid1d(Nc * dst.kp, 256), 256, 0, ex.stream>>>(s, Nc, K, conj ? 1 : 0, dst.kp,
+  k_sl_slice_B<<<grid1d(Nc * (dst.kp / 8), 256), 256, 0, ex.stream>>>(s, Nc, K, conj ? 1 : 0, dst.kp,
                                                                 (const int *)dst.exps.p, dst.ns, dst.bits,
                                                                 (__nv_bfloat16 *)dst.planes.p, 2 * Nc * 2 * dst.kp);
   ADC_CHECK_LAUNCH();
