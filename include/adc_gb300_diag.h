@@ -67,6 +67,12 @@ int adc_memory(const adc_ctx_opaque *ctx, int64_t *in_use, int64_t *peak);
  * every context of the process on that device until it is set again. */
 int adc_diag_set_wait_ns(uint64_t ns);
 
+/* Test hook: the size (complex elements) of one chunk of the setup's chunked
+ * intermediates (the IP third-order coupling's (ea|fk) block, formed in chunks
+ * of its first virtual index); <= 0 restores the default of 2^28. Process-wide,
+ * host only; affects contexts initialised afterwards. Returns ADC_OK. */
+int adc_diag_set_setup_chunk(int64_t elems);
+
 /* 1 when the context forms its EA ladder integrals inside every product
  * (opts.ladder), else 0. ADC_ERR_STATE for a NULL context. */
 int adc_ladder_mode(const adc_ctx_opaque *ctx, int *direct);

@@ -120,6 +120,7 @@ def _load():
         "adc_diag_blockops": (I, [I, I64, I64, I64, ctypes.c_uint64, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_diag_fp64_peak": (I, [I, I64, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_diag_set_wait_ns": (I, [ctypes.c_uint64]),
+        "adc_diag_set_setup_chunk": (I, [ctypes.c_int64]),
         "adc_diag_eigh": (I, [I, P, I, P, P, ctypes.POINTER(D), ctypes.POINTER(I)]),
         "adc_sigma_adjoint": (I, [P, P, P, I64, P, P, P, ctypes.POINTER(D)]),
         "adc_state_density": (I, [P, P, P]),

@@ -129,6 +129,8 @@ int ssfns_run(const adc_c128 *B, int64_t naux, const double *eps_occ, int64_t no
               int64_t nvir, int kind, int order, double x, int nroots, double eta_crit, double tol, int max_iter,
               int precision, const adc_opts *opts, adc_ssfns_root *out);
 void sigma_ee_fp64(adc_ctx *c, const cplx *X, cplx *S, int64_t k);
+// chunk size (complex elements) of the setup's chunked intermediates; <= 0 restores the default
+void set_setup_chunk_elems(int64_t n);
 // significant bits of the sliced sigma products (ADC_PREC_SLICED, ADC_PREC_SLICED24)
 constexpr int kSlicedBits = 40, kSliced24Bits = 24;
 void sigma_ee_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg, int bits = kSlicedBits);

@@ -201,6 +201,11 @@ extern "C" int adc_profile_enable(adc_ctx *c, int on) {
   }
 }
 
+extern "C" int adc_diag_set_setup_chunk(int64_t elems) {
+  set_setup_chunk_elems(elems);
+  return ADC_OK;
+}
+
 extern "C" int adc_diag_set_wait_ns(uint64_t ns) {
   try {
     tc_set_wait_ns(ns);

@@ -141,6 +141,11 @@ DBuf vvvv_L(adc_ctx *c) {
   return L;
 }
 
+// complex elements of one chunk of the setup's chunked intermediates (the
+// IP coupling's (ea|fk) block); a test hook lowers it to force several chunks
+static int64_t g_setup_chunk_elems = (int64_t)1 << 28;
+void set_setup_chunk_elems(int64_t n) { g_setup_chunk_elems = n > 0 ? n : ((int64_t)1 << 28); }
+
 int64_t vvvv_chunk(adc_ctx *c) {
   const int64_t v = c->v;
   return std::min<int64_t>(v, std::max<int64_t>(1, ((int64_t)1 << 26) / (v * v * v)));
@@ -437,7 +442,7 @@ void setup_operators(adc_ctx *c) {
       // + x/2 sum_ef <ef||ak> conj(t_ji^ef) = x sum_ef (ea|fk) conj(t_ji^ef), in chunks of the
       // virtual index a whose (ea|fk) block stays within about 4 GiB:
       // J[a][e][k][f] = sum_Q B_ea B_fk, Tc[a][k][j][i] = sum_ef J[a][e][k][f] conj(t_ji^ef)
-      const int64_t ca = std::max<int64_t>(1, std::min<int64_t>(v, (1ll << 28) / (o * v * v)));
+      const int64_t ca = std::max<int64_t>(1, std::min<int64_t>(v, g_setup_chunk_elems / (o * v * v)));
       DBuf J = cbuf(ex, ca * v * o * v), Tc = cbuf(ex, ca * o * o * o);
       for (int64_t a0 = 0; a0 < v; a0 += ca) {
         const int64_t na = std::min(ca, v - a0);

@@ -168,6 +168,26 @@ def test_grouped_split_sigma(gpu, kind, o, v, Q, order, x, seed, k):
     assert _rel(out[True], out[False]).max() < 1e-5
 
 
+@pytest.mark.parametrize("o,v,Q,x,chunk", [(5, 12, 30, 1.0, 2), (4, 9, 20, 0.5, 4)])
+def test_ip_coupling_intermediate_in_chunks(gpu, o, v, Q, x, chunk):
+    """IP third order: the (ea|fk) block of the second-order coupling formed in
+    chunks of a (here `chunk` virtual indices per chunk, a ragged last one),
+    equal to the oracle and to the context built in one chunk."""
+    p = make_problem(o, v, Q, seed=71, sigma=0.08)
+    X = random_vectors(o + oadc.dims("IP", o, v)[1], 3, seed=72)
+    ref = oadc.sigma_ref("IP", 3, x, p.B, p.eps_occ, p.eps_vir, X)
+    with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP", order=3, x=x) as c1:
+        S1 = c1.sigma(X, "fp64")
+    try:
+        assert gpu.lib.adc_diag_set_setup_chunk(chunk * o * v * v) == 0
+        with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="IP", order=3, x=x) as c2:
+            S2 = c2.sigma(X, "fp64")
+    finally:
+        gpu.lib.adc_diag_set_setup_chunk(0)
+    assert _rel(S2, ref).max() < 1e-12
+    assert _rel(S2, S1).max() < 1e-13
+
+
 def test_sigma_zero_vectors_and_k0(gpu):
     p = make_problem(4, 10, 12, seed=2, sigma=0.1)
     with gpu.Context(p.B, p.eps_occ, p.eps_vir, kind="EA", order=3, x=1.0) as ctx:
