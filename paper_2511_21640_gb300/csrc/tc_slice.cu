@@ -380,9 +380,15 @@ void zgemm_sliced(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx
   fill_zero(ex, err.p, sizeof(int));
   // the digit planes take 4 ns kp bytes per row of A and 8 ns kp per column
   // of B (ns slices of the real embedding): rows and columns in chunks whose
-  // planes stay within about 4 GiB per operand
+  // planes stay within an eighth of the free device memory per operand
+  // (between 1 and 16 GiB), so that B is sliced once where it fits
   const SlParams sp = sl_params(K, ex.sliced_bits);
-  const size_t cap = (size_t)4 << 30;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    fr = (size_t)32 << 30;
+  }
+  const size_t cap = std::min<size_t>((size_t)16 << 30, std::max<size_t>((size_t)1 << 30, fr / 8));
   const int64_t mc = std::min<int64_t>(M, std::max<int64_t>(128, (int64_t)(cap / ((size_t)4 * sp.ns * sp.kp))));
   const int64_t nc = std::min<int64_t>(N, std::max<int64_t>(64, (int64_t)(cap / ((size_t)8 * sp.ns * sp.kp))));
   for (int64_t b = 0; b < batch; ++b) {
