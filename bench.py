@@ -881,6 +881,15 @@ def main():
         fl = sum(e["flops"] for e in pr.values()) / reps
         sig[prec] = {"ms": t, "tflops": fl / (t * 1e-3) / 1e12, "flops": fl}
     log("sigma", sig)
+    # the whole mixed sigma block (packing, FP64 main block, epilogues included) against the
+    # BF16 tensor peak: counted as 3M BF16x3 (9 BF16 real MACs per complex MAC) and as executed
+    # (the real embedding: 12 per complex MAC)
+    peak_tc = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    alg_tf = sig[args.mixed]["tflops"]
+    tensor_share = {"algorithmic_tflops": alg_tf, "tflops_3m_count": alg_tf * 18 / 8,
+                    "frac_3m_count": alg_tf * 18 / 8 / peak_tc, "tflops_mma_executed": alg_tf * 24 / 8,
+                    "frac_mma_executed": alg_tf * 24 / 8 / peak_tc, "peak_tflops": peak_tc,
+                    "peak_kind": f"bf16 dense sustained ({pk_kind})"}
     S64 = ctx.sigma(Xs, "fp64")
 
     def rel_to_fp64(S):
@@ -969,7 +978,7 @@ def main():
         "sigma": {**sig, "speedup": sig["fp64"]["ms"] / sig[args.mixed]["ms"],
                   "rel_diff_mixed_vs_fp64": sig_rel, "rel_diff_sliced_vs_fp64": sig_rel_sliced,
                   "speedup_sliced": (sig["fp64"]["ms"] / sig["sliced"]["ms"]) if "sliced" in sig else None,
-                  "vectors": nroots},
+                  "vectors": nroots, "tensor_roofline": tensor_share},
         "sampled_parity": parity,
         "refine": args.refine,
         "fp64_davidson": fp64,
