@@ -531,6 +531,8 @@ typedef struct {
   int64_t mem_budget;  /* device bytes for resident problems, 0 = 85% of the free memory */
   int init_lanes;      /* concurrent adc_init calls, 0 = 4 */
   int verbose;
+  int setup;           /* adc_opts.setup of every problem's adc_init (ADC_PREC_FP64 or ADC_PREC_SLICED) */
+  int refine;          /* adc_opts.refine of every problem (ADC_PREC_FP64 or ADC_PREC_SLICED) */
 } adc_batch_opts;
 
 /* Host-only planner (no GPU needed): estimated device bytes mem_est[i] and

@@ -88,7 +88,8 @@ class adc_problem(ctypes.Structure):
 
 
 class adc_batch_opts(ctypes.Structure):
-    _fields_ = [("mem_budget", ctypes.c_int64), ("init_lanes", ctypes.c_int), ("verbose", ctypes.c_int)]
+    _fields_ = [("mem_budget", ctypes.c_int64), ("init_lanes", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("setup", ctypes.c_int), ("refine", ctypes.c_int)]
 
 
 def _load():
@@ -604,11 +605,12 @@ def batch_plan(problems, nroots, mem_budget):
     return rc, order, wave, mem, cost
 
 
-def batch_solve(problems, nroots, tol=1e-6, max_iter=300, precision="bf16x3", mem_budget=0, init_lanes=0):
+def batch_solve(problems, nroots, tol=1e-6, max_iter=300, precision="bf16x3", mem_budget=0, init_lanes=0,
+                setup="fp64", refine="fp64"):
     """Solve many problems given as host arrays (``adc_batch_solve``): (omega, err64, status, info, rc)."""
     n = len(problems)
     arr, keep = _problems(problems)
-    o = adc_batch_opts(int(mem_budget), int(init_lanes), 0)
+    o = adc_batch_opts(int(mem_budget), int(init_lanes), 0, PRECISIONS[setup], PRECISIONS[refine])
     omega = np.empty((n, nroots), dtype=np.float64)
     err = np.empty((n, nroots), dtype=np.float64)
     status = np.empty(n, dtype=np.int32)

@@ -627,6 +627,8 @@ int adc_batch_solve(int n, const adc_problem *p, int nroots, double tol, int max
           const adc_problem &q = p[ids[j]];
           adc_opts op;
           adc_opts_default(&op);
+          op.setup = o.setup;
+          op.refine = o.refine;
           irc[j] = adc_init(&ctxs[j], q.B, q.naux, q.eps_occ, q.nocc, q.eps_vir, q.nvir, q.kind, q.order, q.x, &op);
           if (irc[j] == ADC_OK) irc[j] = adc_sync(ctxs[j]);
         }
