@@ -85,6 +85,25 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
       ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar)
       : "memory");
 }
+// the same with an L2 cache policy (createpolicy)
+__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar,
+                                                 uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;"
+      ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ void fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -196,9 +215,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUten
         *abort_flag = 1;
         break;
       }
+      // the products of one k-block back to back (second operand reads from L2)
       const int g = kb_beg + i;
-      const int seg = g / kps;
-      const int kx = (g - seg * kps) * TC_BK;
+      const int seg = g % nseg;
+      const int kx = (g / nseg) * TC_BK;
       const uint32_t fb = smem_u32(&full[s]);
       mbar_expect_tx(fb, L::STAGE);
       uint8_t *sa = smem + s * L::STAGE;
@@ -500,10 +520,24 @@ __device__ __forceinline__ TgTile tg_decode(const TcJob *__restrict__ jobs, int 
   d.J = &jobs[lo];
   const TcJob &J = *d.J;
   const int lt = t - J.tile_begin;
-  const int per_m = J.tiles_n * J.ksplit;
-  const int tm = lt / per_m, rem = lt - tm * per_m;
-  const int tn = rem / J.ksplit;
-  d.split = rem - tn * J.ksplit;
+  // panels of J.panel column blocks (the last one narrower), row blocks
+  // inside a panel, column blocks inside a row block, K splits fastest
+  const int pw = J.panel, np_full = J.tiles_n / pw;
+  const int full = np_full * J.tiles_m * pw * J.ksplit;
+  int P, r, w;
+  if (lt < full) {
+    P = lt / (J.tiles_m * pw * J.ksplit);
+    r = lt - P * (J.tiles_m * pw * J.ksplit);
+    w = pw;
+  } else {
+    P = np_full;
+    r = lt - full;
+    w = J.tiles_n - np_full * pw;
+  }
+  const int per_m = w * J.ksplit;
+  const int tm = r / per_m, rem = r - tm * per_m;
+  const int tn = P * pw + rem / J.ksplit;
+  d.split = rem - (rem / J.ksplit) * J.ksplit;
   d.bn = J.bn;
   d.m0 = tm * TC_BM;
   d.n0 = tn * J.bn;
@@ -560,6 +594,7 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
   if (warp == 0 && lane == 0) {
     // ---------------- tile scheduler and TMA producer
     uint32_t g = 0, g_issued = 0;
+    const uint64_t pol_last = policy_evict_last(), pol_first = policy_evict_first();
     for (uint32_t q = 0;; ++q) {
       const int slot = (int)(q % TG_TQ);
       const uint32_t r = q / TG_TQ;
@@ -590,14 +625,21 @@ k_tc_grouped(const TcJob *__restrict__ jobs, int njobs, int total_tiles, int *co
           stop = true;
           break;
         }
+        // the products of one k-block (hi hi, hi lo, lo hi) back to back, so
+        // that the second read of an operand block comes from L2
         const int kg = d.kb_beg + i;
-        const int seg = kg / J.kps;
-        const int kx = (kg - seg * J.kps) * TC_BK;
+        const int seg = kg % J.nseg;
+        const int kx = (kg / J.nseg) * TC_BK;
         const uint32_t fb = smem_u32(&full[s]);
         mbar_expect_tx(fb, bytes);
         uint8_t *sa = smem + s * TgLayout::STAGE;
-        tma_load_2d(smem_u32(sa), seg == 2 ? &J.mAl : &J.mAh, kx, d.m0, fb);
-        tma_load_2d(smem_u32(sa + TgLayout::A_BYTES), seg == 1 ? &J.mBl : &J.mBh, kx, d.n0, fb);
+        if (J.l2keepB) {
+          tma_load_2d_hint(smem_u32(sa), seg == 2 ? &J.mAl : &J.mAh, kx, d.m0, fb, pol_first);
+          tma_load_2d_hint(smem_u32(sa + TgLayout::A_BYTES), seg == 1 ? &J.mBl : &J.mBh, kx, d.n0, fb, pol_last);
+        } else {
+          tma_load_2d(smem_u32(sa), seg == 2 ? &J.mAl : &J.mAh, kx, d.m0, fb);
+          tma_load_2d(smem_u32(sa + TgLayout::A_BYTES), seg == 1 ? &J.mBl : &J.mBh, kx, d.n0, fb);
+        }
         g_issued = gi + 1;
       }
       if (stop) break;
@@ -972,6 +1014,21 @@ void tc_gemm_grouped(Exec &ex, const std::vector<TcJobDesc> &in, TcGroup &grp, i
     J.ksplit = p.ksplit;
     J.kb_per_split = p.kbps;
     J.tile_begin = (int)tiles;
+    {
+      // B is re-read by every row block. When A is several times larger, the
+      // tiles run in panels of B columns whose planes fit in about a third of
+      // L2, loaded with an evict-last policy (A evict-first, streaming through)
+      const double planes_used = (p.nseg == 1) ? 1.0 : 2.0;
+      const double col_block = (double)p.bn * kp2 * 2.0 * planes_used;  // bytes of one column block of B
+      const double bbytes = (double)std::min<int64_t>(d.B->rows, p.N2) * kp2 * 2.0 * planes_used;
+      const double abytes = (double)std::min<int64_t>(d.A->rows, d.M) * kp2 * 2.0 * planes_used;
+      J.panel = p.tiles_n;
+      J.l2keepB = 0;
+      if (p.tiles_m > 1 && abytes >= 4.0 * bbytes) {
+        J.l2keepB = 1;
+        J.panel = (int)std::max<double>(1.0, std::min<double>(p.tiles_n, std::floor(48e6 / col_block)));
+      }
+    }
     tiles += (int64_t)p.tiles_m * p.tiles_n * p.ksplit;
   }
   ADC_REQUIRE(tiles < (1ll << 31), ADC_ERR_UNSUPPORTED, "tc_gemm_grouped: too many tiles");

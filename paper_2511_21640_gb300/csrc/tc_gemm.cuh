@@ -129,7 +129,11 @@ struct alignas(128) TcJob {
   float *part;  // split-K partials [ksplit][M][N2] or null
   int64_t s_m, s_nh, s_nl, n_in;
   cplx alpha, beta;
-  int M, N2, kps, bn, tiles_n, tiles_m, ksplit, kb_per_split, tile_begin, nseg, pad_[2];
+  int M, N2, kps, bn, tiles_n, tiles_m, ksplit, kb_per_split, tile_begin, nseg;
+  int l2keepB;  // 1: the B operand (re-read by every row block) loaded with an L2 evict-last
+                // policy and A with evict-first, so that B stays in L2 while A streams
+  int panel;    // column blocks per panel: tiles run panel by panel, row blocks inside a
+                // panel, so that one panel of B is re-read from L2 (tiles_n: one panel)
 };
 
 // one job as the host describes it: out = alpha * A B^T + beta * out, same
