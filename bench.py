@@ -701,6 +701,41 @@ def run_init_profile(args, name):
     print(json.dumps(out), flush=True)
 
 
+def run_sigma_only(args, name):
+    """One sigma block of the workload (nroots seeded vectors, device buffers) in one
+    precision, after three warm-up blocks (tile widths tuned, operands packed), inside
+    the NVTX range 'sigma': its CUDA-event time and algorithmic rate (one JSON line)."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_2511_21640_gb300 as adcgpu
+    cfg = dict(CONFIGS[name])
+    p = config_problem(name)
+    ctx = adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind=cfg["kind"], order=cfg["order"], x=cfg["x"],
+                         setup=args.e2e_setup, dd_order=cfg.get("dd_order", 1))
+    X = torch.from_numpy(random_vectors(ctx.N, cfg["nroots"], seed=7)).cuda()
+    for _ in range(3):
+        ctx.sigma(X, args.sigma_only)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    nvtx_range("sigma", True)
+    a.record()
+    ctx.sigma(X, args.sigma_only)
+    b.record()
+    nvtx_range("sigma", False)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms = a.elapsed_time(b)
+    fl = sum(e["flops"] for e in prof.values() if not e.get("name", "").startswith("stage:"))
+    print(json.dumps({"config": name, "precision": args.sigma_only, "vectors": cfg["nroots"], "ms": ms,
+                      "algorithmic_tflops": fl / (ms * 1e-3) / 1e12,
+                      "kernels": {k: {"launches": e["launches"], "ms": round(e["total_ms"], 3)}
+                                  for k, e in prof.items()}}), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -728,6 +763,9 @@ def main():
                     help="CPU baseline: oracle rows, run one per host core (about 30 s each)")
     ap.add_argument("--init-only", action="store_true",
                     help="time adc_init alone (host inputs, the e2e setup) and print its stage and GEMM profile")
+    ap.add_argument("--sigma-only", default=None, choices=["bf16x3", "sliced", "sliced24", "fp64"],
+                    help="one sigma block of nroots vectors in this precision after three warm-up blocks, "
+                         "inside the NVTX range 'sigma' (for a capture of its kernels)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -740,6 +778,10 @@ def main():
     if args.init_only:
         if rank == 0:
             run_init_profile(args, args.config)
+        return
+    if args.sigma_only:
+        if rank == 0:
+            run_sigma_only(args, args.config)
         return
     if args.config in CONFIGS and CONFIGS[args.config]["kind"] == "EE":
         if rank == 0:
