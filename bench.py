@@ -710,8 +710,9 @@ def run_sigma_only(args, name):
     import paper_2511_21640_gb300 as adcgpu
     cfg = dict(CONFIGS[name])
     p = config_problem(name)
+    torch.cuda.set_stream(torch.cuda.Stream())
     ctx = adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind=cfg["kind"], order=cfg["order"], x=cfg["x"],
-                         setup=args.e2e_setup, dd_order=cfg.get("dd_order", 1))
+                         setup=args.e2e_setup, dd_order=cfg.get("dd_order", 1), stream="torch")
     X = torch.from_numpy(random_vectors(ctx.N, cfg["nroots"], seed=7)).cuda()
     for _ in range(3):
         ctx.sigma(X, args.sigma_only)
@@ -720,9 +721,9 @@ def run_sigma_only(args, name):
     b = torch.cuda.Event(enable_timing=True)
     ctx.profile(True)
     nvtx_range("sigma", True)
-    a.record()
+    a.record(torch.cuda.current_stream())
     ctx.sigma(X, args.sigma_only)
-    b.record()
+    b.record(torch.cuda.current_stream())
     nvtx_range("sigma", False)
     torch.cuda.synchronize()
     prof = ctx.profile_read()
