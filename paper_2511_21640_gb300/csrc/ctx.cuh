@@ -141,6 +141,8 @@ void sigma_fp64_share(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int64_t i0,
 void sigma_split(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int nseg);
 // FP64-accurate sigma with the dense contractions as sliced tensor-core products (IP/EA)
 void sigma_sliced(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int bits = kSlicedBits);
+// estimate of the largest device scratch one sigma call of k vectors allocates (bytes)
+double sigma_scratch_bytes(const adc_ctx *c, int64_t k);
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision);
 void release_tc(adc_ctx *c);
 void tc_ensure(adc_ctx *c, int planes = 2);  // split-precision operator copies, built on first use

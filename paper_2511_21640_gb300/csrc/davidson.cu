@@ -451,9 +451,12 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
   int mmax = c->opts.max_subspace > 0 ? c->opts.max_subspace : std::max(8 * kb, 40);
   mmax = (int)std::min<int64_t>(std::min<int64_t>(mmax, N), 1024);
   mmax = std::max(mmax, std::min<int>((int)N, nroots + 1));
+  int krmax = std::max(2 * nroots, kb);
   if (c->opts.max_subspace <= 0) {
     // the operators of the products first (their transient buffers never meet
-    // the subspace), then V and AV within half of the memory left
+    // the subspace); then V and AV take what is left after the Davidson's
+    // other vectors (T, Tn, R: nroots each; Y, SY: krmax each), an estimate of
+    // the largest scratch of one product, and a margin of 8%
     if (c->kind == ADC_EE && c->ee)
       ee_prepare(c, precision == ADC_PREC_FP64 ? 0 : (mixed == ADC_PREC_BF16X6 ? 3 : 2),
                  c->opts.refine == ADC_PREC_SLICED);
@@ -462,11 +465,21 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
     ADC_CUDA(cudaMemGetInfo(&fr, &tot));
     double avail = (double)fr;
     if (c->ex.mem_limit > 0) avail = std::min(avail, (double)(c->ex.mem_limit - c->ex.mem_used));
-    const int64_t fit = (int64_t)(0.5 * std::max(avail, 0.0) / (2.0 * (double)N * sizeof(cplx)));
+    const double vec = (double)N * sizeof(cplx);
+    const double scratch = sigma_scratch_bytes(c, kb);
+    auto fit_of = [&](int kr) {
+      return (int64_t)((0.92 * std::max(avail, 0.0) - (3.0 * nroots + 2.0 * kr) * vec - scratch) / (2.0 * vec));
+    };
     const int lo = (int)std::min<int64_t>(N, std::max(2 * nroots, kb) + kb);
+    int64_t fit = fit_of(krmax);
+    // short of memory: keep fewer Ritz vectors at a collapse (thick restart of nroots)
+    if (fit < lo) {
+      krmax = std::max(nroots, (kb + 1) / 2);
+      fit = fit_of(krmax);
+    }
     if (fit < mmax) mmax = (int)std::max<int64_t>(fit, std::max(lo, std::min<int>((int)N, nroots + 1)));
   }
-  const int krmax = std::min(mmax, std::max(2 * nroots, kb));
+  krmax = std::min(mmax, krmax);
   ADC_REQUIRE(!follow || (nroots == 1 && guess && nguess >= 1), ADC_ERR_ARG,
               "root-specific Davidson: one root and a guess vector");
   Davidson d(c, nroots, mmax, krmax);

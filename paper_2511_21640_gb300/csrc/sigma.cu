@@ -149,6 +149,21 @@ void sigma_fp64_share(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int64_t i0,
   pair_pack(ex, Xf, v, v * k * v, k * v, 1, 0, 1.0, k, nb, v, 1, S + n1, ldS, pv, CR(-x), C1());
 }
 
+double sigma_scratch_bytes(const adc_ctx *c, int64_t k) {
+  const double cs = (double)sizeof(cplx);
+  const double o = (double)c->o, v = (double)c->v, po = (double)npairs(c->o), pv = (double)npairs(c->v);
+  if (c->kind == ADC_EE) {
+    // one vector of the structured product: the gathered doubles of both
+    // coupling GEMMs, their BF16 planes and the sliced digit planes of one of them
+    double b = 8.0 * cs * std::max(o * o * pv, po * v * v);
+    if (c->order == 3 && c->x != 0.0 && c->dd_order == 1) b += 3.0 * cs * (o * v) * (o * v);
+    return b;
+  }
+  // IP/EA: the ring block, the packed B operands (BF16 planes or digit slices) of the block
+  const double ring = (c->kind == ADC_EA) ? (double)k * o * v * v : (double)k * o * v * o;
+  return cs * (2.0 * ring + 8.0 * (double)k * (double)c->N);
+}
+
 void sigma(adc_ctx *c, const cplx *X, cplx *S, int64_t k, int precision) {
   if (k <= 0) return;
   if (precision != ADC_PREC_FP64 && precision != ADC_PREC_BF16X3 && precision != ADC_PREC_BF16X6 &&
