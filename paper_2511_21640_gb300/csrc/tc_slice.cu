@@ -80,67 +80,85 @@ __global__ void k_sl_exp_B(BSrc src, int64_t Nc, int64_t K, int *F) {
   }
 }
 
-// the ns digits of y = x 2^-E into plane i (planes pe elements apart) at pos0,
-// and their negations at pos1 when pos1 >= 0
-__device__ __forceinline__ void digits(double x, int E, int ns, int b, __nv_bfloat16 *base, int64_t pe,
-                                       int64_t pos0, int64_t pos1) {
-  double y = ldexp(x, -E);
-  for (int i = 1; i <= ns; ++i) {
-    const double d = rint(ldexp(y, b * i));
-    y -= ldexp(d, -b * i);  // exact: the remainder has at most 53 significant bits
-    const __nv_bfloat16 h = __double2bfloat16(d);
-    base[(int64_t)(i - 1) * pe + pos0] = h;
-    if (pos1 >= 0) base[(int64_t)(i - 1) * pe + pos1] = __double2bfloat16(-d);
-  }
+// Digits in integer arithmetic (the FP64 pipe is the scarce one): the value
+// y = x 2^-E (|y| < 1) as the integer R = round(y 2^(b ns)) (at most 61 bits),
+// then ns signed digits of b bits, each rounded to nearest with the remainder
+// carried to the next (|d_1| <= 2^b, |d_i| <= 2^(b-1) after it), so that
+// y = sum_i d_i 2^(-b i) to within 2^(-b ns - 1).
+__device__ __forceinline__ long long fixed_of(double x, int E, int bns) { return llrint(ldexp(x, bns - E)); }
+__device__ __forceinline__ int next_digit(long long &R, int sh) {
+  const long long d = (sh > 0) ? ((R + (1LL << (sh - 1))) >> sh) : R;
+  R -= d * (1LL << sh);
+  return (int)d;
 }
 
-// A rows [Re | Im] (conj negates Im), padded to kp with zeros
+// A rows [Re | Im] (conj negates Im), padded to kp with zeros. One thread per
+// 8 consecutive k of a row, 16-byte stores of every slice
 __global__ void k_sl_slice_A(const cplx *__restrict__ src, int64_t M, int64_t K, int64_t s_m, int64_t s_k, int conj,
                              int64_t kp, const int *__restrict__ E, int ns, int b, __nv_bfloat16 *base, int64_t pe) {
-  const int64_t total = M * kp;
+  const int64_t kq = kp >> 3;
+  const int64_t total = M * kq;
+  const int bns = b * ns;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = idx % kp, m = idx / kp;
-    cplx x = cmake(0.0, 0.0);
-    if (k < K) x = src[m * s_m + k * s_k];
-    const double im = conj ? -x.y : x.y;
-    const int64_t row = m * 2 * kp;
-    digits(x.x, E[m], ns, b, base, pe, row + k, -1);
-    digits(im, E[m], ns, b, base, pe, row + kp + k, -1);
+    const int64_t m = idx / kq, k0 = (idx - m * kq) << 3;
+    const cplx *row = src + m * s_m;
+    const int e = E[m];
+    long long Rr[8], Ri[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t k = k0 + j;
+      cplx x = cmake(0.0, 0.0);
+      if (k < K) x = row[k * s_k];
+      Rr[j] = fixed_of(x.x, e, bns);
+      Ri[j] = fixed_of(conj ? -x.y : x.y, e, bns);
+    }
+    const int64_t r0 = m * 2 * kp + k0;
+    for (int i = 1; i <= ns; ++i) {
+      const int sh = b * (ns - i);
+      __align__(16) __nv_bfloat16 dr[8], di[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        dr[j] = __int2bfloat16_rn(next_digit(Rr[j], sh));
+        di[j] = __int2bfloat16_rn(next_digit(Ri[j], sh));
+      }
+      __nv_bfloat16 *pl = base + (int64_t)(i - 1) * pe;
+      *(uint4 *)(pl + r0) = *(const uint4 *)dr;
+      *(uint4 *)(pl + r0 + kp) = *(const uint4 *)di;
+    }
   }
 }
 
-// B rows 2n = [Re | -Im], 2n+1 = [Im | Re] (conj negates Im first)
-// B rows: row 2n = [Re | -Im], row 2n+1 = [Im | Re]. One thread per 8
-// consecutive k of a row; every slice's digits of the 8 elements go out as
-// 16-byte stores (the digits of -Im are the negated digits of Im)
+// B rows: row 2n = [Re | -Im], row 2n+1 = [Im | Re] (conj negates Im first).
+// One thread per 8 consecutive k of a row; every slice's digits of the 8
+// elements go out as 16-byte stores (the digits of -Im are the negated digits of Im)
 __global__ void k_sl_slice_B(BSrc src, int64_t Nc, int64_t K, int conj, int64_t kp, const int *__restrict__ F,
                              int ns, int b, __nv_bfloat16 *base, int64_t pe) {
   const int64_t kq = kp >> 3;
   const int64_t total = Nc * kq;
+  const int bns = b * ns;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = idx / kq, k0 = (idx - n * kq) << 3;
     cplx x[8];
     src.get8(n, k0, K, x);
-    const int E = F[n];
-    double yr[8], yi[8];
+    const int e = F[n];
+    long long Rr[8], Ri[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      yr[j] = ldexp(x[j].x, -E);
-      yi[j] = ldexp(conj ? -x[j].y : x[j].y, -E);
+      Rr[j] = fixed_of(x[j].x, e, bns);
+      Ri[j] = fixed_of(conj ? -x[j].y : x[j].y, e, bns);
     }
     const int64_t r0 = (2 * n) * 2 * kp + k0, r1 = (2 * n + 1) * 2 * kp + k0;
     for (int i = 1; i <= ns; ++i) {
+      const int sh = b * (ns - i);
       __align__(16) __nv_bfloat16 dr[8], di[8], dn[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const double a = rint(ldexp(yr[j], b * i)), c = rint(ldexp(yi[j], b * i));
-        yr[j] -= ldexp(a, -b * i);  // exact: the remainder has at most 53 significant bits
-        yi[j] -= ldexp(c, -b * i);
-        dr[j] = __double2bfloat16(a);
-        di[j] = __double2bfloat16(c);
-        dn[j] = __double2bfloat16(-c);
+        const int a = next_digit(Rr[j], sh), c = next_digit(Ri[j], sh);
+        dr[j] = __int2bfloat16_rn(a);
+        di[j] = __int2bfloat16_rn(c);
+        dn[j] = __int2bfloat16_rn(-c);
       }
       __nv_bfloat16 *pl = base + (int64_t)(i - 1) * pe;
       *(uint4 *)(pl + r0) = *(const uint4 *)dr;
@@ -259,7 +277,7 @@ void sl_pack_A(Exec &ex, SlMat &dst, const cplx *src, int64_t M, int64_t K, int6
   if (M <= 0) return;
   k_sl_exp_A<<<(unsigned)std::min<int64_t>(M, 65535), 256, 0, ex.stream>>>(src, M, K, s_m, s_k, (int *)dst.exps.p);
   ADC_CHECK_LAUNCH();
-  k_sl_slice_A<<<grid1d(M * dst.kp, 256), 256, 0, ex.stream>>>(src, M, K, s_m, s_k, conj ? 1 : 0, dst.kp,
+  k_sl_slice_A<<<grid1d(M * (dst.kp / 8), 256), 256, 0, ex.stream>>>(src, M, K, s_m, s_k, conj ? 1 : 0, dst.kp,
                                                                (const int *)dst.exps.p, dst.ns, dst.bits,
                                                                (__nv_bfloat16 *)dst.planes.p, M * 2 * dst.kp);
   ADC_CHECK_LAUNCH();
