@@ -24,7 +24,8 @@ typedef struct adc_ctx adc_ctx_opaque;
  * long and narrow so that it is split along K; rel_err is then the largest of
  * the three), 4 = the six-product (BF16x6) tensor-core GEMM, 5 = the sliced
  * FP64-accurate tensor-core product of ADC_PREC_SLICED, including the slicing
- * of both operands) and compared with
+ * of both operands, 6 = the setup's route: zgemm as the sliced product with
+ * about 48 bits, in operand chunks (adc_diag_set_sliced_cap)) and compared with
  * the FP64 GEMM. Outputs: rel_err = ||C - C_fp64||_F / ||C_fp64||_F,
  * ms = average time of one launch sequence over `reps` repetitions (CUDA
  * events, after one warm-up). Allocates and frees its own device memory.
@@ -72,6 +73,13 @@ int adc_diag_set_wait_ns(uint64_t ns);
  * of its first virtual index); <= 0 restores the default of 2^28. Process-wide,
  * host only; affects contexts initialised afterwards. Returns ADC_OK. */
 int adc_diag_set_setup_chunk(int64_t elems);
+
+/* Test hook: bytes of one operand chunk of the sliced product behind the
+ * setup's large contractions (the digit planes of A row blocks and B column
+ * blocks; when one 128-row tile would exceed it, the inner index is split and
+ * the FP64-accurate partial products add up). <= 0 restores the rule of an
+ * eighth of the free memory (1 to 16 GiB). Process-wide. Returns ADC_OK. */
+int adc_diag_set_sliced_cap(int64_t bytes);
 
 /* 1 when the context forms its EA ladder integrals inside every product
  * (opts.ladder), else 0. ADC_ERR_STATE for a NULL context. */

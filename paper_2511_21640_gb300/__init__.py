@@ -122,6 +122,7 @@ def _load():
         "adc_diag_fp64_peak": (I, [I, I64, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "adc_diag_set_wait_ns": (I, [ctypes.c_uint64]),
         "adc_diag_set_setup_chunk": (I, [ctypes.c_int64]),
+        "adc_diag_set_sliced_cap": (I, [ctypes.c_int64]),
         "adc_diag_eigh": (I, [I, P, I, P, P, ctypes.POINTER(D), ctypes.POINTER(I)]),
         "adc_sigma_adjoint": (I, [P, P, P, I64, P, P, P, ctypes.POINTER(D)]),
         "adc_state_density": (I, [P, P, P]),

@@ -117,7 +117,7 @@ int diag_grouped(int64_t M, int64_t N, int64_t K, uint64_t seed, int reps, doubl
 
 extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_t seed, int reps,
                              double *rel_err, double *ms) {
-  if (M <= 0 || N <= 0 || K <= 0 || reps < 1 || which < 0 || which > 5) return ADC_ERR_ARG;
+  if (M <= 0 || N <= 0 || K <= 0 || reps < 1 || which < 0 || which > 6) return ADC_ERR_ARG;
   if (which == 3) return diag_grouped(M, N, K, seed, reps, rel_err, ms);
   Exec ex;
   try {
@@ -137,6 +137,11 @@ extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_
       auto run = [&]() {
         if (which == 5) {
           sl_gemm(ex, Sa, Sb, M, N, C1(), C0(), C.c(), N, 1, 0, 1, (int *)err.p, sw);
+        } else if (which == 6) {
+          // the setup's route: zgemm as the sliced product with 48 bits (operand chunks, inner splits)
+          ex.sliced_bits = 48;
+          zgemm(ex, M, N, K, 1, C1(), A.c(), 0, K, 1, false, B.c(), 0, 1, K, false, C0(), C.c(), 0, N, 1);
+          ex.sliced_bits = 0;
         } else if (which == 0) {
           zgemm(ex, M, N, K, 1, C1(), A.c(), 0, K, 1, false, B.c(), 0, 1, K, false, C0(), C.c(), 0, N, 1);
         } else if (which == 1 || which == 4) {
@@ -150,7 +155,7 @@ extern "C" int adc_diag_gemm(int which, int64_t M, int64_t N, int64_t K, uint64_
       if (which == 5) {
         sl_pack_A(ex, Sa, A.c(), M, K, K, 1, false, 40);
         sl_pack_B(ex, Sb, B.c(), N, K, K, 0, 1, 1, false, Sa);
-      } else if (which >= 1) {
+      } else if (which >= 1 && which != 6) {
         const int planes = which == 4 ? 3 : 2;
         tc_pack_A(ex, Ta, A.c(), M, K, K, 1, false, planes);
         tc_pack_B(ex, Tb, B.c(), N, K, K, 0, 1, 1, false, planes);
@@ -199,6 +204,11 @@ extern "C" int adc_profile_enable(adc_ctx *c, int on) {
   } catch (const Error &e) {
     return e.code;
   }
+}
+
+extern "C" int adc_diag_set_sliced_cap(int64_t bytes) {
+  set_sliced_cap_bytes(bytes > 0 ? (size_t)bytes : 0);
+  return ADC_OK;
 }
 
 extern "C" int adc_diag_set_setup_chunk(int64_t elems) {

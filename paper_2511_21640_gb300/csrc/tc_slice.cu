@@ -389,6 +389,10 @@ void sl_gemm(Exec &ex, const SlMat &A, const SlMat &B, int64_t M, int64_t N, cpl
 
 // zgemm's operands and output (element strides, conj flags, batch) through
 // the sliced product: used for large contractions when Exec::sliced_bits > 0
+// > 0: fixed bytes per operand chunk of zgemm_sliced instead of the free-memory rule (test hook)
+static size_t g_sliced_cap = 0;
+void set_sliced_cap_bytes(size_t bytes) { g_sliced_cap = bytes; }
+
 void zgemm_sliced(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx alpha, const cplx *A, int64_t sAb,
                   int64_t sAm, int64_t sAk, bool conjA, const cplx *B, int64_t sBb, int64_t sBk, int64_t sBn,
                   bool conjB, cplx beta, cplx *C, int64_t sCb, int64_t sCm, int64_t sCn) {
@@ -399,26 +403,41 @@ void zgemm_sliced(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx
   // the digit planes take 4 ns kp bytes per row of A and 8 ns kp per column
   // of B (ns slices of the real embedding): rows and columns in chunks whose
   // planes stay within an eighth of the free device memory per operand
-  // (between 1 and 16 GiB), so that B is sliced once where it fits
-  const SlParams sp = sl_params(K, ex.sliced_bits);
+  // (between 1 and 16 GiB), so that B is sliced once where it fits. When even
+  // one 128-row tile of A or 64 columns of B would exceed that, the inner
+  // index is split as well: the partial products (each FP64-accurate) add up
+  // in the output.
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
     cudaGetLastError();
     fr = (size_t)32 << 30;
   }
-  const size_t cap = std::min<size_t>((size_t)16 << 30, std::max<size_t>((size_t)1 << 30, fr / 8));
-  const int64_t mc = std::min<int64_t>(M, std::max<int64_t>(128, (int64_t)(cap / ((size_t)4 * sp.ns * sp.kp))));
-  const int64_t nc = std::min<int64_t>(N, std::max<int64_t>(64, (int64_t)(cap / ((size_t)8 * sp.ns * sp.kp))));
-  for (int64_t b = 0; b < batch; ++b) {
-    for (int64_t m0 = 0; m0 < M; m0 += mc) {
-      const int64_t mm = std::min(mc, M - m0);
-      sl_pack_A(ex, Sa, A + b * sAb + m0 * sAm, mm, K, sAm, sAk, conjA, ex.sliced_bits);
-      for (int64_t n0 = 0; n0 < N; n0 += nc) {
-        const int64_t nn = std::min(nc, N - n0);
-        // B once per batch entry when it fits in one chunk
-        if (nc < N || m0 == 0) sl_pack_B(ex, Sb, B + b * sBb + n0 * sBn, nn, K, sBn, 0, 1, sBk, conjB, Sa);
-        sl_gemm(ex, Sa, Sb, mm, nn, alpha, beta, C + b * sCb + m0 * sCm + n0 * sCn, sCm, sCn, 0, 1, (int *)err.p,
-                w);
+  const size_t cap =
+      g_sliced_cap ? g_sliced_cap : std::min<size_t>((size_t)16 << 30, std::max<size_t>((size_t)1 << 30, fr / 8));
+  int64_t kc = K;
+  {
+    const SlParams sp = sl_params(K, ex.sliced_bits);
+    const size_t per = (size_t)4 * sp.ns * sp.kp * 128;  // one A row tile (B: 64 columns, the same bytes)
+    if (per > cap) kc = std::max<int64_t>(512, (int64_t)((double)K * (double)cap / (double)per) / 64 * 64);
+  }
+  for (int64_t k0 = 0; k0 < K; k0 += kc) {
+    const int64_t kk = std::min(kc, K - k0);
+    const cplx beta_k = (k0 == 0) ? beta : C1();
+    const SlParams sp = sl_params(kk, ex.sliced_bits);
+    const int64_t mc = std::min<int64_t>(M, std::max<int64_t>(128, (int64_t)(cap / ((size_t)4 * sp.ns * sp.kp))));
+    const int64_t nc = std::min<int64_t>(N, std::max<int64_t>(64, (int64_t)(cap / ((size_t)8 * sp.ns * sp.kp))));
+    for (int64_t b = 0; b < batch; ++b) {
+      const cplx *Ab = A + b * sAb + k0 * sAk, *Bb = B + b * sBb + k0 * sBk;
+      for (int64_t m0 = 0; m0 < M; m0 += mc) {
+        const int64_t mm = std::min(mc, M - m0);
+        sl_pack_A(ex, Sa, Ab + m0 * sAm, mm, kk, sAm, sAk, conjA, ex.sliced_bits);
+        for (int64_t n0 = 0; n0 < N; n0 += nc) {
+          const int64_t nn = std::min(nc, N - n0);
+          // B once per batch entry and inner chunk when it fits in one chunk
+          if (nc < N || m0 == 0) sl_pack_B(ex, Sb, Bb + n0 * sBn, nn, kk, sBn, 0, 1, sBk, conjB, Sa);
+          sl_gemm(ex, Sa, Sb, mm, nn, alpha, beta_k, C + b * sCb + m0 * sCm + n0 * sCn, sCm, sCn, 0, 1,
+                  (int *)err.p, w);
+        }
       }
     }
   }

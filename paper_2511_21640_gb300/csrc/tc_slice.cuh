@@ -59,4 +59,7 @@ void zgemm_sliced(Exec &ex, int64_t M, int64_t N, int64_t K, int64_t batch, cplx
 void sl_gemm(Exec &ex, const SlMat &A, const SlMat &B, int64_t M, int64_t N, cplx alpha, cplx beta, cplx *out,
              int64_t s_m, int64_t s_nh, int64_t s_nl, int64_t n_in, int *err, SlWork &w);
 
+// test hook: bytes per operand chunk of zgemm_sliced (0 restores the free-memory rule)
+void set_sliced_cap_bytes(size_t bytes);
+
 }  // namespace adc

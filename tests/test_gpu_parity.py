@@ -85,6 +85,20 @@ def test_sliced_gemm(gpu, M, N, K):
     assert err < 1e-10, err
 
 
+@pytest.mark.parametrize("cap", [0, 3 << 20, 1 << 20])
+def test_sliced_setup_gemm_in_chunks(gpu, cap):
+    """The setup's sliced route (48 bits) with operand chunks of `cap` bytes:
+    A row blocks, B column blocks and, below one 128-row tile, inner splits
+    whose FP64-accurate partial products add up in the output."""
+    try:
+        assert gpu.lib.adc_diag_set_sliced_cap(cap) == 0
+        for M, N, K in ((300, 200, 3000), (129, 70, 9000)):
+            err, ms = gpu.diag_gemm(6, M, N, K, seed=11)
+            assert err < 1e-12, (M, N, K, err)
+    finally:
+        gpu.lib.adc_diag_set_sliced_cap(0)
+
+
 @pytest.mark.parametrize("M,N,K", [(128, 16, 64), (200, 40, 1000), (129, 130, 70), (1000, 300, 5000),
                                    (64, 8, 20000), (300, 1, 129)])
 def test_grouped_gemm_one_job(gpu, M, N, K):
