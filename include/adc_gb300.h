@@ -183,10 +183,10 @@ int adc_init(adc_ctx **ctx, const adc_c128 *B, int64_t naux,
 int adc_dims(const adc_ctx *ctx, int64_t *n1, int64_t *n2);
 
 /* S[r] = M X[r] for r < k (Eqs. 10-12). X, S: [k][N], host or device, not
- * overlapping. precision: ADC_PREC_FP64, ADC_PREC_BF16X3, ADC_PREC_BF16X6 or
+ * overlapping. precision: ADC_PREC_FP64, ADC_PREC_BF16X3, ADC_PREC_BF16X6,
  * ADC_PREC_SLICED (the FP64-accurate product from exact BF16 digit products
- * on the tensor cores). Uses scratch device memory owned by the context
- * (grown on demand). */
+ * on the tensor cores) or ADC_PREC_SLICED24 (its 24-bit form). Uses scratch
+ * device memory owned by the context (grown on demand). */
 int adc_sigma(adc_ctx *ctx, const adc_c128 *X, adc_c128 *S, int64_t k,
               int precision);
 
@@ -248,7 +248,9 @@ int adc_main_block(adc_ctx *ctx, adc_c128 *M11);
  * base vectors and later corrections come from the FP64 products. A result
  * is accepted only when every FP64 residual norm ||M y - omega y|| <= tol.
  * With opts.refine = ADC_PREC_SLICED those FP64 products (base, check) are
- * the sliced FP64-accurate tensor-core products instead.
+ * the sliced FP64-accurate tensor-core products instead, and once the
+ * refinement stalls twice the corrections take ADC_PREC_SLICED24 before the
+ * 40-bit product (st->sigma_calls_mid counts them).
  *   guess   NULL, or [nguess][N] starting vectors (nguess >= nroots).
  *   omega   [nroots] eigenvalues, ascending (host or device).
  *   Y       NULL or [nroots][N] eigenvectors.
