@@ -470,11 +470,13 @@ int davidson_run(adc_ctx *c, int nroots, double tol, int max_iter, int precision
     auto fit_of = [&](int kr) {
       return (int64_t)((0.92 * std::max(avail, 0.0) - (3.0 * nroots + 2.0 * kr) * vec - scratch) / (2.0 * vec));
     };
-    const int lo = (int)std::min<int64_t>(N, std::max(2 * nroots, kb) + kb);
+    int lo = (int)std::min<int64_t>(N, std::max(2 * nroots, kb) + kb);
     int64_t fit = fit_of(krmax);
-    // short of memory: keep fewer Ritz vectors at a collapse (thick restart of nroots)
+    // short of memory: keep only the wanted roots at a collapse (thick restart
+    // of nroots) and allow a subspace of nroots plus one block
     if (fit < lo) {
-      krmax = std::max(nroots, (kb + 1) / 2);
+      krmax = nroots;
+      lo = (int)std::min<int64_t>(N, nroots + kb);
       fit = fit_of(krmax);
     }
     if (fit < mmax) mmax = (int)std::max<int64_t>(fit, std::max(lo, std::min<int>((int)N, nroots + 1)));
