@@ -362,8 +362,10 @@ def run_batch(args, cfgname):
         probs = batch_problems(cfgname, select=ids)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctxs = [adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind=p.kind, order=p.order, x=p.x, setup=args.e2e_setup,
-                               refine=args.refine) for p in probs]
+        # the sliced setup; the batched solves refine in FP64 (the planner's waves
+        # leave no room for every problem's sliced operator copies)
+        ctxs = [adcgpu.Context(p.B, p.eps_occ, p.eps_vir, kind=p.kind, order=p.order, x=p.x, setup=args.e2e_setup)
+                for p in probs]
         for cx in ctxs:
             cx.sync()
         tot["init_s"] += time.perf_counter() - t0

@@ -534,7 +534,8 @@ typedef struct {
   int init_lanes;      /* concurrent adc_init calls, 0 = 4 */
   int verbose;
   int setup;           /* adc_opts.setup of every problem's adc_init (ADC_PREC_FP64 or ADC_PREC_SLICED) */
-  int refine;          /* adc_opts.refine of every problem (ADC_PREC_FP64 or ADC_PREC_SLICED) */
+  int refine;          /* adc_opts.refine of every problem (ADC_PREC_FP64 or ADC_PREC_SLICED;
+                          the waves then leave room for the sliced operator copies) */
 } adc_batch_opts;
 
 /* Host-only planner (no GPU needed): estimated device bytes mem_est[i] and

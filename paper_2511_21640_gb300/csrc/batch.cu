@@ -348,9 +348,10 @@ bool is_dev(const void *p) {
 }
 
 // device bytes a context of this problem holds after adc_init, plus its
-// split-precision copies, a Davidson run with nroots (subspace max(8 nroots,
-// 40)) and the batched-sigma scratch
-int64_t mem_estimate(const adc_problem &p, int nroots) {
+// split-precision copies (and, with the sliced refinement, the digit slices
+// of the same operators: about five times the split copies), a Davidson run
+// with nroots (subspace max(8 nroots, 40)) and the batched-sigma scratch
+int64_t mem_estimate(const adc_problem &p, int nroots, bool sliced = false) {
   const int64_t o = p.nocc, v = p.nvir, Q = p.naux, nmo = o + v;
   const int64_t pv = v * (v - 1) / 2, po = o * (o - 1) / 2;
   int64_t n1, n2;
@@ -365,8 +366,9 @@ int64_t mem_estimate(const adc_problem &p, int nroots) {
   const int64_t P = (p.kind == ADC_EA) ? pv : po;
   if (p.kind != ADC_EE) {
     if (sat) b += 16 * P * P;                   // packed ladder integrals
-    b += 4 * (n1 * 2 * ((n2 + 63) / 64 * 64) + n2 * 2 * ((n1 + 63) / 64 * 64));  // split copies of Cpl, CplT
-    if (sat) b += 4 * (P * 2 * ((P + 63) / 64 * 64) + o * v * 2 * ((o * v + 63) / 64 * 64));
+    int64_t split = 4 * (n1 * 2 * ((n2 + 63) / 64 * 64) + n2 * 2 * ((n1 + 63) / 64 * 64));  // Cpl, CplT
+    if (sat) split += 4 * (P * 2 * ((P + 63) / 64 * 64) + o * v * 2 * ((o * v + 63) / 64 * 64));
+    b += split + (sliced ? 5 * split : 0);
   }
   const int64_t m = std::max<int64_t>(8 * nroots, 40);
   b += 32 * m * N + 16 * 6 * nroots * N;        // V, AV, Davidson work vectors
@@ -558,15 +560,23 @@ const char *adc_batch_last_error(const adc_batch *b) {
   return g_batch_error.c_str();
 }
 
+static int plan_waves(int n, const adc_problem *p, int nroots, int64_t mem_budget, int *order, int *wave,
+                      int64_t *mem_est, double *cost_est, bool sliced);
+
 int adc_batch_plan(int n, const adc_problem *p, int nroots, int64_t mem_budget, int *order, int *wave,
                    int64_t *mem_est, double *cost_est) {
+  return plan_waves(n, p, nroots, mem_budget, order, wave, mem_est, cost_est, false);
+}
+
+static int plan_waves(int n, const adc_problem *p, int nroots, int64_t mem_budget, int *order, int *wave,
+                      int64_t *mem_est, double *cost_est, bool sliced) {
   if (n < 0 || (n > 0 && (!p || !order || !wave)) || nroots < 1 || mem_budget <= 0) return ADC_ERR_ARG;
   std::vector<int64_t> mem(n);
   std::vector<double> cost(n);
   for (int i = 0; i < n; ++i) {
     if (p[i].nocc < 1 || p[i].nvir < 1 || p[i].naux < 1) return ADC_ERR_ARG;
     if (p[i].kind != ADC_IP && p[i].kind != ADC_EA && p[i].kind != ADC_EE) return ADC_ERR_ARG;
-    mem[i] = mem_estimate(p[i], nroots);
+    mem[i] = mem_estimate(p[i], nroots, sliced);
     cost[i] = cost_estimate(p[i], nroots);
     if (mem_est) mem_est[i] = mem[i];
     if (cost_est) cost_est[i] = cost[i];
@@ -603,7 +613,7 @@ int adc_batch_solve(int n, const adc_problem *p, int nroots, double tol, int max
     budget = (int64_t)(0.85 * (double)fr);
   }
   std::vector<int> order(n), wave(n);
-  int nw = adc_batch_plan(n, p, nroots, budget, order.data(), wave.data(), nullptr, nullptr);
+  int nw = plan_waves(n, p, nroots, budget, order.data(), wave.data(), nullptr, nullptr, o.refine == ADC_PREC_SLICED);
   if (nw < 0) return bfail(nullptr, "adc_batch_solve: invalid problem sizes", nw);
   adc_batch_info acc{};
   int worst = ADC_OK;
