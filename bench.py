@@ -113,7 +113,10 @@ class Clocks:
 THREE_M = ("zgemm", "gram", "combine")
 # k_gram<32, 8, 4, 2, 32> on 32 x 8 vectors of n = 796200 (one launch, ncu): 510,109,184 B read +
 # 4,893,696 B written against (32 + 8) * 796200 * 16 + 32 * 8 * 16 = 509,572,096 algorithmic bytes
-GRAM_DRAM_RATIO = (510109184 + 4893696) / ((32 + 8) * 796200 * 16 + 32 * 8 * 16)  # FP64 kernels whose complex products take 3 real products
+GRAM_DRAM_RATIO = (510109184 + 4893696) / ((32 + 8) * 796200 * 16 + 32 * 8 * 16)
+# k_combine<8>, 32 inputs to 8 outputs of n = 796200 (one launch, ncu): 407,728,128 B read + 82,273,792 B
+# written against (32 + 8) * 796200 * 16 algorithmic bytes
+COMBINE_DRAM_RATIO = (407728128 + 82273792) / ((32 + 8) * 796200 * 16)  # FP64 kernels whose complex products take 3 real products
 
 
 def fp64_peak(adcgpu):
@@ -896,7 +899,9 @@ def main():
     # kernels whose launches differ in shape: DRAM bytes over algorithmic bytes of one
     # captured launch (ncu), times this run's algorithmic bytes per launch
     traffic_ratio = {"gram_fp64": (GRAM_DRAM_RATIO, "ncu capture of one k_gram launch, 32 x 8 vectors of "
-                                                    "n = 796200: DRAM bytes / algorithmic bytes")}
+                                                    "n = 796200: DRAM bytes / algorithmic bytes"),
+                     "combine_fp64": (COMBINE_DRAM_RATIO, "ncu capture of one k_combine launch, 32 to 8 vectors "
+                                                          "of n = 796200: DRAM bytes / algorithmic bytes")}
     base = roof["kernel"].split("/")[0]
     if roof["traffic"] is None and base in traffic_ratio and roof.get("algorithmic_bytes_per_launch"):
         ratio, note = traffic_ratio[base]
