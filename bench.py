@@ -469,7 +469,7 @@ def run_batch(args, cfgname):
         "e2e": {"value": (tot["init_s"] + tot["solve_s"]) / roots, "unit": "s/root",
                 "h2d_bytes_per_step": int(sum(16 * d["naux"] * (d["nocc"] + d["nvir"]) ** 2 for d in sizes)),
                 "d2h_bytes_per_step": int(16 * roots),
-                "includes": "adc_init of every problem (H2D copy + FP64 operator setup) + batched Davidson"},
+                "includes": f"adc_init of every problem (H2D copy + {args.e2e_setup} operator setup) + batched Davidson"},
         "gpu_launches": int(tot.get("launches", 0)), "cpu_baseline": None,
     }
     print(json.dumps(line))
