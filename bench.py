@@ -110,13 +110,13 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-THREE_M = ("zgemm", "gram", "combine")
+THREE_M = ("zgemm", "gram", "combine")  # FP64 kernels whose complex products take 3 real products
 # k_gram<32, 8, 4, 2, 32> on 32 x 8 vectors of n = 796200 (one launch, ncu): 510,109,184 B read +
 # 4,893,696 B written against (32 + 8) * 796200 * 16 + 32 * 8 * 16 = 509,572,096 algorithmic bytes
 GRAM_DRAM_RATIO = (510109184 + 4893696) / ((32 + 8) * 796200 * 16 + 32 * 8 * 16)
 # k_combine<8>, 32 inputs to 8 outputs of n = 796200 (one launch, ncu): 407,728,128 B read + 82,273,792 B
 # written against (32 + 8) * 796200 * 16 algorithmic bytes
-COMBINE_DRAM_RATIO = (407728128 + 82273792) / ((32 + 8) * 796200 * 16)  # FP64 kernels whose complex products take 3 real products
+COMBINE_DRAM_RATIO = (407728128 + 82273792) / ((32 + 8) * 796200 * 16)
 
 
 def fp64_peak(adcgpu):
@@ -162,9 +162,9 @@ def _pair(p, q, n):
 # Sigma vectors per root that the plain FP64 block Davidson (the CPU oracle's
 # algorithm, run on the GPU in FP64) spends on each workload to the bench's
 # residual tolerance; both oracle legs scale seconds per sigma row to seconds
-# per root with the same number. Measured: ea2x3, 302 FP64 sigma vectors for
-# 8 roots (tol 1e-5); the EE workloads use their mixed solves' counts.
-ORACLE_SIGMA_VECTORS_PER_ROOT = {"ea2x3_o40_v200_q1200": 37.75, "ee2x3_o30_v150_q900": 110.0,
+# per root with the same number. Measured: ea2x3, 333 FP64 sigma vectors for
+# 8 roots (its tolerance, 1e-6); the EE workloads use their mixed solves' counts.
+ORACLE_SIGMA_VECTORS_PER_ROOT = {"ea2x3_o40_v200_q1200": 41.625, "ee2x3_o30_v150_q900": 110.0,
                                  "ee3_o60_v300_q1800": 40.0}
 
 
