@@ -145,6 +145,29 @@ def alu_row(name, e, peak64, peak_kind):
             "algorithmic_bytes_per_launch": e.get("bytes", 0.0) / e["launches"], "launches": e["launches"]}
 
 
+def attach_traffic(roof, config):
+    """roof["traffic"]: DRAM bytes per launch of the dominant kernel from an ncu
+    capture. A capture of the same launch shape is kept only for the kernel and
+    workload it was taken on; for kernels whose launches differ in shape the
+    captured launch's DRAM bytes over its algorithmic bytes scale this run's
+    algorithmic bytes per launch."""
+    measured_traffic = {("ea2x3_o40_v200_q1200", "zgemm_fp64/ladder"): 7.795e9}
+    key = (config, roof["kernel"])
+    if key in measured_traffic:
+        roof["traffic"] = measured_traffic[key]
+        roof["traffic_note"] = "one ncu capture of the 320 x 19900 x 19900 FP64 ladder GEMM"
+    traffic_ratio = {"gram_fp64": (GRAM_DRAM_RATIO, "ncu capture of one k_gram launch, 32 x 8 vectors of "
+                                                    "n = 796200: DRAM bytes / algorithmic bytes"),
+                     "combine_fp64": (COMBINE_DRAM_RATIO, "ncu capture of one k_combine launch, 32 to 8 vectors "
+                                                          "of n = 796200: DRAM bytes / algorithmic bytes")}
+    base = roof["kernel"].split("/")[0]
+    if roof.get("traffic") is None and base in traffic_ratio and roof.get("algorithmic_bytes_per_launch"):
+        ratio, note = traffic_ratio[base]
+        roof["traffic"] = ratio * roof["algorithmic_bytes_per_launch"]
+        roof["traffic_note"] = f"{note} = {ratio:.3f}, scaled to this run's launches"
+    return roof
+
+
 def sigma_flops_formula(o, v, Q, k):
     """Algorithmic flops of one EA sigma block of k vectors as the library forms it
     (8 per complex multiply-add): coupling both ways (2 v n2 k), ladder over packed
@@ -889,24 +912,7 @@ def main():
     by_kernel = sorted((roofline_of(k, e) for k, e in prof.items() if e["launches"] > 0),
                        key=lambda r: -r["avg_launch_ms"] * r["launches"])
     roof = by_kernel[0]
-    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an ncu capture of the
-    # same launch shape; kept only for the kernel and workload it was taken on
-    measured_traffic = {("ea2x3_o40_v200_q1200", "zgemm_fp64/ladder"): 7.795e9}
-    key = (args.config, roof["kernel"])
-    if key in measured_traffic:
-        roof["traffic"] = measured_traffic[key]
-        roof["traffic_note"] = "one ncu capture of the 320 x 19900 x 19900 FP64 ladder GEMM"
-    # kernels whose launches differ in shape: DRAM bytes over algorithmic bytes of one
-    # captured launch (ncu), times this run's algorithmic bytes per launch
-    traffic_ratio = {"gram_fp64": (GRAM_DRAM_RATIO, "ncu capture of one k_gram launch, 32 x 8 vectors of "
-                                                    "n = 796200: DRAM bytes / algorithmic bytes"),
-                     "combine_fp64": (COMBINE_DRAM_RATIO, "ncu capture of one k_combine launch, 32 to 8 vectors "
-                                                          "of n = 796200: DRAM bytes / algorithmic bytes")}
-    base = roof["kernel"].split("/")[0]
-    if roof["traffic"] is None and base in traffic_ratio and roof.get("algorithmic_bytes_per_launch"):
-        ratio, note = traffic_ratio[base]
-        roof["traffic"] = ratio * roof["algorithmic_bytes_per_launch"]
-        roof["traffic_note"] = f"{note} = {ratio:.3f}, scaled to this run's launches"
+    attach_traffic(roof, args.config)
     tc_rows = [r for r in by_kernel if r["kernel"].startswith("tc_")]
     roof_tc = tc_rows[0] if tc_rows else None
 

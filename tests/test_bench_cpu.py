@@ -1,0 +1,81 @@
+"""Host-side pieces of bench.py, without a GPU: the FP64 roofline rows, the
+DRAM traffic attached to the dominant kernel, the algorithmic sigma flop
+count, and the reference arm's JSON line (the CPU oracle on the small IP-ADC(3)
+workload)."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _entry(name, launches, ms, flops, nbytes):
+    return {"name": name, "launches": launches, "total_ms": ms, "flops": flops, "bytes": nbytes}
+
+
+def test_alu_row_rates_and_bytes():
+    # 10 launches of 1 ms, 1.2e9 algorithmic flops each: 1.2 TFLOP/s
+    e = _entry("combine_fp64", 10, 10.0, 1.2e10, 5.0e9)
+    r = bench.alu_row("combine_fp64", e, 1.25, "test")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 1.2) < 1e-12
+    assert abs(r["frac"] - 1.2 / 1.25) < 1e-12
+    # 3M products execute 6 of the 8 algorithmic flops
+    assert abs(r["executed_frac"] - 0.75 * 1.2 / 1.25) < 1e-12
+    assert abs(r["algorithmic_bytes_per_launch"] - 5.0e8) < 1e-3
+    # a kernel outside the 3M set executes what it counts
+    r2 = bench.alu_row("other_fp64", e, 1.25, "test")
+    assert abs(r2["executed_frac"] - r2["frac"]) < 1e-15
+
+
+@pytest.mark.parametrize("kernel,ratio", [("combine_fp64", bench.COMBINE_DRAM_RATIO),
+                                          ("gram_fp64/extend", bench.GRAM_DRAM_RATIO)])
+def test_traffic_scaled_from_the_captured_ratio(kernel, ratio):
+    roof = {"kernel": kernel, "traffic": None, "algorithmic_bytes_per_launch": 4.0e8}
+    bench.attach_traffic(roof, "ea2x3_o40_v200_q1200")
+    assert abs(roof["traffic"] - ratio * 4.0e8) < 1e-3
+    assert "scaled" in roof["traffic_note"]
+    # the captured launches read each operand byte about once
+    assert 0.9 < ratio < 1.1
+
+
+def test_traffic_kept_only_where_captured():
+    roof = {"kernel": "zgemm_fp64/ladder", "traffic": None, "algorithmic_bytes_per_launch": 1.0}
+    bench.attach_traffic(roof, "ea2x3_o40_v200_q1200")
+    assert roof["traffic"] == 7.795e9
+    other = {"kernel": "zgemm_fp64/ladder", "traffic": None, "algorithmic_bytes_per_launch": 1.0}
+    bench.attach_traffic(other, "ee2x3_o30_v150_q900")
+    assert other["traffic"] is None
+    tc = {"kernel": "tc_grouped_bf16x3/grouped", "traffic": None, "algorithmic_bytes_per_launch": 1.0}
+    bench.attach_traffic(tc, "ea2x3_o40_v200_q1200")
+    assert tc["traffic"] is None
+
+
+def test_sigma_flops_formula_terms():
+    o, v, k = 40, 200, 8
+    pv = v * (v - 1) // 2
+    n2 = o * pv
+    expect = 8.0 * (2 * v * n2 * k + pv * pv * o * k + (o * v) ** 2 * v * k + v * v * k)
+    assert bench.sigma_flops_formula(o, v, 1200, k) == expect
+    # the bench workload's block of 8 vectors, as reported by the GPU runs
+    assert abs(bench.sigma_flops_formula(o, v, 1200, k) - 1.853e12) / 1.853e12 < 1e-3
+
+
+def test_reference_arm_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--config", "ip3_o8_v24_q96", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = [ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1]
+    d = json.loads(line)
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["higher_is_better"] is False and d["unit"] == "s/root"
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"] == "ip3_o8_v24_q96"
