@@ -250,17 +250,22 @@ def test_p4_ee_error_order_against_fci():
     p = make_problem(o, v, 5, seed=21, sigma=0.35)
     eps = _eps(p)
     lams = np.array([0.02, 0.04, 0.08])
-    errs = {2: [], 3: [], "x": []}
+    errs = {2: [], 3: [], "x": [], "dd0": []}
     for lam in lams:
         w = fci_energies(eps, p.B, o, lam, o, nroots=2)
         exact = w[1] - w[0]
         Bl = np.sqrt(lam) * p.B
-        for key, (order, x) in {2: (2, 0.0), 3: (3, 1.0), "x": (3, 0.5)}.items():
-            M = adc_ee.explicit_matrix(order, x, Bl, p.eps_occ, p.eps_vir)
+        for key, (order, x, dd) in {2: (2, 0.0, 1), 3: (3, 1.0, 1), "x": (3, 0.5, 1), "dd0": (3, 1.0, 0)}.items():
+            M = adc_ee.explicit_matrix(order, x, Bl, p.eps_occ, p.eps_vir, dd_order=dd)
             errs[key].append(abs(np.linalg.eigvalsh(M)[0] - exact))
     assert 2.8 < np.polyfit(np.log(lams), np.log(errs[2]), 1)[0] < 3.2
     assert 3.7 < np.polyfit(np.log(lams), np.log(errs[3]), 1)[0] < 4.3
     assert abs(errs["x"][0] / errs[2][0] - 0.5) < 0.05
+    # ADC(3) with the doubles-doubles block kept at zeroth order: the missing
+    # first-order D/D term reaches the singles through two couplings, an
+    # O(lambda^3) error, so the slope drops back to 3 (not ADC(2)'s error either)
+    assert 2.8 < np.polyfit(np.log(lams), np.log(errs["dd0"]), 1)[0] < 3.2
+    assert abs(errs["dd0"][0] / errs[2][0] - 1.0) > 0.2
 
 
 @pytest.mark.parametrize("order,x,dd", [(3, 1.0, 1), (3, 0.4, 1), (3, 1.0, 0), (2, 0.0, 1)])
