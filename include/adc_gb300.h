@@ -2,9 +2,9 @@
  * adc_gb300.h -- C ABI of the GB300 relativistic CD-ADC sigma library.
  *
  * The library computes the matrix-free product S = M X of the ISR secular
- * matrix M of IP-ADC (1h + 2h1p) and EA-ADC (1p + 2p1h) at second order,
- * third order, or the scaled ADC(2)+x(3) mixture (Sec. 2.1, Eqs. 10-12 of
- * arXiv:2511.21640), solves M X = X Omega for the lowest roots by a block
+ * matrix M of IP-ADC (1h + 2h1p), EA-ADC (1p + 2p1h) and EE-ADC (1h1p +
+ * 2h2p) at second order, third order, or the scaled ADC(2)+x(3) mixture
+ * (Sec. 2.1, Eqs. 10-12 of arXiv:2511.21640), solves M X = X Omega for the lowest roots by a block
  * Davidson method, and builds the MP2 virtual density and frozen natural
  * spinors (Sec. 2.4, Eqs. 25-30). Antisymmetrised integrals are assembled on
  * the device from Cholesky vectors, <pq||rs> = sum_Q (B_pr B_qs - B_ps B_qr)
@@ -85,7 +85,7 @@ enum {
   ADC_ERR_CUDA = -3,        /* a CUDA runtime call failed */
   ADC_ERR_NOCONV = -4,      /* Davidson did not converge; best results returned */
   ADC_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
-  ADC_ERR_UNSUPPORTED = -6, /* combination not built (e.g. the adjoint of IP/EA) */
+  ADC_ERR_UNSUPPORTED = -6, /* combination not built (e.g. adc_sigma_noalloc on an EE context) */
   ADC_ERR_STATE = -7,       /* context not initialised / unusable */
   ADC_ERR_NUMERIC = -8      /* NaN or Inf met in a residual or input */
 };
@@ -95,9 +95,12 @@ typedef struct {
   void *stream;         /* cudaStream_t to run on; NULL = the context's own */
   int block;            /* Davidson block size (new vectors per iteration), 0 = nroots */
   int max_subspace;     /* Davidson subspace limit, 0 = automatic: 8 x the
-                           block (at least 40), lowered so that the subspace
-                           and its products take at most half of the device
-                           memory free once the operators are built */
+                           block (at least 40), lowered to what the device
+                           memory left once the operators are built holds
+                           after the Davidson's other vectors, an estimate of
+                           one product's scratch and an 8% margin (short of
+                           memory: nroots plus one block, keeping nroots Ritz
+                           vectors at a collapse) */
   double herm_tol;      /* relative tolerance of the Hermiticity check of B */
   int64_t mem_limit;    /* bytes the context may allocate, 0 = no limit */
   int verbose;          /* 1 = per-iteration lines on stderr */
