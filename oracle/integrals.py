@@ -23,7 +23,7 @@ import numpy as np
 
 ein = np.einsum
 
-__all__ = ["eri", "Amplitudes"]
+__all__ = ["eri", "Amplitudes", "semicanonical"]
 
 
 def eri(B, nocc, spec):
@@ -86,3 +86,24 @@ class Amplitudes:
     def mp2_energy(self):
         """E2 = 1/4 sum_ijab <ij||ab> t_ij^ab."""
         return 0.25 * ein("ijab,ijab->", eri(self.B, self.nocc, "oovv"), self.t1)
+
+
+def semicanonical(F_occ, F_vir, B):
+    """Problem in the semicanonical basis, from full Fock blocks.
+
+    The method takes a diagonal Fock matrix. A reference whose occupied-occupied
+    and virtual-virtual Fock blocks are not diagonal (a rotated basis) is
+    brought to that form as the natural-spinor basis is in Sec. 2.4 (Eq. 29):
+    each block is diagonalised on its own, F_oo Z_o = Z_o eps_o and
+    F_vv Z_v = Z_v eps_v (eigenvalues ascending), and the Cholesky vectors
+    follow the same rotation W = diag(Z_o, Z_v) as in Eq. 42:
+    B'[Q] = W^H B[Q] W. Returns (eps_occ, eps_vir, B').
+    """
+    eo, Zo = np.linalg.eigh(np.asarray(F_occ))
+    ev, Zv = np.linalg.eigh(np.asarray(F_vir))
+    o, v = Zo.shape[0], Zv.shape[0]
+    W = np.zeros((o + v, o + v), dtype=np.complex128)
+    W[:o, :o] = Zo
+    W[o:, o:] = Zv
+    Bs = ein("pi,Qpq,qj->Qij", W.conj(), B, W)
+    return eo, ev, Bs

@@ -9,7 +9,7 @@ import pytest
 
 from synthetic import make_problem, random_vectors
 from oracle import adc
-from oracle.integrals import Amplitudes, eri
+from oracle.integrals import Amplitudes, eri, semicanonical
 from oracle.isr_series import (antisym_eri_dense, isr_series, fci_energies,
                                mp1_density_bruteforce, FockSpace, rspt_ground_state)
 from oracle import isr_series as isr_mod
@@ -166,6 +166,43 @@ def test_p6a_unitary_invariance_within_degenerate_groups(kind):
         w0 = np.linalg.eigvalsh(adc.explicit_matrix(kind, order, x, p.B, eo, ev))
         w1 = np.linalg.eigvalsh(adc.explicit_matrix(kind, order, x, Br, eo, ev))
         assert np.abs(w0 - w1).max() < 1e-12
+
+
+def _random_block_unitary(o, v, rng):
+    W = np.zeros((o + v, o + v), dtype=np.complex128)
+    for s, n in ((slice(0, o), o), (slice(o, o + v), v)):
+        q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+        W[s, s] = q
+    return W
+
+
+@pytest.mark.parametrize("kind", ["IP", "EA", "EE"])
+def test_p6b_full_fock_blocks_semicanonicalised(kind):
+    """Non-degenerate orbital energies, the basis rotated by a random unitary
+    within the occupied and within the virtual spinors: the Fock blocks are
+    then full. Semicanonicalising them (and rotating B the same way) must give
+    back the original eigenvalues; keeping only the diagonal of the rotated
+    Fock matrix must not (so the check is not trivially met)."""
+    o, v, Q = 3, 5, 7
+    rng = np.random.default_rng(23)
+    p = make_problem(o, v, Q, seed=29, sigma=0.2)
+    U = _random_block_unitary(o, v, rng)
+    Br = np.einsum("pi,Qpq,qj->Qij", U.conj(), p.B, U)
+    F = U.conj().T @ np.diag(np.concatenate([p.eps_occ, p.eps_vir])) @ U
+    eo, ev, Bs = semicanonical(F[:o, :o], F[o:, o:], Br)
+    assert np.abs(eo - p.eps_occ).max() < 1e-13 and np.abs(ev - p.eps_vir).max() < 1e-13
+
+    def spectrum(B, e_o, e_v, order, x):
+        M = (adc_ee.explicit_matrix(order, x, B, e_o, e_v) if kind == "EE"
+             else adc.explicit_matrix(kind, order, x, B, e_o, e_v))
+        return np.linalg.eigvalsh(M)
+
+    for order, x in [(2, 0.0), (3, 0.5), (3, 1.0)]:
+        w0 = spectrum(p.B, p.eps_occ, p.eps_vir, order, x)
+        w1 = spectrum(Bs, eo, ev, order, x)
+        assert np.abs(w0 - w1).max() < 1e-12 * max(1.0, np.abs(w0).max()), (order, x)
+    wd = spectrum(Br, np.diag(F)[:o].real, np.diag(F)[o:].real, 3, 1.0)
+    assert np.abs(spectrum(p.B, p.eps_occ, p.eps_vir, 3, 1.0) - wd).max() > 1e-3
 
 
 # ---------------------------------------------------------------- P7 (Eq. 25)
