@@ -61,6 +61,25 @@ def test_p2_noninteracting_limit(kind):
     assert np.abs(w - np.sort(ref)).max() < 1e-14
 
 
+@pytest.mark.parametrize("dd", [1, 0])
+def test_p2_ee_noninteracting_limit(dd):
+    """B = 0: the EE matrix is the orbital-energy differences, eps_a - eps_i
+    for the singles and eps_a + eps_b - eps_i - eps_j for the doubles (i<j,
+    a<b), at every order and for both doubles-block orders."""
+    from oracle import adc_ee
+    o, v = 3, 4
+    p = make_problem(o, v, 4, seed=2)
+    eo, ev = p.eps_occ, p.eps_vir
+    io, jo = np.triu_indices(o, 1)
+    av, bv = np.triu_indices(v, 1)
+    ref = np.sort(np.concatenate([(ev[None, :] - eo[:, None]).ravel(),
+                                  ((ev[av] + ev[bv])[None, :] - (eo[io] + eo[jo])[:, None]).ravel()]))
+    for order, x in [(2, 0.0), (3, 0.5), (3, 1.0)]:
+        M = adc_ee.explicit_matrix(order, x, np.zeros_like(p.B), eo, ev, dd_order=dd)
+        assert np.abs(M - np.diag(np.diag(M))).max() == 0.0
+        assert np.abs(np.sort(np.linalg.eigvalsh(M)) - ref).max() < 1e-14, (order, x)
+
+
 # ---------------------------------------------------------------- P3
 def test_p3_mp2_energy_matches_rayleigh_schroedinger():
     o, v = 3, 5
