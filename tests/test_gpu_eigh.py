@@ -87,7 +87,9 @@ def test_eigh_degenerate_and_close(gpu, which, case):
 def test_eigh_refined_is_faster(gpu):
     """At the Davidson's usual subspace size the refined solver beats the FP64 Jacobi."""
     A = _hermitian(64, seed=90)
-    _, _, t0, _ = gpu.diag_eigh(0, A)
-    _, _, t1, _ = gpu.diag_eigh(1, A)
+    # best of three calls each, so that one-time costs (module loading) and a
+    # busy moment on the device do not decide the comparison
+    t0 = min(gpu.diag_eigh(0, A)[2] for _ in range(3))
+    t1 = min(gpu.diag_eigh(1, A)[2] for _ in range(3))
     print(f"n = 64: FP64 Jacobi {t0:.3f} ms, FP32 start + FP64 refinement {t1:.3f} ms")
     assert t1 < t0
