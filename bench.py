@@ -885,6 +885,11 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     launches = adcgpu.launch_count() - l0
+    if dist:
+        # kernels of all replicas
+        tl = torch.tensor([launches], dtype=torch.int64, device="cuda")
+        dist.all_reduce(tl, op=dist.ReduceOp.SUM)
+        launches = int(tl.item())
     log(f"timed {ms:.1f} ms for {args.steps} steps")
     prof = ctx.profile_read()
     ctx.profile(False)
