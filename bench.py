@@ -168,6 +168,18 @@ def attach_traffic(roof, config):
     return roof
 
 
+def reduce_across(values, op):
+    """All-reduce numbers over the process group of the replicas: "max" (the
+    slowest replica's times) or "sum" (counts of all replicas). NCCL takes
+    device tensors, gloo host ones. Returns a list of floats."""
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "sum": dist.ReduceOp.SUM}[op])
+    return [float(a) for a in t.tolist()]
+
+
 def sigma_flops_formula(o, v, Q, k):
     """Algorithmic flops of one EA sigma block of k vectors as the library forms it
     (8 per complex multiply-add): coupling both ways (2 v n2 k), ladder over packed
@@ -880,16 +892,11 @@ def main():
     nvtx_range("timed", False)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     launches = adcgpu.launch_count() - l0
     if dist:
-        # kernels of all replicas
-        tl = torch.tensor([launches], dtype=torch.int64, device="cuda")
-        dist.all_reduce(tl, op=dist.ReduceOp.SUM)
-        launches = int(tl.item())
+        # whole job: the slowest replica's time, the kernels of all replicas
+        ms = reduce_across([ms], "max")[0]
+        launches = int(reduce_across([launches], "sum")[0])
     log(f"timed {ms:.1f} ms for {args.steps} steps")
     prof = ctx.profile_read()
     ctx.profile(False)
@@ -1000,9 +1007,7 @@ def main():
         te2e, ti2e = time.perf_counter() - t2, t3 - t2
         if dist:
             # whole job: the slowest replica's time for the roots of all replicas
-            tt = torch.tensor([te2e, ti2e], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te2e, ti2e = (float(a) for a in tt.tolist())
+            te2e, ti2e = reduce_across([te2e, ti2e], "max")
         log(f"e2e {te2e:.1f} s (init {ti2e:.1f} s)")
         ref_om = om64 if fp64 is not None else om
         e2e = {"value": te2e / (nroots * world), "unit": "s/root",

@@ -1,7 +1,8 @@
 """Host-side pieces of bench.py, without a GPU: the FP64 roofline rows, the
 DRAM traffic attached to the dominant kernel, the algorithmic sigma flop
-count, and the reference arm's JSON line (the CPU oracle on the small IP-ADC(3)
-workload)."""
+count, the reference arm's JSON line (the CPU oracle on the small IP-ADC(3)
+workload), and the reductions that turn several replicas' figures into
+whole-job ones (gloo ranks on CPU)."""
 import json
 import os
 import subprocess
@@ -79,3 +80,34 @@ def test_reference_arm_line():
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "ip3_o8_v24_q96"
+
+
+def _reduce_rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # each replica's step time, launch count and end-to-end times
+        mx = bench.reduce_across([10.0 + rank, 3.5 * (world - rank)], "max")
+        sm = bench.reduce_across([100 + rank], "sum")
+        out[rank] = (mx, sm)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_reduce_across_replicas_on_gloo(world):
+    """The whole-job figures of several replicas: the slowest replica's times
+    and the sum of their kernel launches, the same on every rank."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = mp.Manager().dict()
+    mp.spawn(_reduce_rank, args=(world, port, out), nprocs=world, join=True)
+    for r in range(world):
+        mx, sm = out[r]
+        assert mx == [10.0 + world - 1, 3.5 * world]
+        assert sm == [float(sum(100 + q for q in range(world)))]
