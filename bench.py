@@ -360,6 +360,55 @@ def cpu_baseline_of(sample, N, spr, spr_note, kind):
             "blas": _blas_name()}
 
 
+ORACLE_SOLVE_MAX_N = 5000  # the oracle's whole Davidson runs on workloads up to this dimension
+
+
+def oracle_solve_feasible(cfgname):
+    c = CONFIGS.get(cfgname)
+    return c is not None and _dim(c["kind"], c["nocc"], c["nvir"]) <= ORACLE_SOLVE_MAX_N
+
+
+def oracle_davidson_baseline(cfgname):
+    """The oracle's whole FP64 solve of a small workload, in this process, not
+    extrapolated: its ground-state amplitudes and exact diagonal, then its
+    block Davidson (FP64 sigma_ref products) to the workload's residual
+    tolerance. Seconds per root of that wall time; the threads are numpy's
+    defaults (BLAS on every host core, the einsum contractions on one), and
+    the process CPU time over the wall time says how many were busy."""
+    from oracle import adc, adc_ee
+    from oracle.davidson import davidson
+    c = CONFIGS[cfgname]
+    p = config_problem(cfgname)
+    kind, order, x, nroots, tol = c["kind"], c["order"], c["x"], c["nroots"], c.get("tol", 1e-8)
+    dd = c.get("dd_order", 1)
+    calls = [0]
+    w0, c0 = time.perf_counter(), time.process_time()
+    if kind == "EE":
+        T = adc_ee.Tensors(p.B, p.eps_occ, p.eps_vir)
+        diag = adc_ee.diagonal_ref(order, x, p.B, p.eps_occ, p.eps_vir, dd_order=dd, T=T)
+
+        def sig(V):
+            calls[0] += V.shape[0]
+            return adc_ee.sigma_ref(order, x, p.B, p.eps_occ, p.eps_vir, V, dd_order=dd, T=T)
+    else:
+        amp = adc.Amplitudes(p.B, p.eps_occ, p.eps_vir, second_order=(order == 3))
+        diag = adc.diagonal_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, amp=amp)
+
+        def sig(V):
+            calls[0] += V.shape[0]
+            return adc.sigma_ref(kind, order, x, p.B, p.eps_occ, p.eps_vir, V, amp=amp)
+    w, _, rn, it = davidson(sig, diag, diag.shape[0], nroots, tol=tol, max_iter=300)
+    wall, cpu_s = time.perf_counter() - w0, time.process_time() - c0
+    cores = os.cpu_count() or 1
+    return {"value": wall / nroots, "unit": "s/root", "cores": cores, "kind": "oracle",
+            "sample": (f"the whole workload: the oracle's FP64 block Davidson (sigma_ref products, exact "
+                       f"diagonal) for {nroots} roots to a residual of {tol:g}, {it} iterations, {calls[0]} "
+                       f"sigma vectors, {wall:.1f} s wall including its amplitudes; not extrapolated"),
+            "wall_s": wall, "effective_threads": cpu_s / max(wall, 1e-9), "host_cores": cores,
+            "blas": _blas_name(), "iterations": it, "sigma_vectors": calls[0],
+            "omega": [float(a) for a in w], "max_residual": float(np.max(rn))}
+
+
 def sampled_parity(ctx, sample, precisions):
     """The GPU sigma of the sampled vector, in each precision, at the rows the
     oracle computed: largest absolute difference and that over the largest
@@ -684,6 +733,26 @@ def run_reference(args, cfgname):
         o, v, q = c["nocc"], c["nvir"], c["naux"]
     kind, dd_order = c["kind"], c.get("dd_order", 1)
     N = _dim(kind, o, v)
+    if spec[0] == "config" and oracle_solve_feasible(cfgname):
+        # small enough for the oracle's whole solve: every step is one solve
+        for _ in range(args.warmup):
+            import oracle.davidson  # noqa: F401
+        runs = [oracle_davidson_baseline(cfgname) for _ in range(max(args.steps, 1))]
+        cpu = dict(runs[-1])
+        cpu["value"] = float(np.mean([r["value"] for r in runs]))
+        cpu["sample"] = f"{len(runs)} x " + cpu["sample"]
+        value = cpu["value"]
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s/root", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * float(np.mean([r["wall_s"] for r in runs])),
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": cfgname, "nocc": o, "nvir": v, "naux": q,
+                                                "kind": kind, "order": c["order"], "x": c["x"],
+                                                "nroots": c["nroots"]},
+                "cpu_baseline": cpu,
+                "e2e": {"value": value, "unit": "s/root", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
     spr = ORACLE_SIGMA_VECTORS_PER_ROOT.get(cfgname, 40.0)
     note = ("FP64 Davidson count of this workload" if cfgname in ORACLE_SIGMA_VECTORS_PER_ROOT
             else "assumed 40")
@@ -1024,7 +1093,16 @@ def main():
 
     cpu = None
     parity = None
-    if rank == 0 and world == 1 and args.cpu_rows > 0:
+    if rank == 0 and world == 1 and args.cpu_rows > 0 and oracle_solve_feasible(args.config):
+        # the oracle's whole solve of the same workload: its time and its eigenvalues
+        cpu = oracle_davidson_baseline(args.config)
+        ref_w = np.asarray(cpu["omega"])
+        parity = {"oracle_eigenvalues": cpu["omega"],
+                  "max_abs_diff_mixed_davidson": float(np.abs(np.asarray(om) - ref_w).max()),
+                  "max_abs_diff_fp64_davidson": (float(np.abs(np.asarray(om64) - ref_w).max())
+                                                 if fp64 is not None else None)}
+        log("oracle solve", parity)
+    elif rank == 0 and world == 1 and args.cpu_rows > 0:
         smp = oracle_rows_pool(("config", args.config), kind, order, x, 1, args.cpu_rows)
         try:
             parity = sampled_parity(ctx, (smp["X"], smp["idx"], smp["R"]), ("fp64", args.mixed, "sliced"))

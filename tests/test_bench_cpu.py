@@ -80,6 +80,31 @@ def test_reference_arm_line():
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "ip3_o8_v24_q96"
+    # small enough for the oracle's whole solve: timed, not extrapolated, and
+    # its eigenvalues are the lowest of the explicit matrix
+    cb = d["cpu_baseline"]
+    assert "not extrapolated" in cb["sample"] and cb["iterations"] > 0 and cb["max_residual"] <= 1e-8
+    assert abs(d["value"] - cb["wall_s"] / 4) < 1e-9 * d["value"]
+    import numpy as np
+    from oracle import adc
+    from synthetic import config_problem
+    p = config_problem("ip3_o8_v24_q96")
+    w = np.linalg.eigvalsh(adc.explicit_matrix("IP", 3, 1.0, p.B, p.eps_occ, p.eps_vir))[:4]
+    assert np.abs(np.asarray(cb["omega"]) - w).max() < 1e-10
+
+
+def test_reference_arm_rows_line():
+    """A workload too large for the oracle's whole solve (one EA problem of the
+    batched workload): oracle rows on the host cores, scaled to s/root."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--config", "batch64_ipea", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
+    cb = d["cpu_baseline"]
+    assert d["impl"] == "reference" and d["value"] == cb["value"] > 0
+    assert cb["threads_per_process"] == 1 and cb["cores"] >= 1 and "rows" in cb["sample"]
+    assert d["config"]["kind"] == "EA"
 
 
 def _reduce_rank(rank, world, port, out):
