@@ -194,13 +194,23 @@ def _pair(p, q, n):
     return p * n - p * (p + 1) // 2 + (q - p - 1)
 
 
-# Sigma vectors per root that the plain FP64 block Davidson (the CPU oracle's
-# algorithm, run on the GPU in FP64) spends on each workload to the bench's
-# residual tolerance; both oracle legs scale seconds per sigma row to seconds
-# per root with the same number. Measured: ea2x3, 333 FP64 sigma vectors for
-# 8 roots (its tolerance, 1e-6); the EE workloads use their mixed solves' counts.
-ORACLE_SIGMA_VECTORS_PER_ROOT = {"ea2x3_o40_v200_q1200": 41.625, "ee2x3_o30_v150_q900": 110.0,
-                                 "ee3_o60_v300_q1800": 40.0}
+# Sigma vectors per root that scale both oracle legs' seconds per sigma row to
+# seconds per root (one number per workload for both legs), with where it comes
+# from: the FP64 block Davidson (the oracle's algorithm, run on the GPU in FP64)
+# where it was measured, else the closest measured count, else an assumption.
+ORACLE_SIGMA_VECTORS_PER_ROOT = {
+    "ea2x3_o40_v200_q1200": (41.625, "FP64 Davidson count of this workload at its tolerance "
+                                     "(333 sigma vectors for 8 roots)"),
+    "ee2x3_o30_v150_q900": (110.0, "mixed Davidson count of this workload (440 sigma vectors for 4 roots, "
+                                   "residual 1e-6); its FP64 Davidson was not run to the end"),
+    "ee3_o60_v300_q1800": (40.0, "assumed: no solve of this workload has run to the end"),
+}
+
+
+def sigma_vectors_per_root(cfgname, default=None):
+    """(sigma vectors per root, where the number comes from) for a workload,
+    or `default` (a pair, or None) when none is recorded."""
+    return ORACLE_SIGMA_VECTORS_PER_ROOT.get(cfgname, default)
 
 
 def pick_rows(kind, o, v, n_rows, seed):
@@ -623,10 +633,7 @@ def run_ee(args, cfgname):
         except Exception as exc:  # the check reports, it never stops the run
             parity = {"error": str(exc)[:200]}
         log("sampled parity", parity)
-        spr = ORACLE_SIGMA_VECTORS_PER_ROOT.get(cfgname)
-        note = "FP64 Davidson count of this workload"
-        if spr is None:
-            spr, note = st["sigma_calls"] / nroots, "this run's mixed solve"
+        spr, note = sigma_vectors_per_root(cfgname, (st["sigma_calls"] / nroots, "this run's mixed solve"))
         cpu = cpu_baseline_of(smp, ctx.N, spr, note, "EE")
     fns = None
     if cfg.get("fns_eta") is not None:
@@ -753,9 +760,7 @@ def run_reference(args, cfgname):
                 "e2e": {"value": value, "unit": "s/root", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
-    spr = ORACLE_SIGMA_VECTORS_PER_ROOT.get(cfgname, 40.0)
-    note = ("FP64 Davidson count of this workload" if cfgname in ORACLE_SIGMA_VECTORS_PER_ROOT
-            else "assumed 40")
+    spr, note = sigma_vectors_per_root(cfgname, (40.0, "assumed 40"))
     cores = os.cpu_count() or 1
     # warm-up: the oracle modules imported, no timing
     for _ in range(args.warmup):
@@ -1109,10 +1114,8 @@ def main():
         except Exception as exc:  # the check reports, it never stops the run
             parity = {"error": str(exc)[:200]}
         log("sampled parity", parity)
-        spr = ORACLE_SIGMA_VECTORS_PER_ROOT.get(args.config)
-        note = "FP64 Davidson count of this workload"
-        if spr is None:
-            spr, note = np.mean([s["sigma_calls"] for s in stats]) / nroots, "this run's mixed solve"
+        spr, note = sigma_vectors_per_root(
+            args.config, (np.mean([s["sigma_calls"] for s in stats]) / nroots, "this run's mixed solve"))
         cpu = cpu_baseline_of(smp, ctx.N, spr, note, kind)
         cpu["gpu_mixed_sigma_vectors_per_root"] = float(np.mean([s["sigma_calls"] for s in stats]) / nroots)
 

@@ -136,3 +136,14 @@ def test_reduce_across_replicas_on_gloo(world):
         mx, sm = out[r]
         assert mx == [10.0 + world - 1, 3.5 * world]
         assert sm == [float(sum(100 + q for q in range(world)))]
+
+
+def test_sigma_vectors_per_root_sources():
+    """Each recorded scale names where it comes from; unknown workloads take the default."""
+    spr, note = bench.sigma_vectors_per_root("ea2x3_o40_v200_q1200")
+    assert abs(spr - 333 / 8) < 1e-12 and "FP64 Davidson" in note
+    spr, note = bench.sigma_vectors_per_root("ee2x3_o30_v150_q900")
+    assert abs(spr - 440 / 4) < 1e-12 and "mixed" in note
+    assert "assumed" in bench.sigma_vectors_per_root("ee3_o60_v300_q1800")[1]
+    assert bench.sigma_vectors_per_root("nope", (7.0, "x")) == (7.0, "x")
+    assert bench.sigma_vectors_per_root("nope") is None
