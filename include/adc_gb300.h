@@ -371,7 +371,7 @@ int adc_cholesky(const double *V, int64_t n, double tau, int64_t max_rank, doubl
 int adc_cholesky_mo(const double *L, int64_t rank, int64_t nao, const adc_c128 *C, int64_t nmo, adc_c128 *B);
 
 /* ------------------------------------------------------------------------
- * State-specific frozen natural spinors (Sec. 2.3, Eqs. 31-32), EA and EE.
+ * State-specific frozen natural spinors (Sec. 2.4, Eqs. 31-32), EA and EE.
  * ---------------------------------------------------------------------- */
 
 /* Virtual density of one state, D_ab = <Psi| a+_b a_a |Psi>, with |Psi> the

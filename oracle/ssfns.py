@@ -1,4 +1,4 @@
-"""State-specific frozen natural spinors (oracle), Sec. 2.3, Eqs. 31-32.
+"""State-specific frozen natural spinors (oracle), Sec. 2.4, Eqs. 31-32.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 

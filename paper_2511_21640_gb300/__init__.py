@@ -629,7 +629,7 @@ def batch_solve(problems, nroots, tol=1e-6, max_iter=300, precision="bf16x3", me
 def ssfns(B, eps_occ, eps_vir, kind="EA", order=3, x=1.0, nroots=1, eta_crit=1e-5, tol=1e-8, max_iter=300,
           precision="fp64", refine="fp64"):
     """State-specific natural-spinor energies of the nroots lowest EA/EE roots (``adc_ssfns``,
-    Sec. 2.3, Eqs. 31-32): a list of dicts (omega_corrected, omega_fns, omega2_canonical, omega2_fns,
+    Sec. 2.4, Eqs. 31-32): a list of dicts (omega_corrected, omega_fns, omega2_canonical, omega2_fns,
     err64, n_keep, status)."""
     B = np.ascontiguousarray(B, dtype=np.complex128)
     eo = np.ascontiguousarray(eps_occ, dtype=np.float64)

@@ -1,4 +1,4 @@
-// State-specific frozen natural spinors for EA and EE (Sec. 2.3, Eqs. 31-32).
+// State-specific frozen natural spinors for EA and EE (Sec. 2.4, Eqs. 31-32).
 //
 // For root k of the canonical ADC(2) problem with eigenvector y, the state's
 // virtual density is that of the excited configurations weighted by y (the

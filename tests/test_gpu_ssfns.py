@@ -1,4 +1,4 @@
-"""State-specific natural spinors on the GPU (Sec. 2.3, Eqs. 31-32) against the
+"""State-specific natural spinors on the GPU (Sec. 2.4, Eqs. 31-32) against the
 oracle (oracle/ssfns.py): the state density (1e-12), the natural spinors of
 D^MP2 + D^state (as the MP2 ones: occupations 1e-12, semicanonical energies
 1e-10, kept projector 1e-9), the carried-over guess for a given U (1e-12),

@@ -1,4 +1,4 @@
-"""Pins of the state-specific natural-spinor oracle (Sec. 2.3, Eqs. 31-32).
+"""Pins of the state-specific natural-spinor oracle (Sec. 2.4, Eqs. 31-32).
 
 * The closed-form state density equals <Psi| a+_b a_a |Psi> of the weighted
   configurations evaluated in determinant space (EA: N+1 electrons, EE: N).
