@@ -1,0 +1,206 @@
+"""bench.py's GPU leg run against a stand-in for the device library (no GPU).
+
+The stand-in answers the calls the bench makes (context, Davidson, sigma,
+profile, launch counter, FP64 probe) with the explicit matrix of the small
+IP-ADC(3) workload, or with a diagonal matrix of the default workload's
+dimension, and torch's CUDA entry points are replaced by host no-ops. Nothing here measures anything: the test checks that the bench's
+orchestration runs to the end and that its JSON line carries every key of
+the benchmark contract with consistent types and values.
+"""
+import io
+import json
+import os
+import sys
+import time
+import types
+from contextlib import redirect_stdout
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from synthetic import CONFIGS, config_problem  # noqa: E402
+
+CFG = "ip3_o8_v24_q96"
+
+
+def _fake_library(cfg=CFG):
+    """Stand-in library: the explicit matrix of the small workload, or for a
+    large one a diagonal matrix of the right dimension (the bench only needs
+    answers of the right shape there)."""
+    from oracle import adc
+    c = CONFIGS[cfg]
+    if cfg == CFG:
+        p = config_problem(cfg)
+        M = adc.explicit_matrix(c["kind"], c["order"], c["x"], p.B, p.eps_occ, p.eps_vir)
+        w, V = np.linalg.eigh(M)
+        apply = lambda X: X @ M.T  # noqa: E731
+    else:
+        n = bench._dim(c["kind"], c["nocc"], c["nvir"])
+        d = np.linspace(0.5, 9.0, n)
+        w, V = d, None
+        apply = lambda X: X * d[None, :]  # noqa: E731
+    lib = types.ModuleType("paper_2511_21640_gb300")
+    lib.apply = apply
+    lib.launches = 0
+
+    class Context:
+        def __init__(self, B, eo, ev, kind="IP", order=3, x=1.0, **opts):
+            assert (kind, order, x) == (c["kind"], c["order"], c["x"])
+            self.N = w.shape[0]
+            self.prof = False
+            self.stats = {}
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *exc):
+            self.close()
+
+        def close(self):
+            pass
+
+        def _record(self, name, flops, nbytes=0.0):
+            lib.launches += 1
+            if self.prof:
+                e = self.stats.setdefault(name, {"name": name, "launches": 0, "total_ms": 0.0, "flops": 0.0,
+                                                 "bytes": 0.0})
+                e["launches"] += 1
+                e["total_ms"] += 0.5
+                e["flops"] += flops
+                e["bytes"] += nbytes
+
+        def sigma(self, X, precision="fp64"):
+            Xn = X.numpy() if torch.is_tensor(X) else np.asarray(X)
+            k = Xn.shape[0]
+            name = {"fp64": "zgemm_fp64/main", "bf16x3": "tc_bf16x3/sigma",
+                    "sliced": "tc_sliced/sigma"}.get(precision, "other")
+            self._record(name, 8.0 * k * self.N * self.N, 16.0 * k * self.N)
+            return torch.from_numpy(apply(Xn))
+
+        def davidson(self, nroots, tol=1e-8, max_iter=200, precision="fp64", want_vectors=True, **kw):
+            self._record("gram_fp64/extend", 8.0 * 40 * nroots * self.N, 16.0 * 48 * self.N)
+            self._record("combine_fp64", 8.0 * 40 * nroots * self.N, 16.0 * 48 * self.N)
+            st = {"iterations": 12, "sigma_calls": 4 * nroots, "sigma_calls_fp64": nroots,
+                  "sigma_calls_mid": 0, "iterations_fp64": 3}
+            if not want_vectors:
+                Y = None
+            elif V is not None:
+                Y = np.ascontiguousarray(V[:, :nroots].T)
+            else:
+                Y = np.zeros((nroots, self.N), np.complex128)
+                Y[np.arange(nroots), np.arange(nroots)] = 1.0
+            return w[:nroots].copy(), Y, np.full(nroots, 1e-10), st, 0
+
+        def profile(self, on=True):
+            self.prof = bool(on)
+            if on:
+                self.stats = {}
+
+        def profile_read(self):
+            return {k: dict(e) for k, e in self.stats.items()}
+
+    lib.Context = Context
+    lib.launch_count = lambda: lib.launches
+    lib.diag_fp64_peak = lambda blocks, iters: (1.26, 1.0)
+    return lib
+
+
+class _Event:
+    def __init__(self, enable_timing=False):
+        self.t = None
+
+    def record(self, stream=None):
+        self.t = time.perf_counter()
+
+    def elapsed_time(self, other):
+        return 1e3 * (other.t - self.t)
+
+
+def _patch_device(monkeypatch, lib):
+    monkeypatch.setitem(sys.modules, "paper_2511_21640_gb300", lib)
+    for name, val in {"set_device": lambda *a, **k: None, "set_stream": lambda *a, **k: None,
+                      "Stream": lambda *a, **k: object(), "synchronize": lambda *a, **k: None,
+                      "current_stream": lambda *a, **k: object(), "Event": _Event}.items():
+        monkeypatch.setattr(torch.cuda, name, val, raising=False)
+    monkeypatch.setattr(torch.Tensor, "cuda", lambda self, *a, **k: self)
+    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self, *a, **k: self)
+    monkeypatch.setattr(bench, "nvtx_range", lambda *a, **k: None)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+
+
+def _run_main(monkeypatch, argv):
+    monkeypatch.setattr(sys, "argv", ["bench.py", *argv])
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.main()
+    return json.loads([ln for ln in buf.getvalue().splitlines() if ln.startswith("{")][-1])
+
+
+def _check_contract(d):
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "clocks", "gpu_launches", "roofline",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["metric"] == bench.METRIC and d["unit"] == "s/root" and d["higher_is_better"] is False
+    assert d["scaling"] == "weak" and d["vs_baseline"] is None and d["data"] == "synthetic"
+    r = d["roofline"]
+    for key in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert key in r, key
+    assert r["bound"] in ("hbm", "tensor", "alu") and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    cb = d["cpu_baseline"]
+    for key in ("value", "unit", "cores", "kind", "sample"):
+        assert key in cb, key
+    assert cb["kind"] == "oracle" and cb["unit"] == "s/root" and cb["value"] > 0
+    for key in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
+        assert key in d["e2e"], key
+
+
+def test_bench_gpu_leg_line_against_a_stand_in(monkeypatch):
+    _patch_device(monkeypatch, _fake_library())
+    d = _run_main(monkeypatch, ["--config", CFG, "--steps", "2", "--warmup", "3"])
+    _check_contract(d)
+
+    assert (d["n_gpus"], d["steps"], d["warmup"]) == (1, 2, 3)
+    assert d["config"]["workload"] == CFG
+    assert d["value"] > 0 and abs(d["value"] - d["ms_per_step"] / 1e3 / CONFIGS[CFG]["nroots"]) < 1e-12
+    assert d["gpu_launches"] == 2 * 2  # two solves in the timed region, two recorded launches each
+    e = d["e2e"]
+    p = config_problem(CFG)
+    assert e["h2d_bytes_per_step"] == p.B.nbytes + 8 * (p.nocc + p.nvir)
+    assert e["d2h_bytes_per_step"] == 16 * CONFIGS[CFG]["nroots"]
+    # the small workload's oracle solve: its eigenvalues against the stand-in's (the explicit matrix)
+    assert d["sampled_parity"]["max_abs_diff_mixed_davidson"] < 1e-10
+    assert d["sigma"]["rel_diff_mixed_vs_fp64"] == 0.0
+
+
+def test_bench_default_workload_line_against_a_stand_in(monkeypatch):
+    """The default workload (EA-ADC(2)+x(3), o=40, v=200, Q=1200) takes the
+    oracle-rows branch of the CPU baseline; the rows come from the stand-in
+    here, so only the orchestration and the line are checked."""
+    cfg = "ea2x3_o40_v200_q1200"
+    lib = _fake_library(cfg)
+    _patch_device(monkeypatch, lib)
+
+    def rows_pool(spec, kind, order, x, dd_order, n_rows, seed=5, xseed=5, workers=None):
+        c = CONFIGS[cfg]
+        rows, idx = bench.pick_rows(kind, c["nocc"], c["nvir"], n_rows, seed)
+        X = bench.random_vectors(bench._dim(kind, c["nocc"], c["nvir"]), 1, seed=xseed)
+        R = lib.apply(X)[:, idx]
+        return {"X": X, "idx": idx, "R": R, "wall_s": 2.0, "row_s": 2.0, "workers": 2, "rows": n_rows}
+
+    monkeypatch.setattr(bench, "oracle_rows_pool", rows_pool)
+    d = _run_main(monkeypatch, ["--steps", "1", "--warmup", "3", "--cpu-rows", "4"])
+    _check_contract(d)
+    assert d["config"]["workload"] == cfg and d["config"]["N"] == 796200
+    cb = d["cpu_baseline"]
+    spr, _ = bench.sigma_vectors_per_root(cfg)
+    assert abs(cb["value"] - 2.0 / 4 * 796200 * spr) < 1e-6 * cb["value"]
+    assert d["sampled_parity"]["fp64"]["max_abs_err"] == 0.0
+    assert d["e2e"]["h2d_bytes_per_step"] == 16 * 1200 * 240 ** 2 + 8 * 240
