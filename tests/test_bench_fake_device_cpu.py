@@ -204,3 +204,46 @@ def test_bench_default_workload_line_against_a_stand_in(monkeypatch):
     assert abs(cb["value"] - 2.0 / 4 * 796200 * spr) < 1e-6 * cb["value"]
     assert d["sampled_parity"]["fp64"]["max_abs_err"] == 0.0
     assert d["e2e"]["h2d_bytes_per_step"] == 16 * 1200 * 240 ** 2 + 8 * 240
+
+
+def _replica_rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK="0")
+    mp_ = pytest.MonkeyPatch()
+    try:
+        _patch_device(mp_, _fake_library())
+        os.environ.update(RANK=str(rank), WORLD_SIZE=str(world))  # _patch_device cleared them
+        init = dist.init_process_group
+        mp_.setattr(dist, "init_process_group", lambda backend, *a, **k: init("gloo", *a, **k))
+        mp_.setattr(sys, "argv", ["bench.py", "--config", CFG, "--steps", "2", "--warmup", "3"])
+        buf = io.StringIO()
+        with redirect_stdout(buf):
+            bench.main()
+        out[rank] = buf.getvalue()
+    finally:
+        mp_.undo()
+
+
+def test_bench_replicas_on_gloo_ranks():
+    """Two replicas (torchrun's environment, gloo standing in for NCCL): only
+    rank 0 prints, the line is whole-job (n_gpus 2, the launches of both
+    replicas, s/root over both replicas' roots) and carries no CPU baseline
+    (that one runs at one GPU only)."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = mp.Manager().dict()
+    mp.spawn(_replica_rank, args=(2, port, out), nprocs=2, join=True)
+    lines0 = [ln for ln in out[0].splitlines() if ln.startswith("{")]
+    assert len(lines0) == 1 and not [ln for ln in out[1].splitlines() if ln.startswith("{")]
+    d = json.loads(lines0[0])
+    assert d["n_gpus"] == 2 and d["config"]["replicas"] == 2
+    assert d["gpu_launches"] == 2 * 2 * 2  # two replicas, two solves each, two recorded launches each
+    assert abs(d["value"] - d["ms_per_step"] / 1e3 / (2 * CONFIGS[CFG]["nroots"])) < 1e-12
+    assert d["cpu_baseline"] is None
+    e = d["e2e"]
+    assert e["h2d_bytes_per_step"] == 2 * (config_problem(CFG).B.nbytes + 8 * 32)
+    assert "replicas" in e["includes"]
