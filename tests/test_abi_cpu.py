@@ -26,7 +26,8 @@ def _declared():
     names = set()
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
-            txt = open(os.path.join(ROOT, "include", fn)).read()
+            with open(os.path.join(ROOT, "include", fn)) as fh:
+                txt = fh.read()
             names |= set(re.findall(r"\b(adc_[a-z0-9_]+)\s*\(", txt))
     return names
 

@@ -19,7 +19,8 @@ OCC = set("ijklMNOPRSTW")
 
 
 def _table(name, src=SRC):
-    text = open(src).read()
+    with open(src) as fh:
+        text = fh.read()
     m = re.search(r"const Rows " + name + r" = \{(.*?)\};", text, re.S)
     assert m, name
     return re.findall(r'\{"([^"]+)",\s*"([^"]+)"\}', m.group(1))

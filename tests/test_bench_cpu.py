@@ -130,7 +130,7 @@ def test_reduce_across_replicas_on_gloo(world):
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_reduce_rank, args=(world, port, out), nprocs=world, join=True)
     for r in range(world):
         mx, sm = out[r]

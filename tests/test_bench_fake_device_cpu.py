@@ -235,7 +235,7 @@ def test_bench_replicas_on_gloo_ranks():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_replica_rank, args=(2, port, out), nprocs=2, join=True)
     lines0 = [ln for ln in out[0].splitlines() if ln.startswith("{")]
     assert len(lines0) == 1 and not [ln for ln in out[1].splitlines() if ln.startswith("{")]
