@@ -57,3 +57,18 @@ def test_cuda_sources_include_only_the_package_and_the_public_headers():
 
 def test_generators_import_only_numpy():
     assert _imports(os.path.join(ROOT, "synthetic", "__init__.py")) <= {"__future__", "numpy"}
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: the binding, copied without its compiled library,
+    refuses to import."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / PKG
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, PKG, "__init__.py"), pkg / "__init__.py")
+    out = subprocess.run([sys.executable, "-c", f"import {PKG}"], cwd=tmp_path, capture_output=True, text=True,
+                         env={**os.environ, "PYTHONPATH": str(tmp_path)}, timeout=300)
+    assert out.returncode != 0
+    assert "ImportError" in out.stderr and "libadc_gb300.so is missing" in out.stderr
