@@ -136,3 +136,31 @@ def test_property_calls_need_a_context(lib):
     assert L.adc_excited_density(None, p, 1, p) == -7
     assert L.adc_transition_density(None, p, 1, p) == -7
     assert L.adc_memory(None, p, p) == -7
+
+
+def _prototypes():
+    """name -> number of parameters of every function declared in include/*.h."""
+    out = {}
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        with open(os.path.join(ROOT, "include", fn)) as fh:
+            txt = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for m in re.finditer(r"\b(adc_[a-z0-9_]+)\s*\(([^;{}]*?)\)\s*;", txt):
+            params = m.group(2).strip()
+            out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header(lib):
+    """Every function the binding declares to ctypes takes as many arguments
+    as its C prototype (an argument added on one side only would pass garbage)."""
+    protos = _prototypes()
+    checked = 0
+    for name, n in protos.items():
+        f = getattr(lib.lib, name, None)
+        if f is None or f.argtypes is None:
+            continue
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+        checked += 1
+    assert checked == len(protos), (checked, len(protos))
