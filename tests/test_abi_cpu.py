@@ -146,21 +146,42 @@ def _prototypes():
             continue
         with open(os.path.join(ROOT, "include", fn)) as fh:
             txt = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
-        for m in re.finditer(r"\b(adc_[a-z0-9_]+)\s*\(([^;{}]*?)\)\s*;", txt):
-            params = m.group(2).strip()
-            out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+        for m in re.finditer(r"(const\s+char\s*\*|void|int64_t|int)\s+(adc_[a-z0-9_]+)\s*\(([^;{}]*?)\)\s*;",
+                             txt):
+            params = m.group(3).strip()
+            ret = {"void": None, "int64_t": "i64", "int": "i"}.get(m.group(1), "p")
+            out[m.group(2)] = (ret, [] if params in ("", "void") else [_c_kind(q) for q in params.split(",")])
     return out
 
 
+def _c_kind(param):
+    """Kind of a C parameter: pointer, int64, uint64, int or double."""
+    if "*" in param:
+        return "p"
+    for c_t, kind in (("uint64_t", "u64"), ("int64_t", "i64"), ("double", "d"), ("int", "i")):
+        if re.search(r"\b" + c_t + r"\b", param):
+            return kind
+    raise AssertionError(f"unknown parameter type: {param!r}")
+
+
+def _ctypes_kind(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type):
+        return "p"
+    return {ctypes.c_int64: "i64", ctypes.c_uint64: "u64", ctypes.c_int: "i", ctypes.c_double: "d"}[t]
+
+
 def test_binding_signatures_match_the_header(lib):
-    """Every function the binding declares to ctypes takes as many arguments
-    as its C prototype (an argument added on one side only would pass garbage)."""
+    """Every function the binding declares to ctypes takes the arguments of its
+    C prototype, in number and kind (pointer, 64-bit integer, int, double), and
+    returns its kind: an argument added or retyped on one side only would pass
+    garbage."""
     protos = _prototypes()
     checked = 0
-    for name, n in protos.items():
+    for name, (ret, kinds) in protos.items():
         f = getattr(lib.lib, name, None)
         if f is None or f.argtypes is None:
             continue
-        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+        assert [_ctypes_kind(t) for t in f.argtypes] == kinds, (name, f.argtypes, kinds)
+        assert (None if f.restype is None else _ctypes_kind(f.restype)) == ret, (name, f.restype, ret)
         checked += 1
     assert checked == len(protos), (checked, len(protos))
