@@ -146,10 +146,10 @@ def _prototypes():
             continue
         with open(os.path.join(ROOT, "include", fn)) as fh:
             txt = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
-        for m in re.finditer(r"(const\s+char\s*\*|void|int64_t|int)\s+(adc_[a-z0-9_]+)\s*\(([^;{}]*?)\)\s*;",
+        for m in re.finditer(r"(const\s+char\s*\*|\bvoid\s|\bint64_t\s|\bint\s)\s*(adc_[a-z0-9_]+)\s*\(([^;{}]*?)\)\s*;",
                              txt):
             params = m.group(3).strip()
-            ret = {"void": None, "int64_t": "i64", "int": "i"}.get(m.group(1), "p")
+            ret = {"void": None, "int64_t": "i64", "int": "i"}.get(m.group(1).strip(), "p")
             out[m.group(2)] = (ret, [] if params in ("", "void") else [_c_kind(q) for q in params.split(",")])
     return out
 
@@ -184,4 +184,4 @@ def test_binding_signatures_match_the_header(lib):
         assert [_ctypes_kind(t) for t in f.argtypes] == kinds, (name, f.argtypes, kinds)
         assert (None if f.restype is None else _ctypes_kind(f.restype)) == ret, (name, f.restype, ret)
         checked += 1
-    assert checked == len(protos), (checked, len(protos))
+    assert checked == len(protos) == len(_declared()), (checked, len(protos))
