@@ -2,8 +2,9 @@
 
 The stand-in answers the calls the bench makes (context, Davidson, sigma,
 profile, launch counter, FP64 probe) with the explicit matrix of the small
-IP-ADC(3) workload, or with a diagonal matrix of the default workload's
-dimension, and torch's CUDA entry points are replaced by host no-ops. Nothing here measures anything: the test checks that the bench's
+IP-ADC(3) workload, or with a diagonal matrix of a larger workload's
+dimension (the default EA workload, a small EE one), and torch's CUDA entry
+points are replaced by host no-ops. Nothing here measures anything: the test checks that the bench's
 orchestration runs to the end and that its JSON line carries every key of
 the benchmark contract with consistent types and values.
 """
@@ -51,7 +52,8 @@ def _fake_library(cfg=CFG):
 
     class Context:
         def __init__(self, B, eo, ev, kind="IP", order=3, x=1.0, **opts):
-            assert (kind, order, x) == (c["kind"], c["order"], c["x"])
+            # (the gradient check's contexts move x by a finite-difference step)
+            assert (kind, order) == (c["kind"], c["order"]) and abs(x - c["x"]) < 1e-3
             self.N = w.shape[0]
             self.prof = False
             self.stats = {}
@@ -104,6 +106,14 @@ def _fake_library(cfg=CFG):
 
         def profile_read(self):
             return {k: dict(e) for k, e in self.stats.items()}
+
+        def memory(self):
+            return {"in_use": 1 << 30, "peak": 2 << 30}
+
+        def sigma_adjoint(self, Y, wts):
+            self._record("adjoint_fp64", 1.0)
+            p = config_problem(cfg)
+            return np.zeros_like(p.B), np.zeros(p.nocc), np.zeros(p.nvir), 0.0
 
     lib.Context = Context
     lib.launch_count = lambda: lib.launches
@@ -247,3 +257,28 @@ def test_bench_replicas_on_gloo_ranks():
     e = d["e2e"]
     assert e["h2d_bytes_per_step"] == 2 * (config_problem(CFG).B.nbytes + 8 * 32)
     assert "replicas" in e["includes"]
+
+
+def test_bench_ee_leg_line_against_a_stand_in(monkeypatch):
+    """The EE leg (EE-ADC(2)+x(3), o=12, v=60, Q=360) with warm-up solves, the
+    gradient check and the oracle-rows baseline (rows from the stand-in)."""
+    cfg = "ee2x3_o12_v60_q360"
+    lib = _fake_library(cfg)
+    _patch_device(monkeypatch, lib)
+
+    def rows_pool(spec, kind, order, x, dd_order, n_rows, seed=5, xseed=5, workers=None):
+        c = CONFIGS[cfg]
+        rows, idx = bench.pick_rows(kind, c["nocc"], c["nvir"], n_rows, seed)
+        X = bench.random_vectors(bench._dim(kind, c["nocc"], c["nvir"]), 1, seed=xseed)
+        return {"X": X, "idx": idx, "R": lib.apply(X)[:, idx], "wall_s": 1.0, "row_s": 1.0, "workers": 2,
+                "rows": n_rows}
+
+    monkeypatch.setattr(bench, "oracle_rows_pool", rows_pool)
+    d = _run_main(monkeypatch, ["--config", cfg, "--warmup", "3", "--cpu-rows", "4"])
+    _check_contract(d)
+    assert d["warmup"] == 3 and d["config"]["workload"] == cfg
+    e = d["e2e"]
+    p = config_problem(cfg)
+    assert e["h2d_bytes_per_step"] == p.B.nbytes + 8 * (p.nocc + p.nvir)
+    assert abs(e["value"] - (e["init_s"] + e["operators_s"] + e["first_solve_s"]) / 4) < 1e-12
+    assert d["gradient"]["fd_step"] == 1e-5 and d["sampled_parity"]["fp64"]["max_abs_err"] == 0.0
