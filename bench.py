@@ -437,8 +437,9 @@ def run_batch(args, cfgname):
     """Batched IP/EA workload: the problems are planned into waves that fit the
     device memory; each wave is initialised, its batched split-precision sigma
     is timed (graph replays, and the grouped tensor-core kernel alone), and it
-    is solved with the batched Davidson. value = Davidson seconds per root over
-    all problems; e2e adds the adc_init calls (host inputs copied inside)."""
+    is solved with the batched Davidson after --warmup warm-up solves. value =
+    Davidson seconds per root over all problems; e2e is the adc_init calls
+    (host inputs copied inside) plus the first solve of each wave."""
     import torch
     import paper_2511_21640_gb300 as adcgpu
     c = BATCH_CONFIGS[cfgname]
@@ -448,7 +449,7 @@ def run_batch(args, cfgname):
     free = torch.cuda.mem_get_info()[0]
     nw, order, wave, mem, cost = adcgpu.batch_plan(sizes, nroots, int(0.85 * free))
     log(f"{len(sizes)} problems in {nw} waves")
-    tot = dict(init_s=0.0, solve_s=0.0, sig_ms=0.0, sig_flops=0.0, g_ms=0.0, g_flops=0.0, g_launch=0,
+    tot = dict(init_s=0.0, solve_s=0.0, first_solve_s=0.0, sig_ms=0.0, sig_flops=0.0, g_ms=0.0, g_flops=0.0, g_launch=0,
                batches=0, graph_launches=0, sigma_calls=0, sigma_calls_fp64=0, iters=[])
     omegas, errs, status_all = {}, {}, {}
     batch_parity = []
@@ -510,13 +511,22 @@ def run_batch(args, cfgname):
             i3 = b.info()
             tot["sig_ms"] += i3["batch_ms"] - i2["batch_ms"]
             tot["sig_flops"] += i3["tc_flops"] - i2["tc_flops"]
-            i2 = i3
             del Xs, Ss
+            # warm-up solves of the wave (each starts from scratch); the first one
+            # closes the end-to-end figure
+            first = None
+            for _ in range(args.warmup):
+                tw = time.perf_counter()
+                b.davidson(nroots, tol=tol, max_iter=300, precision="bf16x3")
+                first = time.perf_counter() - tw if first is None else first
+            i2 = b.info()
             torch.cuda.synchronize()
             l0 = adcgpu.launch_count()
             t1 = time.perf_counter()
             om, e64, st_codes, sts, rc = b.davidson(nroots, tol=tol, max_iter=300, precision="bf16x3")
-            tot["solve_s"] += time.perf_counter() - t1
+            dt = time.perf_counter() - t1
+            tot["solve_s"] += dt
+            tot["first_solve_s"] += dt if first is None else first
             tot["launches"] = tot.get("launches", 0) + adcgpu.launch_count() - l0
             i3 = b.info()
             tot["batches"] += i3["batches"] - i2["batches"]
@@ -560,10 +570,11 @@ def run_batch(args, cfgname):
                      "batched_products": tot["batches"], "graph_replays": tot["graph_launches"],
                      "max_err64": max(errs.values()), "status_nonzero": [i for i, s in status_all.items() if s]},
         "init_s": tot["init_s"],
-        "e2e": {"value": (tot["init_s"] + tot["solve_s"]) / roots, "unit": "s/root",
+        "e2e": {"value": (tot["init_s"] + tot["first_solve_s"]) / roots, "unit": "s/root",
                 "h2d_bytes_per_step": int(sum(16 * d["naux"] * (d["nocc"] + d["nvir"]) ** 2 for d in sizes)),
                 "d2h_bytes_per_step": int(16 * roots),
-                "includes": f"adc_init of every problem (H2D copy + {args.e2e_setup} operator setup) + batched Davidson"},
+                "includes": f"adc_init of every problem (H2D copy + {args.e2e_setup} operator setup) + the first "
+                            "batched Davidson of each wave"},
         "gpu_launches": int(tot.get("launches", 0)), "cpu_baseline": None,
     }
     print(json.dumps(line))
