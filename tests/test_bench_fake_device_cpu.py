@@ -282,3 +282,78 @@ def test_bench_ee_leg_line_against_a_stand_in(monkeypatch):
     assert e["h2d_bytes_per_step"] == p.B.nbytes + 8 * (p.nocc + p.nvir)
     assert abs(e["value"] - (e["init_s"] + e["operators_s"] + e["first_solve_s"]) / 4) < 1e-12
     assert d["gradient"]["fd_step"] == 1e-5 and d["sampled_parity"]["fp64"]["max_abs_err"] == 0.0
+
+
+def test_bench_batched_leg_line_against_a_stand_in(monkeypatch):
+    """The batched leg over four small problems (two waves) with a stand-in
+    batch: warm-up solves, one timed solve per wave, the line's keys."""
+    from synthetic import make_problem
+    sizes = [dict(kind="IP" if i % 2 == 0 else "EA", nocc=3 + i, nvir=8 + i, naux=6 * (8 + i), order=3, x=0.5,
+                  seed=i) for i in range(4)]
+    monkeypatch.setattr(bench, "batch_sizes", lambda name, n=None: sizes)
+    monkeypatch.setattr(bench, "batch_problems", lambda name, n=None, select=None: [
+        make_problem(sizes[i]["nocc"], sizes[i]["nvir"], sizes[i]["naux"], seed=i, kind=sizes[i]["kind"], x=0.5)
+        for i in (range(len(sizes)) if select is None else select)])
+    lib = types.ModuleType("paper_2511_21640_gb300")
+    lib.launches = 0
+    solves = []
+
+    class Context:
+        def __init__(self, B, eo, ev, kind="IP", order=3, x=1.0, **opts):
+            self.N = bench._dim(kind, len(eo), len(ev))
+            self.d = np.linspace(0.5, 5.0, self.N)
+
+        def sync(self):
+            pass
+
+        def close(self):
+            pass
+
+    class Batch:
+        def __init__(self, ctxs):
+            self.ctxs = ctxs
+            self.i = dict(grouped_ms=0.0, grouped_flops=0.0, grouped_launches=0, batch_ms=0.0, tc_flops=0.0,
+                          batches=0, graph_launches=0)
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *exc):
+            pass
+
+        def use_graphs(self, on=True):
+            pass
+
+        def sigma(self, Xs, precision="bf16x3", outs=None):
+            for c, X, S in zip(self.ctxs, Xs, outs):
+                S.copy_(torch.from_numpy(X.numpy() * c.d[None, :]))
+            for k, dv in (("grouped_ms", 1.0), ("grouped_flops", 1e12), ("grouped_launches", 1),
+                          ("batch_ms", 1.5), ("tc_flops", 1e12), ("batches", 1), ("graph_launches", 1)):
+                self.i[k] += dv
+            lib.launches += 1
+
+        def davidson(self, nroots, tol=1e-8, max_iter=200, precision="bf16x3"):
+            solves.append(len(self.ctxs))
+            lib.launches += 2
+            n = len(self.ctxs)
+            om = np.array([c.d[:nroots] for c in self.ctxs])
+            sts = [{"iterations": 10, "sigma_calls": 3 * nroots, "sigma_calls_fp64": nroots}] * n
+            return om, np.full((n, nroots), 1e-6), np.zeros(n, int), sts, 0
+
+        def info(self):
+            return dict(self.i)
+
+    lib.Context = Context
+    lib.Batch = Batch
+    lib.launch_count = lambda: lib.launches
+    lib.batch_plan = lambda sz, nroots, budget: (2, np.arange(len(sz)), np.array([0, 0, 1, 1]), None, None)
+    _patch_device(monkeypatch, lib)
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda *a: (64 << 30, 80 << 30), raising=False)
+    d = _run_main(monkeypatch, ["--config", "batch64_ipea", "--warmup", "3", "--cpu-rows", "0"])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "clocks", "gpu_launches", "roofline", "e2e"):
+        assert key in d, key
+    assert solves == [2, 2, 2, 2, 2, 2, 2, 2]  # per wave: three warm-up solves and the timed one
+    assert d["warmup"] == 3 and d["config"]["problems"] == 4 and d["config"]["waves"] == 2
+    assert d["gpu_launches"] == 2 * 2  # the two timed solves' launches only
+    assert d["e2e"]["value"] > 0 and "first batched Davidson" in d["e2e"]["includes"]
