@@ -129,6 +129,11 @@ CONFIGS = {
     # a smaller case of the same family, for quick runs of the same measurement
     "ee2x3_o12_v60_q360": dict(nocc=12, nvir=60, naux=360, seed=0, occ_range=(-3.0, -0.3),
                                vir_range=(0.1, 5.0), kind="EE", order=3, x=0.4, nroots=4, tol=1e-8),
+    # stretch shape: the EA workload with twice the virtual spinors, whose packed
+    # <ab||cd> (102 GB) is past the stored form, so the ladder is integral-direct
+    "ea2x3_o40_v400_q2000": dict(nocc=40, nvir=400, naux=2000, seed=0, occ_range=(-3.0, -0.3),
+                                 vir_range=(0.1, 5.0), kind="EA", order=3, x=0.5, nroots=8, tol=1e-6,
+                                 fp64_davidson=False),
 }
 
 
