@@ -16,9 +16,11 @@ def summarise(path):
     for r in rows:
         if r.get("Metric Name") != "gpu__time_duration.sum":
             continue
-        name = r["Kernel Name"].split("(")[0]
-        for pre in ("unnamed>::", "(anonymous namespace)::", "adc::"):
+        # namespaces first: "(anonymous namespace)" holds a parenthesis too
+        name = r["Kernel Name"]
+        for pre in ("(anonymous namespace)::", "<unnamed>::", "adc::"):
             name = name.replace(pre, "")
+        name = name.split("(")[0]
         scale = {"ns": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0, "msecond": 1.0}.get(r["Metric Unit"], 1e-6)
         a = agg[name]
         a[0] += 1

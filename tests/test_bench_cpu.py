@@ -147,3 +147,22 @@ def test_sigma_vectors_per_root_sources():
     assert "assumed" in bench.sigma_vectors_per_root("ee3_o60_v300_q1800")[1]
     assert bench.sigma_vectors_per_root("nope", (7.0, "x")) == (7.0, "x")
     assert bench.sigma_vectors_per_root("nope") is None
+
+
+def test_launch_list_summary(tmp_path):
+    """ncu_launches.py: per-kernel launch counts and device-time totals of an
+    ncu CSV launch list, units converted to ms, namespaces stripped, other
+    metrics and non-CSV lines ignored."""
+    import ncu_launches
+    hdr = '"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = ['"1","adc::(anonymous namespace)::k_gram<32, 8>(const double2 *)","gpu__time_duration.sum","us","1,500"\n',
+            '"2","adc::(anonymous namespace)::k_gram<32, 8>(const double2 *)","gpu__time_duration.sum","ms","2.5"\n',
+            '"3","k_tc_grouped(int)","gpu__time_duration.sum","ns","250000"\n',
+            '"3","k_tc_grouped(int)","dram__bytes_read.sum","byte","7"\n',
+            '"4","void adc::<unnamed>::k_combine<8>(const double2 *)","gpu__time_duration.sum","ms","1.0"\n']
+    f = tmp_path / "launches.csv"
+    f.write_text("==PROF== Connected to process\n" + hdr + "".join(rows))
+    agg = ncu_launches.summarise(str(f))
+    assert set(agg) == {"k_gram<32, 8>", "k_tc_grouped", "void k_combine<8>"}
+    assert agg["k_gram<32, 8>"][0] == 2 and abs(agg["k_gram<32, 8>"][1] - 4.0) < 1e-12
+    assert agg["k_tc_grouped"][0] == 1 and abs(agg["k_tc_grouped"][1] - 0.25) < 1e-12
