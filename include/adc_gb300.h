@@ -93,7 +93,11 @@ enum {
 typedef struct {
   int precision;        /* default precision of adc_davidson's mixed phase */
   void *stream;         /* cudaStream_t to run on; NULL = the context's own */
-  int block;            /* Davidson block size (new vectors per iteration), 0 = nroots */
+  int block;            /* Davidson block size kb, 0 = nroots: the starting
+                           space holds max(2 nroots, kb) unit vectors, the
+                           default subspace 8 kb; every iteration adds the
+                           corrections of the unconverged wanted roots (at
+                           most nroots vectors), also when kb > nroots */
   int max_subspace;     /* Davidson subspace limit, 0 = automatic: 8 x the
                            block (at least 40), lowered to what the device
                            memory left once the operators are built holds
